@@ -1,0 +1,144 @@
+"""Plain Kalman filters with the random-walk forecast -- test infrastructure.
+
+O1 `kf_dense`: Alg. standard (Sec. 2.1, Eqs. prediction, residualcovariance,
+kalmangain and the state update) with F_k = I (the random-walk assumption of
+Sec. 2.1), written with full N x N matrices.  The covariance update uses the
+gain form Sigma+ = Sigma- - K H Sigma-, which equals Eq. filtering
+(Sigma- ^-1 + H^T R^-1 H)^-1 by the Woodbury identity and needs no inverse of
+Sigma-.  The innovation negative log-likelihood of each step is
+    NLL_k = 1/2 (nu^T S^-1 nu + log det S + m log 2 pi),
+the Gaussian log-density of the innovation nu = y - H s_pred under N(0, S).
+
+O2 `kf_crosscov_rows`: the same filter for a fixed H, carried in the
+cross-covariance variables C = Sigma H^T (N x m), T = H Sigma H^T (m x m) and
+c = diag(Sigma).  Every N-indexed quantity is row-local, so the recursion can
+be run for any subset of rows; H s is tracked as its own m-vector.  Per step
+(Sigma- = Sigma + Gamma):
+    C- = C + G, T- = T + A, c- = c + diag(Gamma), S = T- + R,
+    z = S^-1 nu, s += C- z, Hs += T- z,
+    C = C- - C- S^-1 T-, T = T- - T- S^-1 T-, c = c- - rowsum(C- S^-1 * C-)
+with G = Gamma H^T and A = H Gamma H^T.
+
+Readings (the paper's wording is at odds with itself on these):
+  * time index: at step k the filter predicts from k-1 to k and updates with
+    y_k (the algorithms use y_k with H s_k);
+  * start: s_0 = mu_0 (default 0), Sigma_0|0 = alpha_0 Gamma (default 0, as in
+    the experiments of Sec. 4.1.1).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from scipy import linalg
+
+
+def _as_rvec(R, m):
+    R = np.asarray(R, dtype=np.float64)
+    return np.full(m, float(R)) if R.ndim == 0 else R
+
+
+def kf_dense(Gamma, steps, s0=None, alpha0=0.0, keep_cov=True):
+    """Run O1.  steps: iterable of (y (m,), H (m, N) dense, R scalar or (m,)).
+
+    Returns a list of dicts per step: s (posterior mean), Sigma (posterior
+    covariance, if keep_cov), var (its diagonal), nll.
+    """
+    N = Gamma.shape[0]
+    s = np.zeros(N) if s0 is None else np.array(s0, dtype=np.float64)
+    Sigma = alpha0 * Gamma.copy()
+    out = []
+    for y, H, R in steps:
+        m = H.shape[0]
+        Sigma_p = Sigma + Gamma  # predict with F = I
+        nu = y - H @ s
+        PHt = Sigma_p @ H.T
+        S = H @ PHt + np.diag(_as_rvec(R, m))
+        cf = linalg.cho_factor(S, lower=True)
+        z = linalg.cho_solve(cf, nu)
+        K = linalg.cho_solve(cf, PHt.T).T  # Sigma_p H^T S^-1
+        s = s + K @ nu
+        Sigma = Sigma_p - K @ PHt.T
+        Sigma = 0.5 * (Sigma + Sigma.T)
+        logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+        nll = 0.5 * (nu @ z + logdet + m * np.log(2.0 * np.pi))
+        rec = dict(s=s.copy(), var=np.diag(Sigma).copy(), nll=float(nll))
+        if keep_cov:
+            rec["Sigma"] = Sigma.copy()
+        out.append(rec)
+    return out
+
+
+def kf_information_form(Gamma, steps, alpha0=0.0):
+    """Covariances only, via Eq. filtering: Sigma+ = (Sigma-^-1 + H^T R^-1 H)^-1.
+    Used to pin O1 by a second, independent algebra (requires Sigma- SPD, i.e.
+    alpha0 + k > 0)."""
+    Sigma = alpha0 * Gamma.copy()
+    out = []
+    for _, H, R in steps:
+        m = H.shape[0]
+        Sigma_p = Sigma + Gamma
+        info = np.linalg.inv(Sigma_p) + H.T @ np.diag(1.0 / _as_rvec(R, m)) @ H
+        Sigma = np.linalg.inv(info)
+        Sigma = 0.5 * (Sigma + Sigma.T)
+        out.append(Sigma.copy())
+    return out
+
+
+def kf_crosscov_rows(G_rows, A, diag_gamma_rows, HG_full_rows_y, alpha0=0.0):
+    """Run O2 on a subset of rows for a fixed H.
+
+    G_rows: (n_rows, m) rows of G = Gamma H^T; A: (m, m) = H Gamma H^T;
+    diag_gamma_rows: (n_rows,) diag(Gamma) on those rows;
+    HG_full_rows_y: iterable of (y (m,), R scalar or (m,)).
+    Start: s_0 = 0 and Sigma_0 = alpha0 Gamma.
+    Returns per-step dicts: s_rows, var_rows, nll.
+    """
+    n, m = G_rows.shape
+    C = alpha0 * G_rows.copy()
+    T = alpha0 * A.copy()
+    c = alpha0 * np.array(diag_gamma_rows, dtype=np.float64)
+    s = np.zeros(n)
+    hs = np.zeros(m)
+    out = []
+    for y, R in HG_full_rows_y:
+        Cp = C + G_rows
+        Tp = T + A
+        cp = c + diag_gamma_rows
+        S = Tp + np.diag(_as_rvec(R, m))
+        cf = linalg.cho_factor(S, lower=True)
+        nu = y - hs
+        z = linalg.cho_solve(cf, nu)
+        s = s + Cp @ z
+        hs = hs + Tp @ z
+        SiT = linalg.cho_solve(cf, Tp)
+        SiCt = linalg.cho_solve(cf, Cp.T)
+        C = Cp - Cp @ SiT
+        T = Tp - Tp @ SiT
+        T = 0.5 * (T + T.T)
+        c = cp - np.einsum("ij,ji->i", Cp, SiCt)
+        logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+        nll = 0.5 * (nu @ z + logdet + m * np.log(2.0 * np.pi))
+        out.append(dict(s_rows=s.copy(), var_rows=c.copy(), nll=float(nll)))
+    return out
+
+
+def scalar_closed_form(gamma, h, rho, steps, alpha0=0.0):
+    """N = m = 1 random walk: Sigma_k = e_k gamma with e = alpha - d; the
+    predict adds 1 to e, the update maps e -> 1/(1/e + lam) with
+    lam = h^2 gamma / rho (the per-mode form of the D recurrence of
+    Alg. kalmanconstantH).  Returns the list of Sigma_k."""
+    lam = h * h * gamma / rho
+    e = alpha0
+    out = []
+    for _ in range(steps):
+        e = e + 1.0
+        e = 1.0 / (1.0 / e + lam)
+        out.append(e * gamma)
+    return out
+
+
+def scalar_steady_state(gamma, h, rho):
+    """Fixed point of the scalar recurrence: e = 1/(1/(e+1) + lam), i.e.
+    lam e^2 + lam e - 1 = 0 -> e = (-lam + sqrt(lam^2 + 4 lam)) / (2 lam)."""
+    lam = h * h * gamma / rho
+    return gamma * (-lam + np.sqrt(lam * lam + 4.0 * lam)) / (2.0 * lam)

@@ -1,0 +1,228 @@
+"""Pins for the CPU oracle and the input generators (no GPU).
+
+Each test checks the oracle against something other than itself: a closed
+form, a library routine, a second independent algebra, or brute force.
+"""
+
+import numpy as np
+import pytest
+from scipy import linalg, special, stats
+
+from oracle import covariance, kalman, matern, uq
+import synth
+
+
+# ----------------------------------------------------------------------------
+# Matern kernel (Sec. 2.2.1, Eq. maternfamily)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_matern_closed_forms_match_bessel_formula(nu):
+    """The nu = 1/2 and 3/2 closed forms equal the K_nu formula (scipy kv)."""
+    r = np.linspace(1e-4, 3.0, 400)
+    for ell in (0.05, 0.2, 1.0):
+        a = matern.matern(r, nu, ell, 2.5)
+        b = matern.matern_general(r, nu, ell, 2.5)
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-300)
+
+
+def test_matern_general_nu_5_2_textbook_form():
+    """nu = 5/2: sigma2 (1 + z + z^2/3) e^-z with z = sqrt(5) r / ell; also
+    C(0) = sigma2 (continuity at r = 0)."""
+    r = np.linspace(1e-6, 2.0, 100)
+    z = np.sqrt(5.0) * r / 0.3
+    ref = 1.7 * (1 + z + z * z / 3) * np.exp(-z)
+    np.testing.assert_allclose(matern.matern_general(r, 2.5, 0.3, 1.7), ref, rtol=1e-11)
+    assert matern.matern_general(np.array([0.0]), 2.5, 0.3, 1.7)[0] == 1.7
+    assert abs(matern.matern_general(np.array([1e-9]), 1.5, 0.3, 1.7)[0] - 1.7) < 1e-7
+
+
+# ----------------------------------------------------------------------------
+# ray tracer (Eq. lineartomography)
+# ----------------------------------------------------------------------------
+def test_ray_row_sums_equal_ray_lengths():
+    p0, p1 = synth.cross_well_geometry_2d(8, 4)
+    h = synth.trace_rays_2d(32, 32, p0, p1)
+    lengths = np.hypot(p1[:, 0] - p0[:, 0], p1[:, 1] - p0[:, 1])
+    sums = np.add.reduceat(h.val, h.rowptr[:-1])
+    np.testing.assert_allclose(sums, lengths, rtol=1e-14)
+    assert np.all(h.val > 0)
+    # columns sorted and unique within each row
+    for i in range(h.nrows):
+        c = h.col[h.rowptr[i] : h.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+def test_ray_through_cell_centres_and_along_grid_line():
+    # horizontal ray through a row of cell centres: length 1/nx in each cell
+    h = synth.trace_rays_2d(4, 4, np.array([[0, 0.375]]), np.array([[1, 0.375]]))
+    np.testing.assert_array_equal(h.col, [4, 5, 6, 7])
+    np.testing.assert_allclose(h.val, 0.25)
+    # a ray along the grid line y = 1/2 is shared equally by the two rows
+    h = synth.trace_rays_2d(4, 4, np.array([[0, 0.5]]), np.array([[1, 0.5]]))
+    np.testing.assert_array_equal(h.col, [4, 5, 6, 7, 8, 9, 10, 11])
+    np.testing.assert_allclose(h.val, 0.125)
+    # diagonal of the square through grid vertices: sqrt(2)/n in each diagonal cell
+    h = synth.trace_rays_2d(5, 5, np.array([[0, 0.0]]), np.array([[1, 1.0]]))
+    np.testing.assert_array_equal(h.col, [0, 6, 12, 18, 24])
+    np.testing.assert_allclose(h.val, np.sqrt(2) / 5)
+
+
+def test_ray_3d_row_sums():
+    p0, p1 = synth.cross_well_geometry_3d((2, 3), (3, 2))
+    h = synth.trace_rays_3d(6, 5, 4, p0, p1)
+    lengths = np.linalg.norm(p1 - p0, axis=1)
+    sums = np.add.reduceat(h.val, h.rowptr[:-1])
+    np.testing.assert_allclose(sums, lengths, rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# exact Gamma products
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(7, 5), (4, 3, 5), (16, 16)])
+def test_grid_fft_product_equals_dense(shape):
+    rng = np.random.default_rng(1)
+    pts = synth.grid_points_2d(*shape) if len(shape) == 2 else synth.grid_points_3d(*shape)
+    G = covariance.dense_gamma(pts, 1.5, 0.3, 1.3)
+    X = rng.standard_normal((pts.shape[0], 5))
+    np.testing.assert_allclose(covariance.grid_gamma_times(shape, X, 1.5, 0.3, 1.3), G @ X, rtol=0, atol=1e-12 * np.abs(G @ X).max())
+
+
+def test_direct_row_sums_equal_dense():
+    rng = np.random.default_rng(2)
+    pts = rng.uniform(size=(300, 2))
+    G = covariance.dense_gamma(pts, 0.5, 0.1, 1.0)
+    X = rng.standard_normal((300, 3))
+    rows = np.array([0, 17, 299])
+    np.testing.assert_allclose(covariance.gamma_rows_times(pts, rows, X, 0.5, 0.1, 1.0), (G @ X)[rows], rtol=1e-13)
+    p0, p1 = synth.cross_well_geometry_2d(3, 3)
+    pts = synth.grid_points_2d(10, 10)
+    h = synth.trace_rays_2d(10, 10, p0, p1)
+    G = covariance.dense_gamma(pts, 0.5, 0.1, 1.0)
+    Hd = synth.csr_to_dense(h)
+    rows = np.arange(0, 100, 7)
+    np.testing.assert_allclose(covariance.gamma_rows_times_sparse_t(pts, rows, h, 0.5, 0.1, 1.0), (G @ Hd.T)[rows], rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# O1: dense Kalman filter
+# ----------------------------------------------------------------------------
+def test_kf_dense_scalar_closed_form_and_steady_state():
+    """N = m = 1: Sigma_k follows e <- 1/(1/(e+1) + lam) and converges to the
+    root of lam e^2 + lam e - 1 = 0."""
+    gamma, h, rho = 0.7, 1.3, 0.05
+    steps = [(np.array([0.1 * k]), np.array([[h]]), rho) for k in range(200)]
+    res = kalman.kf_dense(np.array([[gamma]]), steps)
+    ref = kalman.scalar_closed_form(gamma, h, rho, 200)
+    np.testing.assert_allclose([r["Sigma"][0, 0] for r in res], ref, rtol=1e-13)
+    assert abs(res[-1]["Sigma"][0, 0] - kalman.scalar_steady_state(gamma, h, rho)) < 1e-14
+
+
+def _random_problem(rng, N, ms, alpha0=0.0):
+    pts = rng.uniform(size=(N, 2))
+    Gamma = covariance.dense_gamma(pts, 1.5, 0.3, 1.0)
+    steps = []
+    for m in ms:
+        H = rng.standard_normal((m, N))
+        steps.append((rng.standard_normal(m), H, rng.uniform(0.05, 0.2, m)))
+    return Gamma, steps
+
+
+def test_kf_dense_matches_information_form():
+    """Gain form (O1) == Eq. filtering (inverse of Sigma-^-1 + H^T R^-1 H)."""
+    rng = np.random.default_rng(3)
+    Gamma, steps = _random_problem(rng, 12, [3, 5, 2, 4, 6])
+    a = kalman.kf_dense(Gamma, steps, alpha0=0.5)
+    b = kalman.kf_information_form(Gamma, steps, alpha0=0.5)
+    for ra, Sb in zip(a, b):
+        np.testing.assert_allclose(ra["Sigma"], Sb, rtol=1e-10, atol=1e-12)
+
+
+def _batch_gaussian(Gamma, steps, alpha0):
+    """Joint Gaussian of (s_K, y_1..y_K) under s_k = s_0 + w_1 + ... + w_k:
+    Cov(s_i, s_j) = (alpha0 + min(i, j)) Gamma."""
+    K = len(steps)
+    Hs = [H for _, H, _ in steps]
+    ms = [H.shape[0] for H in Hs]
+    off = np.concatenate([[0], np.cumsum(ms)])
+    Cyy = np.zeros((off[-1], off[-1]))
+    Csy = np.zeros((Gamma.shape[0], off[-1]))
+    for i in range(K):
+        for j in range(K):
+            Cyy[off[i] : off[i + 1], off[j] : off[j + 1]] = (alpha0 + min(i, j) + 1) * Hs[i] @ Gamma @ Hs[j].T
+        R = np.asarray(steps[i][2], dtype=float)
+        Cyy[off[i] : off[i + 1], off[i] : off[i + 1]] += np.diag(np.broadcast_to(R, (ms[i],)))
+        Csy[:, off[i] : off[i + 1]] = (alpha0 + min(K - 1, i) + 1) * Gamma @ Hs[i].T
+    Y = np.concatenate([y for y, _, _ in steps])
+    return Cyy, Csy, Y
+
+
+def test_kf_dense_equals_batch_posterior_and_likelihood():
+    """After K steps the filter's mean/covariance equal the batch Gaussian
+    conditional of s_K given all y, and the summed innovation NLL equals
+    -log N(Y; 0, Cov(Y)) (prediction-error decomposition)."""
+    rng = np.random.default_rng(4)
+    Gamma, steps = _random_problem(rng, 9, [2, 4, 3, 3])
+    alpha0 = 0.3
+    res = kalman.kf_dense(Gamma, steps, alpha0=alpha0)
+    Cyy, Csy, Y = _batch_gaussian(Gamma, steps, alpha0)
+    s_batch = Csy @ np.linalg.solve(Cyy, Y)
+    Sig_batch = (alpha0 + len(steps)) * Gamma - Csy @ np.linalg.solve(Cyy, Csy.T)
+    np.testing.assert_allclose(res[-1]["s"], s_batch, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(res[-1]["Sigma"], Sig_batch, rtol=1e-9, atol=1e-11)
+    nll_batch = -stats.multivariate_normal(mean=np.zeros(Y.shape[0]), cov=Cyy).logpdf(Y)
+    assert abs(sum(r["nll"] for r in res) - nll_batch) < 1e-9 * abs(nll_batch)
+
+
+# ----------------------------------------------------------------------------
+# O2: cross-covariance recursion on sampled rows
+# ----------------------------------------------------------------------------
+def test_crosscov_rows_match_dense_filter():
+    rng = np.random.default_rng(5)
+    N, m = 40, 6
+    Gamma, _ = _random_problem(rng, N, [])
+    H = rng.standard_normal((m, N))
+    ys = [(rng.standard_normal(m), 0.1) for _ in range(7)]
+    dense = kalman.kf_dense(Gamma, [(y, H, R) for y, R in ys], alpha0=0.2)
+    rows = np.array([0, 5, 11, 39])
+    G = Gamma @ H.T
+    o2 = kalman.kf_crosscov_rows(G[rows], H @ G, np.diag(Gamma)[rows], ys, alpha0=0.2)
+    for a, b in zip(dense, o2):
+        np.testing.assert_allclose(b["s_rows"], a["s"][rows], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(b["var_rows"], a["var"][rows], rtol=1e-10, atol=1e-12)
+        assert abs(a["nll"] - b["nll"]) < 1e-10 * max(1.0, abs(a["nll"]))
+
+
+# ----------------------------------------------------------------------------
+# Sec. 3 uncertainty measures
+# ----------------------------------------------------------------------------
+def test_lowrank_factor_realization_and_entropy():
+    rng = np.random.default_rng(6)
+    Gamma, steps = _random_problem(rng, 15, [3, 3, 4])
+    res = kalman.kf_dense(Gamma, steps)
+    Sigma = res[-1]["Sigma"]
+    alpha = float(len(steps))
+    W, d = uq.lowrank_from_dense(Sigma, Gamma, alpha)
+    # Eq. sigmakk and the Gamma^-1-orthonormality of W
+    np.testing.assert_allclose(alpha * Gamma - (W * d) @ W.T, Sigma, atol=1e-10)
+    np.testing.assert_allclose(W.T @ np.linalg.solve(Gamma, W), np.eye(W.shape[1]), atol=1e-9)
+    assert np.all(d > 0) and np.all(d < alpha) and W.shape[1] <= 10
+    # the Sec. 3.3 factor with the symmetric square root: L L^T = Sigma
+    L = uq.paper_factor(Gamma, W, d, alpha)
+    np.testing.assert_allclose(L @ L.T, Sigma, atol=1e-9)
+    # the general-factor map a = chol(Gamma) s_u: its linear part has L' L'^T = Sigma
+    Lg = linalg.cholesky(Gamma, lower=True)
+    x = uq.realization(np.zeros(15), Sigma, Gamma, alpha, Lg)
+    np.testing.assert_allclose(x @ x.T, Sigma, atol=1e-9)
+    # relative entropy via Sylvester: 1/2 (N log alpha + sum log(1 - d/alpha))
+    ent = 0.5 * (15 * np.log(alpha) + np.sum(np.log(1.0 - d / alpha)))
+    assert abs(uq.relative_entropy(Sigma, Gamma) - ent) < 1e-8
+    assert abs(uq.a_optimality_identity(Sigma) - (alpha * np.trace(Gamma) - np.sum(d * np.sum(W * W, axis=0)))) < 1e-9
+
+
+def test_generator_is_deterministic_and_shaped():
+    a = synth.tomography_workload((16, 12), 4, 3, 3, 0.1, 1.0, 1e-4, seed=synth.BASE_SEED)
+    b = synth.tomography_workload((16, 12), 4, 3, 3, 0.1, 1.0, 1e-4, seed=synth.BASE_SEED)
+    np.testing.assert_array_equal(a["y"], b["y"])
+    assert a["truth"].shape == (3, 192) and a["y"].shape == (3, 12)
+    inc = np.diff(np.vstack([np.zeros(192), a["truth"]]), axis=0)
+    assert 0.3 < inc.var() < 3.0
