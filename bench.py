@@ -1,0 +1,410 @@
+"""Benchmark: filter steps/s and H-apply GB/s on the 512 x 512 tomography
+workload (N = 262,144 cells, m = 1024 rays = 32 x 32 source/receiver pairs,
+Matern nu = 1/2, ell = 0.05, R = 1e-4 I), FP32 path vs FP64 path.
+
+One step = one general-path filter step (densify H^T, H-apply Gamma_H H^T,
+gathers, innovation and mean update, data-space GEP, Gamma^-1-orthonormal
+merge, rotation of W and X) on device-resident inputs.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the filter
+(the path does not shard without an all-to-all), the timing
+is the max over ranks and `value` sums all ranks' steps.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filter steps/s and H-apply GB/s at N=262k,m=1024, FP32 vs FP64 path at stated err"
+WORKLOAD = dict(grid=(512, 512), src=32, rec=32, nu=0.5, ell=0.05, sigma2=1.0, noise=1e-4, leaf=64, eta=1.0,
+                aca_tol=1e-8, k_cap=32)
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(steps, seed_offset=0):
+    import synth
+
+    w = WORKLOAD
+    t0 = time.time()
+    wl = synth.tomography_workload(w["grid"], w["src"], w["rec"], steps, 0.05, 1.0, w["noise"],
+                                   seed=synth.BASE_SEED + 2 + 1000 * seed_offset)
+    log(f"[bench] workload: N={wl['points'].shape[0]} m={wl['H'].nrows} nnz={wl['H'].nnz} "
+        f"steps={steps} ({time.time() - t0:.1f}s)")
+    return wl
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_1405_2276_gb300 import build
+
+    build()
+    from paper_1405_2276_gb300 import fkf
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    total_steps = args.warmup + args.steps
+    wl = make_workload(total_steps, seed_offset=rank)
+    pts, h, ys = wl["points"], wl["H"], wl["y"]
+    n, m = pts.shape[0], h.nrows
+    stream = torch.cuda.Stream()
+    ctx = fkf.fkf_create(local, stream.cuda_stream)
+    res = {}
+
+    def build_hmat(prec):
+        t0 = time.time()
+        hm = fkf.fkf_hmatrix_build(ctx, pts, w["nu"], w["ell"], w["sigma2"], leaf=w["leaf"], eta=w["eta"],
+                                   aca_tol=w["aca_tol"], k_cap=w["k_cap"], precision=prec)
+        info = fkf.fkf_hmatrix_info(hm)
+        log(f"[bench] H-matrix prec={prec}: far={info['n_far']} near={info['n_near']} "
+            f"far_entries={info['far_entries']:.3e} near_entries={info['near_entries']:.3e} "
+            f"mean_rank={info['mean_rank']:.1f} build={time.time() - t0:.1f}s")
+        return hm, info
+
+    # device-resident inputs
+    rowptr_d = torch.from_numpy(h.rowptr).cuda()
+    col_d = torch.from_numpy(h.col).cuda()
+    val_d = torch.from_numpy(h.val).cuda()
+    ys_d = torch.from_numpy(np.ascontiguousarray(ys)).cuda()
+    torch.cuda.synchronize()
+
+    def step_dev(f, k):
+        fkf.fkf_filter_step(f, ys_d[k], m, rowptr_d, col_d, val_d, None, w["noise"],
+                            flags=fkf.FKF_STEP_INPUTS_ON_DEVICE, want_nll=False)
+
+    # ---------------- FP32 path (the headline) ----------------
+    hm32, info32 = build_hmat(fkf.FKF_FP32)
+    f32 = fkf.fkf_filter_create(hm32, None, 0.0, 1e-12, m, 2 * m)
+    snap32 = None
+    cmp_step = min(3, args.warmup)
+    for k in range(args.warmup):
+        step_dev(f32, k)
+        if k + 1 == cmp_step:
+            snap32 = fkf.fkf_filter_get(f32, n)
+            v = torch.empty(n, dtype=torch.float64, device="cuda")
+            fkf.fkf_variance(f32, v)
+            snap32["var"] = v.cpu().numpy()
+    log(f"[bench] FP32 warmup done: rank r={fkf.fkf_filter_get(f32, n, want_s=False)['r']}")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = fkf.fkf_launch_count(ctx)
+    c0 = fkf.fkf_library_call_count(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    phases = np.zeros(6)
+    ev0.record(stream)
+    t0 = time.time()
+    for k in range(args.warmup, total_steps):
+        step_dev(f32, k)
+        phases += np.array(fkf.fkf_filter_phase_times(f32))
+    ev1.record(stream)
+    ev1.synchronize()
+    wall = time.time() - t0
+    ms_dev = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = fkf.fkf_launch_count(ctx) - l0
+    libcalls = fkf.fkf_library_call_count(ctx) - c0
+    t_local = ms_dev / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    res["fp32"] = dict(ms_per_step=1e3 * t_max / args.steps, steps_per_s=world * args.steps / t_max,
+                       wall_s=wall, phases_ms=(phases / args.steps).tolist(), launches=launches,
+                       lib_calls=libcalls, clocks=clk)
+    log(f"[bench] FP32 path: {res['fp32']['ms_per_step']:.1f} ms/step; phases(ms) "
+        + " ".join(f"{p:.1f}" for p in res["fp32"]["phases_ms"]))
+
+    # ---------------- H-apply alone (the dominant kernel), m = 1024 columns ----------------
+    def time_apply(hm, info, prec, reps):
+        dt = torch.float32 if prec == fkf.FKF_FP32 else torch.float64
+        g = torch.Generator(device="cuda").manual_seed(5)
+        X = torch.randn((n, m), device="cuda", dtype=dt, generator=g)
+        Y = torch.empty_like(X)
+        torch.cuda.synchronize()
+        fkf.fkf_hmatrix_apply_clustered(hm, X, Y)  # warm
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fkf.fkf_hmatrix_apply_clustered(hm, X, Y)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        wsz = 4 if prec == fkf.FKF_FP32 else 8
+        alg_bytes = (info["far_entries"] + info["near_entries"]) * wsz + 2 * n * m * wsz
+        flops = info["flops_per_col"] * m
+        del X, Y
+        return dict(ms=t * 1e3, gbs=alg_bytes / t / 1e9, tflops=flops / t / 1e12, alg_bytes=alg_bytes, flops=flops)
+
+    res["happly32"] = time_apply(hm32, info32, fkf.FKF_FP32, 5)
+    log(f"[bench] H-apply FP32: {res['happly32']}")
+
+    # ---------------- end to end through the C-ABI with host buffers ----------------
+    e2e_steps = min(args.steps, 5)
+    s_host = np.zeros(n)
+    nll = 0.0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(e2e_steps):
+        kk = (args.warmup + k) % total_steps
+        nll = fkf.fkf_filter_step(f32, ys[kk], m, h.rowptr, h.col, h.val, None, w["noise"])
+        st = fkf.fkf_filter_get(f32, n, want_D=False)
+        s_host = st["s"]
+    e2e_t = time.time() - t0
+    h2d = ys[0].nbytes + h.rowptr.nbytes + h.col.nbytes + h.val.nbytes
+    d2h = 8 + s_host.nbytes
+    res["e2e"] = dict(value=world * e2e_steps / e2e_t, unit="steps/s", h2d_bytes_per_step=int(h2d),
+                      d2h_bytes_per_step=int(d2h), steps=e2e_steps, nll_last=nll)
+    fkf.fkf_filter_destroy(f32)
+    fkf.fkf_hmatrix_destroy(hm32)
+
+    # ---------------- FP64 path (reference precision on the GPU) ----------------
+    if args.fp64_steps > 0 and rank == 0:
+        hm64, info64 = build_hmat(fkf.FKF_FP64)
+        f64 = fkf.fkf_filter_create(hm64, None, 0.0, 1e-12, m, 2 * m)
+        snap64 = None
+        n64 = max(args.fp64_steps, cmp_step)
+        times = []
+        for k in range(n64):
+            torch.cuda.synchronize()
+            t1 = time.time()
+            step_dev(f64, k)
+            torch.cuda.synchronize()
+            times.append(time.time() - t1)
+            if k + 1 == cmp_step:
+                snap64 = fkf.fkf_filter_get(f64, n)
+                v = torch.empty(n, dtype=torch.float64, device="cuda")
+                fkf.fkf_variance(f64, v)
+                snap64["var"] = v.cpu().numpy()
+        t_steady = float(np.mean(times[1:])) if len(times) > 1 else times[0]
+        res["fp64"] = dict(ms_per_step=1e3 * t_steady, steps_per_s=1.0 / t_steady,
+                           phases_ms=fkf.fkf_filter_phase_times(f64), steps=n64)
+        res["happly64"] = time_apply(hm64, info64, fkf.FKF_FP64, 1)
+        log(f"[bench] FP64 path: {res['fp64']}  H-apply {res['happly64']}")
+        if snap32 is not None and snap64 is not None:
+            es = float(np.abs(snap32["s"] - snap64["s"]).max() / np.abs(snap64["s"]).max())
+            ev = float(np.abs(snap32["var"] - snap64["var"]).max() / np.abs(snap64["var"]).max())
+            res["err_fp32_vs_fp64"] = {"step": cmp_step, "s_hat_rel_max": es, "var_rel_max": ev}
+        fkf.fkf_filter_destroy(f64)
+        fkf.fkf_hmatrix_destroy(hm64)
+    fkf.fkf_destroy(ctx)
+    res["snap32"] = snap32 if cmp_step == 3 else None
+    res["snap64"] = snap64 if (args.fp64_steps > 0 and rank == 0 and cmp_step == 3) else None
+    res["info32"] = info32
+    res["n"], res["m"] = n, m
+    return res, wl
+
+
+def cpu_oracle_baseline(wl, sample_rows=2048, steps=3):
+    """The oracle as it stands (O2: exact cross-covariance Kalman recursion for a
+    fixed H, FP64 NumPy) on a bounded sample of the workload: all m x m work
+    plus `sample_rows` of the N state rows; the per-row cost is scaled to N."""
+    from oracle import covariance, kalman
+    import synth
+
+    w = WORKLOAD
+    pts, h = wl["points"], wl["H"]
+    n, m = pts.shape[0], h.nrows
+    t0 = time.time()
+    Ht = synth.csr_to_dense(h).T.copy()
+    G = covariance.grid_gamma_times(w["grid"], Ht, w["nu"], w["ell"], w["sigma2"], batch=64,
+                                    workers=os.cpu_count())  # exact Gamma H^T
+    A = Ht.T @ G
+    A = 0.5 * (A + A.T)
+    t_setup = time.time() - t0
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(n, sample_rows, replace=False))
+    ys = [(wl["y"][k], w["noise"]) for k in range(steps)]
+    t1 = time.time()
+    out_rows = kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys)
+    t_rows = (time.time() - t1) / steps
+    t2 = time.time()
+    kalman.kf_crosscov_rows(G[rows[:0]], A, np.zeros(0), ys)
+    t_glob = (time.time() - t2) / steps
+    t_step = t_glob + max(t_rows - t_glob, 0.0) * n / sample_rows
+    return dict(value=1.0 / t_step, unit="steps/s", cores=os.cpu_count(), kind="oracle",
+                sample=f"O2 (exact cross-covariance KF, FP64 NumPy) for {steps} steps on {sample_rows} of {n} rows "
+                       f"plus all m x m work; per-row time scaled to N; one-time exact Gamma H^T by FFT "
+                       f"({t_setup:.1f}s) not counted",
+                seconds_per_step=t_step, rows=rows, out_rows=out_rows, setup_s=t_setup)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=2048)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        wl = make_workload(args.warmup + args.steps)
+        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=min(args.steps, 3))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * cb["seconds_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "2D 512x512 cross-well tomography, N=262144, m=1024, Matern nu=1/2 ell=0.05",
+                           "global_batch": 1, "seq_len": 0, "parallelism": "none (CPU oracle)"},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    res, wl = run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    if rank != 0:
+        return
+    peaks, src = measured_peaks()
+    cpu = None
+    err_oracle = None
+    if not args.no_cpu:
+        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=3)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        err_oracle = {}
+        ref = cb["out_rows"][2]
+        rows = cb["rows"]
+        for name, snap in (("fp32", res.get("snap32")), ("fp64", res.get("snap64"))):
+            if snap is None:
+                continue
+            err_oracle[name] = {
+                "step": 3,
+                "s_hat_rel_max": float(np.abs(snap["s"][rows] - ref["s_rows"]).max() / np.abs(ref["s_rows"]).max()),
+                "var_rel_max": float(np.abs(snap["var"][rows] - ref["var_rows"]).max() / np.abs(ref["var_rows"]).max()),
+            }
+    ha = res["happly32"]
+    fp32_peak = FP32_SIMT_PEAK_TFLOPS
+    roof = {"kernel": "H-apply (phase-1 slot reduction + phase-2 leaf products), FP32 SIMT",
+            "bound": "alu", "achieved": ha["tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": ha["tflops"] / fp32_peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "hbm_gbs_algorithmic": ha["gbs"], "hbm_frac_of_measured": ha["gbs"] / peaks["hbm_gbs"]}
+    fp32 = res["fp32"]
+    line = {
+        "metric": METRIC, "value": fp32["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fp32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (N-scale) + f64 (m x m)", "data": "synthetic",
+        "config": {"workload": "2D 512x512 cross-well tomography, N=262144, m=1024 (32x32 rays), Matern nu=1/2 "
+                               "ell=0.05, H-matrix leaf 64 eta 1 ACA 1e-8 rank cap 32, R=1e-4 I, general path",
+                   "global_batch": world, "seq_len": 0, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (H-matrix operator and W exceed 129 MB)"},
+        "happly_gbs": ha["gbs"], "happly_ms": ha["ms"], "happly_tflops": ha["tflops"],
+        "fp64_path": ({"steps_per_s": res["fp64"]["steps_per_s"], "ms_per_step": res["fp64"]["ms_per_step"],
+                       "happly_gbs": res["happly64"]["gbs"], "happly_ms": res["happly64"]["ms"],
+                       "happly_tflops": res["happly64"]["tflops"], "phases_ms": res["fp64"]["phases_ms"]}
+                      if "fp64" in res else None),
+        "err_fp32_vs_fp64": res.get("err_fp32_vs_fp64"),
+        "err_vs_oracle": err_oracle,
+        "phases_ms": dict(zip(["densify", "h_apply", "gather_innov_mean", "gep", "orth_merge", "rotation"],
+                              fp32["phases_ms"])),
+        "roofline": roof, "peaks_source": src,
+        "cpu_baseline": cpu,
+        "e2e": {k: res["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
+        "gpu_launches": fp32["launches"], "library_calls": fp32["lib_calls"],
+        "clocks": fp32["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * fkf.h -- C-ABI of the GB300 fast random-walk Kalman filter.
+ *
+ * The method (Saibaba, Miller, Kitanidis, "Fast Kalman filter using
+ * hierarchical matrices and a low-rank perturbative approach"):
+ *   state model   s_k = s_{k-1} + w_k,  w_k ~ N(0, Gamma)       (Sec. 2.1, F_k = I)
+ *   measurements  y_k = H_k s_k + v_k,  v_k ~ N(0, R_k)          (Sec. 2.1)
+ *   posterior     Sigma_k|k = alpha_k Gamma - W_k D_k W_k^T,
+ *                 W_k^T Gamma^-1 W_k = I, D_k diagonal           (Eq. sigmakk)
+ * Gamma is a Matern covariance (Eq. maternfamily) held as a hierarchical
+ * (H-) matrix (Sec. 2.2.1).  One filter step = predict (alpha += 1, Sec. 2.4)
+ * + update with (y_k, H_k, R_k) through a data-space generalized
+ * eigenproblem (Eqs. ghep, geneigendecomposition), a Gamma^-1-orthonormal
+ * merge of the new directions (Alg. lowrankaddition) and the
+ * Sherman-Morrison-Woodbury update of alpha_k, D_k, W_k (Sec. 2.4).
+ *
+ * Conventions (every entry point):
+ *  - Every call returns fkf_status; FKF_OK = 0.  On error the objects are
+ *    left as they were before the call (a filter step is transactional) and
+ *    fkf_last_error(ctx) returns a one-line explanation.
+ *  - Ownership: the library owns the opaque objects and all memory it
+ *    allocates for them; the caller owns every pointer it passes and keeps it
+ *    valid for the duration of the call.
+ *  - Pointers named *_dev are device pointers on the context's device; all
+ *    others are host pointers unless a flag says otherwise.  Device work is
+ *    issued on the context's stream; host outputs are complete on return.
+ *  - Point order: all N-indexed inputs/outputs use the caller's original
+ *    point order (the library permutes internally to cluster order).
+ *  - Dense N x n blocks of vectors are row-major: element (i, j) at
+ *    ptr[i*ld + j], ld >= n.
+ *  - Not thread-safe per object: calls on the same ctx must be serialised.
+ */
+#ifndef FKF_H
+#define FKF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fkf_ctx fkf_ctx;
+typedef struct fkf_hmat fkf_hmat;
+typedef struct fkf_filter fkf_filter;
+
+typedef enum {
+  FKF_OK = 0,
+  FKF_EINVAL = 1,   /* bad argument (size, pointer, parameter) */
+  FKF_ENOMEM = 2,   /* device or host allocation failed */
+  FKF_ENOTSPD = 3,  /* a matrix that must be SPD is not (innovation covariance, Gram) */
+  FKF_ENOCONV = 4,  /* eigensolver did not converge */
+  FKF_ETIMEOUT = 5, /* a bounded device wait gave up */
+  FKF_ECUDA = 6,    /* CUDA runtime / library error */
+  FKF_ESTATE = 7    /* object in a state that does not allow the call */
+} fkf_status;
+
+typedef enum {
+  FKF_FP64 = 0, /* all N-scale storage and arithmetic in FP64 */
+  FKF_FP32 = 1  /* N-scale storage/arithmetic in FP32; m x m and r x r work in FP64 */
+} fkf_precision;
+
+/* Matern kernel (Eq. maternfamily) with inverse scale 1/ell and variance
+ * sigma2: C(r) = sigma2 * 2^(1-nu)/Gamma(nu) * (sqrt(2 nu) r/ell)^nu K_nu(...).
+ * Supported: nu in {0.5, 1.5, 2.5} (exponential-times-polynomial closed forms). */
+typedef struct {
+  double nu;
+  double ell;
+  double sigma2;
+} fkf_matern;
+
+/* H-matrix construction (Sec. 2.2.1; the paper defers the construction to
+ * the H-matrix literature).  leaf: maximum points per leaf cluster; eta:
+ * admissibility min(diam t, diam s) <= eta * dist(t, s) on bounding boxes
+ * (eta = 0 makes every block dense, i.e. Gamma exactly); aca_tol: relative
+ * Frobenius tolerance of each low-rank block (Sec. 4.1.2); k_cap: maximum
+ * block rank (a block that does not converge within k_cap is subdivided, or
+ * stored dense when it cannot be). */
+typedef struct {
+  int32_t leaf;
+  double eta;
+  double aca_tol;
+  int32_t k_cap;
+} fkf_hparams;
+
+/* Statistics of a built H-matrix (exact counts from the built trees). */
+typedef struct {
+  int64_t n;              /* points */
+  int32_t dim;            /* 2 or 3 */
+  int32_t precision;      /* fkf_precision */
+  int64_t n_clusters;
+  int64_t n_leaves;
+  int64_t n_far;          /* admissible (low-rank) blocks, t <= s */
+  int64_t n_near;         /* dense leaf blocks, t <= s */
+  int64_t far_entries;    /* sum over far blocks of k_b (|t| + |s|) */
+  int64_t near_entries;   /* sum over near blocks of |t||s| (stored once) */
+  int64_t max_rank;
+  double mean_rank;
+  int64_t device_bytes;   /* device memory held by the operator */
+  int64_t flops_per_col;  /* 2 * (entries of Gamma_H used per apply column) */
+  int64_t bytes_per_col;  /* algorithmic bytes per apply column besides the operator (read X, write Y) */
+  int64_t operator_bytes; /* algorithmic operator bytes read per apply panel */
+  double build_seconds;
+} fkf_hmat_info;
+
+/* ---- context -------------------------------------------------------------
+ * fkf_create: bind to CUDA device `device` and the CUDA stream `cuda_stream`
+ * (a cudaStream_t, or NULL for a library-created stream).  */
+fkf_status fkf_create(fkf_ctx** out, int32_t device, void* cuda_stream);
+void fkf_destroy(fkf_ctx* ctx);
+const char* fkf_last_error(const fkf_ctx* ctx);
+/* Kernels of this library launched by this context since creation. */
+int64_t fkf_launch_count(const fkf_ctx* ctx);
+/* cuSOLVER dense-routine calls (syevd, potrf, potrs) issued by this context. */
+int64_t fkf_library_call_count(const fkf_ctx* ctx);
+
+/* ---- H-matrix (Sec. 2.2.1) ----------------------------------------------
+ * fkf_hmatrix_build: points (host, N x dim row-major, dim 2 or 3) -> Gamma_H.
+ * Construction runs on the host CPU (cluster tree, block tree, ACA with
+ * partial pivoting) and the result is laid out as flat arrays on the device.
+ * Errors: EINVAL (N < 1, dim, nu unsupported, leaf < 1, aca_tol <= 0,
+ * k_cap < 1), ENOMEM, ECUDA. */
+fkf_status fkf_hmatrix_build(fkf_ctx* ctx, const double* points, int64_t n, int32_t dim, fkf_matern kernel,
+                             fkf_hparams hp, fkf_precision prec, fkf_hmat** out);
+fkf_status fkf_hmatrix_info(const fkf_hmat* h, fkf_hmat_info* info);
+/* Y = Gamma_H X for an N x ncols block (row-major, original point order).
+ * X_dev / Y_dev hold doubles for FKF_FP64 and floats for FKF_FP32; they
+ * must not overlap.  ldx, ldy >= ncols.  Errors: EINVAL, ENOMEM, ECUDA. */
+fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy, int64_t ncols);
+/* Same product with X and Y already in cluster order (no permutation). */
+fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
+                                       int64_t ncols);
+/* Permutation: perm[i] = original index of the i-th point in cluster order. */
+fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host);
+/* Dense copy of Gamma_H (host, N x N row-major, original order); N <= 8192. */
+fkf_status fkf_hmatrix_densify(fkf_hmat* h, double* out_host);
+void fkf_hmatrix_destroy(fkf_hmat* h);
+
+/* ---- filter ---------------------------------------------------------------
+ * fkf_filter_create: s_0 = s0 (host, N, original order; NULL = 0),
+ * Sigma_0|0 = alpha0 * Gamma (Sec. 2.3 induction start; alpha0 >= 0),
+ * trunc_tol: eigenvalues of the merged low-rank term below trunc_tol times the
+ * largest are dropped (Alg. lowrankaddition step 4; relative reading);
+ * m_max: largest measurement count per step; r_max: rank cap of W_k. */
+fkf_status fkf_filter_create(fkf_hmat* h, const double* s0, double alpha0, double trunc_tol, int32_t m_max,
+                             int32_t r_max, fkf_filter** out);
+void fkf_filter_destroy(fkf_filter* f);
+
+/* Flags for fkf_filter_step. */
+#define FKF_STEP_INPUTS_ON_DEVICE 1 /* y, H_rowptr, H_col, H_val, R are device pointers */
+#define FKF_STEP_SKIP_MEAN_SYNC 2   /* do not copy the NLL to the host (nll_out ignored) */
+
+/* One predict + update (Sec. 2.4 / Alg. extkalman without linearisation):
+ *   y (m), H_k as CSR m x N (rowptr int64 m+1, col int32 original point
+ *   indices, val double), R_k = diag(R) (m doubles) or, if R == NULL,
+ *   r_scalar * I (r_scalar > 0).  nll_out (host, nullable) receives the
+ *   innovation negative log-likelihood 1/2 (nu^T S^-1 nu + log det S + m log 2 pi).
+ * Errors: EINVAL (m < 1 or > m_max, bad CSR, nonpositive R), ENOTSPD (S not
+ * SPD), ENOCONV, ECUDA; the filter state is unchanged on error. */
+fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr, const int32_t* H_col,
+                           const double* H_val, const double* R, double r_scalar, int32_t flags, double* nll_out);
+
+/* Current state: s_hat (host, N, original order; nullable), alpha, rank r,
+ * D (host, r doubles; nullable), W (device, N x r row-major in original
+ * order, precision's element type; nullable, ldw >= r). */
+fkf_status fkf_filter_get(fkf_filter* f, double* s_hat, double* alpha, int32_t* r, double* D, void* W_dev, int64_t ldw);
+/* Posterior variance diag(Sigma_k|k) = alpha_k diag(Gamma) - diag(W D W^T)
+ * (Sec. 3.1) into var_dev (device, N doubles, original order). */
+fkf_status fkf_variance(fkf_filter* f, double* var_dev);
+/* Conditional realizations (Sec. 3.3): out = s_hat + sqrt(alpha)(a - W Sig X^T a),
+ * Sig = I - (I - D/alpha)^(1/2), for ns columns a = L_Gamma s_u supplied by the
+ * caller (any L_Gamma with L_Gamma L_Gamma^T = Gamma).  a_dev, out_dev:
+ * device, N x ns row-major doubles, original order. */
+fkf_status fkf_conditional_realization(fkf_filter* f, const double* a_dev, int32_t ns, double* out_dev);
+/* Relative entropy H[s_k|w_k] = 1/2 (N log alpha + sum_j log(1 - d_j/alpha)) and
+ * A-optimality Trace(Sigma_k|k) = alpha Trace(Gamma) - sum_j d_j ||W_j||^2 (Sec. 3.1, 3.2). */
+fkf_status fkf_uncertainty_scalars(fkf_filter* f, double* rel_entropy, double* trace_sigma);
+/* Orthonormality drift max |X^T W - I| with X = Gamma^-1 W carried alongside W. */
+fkf_status fkf_filter_orthonormality(fkf_filter* f, double* max_abs_err);
+/* Re-establish W = Gamma_H X and W^T Gamma^-1 W = I (one H-apply of r columns,
+ * a Gram and a small Cholesky/eigen rotation); the covariance it represents
+ * is kept. */
+fkf_status fkf_filter_refresh(fkf_filter* f);
+/* Checkpoint / restore of (k, alpha, r, s_hat, D, W, X) to a binary file. */
+fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path);
+fkf_status fkf_filter_restore(fkf_filter* f, const char* path);
+/* Per-phase device time of the last step in milliseconds (CUDA events on the
+ * context stream): [0] densify H^T, [1] H-apply, [2] data-space GEP and
+ * innovation, [3] orthonormalisation + merge, [4] rotation, [5] mean update. */
+fkf_status fkf_filter_phase_times(fkf_filter* f, double* ms6);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FKF_H */

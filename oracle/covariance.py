@@ -78,9 +78,18 @@ def _grid_symbol(shape, nu, ell, sigma2):
     return np.fft.rfftn(c)
 
 
-def grid_gamma_times(shape, X, nu, ell, sigma2, batch=16):
+def grid_gamma_times(shape, X, nu, ell, sigma2, batch=16, workers=None):
     """Gamma X for the cell centres of a regular grid of `shape` (cells per
-    axis on the unit domain; index order: first coordinate fastest)."""
+    axis on the unit domain; index order: first coordinate fastest).
+    workers: threads for the FFTs (scipy.fft), None = numpy's single thread."""
+    if workers:
+        from scipy import fft as sfft
+
+        rfftn = lambda a, s, axes: sfft.rfftn(a, s=s, axes=axes, workers=workers)  # noqa: E731
+        irfftn = lambda a, s, axes: sfft.irfftn(a, s=s, axes=axes, workers=workers)  # noqa: E731
+    else:
+        rfftn = lambda a, s, axes: np.fft.rfftn(a, s=s, axes=axes)  # noqa: E731
+        irfftn = lambda a, s, axes: np.fft.irfftn(a, s=s, axes=axes)  # noqa: E731
     shape = tuple(int(s) for s in shape)
     X = np.asarray(X, dtype=np.float64)
     squeeze = X.ndim == 1
@@ -93,8 +102,8 @@ def grid_gamma_times(shape, X, nu, ell, sigma2, batch=16):
     out = np.zeros_like(X)
     for a in range(0, X.shape[1], batch):
         cols = X[:, a : a + batch].T.reshape((-1,) + rshape)
-        f = np.fft.rfftn(cols, s=pad, axes=axes)
-        y = np.fft.irfftn(f * sym[None], s=pad, axes=axes)
+        f = rfftn(cols, pad, axes)
+        y = irfftn(f * sym[None], pad, axes)
         sl = (slice(None),) + tuple(slice(0, n) for n in rshape)
         out[:, a : a + batch] = y[sl].reshape(cols.shape[0], -1).T
     return out[:, 0] if squeeze else out

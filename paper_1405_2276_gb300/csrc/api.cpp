@@ -1,0 +1,304 @@
+// C-ABI entry points (include/fkf.h): argument checks, object lifetime,
+// error reporting, and dispatch to the device implementations.
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.h"
+#include "hmat_host.h"
+
+// filter.cu
+struct fkf_filter;
+fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double trunc_tol, int m_max, int r_max,
+                         fkf_filter** out);
+void filter_destroy(fkf_filter* f);
+fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* rowptr, const int32_t* col,
+                       const double* val, const double* R, double r_scalar, int flags, double* nll_out);
+fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, double* D, void* W_dev, int64_t ldw);
+fkf_status filter_variance(fkf_filter* f, double* var_dev);
+fkf_status filter_realization(fkf_filter* f, const double* a_dev, int ns, double* out_dev);
+fkf_status filter_uncertainty(fkf_filter* f, double* ent, double* tr);
+fkf_status filter_orthonormality(fkf_filter* f, double* err);
+fkf_status filter_refresh(fkf_filter* f);
+fkf_status filter_checkpoint(fkf_filter* f, const char* path);
+fkf_status filter_restore(fkf_filter* f, const char* path);
+fkf_status filter_phase_times(fkf_filter* f, double* ms6);
+fkf_ctx* filter_ctx(fkf_filter* f);
+
+fkf_status set_err(fkf_ctx* ctx, fkf_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+fkf_status dev_alloc(fkf_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return FKF_OK;
+  b.release();
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, FKF_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.p = p;
+  b.bytes = bytes;
+  return FKF_OK;
+}
+
+fkf_status dev_upload(fkf_ctx* ctx, DevBuf& b, const void* host, size_t bytes) {
+  FKF_TRY(dev_alloc(ctx, b, bytes));
+  FKF_CUDA(ctx, cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return FKF_OK;
+}
+
+#define FKF_API extern "C" __attribute__((visibility("default")))
+
+FKF_API fkf_status fkf_create(fkf_ctx** out, int32_t device, void* cuda_stream) {
+  if (!out) return FKF_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return FKF_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return FKF_EINVAL;
+  fkf_ctx* ctx = new (std::nothrow) fkf_ctx();
+  if (!ctx) return FKF_ENOMEM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return FKF_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return FKF_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return FKF_OK;
+}
+
+FKF_API void fkf_destroy(fkf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->solver) cusolverDnDestroy(reinterpret_cast<cusolverDnHandle_t>(ctx->solver));
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+FKF_API const char* fkf_last_error(const fkf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+FKF_API int64_t fkf_launch_count(const fkf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+FKF_API int64_t fkf_library_call_count(const fkf_ctx* ctx) { return ctx ? ctx->lib_calls.load() : 0; }
+
+FKF_API fkf_status fkf_hmatrix_build(fkf_ctx* ctx, const double* points, int64_t n, int32_t dim, fkf_matern kernel,
+                                     fkf_hparams hp, fkf_precision prec, fkf_hmat** out) {
+  if (!ctx || !out) return FKF_EINVAL;
+  *out = nullptr;
+  if (!points || n < 1) return set_err(ctx, FKF_EINVAL, "hmatrix_build: points and n >= 1 required");
+  if (dim != 2 && dim != 3) return set_err(ctx, FKF_EINVAL, "hmatrix_build: dim must be 2 or 3");
+  if (!(kernel.nu == 0.5 || kernel.nu == 1.5 || kernel.nu == 2.5))
+    return set_err(ctx, FKF_EINVAL, "hmatrix_build: nu must be 0.5, 1.5 or 2.5");
+  if (!(kernel.ell > 0) || !(kernel.sigma2 > 0))
+    return set_err(ctx, FKF_EINVAL, "hmatrix_build: ell and sigma2 must be > 0");
+  if (hp.leaf < 1 || !(hp.eta >= 0) || !(hp.aca_tol > 0) || hp.k_cap < 1)
+    return set_err(ctx, FKF_EINVAL, "hmatrix_build: leaf >= 1, eta >= 0, aca_tol > 0, k_cap >= 1 required");
+  if (prec != FKF_FP64 && prec != FKF_FP32) return set_err(ctx, FKF_EINVAL, "hmatrix_build: bad precision");
+  for (int64_t i = 0; i < n * dim; i++)
+    if (!std::isfinite(points[i])) return set_err(ctx, FKF_EINVAL, "hmatrix_build: non-finite coordinate");
+  FKF_CUDA(ctx, cudaSetDevice(ctx->device));
+  fkf_hmat* h = new (std::nothrow) fkf_hmat();
+  if (!h) return set_err(ctx, FKF_ENOMEM, "host allocation");
+  h->ctx = ctx;
+  h->n = n;
+  h->dim = dim;
+  h->prec = prec;
+  h->kernel = kernel;
+  h->hp = hp;
+  HostHmat* hh = nullptr;
+  fkf_status st = hmat_build_host(ctx, points, n, dim, kernel, hp, &hh, h->perm);
+  if (st == FKF_OK) st = hmat_upload(h, *hh);
+  if (st == FKF_OK) {
+    std::vector<int64_t> iperm(n);
+    for (int64_t i = 0; i < n; i++) iperm[h->perm[i]] = i;
+    st = dev_upload(ctx, h->perm_d, h->perm.data(), n * 8);
+    if (st == FKF_OK) st = dev_upload(ctx, h->iperm_d, iperm.data(), n * 8);
+    h->points_clustered = hh->pts;
+  }
+  hmat_free_host(hh);
+  if (st != FKF_OK) {
+    delete h;
+    return st;
+  }
+  // panel width: keep the slot workspace under ~8 GB
+  const size_t w = prec == FKF_FP64 ? 8 : 4;
+  int64_t panel = 1024;
+  while (panel > 128 && (double)h->ktot * panel * w > 8e9) panel /= 2;
+  h->panel = panel;
+  *out = h;
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_info(const fkf_hmat* h, fkf_hmat_info* info) {
+  if (!h || !info) return FKF_EINVAL;
+  *info = h->info;
+  return FKF_OK;
+}
+
+static fkf_status check_apply_args(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols) {
+  if (!X || !Y || ncols < 0 || ldx < ncols || ldy < ncols)
+    return set_err(h->ctx, FKF_EINVAL, "hmatrix_apply: need X, Y, ncols >= 0, ldx >= ncols, ldy >= ncols");
+  const size_t w = h->prec == FKF_FP64 ? 8 : 4;
+  const char* x0 = (const char*)X;
+  const char* x1 = x0 + ((h->n - 1) * ldx + ncols) * w;
+  const char* y0 = (const char*)Y;
+  const char* y1 = y0 + ((h->n - 1) * ldy + ncols) * w;
+  if (ncols > 0 && x0 < y1 && y0 < x1) return set_err(h->ctx, FKF_EINVAL, "hmatrix_apply: X and Y overlap");
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev,
+                                               int64_t ldy, int64_t ncols) {
+  if (!h) return FKF_EINVAL;
+  FKF_TRY(check_apply_args(h, X_dev, ldx, Y_dev, ldy, ncols));
+  FKF_TRY(hmat_apply_clustered(h, X_dev, ldx, Y_dev, ldy, ncols));
+  FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
+                                     int64_t ncols) {
+  if (!h) return FKF_EINVAL;
+  FKF_TRY(check_apply_args(h, X_dev, ldx, Y_dev, ldy, ncols));
+  if (ncols == 0) return FKF_OK;
+  fkf_ctx* ctx = h->ctx;
+  const size_t w = h->prec == FKF_FP64 ? 8 : 4;
+  const size_t need = (size_t)h->n * ncols * w;
+  FKF_TRY(dev_alloc(ctx, h->xperm, need));
+  FKF_TRY(dev_alloc(ctx, h->yperm, need));
+  FKF_TRY(hmat_permute_rows(h, X_dev, ldx, h->perm_d.as<int64_t>(), h->xperm.p, ncols, h->n, ncols));
+  FKF_TRY(hmat_apply_clustered(h, h->xperm.p, ncols, h->yperm.p, ncols, ncols));
+  FKF_TRY(hmat_permute_rows(h, h->yperm.p, ncols, h->iperm_d.as<int64_t>(), Y_dev, ldy, h->n, ncols));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host) {
+  if (!h || !perm_host) return FKF_EINVAL;
+  std::memcpy(perm_host, h->perm.data(), h->n * sizeof(int64_t));
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_densify(fkf_hmat* h, double* out_host) {
+  if (!h || !out_host) return FKF_EINVAL;
+  fkf_ctx* ctx = h->ctx;
+  const int64_t n = h->n;
+  if (n > 8192) return set_err(ctx, FKF_EINVAL, "hmatrix_densify: N <= 8192 required");
+  const size_t w = h->prec == FKF_FP64 ? 8 : 4;
+  const int64_t cb = std::min<int64_t>(n, 1024);
+  DevBuf X, Y;
+  FKF_TRY(dev_alloc(ctx, X, (size_t)n * cb * w));
+  FKF_TRY(dev_alloc(ctx, Y, (size_t)n * cb * w));
+  std::vector<char> hx((size_t)n * cb * w), hy((size_t)n * cb * w);
+  for (int64_t c0 = 0; c0 < n; c0 += cb) {
+    const int64_t nc = std::min<int64_t>(cb, n - c0);
+    std::memset(hx.data(), 0, hx.size());
+    for (int64_t j = 0; j < nc; j++) {
+      if (w == 8)
+        reinterpret_cast<double*>(hx.data())[(c0 + j) * nc + j] = 1.0;
+      else
+        reinterpret_cast<float*>(hx.data())[(c0 + j) * nc + j] = 1.0f;
+    }
+    FKF_CUDA(ctx, cudaMemcpyAsync(X.p, hx.data(), (size_t)n * nc * w, cudaMemcpyHostToDevice, ctx->stream));
+    FKF_TRY(fkf_hmatrix_apply(h, X.p, nc, Y.p, nc, nc));
+    FKF_CUDA(ctx, cudaMemcpyAsync(hy.data(), Y.p, (size_t)n * nc * w, cudaMemcpyDeviceToHost, ctx->stream));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t j = 0; j < nc; j++)
+        out_host[i * n + c0 + j] = w == 8 ? reinterpret_cast<double*>(hy.data())[i * nc + j]
+                                          : (double)reinterpret_cast<float*>(hy.data())[i * nc + j];
+  }
+  return FKF_OK;
+}
+
+FKF_API void fkf_hmatrix_destroy(fkf_hmat* h) { delete h; }
+
+FKF_API fkf_status fkf_filter_create(fkf_hmat* h, const double* s0, double alpha0, double trunc_tol, int32_t m_max,
+                                     int32_t r_max, fkf_filter** out) {
+  if (!h || !out) return FKF_EINVAL;
+  *out = nullptr;
+  FKF_CUDA(h->ctx, cudaSetDevice(h->ctx->device));
+  return filter_create(h, s0, alpha0, trunc_tol, m_max, r_max, out);
+}
+
+FKF_API void fkf_filter_destroy(fkf_filter* f) { filter_destroy(f); }
+
+FKF_API fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr,
+                                   const int32_t* H_col, const double* H_val, const double* R, double r_scalar,
+                                   int32_t flags, double* nll_out) {
+  if (!f) return FKF_EINVAL;
+  if (!y || !H_rowptr || (!H_col && m > 0) || (!H_val && m > 0))
+    return set_err(filter_ctx(f), FKF_EINVAL, "filter_step: null input pointer");
+  return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out);
+}
+
+FKF_API fkf_status fkf_filter_get(fkf_filter* f, double* s_hat, double* alpha, int32_t* r, double* D, void* W_dev,
+                                  int64_t ldw) {
+  if (!f) return FKF_EINVAL;
+  return filter_get(f, s_hat, alpha, r, D, W_dev, ldw);
+}
+
+FKF_API fkf_status fkf_variance(fkf_filter* f, double* var_dev) {
+  if (!f || !var_dev) return FKF_EINVAL;
+  return filter_variance(f, var_dev);
+}
+
+FKF_API fkf_status fkf_conditional_realization(fkf_filter* f, const double* a_dev, int32_t ns, double* out_dev) {
+  if (!f || !a_dev || !out_dev) return FKF_EINVAL;
+  return filter_realization(f, a_dev, ns, out_dev);
+}
+
+FKF_API fkf_status fkf_uncertainty_scalars(fkf_filter* f, double* rel_entropy, double* trace_sigma) {
+  if (!f) return FKF_EINVAL;
+  return filter_uncertainty(f, rel_entropy, trace_sigma);
+}
+
+FKF_API fkf_status fkf_filter_orthonormality(fkf_filter* f, double* max_abs_err) {
+  if (!f || !max_abs_err) return FKF_EINVAL;
+  return filter_orthonormality(f, max_abs_err);
+}
+
+FKF_API fkf_status fkf_filter_refresh(fkf_filter* f) {
+  if (!f) return FKF_EINVAL;
+  return filter_refresh(f);
+}
+
+FKF_API fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path) {
+  if (!f || !path) return FKF_EINVAL;
+  return filter_checkpoint(f, path);
+}
+
+FKF_API fkf_status fkf_filter_restore(fkf_filter* f, const char* path) {
+  if (!f || !path) return FKF_EINVAL;
+  return filter_restore(f, path);
+}
+
+FKF_API fkf_status fkf_filter_phase_times(fkf_filter* f, double* ms6) {
+  if (!f || !ms6) return FKF_EINVAL;
+  return filter_phase_times(f, ms6);
+}

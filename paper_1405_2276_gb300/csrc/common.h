@@ -1,0 +1,155 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fkf.h"
+
+struct cusolverDnContext;
+
+// A device buffer owned by the library.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+
+struct fkf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  cusolverDnContext* solver = nullptr;
+  std::atomic<int64_t> launches{0};   // kernels of this library
+  std::atomic<int64_t> lib_calls{0};  // cuSOLVER routine calls
+  DevBuf solver_info;  // status word for cuSOLVER calls
+};
+
+// Error plumbing: every internal function returns fkf_status and records a
+// message on the context.
+fkf_status set_err(fkf_ctx* ctx, fkf_status st, const char* fmt, ...);
+
+#define FKF_CUDA(ctx, expr)                                                                             \
+  do {                                                                                                  \
+    cudaError_t e_ = (expr);                                                                            \
+    if (e_ != cudaSuccess)                                                                              \
+      return set_err((ctx), e_ == cudaErrorMemoryAllocation ? FKF_ENOMEM : FKF_ECUDA, "%s: %s (%s:%d)", \
+                     #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+  } while (0)
+
+#define FKF_TRY(expr)               \
+  do {                              \
+    fkf_status s_ = (expr);         \
+    if (s_ != FKF_OK) return s_;    \
+  } while (0)
+
+// Check the most recent launch.
+#define FKF_LAUNCHED(ctx)                                                                    \
+  do {                                                                                       \
+    (ctx)->launches++;                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess)                                                                   \
+      return set_err((ctx), FKF_ECUDA, "launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, \
+                     __LINE__);                                                              \
+  } while (0)
+
+fkf_status dev_alloc(fkf_ctx* ctx, DevBuf& b, size_t bytes);  // grows, keeps nothing
+fkf_status dev_upload(fkf_ctx* ctx, DevBuf& b, const void* host, size_t bytes);
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ----------------------------------------------------------------------------
+// H-matrix, device side
+// ----------------------------------------------------------------------------
+// Phase-1 work item: rows [r0, r0+nr) of cluster c, slot tile [q0, q0+nq).
+struct P1Item {
+  int64_t fac_off;   // element offset of Fac_c (|c| x K_c, row-major)
+  int64_t x_row;     // first row of X (cluster order) = c.begin + r0
+  int64_t out_row;   // first output row: partial buffer row, or -1 => scatter via map
+  int64_t map_off;   // global slot index of slot q0 (for the scatter map)
+  int32_t K;         // K_c (row stride of Fac_c)
+  int32_t r0, nr;    // row range inside the cluster
+  int32_t q0, nq;    // slot range
+  int32_t pad;
+};
+
+// Phase-1b reduction item: sum `nch` partials of nq slots x panel, scatter.
+struct P1Reduce {
+  int64_t part_row;  // first partial row (chunk-major: chunk j at part_row + j*nq)
+  int64_t map_off;   // global slot index of the first slot
+  int32_t nq, nch;
+};
+
+// Phase-2 segment: Y_tau += A (|tau| x K, row-major, lda) * B (K rows, ldb = panel)
+struct P2Seg {
+  int64_t a_off;     // element offset into Fac (far) or Near (near)
+  int64_t b_row;     // first row of the B operand (Zmix row for far, X row for near)
+  int32_t lda;
+  int32_t K;
+  int32_t near;      // 0: A in Fac, B in Zmix; 1: A in Near, B in X
+  int32_t pad;
+};
+
+struct P2Leaf {
+  int64_t row0;      // first row of the leaf (cluster order)
+  int32_t rows;      // |tau|
+  int32_t seg0, nseg;
+  int32_t pad;
+};
+
+struct HostHmat;  // host-side build result (hbuild.cpp)
+
+struct fkf_hmat {
+  fkf_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int dim = 0;
+  fkf_precision prec = FKF_FP64;
+  fkf_matern kernel{};
+  fkf_hparams hp{};
+  fkf_hmat_info info{};
+  std::vector<int64_t> perm;  // perm[i] = original index of cluster-order point i
+  std::vector<double> points_clustered;  // N x dim in cluster order
+  // device operator
+  DevBuf fac, nearv;          // factor stacks, near stacks (element type = precision)
+  DevBuf p1items, p1red, p2seg, p2leaf, slotmap;  // schedules
+  DevBuf perm_d, iperm_d;     // int64
+  int64_t n_p1 = 0, n_p1red = 0, n_leaf = 0, ktot = 0, part_rows = 0;
+  int32_t max_leaf = 0;
+  // workspace
+  DevBuf zmix, part, xperm, yperm;
+  int64_t panel = 256;
+};
+
+// happly.cu
+fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh);
+fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
+// dst[i, :] = src[idx[i], :] for i < nrows (element type = precision / FP64)
+fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const int64_t* idx_dev, void* dst,
+                             int64_t ldd, int64_t nrows, int64_t ncols);
+fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, const int64_t* idx_dev, double* dst,
+                                 int64_t ldd, int64_t nrows, int64_t ncols);
+
+// hbuild.cpp
+fkf_status hmat_build_host(fkf_ctx* ctx, const double* pts, int64_t n, int dim, fkf_matern k, fkf_hparams hp,
+                           HostHmat** out, std::vector<int64_t>& perm);
+void hmat_free_host(HostHmat* hh);
+double kernel_eval(const fkf_matern& k, double r);

@@ -1,0 +1,172 @@
+// Dense products on the SIMT tile engine: tall-skinny rotations
+// (N x K times K x n), Gram matrices A^T B with a long reduction (split over
+// row chunks, summed in a fixed order in FP64), and the small FP64 products of
+// the data-space algebra.
+#include <algorithm>
+
+#include "common.h"
+#include "dense.h"
+#include "tile.cuh"
+
+namespace {
+
+// C = alpha op(A) op(B) + beta C, all row-major.
+template <typename T, bool A_KC, bool B_KC>
+__global__ void __launch_bounds__(kTileThreads) k_gemm(int M, int N, int K, T alpha, const T* __restrict__ A,
+                                                       int64_t lda, const T* __restrict__ B, int64_t ldb, T beta,
+                                                       T* __restrict__ C, int64_t ldc) {
+  __shared__ TileSmem<T> sm;
+  constexpr int BM = TileCfg<T>::BM, BN = TileCfg<T>::BN;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int mv = min(BM, M - m0), nv = min(BN, N - n0);
+  T acc[TileCfg<T>::TM][TileCfg<T>::TN];
+  tile_zero<T>(acc);
+  const T* Ap = A_KC ? A + (int64_t)m0 * lda : A + m0;
+  const T* Bp = B_KC ? B + (int64_t)n0 * ldb : B + n0;
+  tile_mma<T, A_KC, B_KC>(acc, Ap, lda, mv, Bp, ldb, nv, K, sm);
+#pragma unroll
+  for (int i = 0; i < TileCfg<T>::TM; i++) {
+    const int r = tile_row<T>(i);
+    if (r >= mv) continue;
+    T* dst = C + (int64_t)(m0 + r) * ldc + n0;
+#pragma unroll
+    for (int j = 0; j < TileCfg<T>::TN; j++) {
+      const int c = tile_col<T>(j);
+      if (c < nv) dst[c] = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * dst[c];
+    }
+  }
+}
+
+// Partial Gram: part[z] = A[rows z]^T B[rows z] (A: K x M, B: K x N row-major).
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_gram_part(int M, int N, int64_t K, int64_t chunk,
+                                                            const T* __restrict__ A, int64_t lda,
+                                                            const T* __restrict__ B, int64_t ldb,
+                                                            T* __restrict__ part) {
+  __shared__ TileSmem<T> sm;
+  constexpr int BM = TileCfg<T>::BM, BN = TileCfg<T>::BN;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int mv = min(BM, M - m0), nv = min(BN, N - n0);
+  const int64_t k0 = (int64_t)blockIdx.z * chunk;
+  const int kv = (int)min(chunk, K - k0);
+  T acc[TileCfg<T>::TM][TileCfg<T>::TN];
+  tile_zero<T>(acc);
+  tile_mma<T, false, false>(acc, A + k0 * lda + m0, lda, mv, B + k0 * ldb + n0, ldb, nv, kv, sm);
+  T* P = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int i = 0; i < TileCfg<T>::TM; i++) {
+    const int r = tile_row<T>(i);
+    if (r >= mv) continue;
+#pragma unroll
+    for (int j = 0; j < TileCfg<T>::TN; j++) {
+      const int c = tile_col<T>(j);
+      if (c < nv) P[(int64_t)(m0 + r) * N + n0 + c] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gram_reduce(int M, int N, int nz, const T* __restrict__ part, double* __restrict__ C,
+                              int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int z = 0; z < nz; z++) s += (double)part[(int64_t)z * total + e];
+    C[(e / N) * ldc + e % N] = s;
+  }
+}
+
+template <typename T>
+fkf_status gemm_impl(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
+                     int64_t lda, const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return FKF_OK;
+  constexpr int BM = TileCfg<T>::BM, BN = TileCfg<T>::BN;
+  if (cdiv(M, BM) > 65535 * 1024LL)
+    return set_err(ctx, FKF_EINVAL, "gemm: M too large");
+  dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM));
+  // op(A)(m,k): ta=false -> A[m*lda+k] (k-contiguous); ta=true -> A[k*lda+m]
+  // op(B)(k,n): tb=false -> B[k*ldb+n]; tb=true -> B[n*ldb+k] (k-contiguous)
+  if (!ta && !tb)
+    k_gemm<T, true, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!ta && tb)
+    k_gemm<T, true, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta && !tb)
+    k_gemm<T, false, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else
+    k_gemm<T, false, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
+}  // namespace
+
+fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  if (K <= 0) {
+    // C = beta C
+    return scale_f64(ctx, M, N, beta, C, ldc);
+  }
+  return gemm_impl<double>(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+fkf_status gemm_f32(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc) {
+  if (K <= 0) return scale_f32(ctx, M, N, beta, C, ldc);
+  return gemm_impl<float>(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+template <typename T>
+fkf_status gram_impl(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B,
+                     int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
+  if (M <= 0 || N <= 0) return FKF_OK;
+  if (K <= 0) return scale_f64(ctx, M, N, 0.0, C, ldc);
+  constexpr int BM = TileCfg<T>::BM, BN = TileCfg<T>::BN;
+  const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+  // enough chunks to fill the GPU, each at least 512 rows
+  int64_t nz = std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, tiles), cdiv(K, 512)));
+  nz = std::min<int64_t>(nz, 1024);
+  const int64_t chunk = cdiv(K, nz);
+  nz = cdiv(K, chunk);
+  const size_t need = (size_t)nz * M * N * sizeof(T);
+  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
+  dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM), (unsigned)nz);
+  k_gram_part<T><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, K, chunk, A, lda, B, ldb, ws.as<T>());
+  FKF_LAUNCHED(ctx);
+  const int blocks = (int)std::min<int64_t>(cdiv(M * N, 256), 4096);
+  k_gram_reduce<T><<<blocks, 256, 0, ctx->stream>>>((int)M, (int)N, (int)nz, ws.as<T>(), C, ldc);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
+fkf_status gram_f64(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                    int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
+  return gram_impl<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ws);
+}
+fkf_status gram_f32(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                    int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
+  return gram_impl<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ws);
+}
+
+namespace {
+template <typename T>
+__global__ void k_scale(int64_t M, int64_t N, T beta, T* C, int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    T* p = C + (e / N) * ldc + e % N;
+    *p = beta == T(0) ? T(0) : beta * *p;
+  }
+}
+}  // namespace
+
+fkf_status scale_f64(fkf_ctx* ctx, int64_t M, int64_t N, double beta, double* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return FKF_OK;
+  k_scale<double><<<(int)std::min<int64_t>(cdiv(M * N, 256), 4096), 256, 0, ctx->stream>>>(M, N, beta, C, ldc);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+fkf_status scale_f32(fkf_ctx* ctx, int64_t M, int64_t N, float beta, float* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return FKF_OK;
+  k_scale<float><<<(int)std::min<int64_t>(cdiv(M * N, 256), 4096), 256, 0, ctx->stream>>>(M, N, beta, C, ldc);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}

@@ -1,0 +1,30 @@
+// Dense and small-matrix building blocks (device work on ctx->stream).
+#pragma once
+
+#include <vector>
+
+#include "common.h"
+
+// C = alpha op(A) op(B) + beta C (row-major; ta/tb select transposes).
+fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc);
+fkf_status gemm_f32(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+// C (M x N, FP64) = A^T B with A: K x M, B: K x N (row-major), K long.
+fkf_status gram_f64(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                    int64_t ldb, double* C, int64_t ldc, DevBuf& ws);
+fkf_status gram_f32(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                    int64_t ldb, double* C, int64_t ldc, DevBuf& ws);
+fkf_status scale_f64(fkf_ctx* ctx, int64_t M, int64_t N, double beta, double* C, int64_t ldc);
+fkf_status scale_f32(fkf_ctx* ctx, int64_t M, int64_t N, float beta, float* C, int64_t ldc);
+
+// Symmetric eigensolver (FP64): A (n x n, symmetric, row-major) is replaced
+// by Vt, whose row j is the unit eigenvector of eigenvalue w[j]; eigenvalues
+// ascending.  The eigenvalues are also copied to w_host (synchronises).
+fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws);
+// Cholesky factorisation of an SPD n x n matrix in place; returns
+// FKF_ENOTSPD when a pivot is not positive (synchronises to read the status).
+fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws);
+// Solve A x = b for nrhs right-hand sides stored as nrhs contiguous vectors
+// of length n, with A factored by chol_f64.
+fkf_status chol_solve_f64(fkf_ctx* ctx, int n, const double* Afact, double* b, int nrhs);

@@ -1,0 +1,1107 @@
+// The fast random-walk Kalman filter step and the Sec. 3 uncertainty measures.
+//
+// State (cluster order): s_hat (N, FP64), alpha, D (r, FP64), W (N x r) and
+// X = Gamma^-1 W (N x r), precision T.  W is stored right-aligned in a wide
+// buffer so that [W G] (G = Gamma H_k^T) is one contiguous N x (r + m) block:
+//     WG row i = [ ... | W(i, 0:r) | G(i, 0:m) ]   columns r_max - r ... r_max + m.
+//
+// One step (Sec. 2.4, Alg. extkalman with a linear H_k; Alg. lowrankaddition):
+//   alpha' = alpha + 1                                    (predict, F = I)
+//   G = Gamma_H H^T,  A = H G,  HW = H W                  (one H-apply, gathers)
+//   S = alpha' A - HW D HW^T + R,  z = S^-1 (y - H s)     (Alg. kalmanconstantH)
+//   s += alpha' G z - W (D (HW^T z))
+//   GEP in data space: R^-1/2 A R^-1/2 = Q diag(lam) Q^T, C = R^-1/2 Q lam^-1/2,
+//     U = G C satisfies U^T Gamma^-1 U = I and Gamma^-1 U Lam U^T Gamma^-1 =
+//     H^T R^-1 H (Eq. geneigendecomposition restricted to its range).
+//   Gamma^-1-orthonormalisation against W (Alg. lowrankaddition steps 1-2),
+//     with W^T Gamma^-1 U = HW^T C =: P and the Gram of U - W P equal to
+//     T = I - P^T P (no N-scale Gram needed); T = Q_T Theta Q_T^T.
+//   Merge (step 3-4): M = diag(Dbar, 0) + [P; Theta^1/2 Q_T^T] Lam [...]^T,
+//     Dbar = D / (alpha' (alpha' - D))  (the sign-consistent form of the SMW
+//     expansion of Sigma_pred^-1, as in Alg. extkalman); M = S Dhat S^T,
+//     truncated at trunc_tol * max.
+//   D' = alpha'^2 Dhat / (1 + alpha' Dhat)  (= alpha'(I + alpha'^-1 Dhat^-1)^-1
+//     written without Dhat^-1), and the basis rotation
+//     W' = [W G] [E_W; E_G],  X' = X E_W + H^T E_G           (one tall GEMM each)
+//   with E_G = C Q_T Theta^-1/2 S_2 and E_W = S_1 - P Q_T Theta^-1/2 S_2.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.h"
+#include "dense.h"
+
+namespace {
+
+template <typename T>
+__global__ void k_densify(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                          T* __restrict__ Bt, int64_t ldb, int* __restrict__ flag) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p++) {
+    const int64_t c = col[p];
+    if (c < 0 || c >= n) {
+      atomicOr(flag, 1);
+      continue;
+    }
+    Bt[iperm[c] * ldb + j] += (T)val[p];
+  }
+}
+
+__global__ void k_csc_count(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const int64_t* __restrict__ iperm, int64_t n, int* __restrict__ cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p++) {
+    const int64_t c = col[p];
+    if (c >= 0 && c < n) atomicAdd(&cnt[iperm[c]], 1);
+  }
+}
+
+// exclusive scan of n ints into n+1 int64 (single CTA of 1024 threads)
+__global__ void k_scan(int64_t n, const int* __restrict__ cnt, int64_t* __restrict__ out) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t a = t * per < n ? t * per : n;
+  const int64_t b = a + per < n ? a + per : n;
+  int64_t s = 0;
+  for (int64_t i = a; i < b; i++) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < 1024; i++) {
+      const int64_t v = part[i];
+      part[i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int64_t run = part[t];
+  for (int64_t i = a; i < b; i++) {
+    out[i] = run;
+    run += cnt[i];
+  }
+  if (t == 1023) out[n] = run;
+}
+
+__global__ void k_csc_fill(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                           const int64_t* __restrict__ colptr, int* __restrict__ cursor, int* __restrict__ crow,
+                           double* __restrict__ cval) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p++) {
+    const int64_t c = col[p];
+    if (c < 0 || c >= n) continue;
+    const int64_t ci = iperm[c];
+    const int64_t pos = colptr[ci] + atomicAdd(&cursor[ci], 1);
+    crow[pos] = j;
+    cval[pos] = val[p];
+  }
+}
+
+// sort each column's entries by row (deterministic summation order); merge
+// duplicates is not needed: sums over duplicates are order-fixed after sorting
+__global__ void k_csc_sort(int64_t n, const int64_t* __restrict__ colptr, int* __restrict__ crow,
+                           double* __restrict__ cval) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t a = colptr[i], b = colptr[i + 1];
+  for (int64_t p = a + 1; p < b; p++) {
+    const int r = crow[p];
+    const double v = cval[p];
+    int64_t q = p - 1;
+    while (q >= a && (crow[q] > r || (crow[q] == r && cval[q] > v))) {
+      crow[q + 1] = crow[q];
+      cval[q + 1] = cval[q];
+      q--;
+    }
+    crow[q + 1] = r;
+    cval[q + 1] = v;
+  }
+}
+
+// out (m x ncols, FP64) = H * src[:, 0:ncols]  (src rows in cluster order)
+template <typename T>
+__global__ void k_csr_gather(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                             const T* __restrict__ src, int64_t lds, int ncols, double* __restrict__ out,
+                             int64_t ldo) {
+  const int j = blockIdx.x;
+  const int64_t a = rowptr[j], b = rowptr[j + 1];
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    T acc = 0;
+    for (int64_t p = a; p < b; p++) {
+      const int64_t cc = col[p];
+      if (cc < 0 || cc >= n) continue;
+      acc += (T)val[p] * src[iperm[cc] * lds + c];
+    }
+    out[(int64_t)j * ldo + c] = (double)acc;
+  }
+}
+
+// nu = y - H s (warp per row)
+__global__ void k_innovation(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                             const double* __restrict__ s, const double* __restrict__ y, double* __restrict__ nu) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= m) return;
+  double acc = 0;
+  for (int64_t p = rowptr[w] + lane; p < rowptr[w + 1]; p += 32) {
+    const int64_t c = col[p];
+    if (c >= 0 && c < n) acc += val[p] * s[iperm[c]];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) nu[w] = y[w] - acc;
+}
+
+// As = (A + A^T)/2, At = diag(rs) As diag(rs); S = alpha' As + diag(R)
+__global__ void k_sym(int m, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
+                      const double* __restrict__ rdiag, double alpha1, double* __restrict__ As,
+                      double* __restrict__ At, double* __restrict__ S) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    const double v = 0.5 * (A[(int64_t)i * lda + j] + A[(int64_t)j * lda + i]);
+    As[e] = v;
+    At[e] = v * rs[i] * rs[j];
+    S[e] = alpha1 * v + (i == j ? rdiag[i] : 0.0);
+  }
+}
+
+// HWD = HW * diag(D)
+__global__ void k_scale_cols(int m, int r, const double* __restrict__ HW, int64_t ld, const double* __restrict__ D,
+                             double* __restrict__ out) {
+  const int64_t total = (int64_t)m * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    out[e] = HW[(int64_t)i * ld + j] * D[j];
+  }
+}
+
+// NLL = 1/2 (nu^T z + log det S + m log 2 pi) with S's Cholesky factor on the diagonal
+__global__ void k_nll(int m, const double* __restrict__ nu, const double* __restrict__ z,
+                      const double* __restrict__ L, double* __restrict__ out) {
+  __shared__ double sh[2][32];
+  double a = 0, b = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    a += nu[i] * z[i];
+    b += log(L[(int64_t)i * m + i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = a;
+    sh[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      sa += sh[0][w];
+      sb += sh[1][w];
+    }
+    out[0] = 0.5 * (sa + 2.0 * sb + m * log(2.0 * 3.14159265358979323846));
+  }
+}
+
+// v = [-D .* uz ; alpha' z] cast to T (uz = HW^T z, r entries)
+template <typename T>
+__global__ void k_mean_coef(int r, int m, const double* __restrict__ D, const double* __restrict__ uz,
+                            const double* __restrict__ z, double alpha1, T* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r) v[i] = (T)(-D[i] * uz[i]);
+  else if (i < r + m) v[i] = (T)(alpha1 * z[i - r]);
+}
+
+// s_out = s_in + WG[:, 0:K] v   (warp per row)
+template <typename T>
+__global__ void k_gemv_add(int64_t n, int K, const T* __restrict__ A, int64_t lda, const T* __restrict__ v,
+                           const double* __restrict__ s_in, double* __restrict__ s_out) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const T* row = A + w * lda;
+  T acc = 0;
+  for (int k = lane; k < K; k += 32) acc += row[k] * v[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) s_out[w] = s_in[w] + (double)acc;
+}
+
+// C[i, q] = rs[i] * Vt[(m-1-q), i] / sqrt(a[m-1-q]);  lam[q] = a[m-1-q]
+__global__ void k_build_C(int m, int mlam, const double* __restrict__ Vt, const double* __restrict__ a,
+                          const double* __restrict__ rs, double* __restrict__ C, double* __restrict__ lam) {
+  const int64_t total = (int64_t)m * mlam;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mlam), q = (int)(e % mlam);
+    const int src = m - 1 - q;
+    C[e] = rs[i] * Vt[(int64_t)src * m + i] / sqrt(a[src]);
+    if (i == 0) lam[q] = a[src];
+  }
+}
+
+// out[p, :] = Vt[n-1-p, :] * f(w[n-1-p]) for p < cnt; mode 0: sqrt(w), 1: 1/sqrt(w), 2: 1
+__global__ void k_top_rows(int n, int cnt, const double* __restrict__ Vt, const double* __restrict__ w, int mode,
+                           double* __restrict__ out, int64_t ldo) {
+  const int64_t total = (int64_t)cnt * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / n), j = (int)(e % n);
+    const int src = n - 1 - p;
+    const double f = mode == 0 ? sqrt(w[src]) : (mode == 1 ? 1.0 / sqrt(w[src]) : 1.0);
+    out[(int64_t)p * ldo + j] = Vt[(int64_t)src * n + j] * f;
+  }
+}
+
+__global__ void k_identity(int n, double* __restrict__ out, int64_t ldo) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[(e / n) * ldo + e % n] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_add_identity(int n, double* __restrict__ A, int64_t lda, double s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(int64_t)i * lda + i] += s;
+}
+
+// ZL[i, q] = Z[i, q] * sqrt(lam[q]) (rows of Z from P (first r) then Po)
+__global__ void k_stack_scale(int r, int mp, int mlam, const double* __restrict__ P, const double* __restrict__ Po,
+                              const double* __restrict__ lam, double* __restrict__ ZL) {
+  const int64_t total = (int64_t)(r + mp) * mlam;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mlam), q = (int)(e % mlam);
+    const double z = i < r ? P[(int64_t)i * mlam + q] : Po[(int64_t)(i - r) * mlam + q];
+    ZL[e] = z * sqrt(lam[q]);
+  }
+}
+
+// M[j, j] += D[j] / (alpha' (alpha' - D[j])) for j < r
+__global__ void k_add_dbar(int r, const double* __restrict__ D, double alpha1, double* __restrict__ M, int64_t ldm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < r) M[(int64_t)j * ldm + j] += D[j] / (alpha1 * (alpha1 - D[j]));
+}
+
+// D'[q] = alpha'^2 th / (1 + alpha' th), th = w[n-1-q]
+__global__ void k_new_D(int n, int rnew, const double* __restrict__ w, double alpha1, double* __restrict__ Dn) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < rnew) {
+    const double th = w[n - 1 - q];
+    Dn[q] = alpha1 * alpha1 * th / (1.0 + alpha1 * th);
+  }
+}
+
+// E_W[i, q] = Sk[q, i] for i < r (transpose copy)
+__global__ void k_transpose(int rows, int cols, const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                            int64_t ldd) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), q = (int)(e % cols);
+    dst[(int64_t)i * ldd + q] = src[(int64_t)q * lds + i];
+  }
+}
+
+// A = (A + A^T) / 2 in place (n x n)
+__global__ void k_symmetrize(int n, double* __restrict__ A) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i < j) {
+      const double v = 0.5 * (A[e] + A[(int64_t)j * n + i]);
+      A[e] = v;
+      A[(int64_t)j * n + i] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_cast(int64_t n, const double* __restrict__ src, T* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
+// X[ci, q] += sum_p cval[p] E[crow[p], q]   (warp per cluster-order cell)
+template <typename T>
+__global__ void k_csc_spmm(int64_t n, const int64_t* __restrict__ colptr, const int* __restrict__ crow,
+                           const double* __restrict__ cval, const double* __restrict__ E, int ncols,
+                           T* __restrict__ X, int64_t ldx) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int64_t a = colptr[w], b = colptr[w + 1];
+  if (a == b) return;
+  for (int q = lane; q < ncols; q += 32) {
+    double acc = 0;
+    for (int64_t p = a; p < b; p++) acc += cval[p] * E[(int64_t)crow[p] * ncols + q];
+    X[w * ldx + q] += (T)acc;
+  }
+}
+
+// var[perm[i]] = alpha sigma2 - sum_j D[j] W[i, j]^2   (warp per row)
+template <typename T>
+__global__ void k_variance(int64_t n, int r, const T* __restrict__ W, int64_t ldw, const double* __restrict__ D,
+                           double alpha_sigma2, const int64_t* __restrict__ perm, double* __restrict__ var) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const T* row = W + w * ldw;
+  double acc = 0;
+  for (int j = lane; j < r; j += 32) {
+    const double x = (double)row[j];
+    acc += D[j] * x * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) var[perm[w]] = alpha_sigma2 - acc;
+}
+
+// column sums of squares, per row chunk (partials), then ordered reduction
+template <typename T>
+__global__ void k_colsq_part(int64_t n, int r, const T* __restrict__ W, int64_t ldw, int64_t chunk,
+                             double* __restrict__ part) {
+  const int64_t a = blockIdx.y * chunk, b = a + chunk < n ? a + chunk : n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < r; j += gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int64_t i = a; i < b; i++) {
+      const double x = (double)W[i * ldw + j];
+      s += x * x;
+    }
+    part[(int64_t)blockIdx.y * r + j] = s;
+  }
+}
+
+// a (FP64, original order, ld ns) -> ac (T, cluster order, ld ns)
+template <typename T>
+__global__ void k_gather_cast(int64_t n, int ns, const double* __restrict__ a, const int64_t* __restrict__ perm,
+                              T* __restrict__ ac) {
+  const int64_t total = n * ns;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ns;
+    ac[e] = (T)a[perm[i] * ns + e % ns];
+  }
+}
+
+// out[perm[i], j] = s[i] + sqrt(alpha) (a[i, j] - t[i, j])
+template <typename T>
+__global__ void k_realize(int64_t n, int ns, const double* __restrict__ s, const T* __restrict__ ac,
+                          const T* __restrict__ t, double sqa, const int64_t* __restrict__ perm,
+                          double* __restrict__ out) {
+  const int64_t total = n * ns;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ns;
+    const int j = (int)(e % ns);
+    out[perm[i] * ns + j] = s[i] + sqa * ((double)ac[e] - (double)t[e]);
+  }
+}
+
+// Ys[j, q] = sig_j * Y[j, q], sig_j = 1 - sqrt(1 - D_j / alpha)
+__global__ void k_sig_rows(int r, int ns, const double* __restrict__ Y, const double* __restrict__ D, double alpha,
+                           double* __restrict__ Ys) {
+  const int64_t total = (int64_t)r * ns;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ns);
+    Ys[e] = (1.0 - sqrt(1.0 - D[j] / alpha)) * Y[e];
+  }
+}
+
+inline int nblk(int64_t total, int threads = 256, int cap = 152 * 32) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, threads), cap));
+}
+
+}  // namespace
+
+struct fkf_filter {
+  fkf_hmat* h = nullptr;
+  fkf_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int m_max = 0, r_max = 0;
+  int64_t ldwg = 0;
+  double trunc_tol = 0, gep_tol = 0, orth_tol = 0;
+  int64_t k = 0;
+  double alpha = 0;
+  int r = 0;
+  int cur = 0;
+  size_t w = 8;
+  DevBuf WG[2], Xb[2], Bt, s_hat, s_new, D, Dn;
+  // step inputs
+  DevBuf rowptr, col, val, y, rdiag, rs, flag;
+  DevBuf cnt, cursor, colptr, crow, cval;
+  // small FP64 buffers
+  DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar;
+  DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
+  cudaEvent_t ev[7] = {};
+  double phase_ms[6] = {};
+};
+
+static fkf_status alloc_small(fkf_filter* f) {
+  fkf_ctx* ctx = f->ctx;
+  const int64_t m = f->m_max, r = f->r_max, nm = r + m;
+  auto A = [&](DevBuf& b, int64_t elems) { return dev_alloc(ctx, b, (size_t)std::max<int64_t>(elems, 1) * 8); };
+  FKF_TRY(A(f->HWA, m * nm));
+  FKF_TRY(A(f->As, m * m));
+  FKF_TRY(A(f->At, m * m));
+  FKF_TRY(A(f->S, m * m));
+  FKF_TRY(A(f->a, m));
+  FKF_TRY(A(f->C, m * m));
+  FKF_TRY(A(f->lam, m));
+  FKF_TRY(A(f->P, r * m));
+  FKF_TRY(A(f->Tm, m * m));
+  FKF_TRY(A(f->th, m));
+  FKF_TRY(A(f->Po, m * m));
+  FKF_TRY(A(f->F1t, m * m));
+  FKF_TRY(A(f->ZL, nm * m));
+  FKF_TRY(A(f->M, nm * nm));
+  FKF_TRY(A(f->thM, nm));
+  FKF_TRY(A(f->Sk, r * nm));
+  FKF_TRY(A(f->J, m * r));
+  FKF_TRY(A(f->E, nm * r));
+  FKF_TRY(dev_alloc(ctx, f->Ecast, (size_t)std::max<int64_t>(nm * r, 1) * f->w));
+  FKF_TRY(A(f->nu, m));
+  FKF_TRY(A(f->z, m));
+  FKF_TRY(A(f->uz, r));
+  FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
+  FKF_TRY(A(f->HWD, m * r));
+  FKF_TRY(A(f->nll, 4));
+  FKF_TRY(A(f->dbar, r));
+  FKF_TRY(A(f->y, m));
+  FKF_TRY(A(f->rdiag, m));
+  FKF_TRY(A(f->rs, m));
+  FKF_TRY(A(f->rowptr, m + 1));
+  FKF_TRY(dev_alloc(ctx, f->flag, 64));
+  return FKF_OK;
+}
+
+fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double trunc_tol, int m_max, int r_max,
+                         fkf_filter** out) {
+  fkf_ctx* ctx = h->ctx;
+  if (alpha0 < 0 || !(trunc_tol >= 0) || m_max < 1 || r_max < 1)
+    return set_err(ctx, FKF_EINVAL, "filter_create: alpha0 >= 0, trunc_tol >= 0, m_max >= 1, r_max >= 1 required");
+  fkf_filter* f = new fkf_filter();
+  f->h = h;
+  f->ctx = ctx;
+  f->n = h->n;
+  f->m_max = m_max;
+  f->r_max = r_max;
+  f->ldwg = (int64_t)r_max + m_max;
+  f->trunc_tol = trunc_tol;
+  f->w = h->prec == FKF_FP64 ? 8 : 4;
+  f->gep_tol = h->prec == FKF_FP64 ? 1e-13 : 1e-7;
+  f->orth_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-5;
+  f->alpha = alpha0;
+  auto fail = [&](fkf_status st) {
+    delete f;
+    return st;
+  };
+  const int64_t n = f->n;
+  fkf_status st;
+  for (int b = 0; b < 2; b++) {
+    if ((st = dev_alloc(ctx, f->WG[b], (size_t)n * f->ldwg * f->w)) != FKF_OK) return fail(st);
+    if ((st = dev_alloc(ctx, f->Xb[b], (size_t)n * r_max * f->w)) != FKF_OK) return fail(st);
+  }
+  if ((st = dev_alloc(ctx, f->Bt, (size_t)n * m_max * f->w)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->s_hat, (size_t)n * 8)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->s_new, (size_t)n * 8)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->D, (size_t)r_max * 8)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->Dn, (size_t)r_max * 8)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->cnt, (size_t)n * 4 + 64)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->cursor, (size_t)n * 4 + 64)) != FKF_OK) return fail(st);
+  if ((st = dev_alloc(ctx, f->colptr, (size_t)(n + 1) * 8)) != FKF_OK) return fail(st);
+  if ((st = alloc_small(f)) != FKF_OK) return fail(st);
+  if (s0) {
+    std::vector<double> sc(n);
+    for (int64_t i = 0; i < n; i++) sc[i] = s0[h->perm[i]];
+    if (cudaMemcpyAsync(f->s_hat.p, sc.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+      return fail(set_err(ctx, FKF_ECUDA, "upload s0"));
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(set_err(ctx, FKF_ECUDA, "sync"));
+  } else if (cudaMemsetAsync(f->s_hat.p, 0, n * 8, ctx->stream) != cudaSuccess) {
+    return fail(set_err(ctx, FKF_ECUDA, "memset s0"));
+  }
+  for (int i = 0; i < 7; i++) cudaEventCreate(&f->ev[i]);
+  *out = f;
+  return FKF_OK;
+}
+
+void filter_destroy(fkf_filter* f) {
+  if (!f) return;
+  for (int i = 0; i < 7; i++)
+    if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+  delete f;
+}
+
+template <typename T>
+static fkf_status gemm_T(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const T* A,
+                         int64_t lda, const T* B, int64_t ldb, double beta, T* C, int64_t ldc);
+template <>
+fkf_status gemm_T<double>(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                          const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                          int64_t ldc) {
+  return gemm_f64(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+template <>
+fkf_status gemm_T<float>(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                         const float* A, int64_t lda, const float* B, int64_t ldb, double beta, float* C,
+                         int64_t ldc) {
+  return gemm_f32(ctx, ta, tb, M, N, K, (float)alpha, A, lda, B, ldb, (float)beta, C, ldc);
+}
+
+static fkf_status gram_T(fkf_ctx* ctx, size_t w, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                         const void* B, int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
+  if (w == 8) return gram_f64(ctx, M, N, K, (const double*)A, lda, (const double*)B, ldb, C, ldc, ws);
+  return gram_f32(ctx, M, N, K, (const float*)A, lda, (const float*)B, ldb, C, ldc, ws);
+}
+
+template <typename T>
+static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int64_t* rowptr_in,
+                            const int32_t* col_in, const double* val_in, const double* R_in, double r_scalar,
+                            int flags, double* nll_out) {
+  fkf_ctx* ctx = f->ctx;
+  fkf_hmat* h = f->h;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = f->n;
+  const bool on_dev = (flags & FKF_STEP_INPUTS_ON_DEVICE) != 0;
+  if (m < 1 || m > f->m_max) return set_err(ctx, FKF_EINVAL, "filter_step: m=%d outside [1, %d]", m, f->m_max);
+  if (!R_in && !(r_scalar > 0)) return set_err(ctx, FKF_EINVAL, "filter_step: r_scalar must be > 0 when R is NULL");
+  // ---- inputs: validate rowptr on the host, stage everything on the device
+  std::vector<int64_t> rp(m + 1);
+  if (on_dev)
+    FKF_CUDA(ctx, cudaMemcpyAsync(rp.data(), rowptr_in, (m + 1) * 8, cudaMemcpyDeviceToHost, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  if (!on_dev) std::memcpy(rp.data(), rowptr_in, (m + 1) * 8);
+  if (rp[0] != 0) return set_err(ctx, FKF_EINVAL, "filter_step: rowptr[0] must be 0");
+  for (int j = 0; j < m; j++)
+    if (rp[j + 1] < rp[j]) return set_err(ctx, FKF_EINVAL, "filter_step: rowptr not nondecreasing at %d", j);
+  const int64_t nnz = rp[m];
+  std::vector<double> rdiag(m), rs(m);
+  if (R_in) {
+    if (on_dev)
+      FKF_CUDA(ctx, cudaMemcpyAsync(rdiag.data(), R_in, m * 8, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (!on_dev) std::memcpy(rdiag.data(), R_in, m * 8);
+  } else {
+    std::fill(rdiag.begin(), rdiag.end(), r_scalar);
+  }
+  for (int j = 0; j < m; j++) {
+    if (!(rdiag[j] > 0) || !std::isfinite(rdiag[j]))
+      return set_err(ctx, FKF_EINVAL, "filter_step: R[%d] must be finite and > 0", j);
+    rs[j] = 1.0 / std::sqrt(rdiag[j]);
+  }
+  if (f->col.bytes < (size_t)std::max<int64_t>(nnz, 1) * 4) FKF_TRY(dev_alloc(ctx, f->col, std::max<int64_t>(nnz, 1) * 4));
+  if (f->val.bytes < (size_t)std::max<int64_t>(nnz, 1) * 8) FKF_TRY(dev_alloc(ctx, f->val, std::max<int64_t>(nnz, 1) * 8));
+  if (f->crow.bytes < (size_t)std::max<int64_t>(nnz, 1) * 4) FKF_TRY(dev_alloc(ctx, f->crow, std::max<int64_t>(nnz, 1) * 4));
+  if (f->cval.bytes < (size_t)std::max<int64_t>(nnz, 1) * 8) FKF_TRY(dev_alloc(ctx, f->cval, std::max<int64_t>(nnz, 1) * 8));
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->rowptr.p, rowptr_in, (m + 1) * 8, kind, st));
+  if (nnz > 0) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(f->col.p, col_in, nnz * 4, kind, st));
+    FKF_CUDA(ctx, cudaMemcpyAsync(f->val.p, val_in, nnz * 8, kind, st));
+  }
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->y.p, y_in, m * 8, kind, st));
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->rdiag.p, rdiag.data(), m * 8, cudaMemcpyHostToDevice, st));
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->rs.p, rs.data(), m * 8, cudaMemcpyHostToDevice, st));
+  FKF_CUDA(ctx, cudaMemsetAsync(f->flag.p, 0, 64, st));
+
+  const int r = f->r, rmax = f->r_max;
+  const double alpha1 = f->alpha + 1.0;  // predict
+  const int64_t ld = f->ldwg;
+  T* WGc = f->WG[f->cur].as<T>();
+  T* WGn = f->WG[1 - f->cur].as<T>();
+  T* Xc = f->Xb[f->cur].as<T>();
+  T* Xn = f->Xb[1 - f->cur].as<T>();
+  T* Wc = WGc + (rmax - r);       // N x r, ld
+  T* G = WGc + rmax;              // N x m, ld
+  const int64_t* iperm = h->iperm_d.as<int64_t>();
+  const int64_t* rowptr = f->rowptr.as<int64_t>();
+  const int32_t* col = f->col.as<int32_t>();
+  const double* val = f->val.as<double>();
+
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[0], st));
+  // ---- S1: densify H^T (cluster order) and build its column index
+  FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
+  k_densify<T><<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, val, iperm, n, f->Bt.as<T>(), m, f->flag.as<int>());
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaMemsetAsync(f->cnt.p, 0, (size_t)n * 4, st));
+  FKF_CUDA(ctx, cudaMemsetAsync(f->cursor.p, 0, (size_t)n * 4, st));
+  k_csc_count<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>());
+  FKF_LAUNCHED(ctx);
+  k_scan<<<1, 1024, 0, st>>>(n, f->cnt.as<int>(), f->colptr.as<int64_t>());
+  FKF_LAUNCHED(ctx);
+  k_csc_fill<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
+                                                 f->cursor.as<int>(), f->crow.as<int>(), f->cval.as<double>());
+  FKF_LAUNCHED(ctx);
+  k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
+  // ---- S2: G = Gamma_H H^T
+  FKF_TRY(hmat_apply_clustered(h, f->Bt.p, m, G, ld, m));
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
+  // ---- gathers: [HW | A] = H [W G]; innovation
+  const int nm = r + m;
+  double* HWA = f->HWA.as<double>();
+  k_csr_gather<T><<<m, 256, 0, st>>>(rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm);
+  FKF_LAUNCHED(ctx);
+  k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->s_hat.as<double>(),
+                                                               f->y.as<double>(), f->nu.as<double>());
+  FKF_LAUNCHED(ctx);
+  const double* HW = HWA;       // m x r, ld nm
+  const double* Araw = HWA + r;  // m x m, ld nm
+  double* S = f->S.as<double>();
+  k_sym<<<nblk((int64_t)m * m), 256, 0, st>>>(m, Araw, nm, f->rs.as<double>(), f->rdiag.as<double>(), alpha1,
+                                              f->As.as<double>(), f->At.as<double>(), S);
+  FKF_LAUNCHED(ctx);
+  // S = alpha' A + R - HW D HW^T
+  if (r > 0) {
+    k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(gemm_f64(ctx, false, true, m, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
+  }
+  FKF_TRY(chol_f64(ctx, m, S, f->cholws));
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
+  FKF_TRY(chol_solve_f64(ctx, m, S, f->z.as<double>(), 1));
+  k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, f->nll.as<double>());
+  FKF_LAUNCHED(ctx);
+  // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
+  if (r > 0) FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
+  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, f->D.as<double>(), f->uz.as<double>(), f->z.as<double>(),
+                                                     alpha1, f->vcoef.as<T>());
+  FKF_LAUNCHED(ctx);
+  k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
+                                                       f->s_new.as<double>());
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
+  // ---- S3: data-space GEP  R^-1/2 A R^-1/2 = Q diag(a) Q^T
+  std::vector<double> a_h, th_h, thM_h;
+  FKF_TRY(eigh_f64(ctx, m, f->At.as<double>(), f->a.as<double>(), a_h, f->eigws));
+  int hflag = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
+  const double amax = a_h.empty() ? 0.0 : a_h.back();
+  int mlam = 0;
+  for (int i = m - 1; i >= 0; i--)
+    if (amax > 0 && a_h[i] > f->gep_tol * amax) mlam++;
+    else break;
+  double* C = f->C.as<double>();
+  if (mlam > 0) {
+    k_build_C<<<nblk((int64_t)m * mlam), 256, 0, st>>>(m, mlam, f->At.as<double>(), f->a.as<double>(),
+                                                       f->rs.as<double>(), C, f->lam.as<double>());
+    FKF_LAUNCHED(ctx);
+  }
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[4], st));
+  // ---- S4: Gamma^-1-orthonormalisation of U = G C against W (data space)
+  double* P = f->P.as<double>();
+  int mp = mlam;
+  if (r > 0 && mlam > 0) {
+    FKF_TRY(gemm_f64(ctx, true, false, r, mlam, m, 1.0, HW, nm, C, mlam, 0.0, P, mlam));
+    double* Tm = f->Tm.as<double>();
+    FKF_TRY(gemm_f64(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
+    k_add_identity<<<(int)cdiv(mlam, 256), 256, 0, st>>>(mlam, Tm, mlam, 1.0);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(eigh_f64(ctx, mlam, Tm, f->th.as<double>(), th_h, f->eigws));
+    mp = 0;
+    for (int i = mlam - 1; i >= 0; i--)
+      if (th_h[i] > f->orth_tol) mp++;
+      else break;
+    if (mp > 0) {
+      k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 0, f->Po.as<double>(), mlam);
+      FKF_LAUNCHED(ctx);
+      k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 1, f->F1t.as<double>(), mlam);
+      FKF_LAUNCHED(ctx);
+    }
+  } else if (mlam > 0) {
+    k_identity<<<nblk((int64_t)mlam * mlam), 256, 0, st>>>(mlam, f->Po.as<double>(), mlam);
+    FKF_LAUNCHED(ctx);
+    k_identity<<<nblk((int64_t)mlam * mlam), 256, 0, st>>>(mlam, f->F1t.as<double>(), mlam);
+    FKF_LAUNCHED(ctx);
+  }
+  // ---- S5: merge  M = diag(Dbar, 0) + Z Lam Z^T, Z = [P; Po]
+  const int nM = r + mp;
+  double* M = f->M.as<double>();
+  int rnew = 0;
+  if (nM > 0) {
+    if (mlam > 0) {
+      k_stack_scale<<<nblk((int64_t)nM * mlam), 256, 0, st>>>(r, mp, mlam, P, f->Po.as<double>(), f->lam.as<double>(),
+                                                            f->ZL.as<double>());
+      FKF_LAUNCHED(ctx);
+    }
+    FKF_TRY(gemm_f64(ctx, false, true, nM, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0, M, nM));
+    if (r > 0) {
+      k_add_dbar<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), alpha1, M, nM);
+      FKF_LAUNCHED(ctx);
+    }
+    FKF_TRY(eigh_f64(ctx, nM, M, f->thM.as<double>(), thM_h, f->eigws));
+    const double tmax = thM_h.back();
+    for (int i = nM - 1; i >= 0 && rnew < rmax; i--)
+      if (tmax > 0 && thM_h[i] > f->trunc_tol * tmax && thM_h[i] > 0) rnew++;
+      else break;
+  }
+  double* Dn = f->Dn.as<double>();
+  double* E = f->E.as<double>();
+  if (rnew > 0) {
+    k_new_D<<<(int)cdiv(rnew, 256), 256, 0, st>>>(nM, rnew, f->thM.as<double>(), alpha1, Dn);
+    FKF_LAUNCHED(ctx);
+    // Sk (rnew x nM): rows = kept eigenvectors of M (descending)
+    k_top_rows<<<nblk((int64_t)rnew * nM), 256, 0, st>>>(nM, rnew, M, f->thM.as<double>(), 2, f->Sk.as<double>(), nM);
+    FKF_LAUNCHED(ctx);
+    double* EW = E;                       // r x rnew
+    double* EG = E + (int64_t)r * rnew;   // m x rnew
+    double* J = f->J.as<double>();        // mlam x rnew
+    if (mp > 0) {
+      // J = F1 S2 with F1^T (mp x mlam) and S2^T = Sk[:, r:r+mp]
+      FKF_TRY(gemm_f64(ctx, true, true, mlam, rnew, mp, 1.0, f->F1t.as<double>(), mlam, f->Sk.as<double>() + r, nM,
+                       0.0, J, rnew));
+      FKF_TRY(gemm_f64(ctx, false, false, m, rnew, mlam, 1.0, C, mlam, J, rnew, 0.0, EG, rnew));
+    } else {
+      FKF_CUDA(ctx, cudaMemsetAsync(EG, 0, (size_t)m * rnew * 8, st));
+    }
+    if (r > 0) {
+      k_transpose<<<nblk((int64_t)r * rnew), 256, 0, st>>>(r, rnew, f->Sk.as<double>(), nM, EW, rnew);
+      FKF_LAUNCHED(ctx);
+      if (mp > 0) FKF_TRY(gemm_f64(ctx, false, false, r, rnew, mlam, -1.0, P, mlam, J, rnew, 1.0, EW, rnew));
+    }
+  }
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[5], st));
+  // ---- S6: rotation  W' = [W G] E,  X' = X E_W + H^T E_G
+  T* Wn = WGn + (rmax - rnew);
+  if (rnew > 0) {
+    const T* Et;
+    if (sizeof(T) == 8) {
+      Et = reinterpret_cast<const T*>(E);
+    } else {
+      k_cast<T><<<nblk((int64_t)nm * rnew), 256, 0, st>>>((int64_t)nm * rnew, E, f->Ecast.as<T>());
+      FKF_LAUNCHED(ctx);
+      Et = f->Ecast.as<T>();
+    }
+    FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, nm, 1.0, Wc, ld, Et, rnew, 0.0, Wn, ld));
+    FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, r, 1.0, Xc, rmax, Et, rnew, 0.0, Xn, rmax));
+    k_csc_spmm<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
+                                                          f->cval.as<double>(), E + (int64_t)r * rnew, rnew, Xn, rmax);
+    FKF_LAUNCHED(ctx);
+  }
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[6], st));
+  double nll = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&nll, f->nll.p, 8, cudaMemcpyDeviceToHost, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  FKF_CUDA(ctx, cudaGetLastError());
+  // ---- commit
+  std::swap(f->s_hat.p, f->s_new.p);
+  std::swap(f->D.p, f->Dn.p);
+  f->cur = 1 - f->cur;
+  f->r = rnew;
+  f->alpha = alpha1;
+  f->k++;
+  if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
+  for (int i = 0; i < 6; i++) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, f->ev[i], f->ev[i + 1]);
+    f->phase_ms[i] = ms;
+  }
+  return FKF_OK;
+}
+
+fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* rowptr, const int32_t* col,
+                       const double* val, const double* R, double r_scalar, int flags, double* nll_out) {
+  if (f->w == 8) return step_impl<double>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out);
+  return step_impl<float>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out);
+}
+
+fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, double* D, void* W_dev, int64_t ldw) {
+  fkf_ctx* ctx = f->ctx;
+  if (alpha) *alpha = f->alpha;
+  if (r) *r = f->r;
+  if (s_hat) {
+    std::vector<double> sc(f->n);
+    FKF_CUDA(ctx, cudaMemcpyAsync(sc.data(), f->s_hat.p, f->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < f->n; i++) s_hat[f->h->perm[i]] = sc[i];
+  }
+  if (D && f->r > 0) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(D, f->D.p, f->r * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  if (W_dev && f->r > 0) {
+    if (ldw < f->r) return set_err(ctx, FKF_EINVAL, "filter_get: ldw < r");
+    const char* Wc = f->WG[f->cur].as<char>() + (f->r_max - f->r) * f->w;
+    FKF_TRY(hmat_permute_rows(f->h, Wc, f->ldwg, f->h->iperm_d.as<int64_t>(), W_dev, ldw, f->n, f->r));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FKF_OK;
+}
+
+fkf_status filter_variance(fkf_filter* f, double* var_dev) {
+  fkf_ctx* ctx = f->ctx;
+  const int64_t n = f->n;
+  const double as2 = f->alpha * f->h->kernel.sigma2;
+  const char* Wc = f->WG[f->cur].as<char>() + (f->r_max - f->r) * f->w;
+  if (f->w == 8)
+    k_variance<double><<<(int)cdiv(n * 32, 256), 256, 0, ctx->stream>>>(n, f->r, (const double*)Wc, f->ldwg,
+                                                                         f->D.as<double>(), as2, f->h->perm_d.as<int64_t>(), var_dev);
+  else
+    k_variance<float><<<(int)cdiv(n * 32, 256), 256, 0, ctx->stream>>>(n, f->r, (const float*)Wc, f->ldwg,
+                                                                        f->D.as<double>(), as2, f->h->perm_d.as<int64_t>(), var_dev);
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return FKF_OK;
+}
+
+template <typename T>
+static fkf_status realization_impl(fkf_filter* f, const double* a_dev, int ns, double* out_dev) {
+  fkf_ctx* ctx = f->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = f->n;
+  const int r = f->r;
+  FKF_TRY(dev_alloc(ctx, f->tmp1, (size_t)n * ns * sizeof(T)));
+  FKF_TRY(dev_alloc(ctx, f->tmp2, (size_t)n * ns * sizeof(T)));
+  FKF_TRY(dev_alloc(ctx, f->tmp3, (size_t)std::max(r, 1) * ns * 8 * 2));
+  T* ac = f->tmp1.as<T>();
+  T* t = f->tmp2.as<T>();
+  k_gather_cast<T><<<nblk(n * ns), 256, 0, st>>>(n, ns, a_dev, f->h->perm_d.as<int64_t>(), ac);
+  FKF_LAUNCHED(ctx);
+  const T* Wc = f->WG[f->cur].as<T>() + (f->r_max - r);
+  const T* Xc = f->Xb[f->cur].as<T>();
+  if (r > 0) {
+    double* Y = f->tmp3.as<double>();
+    double* Ys = Y + (int64_t)r * ns;
+    FKF_TRY(gram_T(ctx, f->w, r, ns, n, Xc, f->r_max, ac, ns, Y, ns, f->gramws));  // X^T a
+    k_sig_rows<<<nblk((int64_t)r * ns), 256, 0, st>>>(r, ns, Y, f->D.as<double>(), f->alpha, Ys);
+    FKF_LAUNCHED(ctx);
+    T* Yt = reinterpret_cast<T*>(Y);  // reuse: cast Ys into the first half
+    k_cast<T><<<nblk((int64_t)r * ns), 256, 0, st>>>((int64_t)r * ns, Ys, Yt);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(gemm_T<T>(ctx, false, false, n, ns, r, 1.0, Wc, f->ldwg, Yt, ns, 0.0, t, ns));
+  } else {
+    FKF_CUDA(ctx, cudaMemsetAsync(t, 0, (size_t)n * ns * sizeof(T), st));
+  }
+  k_realize<T><<<nblk(n * ns), 256, 0, st>>>(n, ns, f->s_hat.as<double>(), ac, t, std::sqrt(f->alpha),
+                                              f->h->perm_d.as<int64_t>(), out_dev);
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  return FKF_OK;
+}
+
+fkf_status filter_realization(fkf_filter* f, const double* a_dev, int ns, double* out_dev) {
+  if (ns < 1) return set_err(f->ctx, FKF_EINVAL, "conditional_realization: ns >= 1 required");
+  if (f->alpha <= 0) return set_err(f->ctx, FKF_ESTATE, "conditional_realization: alpha must be > 0 (run a step)");
+  if (f->w == 8) return realization_impl<double>(f, a_dev, ns, out_dev);
+  return realization_impl<float>(f, a_dev, ns, out_dev);
+}
+
+fkf_status filter_uncertainty(fkf_filter* f, double* ent, double* tr) {
+  fkf_ctx* ctx = f->ctx;
+  const int r = f->r;
+  std::vector<double> d(r);
+  if (r > 0) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(d.data(), f->D.p, r * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  if (ent) {
+    if (f->alpha <= 0) return set_err(ctx, FKF_ESTATE, "relative entropy needs alpha > 0");
+    double s = (double)f->n * std::log(f->alpha);
+    for (int j = 0; j < r; j++) s += std::log1p(-d[j] / f->alpha);
+    *ent = 0.5 * s;
+  }
+  if (tr) {
+    double t = f->alpha * (double)f->n * f->h->kernel.sigma2;
+    if (r > 0) {
+      const int64_t n = f->n, chunk = 4096, nz = cdiv(n, chunk);
+      FKF_TRY(dev_alloc(ctx, f->tmp3, (size_t)nz * r * 8));
+      const char* Wc = f->WG[f->cur].as<char>() + (f->r_max - r) * f->w;
+      dim3 grid((unsigned)cdiv(r, 256), (unsigned)nz);
+      if (f->w == 8)
+        k_colsq_part<double><<<grid, 256, 0, ctx->stream>>>(n, r, (const double*)Wc, f->ldwg, chunk, f->tmp3.as<double>());
+      else
+        k_colsq_part<float><<<grid, 256, 0, ctx->stream>>>(n, r, (const float*)Wc, f->ldwg, chunk, f->tmp3.as<double>());
+      FKF_LAUNCHED(ctx);
+      std::vector<double> part((size_t)nz * r);
+      FKF_CUDA(ctx, cudaMemcpyAsync(part.data(), f->tmp3.p, part.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (int j = 0; j < r; j++) {
+        double s = 0;
+        for (int64_t z = 0; z < nz; z++) s += part[z * r + j];
+        t -= d[j] * s;
+      }
+    }
+    *tr = t;
+  }
+  return FKF_OK;
+}
+
+fkf_status filter_orthonormality(fkf_filter* f, double* err) {
+  fkf_ctx* ctx = f->ctx;
+  const int r = f->r;
+  if (r == 0) {
+    *err = 0;
+    return FKF_OK;
+  }
+  FKF_TRY(dev_alloc(ctx, f->tmp3, (size_t)r * r * 8));
+  const char* Wc = f->WG[f->cur].as<char>() + (f->r_max - r) * f->w;
+  FKF_TRY(gram_T(ctx, f->w, r, r, f->n, f->Xb[f->cur].p, f->r_max, Wc, f->ldwg, f->tmp3.as<double>(), r, f->gramws));
+  std::vector<double> g((size_t)r * r);
+  FKF_CUDA(ctx, cudaMemcpyAsync(g.data(), f->tmp3.p, g.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double e = 0;
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) e = std::max(e, std::fabs(g[(size_t)i * r + j] - (i == j ? 1.0 : 0.0)));
+  *err = e;
+  return FKF_OK;
+}
+
+// W <- Gamma_H X, then re-orthonormalise: with Q = X^T W = V th V^T,
+// W~ = W Q^-1/2, and the low-rank term W D W^T = W~ (Q^1/2 D Q^1/2) W~^T is
+// re-diagonalised: Q^1/2 D Q^1/2 = S D' S^T;  E = Q^-1/2 S.
+template <typename T>
+static fkf_status refresh_impl(fkf_filter* f) {
+  fkf_ctx* ctx = f->ctx;
+  cudaStream_t st = ctx->stream;
+  const int r = f->r, rmax = f->r_max;
+  if (r == 0) return FKF_OK;
+  const int64_t n = f->n, ld = f->ldwg, rr = (int64_t)r * r;
+  T* Xc = f->Xb[f->cur].as<T>();
+  T* Wtmp = f->WG[1 - f->cur].as<T>() + rmax;  // G columns of the spare buffer as scratch (ld)
+  FKF_TRY(hmat_apply_clustered(f->h, Xc, rmax, Wtmp, ld, r));
+  FKF_TRY(dev_alloc(ctx, f->tmp3, (size_t)rr * 8 * 6));
+  double* Q = f->tmp3.as<double>();
+  double* B1 = Q + rr;
+  double* Bm1 = B1 + rr;
+  double* Qh = Bm1 + rr;
+  double* Qmh = Qh + rr;
+  double* E = Qmh + rr;
+  FKF_TRY(gram_T(ctx, f->w, r, r, n, Xc, rmax, Wtmp, ld, Q, r, f->gramws));
+  k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Q);
+  FKF_LAUNCHED(ctx);
+  std::vector<double> w_h;
+  FKF_TRY(eigh_f64(ctx, r, Q, f->th.as<double>(), w_h, f->eigws));  // Q -> Vt
+  if (!(w_h[0] > 0)) return set_err(ctx, FKF_ENOTSPD, "refresh: X^T Gamma X not positive definite");
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 0, B1, r);   // diag(sqrt th) Vt
+  FKF_LAUNCHED(ctx);
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 1, Bm1, r);  // diag(1/sqrt th) Vt
+  FKF_LAUNCHED(ctx);
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 2, E, r);    // Vt (same order)
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(gemm_f64(ctx, true, false, r, r, r, 1.0, E, r, B1, r, 0.0, Qh, r));    // Q^1/2
+  FKF_TRY(gemm_f64(ctx, true, false, r, r, r, 1.0, E, r, Bm1, r, 0.0, Qmh, r));  // Q^-1/2
+  // Mx = Q^1/2 D Q^1/2
+  k_scale_cols<<<nblk(rr), 256, 0, st>>>(r, r, Qh, r, f->D.as<double>(), B1);
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(gemm_f64(ctx, false, false, r, r, r, 1.0, B1, r, Qh, r, 0.0, Q, r));
+  k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Q);
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(eigh_f64(ctx, r, Q, f->th.as<double>(), w_h, f->eigws));
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 2, f->Sk.as<double>(), r);  // S^T (desc)
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(gemm_f64(ctx, false, true, r, r, r, 1.0, Qmh, r, f->Sk.as<double>(), r, 0.0, E, r));  // E = Q^-1/2 S
+  std::vector<double> dn(r);
+  for (int q = 0; q < r; q++) dn[q] = std::max(0.0, w_h[r - 1 - q]);
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->Dn.p, dn.data(), r * 8, cudaMemcpyHostToDevice, st));
+  const T* Et;
+  if (sizeof(T) == 8) {
+    Et = reinterpret_cast<const T*>(E);
+  } else {
+    k_cast<T><<<nblk(rr), 256, 0, st>>>(rr, E, f->Ecast.as<T>());
+    FKF_LAUNCHED(ctx);
+    Et = f->Ecast.as<T>();
+  }
+  T* Wn = f->WG[1 - f->cur].as<T>() + (rmax - r);  // columns [rmax - r, rmax): disjoint from Wtmp
+  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Wtmp, ld, Et, r, 0.0, Wn, ld));
+  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Xc, rmax, Et, r, 0.0, f->Xb[1 - f->cur].as<T>(), rmax));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  FKF_CUDA(ctx, cudaGetLastError());
+  std::swap(f->D.p, f->Dn.p);
+  f->cur = 1 - f->cur;
+  return FKF_OK;
+}
+
+fkf_status filter_refresh(fkf_filter* f) {
+  if (f->r > f->m_max) {
+    // refresh uses the G columns of the spare buffer as scratch for Gamma X (r columns)
+    return set_err(f->ctx, FKF_ESTATE, "refresh: rank %d exceeds the scratch width m_max=%d", f->r, f->m_max);
+  }
+  if (f->w == 8) return refresh_impl<double>(f);
+  return refresh_impl<float>(f);
+}
+
+struct CkptHeader {
+  char magic[8];
+  int64_t n, k;
+  double alpha;
+  int32_t r, w;
+};
+
+fkf_status filter_checkpoint(fkf_filter* f, const char* path) {
+  fkf_ctx* ctx = f->ctx;
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return set_err(ctx, FKF_EINVAL, "checkpoint: cannot open %s", path);
+  CkptHeader hd{};
+  std::memcpy(hd.magic, "FKFCKPT1", 8);
+  hd.n = f->n;
+  hd.k = f->k;
+  hd.alpha = f->alpha;
+  hd.r = f->r;
+  hd.w = (int32_t)f->w;
+  const int64_t n = f->n, r = f->r;
+  std::vector<char> buf((size_t)std::max<int64_t>(n * 8, n * r * (int64_t)f->w));
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
+  auto put_dev = [&](const void* src, size_t bytes, int64_t rows, int64_t rowbytes, int64_t ldbytes) -> fkf_status {
+    // rows of rowbytes with stride ldbytes
+    if (cudaMemcpy2D(buf.data(), rowbytes, src, ldbytes, rowbytes, rows, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_err(ctx, FKF_ECUDA, "checkpoint copy");
+    ok = ok && std::fwrite(buf.data(), 1, bytes, fp) == bytes;
+    return FKF_OK;
+  };
+  fkf_status s = put_dev(f->s_hat.p, n * 8, 1, n * 8, n * 8);
+  if (s == FKF_OK && r > 0) s = put_dev(f->D.p, r * 8, 1, r * 8, r * 8);
+  if (s == FKF_OK && r > 0)
+    s = put_dev(f->WG[f->cur].as<char>() + (f->r_max - r) * f->w, n * r * f->w, n, r * f->w, f->ldwg * f->w);
+  if (s == FKF_OK && r > 0) s = put_dev(f->Xb[f->cur].p, n * r * f->w, n, r * f->w, f->r_max * f->w);
+  std::fclose(fp);
+  if (s != FKF_OK) return s;
+  if (!ok) return set_err(ctx, FKF_EINVAL, "checkpoint: write failed");
+  return FKF_OK;
+}
+
+fkf_status filter_restore(fkf_filter* f, const char* path) {
+  fkf_ctx* ctx = f->ctx;
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return set_err(ctx, FKF_EINVAL, "restore: cannot open %s", path);
+  CkptHeader hd{};
+  bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1 && std::memcmp(hd.magic, "FKFCKPT1", 8) == 0;
+  if (!ok || hd.n != f->n || hd.w != (int32_t)f->w || hd.r < 0 || hd.r > f->r_max) {
+    std::fclose(fp);
+    return set_err(ctx, FKF_EINVAL, "restore: incompatible checkpoint %s", path);
+  }
+  const int64_t n = f->n, r = hd.r;
+  std::vector<char> buf((size_t)std::max<int64_t>(n * 8, n * r * (int64_t)f->w));
+  auto get_dev = [&](void* dst, size_t bytes, int64_t rows, int64_t rowbytes, int64_t ldbytes) -> fkf_status {
+    if (std::fread(buf.data(), 1, bytes, fp) != bytes) return set_err(ctx, FKF_EINVAL, "restore: truncated file");
+    if (cudaMemcpy2D(dst, ldbytes, buf.data(), rowbytes, rowbytes, rows, cudaMemcpyHostToDevice) != cudaSuccess)
+      return set_err(ctx, FKF_ECUDA, "restore copy");
+    return FKF_OK;
+  };
+  const int nb = 1 - f->cur;  // write into the spare buffers, then swap (transactional)
+  fkf_status s = get_dev(f->s_new.p, n * 8, 1, n * 8, n * 8);
+  if (s == FKF_OK && r > 0) s = get_dev(f->Dn.p, r * 8, 1, r * 8, r * 8);
+  if (s == FKF_OK && r > 0)
+    s = get_dev(f->WG[nb].as<char>() + (f->r_max - r) * f->w, n * r * f->w, n, r * f->w, f->ldwg * f->w);
+  if (s == FKF_OK && r > 0) s = get_dev(f->Xb[nb].p, n * r * f->w, n, r * f->w, f->r_max * f->w);
+  std::fclose(fp);
+  if (s != FKF_OK) return s;
+  std::swap(f->s_hat.p, f->s_new.p);
+  std::swap(f->D.p, f->Dn.p);
+  f->cur = nb;
+  f->r = (int)r;
+  f->k = hd.k;
+  f->alpha = hd.alpha;
+  return FKF_OK;
+}
+
+fkf_status filter_phase_times(fkf_filter* f, double* ms6) {
+  for (int i = 0; i < 6; i++) ms6[i] = f->phase_ms[i];
+  return FKF_OK;
+}
+
+fkf_ctx* filter_ctx(fkf_filter* f) { return f->ctx; }

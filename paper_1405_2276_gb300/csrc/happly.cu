@@ -1,0 +1,415 @@
+// H-matrix apply Y = Gamma_H X for a tall block X (N x ncols, cluster order).
+//
+// The paper needs Gamma_sys times blocks of vectors (Gamma H^T, Sec. 2.3 and
+// Alg. kalmanconstantH; Gamma W_k, Sec. 2.4) and takes the MVP from an H-matrix
+// (Sec. 2.2.1).  Device layout (all row-major, element type = precision):
+//
+//   Fac_c   |c| x K_c  for every cluster c: the row factors of all far blocks
+//                       that have c as one side, side by side ("slots").  A far
+//                       block b = (t, s) of rank k owns k slots in Fac_t (U_b)
+//                       and k slots in Fac_s (V_b).
+//   Near_l  |l| x Kn_l for every leaf l: the dense blocks Gamma(l, sigma) of all
+//                       near partners sigma, side by side (both orientations
+//                       of a stored pair are written from the same values, so
+//                       Gamma_H is exactly symmetric).
+//
+// Apply, per panel of P columns:
+//   phase 1  Z_c = Fac_c^T X_c        one reduction per cluster (split over row
+//                                      chunks for large clusters, reduced in a
+//                                      fixed order); slot rows are scattered to
+//                                      the partner slot: Zmix[map(g)] = Z[g]
+//   phase 2  Y_l = sum_{c ancestor of l} Fac_c[l rows] Zmix_c
+//                + sum_{sigma near l} Near_l[:, sigma] X_sigma
+// so each row block of Y is written once, by one CTA, with no atomics, and
+// X_c is read once per cluster level instead of once per block.
+#include <algorithm>
+#include <cstring>
+
+#include "common.h"
+#include "hmat_host.h"
+#include "tile.cuh"
+
+namespace {
+
+constexpr int kChunkRows = 2048;  // phase-1 reduction chunk (rows of a cluster)
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_phase1(const P1Item* __restrict__ items, const T* __restrict__ fac,
+                                                         const T* __restrict__ X, int64_t ldx, int ncols,
+                                                         const int64_t* __restrict__ slotmap, T* __restrict__ zmix,
+                                                         T* __restrict__ part, int64_t ldz) {
+  __shared__ TileSmem<T> sm;
+  const P1Item it = items[blockIdx.x];
+  const int n0 = blockIdx.y * TileCfg<T>::BN;
+  const int nv = min(TileCfg<T>::BN, ncols - n0);
+  if (nv <= 0) return;
+  T acc[TileCfg<T>::TM][TileCfg<T>::TN];
+  tile_zero<T>(acc);
+  // A(m = slot, k = row) = Fac_c[(r0 + row) * K + q0 + slot]
+  const T* A = fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0;
+  const T* B = X + it.x_row * ldx + n0;
+  tile_mma<T, false, false>(acc, A, it.K, it.nq, B, ldx, nv, it.nr, sm);
+#pragma unroll
+  for (int i = 0; i < TileCfg<T>::TM; i++) {
+    const int q = tile_row<T>(i);
+    if (q >= it.nq) continue;
+    T* dst = it.out_row < 0 ? zmix + slotmap[it.map_off + q] * ldz : part + (it.out_row + q) * ldz;
+#pragma unroll
+    for (int j = 0; j < TileCfg<T>::TN; j++) {
+      const int n = tile_col<T>(j);
+      if (n < nv) dst[n0 + n] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_phase1_reduce(const P1Reduce* __restrict__ items, const T* __restrict__ part,
+                                const int64_t* __restrict__ slotmap, T* __restrict__ zmix, int64_t ldz, int ncols) {
+  const P1Reduce it = items[blockIdx.x];
+  const int64_t total = (int64_t)it.nq * ncols;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total; e += (int64_t)blockDim.x * gridDim.y) {
+    const int q = (int)(e / ncols), n = (int)(e % ncols);
+    T s = 0;
+    for (int c = 0; c < it.nch; c++) s += part[(it.part_row + (int64_t)c * it.nq + q) * ldz + n];
+    zmix[slotmap[it.map_off + q] * ldz + n] = s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_phase2(const P2Leaf* __restrict__ leaves,
+                                                         const P2Seg* __restrict__ segs, const T* __restrict__ fac,
+                                                         const T* __restrict__ nearv, const T* __restrict__ zmix,
+                                                         int64_t ldz, const T* __restrict__ X, int64_t ldx,
+                                                         T* __restrict__ Y, int64_t ldy, int ncols) {
+  __shared__ TileSmem<T> sm;
+  const P2Leaf lf = leaves[blockIdx.x];
+  const int n0 = blockIdx.y * TileCfg<T>::BN;
+  const int nv = min(TileCfg<T>::BN, ncols - n0);
+  if (nv <= 0) return;
+  T acc[TileCfg<T>::TM][TileCfg<T>::TN];
+  tile_zero<T>(acc);
+  for (int s = 0; s < lf.nseg; s++) {
+    const P2Seg sg = segs[lf.seg0 + s];
+    const T* A = (sg.near ? nearv : fac) + sg.a_off + (int64_t)lf.pad * sg.lda;
+    const T* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
+    tile_mma<T, true, false>(acc, A, sg.lda, lf.rows, B, sg.near ? ldx : ldz, nv, sg.K, sm);
+  }
+#pragma unroll
+  for (int i = 0; i < TileCfg<T>::TM; i++) {
+    const int r = tile_row<T>(i);
+    if (r >= lf.rows) continue;
+    T* dst = Y + (lf.row0 + r) * ldy + n0;
+#pragma unroll
+    for (int j = 0; j < TileCfg<T>::TN; j++) {
+      const int n = tile_col<T>(j);
+      if (n < nv) dst[n] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ src, int64_t lds, const int64_t* __restrict__ idx, T* __restrict__ dst,
+                              int64_t ldd, int64_t nrows, int ncols) {
+  // dst[i, :] = src[idx[i], :]
+  const int64_t total = nrows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols;
+    const int j = (int)(e % ncols);
+    dst[i * ldd + j] = src[idx[i] * lds + j];
+  }
+}
+
+template <typename T>
+fkf_status apply_impl(fkf_hmat* h, const T* X, int64_t ldx, T* Y, int64_t ldy, int64_t ncols) {
+  fkf_ctx* ctx = h->ctx;
+  const int64_t P = h->panel;
+  const size_t zbytes = (size_t)std::max<int64_t>(h->ktot, 1) * P * sizeof(T);
+  if (h->zmix.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zmix, zbytes));
+  const size_t pbytes = (size_t)std::max<int64_t>(h->part_rows, 1) * P * sizeof(T);
+  if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
+  constexpr int BN = TileCfg<T>::BN;
+  for (int64_t c0 = 0; c0 < ncols; c0 += P) {
+    const int nc = (int)std::min<int64_t>(P, ncols - c0);
+    const int ntile = (int)cdiv(nc, BN);
+    if (h->n_p1 > 0) {
+      k_phase1<T><<<dim3((unsigned)h->n_p1, ntile), kTileThreads, 0, ctx->stream>>>(
+          h->p1items.as<P1Item>(), h->fac.as<T>(), X + c0, ldx, nc, h->slotmap.as<int64_t>(), h->zmix.as<T>(),
+          h->part.as<T>(), P);
+      FKF_LAUNCHED(ctx);
+    }
+    if (h->n_p1red > 0) {
+      k_phase1_reduce<T><<<dim3((unsigned)h->n_p1red, 4), 256, 0, ctx->stream>>>(
+          h->p1red.as<P1Reduce>(), h->part.as<T>(), h->slotmap.as<int64_t>(), h->zmix.as<T>(), P, nc);
+      FKF_LAUNCHED(ctx);
+    }
+    k_phase2<T><<<dim3((unsigned)h->n_leaf, ntile), kTileThreads, 0, ctx->stream>>>(
+        h->p2leaf.as<P2Leaf>(), h->p2seg.as<P2Seg>(), h->fac.as<T>(), h->nearv.as<T>(), h->zmix.as<T>(), P, X + c0,
+        ldx, Y + c0, ldy, nc);
+    FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+template <typename T>
+void fill_typed(void* dst, const double* src, size_t n) {
+  T* d = reinterpret_cast<T*>(dst);
+  for (size_t i = 0; i < n; i++) d[i] = (T)src[i];
+}
+
+}  // namespace
+
+fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols) {
+  if (ncols <= 0) return FKF_OK;
+  if (h->prec == FKF_FP64)
+    return apply_impl<double>(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
+  return apply_impl<float>(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
+}
+
+template <typename T>
+static fkf_status permute_rows(fkf_ctx* ctx, const T* src, int64_t lds, const int64_t* idx, T* dst, int64_t ldd,
+                               int64_t nrows, int64_t ncols) {
+  const int64_t total = nrows * ncols;
+  const int blocks = (int)std::min<int64_t>(cdiv(total, 256), 152 * 16);
+  k_gather_rows<T><<<blocks, 256, 0, ctx->stream>>>(src, lds, idx, dst, ldd, nrows, (int)ncols);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
+fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const int64_t* idx_dev, void* dst,
+                             int64_t ldd, int64_t nrows, int64_t ncols) {
+  if (h->prec == FKF_FP64)
+    return permute_rows<double>(h->ctx, (const double*)src, lds, idx_dev, (double*)dst, ldd, nrows, ncols);
+  return permute_rows<float>(h->ctx, (const float*)src, lds, idx_dev, (float*)dst, ldd, nrows, ncols);
+}
+
+fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, const int64_t* idx_dev, double* dst,
+                                 int64_t ldd, int64_t nrows, int64_t ncols) {
+  return permute_rows<double>(ctx, src, lds, idx_dev, dst, ldd, nrows, ncols);
+}
+
+// Lay the host build out as flat device arrays and work lists.
+fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
+  fkf_ctx* ctx = h->ctx;
+  const auto& cl = hh.cl;
+  const int nc = (int)cl.size();
+  const size_t w = h->prec == FKF_FP64 ? 8 : 4;
+  auto csize = [&](int c) { return cl[c].end - cl[c].begin; };
+  // slots per cluster
+  std::vector<std::vector<std::pair<int, int>>> slots(nc);  // (block, side)
+  for (int b = 0; b < (int)hh.far.size(); b++) {
+    slots[hh.far[b].t].push_back({b, 0});
+    slots[hh.far[b].s].push_back({b, 1});
+  }
+  std::vector<int64_t> K(nc, 0), slot_base(nc, 0), fac_off(nc, 0);
+  std::vector<std::vector<int64_t>> slot_col(nc);
+  int64_t ktot = 0, facn = 0;
+  for (int c = 0; c < nc; c++) {
+    int64_t k = 0;
+    for (auto [b, side] : slots[c]) {
+      slot_col[c].push_back(k);
+      k += hh.far[b].k;
+    }
+    K[c] = (k + 3) / 4 * 4;
+    slot_base[c] = ktot;
+    fac_off[c] = facn;
+    ktot += K[c];
+    facn += csize(c) * K[c];
+  }
+  // slot map (involution between the two sides of each block; padding maps to itself)
+  std::vector<int64_t> smap(std::max<int64_t>(ktot, 1));
+  for (int64_t g = 0; g < ktot; g++) smap[g] = g;
+  {
+    std::vector<int64_t> side_row[2];
+    side_row[0].assign(hh.far.size(), 0);
+    side_row[1].assign(hh.far.size(), 0);
+    for (int c = 0; c < nc; c++)
+      for (size_t i = 0; i < slots[c].size(); i++)
+        side_row[slots[c][i].second][slots[c][i].first] = slot_base[c] + slot_col[c][i];
+    for (size_t b = 0; b < hh.far.size(); b++)
+      for (int l = 0; l < hh.far[b].k; l++) {
+        smap[side_row[0][b] + l] = side_row[1][b] + l;
+        smap[side_row[1][b] + l] = side_row[0][b] + l;
+      }
+  }
+  // factor stacks
+  std::vector<double> facv((size_t)std::max<int64_t>(facn, 1), 0.0);
+  for (int c = 0; c < nc; c++) {
+    const int64_t nr = csize(c);
+    for (size_t i = 0; i < slots[c].size(); i++) {
+      const HFar& fb = hh.far[slots[c][i].first];
+      const std::vector<double>& src = slots[c][i].second == 0 ? fb.u : fb.v;
+      for (int l = 0; l < fb.k; l++)
+        for (int64_t r = 0; r < nr; r++) facv[fac_off[c] + r * K[c] + slot_col[c][i] + l] = src[(size_t)l * nr + r];
+    }
+  }
+  // near stacks per leaf
+  std::vector<int> leaves;
+  for (int c = 0; c < nc; c++)
+    if (cl[c].child[0] < 0) leaves.push_back(c);
+  std::sort(leaves.begin(), leaves.end(), [&](int a, int b) { return cl[a].begin < cl[b].begin; });
+  std::vector<int> leaf_id(nc, -1);
+  for (size_t i = 0; i < leaves.size(); i++) leaf_id[leaves[i]] = (int)i;
+  struct NP {
+    int sigma;
+    int64_t pair;
+    bool transposed;
+  };
+  std::vector<std::vector<NP>> partners(leaves.size());
+  for (size_t p = 0; p < hh.near.size(); p++) {
+    const auto [t, s] = hh.near[p];
+    partners[leaf_id[t]].push_back({s, (int64_t)p, false});
+    if (s != t) partners[leaf_id[s]].push_back({t, (int64_t)p, true});
+  }
+  std::vector<int64_t> kn(leaves.size()), near_off(leaves.size());
+  int64_t nearn = 0;
+  for (size_t l = 0; l < leaves.size(); l++) {
+    std::sort(partners[l].begin(), partners[l].end(),
+              [&](const NP& a, const NP& b) { return cl[a.sigma].begin < cl[b.sigma].begin; });
+    int64_t k = 0;
+    for (auto& np : partners[l]) k += csize(np.sigma);
+    kn[l] = (k + 3) / 4 * 4;
+    near_off[l] = nearn;
+    nearn += csize(leaves[l]) * kn[l];
+  }
+  std::vector<double> nearv((size_t)std::max<int64_t>(nearn, 1), 0.0);
+  std::vector<std::vector<int64_t>> pcol(leaves.size());
+  for (size_t l = 0; l < leaves.size(); l++) {
+    const int tau = leaves[l];
+    const int64_t nt = csize(tau);
+    int64_t col = 0;
+    for (auto& np : partners[l]) {
+      pcol[l].push_back(col);
+      const int64_t ns = csize(np.sigma);
+      const double* tile = hh.near_val.data() + hh.near_off[np.pair];
+      for (int64_t a = 0; a < nt; a++)
+        for (int64_t b = 0; b < ns; b++) {
+          // stored tile is (t rows) x (s cols) for the pair (t, s)
+          const double v = np.transposed ? tile[b * nt + a] : tile[a * ns + b];
+          nearv[near_off[l] + a * kn[l] + col + b] = v;
+        }
+      col += ns;
+    }
+  }
+  // phase-1 work list
+  std::vector<P1Item> p1;
+  std::vector<P1Reduce> p1r;
+  int64_t part_rows = 0;
+  const int BQ = 64;
+  for (int c = 0; c < nc; c++) {
+    if (K[c] == 0) continue;
+    const int64_t nr = csize(c);
+    const int nch = (int)cdiv(nr, kChunkRows);
+    for (int64_t q0 = 0; q0 < K[c]; q0 += BQ) {
+      const int nq = (int)std::min<int64_t>(BQ, K[c] - q0);
+      const int64_t base = part_rows;
+      for (int ch = 0; ch < nch; ch++) {
+        P1Item it{};
+        it.fac_off = fac_off[c];
+        it.r0 = ch * kChunkRows;
+        it.nr = (int)std::min<int64_t>(kChunkRows, nr - it.r0);
+        it.x_row = cl[c].begin + it.r0;
+        it.out_row = nch == 1 ? -1 : base + (int64_t)ch * nq;
+        it.map_off = slot_base[c] + q0;
+        it.K = (int)K[c];
+        it.q0 = (int)q0;
+        it.nq = nq;
+        p1.push_back(it);
+      }
+      if (nch > 1) {
+        p1r.push_back(P1Reduce{base, slot_base[c] + q0, nq, nch});
+        part_rows += (int64_t)nch * nq;
+      }
+    }
+  }
+  // phase-2 segments per leaf (row chunks of at most BM rows)
+  const int BM = h->prec == FKF_FP64 ? TileCfg<double>::BM : TileCfg<float>::BM;
+  std::vector<P2Seg> segs;
+  std::vector<P2Leaf> p2;
+  int max_leaf = 0;
+  for (size_t l = 0; l < leaves.size(); l++) {
+    const int tau = leaves[l];
+    const int seg0 = (int)segs.size();
+    for (int c = tau; c >= 0; c = cl[c].parent) {
+      if (K[c] == 0) continue;
+      P2Seg s{};
+      s.a_off = fac_off[c] + (cl[tau].begin - cl[c].begin) * K[c];
+      s.b_row = slot_base[c];
+      s.lda = (int)K[c];
+      s.K = (int)K[c];
+      s.near = 0;
+      segs.push_back(s);
+    }
+    for (size_t i = 0; i < partners[l].size(); i++) {
+      P2Seg s{};
+      s.a_off = near_off[l] + pcol[l][i];
+      s.b_row = cl[partners[l][i].sigma].begin;
+      s.lda = (int)kn[l];
+      s.K = (int)csize(partners[l][i].sigma);
+      s.near = 1;
+      segs.push_back(s);
+    }
+    const int nt = (int)csize(tau);
+    max_leaf = std::max(max_leaf, nt);
+    for (int r0 = 0; r0 < nt; r0 += BM) {
+      P2Leaf lf{};
+      lf.row0 = cl[tau].begin + r0;
+      lf.rows = std::min(BM, nt - r0);
+      lf.seg0 = seg0;
+      lf.nseg = (int)segs.size() - seg0;
+      lf.pad = r0;  // row offset inside the leaf (applied to every segment's A)
+      p2.push_back(lf);
+    }
+  }
+  // upload
+  std::vector<char> tmp;
+  auto upload_vals = [&](DevBuf& dst, const std::vector<double>& src) -> fkf_status {
+    tmp.resize(src.size() * w);
+    if (w == 8)
+      fill_typed<double>(tmp.data(), src.data(), src.size());
+    else
+      fill_typed<float>(tmp.data(), src.data(), src.size());
+    return dev_upload(ctx, dst, tmp.data(), tmp.size());
+  };
+  FKF_TRY(upload_vals(h->fac, facv));
+  FKF_TRY(upload_vals(h->nearv, nearv));
+  std::vector<char>().swap(tmp);
+  FKF_TRY(dev_upload(ctx, h->slotmap, smap.data(), smap.size() * sizeof(int64_t)));
+  if (!p1.empty()) FKF_TRY(dev_upload(ctx, h->p1items, p1.data(), p1.size() * sizeof(P1Item)));
+  if (!p1r.empty()) FKF_TRY(dev_upload(ctx, h->p1red, p1r.data(), p1r.size() * sizeof(P1Reduce)));
+  FKF_TRY(dev_upload(ctx, h->p2seg, segs.data(), std::max<size_t>(segs.size(), 1) * sizeof(P2Seg)));
+  FKF_TRY(dev_upload(ctx, h->p2leaf, p2.data(), p2.size() * sizeof(P2Leaf)));
+  h->n_p1 = (int64_t)p1.size();
+  h->n_p1red = (int64_t)p1r.size();
+  h->n_leaf = (int64_t)p2.size();
+  h->ktot = ktot;
+  h->part_rows = part_rows;
+  h->max_leaf = max_leaf;
+  // statistics
+  fkf_hmat_info& in = h->info;
+  in.n = hh.n;
+  in.dim = hh.dim;
+  in.precision = h->prec;
+  in.n_clusters = nc;
+  in.n_leaves = (int64_t)leaves.size();
+  in.n_far = (int64_t)hh.far.size();
+  in.n_near = (int64_t)hh.near.size();
+  int64_t fe = 0, maxk = 0, near_used = 0;
+  double ksum = 0;
+  for (auto& fb : hh.far) {
+    fe += (int64_t)fb.k * (csize(fb.t) + csize(fb.s));
+    maxk = std::max<int64_t>(maxk, fb.k);
+    ksum += fb.k;
+  }
+  for (auto [t, s] : hh.near) near_used += (t == s ? 1 : 2) * csize(t) * csize(s);
+  in.far_entries = fe;
+  in.near_entries = (int64_t)hh.near_val.size();
+  in.max_rank = maxk;
+  in.mean_rank = hh.far.empty() ? 0.0 : ksum / hh.far.size();
+  in.flops_per_col = 2 * (2 * fe + near_used);
+  in.bytes_per_col = 2 * hh.n * (int64_t)w;
+  in.operator_bytes = (fe + in.near_entries) * (int64_t)w;
+  in.device_bytes = (int64_t)(h->fac.bytes + h->nearv.bytes + h->slotmap.bytes + h->p1items.bytes +
+                              h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes);
+  in.build_seconds = hh.build_seconds;
+  return FKF_OK;
+}

@@ -1,0 +1,272 @@
+"""Python binding of the C-ABI in include/fkf.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and performs
+no arithmetic of the method: device work runs in libfkf.so.  Device buffers
+are passed as torch CUDA tensors (their data_ptr()); host buffers as numpy
+arrays.  A non-OK status raises FkfError carrying fkf_last_error().
+
+The library is loaded from this package directory; importing this module on a
+machine without the built library raises ImportError (there is no fallback).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfkf.so")
+
+FKF_OK, FKF_EINVAL, FKF_ENOMEM, FKF_ENOTSPD, FKF_ENOCONV, FKF_ETIMEOUT, FKF_ECUDA, FKF_ESTATE = range(8)
+STATUS_NAMES = {
+    0: "FKF_OK", 1: "FKF_EINVAL", 2: "FKF_ENOMEM", 3: "FKF_ENOTSPD",
+    4: "FKF_ENOCONV", 5: "FKF_ETIMEOUT", 6: "FKF_ECUDA", 7: "FKF_ESTATE",
+}
+FKF_FP64, FKF_FP32 = 0, 1
+FKF_STEP_INPUTS_ON_DEVICE = 1
+FKF_STEP_SKIP_MEAN_SYNC = 2
+
+
+class fkf_matern(C.Structure):
+    _fields_ = [("nu", C.c_double), ("ell", C.c_double), ("sigma2", C.c_double)]
+
+
+class fkf_hparams(C.Structure):
+    _fields_ = [("leaf", C.c_int32), ("eta", C.c_double), ("aca_tol", C.c_double), ("k_cap", C.c_int32)]
+
+
+class fkf_hmat_info(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("dim", C.c_int32), ("precision", C.c_int32),
+        ("n_clusters", C.c_int64), ("n_leaves", C.c_int64), ("n_far", C.c_int64), ("n_near", C.c_int64),
+        ("far_entries", C.c_int64), ("near_entries", C.c_int64), ("max_rank", C.c_int64),
+        ("mean_rank", C.c_double), ("device_bytes", C.c_int64), ("flops_per_col", C.c_int64),
+        ("bytes_per_col", C.c_int64), ("operator_bytes", C.c_int64), ("build_seconds", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FkfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() or paper_1405_2276_gb300/builder.py")
+_lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_sigs = {
+    "fkf_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P]),
+    "fkf_destroy": (None, [_P]),
+    "fkf_last_error": (C.c_char_p, [_P]),
+    "fkf_launch_count": (C.c_int64, [_P]),
+    "fkf_library_call_count": (C.c_int64, [_P]),
+    "fkf_hmatrix_build": (C.c_int, [_P, _P, C.c_int64, C.c_int32, fkf_matern, fkf_hparams, C.c_int, C.POINTER(_P)]),
+    "fkf_hmatrix_info": (C.c_int, [_P, C.POINTER(fkf_hmat_info)]),
+    "fkf_hmatrix_apply": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_hmatrix_apply_clustered": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_hmatrix_permutation": (C.c_int, [_P, _P]),
+    "fkf_hmatrix_densify": (C.c_int, [_P, _P]),
+    "fkf_hmatrix_destroy": (None, [_P]),
+    "fkf_filter_create": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_P)]),
+    "fkf_filter_destroy": (None, [_P]),
+    "fkf_filter_step": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.c_double, C.c_int32, _P]),
+    "fkf_filter_get": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64]),
+    "fkf_variance": (C.c_int, [_P, _P]),
+    "fkf_conditional_realization": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "fkf_uncertainty_scalars": (C.c_int, [_P, _P, _P]),
+    "fkf_filter_orthonormality": (C.c_int, [_P, _P]),
+    "fkf_filter_refresh": (C.c_int, [_P]),
+    "fkf_filter_checkpoint": (C.c_int, [_P, C.c_char_p]),
+    "fkf_filter_restore": (C.c_int, [_P, C.c_char_p]),
+    "fkf_filter_phase_times": (C.c_int, [_P, _P]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+def _ptr(x):
+    """Pointer of a torch tensor (data_ptr), numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+class Handle:
+    """Opaque pointer with the context it reports errors on."""
+
+    def __init__(self, ptr, ctx=None):
+        self.ptr = ptr
+        self.ctx = ctx if ctx is not None else self
+
+
+def _check(status, ctx):
+    if status != FKF_OK:
+        msg = _lib.fkf_last_error(ctx.ptr if ctx is not None else None)
+        raise FkfError(status, msg.decode() if msg else "")
+
+
+# ---- context -----------------------------------------------------------------
+def fkf_create(device: int = 0, cuda_stream: int | None = None) -> Handle:
+    out = _P()
+    st = _lib.fkf_create(C.byref(out), device, cuda_stream)
+    if st != FKF_OK:
+        raise FkfError(st, "fkf_create failed (no CUDA device or bad arguments)")
+    return Handle(out.value)
+
+
+def fkf_destroy(ctx: Handle) -> None:
+    _lib.fkf_destroy(ctx.ptr)
+
+
+def fkf_last_error(ctx: Handle) -> str:
+    return _lib.fkf_last_error(ctx.ptr).decode()
+
+
+def fkf_launch_count(ctx: Handle) -> int:
+    return int(_lib.fkf_launch_count(ctx.ptr))
+
+
+def fkf_library_call_count(ctx: Handle) -> int:
+    return int(_lib.fkf_library_call_count(ctx.ptr))
+
+
+# ---- H-matrix ------------------------------------------------------------------
+def fkf_hmatrix_build(ctx, points, nu, ell, sigma2, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32, precision=FKF_FP64):
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = pts.shape
+    out = _P()
+    st = _lib.fkf_hmatrix_build(ctx.ptr, pts.ctypes.data, n, dim, fkf_matern(nu, ell, sigma2),
+                                fkf_hparams(leaf, eta, aca_tol, k_cap), precision, C.byref(out))
+    _check(st, ctx)
+    return Handle(out.value, ctx)
+
+
+def fkf_hmatrix_info(h) -> dict:
+    info = fkf_hmat_info()
+    _check(_lib.fkf_hmatrix_info(h.ptr, C.byref(info)), h.ctx)
+    return info.as_dict()
+
+
+def fkf_hmatrix_apply(h, X, Y, ncols=None, ldx=None, ldy=None):
+    ncols = X.shape[1] if ncols is None else ncols
+    ldx = X.stride(0) if ldx is None else ldx
+    ldy = Y.stride(0) if ldy is None else ldy
+    _check(_lib.fkf_hmatrix_apply(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
+
+
+def fkf_hmatrix_apply_clustered(h, X, Y, ncols=None, ldx=None, ldy=None):
+    ncols = X.shape[1] if ncols is None else ncols
+    ldx = X.stride(0) if ldx is None else ldx
+    ldy = Y.stride(0) if ldy is None else ldy
+    _check(_lib.fkf_hmatrix_apply_clustered(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
+
+
+def fkf_hmatrix_permutation(h, n):
+    out = np.zeros(n, dtype=np.int64)
+    _check(_lib.fkf_hmatrix_permutation(h.ptr, out.ctypes.data), h.ctx)
+    return out
+
+
+def fkf_hmatrix_densify(h, n):
+    out = np.zeros((n, n))
+    _check(_lib.fkf_hmatrix_densify(h.ptr, out.ctypes.data), h.ctx)
+    return out
+
+
+def fkf_hmatrix_destroy(h) -> None:
+    _lib.fkf_hmatrix_destroy(h.ptr)
+
+
+# ---- filter --------------------------------------------------------------------
+def fkf_filter_create(h, s0=None, alpha0=0.0, trunc_tol=1e-12, m_max=1024, r_max=2048):
+    s0p = None
+    if s0 is not None:
+        s0 = np.ascontiguousarray(s0, dtype=np.float64)
+        s0p = s0.ctypes.data
+    out = _P()
+    _check(_lib.fkf_filter_create(h.ptr, s0p, alpha0, trunc_tol, m_max, r_max, C.byref(out)), h.ctx)
+    return Handle(out.value, h.ctx)
+
+
+def fkf_filter_destroy(f) -> None:
+    _lib.fkf_filter_destroy(f.ptr)
+
+
+def fkf_filter_step(f, y, m, rowptr, col, val, R=None, r_scalar=0.0, flags=0, want_nll=True):
+    """y, rowptr (int64), col (int32), val (float64), R: numpy host arrays or,
+    with FKF_STEP_INPUTS_ON_DEVICE in flags, torch CUDA tensors."""
+    nll = C.c_double(0.0)
+    st = _lib.fkf_filter_step(f.ptr, _ptr(y), m, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(R), r_scalar, flags,
+                              C.byref(nll) if want_nll else None)
+    _check(st, f.ctx)
+    return nll.value
+
+
+def fkf_filter_get(f, n, want_s=True, want_D=True, W=None):
+    alpha = C.c_double(0)
+    r = C.c_int32(0)
+    s = np.zeros(n) if want_s else None
+    # rank first, to size D
+    _check(_lib.fkf_filter_get(f.ptr, None, C.byref(alpha), C.byref(r), None, None, 0), f.ctx)
+    D = np.zeros(max(r.value, 1)) if want_D else None
+    _check(_lib.fkf_filter_get(f.ptr, _ptr(s), None, None, _ptr(D), _ptr(W), W.stride(0) if W is not None else 0),
+           f.ctx)
+    return dict(s=s, alpha=alpha.value, r=r.value, D=D[: r.value] if D is not None else None)
+
+
+def fkf_variance(f, var_dev) -> None:
+    _check(_lib.fkf_variance(f.ptr, _ptr(var_dev)), f.ctx)
+
+
+def fkf_conditional_realization(f, a_dev, out_dev, ns=None) -> None:
+    ns = a_dev.shape[1] if ns is None else ns
+    _check(_lib.fkf_conditional_realization(f.ptr, _ptr(a_dev), ns, _ptr(out_dev)), f.ctx)
+
+
+def fkf_uncertainty_scalars(f):
+    e = C.c_double(0)
+    t = C.c_double(0)
+    _check(_lib.fkf_uncertainty_scalars(f.ptr, C.byref(e), C.byref(t)), f.ctx)
+    return e.value, t.value
+
+
+def fkf_filter_orthonormality(f) -> float:
+    e = C.c_double(0)
+    _check(_lib.fkf_filter_orthonormality(f.ptr, C.byref(e)), f.ctx)
+    return e.value
+
+
+def fkf_filter_refresh(f) -> None:
+    _check(_lib.fkf_filter_refresh(f.ptr), f.ctx)
+
+
+def fkf_filter_checkpoint(f, path: str) -> None:
+    _check(_lib.fkf_filter_checkpoint(f.ptr, path.encode()), f.ctx)
+
+
+def fkf_filter_restore(f, path: str) -> None:
+    _check(_lib.fkf_filter_restore(f.ptr, path.encode()), f.ctx)
+
+
+def fkf_filter_phase_times(f):
+    out = (C.c_double * 6)()
+    _check(_lib.fkf_filter_phase_times(f.ptr, out), f.ctx)
+    return list(out)

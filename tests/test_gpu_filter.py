@@ -1,0 +1,284 @@
+"""Filter steps on the GPU (through the C-ABI) against the oracle's dense
+Kalman filter (O1) and the fixed-H cross-covariance recursion (O2).
+
+Tolerances:
+  * FP64 path with Gamma_H = Gamma (eta = 0, every block dense): relative
+    1e-10 on s_hat, diag(Sigma), NLL and the full Sigma (the only differences
+    are rounding orders);
+  * FP64 path with a compressed Gamma_H (ACA tolerance tol): the oracle uses
+    the exact Gamma, so the bound is tol times the filter's sensitivity to a
+    relative perturbation of Gamma, estimated by the oracle itself (perturb
+    Gamma, rerun O1), times a safety factor of 100;
+  * FP32 path: its error against the oracle is reported and bounded loosely.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import covariance, kalman, uq
+from tests.helpers import TINY, lib, rel_err, run_filter, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fkf():
+    from paper_1405_2276_gb300 import build
+
+    build()
+    return lib()
+
+
+def _tiny(steps=None):
+    wl = workload(TINY, steps)
+    pts = wl["points"]
+    G = covariance.dense_gamma(pts, TINY["nu"], TINY["ell"], TINY["sigma2"])
+    steps_gpu = [(wl["y"][k], wl["H"], TINY["noise"]) for k in range(wl["y"].shape[0])]
+    Hd = synth.csr_to_dense(wl["H"])
+    steps_o = [(wl["y"][k], Hd, TINY["noise"]) for k in range(wl["y"].shape[0])]
+    return wl, pts, G, steps_gpu, steps_o
+
+
+KERN = (TINY["nu"], TINY["ell"], TINY["sigma2"])
+
+
+def test_fp64_exact_gamma_matches_dense_kf(fkf):
+    wl, pts, G, sg, so = _tiny()
+    ref = kalman.kf_dense(G, so)
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=0, eta=0.0, want_W=True)
+    m = wl["H"].nrows
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert a["alpha"] == k + 1
+        assert 0 < a["r"] <= m
+        assert rel_err(a["s"], b["s"]) < 1e-10, k
+        assert rel_err(a["var"], b["var"]) < 1e-10, k
+        assert abs(a["nll"] - b["nll"]) < 1e-10 * abs(b["nll"]), k
+        # full covariance alpha Gamma - W D W^T  (fixes span(W), basis-free)
+        Sig = a["alpha"] * G - (a["W"] * a["D"]) @ a["W"].T
+        assert rel_err(Sig, b["Sigma"]) < 1e-10, k
+        assert np.all(a["D"] > 0) and np.all(a["D"] < a["alpha"])
+    # W^T Gamma^-1 W = I
+    W = got[-1]["W"]
+    np.testing.assert_allclose(W.T @ np.linalg.solve(G, W), np.eye(W.shape[1]), atol=1e-8)
+    assert fkf.fkf_filter_orthonormality(f) < 1e-9
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def _sensitivity(G, so, delta=1e-8, seed=0):
+    """Oracle-only estimate of the relative change of O1's outputs per unit
+    relative symmetric perturbation of Gamma."""
+    rng = np.random.default_rng(seed)
+    E = rng.standard_normal(G.shape)
+    E = 0.5 * (E + E.T)
+    E *= delta * np.linalg.norm(G) / np.linalg.norm(E)
+    a = kalman.kf_dense(G, so, keep_cov=False)
+    b = kalman.kf_dense(G + E, so, keep_cov=False)
+    amp = 0.0
+    for x, y in zip(a, b):
+        amp = max(amp, rel_err(y["s"], x["s"]) / delta, rel_err(y["var"], x["var"]) / delta)
+    return amp
+
+
+def test_fp64_compressed_gamma_within_compression_bound(fkf):
+    wl, pts, G, sg, so = _tiny()
+    ref = kalman.kf_dense(G, so, keep_cov=False)
+    tol = 1e-8
+    amp = _sensitivity(G, so)
+    bound = 100 * amp * tol
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=0, eta=1.0, aca_tol=tol, leaf=64)
+    assert fkf.fkf_hmatrix_info(hm)["n_far"] > 0
+    worst = max(max(rel_err(a["s"], b["s"]), rel_err(a["var"], b["var"])) for a, b in zip(got, ref))
+    print(f"compressed FP64 vs exact-Gamma oracle: worst rel err {worst:.3e} (bound {bound:.3e}, amp {amp:.1f})")
+    assert worst < bound
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_time_varying_operators_match_dense_kf(fkf):
+    """A new H_k (and a new m_k) every step: the rank grows as sum m_k and the
+    general path (orthonormalisation + merge) is exercised."""
+    rng = np.random.default_rng(synth.BASE_SEED + 100)
+    nx = ny = 24
+    pts = synth.grid_points_2d(nx, ny)
+    ms = [5, 12, 7, 20, 9, 16, 3]
+    ops = synth.varying_ray_operators(rng, nx, ny, ms)
+    truth = synth.random_walk_truth(rng, (nx, ny), len(ms), 0.2, 1.0)
+    ys = [synth.measurements(rng, h, truth[k], 1e-4) for k, h in enumerate(ops)]
+    G = covariance.dense_gamma(pts, 1.5, 0.25, 1.0)
+    so = [(ys[k], synth.csr_to_dense(ops[k]), 1e-4) for k in range(len(ms))]
+    ref = kalman.kf_dense(G, so)
+    sg = [(ys[k], ops[k], 1e-4) for k in range(len(ms))]
+    got, ctx, hm, f = run_filter(pts, (1.5, 0.25, 1.0), sg, precision=0, eta=0.0, leaf=32, want_W=True,
+                                 m_max=max(ms), r_max=sum(ms))
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert a["r"] <= sum(ms[: k + 1])
+        assert rel_err(a["s"], b["s"]) < 1e-10, k
+        assert rel_err(a["var"], b["var"]) < 1e-10, k
+        Sig = a["alpha"] * G - (a["W"] * a["D"]) @ a["W"].T
+        assert rel_err(Sig, b["Sigma"]) < 1e-10, k
+        assert abs(a["nll"] - b["nll"]) < 1e-10 * abs(b["nll"]), k
+    assert got[-1]["r"] > max(ms)  # rank really grew
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_diagonal_R_and_zero_rows(fkf):
+    """Per-measurement noise variances and an all-zero row of H."""
+    rng = np.random.default_rng(5)
+    nx, ny = 16, 12
+    pts = synth.grid_points_2d(nx, ny)
+    ops = synth.varying_ray_operators(rng, nx, ny, [6, 6, 6])
+    # zero out row 2 of the second operator
+    h = ops[1]
+    keep = np.ones(h.nnz, bool)
+    keep[h.rowptr[2] : h.rowptr[3]] = False
+    cnt = np.diff(h.rowptr)
+    cnt[2] = 0
+    ops[1] = synth.Csr(np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64), h.col[keep], h.val[keep], h.ncols)
+    Rs = [rng.uniform(5e-5, 5e-4, 6) for _ in range(3)]
+    ys = [rng.standard_normal(6) for _ in range(3)]
+    G = covariance.dense_gamma(pts, 0.5, 0.3, 1.5)
+    ref = kalman.kf_dense(G, [(ys[k], synth.csr_to_dense(ops[k]), Rs[k]) for k in range(3)])
+    got, ctx, hm, f = run_filter(pts, (0.5, 0.3, 1.5), [(ys[k], ops[k], Rs[k]) for k in range(3)], eta=0.0, leaf=16)
+    for a, b in zip(got, ref):
+        assert rel_err(a["s"], b["s"]) < 1e-10
+        assert rel_err(a["var"], b["var"]) < 1e-10
+        assert abs(a["nll"] - b["nll"]) < 1e-10 * abs(b["nll"])
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_fp32_path_error_vs_oracle(fkf):
+    wl, pts, G, sg, so = _tiny()
+    ref = kalman.kf_dense(G, so, keep_cov=False)
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=1, eta=1.0, aca_tol=1e-8)
+    es = max(rel_err(a["s"], b["s"]) for a, b in zip(got, ref))
+    ev = max(rel_err(a["var"], b["var"]) for a, b in zip(got, ref))
+    print(f"FP32 path vs FP64 oracle: s_hat rel err {es:.3e}, variance rel err {ev:.3e}")
+    assert es < 5e-3 and ev < 5e-3
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_realization_variance_and_scalars(fkf):
+    import torch
+
+    wl, pts, G, sg, so = _tiny(steps=4)
+    ref = kalman.kf_dense(G, so)
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=0, eta=0.0)
+    n = pts.shape[0]
+    Sig = ref[-1]["Sigma"]
+    alpha = got[-1]["alpha"]
+    rng = np.random.default_rng(9)
+    L = np.linalg.cholesky(G)
+    a = L @ rng.standard_normal((n, 16))
+    a_t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.empty_like(a_t)
+    fkf.fkf_conditional_realization(f, a_t, out)
+    x_ref = uq.realization(ref[-1]["s"], Sig, G, alpha, a)
+    assert rel_err(out.cpu().numpy(), x_ref) < 1e-9
+    ent, tr = fkf.fkf_uncertainty_scalars(f)
+    assert abs(ent - uq.relative_entropy(Sig, G)) < 1e-8 * abs(ent)
+    assert abs(tr - uq.a_optimality_identity(Sig)) < 1e-10 * abs(tr)
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_checkpoint_restore_is_bitwise(fkf, tmp_path):
+    wl, pts, G, sg, so = _tiny()
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, *KERN, leaf=64, eta=1.0, aca_tol=1e-8)
+    n = pts.shape[0]
+    m = wl["H"].nrows
+
+    def step(f, k):
+        h = wl["H"]
+        return fkf.fkf_filter_step(f, wl["y"][k], m, h.rowptr, h.col, h.val, None, TINY["noise"])
+
+    f1 = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)
+    for k in range(5):
+        step(f1, k)
+    path = str(tmp_path / "ck.bin")
+    fkf.fkf_filter_checkpoint(f1, path)
+    n1 = [step(f1, k) for k in range(5, 8)]
+    s1 = fkf.fkf_filter_get(f1, n)
+    f2 = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)
+    fkf.fkf_filter_restore(f2, path)
+    n2 = [step(f2, k) for k in range(5, 8)]
+    s2 = fkf.fkf_filter_get(f2, n)
+    assert n1 == n2
+    np.testing.assert_array_equal(s1["s"], s2["s"])
+    np.testing.assert_array_equal(s1["D"], s2["D"])
+    assert s1["alpha"] == s2["alpha"] == 8
+    for f in (f1, f2):
+        fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_invalid_inputs_leave_state_unchanged(fkf):
+    wl, pts, G, sg, so = _tiny(steps=3)
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, *KERN, leaf=64, eta=0.0)
+    n = pts.shape[0]
+    h = wl["H"]
+    m = h.nrows
+    f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)
+    fkf.fkf_filter_step(f, wl["y"][0], m, h.rowptr, h.col, h.val, None, 1e-4)
+    before = fkf.fkf_filter_get(f, n)
+    bad_col = h.col.copy()
+    bad_col[3] = n + 5
+    cases = [
+        dict(col=bad_col, R=None, rs=1e-4, m=m),
+        dict(col=h.col, R=None, rs=-1.0, m=m),
+        dict(col=h.col, R=np.full(m, 0.0), rs=0.0, m=m),
+        dict(col=h.col, R=None, rs=1e-4, m=m + 1),
+    ]
+    for c in cases:
+        with pytest.raises(fkf.FkfError) as e:
+            rowptr = h.rowptr if c["m"] == m else np.concatenate([h.rowptr, h.rowptr[-1:]])
+            fkf.fkf_filter_step(f, np.zeros(c["m"]), c["m"], rowptr, c["col"], h.val, c["R"], c["rs"])
+        assert e.value.status == fkf.FKF_EINVAL
+        after = fkf.fkf_filter_get(f, n)
+        np.testing.assert_array_equal(after["s"], before["s"])
+        np.testing.assert_array_equal(after["D"], before["D"])
+        assert after["alpha"] == before["alpha"] and after["r"] == before["r"]
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_refresh_keeps_covariance(fkf):
+    wl, pts, G, sg, so = _tiny(steps=6)
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=0, eta=0.0)
+    import torch
+
+    n = pts.shape[0]
+    v0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    fkf.fkf_variance(f, v0)
+    fkf.fkf_filter_refresh(f)
+    v1 = torch.empty_like(v0)
+    fkf.fkf_variance(f, v1)
+    assert rel_err(v1.cpu().numpy(), v0.cpu().numpy()) < 1e-10
+    assert fkf.fkf_filter_orthonormality(f) < 1e-10
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_fixed_geometry_rank_stays_at_m(fkf):
+    wl, pts, G, sg, so = _tiny()
+    got, ctx, hm, f = run_filter(pts, KERN, sg, precision=0, eta=1.0, aca_tol=1e-8, want_var=False)
+    m = wl["H"].nrows
+    assert all(g["r"] <= m for g in got)
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)

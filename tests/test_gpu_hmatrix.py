@@ -1,0 +1,144 @@
+"""H-matrix apply on the GPU (through the C-ABI) against the oracle's exact
+Matern products (direct summation / dense Gamma)."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import covariance
+from tests.helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fkf():
+    from paper_1405_2276_gb300 import build
+
+    build()
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def ctx(fkf):
+    c = fkf.fkf_create(0)
+    yield c
+    fkf.fkf_destroy(c)
+
+
+def _apply(fkf, hm, X, prec):
+    import torch
+
+    dt = torch.float64 if prec == fkf.FKF_FP64 else torch.float32
+    Xt = torch.from_numpy(X).to("cuda", dt).contiguous()
+    Yt = torch.empty_like(Xt)
+    fkf.fkf_hmatrix_apply(hm, Xt, Yt)
+    return Yt.double().cpu().numpy()
+
+
+CASES = [
+    # grid, leaf, nu, ell, precision, aca_tol, tolerance on max|err|/max|ref|
+    ((37, 23), 16, 1.5, 0.2, 0, 1e-10, 2e-8),
+    ((32, 32), 64, 1.5, 0.2, 0, 1e-10, 2e-8),
+    ((64, 48), 32, 0.5, 0.1, 0, 1e-10, 2e-8),
+    ((37, 23), 16, 1.5, 0.2, 1, 1e-10, 2e-5),
+    ((64, 48), 32, 0.5, 0.1, 1, 1e-8, 2e-5),
+]
+
+
+@pytest.mark.parametrize("grid,leaf,nu,ell,prec,tol,bound", CASES)
+def test_apply_matches_dense_gamma(fkf, ctx, grid, leaf, nu, ell, prec, tol, bound):
+    pts = synth.grid_points_2d(*grid)
+    n = pts.shape[0]
+    G = covariance.dense_gamma(pts, nu, ell, 1.0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, nu, ell, 1.0, leaf=leaf, eta=1.0, aca_tol=tol, k_cap=64, precision=prec)
+    info = fkf.fkf_hmatrix_info(hm)
+    assert info["n"] == n and info["n_far"] > 0
+    rng = np.random.default_rng(7)
+    for ncols in (1, 7, 130, 300):
+        X = rng.standard_normal((n, ncols))
+        Y = _apply(fkf, hm, X, prec)
+        ref = G @ X
+        err = np.abs(Y - ref).max() / np.abs(ref).max()
+        assert err < bound, (ncols, err)
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eta_zero_is_exact_and_symmetric(fkf, ctx, prec):
+    """eta = 0: every block dense, so Gamma_H = Gamma up to rounding; the
+    densified operator is exactly symmetric (each entry is stored once)."""
+    pts = synth.grid_points_2d(20, 13)
+    n = pts.shape[0]
+    G = covariance.dense_gamma(pts, 1.5, 0.3, 2.0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.3, 2.0, leaf=16, eta=0.0, precision=prec)
+    assert fkf.fkf_hmatrix_info(hm)["n_far"] == 0
+    D = fkf.fkf_hmatrix_densify(hm, n)
+    np.testing.assert_array_equal(D, D.T)
+    np.testing.assert_allclose(D, G, rtol=0, atol=(1e-15 if prec == 0 else 1e-7) * 2.0)
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_compressed_operator_exactly_symmetric(fkf, ctx):
+    pts = synth.grid_points_2d(40, 30)
+    n = pts.shape[0]
+    for prec in (0, 1):
+        hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.1, 1.0, leaf=32, eta=1.0, aca_tol=1e-6, precision=prec)
+        D = fkf.fkf_hmatrix_densify(hm, n)
+        np.testing.assert_array_equal(D, D.T)
+        G = covariance.dense_gamma(pts, 0.5, 0.1, 1.0)
+        # block-wise relative Frobenius tolerance 1e-6 -> global relative Frobenius error of that order
+        assert np.linalg.norm(D - G) / np.linalg.norm(G) < 1e-5
+        fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_permutation_is_a_permutation(fkf, ctx):
+    pts = synth.grid_points_2d(37, 23)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.2, 1.0, leaf=16)
+    p = fkf.fkf_hmatrix_permutation(hm, pts.shape[0])
+    np.testing.assert_array_equal(np.sort(p), np.arange(pts.shape[0]))
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_ragged_3d_points(fkf, ctx):
+    pts = synth.grid_points_3d(9, 7, 11)
+    n = pts.shape[0]
+    G = covariance.dense_gamma(pts, 0.5, 0.3, 1.0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.3, 1.0, leaf=40, eta=1.0, aca_tol=1e-10, k_cap=48)
+    X = np.random.default_rng(3).standard_normal((n, 33))
+    Y = _apply(fkf, hm, X, 0)
+    assert np.abs(Y - G @ X).max() / np.abs(G @ X).max() < 2e-8
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+@pytest.mark.parametrize("prec,bound", [(0, 1e-6), (1, 3e-5)])
+def test_medium_grid_sampled_rows(fkf, ctx, prec, bound):
+    """256 x 256 grid (N = 65,536), nu = 3/2, ell = 0.1, leaf 64, ACA 1e-8,
+    eta = 1, rank cap 32: sampled rows of Gamma_H X against direct sums."""
+    pts = synth.grid_points_2d(256, 256)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.1, 1.0, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32, precision=prec)
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((n, 200))
+    Y = _apply(fkf, hm, X, prec)
+    rows = rng.choice(n, 48, replace=False)
+    ref = covariance.gamma_rows_times(pts, rows, X, 1.5, 0.1, 1.0)
+    err = np.abs(Y[rows] - ref).max() / np.abs(ref).max()
+    assert err < bound, err
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_invalid_arguments(fkf, ctx):
+    pts = synth.grid_points_2d(8, 8)
+    with pytest.raises(fkf.FkfError) as e:
+        fkf.fkf_hmatrix_build(ctx, pts, 0.7, 0.2, 1.0)
+    assert e.value.status == fkf.FKF_EINVAL
+    with pytest.raises(fkf.FkfError):
+        fkf.fkf_hmatrix_build(ctx, pts, 0.5, -1.0, 1.0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.2, 1.0, leaf=8)
+    import torch
+
+    X = torch.zeros((64, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(fkf.FkfError):  # X and Y overlap
+        fkf.fkf_hmatrix_apply(hm, X, X)
+    fkf.fkf_hmatrix_destroy(hm)

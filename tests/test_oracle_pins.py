@@ -84,7 +84,9 @@ def test_grid_fft_product_equals_dense(shape):
     pts = synth.grid_points_2d(*shape) if len(shape) == 2 else synth.grid_points_3d(*shape)
     G = covariance.dense_gamma(pts, 1.5, 0.3, 1.3)
     X = rng.standard_normal((pts.shape[0], 5))
-    np.testing.assert_allclose(covariance.grid_gamma_times(shape, X, 1.5, 0.3, 1.3), G @ X, rtol=0, atol=1e-12 * np.abs(G @ X).max())
+    for workers in (None, 2):
+        Y = covariance.grid_gamma_times(shape, X, 1.5, 0.3, 1.3, workers=workers)
+        np.testing.assert_allclose(Y, G @ X, rtol=0, atol=1e-12 * np.abs(G @ X).max())
 
 
 def test_direct_row_sums_equal_dense():
