@@ -144,7 +144,8 @@ def test_diagonal_R_and_zero_rows(fkf):
     ys = [rng.standard_normal(6) for _ in range(3)]
     G = covariance.dense_gamma(pts, 0.5, 0.3, 1.5)
     ref = kalman.kf_dense(G, [(ys[k], synth.csr_to_dense(ops[k]), Rs[k]) for k in range(3)])
-    got, ctx, hm, f = run_filter(pts, (0.5, 0.3, 1.5), [(ys[k], ops[k], Rs[k]) for k in range(3)], eta=0.0, leaf=16)
+    got, ctx, hm, f = run_filter(pts, (0.5, 0.3, 1.5), [(ys[k], ops[k], Rs[k]) for k in range(3)], eta=0.0, leaf=16,
+                                 m_max=6, r_max=18)
     for a, b in zip(got, ref):
         assert rel_err(a["s"], b["s"]) < 1e-10
         assert rel_err(a["var"], b["var"]) < 1e-10
