@@ -129,6 +129,43 @@ fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* 
 /* Same product with X and Y already in cluster order (no permutation). */
 fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
                                        int64_t ncols);
+/* Size of the fixed device scratch used by fkf_hmatrix_apply_clustered_noalloc:
+ * one file-scope device array of this many bytes, which every GPU that loads
+ * this library holds until the process exits. */
+#define FKF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* fkf_hmatrix_apply_clustered without any device memory allocation.  The
+ * paper has no counterpart; this is a deployment variant of the same product.
+ *
+ * Who needs it: callers that must not call cudaMalloc/cudaFree while they
+ * run -- for example a real-time assimilation loop whose latency budget
+ * cannot absorb an allocator call (cudaMalloc can synchronise the device and
+ * block), or a host process whose device memory is entirely owned by another
+ * allocator (a framework's caching pool) so that extra driver allocations
+ * would fail or fragment it.  The regular apply grows library-owned
+ * workspaces with cudaMalloc on first use; this one never allocates.
+ *
+ * Same arguments, layout and result as fkf_hmatrix_apply_clustered (X, Y in
+ * cluster order, row-major, precision's element type; the caller passes and
+ * owns both).  The slot workspace and the split-reduction partials live in a
+ * library-wide static device array of FKF_NOALLOC_SCRATCH_BYTES bytes; the
+ * columns are processed in panels as wide as that array allows (at least one
+ * column).  An operator that needs more than FKF_NOALLOC_SCRATCH_BYTES for a
+ * single column is rejected with FKF_EINVAL and a message giving both sizes.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * array (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.
+ * Sharing: all calls, from every context and stream of the process, share
+ * the one array, which keeps the last call's contents; nothing in it has to
+ * start at zero (each call writes every element it later reads).  Calls that
+ * overlap on the GPU (different streams, or different host threads) race on
+ * the array and give wrong results: serialise them.
+ * The stream is synchronised before return, like fkf_hmatrix_apply_clustered.
+ * Errors: EINVAL (arguments, operator too large for the scratch), ECUDA. */
+fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev,
+                                               int64_t ldy, int64_t ncols);
 /* Permutation: perm[i] = original index of the i-th point in cluster order. */
 fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host);
 /* Dense copy of Gamma_H (host, N x N row-major, original order); N <= 8192. */

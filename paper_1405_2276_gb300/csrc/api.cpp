@@ -181,6 +181,16 @@ FKF_API fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, i
   return FKF_OK;
 }
 
+// Variant that never allocates device memory (static scratch; see fkf.h).
+FKF_API fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev,
+                                                       int64_t ldy, int64_t ncols) {
+  if (!h) return FKF_EINVAL;
+  FKF_TRY(check_apply_args(h, X_dev, ldx, Y_dev, ldy, ncols));
+  FKF_TRY(hmat_apply_clustered_noalloc(h, X_dev, ldx, Y_dev, ldy, ncols));
+  FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
                                      int64_t ncols) {
   if (!h) return FKF_EINVAL;

@@ -142,6 +142,8 @@ struct fkf_hmat {
 // happly.cu
 fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh);
 fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
+fkf_status hmat_apply_clustered_noalloc(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                        int64_t ncols);
 // dst[i, :] = src[idx[i], :] for i < nrows (element type = precision / FP64)
 fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const int64_t* idx_dev, void* dst,
                              int64_t ldd, int64_t nrows, int64_t ncols);

@@ -24,6 +24,7 @@
 // X_c is read once per cluster level instead of once per block.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "common.h"
 #include "hmat_host.h"
@@ -412,4 +413,85 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
                               h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes);
   in.build_seconds = hh.build_seconds;
   return FKF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Apply without allocating: the phase-1 slot workspace (Zmix) and the
+// split-reduction partials live in one file-scope device array of fixed size
+// instead of cudaMalloc'd buffers.  Columns are processed in panels as wide
+// as that array allows.  Every call (on any stream) shares the array, so
+// calls that overlap on the GPU race; nothing in it needs to start at zero
+// (phase 1 writes every slot row and every partial it later reads).
+// ----------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FKF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on ctx->device, looked up once per device
+// (with that device current) and cached.
+fkf_status noalloc_scratch(fkf_ctx* ctx, void** out) {
+  if (ctx->device < 0 || ctx->device >= kMaxDevices)
+    return set_err(ctx, FKF_EINVAL, "apply_noalloc: device index %d >= %d", ctx->device, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[ctx->device]) {
+    int prev = 0;
+    FKF_CUDA(ctx, cudaGetDevice(&prev));
+    FKF_CUDA(ctx, cudaSetDevice(ctx->device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess || !p)
+      return set_err(ctx, FKF_ECUDA, "apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[ctx->device] = p;
+  }
+  *out = g_noalloc_ptr[ctx->device];
+  return FKF_OK;
+}
+
+template <typename T>
+fkf_status apply_noalloc_impl(fkf_hmat* h, const T* X, int64_t ldx, T* Y, int64_t ldy, int64_t ncols) {
+  fkf_ctx* ctx = h->ctx;
+  void* base = nullptr;
+  FKF_TRY(noalloc_scratch(ctx, &base));
+  const int64_t rows = std::max<int64_t>(h->ktot, 1) + h->part_rows;
+  const int64_t P = std::min<int64_t>(ncols, (int64_t)(FKF_NOALLOC_SCRATCH_BYTES / (rows * (int64_t)sizeof(T))));
+  if (P < 1)
+    return set_err(ctx, FKF_EINVAL,
+                   "apply_noalloc: operator needs %lld bytes of scratch per column; the static scratch holds %lld "
+                   "bytes (use fkf_hmatrix_apply_clustered)",
+                   (long long)(rows * (int64_t)sizeof(T)), (long long)FKF_NOALLOC_SCRATCH_BYTES);
+  T* zmix = reinterpret_cast<T*>(base);
+  T* part = zmix + std::max<int64_t>(h->ktot, 1) * P;
+  constexpr int BN = TileCfg<T>::BN;
+  for (int64_t c0 = 0; c0 < ncols; c0 += P) {
+    const int nc = (int)std::min<int64_t>(P, ncols - c0);
+    const int ntile = (int)cdiv(nc, BN);
+    if (h->n_p1 > 0) {
+      k_phase1<T><<<dim3((unsigned)h->n_p1, ntile), kTileThreads, 0, ctx->stream>>>(
+          h->p1items.as<P1Item>(), h->fac.as<T>(), X + c0, ldx, nc, h->slotmap.as<int64_t>(), zmix, part, P);
+      FKF_LAUNCHED(ctx);
+    }
+    if (h->n_p1red > 0) {
+      k_phase1_reduce<T><<<dim3((unsigned)h->n_p1red, 4), 256, 0, ctx->stream>>>(
+          h->p1red.as<P1Reduce>(), part, h->slotmap.as<int64_t>(), zmix, P, nc);
+      FKF_LAUNCHED(ctx);
+    }
+    k_phase2<T><<<dim3((unsigned)h->n_leaf, ntile), kTileThreads, 0, ctx->stream>>>(
+        h->p2leaf.as<P2Leaf>(), h->p2seg.as<P2Seg>(), h->fac.as<T>(), h->nearv.as<T>(), zmix, P, X + c0, ldx,
+        Y + c0, ldy, nc);
+    FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+}  // namespace
+
+fkf_status hmat_apply_clustered_noalloc(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                        int64_t ncols) {
+  if (ncols <= 0) return FKF_OK;
+  if (h->prec == FKF_FP64)
+    return apply_noalloc_impl<double>(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
+  return apply_noalloc_impl<float>(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
 }

@@ -71,6 +71,7 @@ _sigs = {
     "fkf_hmatrix_info": (C.c_int, [_P, C.POINTER(fkf_hmat_info)]),
     "fkf_hmatrix_apply": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_hmatrix_apply_clustered": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_hmatrix_apply_clustered_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_hmatrix_permutation": (C.c_int, [_P, _P]),
     "fkf_hmatrix_densify": (C.c_int, [_P, _P]),
     "fkf_hmatrix_destroy": (None, [_P]),
@@ -177,6 +178,16 @@ def fkf_hmatrix_apply_clustered(h, X, Y, ncols=None, ldx=None, ldy=None):
     ldx = X.stride(0) if ldx is None else ldx
     ldy = Y.stride(0) if ldy is None else ldy
     _check(_lib.fkf_hmatrix_apply_clustered(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
+
+
+def fkf_hmatrix_apply_clustered_noalloc(h, X, Y, ncols=None, ldx=None, ldy=None):
+    """Same product as fkf_hmatrix_apply_clustered, for callers that cannot
+    allocate device memory: the library uses its fixed static scratch
+    (FKF_NOALLOC_SCRATCH_BYTES per GPU) and never calls cudaMalloc."""
+    ncols = X.shape[1] if ncols is None else ncols
+    ldx = X.stride(0) if ldx is None else ldx
+    ldy = Y.stride(0) if ldy is None else ldy
+    _check(_lib.fkf_hmatrix_apply_clustered_noalloc(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
 
 
 def fkf_hmatrix_permutation(h, n):
