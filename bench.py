@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "filter steps/s and H-apply GB/s at N=262k,m=1024, FP32 vs FP64 path at stated err"
 WORKLOAD = dict(grid=(512, 512), src=32, rec=32, nu=0.5, ell=0.05, sigma2=1.0, noise=1e-4, leaf=64, eta=1.0,
                 aca_tol=1e-8, k_cap=32)
+# smaller case of the same workload family (profiling captures only; never a bench line)
+MEDIUM = dict(grid=(256, 256), src=20, rec=20, nu=1.5, ell=0.1, sigma2=1.0, noise=1e-4, leaf=64, eta=1.0,
+              aca_tol=1e-8, k_cap=32)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 
@@ -104,7 +107,7 @@ def make_workload(steps, seed_offset=0):
 
     w = WORKLOAD
     t0 = time.time()
-    wl = synth.tomography_workload(w["grid"], w["src"], w["rec"], steps, 0.05, 1.0, w["noise"],
+    wl = synth.tomography_workload(w["grid"], w["src"], w["rec"], steps, w["ell"], w["sigma2"], w["noise"],
                                    seed=synth.BASE_SEED + 2 + 1000 * seed_offset)
     log(f"[bench] workload: N={wl['points'].shape[0]} m={wl['H'].nrows} nnz={wl['H'].nnz} "
         f"steps={steps} ({time.time() - t0:.1f}s)")
@@ -323,7 +326,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "medium"],
+                    help="medium = 256x256, m=400: for profiler captures only")
     args = ap.parse_args()
+    global WORKLOAD
+    if args.workload == "medium":
+        WORKLOAD = MEDIUM
     assert args.warmup >= 3, "at least 3 warm-up steps"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -220,9 +220,19 @@ fkf_status fkf_filter_refresh(fkf_filter* f);
 /* Checkpoint / restore of (k, alpha, r, s_hat, D, W, X) to a binary file. */
 fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path);
 fkf_status fkf_filter_restore(fkf_filter* f, const char* path);
+/* Numerical thresholds of the step (all relative, in [0, 1)):
+ *  gep_tol   -- data-space GEP modes with eigenvalue <= gep_tol * largest are
+ *               dropped (they carry no information: null directions of H);
+ *  orth_tol  -- candidate new directions whose Gamma^-1-norm squared outside
+ *               span(W) is <= orth_tol are taken as already in span(W)
+ *               (Alg. lowrankaddition step 2 made rank-revealing);
+ *  trunc_tol -- merged low-rank eigenvalues <= trunc_tol * largest are
+ *               truncated (Alg. lowrankaddition step 4).
+ * Defaults: FP64 1e-13 / 1e-10 / (create's trunc_tol); FP32 1e-7 / 1e-3 / same. */
+fkf_status fkf_filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol);
 /* Per-phase device time of the last step in milliseconds (CUDA events on the
- * context stream): [0] densify H^T, [1] H-apply, [2] data-space GEP and
- * innovation, [3] orthonormalisation + merge, [4] rotation, [5] mean update. */
+ * context stream): [0] densify H^T, [1] H-apply, [2] gathers, innovation and
+ * mean update, [3] data-space GEP, [4] orthonormalisation + merge, [5] rotation. */
 fkf_status fkf_filter_phase_times(fkf_filter* f, double* ms6);
 
 #ifdef __cplusplus

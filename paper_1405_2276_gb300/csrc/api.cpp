@@ -26,6 +26,7 @@ fkf_status filter_refresh(fkf_filter* f);
 fkf_status filter_checkpoint(fkf_filter* f, const char* path);
 fkf_status filter_restore(fkf_filter* f, const char* path);
 fkf_status filter_phase_times(fkf_filter* f, double* ms6);
+fkf_status filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol);
 fkf_ctx* filter_ctx(fkf_filter* f);
 
 fkf_status set_err(fkf_ctx* ctx, fkf_status st, const char* fmt, ...) {
@@ -306,6 +307,11 @@ FKF_API fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path) {
 FKF_API fkf_status fkf_filter_restore(fkf_filter* f, const char* path) {
   if (!f || !path) return FKF_EINVAL;
   return filter_restore(f, path);
+}
+
+FKF_API fkf_status fkf_filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol) {
+  if (!f) return FKF_EINVAL;
+  return filter_set_tolerances(f, gep_tol, orth_tol, trunc_tol);
 }
 
 FKF_API fkf_status fkf_filter_phase_times(fkf_filter* f, double* ms6) {

@@ -305,6 +305,21 @@ __global__ void k_transpose(int rows, int cols, const double* __restrict__ src, 
   }
 }
 
+// out = ||A||_F over n entries (single CTA)
+__global__ void k_frob(int64_t n, const double* __restrict__ A, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += A[e] * A[e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    out[0] = sqrt(t);
+  }
+}
+
 // A = (A + A^T) / 2 in place (n x n)
 __global__ void k_symmetrize(int n, double* __restrict__ A) {
   const int64_t total = (int64_t)n * n;
@@ -490,7 +505,9 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
   f->trunc_tol = trunc_tol;
   f->w = h->prec == FKF_FP64 ? 8 : 4;
   f->gep_tol = h->prec == FKF_FP64 ? 1e-13 : 1e-7;
-  f->orth_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-5;
+  // FP32 storage of W, X and G leaves a noise floor of ~1e-5 in the data-space
+  // Gram T; new directions are only accepted clearly above it.
+  f->orth_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-3;
   f->alpha = alpha0;
   auto fail = [&](fkf_status st) {
     delete f;
@@ -700,11 +717,20 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_TRY(gemm_f64(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
     k_add_identity<<<(int)cdiv(mlam, 256), 256, 0, st>>>(mlam, Tm, mlam, 1.0);
     FKF_LAUNCHED(ctx);
-    FKF_TRY(eigh_f64(ctx, mlam, Tm, f->th.as<double>(), th_h, f->eigws));
+    // every eigenvalue of T is bounded by ||T||_F: when that is below the
+    // threshold no new direction exists and the eigensolve is skipped
+    k_frob<<<1, 1024, 0, st>>>((int64_t)mlam * mlam, Tm, f->nll.as<double>() + 1);
+    FKF_LAUNCHED(ctx);
+    double tfrob = 0;
+    FKF_CUDA(ctx, cudaMemcpyAsync(&tfrob, f->nll.as<double>() + 1, 8, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
     mp = 0;
-    for (int i = mlam - 1; i >= 0; i--)
-      if (th_h[i] > f->orth_tol) mp++;
-      else break;
+    if (tfrob > f->orth_tol) {
+      FKF_TRY(eigh_f64(ctx, mlam, Tm, f->th.as<double>(), th_h, f->eigws));
+      for (int i = mlam - 1; i >= 0; i--)
+        if (th_h[i] > f->orth_tol) mp++;
+        else break;
+    }
     if (mp > 0) {
       k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 0, f->Po.as<double>(), mlam);
       FKF_LAUNCHED(ctx);
@@ -1096,6 +1122,15 @@ fkf_status filter_restore(fkf_filter* f, const char* path) {
   f->r = (int)r;
   f->k = hd.k;
   f->alpha = hd.alpha;
+  return FKF_OK;
+}
+
+fkf_status filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol) {
+  if (!(gep_tol >= 0 && gep_tol < 1) || !(orth_tol >= 0 && orth_tol < 1) || !(trunc_tol >= 0 && trunc_tol < 1))
+    return set_err(f->ctx, FKF_EINVAL, "set_tolerances: each tolerance must be in [0, 1)");
+  f->gep_tol = gep_tol;
+  f->orth_tol = orth_tol;
+  f->trunc_tol = trunc_tol;
   return FKF_OK;
 }
 

@@ -87,6 +87,7 @@ _sigs = {
     "fkf_filter_checkpoint": (C.c_int, [_P, C.c_char_p]),
     "fkf_filter_restore": (C.c_int, [_P, C.c_char_p]),
     "fkf_filter_phase_times": (C.c_int, [_P, _P]),
+    "fkf_filter_set_tolerances": (C.c_int, [_P, C.c_double, C.c_double, C.c_double]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -275,6 +276,10 @@ def fkf_filter_checkpoint(f, path: str) -> None:
 
 def fkf_filter_restore(f, path: str) -> None:
     _check(_lib.fkf_filter_restore(f.ptr, path.encode()), f.ctx)
+
+
+def fkf_filter_set_tolerances(f, gep_tol, orth_tol, trunc_tol) -> None:
+    _check(_lib.fkf_filter_set_tolerances(f.ptr, gep_tol, orth_tol, trunc_tol), f.ctx)
 
 
 def fkf_filter_phase_times(f):
