@@ -220,6 +220,26 @@ fkf_status fkf_filter_refresh(fkf_filter* f);
 /* Checkpoint / restore of (k, alpha, r, s_hat, D, W, X) to a binary file. */
 fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path);
 fkf_status fkf_filter_restore(fkf_filter* f, const char* path);
+/* Summed innovation NLL of K steps with a FIXED measurement operator H
+ * (the setting of Alg. kalmanconstantH, Sec. 2.3) and its exact gradient by
+ * reverse mode, with respect to the measurements y_k, the prior mean s_0, the
+ * Matern variance sigma2 (Gamma = sigma2 * Gamma_1) and the noise variance rho
+ * (R = rho I).  For a fixed H the NLL depends on the state only through
+ * h_k = H s_k|k and T_k = H Sigma_k|k H^T, whose recursion closes in data
+ * space (m x m) once A = H Gamma_H H^T is known (one H-apply); the adjoint
+ * recursion runs backwards over k and recomputes the Cholesky factors of the
+ * innovation covariances S_k from stored T_{k-1} instead of storing them.
+ * The NLL equals the sum of fkf_filter_step's nll_out over the same steps
+ * started from (s0, alpha0).
+ *   y (host, K x m row-major), H as CSR (host; rowptr m+1, col original point
+ *   indices), s0 (host, N original order, or NULL = 0), alpha0 >= 0, rho > 0.
+ *   Outputs (host, each nullable): nll_out, grad_y (K x m), grad_s0 (N,
+ *   original order), grad_sigma2, grad_rho.  Device memory: O(K m^2 + N m).
+ * Errors: EINVAL (sizes, CSR, rho <= 0), ENOTSPD, ENOMEM, ECUDA. */
+fkf_status fkf_nll_gradient(fkf_hmat* h, int32_t K, int32_t m, const double* y, const int64_t* H_rowptr,
+                            const int32_t* H_col, const double* H_val, double rho, const double* s0, double alpha0,
+                            double* nll_out, double* grad_y, double* grad_s0, double* grad_sigma2,
+                            double* grad_rho);
 /* Numerical thresholds of the step (all relative, in [0, 1)):
  *  gep_tol   -- data-space GEP modes with eigenvalue <= gep_tol * largest are
  *               dropped (they carry no information: null directions of H);

@@ -142,3 +142,43 @@ def scalar_steady_state(gamma, h, rho):
     lam e^2 + lam e - 1 = 0 -> e = (-lam + sqrt(lam^2 + 4 lam)) / (2 lam)."""
     lam = h * h * gamma / rho
     return gamma * (-lam + np.sqrt(lam * lam + 4.0 * lam)) / (2.0 * lam)
+
+
+def nll_batch_and_gradients(Gamma1, sigma2, rho, Hs, ys, s0=None, alpha0=0.0):
+    """The summed innovation NLL of K filter steps and its exact gradients, from
+    the joint Gaussian of all measurements (prediction-error decomposition):
+
+        Y ~ N(mu, C),  mu_k = H_k s0,
+        C[i, j] = (alpha0 + min(i, j)) sigma2 H_i Gamma1 H_j^T + delta_ij rho I
+        (steps i, j counted from 1; s_k = s0 + w_1 + ... + w_k, Gamma = sigma2 Gamma1),
+        NLL = 1/2 (Y - mu)^T C^-1 (Y - mu) + 1/2 log det C + M/2 log 2 pi.
+
+    Gradients: dNLL/dY = C^-1 (Y - mu) =: q; dNLL/ds0 = -sum_k H_k^T q_k;
+    dNLL/dtheta = 1/2 tr(C^-1 dC) - 1/2 q^T dC q for theta in {sigma2, rho}
+    (dC/dsigma2 = C_Gamma / sigma2, dC/drho = I).
+    Returns (nll, grad_y (list of m_k arrays), grad_s0, grad_sigma2, grad_rho)."""
+    K = len(Hs)
+    N = Gamma1.shape[0]
+    s0 = np.zeros(N) if s0 is None else np.asarray(s0, dtype=np.float64)
+    ms = [H.shape[0] for H in Hs]
+    off = np.concatenate([[0], np.cumsum(ms)]).astype(int)
+    M = int(off[-1])
+    CG = np.zeros((M, M))
+    for i in range(K):
+        for j in range(K):
+            CG[off[i] : off[i + 1], off[j] : off[j + 1]] = (alpha0 + min(i, j) + 1) * sigma2 * (
+                Hs[i] @ Gamma1 @ Hs[j].T)
+    C = CG + rho * np.eye(M)
+    Y = np.concatenate([np.asarray(y, dtype=np.float64) for y in ys])
+    mu = np.concatenate([H @ s0 for H in Hs])
+    cf = linalg.cho_factor(C, lower=True)
+    d = Y - mu
+    q = linalg.cho_solve(cf, d)
+    logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+    nll = 0.5 * (d @ q + logdet + M * np.log(2.0 * np.pi))
+    Ci = linalg.cho_solve(cf, np.eye(M))
+    g_sigma2 = 0.5 * (np.sum(Ci * CG) - q @ CG @ q) / sigma2
+    g_rho = 0.5 * (np.trace(Ci) - q @ q)
+    g_y = [q[off[k] : off[k + 1]].copy() for k in range(K)]
+    g_s0 = -sum(Hs[k].T @ g_y[k] for k in range(K))
+    return float(nll), g_y, g_s0, float(g_sigma2), float(g_rho)

@@ -309,6 +309,20 @@ FKF_API fkf_status fkf_filter_restore(fkf_filter* f, const char* path) {
   return filter_restore(f, path);
 }
 
+fkf_status filter_nll_gradient(fkf_hmat* h, int K, int m, const double* y, const int64_t* rowptr, const int32_t* col,
+                               const double* val, double rho, const double* s0, double alpha0, double* nll,
+                               double* gy, double* gs0, double* gsig, double* grho);
+
+FKF_API fkf_status fkf_nll_gradient(fkf_hmat* h, int32_t K, int32_t m, const double* y, const int64_t* H_rowptr,
+                                    const int32_t* H_col, const double* H_val, double rho, const double* s0,
+                                    double alpha0, double* nll_out, double* grad_y, double* grad_s0,
+                                    double* grad_sigma2, double* grad_rho) {
+  if (!h) return FKF_EINVAL;
+  if (!y || !H_rowptr || !H_col || !H_val) return set_err(h->ctx, FKF_EINVAL, "nll_gradient: null input pointer");
+  return filter_nll_gradient(h, K, m, y, H_rowptr, H_col, H_val, rho, s0, alpha0, nll_out, grad_y, grad_s0,
+                             grad_sigma2, grad_rho);
+}
+
 FKF_API fkf_status fkf_filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol) {
   if (!f) return FKF_EINVAL;
   return filter_set_tolerances(f, gep_tol, orth_tol, trunc_tol);

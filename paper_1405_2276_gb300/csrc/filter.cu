@@ -1140,3 +1140,318 @@ fkf_status filter_phase_times(fkf_filter* f, double* ms6) {
 }
 
 fkf_ctx* filter_ctx(fkf_filter* f) { return f->ctx; }
+
+// ---------------------------------------------------------------------------
+// Reverse-mode gradient of the summed innovation NLL for a fixed H.
+//
+// For a fixed H (the setting of Alg. kalmanconstantH) the NLL depends on the
+// state only through h_k = H s_k|k and T_k = H Sigma_k|k H^T, whose recursion
+// closes in data space (predict Sigma += Gamma, Sec. 2.3):
+//   P_k = T_{k-1} + A,  S_k = P_k + rho I,  nu_k = y_k - h_{k-1},
+//   z_k = S_k^-1 nu_k,  h_k = h_{k-1} + P_k z_k,  T_k = rho P_k S_k^-1,
+//   NLL = sum_k 1/2 (nu_k^T z_k + log det S_k + m log 2 pi),
+// with A = H Gamma_H H^T from one H-apply, h_0 = H s_0, T_0 = alpha_0 A.
+// The adjoint runs k = K..1 with hbar, Tbar (m x m):
+//   zbar = P hbar,  X1 = P S^-1,  w = S^-1 zbar,
+//   Sbar = 1/2 S^-1 - 1/2 z z^T + X1^T Tbar X1 - 1/2 (w z^T + z w^T)
+//   Pbar = Tbar - (Tbar X1 + X1^T Tbar) + 1/2 (hbar z^T + z hbar^T) + Sbar
+//   ybar_k = z + w,  hbar <- hbar - ybar_k,  Tbar <- Pbar,
+//   dNLL/drho += tr(Sbar),  dNLL/dsigma2 += tr(Pbar A) / sigma2,
+// and finally dNLL/ds0 = H^T hbar_0, dNLL/dsigma2 += alpha_0 tr(Tbar_0 A)/sigma2
+// (Gamma_H = sigma2 Gamma_1: the H-matrix scales linearly with sigma2).
+// The Cholesky factors of S_k are recomputed in the backward pass from the
+// stored T_{k-1}; nothing of size N is stored per step.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_spmv_orig(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, int64_t n, const double* __restrict__ s,
+                            double* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= m) return;
+  double acc = 0;
+  for (int64_t p = rowptr[w] + lane; p < rowptr[w + 1]; p += 32) {
+    const int64_t c = col[p];
+    if (c >= 0 && c < n) acc += val[p] * s[c];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[w] = acc;
+}
+
+// C = a*A + b*B (+ d on the diagonal), n x n
+__global__ void k_lincomb(int n, double a, const double* __restrict__ A, double b, const double* __restrict__ B,
+                          double d, double* __restrict__ C) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    C[e] = a * A[e] + (B ? b * B[e] : 0.0) + ((e / n == e % n) ? d : 0.0);
+}
+
+// v_out = a*x + b*y (n)
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// Sbar = sym(Q) + 1/2 Sinv - 1/2 z z^T - 1/2 (w z^T + z w^T), Q = X1^T Tbar X1
+// Pbar = Tbar - (TX + TX^T) + 1/2 (hb z^T + z hb^T) + Sbar
+__global__ void k_adjoint_mats(int m, const double* __restrict__ Q, const double* __restrict__ Sinv,
+                               const double* __restrict__ z, const double* __restrict__ w,
+                               const double* __restrict__ Tbar, const double* __restrict__ TX,
+                               const double* __restrict__ hb, double* __restrict__ Sbar, double* __restrict__ Pbar) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    const int64_t t = (int64_t)j * m + i;
+    const double sb = 0.5 * (Q[e] + Q[t]) + 0.5 * Sinv[e] - 0.5 * z[i] * z[j] - 0.5 * (w[i] * z[j] + z[i] * w[j]);
+    Sbar[e] = sb;
+    Pbar[e] = Tbar[e] - (TX[e] + TX[t]) + 0.5 * (hb[i] * z[j] + z[i] * hb[j]) + sb;
+  }
+}
+
+// acc[0] += tr(Sbar), acc[1] += sum(Pbar .* A)  (single CTA)
+__global__ void k_adjoint_scalars(int m, const double* __restrict__ Sbar, const double* __restrict__ Pbar,
+                                  const double* __restrict__ A, double* __restrict__ acc) {
+  __shared__ double sh[2][32];
+  double a = 0, b = 0;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    if (e / m == e % m) a += Sbar[e];
+    b += Pbar[e] * A[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = a;
+    sh[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      sa += sh[0][i];
+      sb += sh[1][i];
+    }
+    acc[0] += sa;
+    acc[1] += sb;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, const int64_t* rowptr_h,
+                                    const int32_t* col_h, const double* val_h, double rho, const double* s0,
+                                    double alpha0, double* nll_out, double* gy, double* gs0, double* gsig,
+                                    double* grho) {
+  fkf_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = h->n, mm = (int64_t)m * m;
+  const int64_t nnz = rowptr_h[m];
+  // --- inputs
+  DevBuf rowptr, col, val, yd, s0d, Bt, G, HG, flag;
+  FKF_TRY(dev_upload(ctx, rowptr, rowptr_h, (m + 1) * 8));
+  FKF_TRY(dev_upload(ctx, col, col_h, std::max<int64_t>(nnz, 1) * 4));
+  FKF_TRY(dev_upload(ctx, val, val_h, std::max<int64_t>(nnz, 1) * 8));
+  FKF_TRY(dev_upload(ctx, yd, y, (size_t)K * m * 8));
+  FKF_TRY(dev_alloc(ctx, s0d, n * 8));
+  if (s0) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(s0d.p, s0, n * 8, cudaMemcpyHostToDevice, st));
+  } else {
+    FKF_CUDA(ctx, cudaMemsetAsync(s0d.p, 0, n * 8, st));
+  }
+  FKF_TRY(dev_alloc(ctx, flag, 64));
+  FKF_CUDA(ctx, cudaMemsetAsync(flag.p, 0, 64, st));
+  const int64_t* iperm = h->iperm_d.as<int64_t>();
+  // --- A = H Gamma_H H^T (one H-apply of m columns)
+  FKF_TRY(dev_alloc(ctx, Bt, (size_t)n * m * sizeof(T)));
+  FKF_TRY(dev_alloc(ctx, G, (size_t)n * m * sizeof(T)));
+  FKF_CUDA(ctx, cudaMemsetAsync(Bt.p, 0, (size_t)n * m * sizeof(T), st));
+  k_densify<T><<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm,
+                                                  n, Bt.as<T>(), m, flag.as<int>());
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(hmat_apply_clustered(h, Bt.p, m, G.p, m, m));
+  DevBuf A, Araw;
+  FKF_TRY(dev_alloc(ctx, Araw, mm * 8));
+  FKF_TRY(dev_alloc(ctx, A, mm * 8));
+  k_csr_gather<T><<<m, 256, 0, st>>>(rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm, n, G.as<T>(), m,
+                                     m, Araw.as<double>(), m);
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaMemcpyAsync(A.p, Araw.p, mm * 8, cudaMemcpyDeviceToDevice, st));
+  k_symmetrize<<<nblk(mm), 256, 0, st>>>(m, A.as<double>());
+  FKF_LAUNCHED(ctx);
+  G.release();
+  Bt.release();
+  int hflag = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag.p, 4, cudaMemcpyDeviceToHost, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  if (hflag) return set_err(ctx, FKF_EINVAL, "nll_gradient: H column index outside [0, N)");
+  // --- forward data-space recursion, storing T_{k-1} and h_{k-1}
+  DevBuf Ts, hs, T0, P, S, X1, nu, z, nll_acc, chws;
+  FKF_TRY(dev_alloc(ctx, Ts, (size_t)K * mm * 8));
+  FKF_TRY(dev_alloc(ctx, hs, (size_t)(K + 1) * m * 8));
+  FKF_TRY(dev_alloc(ctx, P, mm * 8));
+  FKF_TRY(dev_alloc(ctx, S, mm * 8));
+  FKF_TRY(dev_alloc(ctx, X1, mm * 8));
+  FKF_TRY(dev_alloc(ctx, nu, m * 8));
+  FKF_TRY(dev_alloc(ctx, z, m * 8));
+  FKF_TRY(dev_alloc(ctx, nll_acc, 64));
+  double* Ad = A.as<double>();
+  double* Td = Ts.as<double>();
+  double* hd = hs.as<double>();
+  k_lincomb<<<nblk(mm), 256, 0, st>>>(m, alpha0, Ad, 0.0, nullptr, 0.0, Td);  // T_0 = alpha0 A
+  FKF_LAUNCHED(ctx);
+  k_spmv_orig<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(),
+                                                              val.as<double>(), n, s0d.as<double>(), hd);
+  FKF_LAUNCHED(ctx);
+  double nll = 0;
+  for (int k = 0; k < K; k++) {
+    double* Tk = Td + (int64_t)k * mm;  // T_{k-1} (the state before step k)
+    double* hk = hd + (int64_t)k * m;   // h_{k-1}
+    k_lincomb<<<nblk(mm), 256, 0, st>>>(m, 1.0, Tk, 1.0, Ad, 0.0, P.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_lincomb<<<nblk(mm), 256, 0, st>>>(m, 1.0, P.as<double>(), 0.0, nullptr, rho, S.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_f64(ctx, m, S.as<double>(), chws));
+    k_axpby<<<(int)cdiv(m, 256), 256, 0, st>>>(m, 1.0, yd.as<double>() + (int64_t)k * m, -1.0, hk, nu.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaMemcpyAsync(z.p, nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
+    FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), z.as<double>(), 1));
+    k_nll<<<1, 256, 0, st>>>(m, nu.as<double>(), z.as<double>(), S.as<double>(), nll_acc.as<double>());
+    FKF_LAUNCHED(ctx);
+    double nk = 0;
+    FKF_CUDA(ctx, cudaMemcpyAsync(&nk, nll_acc.p, 8, cudaMemcpyDeviceToHost, st));
+    // h_k = h_{k-1} + P z
+    FKF_CUDA(ctx, cudaMemcpyAsync(hk + m, hk, m * 8, cudaMemcpyDeviceToDevice, st));
+    FKF_TRY(gemm_f64(ctx, false, false, m, 1, m, 1.0, P.as<double>(), m, z.as<double>(), 1, 1.0, hk + m, 1));
+    if (k + 1 < K) {
+      // T_k = rho P S^-1 (row-major P S^-1 from a column-major solve of the symmetric P)
+      FKF_CUDA(ctx, cudaMemcpyAsync(X1.p, P.p, mm * 8, cudaMemcpyDeviceToDevice, st));
+      FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), X1.as<double>(), m));
+      k_lincomb<<<nblk(mm), 256, 0, st>>>(m, rho, X1.as<double>(), 0.0, nullptr, 0.0, Tk + mm);
+      FKF_LAUNCHED(ctx);
+      k_symmetrize<<<nblk(mm), 256, 0, st>>>(m, Tk + mm);
+      FKF_LAUNCHED(ctx);
+    }
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    nll += nk;
+  }
+  if (nll_out) *nll_out = nll;
+  if (!gy && !gs0 && !gsig && !grho) return FKF_OK;
+  // --- backward
+  DevBuf Tbar, Pbar, Sbar, Sinv, TX, Q, hbar, zbar, w, gyd, acc;
+  FKF_TRY(dev_alloc(ctx, Tbar, mm * 8));
+  FKF_TRY(dev_alloc(ctx, Pbar, mm * 8));
+  FKF_TRY(dev_alloc(ctx, Sbar, mm * 8));
+  FKF_TRY(dev_alloc(ctx, Sinv, mm * 8));
+  FKF_TRY(dev_alloc(ctx, TX, mm * 8));
+  FKF_TRY(dev_alloc(ctx, Q, mm * 8));
+  FKF_TRY(dev_alloc(ctx, hbar, m * 8));
+  FKF_TRY(dev_alloc(ctx, zbar, m * 8));
+  FKF_TRY(dev_alloc(ctx, w, m * 8));
+  FKF_TRY(dev_alloc(ctx, gyd, (size_t)K * m * 8));
+  FKF_TRY(dev_alloc(ctx, acc, 64));
+  FKF_CUDA(ctx, cudaMemsetAsync(Tbar.p, 0, mm * 8, st));
+  FKF_CUDA(ctx, cudaMemsetAsync(hbar.p, 0, m * 8, st));
+  FKF_CUDA(ctx, cudaMemsetAsync(acc.p, 0, 64, st));
+  for (int k = K - 1; k >= 0; k--) {
+    double* Tk = Td + (int64_t)k * mm;
+    double* hk = hd + (int64_t)k * m;
+    // recompute P, S = chol(P + rho I), z
+    k_lincomb<<<nblk(mm), 256, 0, st>>>(m, 1.0, Tk, 1.0, Ad, 0.0, P.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_lincomb<<<nblk(mm), 256, 0, st>>>(m, 1.0, P.as<double>(), 0.0, nullptr, rho, S.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_f64(ctx, m, S.as<double>(), chws));
+    k_axpby<<<(int)cdiv(m, 256), 256, 0, st>>>(m, 1.0, yd.as<double>() + (int64_t)k * m, -1.0, hk, z.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), z.as<double>(), 1));
+    // zbar = P hbar ; w = S^-1 zbar ; X1 = P S^-1 ; Sinv
+    FKF_TRY(gemm_f64(ctx, false, false, m, 1, m, 1.0, P.as<double>(), m, hbar.as<double>(), 1, 0.0, zbar.as<double>(), 1));
+    FKF_CUDA(ctx, cudaMemcpyAsync(w.p, zbar.p, m * 8, cudaMemcpyDeviceToDevice, st));
+    FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), w.as<double>(), 1));
+    FKF_CUDA(ctx, cudaMemcpyAsync(X1.p, P.p, mm * 8, cudaMemcpyDeviceToDevice, st));
+    FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), X1.as<double>(), m));
+    k_identity<<<nblk(mm), 256, 0, st>>>(m, Sinv.as<double>(), m);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), Sinv.as<double>(), m));
+    // TX = Tbar X1 ; Q = X1^T TX
+    FKF_TRY(gemm_f64(ctx, false, false, m, m, m, 1.0, Tbar.as<double>(), m, X1.as<double>(), m, 0.0, TX.as<double>(), m));
+    FKF_TRY(gemm_f64(ctx, true, false, m, m, m, 1.0, X1.as<double>(), m, TX.as<double>(), m, 0.0, Q.as<double>(), m));
+    k_adjoint_mats<<<nblk(mm), 256, 0, st>>>(m, Q.as<double>(), Sinv.as<double>(), z.as<double>(), w.as<double>(),
+                                             Tbar.as<double>(), TX.as<double>(), hbar.as<double>(), Sbar.as<double>(),
+                                             Pbar.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_adjoint_scalars<<<1, 1024, 0, st>>>(m, Sbar.as<double>(), Pbar.as<double>(), Ad, acc.as<double>());
+    FKF_LAUNCHED(ctx);
+    // ybar_k = z + w ; hbar <- hbar - ybar_k ; Tbar <- Pbar
+    double* gk = gyd.as<double>() + (int64_t)k * m;
+    k_axpby<<<(int)cdiv(m, 256), 256, 0, st>>>(m, 1.0, z.as<double>(), 1.0, w.as<double>(), gk);
+    FKF_LAUNCHED(ctx);
+    k_axpby<<<(int)cdiv(m, 256), 256, 0, st>>>(m, 1.0, hbar.as<double>(), -1.0, gk, hbar.as<double>());
+    FKF_LAUNCHED(ctx);
+    std::swap(Tbar.p, Pbar.p);
+  }
+  // alpha0 term of the sigma2 gradient: acc[1] += alpha0 tr(Tbar_0 A)
+  if (alpha0 != 0.0) {
+    FKF_CUDA(ctx, cudaMemsetAsync(Sbar.p, 0, mm * 8, st));
+    k_lincomb<<<nblk(mm), 256, 0, st>>>(m, alpha0, Tbar.as<double>(), 0.0, nullptr, 0.0, Pbar.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_adjoint_scalars<<<1, 1024, 0, st>>>(m, Sbar.as<double>(), Pbar.as<double>(), Ad, acc.as<double>());
+    FKF_LAUNCHED(ctx);
+  }
+  double acc_h[2] = {0, 0};
+  FKF_CUDA(ctx, cudaMemcpyAsync(acc_h, acc.p, 16, cudaMemcpyDeviceToHost, st));
+  if (gy) FKF_CUDA(ctx, cudaMemcpyAsync(gy, gyd.p, (size_t)K * m * 8, cudaMemcpyDeviceToHost, st));
+  if (gs0) {
+    // dNLL/ds0 = H^T hbar_0 through a column index of H (deterministic order)
+    DevBuf cnt, cursor, colptr, crow, cval, gc, go;
+    FKF_TRY(dev_alloc(ctx, cnt, n * 4 + 64));
+    FKF_TRY(dev_alloc(ctx, cursor, n * 4 + 64));
+    FKF_TRY(dev_alloc(ctx, colptr, (n + 1) * 8));
+    FKF_TRY(dev_alloc(ctx, crow, std::max<int64_t>(nnz, 1) * 4));
+    FKF_TRY(dev_alloc(ctx, cval, std::max<int64_t>(nnz, 1) * 8));
+    FKF_TRY(dev_alloc(ctx, gc, n * 8));
+    FKF_TRY(dev_alloc(ctx, go, n * 8));
+    FKF_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, n * 4, st));
+    FKF_CUDA(ctx, cudaMemsetAsync(cursor.p, 0, n * 4, st));
+    FKF_CUDA(ctx, cudaMemsetAsync(gc.p, 0, n * 8, st));
+    k_csc_count<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), iperm, n, cnt.as<int>());
+    FKF_LAUNCHED(ctx);
+    k_scan<<<1, 1024, 0, st>>>(n, cnt.as<int>(), colptr.as<int64_t>());
+    FKF_LAUNCHED(ctx);
+    k_csc_fill<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm,
+                                                   n, colptr.as<int64_t>(), cursor.as<int>(), crow.as<int>(),
+                                                   cval.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, colptr.as<int64_t>(), crow.as<int>(), cval.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_csc_spmm<double><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, colptr.as<int64_t>(), crow.as<int>(),
+                                                               cval.as<double>(), hbar.as<double>(), 1, gc.as<double>(), 1);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(hmat_permute_rows_f64(ctx, gc.as<double>(), 1, iperm, go.as<double>(), 1, n, 1));
+    FKF_CUDA(ctx, cudaMemcpyAsync(gs0, go.p, n * 8, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  FKF_CUDA(ctx, cudaGetLastError());
+  if (grho) *grho = acc_h[0];
+  if (gsig) *gsig = acc_h[1] / h->kernel.sigma2;
+  return FKF_OK;
+}
+
+fkf_status filter_nll_gradient(fkf_hmat* h, int K, int m, const double* y, const int64_t* rowptr, const int32_t* col,
+                               const double* val, double rho, const double* s0, double alpha0, double* nll,
+                               double* gy, double* gs0, double* gsig, double* grho) {
+  fkf_ctx* ctx = h->ctx;
+  if (K < 1 || m < 1) return set_err(ctx, FKF_EINVAL, "nll_gradient: K >= 1 and m >= 1 required");
+  if (!(rho > 0) || !(alpha0 >= 0)) return set_err(ctx, FKF_EINVAL, "nll_gradient: rho > 0 and alpha0 >= 0 required");
+  if (rowptr[0] != 0) return set_err(ctx, FKF_EINVAL, "nll_gradient: rowptr[0] must be 0");
+  for (int j = 0; j < m; j++)
+    if (rowptr[j + 1] < rowptr[j]) return set_err(ctx, FKF_EINVAL, "nll_gradient: rowptr not nondecreasing");
+  if (h->prec == FKF_FP64)
+    return nll_gradient_impl<double>(h, K, m, y, rowptr, col, val, rho, s0, alpha0, nll, gy, gs0, gsig, grho);
+  return nll_gradient_impl<float>(h, K, m, y, rowptr, col, val, rho, s0, alpha0, nll, gy, gs0, gsig, grho);
+}

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 template <typename T>
 struct TileCfg;
 template <>
@@ -24,8 +26,8 @@ template <typename T>
 struct TileSmem {
   static constexpr int BM = TileCfg<T>::BM, BN = TileCfg<T>::BN, BK = TileCfg<T>::BK;
   static constexpr int LDA = BM + 4, LDB = BN + 4;
-  T a[BK * LDA];
-  T b[BK * LDB];
+  alignas(16) T a[BK * LDA];
+  alignas(16) T b[BK * LDB];
 };
 
 // Accumulate acc += op(A)[0:M, 0:K] * op(B)[0:K, 0:N] for one CTA tile.
@@ -102,11 +104,28 @@ __device__ __forceinline__ void tile_mma(T (&acc)[TileCfg<T>::TM][TileCfg<T>::TN
     if (k0 + BK < K) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; kk++) {
+      // 16-byte shared loads; the thread's TN columns are two strips of TN/2
+      // at tx*TN/2 and BN/2 + tx*TN/2 so that each quarter-warp reads one
+      // contiguous 128-byte line (no bank conflicts)
       T a[TM], b[TN];
+      constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
+      using vec_t = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
 #pragma unroll
-      for (int i = 0; i < TM; i++) a[i] = sm.a[kk * LDA + ty * TM + i];
+      for (int i = 0; i < TM; i += V) {
+        const vec_t v = *reinterpret_cast<const vec_t*>(&sm.a[kk * LDA + ty * TM + i]);
+        const T* pv = reinterpret_cast<const T*>(&v);
 #pragma unroll
-      for (int j = 0; j < TN; j++) b[j] = sm.b[kk * LDB + tx * TN + j];
+        for (int u = 0; u < V; u++) a[i + u] = pv[u];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int j = 0; j < TN / 2; j += V) {
+          const vec_t v = *reinterpret_cast<const vec_t*>(&sm.b[kk * LDB + h * (BN / 2) + tx * (TN / 2) + j]);
+          const T* pv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int u = 0; u < V; u++) b[h * (TN / 2) + j + u] = pv[u];
+        }
 #pragma unroll
       for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -130,5 +149,7 @@ __device__ __forceinline__ int tile_row(int i) {
 }
 template <typename T>
 __device__ __forceinline__ int tile_col(int j) {
-  return (threadIdx.x % (TileCfg<T>::BN / TileCfg<T>::TN)) * TileCfg<T>::TN + j;
+  constexpr int TN = TileCfg<T>::TN, BN = TileCfg<T>::BN;
+  const int tx = threadIdx.x % (BN / TN);
+  return (j < TN / 2 ? 0 : BN / 2) + tx * (TN / 2) + (j % (TN / 2));
 }

@@ -88,6 +88,8 @@ _sigs = {
     "fkf_filter_restore": (C.c_int, [_P, C.c_char_p]),
     "fkf_filter_phase_times": (C.c_int, [_P, _P]),
     "fkf_filter_set_tolerances": (C.c_int, [_P, C.c_double, C.c_double, C.c_double]),
+    "fkf_nll_gradient": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, C.c_double, _P, C.c_double,
+                                   _P, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -276,6 +278,28 @@ def fkf_filter_checkpoint(f, path: str) -> None:
 
 def fkf_filter_restore(f, path: str) -> None:
     _check(_lib.fkf_filter_restore(f.ptr, path.encode()), f.ctx)
+
+
+def fkf_nll_gradient(h, y, rowptr, col, val, rho, s0=None, alpha0=0.0, want_grads=True):
+    """Summed NLL of K fixed-H steps and its gradients (host numpy arrays).
+    y: (K, m).  Returns (nll, grad_y (K, m), grad_s0 (N,), grad_sigma2, grad_rho)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    K, m = y.shape
+    n = fkf_hmatrix_info(h)["n"]
+    nll = C.c_double(0)
+    gy = np.zeros((K, m)) if want_grads else None
+    gs = np.zeros(n) if want_grads else None
+    gsig = C.c_double(0)
+    grho = C.c_double(0)
+    s0p = None
+    if s0 is not None:
+        s0 = np.ascontiguousarray(s0, dtype=np.float64)
+        s0p = s0.ctypes.data
+    st = _lib.fkf_nll_gradient(h.ptr, K, m, y.ctypes.data, _ptr(rowptr), _ptr(col), _ptr(val), rho, s0p, alpha0,
+                               C.byref(nll), _ptr(gy), _ptr(gs), C.byref(gsig) if want_grads else None,
+                               C.byref(grho) if want_grads else None)
+    _check(st, h.ctx)
+    return nll.value, gy, gs, gsig.value, grho.value
 
 
 def fkf_filter_set_tolerances(f, gep_tol, orth_tol, trunc_tol) -> None:

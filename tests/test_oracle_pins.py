@@ -228,3 +228,42 @@ def test_generator_is_deterministic_and_shaped():
     assert a["truth"].shape == (3, 192) and a["y"].shape == (3, 12)
     inc = np.diff(np.vstack([np.zeros(192), a["truth"]]), axis=0)
     assert 0.3 < inc.var() < 3.0
+
+
+def test_batch_gradients_match_central_differences_of_dense_kf():
+    """The batch-Gaussian gradients are pinned by central finite differences of
+    the dense filter's summed NLL (a different algebra: the recursion)."""
+    rng = np.random.default_rng(8)
+    N, ms = 10, [3, 4, 3]
+    pts = rng.uniform(size=(N, 2))
+    G1 = covariance.dense_gamma(pts, 1.5, 0.3, 1.0)
+    Hs = [rng.standard_normal((m, N)) for m in ms]
+    ys = [rng.standard_normal(m) for m in ms]
+    s0 = rng.standard_normal(N)
+    sigma2, rho, alpha0 = 0.7, 0.05, 0.4
+
+    def total(sig, r, yv, s):
+        res = kalman.kf_dense(sig * G1, [(yv[k], Hs[k], r) for k in range(len(ms))], s0=s, alpha0=alpha0,
+                              keep_cov=False)
+        return sum(x["nll"] for x in res)
+
+    nll, gy, gs0, gsig, grho = kalman.nll_batch_and_gradients(G1, sigma2, rho, Hs, ys, s0, alpha0)
+    assert abs(nll - total(sigma2, rho, ys, s0)) < 1e-10 * abs(nll)
+    h = 1e-6
+    fd_sig = (total(sigma2 + h, rho, ys, s0) - total(sigma2 - h, rho, ys, s0)) / (2 * h)
+    fd_rho = (total(sigma2, rho + h, ys, s0) - total(sigma2, rho - h, ys, s0)) / (2 * h)
+    assert abs(fd_sig - gsig) < 1e-6 * max(1, abs(gsig))
+    assert abs(fd_rho - grho) < 1e-6 * max(1, abs(grho))
+    for k, j in [(0, 1), (2, 2), (1, 0)]:
+        yp = [y.copy() for y in ys]
+        ym = [y.copy() for y in ys]
+        yp[k][j] += h
+        ym[k][j] -= h
+        fd = (total(sigma2, rho, yp, s0) - total(sigma2, rho, ym, s0)) / (2 * h)
+        assert abs(fd - gy[k][j]) < 1e-6 * max(1, abs(fd))
+    for i in (0, 7):
+        sp, sm_ = s0.copy(), s0.copy()
+        sp[i] += h
+        sm_[i] -= h
+        fd = (total(sigma2, rho, ys, sp) - total(sigma2, rho, ys, sm_)) / (2 * h)
+        assert abs(fd - gs0[i]) < 1e-6 * max(1, abs(fd))
