@@ -196,6 +196,30 @@ void fkf_filter_destroy(fkf_filter* f);
 fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr, const int32_t* H_col,
                            const double* H_val, const double* R, double r_scalar, int32_t flags, double* nll_out);
 
+/* One filter's inputs and outputs for fkf_filter_step_batched. */
+typedef struct {
+  fkf_filter* filter;
+  const double* y;
+  int32_t m;
+  const int64_t* H_rowptr;
+  const int32_t* H_col;
+  const double* H_val;
+  const double* R;   /* m doubles or NULL (then r_scalar * I) */
+  double r_scalar;
+  double nll;        /* out: innovation NLL of this step */
+  int32_t status;    /* out: fkf_status of this filter's step */
+} fkf_step_desc;
+
+/* Step many independent filters at once (uneven N, m, kernels).  Every
+ * filter must belong to a different context (each context owns one CUDA
+ * stream); the steps are issued concurrently, one host worker per context,
+ * so the GPU overlaps the filters' kernels.  Each filter's step is
+ * transactional on its own; descs[i].status reports it.  Returns FKF_OK when
+ * every step succeeded, else the status of the first failing entry.  flags as
+ * for fkf_filter_step (applied to every entry).  Errors: EINVAL (nb < 1,
+ * a context used twice), or the per-filter errors. */
+fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int32_t flags);
+
 /* Current state: s_hat (host, N, original order; nullable), alpha, rank r,
  * D (host, r doubles; nullable), W (device, N x r row-major in original
  * order, precision's element type; nullable, ldw >= r). */

@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <algorithm>
 
 #include "common.h"
 #include "hmat_host.h"
@@ -266,6 +268,38 @@ FKF_API fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, co
   if (!y || !H_rowptr || (!H_col && m > 0) || (!H_val && m > 0))
     return set_err(filter_ctx(f), FKF_EINVAL, "filter_step: null input pointer");
   return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out);
+}
+
+FKF_API fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int32_t flags) {
+  if (!descs || nb < 1) return FKF_EINVAL;
+  std::vector<fkf_ctx*> ctxs(nb);
+  for (int i = 0; i < nb; i++) {
+    if (!descs[i].filter) return FKF_EINVAL;
+    ctxs[i] = filter_ctx(descs[i].filter);
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) return set_err(ctxs[i], FKF_EINVAL, "step_batched: filters %d and %d share a context", j, i);
+  }
+  const int nthreads = (int)std::min<int64_t>(nb, std::max(1u, std::thread::hardware_concurrency()));
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    while (true) {
+      const int i = next.fetch_add(1);
+      if (i >= nb) break;
+      fkf_step_desc& d = descs[i];
+      fkf_ctx* ctx = ctxs[i];
+      fkf_status st = FKF_OK;
+      if (cudaSetDevice(ctx->device) != cudaSuccess) st = set_err(ctx, FKF_ECUDA, "cudaSetDevice failed");
+      if (st == FKF_OK) st = fkf_filter_step(d.filter, d.y, d.m, d.H_rowptr, d.H_col, d.H_val, d.R, d.r_scalar, flags,
+                                             &d.nll);
+      d.status = st;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; t++) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < nb; i++)
+    if (descs[i].status != FKF_OK) return (fkf_status)descs[i].status;
+  return FKF_OK;
 }
 
 FKF_API fkf_status fkf_filter_get(fkf_filter* f, double* s_hat, double* alpha, int32_t* r, double* D, void* W_dev,

@@ -50,6 +50,14 @@ class fkf_hmat_info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fkf_step_desc(C.Structure):
+    _fields_ = [
+        ("filter", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int32), ("H_rowptr", C.c_void_p),
+        ("H_col", C.c_void_p), ("H_val", C.c_void_p), ("R", C.c_void_p), ("r_scalar", C.c_double),
+        ("nll", C.c_double), ("status", C.c_int32),
+    ]
+
+
 class FkfError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -90,6 +98,7 @@ _sigs = {
     "fkf_filter_set_tolerances": (C.c_int, [_P, C.c_double, C.c_double, C.c_double]),
     "fkf_nll_gradient": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, C.c_double, _P, C.c_double,
                                    _P, _P, _P, _P, _P]),
+    "fkf_filter_step_batched": (C.c_int, [C.POINTER(fkf_step_desc), C.c_int32, C.c_int32]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -232,6 +241,31 @@ def fkf_filter_step(f, y, m, rowptr, col, val, R=None, r_scalar=0.0, flags=0, wa
                               C.byref(nll) if want_nll else None)
     _check(st, f.ctx)
     return nll.value
+
+
+def fkf_filter_step_batched(entries, flags=0):
+    """entries: list of (filter, y, rowptr, col, val, R or None, r_scalar), each
+    filter on its own context.  Returns the list of per-filter NLLs; raises
+    FkfError (with the first failing status) if any step failed."""
+    nb = len(entries)
+    descs = (fkf_step_desc * nb)()
+    keep = []
+    for i, (f, y, rowptr, col, val, R, rs) in enumerate(entries):
+        y = np.ascontiguousarray(y, dtype=np.float64) if isinstance(y, np.ndarray) else y
+        keep.append(y)
+        d = descs[i]
+        d.filter = f.ptr
+        d.y = _ptr(y)
+        d.m = int(rowptr.shape[0] - 1)
+        d.H_rowptr, d.H_col, d.H_val = _ptr(rowptr), _ptr(col), _ptr(val)
+        d.R = _ptr(R)
+        d.r_scalar = rs
+    st = _lib.fkf_filter_step_batched(descs, nb, flags)
+    if st != FKF_OK:
+        bad = next(i for i in range(nb) if descs[i].status != FKF_OK) if any(
+            descs[i].status != FKF_OK for i in range(nb)) else 0
+        _check(st, entries[bad][0].ctx)
+    return [descs[i].nll for i in range(nb)]
 
 
 def fkf_filter_get(f, n, want_s=True, want_D=True, W=None):

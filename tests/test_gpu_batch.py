@@ -1,0 +1,103 @@
+"""Batched steps of independent filters with uneven sizes (fkf_filter_step_batched)
+against the same filters stepped one at a time, and one of them against the
+dense oracle."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import covariance, kalman
+from tests.helpers import lib, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fkf():
+    from paper_1405_2276_gb300 import build
+
+    build()
+    return lib()
+
+
+SPECS = [  # grid, n_src, n_rec, nu, ell, precision
+    ((16, 16), 4, 3, 0.5, 0.25, 0),
+    ((24, 20), 5, 5, 1.5, 0.1, 0),
+    ((32, 32), 8, 4, 1.5, 0.2, 1),
+    ((20, 28), 3, 7, 0.5, 0.05, 1),
+    ((40, 24), 6, 6, 1.5, 0.3, 0),
+    ((12, 36), 2, 9, 0.5, 0.15, 1),
+]
+
+
+def _make(fkf, specs, steps):
+    out = []
+    for i, (grid, ns, nr, nu, ell, prec) in enumerate(specs):
+        wl = synth.tomography_workload(grid, ns, nr, steps, ell, 1.0, 1e-4, seed=synth.BASE_SEED + 1000 * 3 + i)
+        ctx = fkf.fkf_create(0)
+        hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, precision=prec)
+        m = wl["H"].nrows
+        f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)
+        out.append(dict(wl=wl, ctx=ctx, hm=hm, f=f, spec=(grid, ns, nr, nu, ell, prec)))
+    return out
+
+
+def _free(fkf, objs):
+    for o in objs:
+        fkf.fkf_filter_destroy(o["f"])
+        fkf.fkf_hmatrix_destroy(o["hm"])
+        fkf.fkf_destroy(o["ctx"])
+
+
+def test_batched_equals_sequential(fkf):
+    steps = 3
+    a = _make(fkf, SPECS, steps)
+    b = _make(fkf, SPECS, steps)
+    for k in range(steps):
+        entries = []
+        for o in a:
+            h = o["wl"]["H"]
+            entries.append((o["f"], o["wl"]["y"][k], h.rowptr, h.col, h.val, None, 1e-4))
+        nll_b = fkf.fkf_filter_step_batched(entries)
+        nll_s = []
+        for o in b:
+            h = o["wl"]["H"]
+            nll_s.append(fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4))
+        assert nll_b == nll_s
+    for oa, ob in zip(a, b):
+        n = oa["wl"]["points"].shape[0]
+        sa, sb = fkf.fkf_filter_get(oa["f"], n), fkf.fkf_filter_get(ob["f"], n)
+        np.testing.assert_array_equal(sa["s"], sb["s"])
+        np.testing.assert_array_equal(sa["D"], sb["D"])
+    # first filter (FP64) against the dense oracle
+    o = a[0]
+    grid, ns, nr, nu, ell, prec = o["spec"]
+    G = covariance.dense_gamma(o["wl"]["points"], nu, ell, 1.0)
+    Hd = synth.csr_to_dense(o["wl"]["H"])
+    ref = kalman.kf_dense(G, [(o["wl"]["y"][k], Hd, 1e-4) for k in range(steps)], keep_cov=False)
+    st = fkf.fkf_filter_get(o["f"], o["wl"]["points"].shape[0])
+    assert rel_err(st["s"], ref[-1]["s"]) < 1e-6
+    _free(fkf, a)
+    _free(fkf, b)
+
+
+def test_batched_rejects_shared_context_and_reports_per_filter_status(fkf):
+    objs = _make(fkf, SPECS[:2], 1)
+    ctx = objs[0]["ctx"]
+    f2 = fkf.fkf_filter_create(objs[0]["hm"], None, 0.0, 1e-12, 16, 32)
+    h = objs[0]["wl"]["H"]
+    with pytest.raises(fkf.FkfError) as e:
+        fkf.fkf_filter_step_batched([(objs[0]["f"], objs[0]["wl"]["y"][0], h.rowptr, h.col, h.val, None, 1e-4),
+                                     (f2, objs[0]["wl"]["y"][0], h.rowptr, h.col, h.val, None, 1e-4)])
+    assert e.value.status == fkf.FKF_EINVAL
+    # a bad noise variance in the second entry fails only that entry
+    h1 = objs[1]["wl"]["H"]
+    with pytest.raises(fkf.FkfError) as e:
+        fkf.fkf_filter_step_batched([(objs[0]["f"], objs[0]["wl"]["y"][0], h.rowptr, h.col, h.val, None, 1e-4),
+                                     (objs[1]["f"], objs[1]["wl"]["y"][0], h1.rowptr, h1.col, h1.val, None, -1.0)])
+    assert e.value.status == fkf.FKF_EINVAL
+    assert fkf.fkf_filter_get(objs[0]["f"], objs[0]["wl"]["points"].shape[0])["alpha"] == 1.0
+    assert fkf.fkf_filter_get(objs[1]["f"], objs[1]["wl"]["points"].shape[0])["alpha"] == 0.0
+    fkf.fkf_filter_destroy(f2)
+    del ctx
+    _free(fkf, objs)
