@@ -224,6 +224,18 @@ fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int32_t fla
  * D (host, r doubles; nullable), W (device, N x r row-major in original
  * order, precision's element type; nullable, ldw >= r). */
 fkf_status fkf_filter_get(fkf_filter* f, double* s_hat, double* alpha, int32_t* r, double* D, void* W_dev, int64_t ldw);
+/* Bookkeeping of the filter (no device work). */
+typedef struct {
+  int64_t k;          /* steps taken */
+  double alpha;       /* alpha_k */
+  int32_t r;          /* rank of the low-rank term */
+  int32_t last_path;  /* last step: 0 = new directions merged (GEP, orthonormalisation,
+                         merge, rotation); 1 = no information outside span(W): basis kept,
+                         weight updated in information form */
+  int32_t diagonal;   /* 1 if the weight is currently diagonal (the paper's D_k) */
+} fkf_filter_stats;
+fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);
+
 /* Posterior variance diag(Sigma_k|k) = alpha_k diag(Gamma) - diag(W D W^T)
  * (Sec. 3.1) into var_dev (device, N doubles, original order). */
 fkf_status fkf_variance(fkf_filter* f, double* var_dev);

@@ -357,6 +357,14 @@ FKF_API fkf_status fkf_nll_gradient(fkf_hmat* h, int32_t K, int32_t m, const dou
                              grad_sigma2, grad_rho);
 }
 
+void filter_stats(const fkf_filter* f, fkf_filter_stats* s);
+
+FKF_API fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out) {
+  if (!f || !out) return FKF_EINVAL;
+  filter_stats(f, out);
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_filter_set_tolerances(fkf_filter* f, double gep_tol, double orth_tol, double trunc_tol) {
   if (!f) return FKF_EINVAL;
   return filter_set_tolerances(f, gep_tol, orth_tol, trunc_tol);

@@ -216,7 +216,7 @@ template <typename T>
 __global__ void k_mean_coef(int r, int m, const double* __restrict__ D, const double* __restrict__ uz,
                             const double* __restrict__ z, double alpha1, T* __restrict__ v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < r) v[i] = (T)(-D[i] * uz[i]);
+  if (i < r) v[i] = (T)(D ? -D[i] * uz[i] : -uz[i]);  // D == nullptr: uz already weighted
   else if (i < r + m) v[i] = (T)(alpha1 * z[i - r]);
 }
 
@@ -303,6 +303,73 @@ __global__ void k_transpose(int rows, int cols, const double* __restrict__ src, 
     const int i = (int)(e / cols), q = (int)(e % cols);
     dst[(int64_t)i * ldd + q] = src[(int64_t)q * lds + i];
   }
+}
+
+// C = a*A + b*B (+ d on the diagonal), n x n; C may alias A or B (elementwise)
+__global__ void k_lincomb(int n, double a, const double* A, double b, const double* B, double d, double* C) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    C[e] = a * A[e] + (B ? b * B[e] : 0.0) + ((e / n == e % n) ? d : 0.0);
+}
+
+// out = || diag(rs) A diag(rs) ||_F for an m x m matrix (single CTA)
+__global__ void k_frob_scaled(int m, const double* __restrict__ A, const double* __restrict__ rs,
+                              double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const double v = A[e] * rs[e / m] * rs[e % m];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    out[0] = sqrt(t);
+  }
+}
+
+// out[i, j] = rs[i] * A[i*lda + j]  (m x r)
+__global__ void k_scale_rows(int m, int r, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
+                             double* __restrict__ out) {
+  const int64_t total = (int64_t)m * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    out[e] = rs[i] * A[(int64_t)i * lda + j];
+  }
+}
+
+// E = diag(alpha1 - d) (r x r)
+__global__ void k_diag_from(int r, const double* __restrict__ d, double alpha1, double* __restrict__ E) {
+  const int64_t total = (int64_t)r * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    E[e] = i == j ? alpha1 - d[i] : 0.0;
+  }
+}
+
+// M[i, j] += B[i, j] + (i == j ? c : 0) for the leading r x r block of M (ld ldm)
+__global__ void k_add_block(int r, const double* __restrict__ B, double c, double* __restrict__ M, int64_t ldm) {
+  const int64_t total = (int64_t)r * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    M[(int64_t)i * ldm + j] += B[e] + (i == j ? c : 0.0);
+  }
+}
+
+// out = d .* x (n)
+__global__ void k_vmul(int n, const double* __restrict__ d, const double* __restrict__ x, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = d[i] * x[i];
+}
+
+// out[q] = w[n-1-q] for q < n (descending copy of ascending eigenvalues)
+__global__ void k_rev(int n, const double* __restrict__ w, double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = w[n - 1 - q];
 }
 
 // out = ||A||_F over n entries (single CTA)
@@ -441,6 +508,13 @@ struct fkf_filter {
   int cur = 0;
   size_t w = 8;
   DevBuf WG[2], Xb[2], Bt, s_hat, s_new, D, Dn;
+  // When diag is false the low-rank weight is the full symmetric r x r matrix
+  // Df (Sigma = alpha Gamma - W Df W^T, W^T Gamma^-1 W = I); observers first
+  // diagonalise it (canonicalize) so that the state has the paper's form.
+  bool diag = true;
+  DevBuf Df, Dfn, Ep, Qm;
+  double new_tol = 0;  // relative information outside span(W) below which the basis is kept
+  int last_path = 0;   // 0: general merge, 1: basis kept (no new directions)
   // step inputs
   DevBuf rowptr, col, val, y, rdiag, rs, flag;
   DevBuf cnt, cursor, colptr, crow, cval;
@@ -487,6 +561,10 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->rs, m));
   FKF_TRY(A(f->rowptr, m + 1));
   FKF_TRY(dev_alloc(ctx, f->flag, 64));
+  FKF_TRY(A(f->Df, r * r));
+  FKF_TRY(A(f->Dfn, r * r));
+  FKF_TRY(A(f->Ep, r * r));
+  FKF_TRY(A(f->Qm, r * r));
   return FKF_OK;
 }
 
@@ -508,6 +586,9 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
   // FP32 storage of W, X and G leaves a noise floor of ~1e-5 in the data-space
   // Gram T; new directions are only accepted clearly above it.
   f->orth_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-3;
+  // ||R^-1/2 (A - HW HW^T) R^-1/2||_F / ||R^-1/2 A R^-1/2||_F below new_tol:
+  // the step's information lies in span(W) and the basis is kept
+  f->new_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-4;
   f->alpha = alpha0;
   auto fail = [&](fkf_status st) {
     delete f;
@@ -669,10 +750,16 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   k_sym<<<nblk((int64_t)m * m), 256, 0, st>>>(m, Araw, nm, f->rs.as<double>(), f->rdiag.as<double>(), alpha1,
                                               f->As.as<double>(), f->At.as<double>(), S);
   FKF_LAUNCHED(ctx);
-  // S = alpha' A + R - HW D HW^T
+  // S = alpha' A + R - HW D HW^T   (D diagonal, or the full r x r weight Df)
+  const bool diag = f->diag;
+  double* Dfc = f->Df.as<double>();
   if (r > 0) {
-    k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
-    FKF_LAUNCHED(ctx);
+    if (diag) {
+      k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
+      FKF_LAUNCHED(ctx);
+    } else {
+      FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
+    }
     FKF_TRY(gemm_f64(ctx, false, true, m, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
   }
   FKF_TRY(chol_f64(ctx, m, S, f->cholws));
@@ -681,21 +768,100 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, f->nll.as<double>());
   FKF_LAUNCHED(ctx);
   // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
-  if (r > 0) FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
-  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, f->D.as<double>(), f->uz.as<double>(), f->z.as<double>(),
-                                                     alpha1, f->vcoef.as<T>());
+  if (r > 0) {
+    FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
+    if (diag) {
+      k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->uz.as<double>(), f->dbar.as<double>());
+      FKF_LAUNCHED(ctx);
+    } else {
+      FKF_TRY(gemm_f64(ctx, false, false, r, 1, r, 1.0, Dfc, r, f->uz.as<double>(), 1, 0.0, f->dbar.as<double>(), 1));
+    }
+  }
+  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, nullptr, f->dbar.as<double>(), f->z.as<double>(), alpha1,
+                                                     f->vcoef.as<T>());
   FKF_LAUNCHED(ctx);
   k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
                                                        f->s_new.as<double>());
   FKF_LAUNCHED(ctx);
   FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
+  // ---- does the step bring information outside span(W)?  The Gamma^-1-Gram
+  // of G's component outside span(W) is A - HW HW^T (X^T G = (HW)^T, X^T W = I);
+  // compared with A in the noise-whitened metric.
+  double ratio = 1.0;
+  {
+    double* nrm = f->nll.as<double>() + 1;
+    if (r > 0) {
+      double* T0 = f->Tm.as<double>();
+      FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
+      FKF_TRY(gemm_f64(ctx, false, true, m, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
+      k_frob_scaled<<<1, 1024, 0, st>>>(m, T0, f->rs.as<double>(), nrm);
+      FKF_LAUNCHED(ctx);
+      k_frob<<<1, 1024, 0, st>>>((int64_t)m * m, f->At.as<double>(), nrm + 1);
+      FKF_LAUNCHED(ctx);
+    }
+    double hv[2] = {1.0, 1.0};
+    int hflag = 0;
+    if (r > 0) FKF_CUDA(ctx, cudaMemcpyAsync(hv, nrm, 16, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
+    if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
+  }
+  if (r > 0 && ratio <= f->new_tol) {
+    // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated
+    // in information form, E' = (E^-1 + Q)^-1, E = alpha' I - D (predicted),
+    // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight)
+    double* Ep = f->Ep.as<double>();
+    double* Dn2 = f->Dfn.as<double>();
+    double* Qm = f->Qm.as<double>();
+    const int64_t rr = (int64_t)r * r;
+    if (diag) {
+      k_diag_from<<<nblk(rr), 256, 0, st>>>(r, f->D.as<double>(), alpha1, Ep);
+    } else {
+      k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Dfc, 0.0, nullptr, alpha1, Ep);
+    }
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_f64(ctx, r, Ep, f->cholws));
+    k_identity<<<nblk(rr), 256, 0, st>>>(r, Dn2, r);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_solve_f64(ctx, r, Ep, Dn2, r));  // E^-1
+    k_scale_rows<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->rs.as<double>(), f->HWD.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(gemm_f64(ctx, true, false, r, r, m, 1.0, f->HWD.as<double>(), r, f->HWD.as<double>(), r, 0.0, Qm, r));
+    k_lincomb<<<nblk(rr), 256, 0, st>>>(r, 1.0, Dn2, 1.0, Qm, 0.0, Dn2);  // E^-1 + Q
+    FKF_LAUNCHED(ctx);
+    k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Dn2);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_f64(ctx, r, Dn2, f->cholws));
+    k_identity<<<nblk(rr), 256, 0, st>>>(r, Ep, r);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_solve_f64(ctx, r, Dn2, Ep, r));  // E' = (E^-1 + Q)^-1
+    k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Ep);
+    FKF_LAUNCHED(ctx);
+    k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Ep, 0.0, nullptr, alpha1, Dn2);  // D' = alpha' I - E'
+    FKF_LAUNCHED(ctx);
+    for (int e = 4; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
+    double nll = 0;
+    FKF_CUDA(ctx, cudaMemcpyAsync(&nll, f->nll.p, 8, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    FKF_CUDA(ctx, cudaGetLastError());
+    std::swap(f->s_hat.p, f->s_new.p);
+    std::swap(f->Df.p, f->Dfn.p);
+    f->diag = false;
+    f->alpha = alpha1;
+    f->k++;
+    f->last_path = 1;
+    if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
+    for (int i = 0; i < 6; i++) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, f->ev[i], f->ev[i + 1]);
+      f->phase_ms[i] = ms;
+    }
+    return FKF_OK;
+  }
   // ---- S3: data-space GEP  R^-1/2 A R^-1/2 = Q diag(a) Q^T
   std::vector<double> a_h, th_h, thM_h;
   FKF_TRY(eigh_f64(ctx, m, f->At.as<double>(), f->a.as<double>(), a_h, f->eigws));
-  int hflag = 0;
-  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-  FKF_CUDA(ctx, cudaStreamSynchronize(st));
-  if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
   const double amax = a_h.empty() ? 0.0 : a_h.back();
   int mlam = 0;
   for (int i = m - 1; i >= 0; i--)
@@ -754,8 +920,20 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       FKF_LAUNCHED(ctx);
     }
     FKF_TRY(gemm_f64(ctx, false, true, nM, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0, M, nM));
-    if (r > 0) {
+    if (r > 0 && diag) {
       k_add_dbar<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), alpha1, M, nM);
+      FKF_LAUNCHED(ctx);
+    } else if (r > 0) {
+      // full weight: Dbar = D (alpha' I - D)^-1 / alpha' = (alpha' I - D)^-1 - I / alpha'
+      const int64_t rr = (int64_t)r * r;
+      double* Ep = f->Ep.as<double>();
+      k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Dfc, 0.0, nullptr, alpha1, Ep);
+      FKF_LAUNCHED(ctx);
+      FKF_TRY(chol_f64(ctx, r, Ep, f->cholws));
+      k_identity<<<nblk(rr), 256, 0, st>>>(r, f->Qm.as<double>(), r);
+      FKF_LAUNCHED(ctx);
+      FKF_TRY(chol_solve_f64(ctx, r, Ep, f->Qm.as<double>(), r));
+      k_add_block<<<nblk(rr), 256, 0, st>>>(r, f->Qm.as<double>(), -1.0 / alpha1, M, nM);
       FKF_LAUNCHED(ctx);
     }
     FKF_TRY(eigh_f64(ctx, nM, M, f->thM.as<double>(), thM_h, f->eigws));
@@ -819,6 +997,8 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   f->r = rnew;
   f->alpha = alpha1;
   f->k++;
+  f->diag = true;
+  f->last_path = 0;
   if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
   for (int i = 0; i < 6; i++) {
     float ms = 0;
@@ -834,8 +1014,56 @@ fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* row
   return step_impl<float>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out);
 }
 
+// Bring the state to the paper's form (Eq. sigmakk with D diagonal): with the
+// full weight Df = V diag(d) V^T (V orthogonal), W <- W V and X <- X V keep
+// X^T W = I and Sigma unchanged.
+template <typename T>
+static fkf_status canonicalize_impl(fkf_filter* f) {
+  fkf_ctx* ctx = f->ctx;
+  cudaStream_t st = ctx->stream;
+  const int r = f->r, rmax = f->r_max;
+  const int64_t n = f->n, ld = f->ldwg, rr = (int64_t)r * r;
+  double* Vt = f->Qm.as<double>();
+  FKF_CUDA(ctx, cudaMemcpyAsync(Vt, f->Df.p, rr * 8, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> w_h;
+  FKF_TRY(eigh_f64(ctx, r, Vt, f->thM.as<double>(), w_h, f->eigws));
+  double* E = f->E.as<double>();
+  k_transpose<<<nblk(rr), 256, 0, st>>>(r, r, Vt, r, E, r);  // E = V (columns = eigenvectors)
+  FKF_LAUNCHED(ctx);
+  const T* Et;
+  if (sizeof(T) == 8) {
+    Et = reinterpret_cast<const T*>(E);
+  } else {
+    k_cast<T><<<nblk(rr), 256, 0, st>>>(rr, E, f->Ecast.as<T>());
+    FKF_LAUNCHED(ctx);
+    Et = f->Ecast.as<T>();
+  }
+  const T* Wc = f->WG[f->cur].as<T>() + (rmax - r);
+  T* Wn = f->WG[1 - f->cur].as<T>() + (rmax - r);
+  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Wc, ld, Et, r, 0.0, Wn, ld));
+  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, f->Xb[f->cur].as<T>(), rmax, Et, r, 0.0,
+                    f->Xb[1 - f->cur].as<T>(), rmax));
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->D.p, f->thM.p, r * 8, cudaMemcpyDeviceToDevice, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  FKF_CUDA(ctx, cudaGetLastError());
+  f->cur = 1 - f->cur;
+  f->diag = true;
+  return FKF_OK;
+}
+
+static fkf_status canonicalize(fkf_filter* f) {
+  if (f->diag) return FKF_OK;
+  if (f->r == 0) {
+    f->diag = true;
+    return FKF_OK;
+  }
+  if (f->w == 8) return canonicalize_impl<double>(f);
+  return canonicalize_impl<float>(f);
+}
+
 fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, double* D, void* W_dev, int64_t ldw) {
   fkf_ctx* ctx = f->ctx;
+  if (D || W_dev) FKF_TRY(canonicalize(f));
   if (alpha) *alpha = f->alpha;
   if (r) *r = f->r;
   if (s_hat) {
@@ -859,6 +1087,7 @@ fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, doubl
 
 fkf_status filter_variance(fkf_filter* f, double* var_dev) {
   fkf_ctx* ctx = f->ctx;
+  FKF_TRY(canonicalize(f));
   const int64_t n = f->n;
   const double as2 = f->alpha * f->h->kernel.sigma2;
   const char* Wc = f->WG[f->cur].as<char>() + (f->r_max - f->r) * f->w;
@@ -911,12 +1140,14 @@ static fkf_status realization_impl(fkf_filter* f, const double* a_dev, int ns, d
 fkf_status filter_realization(fkf_filter* f, const double* a_dev, int ns, double* out_dev) {
   if (ns < 1) return set_err(f->ctx, FKF_EINVAL, "conditional_realization: ns >= 1 required");
   if (f->alpha <= 0) return set_err(f->ctx, FKF_ESTATE, "conditional_realization: alpha must be > 0 (run a step)");
+  FKF_TRY(canonicalize(f));
   if (f->w == 8) return realization_impl<double>(f, a_dev, ns, out_dev);
   return realization_impl<float>(f, a_dev, ns, out_dev);
 }
 
 fkf_status filter_uncertainty(fkf_filter* f, double* ent, double* tr) {
   fkf_ctx* ctx = f->ctx;
+  FKF_TRY(canonicalize(f));
   const int r = f->r;
   std::vector<double> d(r);
   if (r > 0) {
@@ -1041,6 +1272,7 @@ static fkf_status refresh_impl(fkf_filter* f) {
 }
 
 fkf_status filter_refresh(fkf_filter* f) {
+  FKF_TRY(canonicalize(f));
   if (f->r > f->m_max) {
     // refresh uses the G columns of the spare buffer as scratch for Gamma X (r columns)
     return set_err(f->ctx, FKF_ESTATE, "refresh: rank %d exceeds the scratch width m_max=%d", f->r, f->m_max);
@@ -1058,6 +1290,7 @@ struct CkptHeader {
 
 fkf_status filter_checkpoint(fkf_filter* f, const char* path) {
   fkf_ctx* ctx = f->ctx;
+  FKF_TRY(canonicalize(f));
   FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return set_err(ctx, FKF_EINVAL, "checkpoint: cannot open %s", path);
@@ -1122,6 +1355,7 @@ fkf_status filter_restore(fkf_filter* f, const char* path) {
   f->r = (int)r;
   f->k = hd.k;
   f->alpha = hd.alpha;
+  f->diag = true;
   return FKF_OK;
 }
 
@@ -1140,6 +1374,14 @@ fkf_status filter_phase_times(fkf_filter* f, double* ms6) {
 }
 
 fkf_ctx* filter_ctx(fkf_filter* f) { return f->ctx; }
+
+void filter_stats(const fkf_filter* f, fkf_filter_stats* s) {
+  s->k = f->k;
+  s->alpha = f->alpha;
+  s->r = f->r;
+  s->last_path = f->last_path;
+  s->diagonal = f->diag ? 1 : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Reverse-mode gradient of the summed innovation NLL for a fixed H.
@@ -1178,13 +1420,6 @@ __global__ void k_spmv_orig(int m, const int64_t* __restrict__ rowptr, const int
   if (lane == 0) out[w] = acc;
 }
 
-// C = a*A + b*B (+ d on the diagonal), n x n
-__global__ void k_lincomb(int n, double a, const double* __restrict__ A, double b, const double* __restrict__ B,
-                          double d, double* __restrict__ C) {
-  const int64_t total = (int64_t)n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    C[e] = a * A[e] + (B ? b * B[e] : 0.0) + ((e / n == e % n) ? d : 0.0);
-}
 
 // v_out = a*x + b*y (n)
 __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,

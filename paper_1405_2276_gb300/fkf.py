@@ -58,6 +58,11 @@ class fkf_step_desc(C.Structure):
     ]
 
 
+class fkf_filter_stats(C.Structure):
+    _fields_ = [("k", C.c_int64), ("alpha", C.c_double), ("r", C.c_int32), ("last_path", C.c_int32),
+                ("diagonal", C.c_int32)]
+
+
 class FkfError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -99,6 +104,7 @@ _sigs = {
     "fkf_nll_gradient": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, C.c_double, _P, C.c_double,
                                    _P, _P, _P, _P, _P]),
     "fkf_filter_step_batched": (C.c_int, [C.POINTER(fkf_step_desc), C.c_int32, C.c_int32]),
+    "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -278,6 +284,12 @@ def fkf_filter_get(f, n, want_s=True, want_D=True, W=None):
     _check(_lib.fkf_filter_get(f.ptr, _ptr(s), None, None, _ptr(D), _ptr(W), W.stride(0) if W is not None else 0),
            f.ctx)
     return dict(s=s, alpha=alpha.value, r=r.value, D=D[: r.value] if D is not None else None)
+
+
+def fkf_filter_get_stats(f) -> dict:
+    s = fkf_filter_stats()
+    _check(_lib.fkf_filter_get_stats(f.ptr, C.byref(s)), f.ctx)
+    return {k: getattr(s, k) for k, _ in s._fields_}
 
 
 def fkf_variance(f, var_dev) -> None:

@@ -283,3 +283,45 @@ def test_fixed_geometry_rank_stays_at_m(fkf):
     fkf.fkf_filter_destroy(f)
     fkf.fkf_hmatrix_destroy(hm)
     fkf.fkf_destroy(ctx)
+
+
+def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
+    """A repeated operator brings no information outside span(W): the basis is
+    kept and the (then non-diagonal) weight is updated in information form,
+    several steps in a row with no observation in between; a new operator
+    then forces the merge path.  Everything against the dense oracle."""
+    rng = np.random.default_rng(synth.BASE_SEED + 7)
+    nx = ny = 20
+    pts = synth.grid_points_2d(nx, ny)
+    p0, p1 = synth.cross_well_geometry_2d(6, 4)
+    Ha = synth.trace_rays_2d(nx, ny, p0, p1)
+    Hb = synth.varying_ray_operators(rng, nx, ny, [15])[0]
+    seq = [Ha, Ha, Ha, Ha, Hb, Ha, Ha, Ha]
+    ys = [rng.standard_normal(h.nrows) * 0.3 for h in seq]
+    G = covariance.dense_gamma(pts, 1.5, 0.25, 1.0)
+    ref = kalman.kf_dense(G, [(ys[k], synth.csr_to_dense(h), 1e-4) for k, h in enumerate(seq)])
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.25, 1.0, leaf=32, eta=0.0)
+    f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, 24, 48)
+    paths = []
+    for k, h in enumerate(seq):
+        nll = fkf.fkf_filter_step(f, ys[k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
+        assert abs(nll - ref[k]["nll"]) < 1e-10 * abs(ref[k]["nll"]), k
+        paths.append(fkf.fkf_filter_get_stats(f)["last_path"])
+    assert paths == [0, 1, 1, 1, 0, 1, 1, 1]
+    assert fkf.fkf_filter_get_stats(f)["diagonal"] == 0
+    import torch
+
+    n = pts.shape[0]
+    st = fkf.fkf_filter_get(f, n)
+    assert fkf.fkf_filter_get_stats(f)["diagonal"] == 1
+    W = torch.empty((n, st["r"]), dtype=torch.float64, device="cuda")
+    fkf.fkf_filter_get(f, n, want_s=False, want_D=False, W=W)
+    W = W.cpu().numpy()
+    Sig = st["alpha"] * G - (W * st["D"]) @ W.T
+    assert rel_err(st["s"], ref[-1]["s"]) < 1e-10
+    assert rel_err(Sig, ref[-1]["Sigma"]) < 1e-10
+    np.testing.assert_allclose(W.T @ np.linalg.solve(G, W), np.eye(W.shape[1]), atol=1e-8)
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
