@@ -166,6 +166,13 @@ fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t l
  * Errors: EINVAL (arguments, operator too large for the scratch), ECUDA. */
 fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev,
                                                int64_t ldy, int64_t ncols);
+/* Engine of the H-apply for an FP32 operator: 1 (default) = 5th-generation
+ * tensor cores (tcgen05.mma kind::tf32 with a 3xTF32 split, FP32
+ * accumulation in TMEM); 0 = the FP32 SIMT tile engine.  FP64 operators
+ * always use the FP64 SIMT engine.  Errors: EINVAL (engine not 0/1, or 1 for
+ * an FP64 operator).  A tensor-core wait that expires makes the apply (or the
+ * filter step) return FKF_ETIMEOUT. */
+fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
 /* Permutation: perm[i] = original index of the i-th point in cluster order. */
 fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host);
 /* Dense copy of Gamma_H (host, N x N row-major, original order); N <= 8192. */

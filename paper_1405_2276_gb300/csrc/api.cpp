@@ -181,6 +181,15 @@ FKF_API fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, i
   FKF_TRY(check_apply_args(h, X_dev, ldx, Y_dev, ldy, ncols));
   FKF_TRY(hmat_apply_clustered(h, X_dev, ldx, Y_dev, ldy, ncols));
   FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  return hmat_tc_check(h);
+}
+
+FKF_API fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine) {
+  if (!h) return FKF_EINVAL;
+  if (engine != 0 && engine != 1) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0 or 1");
+  if (engine == 1 && h->prec != FKF_FP32)
+    return set_err(h->ctx, FKF_EINVAL, "set_engine: the tensor-core engine needs an FP32 operator");
+  h->engine = engine;
   return FKF_OK;
 }
 
@@ -208,7 +217,7 @@ FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx
   FKF_TRY(hmat_apply_clustered(h, h->xperm.p, ncols, h->yperm.p, ncols, ncols));
   FKF_TRY(hmat_permute_rows(h, h->yperm.p, ncols, h->iperm_d.as<int64_t>(), Y_dev, ldy, h->n, ncols));
   FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return FKF_OK;
+  return hmat_tc_check(h);
 }
 
 FKF_API fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host) {

@@ -116,6 +116,26 @@ struct P2Leaf {
   int32_t pad;
 };
 
+// Tensor-core phase-2 tile: 128 consecutive rows (whole leaves packed) and
+// its merged segment list; a segment covers tile rows [row_lo, row_hi) and
+// a_off addresses the A row of tile row row_lo.
+struct TcSeg {
+  int64_t a_off;
+  int64_t b_row;
+  int32_t lda;
+  int32_t K;
+  int32_t near;
+  int32_t row_lo, row_hi;
+  int32_t pad;
+};
+
+struct TcTile {
+  int64_t row0;
+  int32_t rows;
+  int32_t seg0, nseg;
+  int32_t pad;
+};
+
 struct HostHmat;  // host-side build result (hbuild.cpp)
 
 struct fkf_hmat {
@@ -134,6 +154,10 @@ struct fkf_hmat {
   DevBuf perm_d, iperm_d;     // int64
   int64_t n_p1 = 0, n_p1red = 0, n_leaf = 0, ktot = 0, part_rows = 0;
   int32_t max_leaf = 0;
+  // tensor-core schedules (FP32 operators)
+  DevBuf tcp1, tcred, tctile, tcseg, tc_err;
+  int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0;
+  int engine = 0;  // 0: SIMT tile engine, 1: tensor cores (tcgen05, FP32 operators only)
   // workspace
   DevBuf zmix, part, xperm, yperm;
   int64_t panel = 256;
@@ -149,6 +173,12 @@ fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const in
                              int64_t ldd, int64_t nrows, int64_t ncols);
 fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, const int64_t* idx_dev, double* dst,
                                  int64_t ldd, int64_t nrows, int64_t ncols);
+
+// happly_tc.cu
+fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols);
+fkf_status hmat_tc_check(fkf_hmat* h);
+void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector<P2Seg>& segs,
+                            std::vector<TcTile>& tiles, std::vector<TcSeg>& tsegs);
 
 // hbuild.cpp
 fkf_status hmat_build_host(fkf_ctx* ctx, const double* pts, int64_t n, int dim, fkf_matern k, fkf_hparams hp,

@@ -845,6 +845,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_CUDA(ctx, cudaMemcpyAsync(&nll, f->nll.p, 8, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
     FKF_CUDA(ctx, cudaGetLastError());
+    FKF_TRY(hmat_tc_check(h));
     std::swap(f->s_hat.p, f->s_new.p);
     std::swap(f->Df.p, f->Dfn.p);
     f->diag = false;
@@ -990,6 +991,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaMemcpyAsync(&nll, f->nll.p, 8, cudaMemcpyDeviceToHost, st));
   FKF_CUDA(ctx, cudaStreamSynchronize(st));
   FKF_CUDA(ctx, cudaGetLastError());
+  FKF_TRY(hmat_tc_check(h));
   // ---- commit
   std::swap(f->s_hat.p, f->s_new.p);
   std::swap(f->D.p, f->Dn.p);

@@ -163,6 +163,7 @@ fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y
   if (ncols <= 0) return FKF_OK;
   if (h->prec == FKF_FP64)
     return apply_impl<double>(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
+  if (h->engine == 1) return hmat_apply_clustered_tc(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
   return apply_impl<float>(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
 }
 
@@ -360,6 +361,51 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
       lf.pad = r0;  // row offset inside the leaf (applied to every segment's A)
       p2.push_back(lf);
     }
+  }
+  // tensor-core schedules (FP32 operators): phase-1 slot tiles of 128, phase-2
+  // tiles of 128 consecutive rows with merged segments
+  if (h->prec == FKF_FP32) {
+    std::vector<P1Item> tp1;
+    std::vector<P1Reduce> tp1r;
+    int64_t tparts = 0;
+    for (int c = 0; c < nc; c++) {
+      if (K[c] == 0) continue;
+      const int64_t nr = csize(c);
+      const int nch = (int)cdiv(nr, kChunkRows);
+      for (int64_t q0 = 0; q0 < K[c]; q0 += 128) {
+        const int nq = (int)std::min<int64_t>(128, K[c] - q0);
+        const int64_t base = tparts;
+        for (int ch = 0; ch < nch; ch++) {
+          P1Item it{};
+          it.fac_off = fac_off[c];
+          it.r0 = ch * kChunkRows;
+          it.nr = (int)std::min<int64_t>(kChunkRows, nr - it.r0);
+          it.x_row = cl[c].begin + it.r0;
+          it.out_row = nch == 1 ? -1 : base + (int64_t)ch * nq;
+          it.map_off = slot_base[c] + q0;
+          it.K = (int)K[c];
+          it.q0 = (int)q0;
+          it.nq = nq;
+          tp1.push_back(it);
+        }
+        if (nch > 1) {
+          tp1r.push_back(P1Reduce{base, slot_base[c] + q0, nq, nch});
+          tparts += (int64_t)nch * nq;
+        }
+      }
+    }
+    std::vector<TcTile> tiles;
+    std::vector<TcSeg> tsegs;
+    hmat_build_tc_schedule(p2, segs, tiles, tsegs);
+    if (!tp1.empty()) FKF_TRY(dev_upload(ctx, h->tcp1, tp1.data(), tp1.size() * sizeof(P1Item)));
+    if (!tp1r.empty()) FKF_TRY(dev_upload(ctx, h->tcred, tp1r.data(), tp1r.size() * sizeof(P1Reduce)));
+    FKF_TRY(dev_upload(ctx, h->tctile, tiles.data(), tiles.size() * sizeof(TcTile)));
+    FKF_TRY(dev_upload(ctx, h->tcseg, tsegs.data(), std::max<size_t>(tsegs.size(), 1) * sizeof(TcSeg)));
+    h->n_tcp1 = (int64_t)tp1.size();
+    h->n_tcred = (int64_t)tp1r.size();
+    h->n_tctile = (int64_t)tiles.size();
+    h->tc_part_rows = std::max(tparts, part_rows);
+    h->engine = 1;
   }
   // upload
   std::vector<char> tmp;

@@ -1,0 +1,404 @@
+// H-apply on the 5th-generation tensor cores (FP32 operators): both phases of
+// the two-phase apply run as 128 x 128 tiles of tcgen05.mma kind::tf32 with
+// the accumulator in TMEM.  Each FP32 operand value x is split into
+// hi = tf32(x) and lo = tf32(x - hi) while it is staged into shared memory, and
+// every product is accumulated as hi*hi + hi*lo + lo*hi (3xTF32, FP32
+// accumulation), which keeps FP32-level accuracy.
+//
+// Staging: 256 threads load a K-chunk of 32 for A (128 rows) and B (128
+// columns) with coalesced global loads, split, and write both halves in the
+// canonical K-major no-swizzle core-matrix layout (umma.cuh); two stages
+// alternate, so the loads of chunk c+1 overlap the MMAs of chunk c, which one
+// thread issues and commits to the stage's mbarrier.  The epilogue reads TMEM
+// with tcgen05.ld (warp w reads lanes 32*(w%4).., columns 64*(w/4)..).
+//
+// Phase 2 tiles are 128 consecutive rows (whole leaves packed together); the
+// segments of the packed leaves are merged where they read the same slot rows
+// with contiguous factor rows (every common ancestor), so those B operands
+// are loaded once per tile instead of once per leaf.
+#include <algorithm>
+#include <cstring>
+
+#include "common.h"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kStages = 2;
+constexpr int kStageBytes = 4 * umma::kChunkBytes;  // A_hi, A_lo, B_hi, B_lo
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kMaxPolls = 1u << 22;  // bounded mbarrier waits (error flag on expiry)
+constexpr uint32_t kIdesc = umma::idesc_tf32(128, 128);
+
+struct Smem {
+  uint8_t* stage[kStages];
+  uint64_t* mbar;      // [kStages]
+  uint32_t* tmem_slot;
+  int* fail;
+};
+
+__device__ __forceinline__ Smem smem_layout(uint8_t* base) {
+  Smem s;
+  for (int i = 0; i < kStages; i++) s.stage[i] = base + i * kStageBytes;
+  uint8_t* tail = base + kStages * kStageBytes;
+  s.mbar = reinterpret_cast<uint64_t*>(tail);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 64);
+  s.fail = reinterpret_cast<int*>(tail + 128);
+  return s;
+}
+
+// Write 4 consecutive-k values (one float4) of row `row` at k (k % 4 == 0),
+// split into the hi and lo chunk buffers.
+__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
+                                     float v3) {
+  uint4 h, l;
+  umma::split_tf32(v0, h.x, l.x);
+  umma::split_tf32(v1, h.y, l.y);
+  umma::split_tf32(v2, h.z, l.z);
+  umma::split_tf32(v3, h.w, l.w);
+  const uint32_t off = umma::chunk_offset(row, k);
+  *reinterpret_cast<uint4*>(hi_base + off) = h;
+  *reinterpret_cast<uint4*>(lo_base + off) = l;
+}
+
+// B chunk: B(k, n) = B[(k0 + k) * ldb + n], k < kv, n < nv (zero elsewhere)
+__device__ __forceinline__ void load_b(uint8_t* st, const float* __restrict__ B, int64_t ldb, int k0, int kv, int nv) {
+  const int t = threadIdx.x;
+  const int n = t & 127, g = t >> 7;
+  uint8_t* bh = st + 2 * umma::kChunkBytes;
+  uint8_t* bl = st + 3 * umma::kChunkBytes;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int k = g * 16 + 4 * j;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int kk = k0 + k + u;
+      v[u] = (n < nv && kk < kv) ? __ldg(B + (int64_t)kk * ldb + n) : 0.f;
+    }
+    put4(bh, bl, n, k, v[0], v[1], v[2], v[3]);
+  }
+}
+
+// A chunk, k-contiguous rows: A(m, k) = A[(m - lo) * lda + k0 + k] for m in [lo, hi), k < kv
+__device__ __forceinline__ void load_a_rows(uint8_t* st, const float* __restrict__ A, int64_t lda, int lo, int hi, int k0,
+                                            int kv, bool vec) {
+  const int t = threadIdx.x;
+  const int m = t & 127, g = t >> 7;
+  const bool rv = m >= lo && m < hi;
+  const float* row = A + (int64_t)(m - lo) * lda + k0;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int k = g * 16 + 4 * j;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (rv) {
+      if (vec && k0 + k + 3 < kv) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(row + k));
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (k0 + k + u < kv) v[u] = __ldg(row + k + u);
+      }
+    }
+    put4(st, st + umma::kChunkBytes, m, k, v[0], v[1], v[2], v[3]);
+  }
+}
+
+// A chunk, m-contiguous: A(m, k) = A[(k0 + k) * lda + m] for m < mv, k < kv
+__device__ __forceinline__ void load_a_cols(uint8_t* st, const float* __restrict__ A, int64_t lda, int mv, int k0,
+                                            int kv) {
+  const int t = threadIdx.x;
+  const int m = t & 127, g = t >> 7;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int k = g * 16 + 4 * j;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int kk = k0 + k + u;
+      v[u] = (m < mv && kk < kv) ? __ldg(A + (int64_t)kk * lda + m) : 0.f;
+    }
+    put4(st, st + umma::kChunkBytes, m, k, v[0], v[1], v[2], v[3]);
+  }
+}
+
+// Issue the 3xTF32 MMAs of one staged chunk (one thread).
+__device__ __forceinline__ void issue_chunk(uint8_t* st, uint32_t tmem, bool first) {
+  const uint32_t a_hi = umma::smem_u32(st), a_lo = a_hi + umma::kChunkBytes;
+  const uint32_t b_hi = a_hi + 2 * umma::kChunkBytes, b_lo = a_hi + 3 * umma::kChunkBytes;
+#pragma unroll
+  for (int kk = 0; kk < umma::kChunk / 8; kk++) {
+    const uint32_t koff = kk * 2 * umma::kLBO;  // two core matrices along K per MMA
+    umma::mma_tf32(tmem, umma::smem_desc(a_hi + koff), umma::smem_desc(b_hi + koff), kIdesc, (first && kk == 0) ? 0u : 1u);
+    umma::mma_tf32(tmem, umma::smem_desc(a_hi + koff), umma::smem_desc(b_lo + koff), kIdesc, 1u);
+    umma::mma_tf32(tmem, umma::smem_desc(a_lo + koff), umma::smem_desc(b_hi + koff), kIdesc, 1u);
+  }
+}
+
+// Pipeline step for chunk number c (stage c % 2).  Returns false if a wait expired.
+template <typename LoadFn>
+__device__ __forceinline__ bool pipeline_chunk(const Smem& s, uint32_t tmem, int c, LoadFn&& load) {
+  const int st = c & 1;
+  if (c >= kStages) {
+    if (!umma::mbar_wait(&s.mbar[st], ((c - kStages) >> 1) & 1, kMaxPolls)) atomicExch(s.fail, 1);
+  }
+  __syncthreads();
+  if (*s.fail) return false;
+  load(s.stage[st]);
+  umma::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    umma::fence_after_sync();
+    issue_chunk(s.stage[st], tmem, c == 0);
+    umma::commit(&s.mbar[st]);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tile_begin(const Smem& s) {
+  if (threadIdx.x < 32) umma::tmem_alloc(s.tmem_slot, kTmemCols);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; i++) umma::mbar_init(&s.mbar[i], 1);
+    *s.fail = 0;
+    umma::fence_mbar_init();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+}
+
+// Wait for the last chunk's MMAs (bounded); returns false on expiry.
+__device__ __forceinline__ bool tile_drain(const Smem& s, int nchunks) {
+  bool ok = true;
+  if (nchunks > 0) {
+    const int c = nchunks - 1;
+    ok = umma::mbar_wait(&s.mbar[c & 1], (c >> 1) & 1, kMaxPolls);
+    if (!ok) atomicExch(s.fail, 1);
+  }
+  __syncthreads();
+  umma::fence_after_sync();
+  return ok && !*s.fail;
+}
+
+__device__ __forceinline__ void tile_end(const Smem& s, uint32_t tmem) {
+  umma::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) umma::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Epilogue: thread owns row (32 * (warp % 4) + lane) and 64 columns starting at
+// 64 * (warp / 4); calls out(row, col, value) for valid entries.
+template <typename OutFn>
+__device__ __forceinline__ void tile_store(uint32_t tmem, int rows, int nv, bool zero, OutFn&& out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane;
+  const int c0 = 64 * (warp >> 2);
+  for (int h = 0; h < 2; h++) {
+    float v[32];
+    if (zero) {
+#pragma unroll
+      for (int i = 0; i < 32; i++) v[i] = 0.f;
+    } else {
+      umma::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * h), v);
+    }
+    if (row < rows) {
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const int col = c0 + 32 * h + i;
+        if (col < nv) out(row, col, v[i]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_phase2_tc(const TcTile* __restrict__ tiles, const TcSeg* __restrict__ segs, const float* __restrict__ fac,
+                const float* __restrict__ nearv, const float* __restrict__ zmix, int64_t ldz,
+                const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy, int ncols,
+                int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const Smem s = smem_layout(smem_raw);
+  const TcTile tl = tiles[blockIdx.x];
+  const int n0 = blockIdx.y * 128;
+  const int nv = min(128, ncols - n0);
+  if (nv <= 0) return;
+  tile_begin(s);
+  const uint32_t tmem = *s.tmem_slot;
+  int c = 0;
+  bool ok = true;
+  for (int si = 0; si < tl.nseg && ok; si++) {
+    const TcSeg sg = segs[tl.seg0 + si];
+    const float* A = (sg.near ? nearv : fac) + sg.a_off;
+    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
+    const int64_t ldb = sg.near ? ldx : ldz;
+    const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
+    for (int k0 = 0; k0 < sg.K && ok; k0 += umma::kChunk, c++) {
+      ok = pipeline_chunk(s, tmem, c, [&](uint8_t* st) {
+        load_a_rows(st, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
+        load_b(st, B, ldb, k0, sg.K, nv);
+      });
+    }
+  }
+  if (!ok) c -= 1;  // the failed chunk was counted but not issued
+  ok = tile_drain(s, c) && ok;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else {
+    float* Yt = Y + tl.row0 * ldy + n0;
+    tile_store(tmem, tl.rows, nv, c == 0, [&](int row, int col, float v) { Yt[(int64_t)row * ldy + col] = v; });
+  }
+  tile_end(s, tmem);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_phase1_tc(const P1Item* __restrict__ items, const float* __restrict__ fac, const float* __restrict__ X,
+                int64_t ldx, int ncols, const int64_t* __restrict__ slotmap, float* __restrict__ zmix,
+                float* __restrict__ part, int64_t ldz, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const Smem s = smem_layout(smem_raw);
+  const P1Item it = items[blockIdx.x];
+  const int n0 = blockIdx.y * 128;
+  const int nv = min(128, ncols - n0);
+  if (nv <= 0) return;
+  tile_begin(s);
+  const uint32_t tmem = *s.tmem_slot;
+  // A(m = slot, k = row) = Fac_c[(r0 + row) * K + q0 + slot]; B(k = row, n) = X[(x_row + row) * ldx + n0 + n]
+  const float* A = fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0;
+  const float* B = X + it.x_row * ldx + n0;
+  int c = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < it.nr && ok; k0 += umma::kChunk, c++) {
+    ok = pipeline_chunk(s, tmem, c, [&](uint8_t* st) {
+      load_a_cols(st, A, it.K, it.nq, k0, it.nr);
+      load_b(st, B, ldx, k0, it.nr, nv);
+    });
+  }
+  if (!ok) c -= 1;
+  ok = tile_drain(s, c) && ok;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else {
+    tile_store(tmem, it.nq, nv, c == 0, [&](int q, int col, float v) {
+      float* dst = it.out_row < 0 ? zmix + slotmap[it.map_off + q] * ldz : part + (it.out_row + q) * ldz;
+      dst[n0 + col] = v;
+    });
+  }
+  tile_end(s, tmem);
+}
+
+__global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const float* __restrict__ part,
+                                   const int64_t* __restrict__ slotmap, float* __restrict__ zmix, int64_t ldz,
+                                   int ncols) {
+  const P1Reduce it = items[blockIdx.x];
+  const int64_t total = (int64_t)it.nq * ncols;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total; e += (int64_t)blockDim.x * gridDim.y) {
+    const int q = (int)(e / ncols), n = (int)(e % ncols);
+    float acc = 0.f;
+    for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldz + n];
+    zmix[slotmap[it.map_off + q] * ldz + n] = acc;
+  }
+}
+
+}  // namespace
+
+// Tensor-core apply for an FP32 operator (cluster order).
+fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+  fkf_ctx* ctx = h->ctx;
+  const int64_t P = h->panel;
+  const size_t zbytes = (size_t)std::max<int64_t>(h->ktot, 1) * P * sizeof(float);
+  if (h->zmix.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zmix, zbytes));
+  const size_t pbytes = (size_t)std::max<int64_t>(h->tc_part_rows, 1) * P * sizeof(float);
+  if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
+  if (h->tc_err.bytes < 64) {
+    FKF_TRY(dev_alloc(ctx, h->tc_err, 64));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, ctx->stream));
+  }
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_phase2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_phase1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  for (int64_t c0 = 0; c0 < ncols; c0 += P) {
+    const int nc = (int)std::min<int64_t>(P, ncols - c0);
+    const int ntile = (int)cdiv(nc, 128);
+    if (h->n_tcp1 > 0) {
+      k_phase1_tc<<<dim3((unsigned)h->n_tcp1, ntile), kThreads, kSmemBytes, ctx->stream>>>(
+          h->tcp1.as<P1Item>(), h->fac.as<float>(), X + c0, ldx, nc, h->slotmap.as<int64_t>(), h->zmix.as<float>(),
+          h->part.as<float>(), P, h->tc_err.as<int>());
+      FKF_LAUNCHED(ctx);
+    }
+    if (h->n_tcred > 0) {
+      k_phase1_reduce_tc<<<dim3((unsigned)h->n_tcred, 4), 256, 0, ctx->stream>>>(
+          h->tcred.as<P1Reduce>(), h->part.as<float>(), h->slotmap.as<int64_t>(), h->zmix.as<float>(), P, nc);
+      FKF_LAUNCHED(ctx);
+    }
+    k_phase2_tc<<<dim3((unsigned)h->n_tctile, ntile), kThreads, kSmemBytes, ctx->stream>>>(
+        h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->fac.as<float>(), h->nearv.as<float>(), h->zmix.as<float>(),
+        P, X + c0, ldx, Y + c0, ldy, nc, h->tc_err.as<int>());
+    FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+// Reads (and clears) the tensor-core wait-expiry flag; synchronises.
+fkf_status hmat_tc_check(fkf_hmat* h) {
+  if (!h->tc_err.p) return FKF_OK;
+  int e = 0;
+  FKF_CUDA(h->ctx, cudaMemcpyAsync(&e, h->tc_err.p, 4, cudaMemcpyDeviceToHost, h->ctx->stream));
+  FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  if (e) {
+    FKF_CUDA(h->ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, h->ctx->stream));
+    return set_err(h->ctx, FKF_ETIMEOUT, "tensor-core H-apply: an mbarrier wait expired");
+  }
+  return FKF_OK;
+}
+
+// Build the tensor-core work lists from the per-leaf segment lists and the
+// cluster factor layout (host).
+void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector<P2Seg>& segs,
+                            std::vector<TcTile>& tiles, std::vector<TcSeg>& tsegs) {
+  size_t i = 0;
+  while (i < leaves.size()) {
+    TcTile t{};
+    t.row0 = leaves[i].row0;
+    t.seg0 = (int)tsegs.size();
+    int rows = 0;
+    while (i < leaves.size() && rows + leaves[i].rows <= 128 && leaves[i].row0 == t.row0 + rows) {
+      const P2Leaf& lf = leaves[i];
+      const int ro = rows;
+      for (int k = 0; k < lf.nseg; k++) {
+        const P2Seg& sg = segs[lf.seg0 + k];
+        const int64_t a_off = sg.a_off + (int64_t)lf.pad * sg.lda;
+        bool merged = false;
+        for (size_t q = t.seg0; q < tsegs.size(); q++) {
+          TcSeg& e = tsegs[q];
+          if (e.near == sg.near && e.b_row == sg.b_row && e.K == sg.K && e.lda == sg.lda && e.row_hi == ro &&
+              e.a_off + (int64_t)(e.row_hi - e.row_lo) * e.lda == a_off) {
+            e.row_hi = ro + lf.rows;
+            merged = true;
+            break;
+          }
+        }
+        if (!merged) {
+          TcSeg e{};
+          e.a_off = a_off;
+          e.b_row = sg.b_row;
+          e.lda = sg.lda;
+          e.K = sg.K;
+          e.near = sg.near;
+          e.row_lo = ro;
+          e.row_hi = ro + lf.rows;
+          tsegs.push_back(e);
+        }
+      }
+      rows += lf.rows;
+      i++;
+    }
+    t.rows = rows;
+    t.nseg = (int)tsegs.size() - t.seg0;
+    tiles.push_back(t);
+  }
+}

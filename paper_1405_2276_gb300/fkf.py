@@ -105,6 +105,7 @@ _sigs = {
                                    _P, _P, _P, _P, _P]),
     "fkf_filter_step_batched": (C.c_int, [C.POINTER(fkf_step_desc), C.c_int32, C.c_int32]),
     "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
+    "fkf_hmatrix_set_engine": (C.c_int, [_P, C.c_int32]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -206,6 +207,11 @@ def fkf_hmatrix_apply_clustered_noalloc(h, X, Y, ncols=None, ldx=None, ldy=None)
     ldx = X.stride(0) if ldx is None else ldx
     ldy = Y.stride(0) if ldy is None else ldy
     _check(_lib.fkf_hmatrix_apply_clustered_noalloc(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
+
+
+def fkf_hmatrix_set_engine(h, engine: int) -> None:
+    """1 = tensor cores (tcgen05, 3xTF32; FP32 operators), 0 = SIMT tile engine."""
+    _check(_lib.fkf_hmatrix_set_engine(h.ptr, engine), h.ctx)
 
 
 def fkf_hmatrix_permutation(h, n):

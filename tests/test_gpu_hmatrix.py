@@ -141,4 +141,35 @@ def test_invalid_arguments(fkf, ctx):
     X = torch.zeros((64, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(fkf.FkfError):  # X and Y overlap
         fkf.fkf_hmatrix_apply(hm, X, X)
+    with pytest.raises(fkf.FkfError):  # tensor-core engine needs an FP32 operator
+        fkf.fkf_hmatrix_set_engine(hm, 1)
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+@pytest.mark.parametrize("grid,leaf,ncols", [((37, 23), 16, 300), ((64, 48), 32, 130), ((256, 256), 64, 260)])
+def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
+    """The tcgen05 3xTF32 engine against the FP32 SIMT engine on the same
+    operator (identical factors) and against the exact product."""
+    import torch
+
+    pts = synth.grid_points_2d(*grid)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.1, 1.0, leaf=leaf, eta=1.0, aca_tol=1e-8, k_cap=32, precision=1)
+    rng = np.random.default_rng(13)
+    X = torch.from_numpy(rng.standard_normal((n, ncols))).to("cuda", torch.float32)
+    Y_tc = torch.empty_like(X)
+    Y_simt = torch.empty_like(X)
+    fkf.fkf_hmatrix_set_engine(hm, 1)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y_tc)
+    fkf.fkf_hmatrix_set_engine(hm, 0)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y_simt)
+    a = Y_tc.double().cpu().numpy()
+    b = Y_simt.double().cpu().numpy()
+    assert np.isfinite(a).all()
+    assert np.abs(a - b).max() / np.abs(b).max() < 1e-5
+    if n <= 4096:
+        perm = fkf.fkf_hmatrix_permutation(hm, n)
+        G = covariance.dense_gamma(pts[perm], 0.5, 0.1, 1.0)  # cluster order
+        ref = G @ X.double().cpu().numpy()
+        assert np.abs(a - ref).max() / np.abs(ref).max() < 2e-5
     fkf.fkf_hmatrix_destroy(hm)
