@@ -49,82 +49,78 @@ __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   return s;
 }
 
-// Write 4 consecutive-k values (one float4) of row `row` at k (k % 4 == 0),
-// split into the hi and lo chunk buffers.
-__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
-                                     float v3) {
+// Per-thread staging registers: thread t covers row/column (t % 128) of the
+// chunk and k in [16 * (t / 128), 16 * (t / 128) + 16) of both operands.
+struct Regs {
+  float a[16];
+  float b[16];
+};
+
+// Split 4 consecutive-k values of `row` at k (k % 4 == 0) and store both halves.
+__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, const float* v) {
   uint4 h, l;
-  umma::split_tf32(v0, h.x, l.x);
-  umma::split_tf32(v1, h.y, l.y);
-  umma::split_tf32(v2, h.z, l.z);
-  umma::split_tf32(v3, h.w, l.w);
+  umma::split_tf32(v[0], h.x, l.x);
+  umma::split_tf32(v[1], h.y, l.y);
+  umma::split_tf32(v[2], h.z, l.z);
+  umma::split_tf32(v[3], h.w, l.w);
   const uint32_t off = umma::chunk_offset(row, k);
   *reinterpret_cast<uint4*>(hi_base + off) = h;
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-// B chunk: B(k, n) = B[(k0 + k) * ldb + n], k < kv, n < nv (zero elsewhere)
-__device__ __forceinline__ void load_b(uint8_t* st, const float* __restrict__ B, int64_t ldb, int k0, int kv, int nv) {
+__device__ __forceinline__ void store_regs(uint8_t* st, const Regs& r) {
   const int t = threadIdx.x;
-  const int n = t & 127, g = t >> 7;
-  uint8_t* bh = st + 2 * umma::kChunkBytes;
-  uint8_t* bl = st + 3 * umma::kChunkBytes;
+  const int row = t & 127, g = t >> 7;
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     const int k = g * 16 + 4 * j;
-    float v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int kk = k0 + k + u;
-      v[u] = (n < nv && kk < kv) ? __ldg(B + (int64_t)kk * ldb + n) : 0.f;
-    }
-    put4(bh, bl, n, k, v[0], v[1], v[2], v[3]);
+    put4(st, st + umma::kChunkBytes, row, k, &r.a[4 * j]);
+    put4(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, row, k, &r.b[4 * j]);
   }
 }
 
-// A chunk, k-contiguous rows: A(m, k) = A[(m - lo) * lda + k0 + k] for m in [lo, hi), k < kv
-__device__ __forceinline__ void load_a_rows(uint8_t* st, const float* __restrict__ A, int64_t lda, int lo, int hi, int k0,
+// B(k, n) = B[(k0 + k) * ldb + n] for k < kv, n < nv (zero elsewhere)
+__device__ __forceinline__ void load_b(float* v, const float* __restrict__ B, int64_t ldb, int k0, int kv, int nv) {
+  const int t = threadIdx.x;
+  const int n = t & 127, g = t >> 7;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const int kk = k0 + g * 16 + i;
+    v[i] = (n < nv && kk < kv) ? __ldg(B + (int64_t)kk * ldb + n) : 0.f;
+  }
+}
+
+// A(m, k) = A[(m - lo) * lda + k0 + k] for m in [lo, hi), k < kv (k-contiguous rows)
+__device__ __forceinline__ void load_a_rows(float* v, const float* __restrict__ A, int64_t lda, int lo, int hi, int k0,
                                             int kv, bool vec) {
   const int t = threadIdx.x;
   const int m = t & 127, g = t >> 7;
   const bool rv = m >= lo && m < hi;
-  const float* row = A + (int64_t)(m - lo) * lda + k0;
+  const float* row = A + (int64_t)(m - lo) * lda + k0 + g * 16;
+  const int kb = k0 + g * 16;
 #pragma unroll
   for (int j = 0; j < 4; j++) {
-    const int k = g * 16 + 4 * j;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (rv) {
-      if (vec && k0 + k + 3 < kv) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(row + k));
-        v[0] = q.x;
-        v[1] = q.y;
-        v[2] = q.z;
-        v[3] = q.w;
-      } else {
+    if (rv && vec && kb + 4 * j + 3 < kv) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(row + 4 * j));
+      v[4 * j] = q.x;
+      v[4 * j + 1] = q.y;
+      v[4 * j + 2] = q.z;
+      v[4 * j + 3] = q.w;
+    } else {
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (k0 + k + u < kv) v[u] = __ldg(row + k + u);
-      }
+      for (int u = 0; u < 4; u++) v[4 * j + u] = (rv && kb + 4 * j + u < kv) ? __ldg(row + 4 * j + u) : 0.f;
     }
-    put4(st, st + umma::kChunkBytes, m, k, v[0], v[1], v[2], v[3]);
   }
 }
 
-// A chunk, m-contiguous: A(m, k) = A[(k0 + k) * lda + m] for m < mv, k < kv
-__device__ __forceinline__ void load_a_cols(uint8_t* st, const float* __restrict__ A, int64_t lda, int mv, int k0,
-                                            int kv) {
+// A(m, k) = A[(k0 + k) * lda + m] for m < mv, k < kv (m-contiguous)
+__device__ __forceinline__ void load_a_cols(float* v, const float* __restrict__ A, int64_t lda, int mv, int k0, int kv) {
   const int t = threadIdx.x;
   const int m = t & 127, g = t >> 7;
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int k = g * 16 + 4 * j;
-    float v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int kk = k0 + k + u;
-      v[u] = (m < mv && kk < kv) ? __ldg(A + (int64_t)kk * lda + m) : 0.f;
-    }
-    put4(st, st + umma::kChunkBytes, m, k, v[0], v[1], v[2], v[3]);
+  for (int i = 0; i < 16; i++) {
+    const int kk = k0 + g * 16 + i;
+    v[i] = (m < mv && kk < kv) ? __ldg(A + (int64_t)kk * lda + m) : 0.f;
   }
 }
 
@@ -141,24 +137,35 @@ __device__ __forceinline__ void issue_chunk(uint8_t* st, uint32_t tmem, bool fir
   }
 }
 
-// Pipeline step for chunk number c (stage c % 2).  Returns false if a wait expired.
-template <typename LoadFn>
-__device__ __forceinline__ bool pipeline_chunk(const Smem& s, uint32_t tmem, int c, LoadFn&& load) {
-  const int st = c & 1;
-  if (c >= kStages) {
-    if (!umma::mbar_wait(&s.mbar[st], ((c - kStages) >> 1) & 1, kMaxPolls)) atomicExch(s.fail, 1);
+// Main loop over the chunks of a tile.  src.first(r) / src.next(r) load the
+// next chunk into registers (returning false when there is none), so the
+// global loads of chunk c+1 are in flight while chunk c is stored, fenced
+// and handed to the tensor core.  Returns the number of chunks issued; a
+// wait that expires sets *s.fail and ends the loop.
+template <typename Src>
+__device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src) {
+  Regs r;
+  bool have = src.first(r);
+  int c = 0;
+  while (have) {
+    const int st = c & 1;
+    if (c >= kStages) {
+      if (!umma::mbar_wait(&s.mbar[st], ((c - kStages) >> 1) & 1, kMaxPolls)) atomicExch(s.fail, 1);
+    }
+    __syncthreads();
+    if (*s.fail) break;
+    store_regs(s.stage[st], r);
+    umma::fence_proxy_async();
+    __syncthreads();
+    have = src.next(r);
+    if (threadIdx.x == 0) {
+      umma::fence_after_sync();
+      issue_chunk(s.stage[st], tmem, c == 0);
+      umma::commit(&s.mbar[st]);
+    }
+    c++;
   }
-  __syncthreads();
-  if (*s.fail) return false;
-  load(s.stage[st]);
-  umma::fence_proxy_async();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    umma::fence_after_sync();
-    issue_chunk(s.stage[st], tmem, c == 0);
-    umma::commit(&s.mbar[st]);
-  }
-  return true;
+  return c;
 }
 
 __device__ __forceinline__ void tile_begin(const Smem& s) {
@@ -217,6 +224,63 @@ __device__ __forceinline__ void tile_store(uint32_t tmem, int rows, int nv, bool
   }
 }
 
+// Chunk source for phase 2: the tile's segments, K-chunks of 32 each.
+struct P2Src {
+  const TcSeg* segs;
+  int seg0, nseg;
+  const float *fac, *nearv, *zmix, *X;
+  int64_t ldz, ldx;
+  int n0, nv;
+  int si = 0, k0 = 0;
+  __device__ bool load(Regs& r) {
+    if (si >= nseg) return false;
+    const TcSeg sg = segs[seg0 + si];
+    const float* A = (sg.near ? nearv : fac) + sg.a_off;
+    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
+    const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
+    load_a_rows(r.a, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
+    load_b(r.b, B, sg.near ? ldx : ldz, k0, sg.K, nv);
+    return true;
+  }
+  __device__ bool first(Regs& r) {
+    si = 0;
+    k0 = 0;
+    while (si < nseg && segs[seg0 + si].K <= 0) si++;
+    return load(r);
+  }
+  __device__ bool next(Regs& r) {
+    k0 += umma::kChunk;
+    if (k0 >= segs[seg0 + si].K) {
+      k0 = 0;
+      si++;
+      while (si < nseg && segs[seg0 + si].K <= 0) si++;
+    }
+    return load(r);
+  }
+};
+
+// Chunk source for phase 1: rows of one cluster chunk, K-chunks of 32.
+struct P1Src {
+  const float *A, *B;
+  int64_t lda, ldb;
+  int mv, kv, nv;
+  int k0 = 0;
+  __device__ bool load(Regs& r) {
+    if (k0 >= kv) return false;
+    load_a_cols(r.a, A, lda, mv, k0, kv);
+    load_b(r.b, B, ldb, k0, kv, nv);
+    return true;
+  }
+  __device__ bool first(Regs& r) {
+    k0 = 0;
+    return load(r);
+  }
+  __device__ bool next(Regs& r) {
+    k0 += umma::kChunk;
+    return load(r);
+  }
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_phase2_tc(const TcTile* __restrict__ tiles, const TcSeg* __restrict__ segs, const float* __restrict__ fac,
                 const float* __restrict__ nearv, const float* __restrict__ zmix, int64_t ldz,
@@ -230,23 +294,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (nv <= 0) return;
   tile_begin(s);
   const uint32_t tmem = *s.tmem_slot;
-  int c = 0;
-  bool ok = true;
-  for (int si = 0; si < tl.nseg && ok; si++) {
-    const TcSeg sg = segs[tl.seg0 + si];
-    const float* A = (sg.near ? nearv : fac) + sg.a_off;
-    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
-    const int64_t ldb = sg.near ? ldx : ldz;
-    const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
-    for (int k0 = 0; k0 < sg.K && ok; k0 += umma::kChunk, c++) {
-      ok = pipeline_chunk(s, tmem, c, [&](uint8_t* st) {
-        load_a_rows(st, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
-        load_b(st, B, ldb, k0, sg.K, nv);
-      });
-    }
-  }
-  if (!ok) c -= 1;  // the failed chunk was counted but not issued
-  ok = tile_drain(s, c) && ok;
+  P2Src src{segs, tl.seg0, tl.nseg, fac, nearv, zmix, X, ldz, ldx, n0, nv};
+  const int c = run_chunks(s, tmem, src);
+  const bool ok = tile_drain(s, c);
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
   } else {
@@ -269,18 +319,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_begin(s);
   const uint32_t tmem = *s.tmem_slot;
   // A(m = slot, k = row) = Fac_c[(r0 + row) * K + q0 + slot]; B(k = row, n) = X[(x_row + row) * ldx + n0 + n]
-  const float* A = fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0;
-  const float* B = X + it.x_row * ldx + n0;
-  int c = 0;
-  bool ok = true;
-  for (int k0 = 0; k0 < it.nr && ok; k0 += umma::kChunk, c++) {
-    ok = pipeline_chunk(s, tmem, c, [&](uint8_t* st) {
-      load_a_cols(st, A, it.K, it.nq, k0, it.nr);
-      load_b(st, B, ldx, k0, it.nr, nv);
-    });
-  }
-  if (!ok) c -= 1;
-  ok = tile_drain(s, c) && ok;
+  P1Src src{fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0, X + it.x_row * ldx + n0, it.K, ldx, it.nq, it.nr, nv};
+  const int c = run_chunks(s, tmem, src);
+  const bool ok = tile_drain(s, c);
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
   } else {

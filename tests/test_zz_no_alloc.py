@@ -30,7 +30,7 @@ def fkf():
     "grid,leaf,prec,ncols,tol",
     [
         ((37, 23), 16, 0, 70, 1e-12),    # small operator: one panel
-        ((37, 23), 16, 1, 300, 1e-6),
+        ((37, 23), 16, 1, 300, 2e-5),  # FP32: the regular apply may run on the tensor cores
         ((256, 256), 64, 0, 40, 1e-12),  # 65,536 points: several panels of the static scratch
     ],
 )
