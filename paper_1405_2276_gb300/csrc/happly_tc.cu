@@ -27,7 +27,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kStages = 2;
 constexpr int kStageBytes = 4 * umma::kChunkBytes;  // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // 65 KB: two CTAs per SM
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kMaxPolls = 1u << 22;  // bounded mbarrier waits (error flag on expiry)
 constexpr uint32_t kIdesc = umma::idesc_tf32(128, 128);
@@ -49,58 +49,35 @@ __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   return s;
 }
 
-// Per-thread staging registers: thread t covers row/column (t % 128) of the
-// chunk and k in [16 * (t / 128), 16 * (t / 128) + 16) of both operands.
+// Staging registers: threads 0..127 hold one operand-A row (16 k values);
+// threads 128..255 hold a 4 x 4 block of operand B (4 columns x 4 k), or
+// for m-contiguous A both halves hold 4 x 4 blocks.  All global loads are
+// 128-bit where alignment allows.
 struct Regs {
-  float a[16];
-  float b[16];
+  float v[16];
 };
 
 // Split 4 consecutive-k values of `row` at k (k % 4 == 0) and store both halves.
-__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, const float* v) {
+__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
+                                     float v3) {
   uint4 h, l;
-  umma::split_tf32(v[0], h.x, l.x);
-  umma::split_tf32(v[1], h.y, l.y);
-  umma::split_tf32(v[2], h.z, l.z);
-  umma::split_tf32(v[3], h.w, l.w);
+  umma::split_tf32(v0, h.x, l.x);
+  umma::split_tf32(v1, h.y, l.y);
+  umma::split_tf32(v2, h.z, l.z);
+  umma::split_tf32(v3, h.w, l.w);
   const uint32_t off = umma::chunk_offset(row, k);
   *reinterpret_cast<uint4*>(hi_base + off) = h;
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-__device__ __forceinline__ void store_regs(uint8_t* st, const Regs& r) {
-  const int t = threadIdx.x;
-  const int row = t & 127, g = t >> 7;
+// One operand row (row = tl, 0..127), 16 consecutive k from A[(row - lo) * lda + k0 ..]
+__device__ __forceinline__ void load_row16(float* v, int tl, const float* __restrict__ A, int64_t lda, int lo, int hi,
+                                           int k0, int kv, bool vec) {
+  const bool rv = tl >= lo && tl < hi;
+  const float* row = A + (int64_t)(tl - lo) * lda + k0;
 #pragma unroll
   for (int j = 0; j < 4; j++) {
-    const int k = g * 16 + 4 * j;
-    put4(st, st + umma::kChunkBytes, row, k, &r.a[4 * j]);
-    put4(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, row, k, &r.b[4 * j]);
-  }
-}
-
-// B(k, n) = B[(k0 + k) * ldb + n] for k < kv, n < nv (zero elsewhere)
-__device__ __forceinline__ void load_b(float* v, const float* __restrict__ B, int64_t ldb, int k0, int kv, int nv) {
-  const int t = threadIdx.x;
-  const int n = t & 127, g = t >> 7;
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const int kk = k0 + g * 16 + i;
-    v[i] = (n < nv && kk < kv) ? __ldg(B + (int64_t)kk * ldb + n) : 0.f;
-  }
-}
-
-// A(m, k) = A[(m - lo) * lda + k0 + k] for m in [lo, hi), k < kv (k-contiguous rows)
-__device__ __forceinline__ void load_a_rows(float* v, const float* __restrict__ A, int64_t lda, int lo, int hi, int k0,
-                                            int kv, bool vec) {
-  const int t = threadIdx.x;
-  const int m = t & 127, g = t >> 7;
-  const bool rv = m >= lo && m < hi;
-  const float* row = A + (int64_t)(m - lo) * lda + k0 + g * 16;
-  const int kb = k0 + g * 16;
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    if (rv && vec && kb + 4 * j + 3 < kv) {
+    if (rv && vec && k0 + 4 * j + 3 < kv) {
       const float4 q = __ldg(reinterpret_cast<const float4*>(row + 4 * j));
       v[4 * j] = q.x;
       v[4 * j + 1] = q.y;
@@ -108,20 +85,43 @@ __device__ __forceinline__ void load_a_rows(float* v, const float* __restrict__ 
       v[4 * j + 3] = q.w;
     } else {
 #pragma unroll
-      for (int u = 0; u < 4; u++) v[4 * j + u] = (rv && kb + 4 * j + u < kv) ? __ldg(row + 4 * j + u) : 0.f;
+      for (int u = 0; u < 4; u++) v[4 * j + u] = (rv && k0 + 4 * j + u < kv) ? __ldg(row + 4 * j + u) : 0.f;
     }
   }
 }
 
-// A(m, k) = A[(k0 + k) * lda + m] for m < mv, k < kv (m-contiguous)
-__device__ __forceinline__ void load_a_cols(float* v, const float* __restrict__ A, int64_t lda, int mv, int k0, int kv) {
-  const int t = threadIdx.x;
-  const int m = t & 127, g = t >> 7;
+__device__ __forceinline__ void put_row16(uint8_t* hi, uint8_t* lo, int tl, const float* v) {
 #pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const int kk = k0 + g * 16 + i;
-    v[i] = (m < mv && kk < kv) ? __ldg(A + (int64_t)kk * lda + m) : 0.f;
+  for (int j = 0; j < 4; j++) put4(hi, lo, tl, 4 * j, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+// 4 x 4 block of an operand stored k-rows x contiguous columns: P(k, c) =
+// P[(k0 + k) * ld + c] for columns c = 4 (tl % 32) .. +3 (< cv) and
+// k = 4 (tl / 32) .. +3 (< kv); v[4 j + i] = P(k = 4 (tl / 32) + j, c = 4 (tl % 32) + i).
+__device__ __forceinline__ void load_blk(float* v, int tl, const float* __restrict__ P, int64_t ld, int cv, int k0,
+                                         int kv, bool vec) {
+  const int c = 4 * (tl & 31), kq = tl >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int k = k0 + 4 * kq + j;
+    const float* row = P + (int64_t)k * ld + c;
+    if (k < kv && vec && c + 3 < cv) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(row));
+      v[4 * j] = q.x;
+      v[4 * j + 1] = q.y;
+      v[4 * j + 2] = q.z;
+      v[4 * j + 3] = q.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++) v[4 * j + i] = (k < kv && c + i < cv) ? __ldg(row + i) : 0.f;
+    }
   }
+}
+
+__device__ __forceinline__ void put_blk(uint8_t* hi, uint8_t* lo, int tl, const float* v) {
+  const int c = 4 * (tl & 31), kq = tl >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; i++) put4(hi, lo, c + i, 4 * kq, v[i], v[4 + i], v[8 + i], v[12 + i]);
 }
 
 // Issue the 3xTF32 MMAs of one staged chunk (one thread).
@@ -154,7 +154,7 @@ __device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src
     }
     __syncthreads();
     if (*s.fail) break;
-    store_regs(s.stage[st], r);
+    src.store(s.stage[st], r);
     umma::fence_proxy_async();
     __syncthreads();
     have = src.next(r);
@@ -224,23 +224,37 @@ __device__ __forceinline__ void tile_store(uint32_t tmem, int rows, int nv, bool
   }
 }
 
-// Chunk source for phase 2: the tile's segments, K-chunks of 32 each.
+// Chunk source for phase 2: the tile's segments, K-chunks of kChunk each.
+// Threads 0..127 stage A rows (factor or near-field rows, k-contiguous);
+// threads 128..255 stage B (slot rows of Zmix or rows of X) in 4 x 4 blocks.
 struct P2Src {
   const TcSeg* segs;
   int seg0, nseg;
   const float *fac, *nearv, *zmix, *X;
   int64_t ldz, ldx;
   int n0, nv;
+  bool bvec_z, bvec_x;
   int si = 0, k0 = 0;
   __device__ bool load(Regs& r) {
     if (si >= nseg) return false;
     const TcSeg sg = segs[seg0 + si];
-    const float* A = (sg.near ? nearv : fac) + sg.a_off;
-    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
-    const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
-    load_a_rows(r.a, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
-    load_b(r.b, B, sg.near ? ldx : ldz, k0, sg.K, nv);
+    const int t = threadIdx.x;
+    if (t < 128) {
+      const float* A = (sg.near ? nearv : fac) + sg.a_off;
+      const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
+      load_row16(r.v, t, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
+    } else {
+      const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
+      load_blk(r.v, t - 128, B, sg.near ? ldx : ldz, nv, k0, sg.K, sg.near ? bvec_x : bvec_z);
+    }
     return true;
+  }
+  __device__ void store(uint8_t* st, const Regs& r) const {
+    const int t = threadIdx.x;
+    if (t < 128)
+      put_row16(st, st + umma::kChunkBytes, t, r.v);
+    else
+      put_blk(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, t - 128, r.v);
   }
   __device__ bool first(Regs& r) {
     si = 0;
@@ -259,17 +273,30 @@ struct P2Src {
   }
 };
 
-// Chunk source for phase 1: rows of one cluster chunk, K-chunks of 32.
+// Chunk source for phase 1: rows of one cluster chunk, K-chunks of kChunk.
+// A(m = slot, k = row) is slot-contiguous, B(k = row, n) column-contiguous:
+// both are staged as 4 x 4 blocks (threads 0..127: A, 128..255: B).
 struct P1Src {
   const float *A, *B;
   int64_t lda, ldb;
   int mv, kv, nv;
+  bool avec, bvec;
   int k0 = 0;
   __device__ bool load(Regs& r) {
     if (k0 >= kv) return false;
-    load_a_cols(r.a, A, lda, mv, k0, kv);
-    load_b(r.b, B, ldb, k0, kv, nv);
+    const int t = threadIdx.x;
+    if (t < 128)
+      load_blk(r.v, t, A, lda, mv, k0, kv, avec);
+    else
+      load_blk(r.v, t - 128, B, ldb, nv, k0, kv, bvec);
     return true;
+  }
+  __device__ void store(uint8_t* st, const Regs& r) const {
+    const int t = threadIdx.x;
+    if (t < 128)
+      put_blk(st, st + umma::kChunkBytes, t, r.v);
+    else
+      put_blk(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, t - 128, r.v);
   }
   __device__ bool first(Regs& r) {
     k0 = 0;
@@ -281,7 +308,7 @@ struct P1Src {
   }
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_phase2_tc(const TcTile* __restrict__ tiles, const TcSeg* __restrict__ segs, const float* __restrict__ fac,
                 const float* __restrict__ nearv, const float* __restrict__ zmix, int64_t ldz,
                 const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy, int ncols,
@@ -294,7 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (nv <= 0) return;
   tile_begin(s);
   const uint32_t tmem = *s.tmem_slot;
-  P2Src src{segs, tl.seg0, tl.nseg, fac, nearv, zmix, X, ldz, ldx, n0, nv};
+  const bool bz = ((ldz & 3) == 0) && ((reinterpret_cast<uintptr_t>(zmix + n0) & 15) == 0);
+  const bool bx = ((ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(X + n0) & 15) == 0);
+  P2Src src{segs, tl.seg0, tl.nseg, fac, nearv, zmix, X, ldz, ldx, n0, nv, bz, bx};
   const int c = run_chunks(s, tmem, src);
   const bool ok = tile_drain(s, c);
   if (!ok) {
@@ -306,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_end(s, tmem);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_phase1_tc(const P1Item* __restrict__ items, const float* __restrict__ fac, const float* __restrict__ X,
                 int64_t ldx, int ncols, const int64_t* __restrict__ slotmap, float* __restrict__ zmix,
                 float* __restrict__ part, int64_t ldz, int* __restrict__ err) {
@@ -319,7 +348,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_begin(s);
   const uint32_t tmem = *s.tmem_slot;
   // A(m = slot, k = row) = Fac_c[(r0 + row) * K + q0 + slot]; B(k = row, n) = X[(x_row + row) * ldx + n0 + n]
-  P1Src src{fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0, X + it.x_row * ldx + n0, it.K, ldx, it.nq, it.nr, nv};
+  const float* A = fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0;
+  const float* B = X + it.x_row * ldx + n0;
+  const bool av = ((it.K & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  const bool bv = ((ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+  P1Src src{A, B, it.K, ldx, it.nq, it.nr, nv, av, bv};
   const int c = run_chunks(s, tmem, src);
   const bool ok = tile_drain(s, c);
   if (!ok) {

@@ -3,12 +3,12 @@
 // matrix descriptors, tcgen05.commit to an mbarrier, tcgen05.ld of the
 // accumulator, and bounded mbarrier waits.
 //
-// Operand layout in shared memory ("K-major, no swizzle"): a 128 x 32 fp32
-// chunk of an operand (rows = M or N index, columns = K) is stored as 8-row x
-// 4-element (16-byte) core matrices; element (row, k) lives at byte
-//     (row / 8) * 1024 + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4,
+// Operand layout in shared memory ("K-major, no swizzle"): a 128 x kChunk
+// fp32 chunk of an operand (rows = M or N index, columns = K) is stored as
+// 8-row x 4-element (16-byte) core matrices; element (row, k) lives at byte
+//     (row / 8) * kSBO + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4,
 // i.e. core matrices adjacent in K are 128 bytes apart (leading-dimension
-// offset) and 8-row groups are 1024 bytes apart (stride-dimension offset).
+// offset) and 8-row groups are kSBO bytes apart (stride-dimension offset).
 // One MMA consumes K = 8 (two core matrices along K).
 #pragma once
 
@@ -18,16 +18,17 @@
 namespace umma {
 
 constexpr int kRows = 128;                  // M (and N) of one tile
-constexpr int kChunk = 32;                  // K elements staged per chunk
-constexpr int kChunkBytes = kRows * kChunk * 4;  // 16 KB per operand chunk
-constexpr uint32_t kLBO = 128, kSBO = 1024;
+constexpr int kChunk = 16;                  // K elements staged per chunk
+constexpr int kChunkBytes = kRows * kChunk * 4;  // 8 KB per operand chunk
+constexpr uint32_t kLBO = 128;                   // next core matrix along K
+constexpr uint32_t kSBO = kChunk / 4 * 128;      // next 8-row group
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 __device__ __forceinline__ uint32_t chunk_offset(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)((row >> 3) * kSBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
