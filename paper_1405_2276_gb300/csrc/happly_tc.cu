@@ -138,14 +138,16 @@ __device__ __forceinline__ void issue_chunk(uint8_t* st, uint32_t tmem, bool fir
 }
 
 // Main loop over the chunks of a tile.  src.first(r) / src.next(r) load the
-// next chunk into registers (returning false when there is none), so the
-// global loads of chunk c+1 are in flight while chunk c is stored, fenced
-// and handed to the tensor core.  Returns the number of chunks issued; a
-// wait that expires sets *s.fail and ends the loop.
+// next chunk into registers (returning false when there is none).  Two
+// register sets are in flight: while chunk c is stored, fenced and handed to
+// the tensor core, the global loads of chunks c+1 and c+2 are outstanding.
+// Returns the number of chunks issued; a wait that expires sets *s.fail and
+// ends the loop.
 template <typename Src>
 __device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src) {
-  Regs r;
+  Regs r, rn;
   bool have = src.first(r);
+  bool have_n = have ? src.next(rn) : false;
   int c = 0;
   while (have) {
     const int st = c & 1;
@@ -157,7 +159,9 @@ __device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src
     src.store(s.stage[st], r);
     umma::fence_proxy_async();
     __syncthreads();
-    have = src.next(r);
+    r = rn;
+    have = have_n;
+    if (have_n) have_n = src.next(rn);
     if (threadIdx.x == 0) {
       umma::fence_after_sync();
       issue_chunk(s.stage[st], tmem, c == 0);
@@ -315,8 +319,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const Smem s = smem_layout(smem_raw);
-  const TcTile tl = tiles[blockIdx.x];
-  const int n0 = blockIdx.y * 128;
+  // x = column tile (fastest): the column tiles of one row tile run together
+  // and share the tile's operator rows through L2
+  const TcTile tl = tiles[blockIdx.y];
+  const int n0 = blockIdx.x * 128;
   const int nv = min(128, ncols - n0);
   if (nv <= 0) return;
   tile_begin(s);
@@ -409,7 +415,7 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
           h->tcred.as<P1Reduce>(), h->part.as<float>(), h->slotmap.as<int64_t>(), h->zmix.as<float>(), P, nc);
       FKF_LAUNCHED(ctx);
     }
-    k_phase2_tc<<<dim3((unsigned)h->n_tctile, ntile), kThreads, kSmemBytes, ctx->stream>>>(
+    k_phase2_tc<<<dim3(ntile, (unsigned)h->n_tctile), kThreads, kSmemBytes, ctx->stream>>>(
         h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->fac.as<float>(), h->nearv.as<float>(), h->zmix.as<float>(),
         P, X + c0, ldx, Y + c0, ldy, nc, h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
