@@ -1,16 +1,21 @@
 // H-apply on the 5th-generation tensor cores (FP32 operators): both phases of
 // the two-phase apply run as 128 x 128 tiles of tcgen05.mma kind::tf32 with
 // the accumulator in TMEM.  Each FP32 operand value x is split into
-// hi = tf32(x) and lo = tf32(x - hi) while it is staged into shared memory, and
-// every product is accumulated as hi*hi + hi*lo + lo*hi (3xTF32, FP32
-// accumulation), which keeps FP32-level accuracy.
+// hi = tf32(x) and lo = tf32(x - hi) while it is staged, and every product is
+// accumulated as hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation), which
+// keeps FP32-level accuracy.
 //
-// Staging: 256 threads load a K-chunk of 32 for A (128 rows) and B (128
-// columns) with coalesced global loads, split, and write both halves in the
-// canonical K-major no-swizzle core-matrix layout (umma.cuh); two stages
-// alternate, so the loads of chunk c+1 overlap the MMAs of chunk c, which one
-// thread issues and commits to the stage's mbarrier.  The epilogue reads TMEM
-// with tcgen05.ld (warp w reads lanes 32*(w%4).., columns 64*(w/4)..).
+// Pipeline per CTA (256 threads, two CTAs per SM):
+//   raw stages (3): cp.async copies FP32 chunks (K = 16) of A and B from
+//                   global memory, two chunks ahead of the one being split;
+//   split stages (2): every thread splits its part of the landed raw chunk
+//                   into hi/lo TF32 halves in the canonical K-major no-swizzle
+//                   core-matrix layout (umma.cuh);
+//   one thread issues the chunk's 6 MMAs (2 K-steps x 3 products) and commits
+//   them to the split stage's mbarrier, which guards that stage's reuse.
+// The epilogue reads TMEM with tcgen05.ld (warp w: lanes 32*(w%4).., columns
+// 64*(w/4)..).  Every mbarrier wait is bounded; an expired wait sets an error
+// flag, the tile drains what it issued, frees its TMEM and returns.
 //
 // Phase 2 tiles are 128 consecutive rows (whole leaves packed together); the
 // segments of the packed leaves are merged where they read the same slot rows
@@ -25,39 +30,102 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kStages = 2;
-constexpr int kStageBytes = 4 * umma::kChunkBytes;  // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // 65 KB: two CTAs per SM
+constexpr int kConv = 2;                                 // split (hi/lo) stages
+constexpr int kRaw = 3;                                  // raw FP32 stages
+constexpr int kConvBytes = 4 * umma::kChunkBytes;        // A_hi, A_lo, B_hi, B_lo (32 KB)
+constexpr int kRawBytes = 2 * umma::kChunkBytes;         // A, B fp32 (16 KB)
+constexpr int kSmemBytes = kConv * kConvBytes + kRaw * kRawBytes + 256;  // 112.25 KB: two CTAs per SM
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kMaxPolls = 1u << 22;  // bounded mbarrier waits (error flag on expiry)
 constexpr uint32_t kIdesc = umma::idesc_tf32(128, 128);
 
+// Stage addresses are computed, not stored in arrays (a dynamically indexed
+// pointer array would live in local memory).
 struct Smem {
-  uint8_t* stage[kStages];
-  uint64_t* mbar;      // [kStages]
+  uint8_t* base;
+  uint64_t* mbar;  // [kConv]
   uint32_t* tmem_slot;
   int* fail;
+  __device__ __forceinline__ uint8_t* conv(int i) const { return base + i * kConvBytes; }
+  __device__ __forceinline__ uint8_t* raw(int i) const { return base + kConv * kConvBytes + i * kRawBytes; }
 };
 
 __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   Smem s;
-  for (int i = 0; i < kStages; i++) s.stage[i] = base + i * kStageBytes;
-  uint8_t* tail = base + kStages * kStageBytes;
+  s.base = base;
+  uint8_t* tail = base + kConv * kConvBytes + kRaw * kRawBytes;
   s.mbar = reinterpret_cast<uint64_t*>(tail);
   s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 64);
   s.fail = reinterpret_cast<int*>(tail + 128);
   return s;
 }
 
-// Staging registers: threads 0..127 hold one operand-A row (16 k values);
-// threads 128..255 hold a 4 x 4 block of operand B (4 columns x 4 k), or
-// for m-contiguous A both halves hold 4 x 4 blocks.  All global loads are
-// 128-bit where alignment allows.
-struct Regs {
-  float v[16];
-};
+// ---- asynchronous global -> shared copies ---------------------------------
+// 16-byte copy of `bytes` (0..16) valid bytes; the rest of the 16 is zero-filled.
+__device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+// 4-byte copy, for sources not 16-byte aligned
+__device__ __forceinline__ void cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Split 4 consecutive-k values of `row` at k (k % 4 == 0) and store both halves.
+// A quad (4 floats) of `valid` leading elements from src into dst (16 bytes);
+// src is read only where valid, the missing elements are stored as zeros.
+__device__ __forceinline__ void copy_quad(void* dst, const float* src, int valid, bool vec) {
+  if (valid <= 0) {
+    *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if (vec) {
+    cp16(dst, src, 4 * min(valid, 4));
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      float* d = reinterpret_cast<float*>(dst) + u;
+      if (u < valid)
+        cp4(d, src + u);
+      else
+        *d = 0.f;
+    }
+  }
+}
+
+// Raw A in "rows" form: 128 rows x 16 floats, quad q of row r at byte
+// r * 64 + ((q ^ ((r >> 1) & 3)) * 16) (conflict-free 16-byte reads by row).
+__device__ __forceinline__ uint32_t raw_row_off(int r, int q) { return (uint32_t)(r * 64 + ((q ^ ((r >> 1) & 3)) * 16)); }
+
+// Raw operand in "k-rows" form: 16 rows (k) x 128 floats, quad q of row k at k * 512 + q * 16.
+__device__ __forceinline__ uint32_t raw_krow_off(int k, int q) { return (uint32_t)(k * 512 + q * 16); }
+
+// Issue the copies of A rows: A(m, k) = A[(m - lo) * lda + k0 + k], m in [lo, hi), k < kv.
+__device__ __forceinline__ void issue_a_rows(uint8_t* raw, const float* A, int64_t lda, int lo, int hi, int k0,
+                                             int kv, bool vec) {
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = threadIdx.x + j * kThreads;
+    const int r = i >> 2, q = i & 3;
+    const bool rv = r >= lo && r < hi;
+    const int valid = rv ? kv - (k0 + 4 * q) : 0;
+    copy_quad(raw + raw_row_off(r, q), A + (int64_t)(rv ? r - lo : 0) * lda + k0 + 4 * q, valid, vec);
+  }
+}
+
+// Issue the copies of a k-rows operand: P(k, c) = P[(k0 + k) * ld + c], k < kv, c < cv.
+__device__ __forceinline__ void issue_krows(uint8_t* raw, const float* P, int64_t ld, int cv, int k0, int kv,
+                                            bool vec) {
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = threadIdx.x + j * kThreads;
+    const int k = i >> 5, q = i & 31;
+    const bool kvld = k0 + k < kv;
+    const int valid = kvld ? cv - 4 * q : 0;
+    copy_quad(raw + raw_krow_off(k, q), P + (int64_t)(kvld ? k0 + k : 0) * ld + 4 * q, valid, vec);
+  }
+}
+
+// ---- split into the tensor-core layout ---------------------------------------
 __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
                                      float v3) {
   uint4 h, l;
@@ -70,62 +138,27 @@ __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-// One operand row (row = tl, 0..127), 16 consecutive k from A[(row - lo) * lda + k0 ..]
-__device__ __forceinline__ void load_row16(float* v, int tl, const float* __restrict__ A, int64_t lda, int lo, int hi,
-                                           int k0, int kv, bool vec) {
-  const bool rv = tl >= lo && tl < hi;
-  const float* row = A + (int64_t)(tl - lo) * lda + k0;
+// row r (= tl) of a raw rows-form operand -> (row, k = 0..15)
+__device__ __forceinline__ void split_row(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int r) {
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    if (rv && vec && k0 + 4 * j + 3 < kv) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(row + 4 * j));
-      v[4 * j] = q.x;
-      v[4 * j + 1] = q.y;
-      v[4 * j + 2] = q.z;
-      v[4 * j + 3] = q.w;
-    } else {
-#pragma unroll
-      for (int u = 0; u < 4; u++) v[4 * j + u] = (rv && k0 + 4 * j + u < kv) ? __ldg(row + 4 * j + u) : 0.f;
-    }
+  for (int q = 0; q < 4; q++) {
+    const float4 v = *reinterpret_cast<const float4*>(raw + raw_row_off(r, q));
+    put4(hi, lo, r, 4 * q, v.x, v.y, v.z, v.w);
   }
 }
 
-__device__ __forceinline__ void put_row16(uint8_t* hi, uint8_t* lo, int tl, const float* v) {
+// column c (= tl) of a raw k-rows operand -> (row = c, k = 0..15); a warp reads
+// 32 consecutive floats per k and writes 8 distinct rows per quarter-warp
+// (both free of bank conflicts)
+__device__ __forceinline__ void split_col(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int c) {
+  const float* r = reinterpret_cast<const float*>(raw) + c;
 #pragma unroll
-  for (int j = 0; j < 4; j++) put4(hi, lo, tl, 4 * j, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  for (int q = 0; q < 4; q++)
+    put4(hi, lo, c, 4 * q, r[(4 * q + 0) * 128], r[(4 * q + 1) * 128], r[(4 * q + 2) * 128], r[(4 * q + 3) * 128]);
 }
 
-// 4 x 4 block of an operand stored k-rows x contiguous columns: P(k, c) =
-// P[(k0 + k) * ld + c] for columns c = 4 (tl % 32) .. +3 (< cv) and
-// k = 4 (tl / 32) .. +3 (< kv); v[4 j + i] = P(k = 4 (tl / 32) + j, c = 4 (tl % 32) + i).
-__device__ __forceinline__ void load_blk(float* v, int tl, const float* __restrict__ P, int64_t ld, int cv, int k0,
-                                         int kv, bool vec) {
-  const int c = 4 * (tl & 31), kq = tl >> 5;
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int k = k0 + 4 * kq + j;
-    const float* row = P + (int64_t)k * ld + c;
-    if (k < kv && vec && c + 3 < cv) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(row));
-      v[4 * j] = q.x;
-      v[4 * j + 1] = q.y;
-      v[4 * j + 2] = q.z;
-      v[4 * j + 3] = q.w;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; i++) v[4 * j + i] = (k < kv && c + i < cv) ? __ldg(row + i) : 0.f;
-    }
-  }
-}
-
-__device__ __forceinline__ void put_blk(uint8_t* hi, uint8_t* lo, int tl, const float* v) {
-  const int c = 4 * (tl & 31), kq = tl >> 5;
-#pragma unroll
-  for (int i = 0; i < 4; i++) put4(hi, lo, c + i, 4 * kq, v[i], v[4 + i], v[8 + i], v[12 + i]);
-}
-
-// Issue the 3xTF32 MMAs of one staged chunk (one thread).
-__device__ __forceinline__ void issue_chunk(uint8_t* st, uint32_t tmem, bool first) {
+// Issue the 3xTF32 MMAs of one split chunk (one thread).
+__device__ __forceinline__ void issue_mma(uint8_t* st, uint32_t tmem, bool first) {
   const uint32_t a_hi = umma::smem_u32(st), a_lo = a_hi + umma::kChunkBytes;
   const uint32_t b_hi = a_hi + 2 * umma::kChunkBytes, b_lo = a_hi + 3 * umma::kChunkBytes;
 #pragma unroll
@@ -137,45 +170,47 @@ __device__ __forceinline__ void issue_chunk(uint8_t* st, uint32_t tmem, bool fir
   }
 }
 
-// Main loop over the chunks of a tile.  src.first(r) / src.next(r) load the
-// next chunk into registers (returning false when there is none).  Two
-// register sets are in flight: while chunk c is stored, fenced and handed to
-// the tensor core, the global loads of chunks c+1 and c+2 are outstanding.
-// Returns the number of chunks issued; a wait that expires sets *s.fail and
-// ends the loop.
+// Main loop.  src.issue(raw) issues the copies of the next chunk (uniform
+// across the CTA; false when there is none); src.split(raw, conv) splits a
+// landed chunk.  Returns the number of chunks handed to the tensor core.
 template <typename Src>
 __device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src) {
-  Regs r, rn;
-  bool have = src.first(r);
-  bool have_n = have ? src.next(rn) : false;
+  int issued = 0;
+#pragma unroll
+  for (int i = 0; i < kRaw - 1; i++) {
+    if (src.issue(s.raw(i))) issued++;
+    cp_commit();
+  }
   int c = 0;
-  while (have) {
-    const int st = c & 1;
-    if (c >= kStages) {
-      if (!umma::mbar_wait(&s.mbar[st], ((c - kStages) >> 1) & 1, kMaxPolls)) atomicExch(s.fail, 1);
+  while (c < issued) {
+    const int cs = c % kConv;
+    if (c >= kConv) {
+      if (!umma::mbar_wait(&s.mbar[cs], ((c - kConv) / kConv) & 1, kMaxPolls)) atomicExch(s.fail, 1);
     }
+    cp_wait1();  // this thread's copies of chunk c have landed
     __syncthreads();
     if (*s.fail) break;
-    src.store(s.stage[st], r);
+    // the raw stage of chunk c-1 is free (split in the previous iteration)
+    if (src.issue(s.raw((c + kRaw - 1) % kRaw))) issued++;
+    cp_commit();
+    src.split(s.raw(c % kRaw), s.conv(cs));
     umma::fence_proxy_async();
     __syncthreads();
-    r = rn;
-    have = have_n;
-    if (have_n) have_n = src.next(rn);
     if (threadIdx.x == 0) {
       umma::fence_after_sync();
-      issue_chunk(s.stage[st], tmem, c == 0);
-      umma::commit(&s.mbar[st]);
+      issue_mma(s.conv(cs), tmem, c == 0);
+      umma::commit(&s.mbar[cs]);
     }
     c++;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   return c;
 }
 
 __device__ __forceinline__ void tile_begin(const Smem& s) {
   if (threadIdx.x < 32) umma::tmem_alloc(s.tmem_slot, kTmemCols);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; i++) umma::mbar_init(&s.mbar[i], 1);
+    for (int i = 0; i < kConv; i++) umma::mbar_init(&s.mbar[i], 1);
     *s.fail = 0;
     umma::fence_mbar_init();
   }
@@ -189,7 +224,7 @@ __device__ __forceinline__ bool tile_drain(const Smem& s, int nchunks) {
   bool ok = true;
   if (nchunks > 0) {
     const int c = nchunks - 1;
-    ok = umma::mbar_wait(&s.mbar[c & 1], (c >> 1) & 1, kMaxPolls);
+    ok = umma::mbar_wait(&s.mbar[c % kConv], (c / kConv) & 1, kMaxPolls);
     if (!ok) atomicExch(s.fail, 1);
   }
   __syncthreads();
@@ -229,8 +264,8 @@ __device__ __forceinline__ void tile_store(uint32_t tmem, int rows, int nv, bool
 }
 
 // Chunk source for phase 2: the tile's segments, K-chunks of kChunk each.
-// Threads 0..127 stage A rows (factor or near-field rows, k-contiguous);
-// threads 128..255 stage B (slot rows of Zmix or rows of X) in 4 x 4 blocks.
+// A = factor / near-field rows (k-contiguous, rows form); B = slot rows of
+// Zmix or rows of X (k-rows form).
 struct P2Src {
   const TcSeg* segs;
   int seg0, nseg;
@@ -239,76 +274,59 @@ struct P2Src {
   int n0, nv;
   bool bvec_z, bvec_x;
   int si = 0, k0 = 0;
-  __device__ bool load(Regs& r) {
+  bool started = false;
+  __device__ bool issue(uint8_t* raw) {
+    if (!started) {
+      started = true;
+      si = 0;
+      k0 = 0;
+    } else {
+      k0 += umma::kChunk;
+      if (si < nseg && k0 >= segs[seg0 + si].K) {
+        k0 = 0;
+        si++;
+      }
+    }
+    while (si < nseg && segs[seg0 + si].K <= 0) si++;
     if (si >= nseg) return false;
     const TcSeg sg = segs[seg0 + si];
-    const int t = threadIdx.x;
-    if (t < 128) {
-      const float* A = (sg.near ? nearv : fac) + sg.a_off;
-      const bool vec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
-      load_row16(r.v, t, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, vec);
-    } else {
-      const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
-      load_blk(r.v, t - 128, B, sg.near ? ldx : ldz, nv, k0, sg.K, sg.near ? bvec_x : bvec_z);
-    }
+    const float* A = (sg.near ? nearv : fac) + sg.a_off;
+    const bool avec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
+    issue_a_rows(raw, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, avec);
+    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
+    issue_krows(raw + umma::kChunkBytes, B, sg.near ? ldx : ldz, nv, k0, sg.K, sg.near ? bvec_x : bvec_z);
     return true;
   }
-  __device__ void store(uint8_t* st, const Regs& r) const {
+  __device__ void split(const uint8_t* raw, uint8_t* conv) const {
     const int t = threadIdx.x;
     if (t < 128)
-      put_row16(st, st + umma::kChunkBytes, t, r.v);
+      split_row(raw, conv, conv + umma::kChunkBytes, t);
     else
-      put_blk(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, t - 128, r.v);
-  }
-  __device__ bool first(Regs& r) {
-    si = 0;
-    k0 = 0;
-    while (si < nseg && segs[seg0 + si].K <= 0) si++;
-    return load(r);
-  }
-  __device__ bool next(Regs& r) {
-    k0 += umma::kChunk;
-    if (k0 >= segs[seg0 + si].K) {
-      k0 = 0;
-      si++;
-      while (si < nseg && segs[seg0 + si].K <= 0) si++;
-    }
-    return load(r);
+      split_col(raw + umma::kChunkBytes, conv + 2 * umma::kChunkBytes, conv + 3 * umma::kChunkBytes, t - 128);
   }
 };
 
 // Chunk source for phase 1: rows of one cluster chunk, K-chunks of kChunk.
-// A(m = slot, k = row) is slot-contiguous, B(k = row, n) column-contiguous:
-// both are staged as 4 x 4 blocks (threads 0..127: A, 128..255: B).
+// A(m = slot, k = row) and B(k = row, n) are both in k-rows form.
 struct P1Src {
   const float *A, *B;
   int64_t lda, ldb;
   int mv, kv, nv;
   bool avec, bvec;
-  int k0 = 0;
-  __device__ bool load(Regs& r) {
+  int k0 = -umma::kChunk;
+  __device__ bool issue(uint8_t* raw) {
+    k0 += umma::kChunk;
     if (k0 >= kv) return false;
-    const int t = threadIdx.x;
-    if (t < 128)
-      load_blk(r.v, t, A, lda, mv, k0, kv, avec);
-    else
-      load_blk(r.v, t - 128, B, ldb, nv, k0, kv, bvec);
+    issue_krows(raw, A, lda, mv, k0, kv, avec);
+    issue_krows(raw + umma::kChunkBytes, B, ldb, nv, k0, kv, bvec);
     return true;
   }
-  __device__ void store(uint8_t* st, const Regs& r) const {
+  __device__ void split(const uint8_t* raw, uint8_t* conv) const {
     const int t = threadIdx.x;
     if (t < 128)
-      put_blk(st, st + umma::kChunkBytes, t, r.v);
+      split_col(raw, conv, conv + umma::kChunkBytes, t);
     else
-      put_blk(st + 2 * umma::kChunkBytes, st + 3 * umma::kChunkBytes, t - 128, r.v);
-  }
-  __device__ bool first(Regs& r) {
-    k0 = 0;
-    return load(r);
-  }
-  __device__ bool next(Regs& r) {
-    k0 += umma::kChunk;
-    return load(r);
+      split_col(raw + umma::kChunkBytes, conv + 2 * umma::kChunkBytes, conv + 3 * umma::kChunkBytes, t - 128);
   }
 };
 
