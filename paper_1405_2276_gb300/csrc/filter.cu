@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "common.h"
 #include "dense.h"
@@ -126,21 +127,100 @@ __global__ void k_csc_sort(int64_t n, const int64_t* __restrict__ colptr, int* _
 }
 
 // out (m x ncols, FP64) = H * src[:, 0:ncols]  (src rows in cluster order)
-template <typename T>
-__global__ void k_csr_gather(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
-                             const T* __restrict__ src, int64_t lds, int ncols, double* __restrict__ out,
-                             int64_t ldo) {
+// out[j, c] = sum_p val[p] * src[iperm[col[p]], c] for the rows j of a CSR
+// matrix (c < ncols).  One CTA per (row, column block); the row's (index,
+// value) pairs are staged in shared memory in chunks, and each thread keeps V
+// consecutive columns (one 16-byte load per nonzero when V > 1).  The loads of
+// four nonzeros are issued before their products, which are summed in p order.
+constexpr int kGatherThreads = 256;
+constexpr int kGatherChunk = 1024;
+
+template <typename T, int V>
+__device__ __forceinline__ void load_cols(const T* p, T (&o)[V]) {
+  if constexpr (V == 1) {
+    o[0] = *p;
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    o[0] = x.x, o[1] = x.y, o[2] = x.z, o[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    o[0] = x.x, o[1] = x.y;
+  }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kGatherThreads, 4)
+    k_csr_gather(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                 const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                 const T* __restrict__ src, int64_t lds, int ncols, double* __restrict__ out, int64_t ldo) {
+  __shared__ int s_idx[kGatherChunk];
+  __shared__ T s_val[kGatherChunk];
   const int j = blockIdx.x;
+  const int c0 = (blockIdx.y * kGatherThreads + threadIdx.x) * V;
   const int64_t a = rowptr[j], b = rowptr[j + 1];
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-    T acc = 0;
-    for (int64_t p = a; p < b; p++) {
-      const int64_t cc = col[p];
-      if (cc < 0 || cc >= n) continue;
-      acc += (T)val[p] * src[iperm[cc] * lds + c];
+  T acc[V];
+#pragma unroll
+  for (int u = 0; u < V; u++) acc[u] = 0;
+  const bool full = c0 + V <= ncols;
+  for (int64_t base = a; base < b; base += kGatherChunk) {
+    const int cnt = (int)(b - base < kGatherChunk ? b - base : kGatherChunk);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += kGatherThreads) {
+      const int64_t cc = col[base + i];
+      const bool ok = cc >= 0 && cc < n;
+      s_idx[i] = ok ? (int)iperm[cc] : 0;
+      s_val[i] = ok ? (T)val[base + i] : (T)0;
     }
-    out[(int64_t)j * ldo + c] = (double)acc;
+    __syncthreads();
+    if (full) {
+      const T* s0 = src + c0;
+      int i = 0;
+      for (; i + 4 <= cnt; i += 4) {
+        T x[4][V];
+#pragma unroll
+        for (int q = 0; q < 4; q++) load_cols<T, V>(s0 + (int64_t)s_idx[i + q] * lds, x[q]);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const T v = s_val[i + q];
+#pragma unroll
+          for (int u = 0; u < V; u++) acc[u] += v * x[q][u];
+        }
+      }
+      for (; i < cnt; i++) {
+        T x[V];
+        load_cols<T, V>(s0 + (int64_t)s_idx[i] * lds, x);
+        const T v = s_val[i];
+#pragma unroll
+        for (int u = 0; u < V; u++) acc[u] += v * x[u];
+      }
+    } else if (c0 < ncols) {
+      for (int i = 0; i < cnt; i++) {
+        const T* xr = src + (int64_t)s_idx[i] * lds;
+        const T v = s_val[i];
+#pragma unroll
+        for (int u = 0; u < V; u++)
+          if (c0 + u < ncols) acc[u] += v * xr[c0 + u];
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < V; u++)
+    if (c0 + u < ncols) out[(int64_t)j * ldo + c0 + u] = (double)acc[u];
+}
+
+// Launch of k_csr_gather: 16-byte column vectors when src and lds allow them.
+template <typename T>
+static void csr_gather(int m, const int64_t* rowptr, const int32_t* col, const double* val, const int64_t* iperm,
+                       int64_t n, const T* src, int64_t lds, int ncols, double* out, int64_t ldo, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(T);
+  if (m <= 0 || ncols <= 0) return;
+  const bool vec = (reinterpret_cast<uintptr_t>(src) % 16 == 0) && (lds % V == 0);
+  if (vec) {
+    const dim3 grid((unsigned)m, (unsigned)cdiv(ncols, kGatherThreads * V));
+    k_csr_gather<T, V><<<grid, kGatherThreads, 0, st>>>(rowptr, col, val, iperm, n, src, lds, ncols, out, ldo);
+  } else {
+    const dim3 grid((unsigned)m, (unsigned)cdiv(ncols, kGatherThreads));
+    k_csr_gather<T, 1><<<grid, kGatherThreads, 0, st>>>(rowptr, col, val, iperm, n, src, lds, ncols, out, ldo);
   }
 }
 
@@ -332,17 +412,17 @@ __global__ void k_frob_scaled(int m, const double* __restrict__ A, const double*
   }
 }
 
-// out[i, j] = rs[i] * A[i*lda + j]  (m x r)
-__global__ void k_scale_rows(int m, int r, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
-                             double* __restrict__ out) {
+// E = diag(alpha1 - d) (r x r)
+// K^T = (alpha' HW - HW D)^T = (HW E)^T, r x m (HW: m x r, ld ldh; HWD: m x r, ld r)
+__global__ void k_hwe_t(int m, int r, const double* __restrict__ HW, int64_t ldh, const double* __restrict__ HWD,
+                        double alpha1, double* __restrict__ Kt) {
   const int64_t total = (int64_t)m * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / r), j = (int)(e % r);
-    out[e] = rs[i] * A[(int64_t)i * lda + j];
+    const int i = (int)(e / m), j = (int)(e % m);
+    Kt[e] = alpha1 * HW[(int64_t)j * ldh + i] - HWD[(int64_t)j * r + i];
   }
 }
 
-// E = diag(alpha1 - d) (r x r)
 __global__ void k_diag_from(int r, const double* __restrict__ d, double alpha1, double* __restrict__ E) {
   const int64_t total = (int64_t)r * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -739,7 +819,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   // ---- gathers: [HW | A] = H [W G]; innovation
   const int nm = r + m;
   double* HWA = f->HWA.as<double>();
-  k_csr_gather<T><<<m, 256, 0, st>>>(rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm);
+  csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm, st);
   FKF_LAUNCHED(ctx);
   k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->s_hat.as<double>(),
                                                                f->y.as<double>(), f->nu.as<double>());
@@ -811,9 +891,15 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated
     // in information form, E' = (E^-1 + Q)^-1, E = alpha' I - D (predicted),
     // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight)
+    // Evaluated in the Woodbury form E' = E - K^T S^-1 K, K = HW E, with the
+    // innovation covariance S = alpha' A - HW D HW^T + R already factored for
+    // the mean (S = HW E HW^T + R up to the new_tol residual A - HW HW^T), and
+    // HW D already formed for S: one m x m solve with r right-hand sides and
+    // one r x r x m product, no r x r factorisation.
     double* Ep = f->Ep.as<double>();
     double* Dn2 = f->Dfn.as<double>();
-    double* Qm = f->Qm.as<double>();
+    double* Kt = f->P.as<double>();  // r x m: K^T
+    double* Yt = f->J.as<double>();  // r x m: (S^-1 K)^T
     const int64_t rr = (int64_t)r * r;
     if (diag) {
       k_diag_from<<<nblk(rr), 256, 0, st>>>(r, f->D.as<double>(), alpha1, Ep);
@@ -821,21 +907,11 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Dfc, 0.0, nullptr, alpha1, Ep);
     }
     FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_f64(ctx, r, Ep, f->cholws));
-    k_identity<<<nblk(rr), 256, 0, st>>>(r, Dn2, r);
+    k_hwe_t<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), alpha1, Kt);
     FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_solve_f64(ctx, r, Ep, Dn2, r));  // E^-1
-    k_scale_rows<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->rs.as<double>(), f->HWD.as<double>());
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(gemm_f64(ctx, true, false, r, r, m, 1.0, f->HWD.as<double>(), r, f->HWD.as<double>(), r, 0.0, Qm, r));
-    k_lincomb<<<nblk(rr), 256, 0, st>>>(r, 1.0, Dn2, 1.0, Qm, 0.0, Dn2);  // E^-1 + Q
-    FKF_LAUNCHED(ctx);
-    k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Dn2);
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_f64(ctx, r, Dn2, f->cholws));
-    k_identity<<<nblk(rr), 256, 0, st>>>(r, Ep, r);
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_solve_f64(ctx, r, Dn2, Ep, r));  // E' = (E^-1 + Q)^-1
+    FKF_CUDA(ctx, cudaMemcpyAsync(Yt, Kt, (size_t)m * r * 8, cudaMemcpyDeviceToDevice, st));
+    FKF_TRY(chol_solve_f64(ctx, m, S, Yt, r));
+    FKF_TRY(gemm_f64(ctx, false, true, r, r, m, -1.0, Kt, m, Yt, m, 1.0, Ep, r));
     k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Ep);
     FKF_LAUNCHED(ctx);
     k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Ep, 0.0, nullptr, alpha1, Dn2);  // D' = alpha' I - E'
@@ -1513,8 +1589,8 @@ static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, 
   DevBuf A, Araw;
   FKF_TRY(dev_alloc(ctx, Araw, mm * 8));
   FKF_TRY(dev_alloc(ctx, A, mm * 8));
-  k_csr_gather<T><<<m, 256, 0, st>>>(rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm, n, G.as<T>(), m,
-                                     m, Araw.as<double>(), m);
+  csr_gather<T>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm, n, G.as<T>(), m, m,
+                Araw.as<double>(), m, st);
   FKF_LAUNCHED(ctx);
   FKF_CUDA(ctx, cudaMemcpyAsync(A.p, Araw.p, mm * 8, cudaMemcpyDeviceToDevice, st));
   k_symmetrize<<<nblk(mm), 256, 0, st>>>(m, A.as<double>());
