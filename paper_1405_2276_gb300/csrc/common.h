@@ -89,7 +89,8 @@ struct P1Item {
   int32_t K;         // K_c (row stride of Fac_c)
   int32_t r0, nr;    // row range inside the cluster
   int32_t q0, nq;    // slot range
-  int32_t pad;
+  int32_t nchunk;    // tensor-core engine: K-chunks of 16 rows
+  int64_t a_chunk0;  // tensor-core engine: first chunk of the item's split operator stream
 };
 
 // Phase-1b reduction item: sum `nch` partials of nq slots x panel, scatter.
@@ -131,9 +132,20 @@ struct TcSeg {
 
 struct TcTile {
   int64_t row0;
+  int64_t a_chunk0;  // first chunk of the tile's split operator stream
   int32_t rows;
   int32_t seg0, nseg;
-  int32_t pad;
+  int32_t nchunk;    // K-chunks of 16 over all segments
+};
+
+// One 128 x 16 chunk of a split operator stream: element (i, k) is
+// src[src_off + (i - row_lo) * si + k * sk] for row_lo <= i < row_hi and
+// k < kv, zero elsewhere (src = the far factors, or the near blocks if near).
+struct TcAChunk {
+  int64_t src_off;
+  int32_t si, sk;
+  int32_t row_lo, row_hi;
+  int32_t kv, near;
 };
 
 struct HostHmat;  // host-side build result (hbuild.cpp)
@@ -156,7 +168,9 @@ struct fkf_hmat {
   int32_t max_leaf = 0;
   // tensor-core schedules (FP32 operators)
   DevBuf tcp1, tcred, tctile, tcseg, tc_err;
-  int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0;
+  std::vector<TcSeg> tcseg_host;  // phase-2 segments (host copy, for the stream builder)
+  DevBuf tca;  // split operator streams: 16 KB per chunk (TF32 hi | lo, tensor-core smem layout)
+  int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0;
   int engine = 0;  // 0: SIMT tile engine, 1: tensor cores (tcgen05, FP32 operators only)
   // workspace
   DevBuf zmix, part, xperm, yperm;
@@ -179,6 +193,10 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
 fkf_status hmat_tc_check(fkf_hmat* h);
 void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector<P2Seg>& segs,
                             std::vector<TcTile>& tiles, std::vector<TcSeg>& tsegs);
+// Split operator streams for the tensor-core engine (after fac/nearv are on
+// the device): numbers the chunks of every phase-1 item and phase-2 tile,
+// writes them to h->tca, uploads the work lists.
+fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::vector<TcTile>& tiles);
 
 // hbuild.cpp
 fkf_status hmat_build_host(fkf_ctx* ctx, const double* pts, int64_t n, int dim, fkf_matern k, fkf_hparams hp,

@@ -364,8 +364,9 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   }
   // tensor-core schedules (FP32 operators): phase-1 slot tiles of 128, phase-2
   // tiles of 128 consecutive rows with merged segments
+  std::vector<P1Item> tp1;
+  std::vector<TcTile> tiles;
   if (h->prec == FKF_FP32) {
-    std::vector<P1Item> tp1;
     std::vector<P1Reduce> tp1r;
     int64_t tparts = 0;
     for (int c = 0; c < nc; c++) {
@@ -394,13 +395,11 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
         }
       }
     }
-    std::vector<TcTile> tiles;
     std::vector<TcSeg> tsegs;
     hmat_build_tc_schedule(p2, segs, tiles, tsegs);
-    if (!tp1.empty()) FKF_TRY(dev_upload(ctx, h->tcp1, tp1.data(), tp1.size() * sizeof(P1Item)));
     if (!tp1r.empty()) FKF_TRY(dev_upload(ctx, h->tcred, tp1r.data(), tp1r.size() * sizeof(P1Reduce)));
-    FKF_TRY(dev_upload(ctx, h->tctile, tiles.data(), tiles.size() * sizeof(TcTile)));
     FKF_TRY(dev_upload(ctx, h->tcseg, tsegs.data(), std::max<size_t>(tsegs.size(), 1) * sizeof(TcSeg)));
+    h->tcseg_host = std::move(tsegs);
     h->n_tcp1 = (int64_t)tp1.size();
     h->n_tcred = (int64_t)tp1r.size();
     h->n_tctile = (int64_t)tiles.size();
@@ -420,6 +419,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   FKF_TRY(upload_vals(h->fac, facv));
   FKF_TRY(upload_vals(h->nearv, nearv));
   std::vector<char>().swap(tmp);
+  if (h->prec == FKF_FP32) FKF_TRY(hmat_build_tc_streams(h, tp1, tiles));
   FKF_TRY(dev_upload(ctx, h->slotmap, smap.data(), smap.size() * sizeof(int64_t)));
   if (!p1.empty()) FKF_TRY(dev_upload(ctx, h->p1items, p1.data(), p1.size() * sizeof(P1Item)));
   if (!p1r.empty()) FKF_TRY(dev_upload(ctx, h->p1red, p1r.data(), p1r.size() * sizeof(P1Reduce)));
@@ -456,7 +456,8 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   in.bytes_per_col = 2 * hh.n * (int64_t)w;
   in.operator_bytes = (fe + in.near_entries) * (int64_t)w;
   in.device_bytes = (int64_t)(h->fac.bytes + h->nearv.bytes + h->slotmap.bytes + h->p1items.bytes +
-                              h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes);
+                              h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes + h->tca.bytes + h->tcp1.bytes +
+                              h->tctile.bytes + h->tcseg.bytes + h->tcred.bytes);
   in.build_seconds = hh.build_seconds;
   return FKF_OK;
 }

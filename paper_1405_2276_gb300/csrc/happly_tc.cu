@@ -1,26 +1,31 @@
-// H-apply on the 5th-generation tensor cores (FP32 operators): both phases of
-// the two-phase apply run as 128 x 128 tiles of tcgen05.mma kind::tf32 with
-// the accumulator in TMEM.  Each FP32 operand value x is split into
-// hi = tf32(x) and lo = tf32(x - hi) while it is staged, and every product is
-// accumulated as hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation), which
-// keeps FP32-level accuracy.
+// H-apply on the 5th-generation tensor cores (FP32 operators).  Both phases
+// of the two-phase apply run as 128 x 256 output tiles of tcgen05.mma
+// kind::tf32 with FP32 accumulators in TMEM.  Every FP32 value x is split into
+// hi = tf32(x) and lo = tf32(x - hi), and each product is accumulated as
+// hi*hi + hi*lo + lo*hi (3xTF32), which keeps FP32-level accuracy.
 //
-// Pipeline per CTA (256 threads, two CTAs per SM):
-//   raw stages (3): cp.async copies FP32 chunks (K = 16) of A and B from
-//                   global memory, two chunks ahead of the one being split;
-//   split stages (2): every thread splits its part of the landed raw chunk
-//                   into hi/lo TF32 halves in the canonical K-major no-swizzle
-//                   core-matrix layout (umma.cuh);
-//   one thread issues the chunk's 6 MMAs (2 K-steps x 3 products) and commits
-//   them to the split stage's mbarrier, which guards that stage's reuse.
-// The epilogue reads TMEM with tcgen05.ld (warp w: lanes 32*(w%4).., columns
-// 64*(w/4)..).  Every mbarrier wait is bounded; an expired wait sets an error
-// flag, the tile drains what it issued, frees its TMEM and returns.
+// The operator side (A) is split once, when the operator is built: every
+// phase-1 item and every phase-2 tile owns a stream of 16 KB chunks (a
+// 128 x 16 TF32 hi block and its lo block, already in the tensor core's
+// shared-memory layout), so a chunk reaches shared memory with one bulk copy.
+// The vector side (B: rows of X or of the slot workspace) is copied as FP32
+// with cp.async and split in shared memory by four producer warps.
 //
-// Phase 2 tiles are 128 consecutive rows (whole leaves packed together); the
-// segments of the packed leaves are merged where they read the same slot rows
-// with contiguous factor rows (every common ancestor), so those B operands
-// are loaded once per tile instead of once per leaf.
+// One persistent CTA per SM, warp-specialised:
+//   warps 0-3  B producers: cp.async two chunks ahead (three raw stages),
+//              split into two hi/lo stages, arrive on full_b;
+//   warp 4     A producer (one thread): bulk copies into four stages, full_a;
+//   warp 5     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
+//              products), commits to empty_a / empty_b, and to acc_full after
+//              a tile's last chunk; also allocates and frees TMEM;
+//   warps 6-9  epilogue: tcgen05.ld of the finished accumulator, stores,
+//              arrive on acc_empty.
+// Two accumulators (2 x 256 TMEM columns) let the epilogue of one tile run
+// under the MMAs of the next.  Tiles are dealt round-robin over the CTAs, the
+// column tiles of one work item consecutively (they share its A stream
+// through L2).  Every mbarrier wait is bounded: an expired wait sets a flag,
+// every role leaves its loop, the MMA issuer waits (bounded) for its
+// outstanding MMAs, TMEM is freed and the host sees the error flag.
 #include <algorithm>
 #include <cstring>
 
@@ -29,49 +34,86 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kConv = 2;                                 // split (hi/lo) stages
-constexpr int kRaw = 3;                                  // raw FP32 stages
-constexpr int kConvBytes = 4 * umma::kChunkBytes;        // A_hi, A_lo, B_hi, B_lo (32 KB)
-constexpr int kRawBytes = 2 * umma::kChunkBytes;         // A, B fp32 (16 KB)
-constexpr int kSmemBytes = kConv * kConvBytes + kRaw * kRawBytes + 256;  // 112.25 KB: two CTAs per SM
-constexpr uint32_t kTmemCols = 128;
-constexpr uint32_t kMaxPolls = 1u << 22;  // bounded mbarrier waits (error flag on expiry)
-constexpr uint32_t kIdesc = umma::idesc_tf32(128, 128);
+constexpr int kM = 128;                    // tile rows = TMEM lanes
+constexpr int kN = 256;                    // tile columns = MMA N
+constexpr int kK = umma::kChunk;           // 16: K per chunk
+constexpr int kABytes = kM * kK * 4;       // 8 KB: one TF32 half of an A chunk
+constexpr int kAChunkBytes = 2 * kABytes;  // 16 KB: hi | lo
+constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk, or the raw FP32 chunk
+constexpr int kSA = 4;                     // A stages
+constexpr int kSB = 2;                     // split B stages
+constexpr int kR = 3;                      // raw B stages
+constexpr int kSmemBytes = kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes + 256;  // 176.25 KB
+constexpr int kBThreads = 128;             // warps 0-3
+constexpr int kAWarp = 4, kMmaWarp = 5;    // warps 6-9: epilogue
+constexpr int kThreads = 320;
+constexpr uint32_t kTmemCols = 2 * kN;
+constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
 
-// Stage addresses are computed, not stored in arrays (a dynamically indexed
-// pointer array would live in local memory).
+// barrier indices
+constexpr int FA = 0, EA = FA + kSA, FB = EA + kSA, EB = FB + kSB, AF = EB + kSB, AE = AF + 2, FIN = AE + 2,
+              NBAR = FIN + 1;
+static_assert(NBAR * 8 <= 192, "barrier area");
+
 struct Smem {
   uint8_t* base;
-  uint64_t* mbar;  // [kConv]
+  uint64_t* bar;
   uint32_t* tmem_slot;
   int* fail;
-  __device__ __forceinline__ uint8_t* conv(int i) const { return base + i * kConvBytes; }
-  __device__ __forceinline__ uint8_t* raw(int i) const { return base + kConv * kConvBytes + i * kRawBytes; }
+  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kAChunkBytes; }
+  __device__ __forceinline__ uint8_t* bc(int s) const { return base + kSA * kAChunkBytes + s * 2 * kBBytes; }
+  __device__ __forceinline__ uint8_t* braw(int s) const {
+    return base + kSA * kAChunkBytes + kSB * 2 * kBBytes + s * kBBytes;
+  }
+  __device__ __forceinline__ bool failed() const { return *reinterpret_cast<volatile int*>(fail) != 0; }
+  __device__ __forceinline__ void set_fail() const { atomicExch(fail, 1); }
 };
 
 __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   Smem s;
   s.base = base;
-  uint8_t* tail = base + kConv * kConvBytes + kRaw * kRawBytes;
-  s.mbar = reinterpret_cast<uint64_t*>(tail);
-  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 64);
-  s.fail = reinterpret_cast<int*>(tail + 128);
+  uint8_t* tail = base + kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes;
+  s.bar = reinterpret_cast<uint64_t*>(tail);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 192);
+  s.fail = reinterpret_cast<int*>(tail + 224);
   return s;
 }
 
-// ---- asynchronous global -> shared copies ---------------------------------
-// 16-byte copy of `bytes` (0..16) valid bytes; the rest of the 16 is zero-filled.
+__device__ __forceinline__ bool wait_bar(const Smem& s, int i, uint32_t parity) {
+  if (umma::mbar_wait(&s.bar[i], parity, kMaxPolls)) return true;
+  s.set_fail();
+  return false;
+}
+
+// ---- B side: cp.async of FP32 chunks, split in shared memory ----------------
 __device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(bytes)
                : "memory");
 }
-// 4-byte copy, for sources not 16-byte aligned
 __device__ __forceinline__ void cp4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Barrier over the four B-producer warps (named barrier 1) that also ORs a
+// predicate across them, so that all of them take the same exit decision.
+__device__ __forceinline__ bool bar_or_b(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
 
 // A quad (4 floats) of `valid` leading elements from src into dst (16 bytes);
 // src is read only where valid, the missing elements are stored as zeros.
@@ -92,40 +134,20 @@ __device__ __forceinline__ void copy_quad(void* dst, const float* src, int valid
   }
 }
 
-// Raw A in "rows" form: 128 rows x 16 floats, quad q of row r at byte
-// r * 64 + ((q ^ ((r >> 1) & 3)) * 16) (conflict-free 16-byte reads by row).
-__device__ __forceinline__ uint32_t raw_row_off(int r, int q) { return (uint32_t)(r * 64 + ((q ^ ((r >> 1) & 3)) * 16)); }
-
-// Raw operand in "k-rows" form: 16 rows (k) x 128 floats, quad q of row k at k * 512 + q * 16.
-__device__ __forceinline__ uint32_t raw_krow_off(int k, int q) { return (uint32_t)(k * 512 + q * 16); }
-
-// Issue the copies of A rows: A(m, k) = A[(m - lo) * lda + k0 + k], m in [lo, hi), k < kv.
-__device__ __forceinline__ void issue_a_rows(uint8_t* raw, const float* A, int64_t lda, int lo, int hi, int k0,
-                                             int kv, bool vec) {
+// Raw B chunk: 16 rows (k) x 256 floats, quad q of row k at byte k * 1024 + q * 16.
+// Copies of P(k, c) = P[(k0 + k) * ld + c] for k0 + k < kv, c < cv; thread t of 128.
+__device__ __forceinline__ void issue_b(uint8_t* raw, const float* P, int64_t ld, int cv, int k0, int kv, bool vec,
+                                        int t) {
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
-    const int i = threadIdx.x + j * kThreads;
-    const int r = i >> 2, q = i & 3;
-    const bool rv = r >= lo && r < hi;
-    const int valid = rv ? kv - (k0 + 4 * q) : 0;
-    copy_quad(raw + raw_row_off(r, q), A + (int64_t)(rv ? r - lo : 0) * lda + k0 + 4 * q, valid, vec);
-  }
-}
-
-// Issue the copies of a k-rows operand: P(k, c) = P[(k0 + k) * ld + c], k < kv, c < cv.
-__device__ __forceinline__ void issue_krows(uint8_t* raw, const float* P, int64_t ld, int cv, int k0, int kv,
-                                            bool vec) {
-#pragma unroll
-  for (int j = 0; j < 2; j++) {
-    const int i = threadIdx.x + j * kThreads;
-    const int k = i >> 5, q = i & 31;
+  for (int j = 0; j < (kK * kN / 4) / kBThreads; j++) {
+    const int i = t + j * kBThreads;
+    const int k = i / (kN / 4), q = i % (kN / 4);
     const bool kvld = k0 + k < kv;
     const int valid = kvld ? cv - 4 * q : 0;
-    copy_quad(raw + raw_krow_off(k, q), P + (int64_t)(kvld ? k0 + k : 0) * ld + 4 * q, valid, vec);
+    copy_quad(raw + k * (kN * 4) + q * 16, P + (int64_t)(kvld ? k0 + k : 0) * ld + 4 * q, valid, vec);
   }
 }
 
-// ---- split into the tensor-core layout ---------------------------------------
 __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
                                      float v3) {
   uint4 h, l;
@@ -138,256 +160,346 @@ __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-// row r (= tl) of a raw rows-form operand -> (row, k = 0..15)
-__device__ __forceinline__ void split_row(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int r) {
+// Columns t and t + 128 of a raw chunk -> (row = column, k = 0..15) of the
+// split stage.  A warp reads 32 consecutive floats per k and writes 8
+// distinct rows per quarter-warp (no bank conflicts).
+__device__ __forceinline__ void split_b(const uint8_t* raw, uint8_t* conv, int t) {
+  uint8_t* hi = conv;
+  uint8_t* lo = conv + kBBytes;
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const float4 v = *reinterpret_cast<const float4*>(raw + raw_row_off(r, q));
-    put4(hi, lo, r, 4 * q, v.x, v.y, v.z, v.w);
+  for (int h = 0; h < 2; h++) {
+    const int c = t + h * kBThreads;
+    const float* r = reinterpret_cast<const float*>(raw) + c;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      put4(hi, lo, c, 4 * q, r[(4 * q + 0) * kN], r[(4 * q + 1) * kN], r[(4 * q + 2) * kN], r[(4 * q + 3) * kN]);
   }
 }
 
-// column c (= tl) of a raw k-rows operand -> (row = c, k = 0..15); a warp reads
-// 32 consecutive floats per k and writes 8 distinct rows per quarter-warp
-// (both free of bank conflicts)
-__device__ __forceinline__ void split_col(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int c) {
-  const float* r = reinterpret_cast<const float*>(raw) + c;
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-    put4(hi, lo, c, 4 * q, r[(4 * q + 0) * 128], r[(4 * q + 1) * 128], r[(4 * q + 2) * 128], r[(4 * q + 3) * 128]);
-}
+// ---- the two phases' work items -------------------------------------------
+struct BSeg {
+  const float* p;  // first row of the segment's B rows
+  int64_t ld;
+  int K;
+};
 
-// Issue the 3xTF32 MMAs of one split chunk (one thread).
-__device__ __forceinline__ void issue_mma(uint8_t* st, uint32_t tmem, bool first) {
-  const uint32_t a_hi = umma::smem_u32(st), a_lo = a_hi + umma::kChunkBytes;
-  const uint32_t b_hi = a_hi + 2 * umma::kChunkBytes, b_lo = a_hi + 3 * umma::kChunkBytes;
-#pragma unroll
-  for (int kk = 0; kk < umma::kChunk / 8; kk++) {
-    const uint32_t koff = kk * 2 * umma::kLBO;  // two core matrices along K per MMA
-    umma::mma_tf32(tmem, umma::smem_desc(a_hi + koff), umma::smem_desc(b_hi + koff), kIdesc, (first && kk == 0) ? 0u : 1u);
-    umma::mma_tf32(tmem, umma::smem_desc(a_hi + koff), umma::smem_desc(b_lo + koff), kIdesc, 1u);
-    umma::mma_tf32(tmem, umma::smem_desc(a_lo + koff), umma::smem_desc(b_hi + koff), kIdesc, 1u);
+// Phase 2: tiles of 128 consecutive rows; B segments = slot rows of the slot
+// workspace (far) or rows of X (near); output rows of Y.
+struct Ph2 {
+  const TcTile* tiles;
+  const TcSeg* segs;
+  const float* zmix;
+  int64_t ldz;
+  const float* X;
+  int64_t ldx;
+  float* Y;
+  int64_t ldy;
+  __device__ __forceinline__ int nchunk(int64_t w) const { return tiles[w].nchunk; }
+  __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return tiles[w].a_chunk0; }
+  __device__ __forceinline__ int nseg(int64_t w) const { return tiles[w].nseg; }
+  __device__ __forceinline__ BSeg seg(int64_t w, int j) const {
+    const TcSeg sg = segs[tiles[w].seg0 + j];
+    if (sg.near) return BSeg{X + sg.b_row * ldx, ldx, sg.K};
+    return BSeg{zmix + sg.b_row * ldz, ldz, sg.K};
   }
-}
+  __device__ __forceinline__ float* row_ptr(int64_t w, int row) const {
+    const TcTile& t = tiles[w];
+    return row < t.rows ? Y + (t.row0 + row) * ldy : nullptr;
+  }
+};
 
-// Main loop.  src.issue(raw) issues the copies of the next chunk (uniform
-// across the CTA; false when there is none); src.split(raw, conv) splits a
-// landed chunk.  Returns the number of chunks handed to the tensor core.
-template <typename Src>
-__device__ __forceinline__ int run_chunks(const Smem& s, uint32_t tmem, Src& src) {
-  int issued = 0;
-#pragma unroll
-  for (int i = 0; i < kRaw - 1; i++) {
-    if (src.issue(s.raw(i))) issued++;
-    cp_commit();
+// Phase 1: items (cluster, 128-slot tile, <= 2048-row chunk); one B segment
+// (the chunk's rows of X); output slot rows scattered through the slot map,
+// or partial rows when the cluster is split into several row chunks.
+struct Ph1 {
+  const P1Item* items;
+  const float* X;
+  int64_t ldx;
+  const int64_t* slotmap;
+  float* zmix;
+  float* part;
+  int64_t ldz;
+  __device__ __forceinline__ int nchunk(int64_t w) const { return items[w].nchunk; }
+  __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return items[w].a_chunk0; }
+  __device__ __forceinline__ int nseg(int64_t) const { return 1; }
+  __device__ __forceinline__ BSeg seg(int64_t w, int) const {
+    const P1Item& it = items[w];
+    return BSeg{X + it.x_row * ldx, ldx, it.nr};
   }
-  int c = 0;
-  while (c < issued) {
-    const int cs = c % kConv;
-    if (c >= kConv) {
-      if (!umma::mbar_wait(&s.mbar[cs], ((c - kConv) / kConv) & 1, kMaxPolls)) atomicExch(s.fail, 1);
+  __device__ __forceinline__ float* row_ptr(int64_t w, int row) const {
+    const P1Item& it = items[w];
+    if (row >= it.nq) return nullptr;
+    return it.out_row < 0 ? zmix + slotmap[it.map_off + row] * ldz : part + (it.out_row + row) * ldz;
+  }
+};
+
+// Walks this CTA's B chunks in order (tiles blockIdx.x, + gridDim.x, ...; in
+// each, its segments' K-chunks), skipping tiles without chunks.
+template <class Ph>
+struct BCursor {
+  const Ph* ph;
+  int64_t ntiles;
+  int nct, ncols;
+  int64_t id, w;
+  int j, nseg, k0, nv;
+  BSeg sg;
+  const float* base;
+  bool vec, valid;
+
+  __device__ __forceinline__ bool find_seg() {
+    for (; j < nseg; j++) {
+      sg = ph->seg(w, j);
+      if (sg.K > 0) {
+        const int n0 = (int)(id % nct) * kN;
+        base = sg.p + n0;
+        vec = (sg.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(base) & 15) == 0);
+        return true;
+      }
     }
-    cp_wait1();  // this thread's copies of chunk c have landed
-    __syncthreads();
-    if (*s.fail) break;
-    // the raw stage of chunk c-1 is free (split in the previous iteration)
-    if (src.issue(s.raw((c + kRaw - 1) % kRaw))) issued++;
+    return false;
+  }
+  __device__ __forceinline__ void enter() {
+    valid = false;
+    for (; id < ntiles; id += gridDim.x) {
+      w = id / nct;
+      nv = min(kN, ncols - (int)(id % nct) * kN);
+      nseg = ph->nseg(w);
+      j = 0;
+      k0 = 0;
+      if (find_seg()) {
+        valid = true;
+        return;
+      }
+    }
+  }
+  __device__ __forceinline__ void start() {
+    id = blockIdx.x;
+    enter();
+  }
+  __device__ __forceinline__ void advance() {
+    k0 += kK;
+    if (k0 < sg.K) return;
+    k0 = 0;
+    j++;
+    if (find_seg()) return;
+    id += gridDim.x;
+    enter();
+  }
+};
+
+// ---- roles -----------------------------------------------------------------
+template <class Ph>
+__device__ __forceinline__ void b_producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols) {
+  const int t = threadIdx.x;
+  int64_t total = 0;
+  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) total += ph.nchunk(id / nct);
+  BCursor<Ph> cur;
+  cur.ph = &ph;
+  cur.ntiles = ntiles;
+  cur.nct = nct;
+  cur.ncols = ncols;
+  cur.start();
+#pragma unroll
+  for (int i = 0; i < kR - 1; i++) {
+    if (cur.valid) {
+      issue_b(s.braw(i), cur.base, cur.sg.ld, cur.nv, cur.k0, cur.sg.K, cur.vec, t);
+      cur.advance();
+    }
     cp_commit();
-    src.split(s.raw(c % kRaw), s.conv(cs));
+  }
+  for (int64_t g = 0; g < total; g++) {
+    cp_wait<kR - 2>();  // this thread's copies of chunk g have landed
+    if (bar_or_b(s.failed())) break;  // everyone's copies of g have landed; raw stage of g-1 is free
+    if (cur.valid) {
+      issue_b(s.braw((int)((g + kR - 1) % kR)), cur.base, cur.sg.ld, cur.nv, cur.k0, cur.sg.K, cur.vec, t);
+      cur.advance();
+    }
+    cp_commit();
+    const int sb = (int)(g % kSB);
+    if (g >= kSB) wait_bar(s, EB + sb, (uint32_t)((g / kSB) - 1) & 1);
+    split_b(s.braw((int)(g % kR)), s.bc(sb), t);
     umma::fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      umma::fence_after_sync();
-      issue_mma(s.conv(cs), tmem, c == 0);
-      umma::commit(&s.mbar[cs]);
-    }
-    c++;
+    umma::mbar_arrive(&s.bar[FB + sb]);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  return c;
 }
 
-__device__ __forceinline__ void tile_begin(const Smem& s) {
-  if (threadIdx.x < 32) umma::tmem_alloc(s.tmem_slot, kTmemCols);
+template <class Ph>
+__device__ __forceinline__ void a_producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct,
+                                           const uint8_t* astream) {
+  int64_t g = 0;
+  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) {
+    const int64_t w = id / nct;
+    const int nch = ph.nchunk(w);
+    const int64_t a0 = ph.a_chunk0(w);
+    for (int c = 0; c < nch; c++, g++) {
+      if (s.failed()) return;
+      const int sa = (int)(g % kSA);
+      if (g >= kSA && !wait_bar(s, EA + sa, (uint32_t)((g / kSA) - 1) & 1)) return;
+      umma::mbar_arrive_expect_tx(&s.bar[FA + sa], kAChunkBytes);
+      umma::bulk_g2s(s.a(sa), astream + (a0 + c) * (int64_t)kAChunkBytes, kAChunkBytes, &s.bar[FA + sa]);
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, uint32_t acc, bool first) {
+  const uint32_t a_hi = umma::smem_u32(a), a_lo = a_hi + kABytes;
+  const uint32_t b_hi = umma::smem_u32(b), b_lo = b_hi + kBBytes;
+#pragma unroll
+  for (int kk = 0; kk < kK / 8; kk++) {
+    const uint32_t koff = kk * 2 * umma::kLBO;  // two core matrices along K per MMA
+    umma::mma_tf32(acc, umma::smem_desc(a_hi + koff), umma::smem_desc(b_hi + koff), kIdesc,
+                   (first && kk == 0) ? 0u : 1u);
+    umma::mma_tf32(acc, umma::smem_desc(a_hi + koff), umma::smem_desc(b_lo + koff), kIdesc, 1u);
+    umma::mma_tf32(acc, umma::smem_desc(a_lo + koff), umma::smem_desc(b_hi + koff), kIdesc, 1u);
+  }
+}
+
+template <class Ph>
+__device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t ntiles, int nct, uint32_t tmem) {
+  int64_t g = 0;
+  int tl = 0;
+  bool ok = true;
+  for (int64_t id = blockIdx.x; ok && id < ntiles; id += gridDim.x, tl++) {
+    const int nch = ph.nchunk(id / nct);
+    const int b = tl & 1;
+    if (tl >= 2 && !wait_bar(s, AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
+    umma::fence_after_sync();
+    const uint32_t acc = tmem + (uint32_t)(b * kN);
+    for (int c = 0; c < nch; c++, g++) {
+      const int sa = (int)(g % kSA), sb = (int)(g % kSB);
+      if (s.failed() || !wait_bar(s, FA + sa, (uint32_t)(g / kSA) & 1) ||
+          !wait_bar(s, FB + sb, (uint32_t)(g / kSB) & 1)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      issue_mma(s.a(sa), s.bc(sb), acc, c == 0);
+      umma::commit(&s.bar[EA + sa]);
+      umma::commit(&s.bar[EB + sb]);
+    }
+    if (!ok) break;
+    if (nch > 0)
+      umma::commit(&s.bar[AF + b]);
+    else
+      umma::mbar_arrive(&s.bar[AF + b]);
+  }
+  // every MMA issued here has completed before TMEM is released
+  umma::commit(&s.bar[FIN]);
+  wait_bar(s, FIN, 0);
+}
+
+template <class Ph>
+__device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols,
+                                         uint32_t tmem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
+  const int row = 32 * quarter + lane;
+  int tl = 0;
+  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
+    const int b = tl & 1;
+    if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    umma::fence_after_sync();
+    if (s.failed()) break;
+    const int64_t w = id / nct;
+    const int n0 = (int)(id % nct) * kN;
+    const int nv = min(kN, ncols - n0);
+    const bool zero = ph.nchunk(w) == 0;
+    float* dst = ph.row_ptr(w, row);
+    if (dst) dst += n0;
+    const bool vec4 = dst && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+#pragma unroll 1
+    for (int j = 0; j < kN / 32; j++) {
+      float v[32];
+      if (zero) {
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = 0.f;
+      } else {
+        umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
+      }
+      if (dst) {
+        const int c0 = 32 * j;
+        if (vec4 && c0 + 32 <= nv) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; i++)
+            if (c0 + i < nv) dst[c0 + i] = v[i];
+        }
+      }
+    }
+    umma::fence_before_sync();
+    umma::mbar_arrive(&s.bar[AE + b]);
+  }
+}
+
+template <class Ph>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_apply(const Ph ph, int64_t nwork, int nct, int ncols, const uint8_t* __restrict__ astream,
+               int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const Smem s = smem_layout(smem_raw);
+  const int warp = threadIdx.x >> 5;
+  const int64_t ntiles = nwork * nct;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kConv; i++) umma::mbar_init(&s.mbar[i], 1);
+    for (int i = FA; i < EA; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = EA; i < FB; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = FB; i < EB; i++) umma::mbar_init(&s.bar[i], kBThreads);
+    for (int i = EB; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = AF; i < AE; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 128);
+    umma::mbar_init(&s.bar[FIN], 1);
     *s.fail = 0;
     umma::fence_mbar_init();
   }
+  if (warp == kMmaWarp) umma::tmem_alloc(s.tmem_slot, kTmemCols);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
-}
-
-// Wait for the last chunk's MMAs (bounded); returns false on expiry.
-__device__ __forceinline__ bool tile_drain(const Smem& s, int nchunks) {
-  bool ok = true;
-  if (nchunks > 0) {
-    const int c = nchunks - 1;
-    ok = umma::mbar_wait(&s.mbar[c % kConv], (c / kConv) & 1, kMaxPolls);
-    if (!ok) atomicExch(s.fail, 1);
+  const uint32_t tmem = *s.tmem_slot;
+  if (warp < 4) {
+    b_producer(s, ph, ntiles, nct, ncols);
+  } else if (warp == kAWarp) {
+    if ((threadIdx.x & 31) == 0) a_producer(s, ph, ntiles, nct, astream);
+  } else if (warp == kMmaWarp) {
+    if ((threadIdx.x & 31) == 0) mma_issuer(s, ph, ntiles, nct, tmem);
+    __syncwarp();
+  } else {
+    epilogue(s, ph, ntiles, nct, ncols, tmem);
   }
-  __syncthreads();
-  umma::fence_after_sync();
-  return ok && !*s.fail;
-}
-
-__device__ __forceinline__ void tile_end(const Smem& s, uint32_t tmem) {
   umma::fence_before_sync();
   __syncthreads();
-  if (threadIdx.x < 32) umma::tmem_dealloc(tmem, kTmemCols);
+  if (threadIdx.x == 0 && s.failed()) atomicExch(err, 1);
+  if (warp == kMmaWarp) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, kTmemCols);
+  }
 }
 
-// Epilogue: thread owns row (32 * (warp % 4) + lane) and 64 columns starting at
-// 64 * (warp / 4); calls out(row, col, value) for valid entries.
-template <typename OutFn>
-__device__ __forceinline__ void tile_store(uint32_t tmem, int rows, int nv, bool zero, OutFn&& out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * (warp & 3) + lane;
-  const int c0 = 64 * (warp >> 2);
-  for (int h = 0; h < 2; h++) {
-    float v[32];
-    if (zero) {
+// Writes the split operator chunks: element (i, k) of chunk c (see TcAChunk)
+// into its hi and lo blocks in the tensor-core layout.
+__global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const float* __restrict__ fac,
+                             const float* __restrict__ nearv, uint8_t* __restrict__ out) {
+  for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+    const TcAChunk ch = d[c];
+    const float* src = ch.near ? nearv : fac;
+    uint8_t* hi = out + c * kAChunkBytes;
+    uint8_t* lo = hi + kABytes;
+    for (int e = threadIdx.x; e < kM * kK / 4; e += blockDim.x) {
+      const int i = e >> 2, kq = e & 3;
+      float v[4];
 #pragma unroll
-      for (int i = 0; i < 32; i++) v[i] = 0.f;
-    } else {
-      umma::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * h), v);
-    }
-    if (row < rows) {
-#pragma unroll
-      for (int i = 0; i < 32; i++) {
-        const int col = c0 + 32 * h + i;
-        if (col < nv) out(row, col, v[i]);
+      for (int u = 0; u < 4; u++) {
+        const int k = 4 * kq + u;
+        v[u] = (i >= ch.row_lo && i < ch.row_hi && k < ch.kv)
+                   ? src[ch.src_off + (int64_t)(i - ch.row_lo) * ch.si + (int64_t)k * ch.sk]
+                   : 0.f;
       }
+      put4(hi, lo, i, 4 * kq, v[0], v[1], v[2], v[3]);
     }
   }
-}
-
-// Chunk source for phase 2: the tile's segments, K-chunks of kChunk each.
-// A = factor / near-field rows (k-contiguous, rows form); B = slot rows of
-// Zmix or rows of X (k-rows form).
-struct P2Src {
-  const TcSeg* segs;
-  int seg0, nseg;
-  const float *fac, *nearv, *zmix, *X;
-  int64_t ldz, ldx;
-  int n0, nv;
-  bool bvec_z, bvec_x;
-  int si = 0, k0 = 0;
-  bool started = false;
-  __device__ bool issue(uint8_t* raw) {
-    if (!started) {
-      started = true;
-      si = 0;
-      k0 = 0;
-    } else {
-      k0 += umma::kChunk;
-      if (si < nseg && k0 >= segs[seg0 + si].K) {
-        k0 = 0;
-        si++;
-      }
-    }
-    while (si < nseg && segs[seg0 + si].K <= 0) si++;
-    if (si >= nseg) return false;
-    const TcSeg sg = segs[seg0 + si];
-    const float* A = (sg.near ? nearv : fac) + sg.a_off;
-    const bool avec = ((sg.a_off & 3) == 0) && ((sg.lda & 3) == 0);
-    issue_a_rows(raw, A, sg.lda, sg.row_lo, sg.row_hi, k0, sg.K, avec);
-    const float* B = sg.near ? X + sg.b_row * ldx + n0 : zmix + sg.b_row * ldz + n0;
-    issue_krows(raw + umma::kChunkBytes, B, sg.near ? ldx : ldz, nv, k0, sg.K, sg.near ? bvec_x : bvec_z);
-    return true;
-  }
-  __device__ void split(const uint8_t* raw, uint8_t* conv) const {
-    const int t = threadIdx.x;
-    if (t < 128)
-      split_row(raw, conv, conv + umma::kChunkBytes, t);
-    else
-      split_col(raw + umma::kChunkBytes, conv + 2 * umma::kChunkBytes, conv + 3 * umma::kChunkBytes, t - 128);
-  }
-};
-
-// Chunk source for phase 1: rows of one cluster chunk, K-chunks of kChunk.
-// A(m = slot, k = row) and B(k = row, n) are both in k-rows form.
-struct P1Src {
-  const float *A, *B;
-  int64_t lda, ldb;
-  int mv, kv, nv;
-  bool avec, bvec;
-  int k0 = -umma::kChunk;
-  __device__ bool issue(uint8_t* raw) {
-    k0 += umma::kChunk;
-    if (k0 >= kv) return false;
-    issue_krows(raw, A, lda, mv, k0, kv, avec);
-    issue_krows(raw + umma::kChunkBytes, B, ldb, nv, k0, kv, bvec);
-    return true;
-  }
-  __device__ void split(const uint8_t* raw, uint8_t* conv) const {
-    const int t = threadIdx.x;
-    if (t < 128)
-      split_col(raw, conv, conv + umma::kChunkBytes, t);
-    else
-      split_col(raw + umma::kChunkBytes, conv + 2 * umma::kChunkBytes, conv + 3 * umma::kChunkBytes, t - 128);
-  }
-};
-
-__global__ void __launch_bounds__(kThreads, 2)
-    k_phase2_tc(const TcTile* __restrict__ tiles, const TcSeg* __restrict__ segs, const float* __restrict__ fac,
-                const float* __restrict__ nearv, const float* __restrict__ zmix, int64_t ldz,
-                const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy, int ncols,
-                int* __restrict__ err) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem s = smem_layout(smem_raw);
-  // x = column tile (fastest): the column tiles of one row tile run together
-  // and share the tile's operator rows through L2
-  const TcTile tl = tiles[blockIdx.y];
-  const int n0 = blockIdx.x * 128;
-  const int nv = min(128, ncols - n0);
-  if (nv <= 0) return;
-  tile_begin(s);
-  const uint32_t tmem = *s.tmem_slot;
-  const bool bz = ((ldz & 3) == 0) && ((reinterpret_cast<uintptr_t>(zmix + n0) & 15) == 0);
-  const bool bx = ((ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(X + n0) & 15) == 0);
-  P2Src src{segs, tl.seg0, tl.nseg, fac, nearv, zmix, X, ldz, ldx, n0, nv, bz, bx};
-  const int c = run_chunks(s, tmem, src);
-  const bool ok = tile_drain(s, c);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-  } else {
-    float* Yt = Y + tl.row0 * ldy + n0;
-    tile_store(tmem, tl.rows, nv, c == 0, [&](int row, int col, float v) { Yt[(int64_t)row * ldy + col] = v; });
-  }
-  tile_end(s, tmem);
-}
-
-__global__ void __launch_bounds__(kThreads, 2)
-    k_phase1_tc(const P1Item* __restrict__ items, const float* __restrict__ fac, const float* __restrict__ X,
-                int64_t ldx, int ncols, const int64_t* __restrict__ slotmap, float* __restrict__ zmix,
-                float* __restrict__ part, int64_t ldz, int* __restrict__ err) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem s = smem_layout(smem_raw);
-  const P1Item it = items[blockIdx.x];
-  const int n0 = blockIdx.y * 128;
-  const int nv = min(128, ncols - n0);
-  if (nv <= 0) return;
-  tile_begin(s);
-  const uint32_t tmem = *s.tmem_slot;
-  // A(m = slot, k = row) = Fac_c[(r0 + row) * K + q0 + slot]; B(k = row, n) = X[(x_row + row) * ldx + n0 + n]
-  const float* A = fac + it.fac_off + (int64_t)it.r0 * it.K + it.q0;
-  const float* B = X + it.x_row * ldx + n0;
-  const bool av = ((it.K & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-  const bool bv = ((ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
-  P1Src src{A, B, it.K, ldx, it.nq, it.nr, nv, av, bv};
-  const int c = run_chunks(s, tmem, src);
-  const bool ok = tile_drain(s, c);
-  if (!ok) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-  } else {
-    tile_store(tmem, it.nq, nv, c == 0, [&](int q, int col, float v) {
-      float* dst = it.out_row < 0 ? zmix + slotmap[it.map_off + q] * ldz : part + (it.out_row + q) * ldz;
-      dst[n0 + col] = v;
-    });
-  }
-  tile_end(s, tmem);
 }
 
 __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const float* __restrict__ part,
@@ -417,15 +529,20 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     FKF_TRY(dev_alloc(ctx, h->tc_err, 64));
     FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, ctx->stream));
   }
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_phase2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_phase1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  int sms = 0;
+  FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  const uint8_t* astream = h->tca.as<uint8_t>();
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
-    const int ntile = (int)cdiv(nc, 128);
+    const int nct = (int)cdiv(nc, kN);
     if (h->n_tcp1 > 0) {
-      k_phase1_tc<<<dim3((unsigned)h->n_tcp1, ntile), kThreads, kSmemBytes, ctx->stream>>>(
-          h->tcp1.as<P1Item>(), h->fac.as<float>(), X + c0, ldx, nc, h->slotmap.as<int64_t>(), h->zmix.as<float>(),
-          h->part.as<float>(), P, h->tc_err.as<int>());
+      const Ph1 ph{h->tcp1.as<P1Item>(), X + c0, ldx, h->slotmap.as<int64_t>(), h->zmix.as<float>(),
+                   h->part.as<float>(), P};
+      const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
+      k_tc_apply<Ph1><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream,
+                                                                   h->tc_err.as<int>());
       FKF_LAUNCHED(ctx);
     }
     if (h->n_tcred > 0) {
@@ -433,10 +550,64 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
           h->tcred.as<P1Reduce>(), h->part.as<float>(), h->slotmap.as<int64_t>(), h->zmix.as<float>(), P, nc);
       FKF_LAUNCHED(ctx);
     }
-    k_phase2_tc<<<dim3(ntile, (unsigned)h->n_tctile), kThreads, kSmemBytes, ctx->stream>>>(
-        h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->fac.as<float>(), h->nearv.as<float>(), h->zmix.as<float>(),
-        P, X + c0, ldx, Y + c0, ldy, nc, h->tc_err.as<int>());
+    const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zmix.as<float>(), P, X + c0, ldx, Y + c0, ldy};
+    const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
+    k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream,
+                                                                 h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::vector<TcTile>& tiles) {
+  fkf_ctx* ctx = h->ctx;
+  std::vector<TcAChunk> ch;
+  for (P1Item& it : items) {
+    it.a_chunk0 = (int64_t)ch.size();
+    it.nchunk = (int)cdiv(it.nr, kK);
+    for (int c = 0; c < it.nchunk; c++) {
+      TcAChunk a{};
+      a.src_off = it.fac_off + (int64_t)(it.r0 + c * kK) * it.K + it.q0;
+      a.si = 1;
+      a.sk = it.K;
+      a.row_lo = 0;
+      a.row_hi = it.nq;
+      a.kv = std::min(kK, it.nr - c * kK);
+      a.near = 0;
+      ch.push_back(a);
+    }
+  }
+  for (TcTile& t : tiles) {
+    t.a_chunk0 = (int64_t)ch.size();
+    int nch = 0;
+    for (int j = 0; j < t.nseg; j++) {
+      const TcSeg& sg = h->tcseg_host[t.seg0 + j];
+      for (int k0 = 0; k0 < sg.K; k0 += kK, nch++) {
+        TcAChunk a{};
+        a.src_off = sg.a_off + k0;
+        a.si = sg.lda;
+        a.sk = 1;
+        a.row_lo = sg.row_lo;
+        a.row_hi = sg.row_hi;
+        a.kv = std::min(kK, sg.K - k0);
+        a.near = sg.near;
+        ch.push_back(a);
+      }
+    }
+    t.nchunk = nch;
+  }
+  if (!items.empty()) FKF_TRY(dev_upload(ctx, h->tcp1, items.data(), items.size() * sizeof(P1Item)));
+  if (!tiles.empty()) FKF_TRY(dev_upload(ctx, h->tctile, tiles.data(), tiles.size() * sizeof(TcTile)));
+  h->n_tca = (int64_t)ch.size();
+  FKF_TRY(dev_alloc(ctx, h->tca, (size_t)std::max<int64_t>(h->n_tca, 1) * kAChunkBytes));
+  if (h->n_tca > 0) {
+    DevBuf desc;
+    FKF_TRY(dev_upload(ctx, desc, ch.data(), ch.size() * sizeof(TcAChunk)));
+    const int grid = (int)std::min<int64_t>(h->n_tca, 152 * 8);
+    k_tc_build_a<<<grid, 256, 0, ctx->stream>>>(desc.as<TcAChunk>(), h->n_tca, h->fac.as<float>(),
+                                                h->nearv.as<float>(), h->tca.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
   return FKF_OK;
 }
