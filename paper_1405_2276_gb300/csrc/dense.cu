@@ -37,6 +37,47 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm(int M, int N, int K, T al
   }
 }
 
+// Symmetric result C = alpha op(A) op(B) + beta C (N x N) when op(A) op(B) is
+// symmetric: only the tiles on and below the diagonal are computed (tile t of
+// the lower triangle, row-major order), and each computed entry (i >= j) is
+// written to both (i, j) and (j, i).  C must be symmetric on entry when beta
+// is not zero.
+template <typename T, bool A_KC, bool B_KC>
+__global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha, const T* __restrict__ A,
+                                                           int64_t lda, const T* __restrict__ B, int64_t ldb,
+                                                           T beta, T* __restrict__ C, int64_t ldc) {
+  static_assert(TileCfg<T>::BM == TileCfg<T>::BN, "square tiles");
+  __shared__ TileSmem<T> sm;
+  constexpr int BM = TileCfg<T>::BM;
+  const int t = blockIdx.x;
+  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+  while (bi * (bi + 1) / 2 > t) bi--;
+  const int bj = t - bi * (bi + 1) / 2;
+  const int m0 = bi * BM, n0 = bj * BM;
+  const int mv = min(BM, N - m0), nv = min(BM, N - n0);
+  T acc[TileCfg<T>::TM][TileCfg<T>::TN];
+  tile_zero<T>(acc);
+  const T* Ap = A_KC ? A + (int64_t)m0 * lda : A + m0;
+  const T* Bp = B_KC ? B + (int64_t)n0 * ldb : B + n0;
+  tile_mma<T, A_KC, B_KC>(acc, Ap, lda, mv, Bp, ldb, nv, K, sm);
+#pragma unroll
+  for (int i = 0; i < TileCfg<T>::TM; i++) {
+    const int r = tile_row<T>(i);
+    if (r >= mv) continue;
+#pragma unroll
+    for (int j = 0; j < TileCfg<T>::TN; j++) {
+      const int c = tile_col<T>(j);
+      const int gi = m0 + r, gj = n0 + c;
+      if (c >= nv || gi < gj) continue;
+      T* dst = C + (int64_t)gi * ldc + gj;
+      const T v = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *dst;
+      *dst = v;
+      if (gi != gj) C[(int64_t)gj * ldc + gi] = v;
+    }
+  }
+}
+
 // Partial Gram: part[z] = A[rows z]^T B[rows z] (A: K x M, B: K x N row-major).
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_gram_part(int M, int N, int64_t K, int64_t chunk,
@@ -107,6 +148,25 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
     return scale_f64(ctx, M, N, beta, C, ldc);
   }
   return gemm_impl<double>(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, double alpha, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  if (N <= 0) return FKF_OK;
+  if (K <= 0) return scale_f64(ctx, N, N, beta, C, ldc);
+  constexpr int BM = TileCfg<double>::BM;
+  const int64_t nb = cdiv(N, BM);
+  const unsigned grid = (unsigned)(nb * (nb + 1) / 2);
+  if (!ta && !tb)
+    k_gemm_sym<double, true, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!ta && tb)
+    k_gemm_sym<double, true, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta && !tb)
+    k_gemm_sym<double, false, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else
+    k_gemm_sym<double, false, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
 }
 
 fkf_status gemm_f32(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,

@@ -51,13 +51,19 @@ __global__ void k_densify(int m, const int64_t* __restrict__ rowptr, const int32
   }
 }
 
+// Column counts of H in cluster order (warp per row); flags column indices
+// outside [0, n).
 __global__ void k_csc_count(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const int64_t* __restrict__ iperm, int64_t n, int* __restrict__ cnt) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+                            const int64_t* __restrict__ iperm, int64_t n, int* __restrict__ cnt,
+                            int* __restrict__ flag) {
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= m) return;
-  for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p++) {
+  for (int64_t p = rowptr[j] + lane; p < rowptr[j + 1]; p += 32) {
     const int64_t c = col[p];
-    if (c >= 0 && c < n) atomicAdd(&cnt[iperm[c]], 1);
+    if (c >= 0 && c < n)
+      atomicAdd(&cnt[iperm[c]], 1);
+    else
+      atomicOr(flag, 1);
   }
 }
 
@@ -89,13 +95,15 @@ __global__ void k_scan(int64_t n, const int* __restrict__ cnt, int64_t* __restri
   if (t == 1023) out[n] = run;
 }
 
+// Scatter the entries into their columns (warp per row; the order inside a
+// column is fixed afterwards by k_csc_sort).
 __global__ void k_csc_fill(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
                            const int64_t* __restrict__ colptr, int* __restrict__ cursor, int* __restrict__ crow,
                            double* __restrict__ cval) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= m) return;
-  for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p++) {
+  for (int64_t p = rowptr[j] + lane; p < rowptr[j + 1]; p += 32) {
     const int64_t c = col[p];
     if (c < 0 || c >= n) continue;
     const int64_t ci = iperm[c];
@@ -124,6 +132,17 @@ __global__ void k_csc_sort(int64_t n, const int64_t* __restrict__ colptr, int* _
     crow[q + 1] = r;
     cval[q + 1] = v;
   }
+}
+
+// Bt (n x m, cluster order) += H^T from the sorted CSC form: thread per
+// column of H = row of Bt; duplicates are summed in the sorted order.
+template <typename T>
+__global__ void k_densify_csc(int64_t n, const int64_t* __restrict__ colptr, const int* __restrict__ crow,
+                              const double* __restrict__ cval, T* __restrict__ Bt, int64_t ldb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T* row = Bt + i * ldb;
+  for (int64_t p = colptr[i]; p < colptr[i + 1]; p++) row[crow[p]] += (T)cval[p];
 }
 
 // out (m x ncols, FP64) = H * src[:, 0:ncols]  (src rows in cluster order)
@@ -392,26 +411,6 @@ __global__ void k_lincomb(int n, double a, const double* A, double b, const doub
     C[e] = a * A[e] + (B ? b * B[e] : 0.0) + ((e / n == e % n) ? d : 0.0);
 }
 
-// out = || diag(rs) A diag(rs) ||_F for an m x m matrix (single CTA)
-__global__ void k_frob_scaled(int m, const double* __restrict__ A, const double* __restrict__ rs,
-                              double* __restrict__ out) {
-  __shared__ double sh[32];
-  double s = 0;
-  const int64_t total = (int64_t)m * m;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    const double v = A[e] * rs[e / m] * rs[e % m];
-    s += v * v;
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
-    out[0] = sqrt(t);
-  }
-}
-
 // E = diag(alpha1 - d) (r x r)
 // K^T = (alpha' HW - HW D)^T = (HW E)^T, r x m (HW: m x r, ld ldh; HWD: m x r, ld r)
 __global__ void k_hwe_t(int m, int r, const double* __restrict__ HW, int64_t ldh, const double* __restrict__ HWD,
@@ -446,25 +445,50 @@ __global__ void k_vmul(int n, const double* __restrict__ d, const double* __rest
   if (i < n) out[i] = d[i] * x[i];
 }
 
-// out[q] = w[n-1-q] for q < n (descending copy of ascending eigenvalues)
-__global__ void k_rev(int n, const double* __restrict__ w, double* __restrict__ out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) out[q] = w[n - 1 - q];
-}
 
 // out = ||A||_F over n entries (single CTA)
-__global__ void k_frob(int64_t n, const double* __restrict__ A, double* __restrict__ out) {
+// Frobenius norms in two passes with a fixed summation order: block b sums
+// the squares of its contiguous range of A (optionally scaled as
+// rs[i] A[i, j] rs[j] for an m x m matrix) into part[b]; one block adds the
+// kFrobBlocks partials.
+constexpr int kFrobBlocks = 304;
+
+__global__ void k_frob_part(int64_t n, const double* __restrict__ A, const double* __restrict__ rs, int m,
+                            double* __restrict__ part) {
   __shared__ double sh[32];
+  const int64_t per = (n + kFrobBlocks - 1) / kFrobBlocks;
+  const int64_t a = blockIdx.x * per, b = a + per < n ? a + per : n;
   double s = 0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += A[e] * A[e];
+  for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+    const double v = rs ? A[e] * rs[e / m] * rs[e % m] : A[e];
+    s += v * v;
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_frob_final(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int b = 0; b < kFrobBlocks; b++) t += part[b];
     out[0] = sqrt(t);
   }
+}
+
+// out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
+static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part,
+                       double* out) {
+  k_frob_part<<<kFrobBlocks, 256, 0, ctx->stream>>>(n, A, rs, m, part);
+  FKF_LAUNCHED(ctx);
+  k_frob_final<<<1, 32, 0, ctx->stream>>>(part, out);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
 }
 
 // A = (A + A^T) / 2 in place (n x n)
@@ -600,7 +624,7 @@ struct fkf_filter {
   DevBuf cnt, cursor, colptr, crow, cval;
   // small FP64 buffers
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
-  DevBuf nu, z, uz, vcoef, HWD, nll, dbar;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red;
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
   cudaEvent_t ev[7] = {};
   double phase_ms[6] = {};
@@ -635,6 +659,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
   FKF_TRY(A(f->HWD, m * r));
   FKF_TRY(A(f->nll, 4));
+  FKF_TRY(A(f->red, kFrobBlocks));
   FKF_TRY(A(f->dbar, r));
   FKF_TRY(A(f->y, m));
   FKF_TRY(A(f->rdiag, m));
@@ -797,20 +822,23 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   const double* val = f->val.as<double>();
 
   FKF_CUDA(ctx, cudaEventRecord(f->ev[0], st));
-  // ---- S1: densify H^T (cluster order) and build its column index
-  FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
-  k_densify<T><<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, val, iperm, n, f->Bt.as<T>(), m, f->flag.as<int>());
-  FKF_LAUNCHED(ctx);
+  // ---- S1: column index of H (CSC, cluster order) and the dense H^T
   FKF_CUDA(ctx, cudaMemsetAsync(f->cnt.p, 0, (size_t)n * 4, st));
   FKF_CUDA(ctx, cudaMemsetAsync(f->cursor.p, 0, (size_t)n * 4, st));
-  k_csc_count<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>());
+  k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>(),
+                                                                f->flag.as<int>());
   FKF_LAUNCHED(ctx);
   k_scan<<<1, 1024, 0, st>>>(n, f->cnt.as<int>(), f->colptr.as<int64_t>());
   FKF_LAUNCHED(ctx);
-  k_csc_fill<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
-                                                 f->cursor.as<int>(), f->crow.as<int>(), f->cval.as<double>());
+  k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
+                                                               f->cursor.as<int>(), f->crow.as<int>(),
+                                                               f->cval.as<double>());
   FKF_LAUNCHED(ctx);
   k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
+  k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
+                                                      f->cval.as<double>(), f->Bt.as<T>(), m);
   FKF_LAUNCHED(ctx);
   FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
   // ---- S2: G = Gamma_H H^T
@@ -840,7 +868,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     } else {
       FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
     }
-    FKF_TRY(gemm_f64(ctx, false, true, m, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
+    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
   }
   FKF_TRY(chol_f64(ctx, m, S, f->cholws));
   FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
@@ -873,11 +901,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     if (r > 0) {
       double* T0 = f->Tm.as<double>();
       FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
-      FKF_TRY(gemm_f64(ctx, false, true, m, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
-      k_frob_scaled<<<1, 1024, 0, st>>>(m, T0, f->rs.as<double>(), nrm);
-      FKF_LAUNCHED(ctx);
-      k_frob<<<1, 1024, 0, st>>>((int64_t)m * m, f->At.as<double>(), nrm + 1);
-      FKF_LAUNCHED(ctx);
+      FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
+      FKF_TRY(frob(ctx, (int64_t)m * m, T0, f->rs.as<double>(), m, f->red.as<double>(), nrm));
+      FKF_TRY(frob(ctx, (int64_t)m * m, f->At.as<double>(), nullptr, m, f->red.as<double>(), nrm + 1));
     }
     double hv[2] = {1.0, 1.0};
     int hflag = 0;
@@ -911,9 +937,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_LAUNCHED(ctx);
     FKF_CUDA(ctx, cudaMemcpyAsync(Yt, Kt, (size_t)m * r * 8, cudaMemcpyDeviceToDevice, st));
     FKF_TRY(chol_solve_f64(ctx, m, S, Yt, r));
-    FKF_TRY(gemm_f64(ctx, false, true, r, r, m, -1.0, Kt, m, Yt, m, 1.0, Ep, r));
-    k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Ep);
-    FKF_LAUNCHED(ctx);
+    FKF_TRY(gemm_sym_f64(ctx, false, true, r, m, -1.0, Kt, m, Yt, m, 1.0, Ep, r));
     k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Ep, 0.0, nullptr, alpha1, Dn2);  // D' = alpha' I - E'
     FKF_LAUNCHED(ctx);
     for (int e = 4; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
@@ -962,8 +986,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_LAUNCHED(ctx);
     // every eigenvalue of T is bounded by ||T||_F: when that is below the
     // threshold no new direction exists and the eigensolve is skipped
-    k_frob<<<1, 1024, 0, st>>>((int64_t)mlam * mlam, Tm, f->nll.as<double>() + 1);
-    FKF_LAUNCHED(ctx);
+    FKF_TRY(frob(ctx, (int64_t)mlam * mlam, Tm, nullptr, mlam, f->red.as<double>(), f->nll.as<double>() + 1));
     double tfrob = 0;
     FKF_CUDA(ctx, cudaMemcpyAsync(&tfrob, f->nll.as<double>() + 1, 8, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
@@ -1731,11 +1754,12 @@ static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, 
     FKF_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, n * 4, st));
     FKF_CUDA(ctx, cudaMemsetAsync(cursor.p, 0, n * 4, st));
     FKF_CUDA(ctx, cudaMemsetAsync(gc.p, 0, n * 8, st));
-    k_csc_count<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), iperm, n, cnt.as<int>());
+    k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), iperm, n,
+                                                                  cnt.as<int>(), flag.as<int>());
     FKF_LAUNCHED(ctx);
     k_scan<<<1, 1024, 0, st>>>(n, cnt.as<int>(), colptr.as<int64_t>());
     FKF_LAUNCHED(ctx);
-    k_csc_fill<<<(int)cdiv(m, 128), 128, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm,
+    k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm,
                                                    n, colptr.as<int64_t>(), cursor.as<int>(), crow.as<int>(),
                                                    cval.as<double>());
     FKF_LAUNCHED(ctx);

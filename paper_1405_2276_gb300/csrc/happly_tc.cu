@@ -12,13 +12,13 @@
 // with cp.async and split in shared memory by four producer warps.
 //
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-3  B producers: cp.async two chunks ahead (three raw stages),
-//              split into two hi/lo stages, arrive on full_b;
-//   warp 4     A producer (one thread): bulk copies into four stages, full_a;
-//   warp 5     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
+//   warps 0-7  B producers: cp.async kR-1 chunks ahead (kR raw stages),
+//              split into three hi/lo stages, arrive on full_b;
+//   warp 8     A producer (one thread): bulk copies into four stages, full_a;
+//   warp 9     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
 //              products), commits to empty_a / empty_b, and to acc_full after
 //              a tile's last chunk; also allocates and frees TMEM;
-//   warps 6-9  epilogue: tcgen05.ld of the finished accumulator, stores,
+//   warps 10-13 epilogue: tcgen05.ld of the finished accumulator, stores,
 //              arrive on acc_empty.
 // Two accumulators (2 x 256 TMEM columns) let the epilogue of one tile run
 // under the MMAs of the next.  Tiles are dealt round-robin over the CTAs, the
@@ -32,6 +32,17 @@
 #include "common.h"
 #include "umma.cuh"
 
+// Pipeline depths (compile-time tuning knobs).
+#ifndef FKF_TC_RAW_STAGES
+#define FKF_TC_RAW_STAGES 3
+#endif
+#ifndef FKF_TC_A_PREFETCH
+#define FKF_TC_A_PREFETCH 0
+#endif
+#ifndef FKF_TC_B_PREFETCH
+#define FKF_TC_B_PREFETCH 0
+#endif
+
 namespace {
 
 constexpr int kM = 128;                    // tile rows = TMEM lanes
@@ -41,12 +52,15 @@ constexpr int kABytes = kM * kK * 4;       // 8 KB: one TF32 half of an A chunk
 constexpr int kAChunkBytes = 2 * kABytes;  // 16 KB: hi | lo
 constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk, or the raw FP32 chunk
 constexpr int kSA = 4;                     // A stages
-constexpr int kSB = 2;                     // split B stages
-constexpr int kR = 3;                      // raw B stages
-constexpr int kSmemBytes = kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes + 256;  // 176.25 KB
-constexpr int kBThreads = 128;             // warps 0-3
-constexpr int kAWarp = 4, kMmaWarp = 5;    // warps 6-9: epilogue
-constexpr int kThreads = 320;
+constexpr int kSB = 3;                     // split B stages
+constexpr int kR = FKF_TC_RAW_STAGES;      // raw B stages
+constexpr int kAPrefetch = FKF_TC_A_PREFETCH;  // A chunks prefetched into L2 ahead of their copy (0: none)
+constexpr int kBPrefetch = FKF_TC_B_PREFETCH;  // B chunks prefetched into L2 ahead of their copy (0: none)
+constexpr int kSmemBytes = kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes + 256;  // 208.25 KB (kR = 3)
+static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+constexpr int kBThreads = 256;             // warps 0-7: B producers, one column each
+constexpr int kAWarp = 8, kMmaWarp = 9;    // warps 10-13: epilogue
+constexpr int kThreads = 448;
 constexpr uint32_t kTmemCols = 2 * kN;
 constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
@@ -95,19 +109,23 @@ __device__ __forceinline__ void cp4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// L2 prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Barrier over the four B-producer warps (named barrier 1) that also ORs a
+// Barrier over the B-producer warps (named barrier 1) that also ORs a
 // predicate across them, so that all of them take the same exit decision.
 __device__ __forceinline__ bool bar_or_b(bool pred) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.b32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "bar.red.or.pred q, 1, 256, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}\n"
       : "=r"(r)
       : "r"((uint32_t)pred)
@@ -135,7 +153,7 @@ __device__ __forceinline__ void copy_quad(void* dst, const float* src, int valid
 }
 
 // Raw B chunk: 16 rows (k) x 256 floats, quad q of row k at byte k * 1024 + q * 16.
-// Copies of P(k, c) = P[(k0 + k) * ld + c] for k0 + k < kv, c < cv; thread t of 128.
+// Copies of P(k, c) = P[(k0 + k) * ld + c] for k0 + k < kv, c < cv; thread t of kBThreads.
 __device__ __forceinline__ void issue_b(uint8_t* raw, const float* P, int64_t ld, int cv, int k0, int kv, bool vec,
                                         int t) {
 #pragma unroll
@@ -160,20 +178,17 @@ __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-// Columns t and t + 128 of a raw chunk -> (row = column, k = 0..15) of the
-// split stage.  A warp reads 32 consecutive floats per k and writes 8
-// distinct rows per quarter-warp (no bank conflicts).
+// Column t of a raw chunk -> (row = t, k = 0..15) of the split stage.  A
+// warp reads 32 consecutive floats per k and writes 8 distinct rows per
+// quarter-warp (no bank conflicts).
 __device__ __forceinline__ void split_b(const uint8_t* raw, uint8_t* conv, int t) {
+  static_assert(kBThreads == kN, "one B-producer thread per column");
   uint8_t* hi = conv;
   uint8_t* lo = conv + kBBytes;
+  const float* r = reinterpret_cast<const float*>(raw) + t;
 #pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const int c = t + h * kBThreads;
-    const float* r = reinterpret_cast<const float*>(raw) + c;
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-      put4(hi, lo, c, 4 * q, r[(4 * q + 0) * kN], r[(4 * q + 1) * kN], r[(4 * q + 2) * kN], r[(4 * q + 3) * kN]);
-  }
+  for (int q = 0; q < 4; q++)
+    put4(hi, lo, t, 4 * q, r[(4 * q + 0) * kN], r[(4 * q + 1) * kN], r[(4 * q + 2) * kN], r[(4 * q + 3) * kN]);
 }
 
 // ---- the two phases' work items -------------------------------------------
@@ -299,6 +314,11 @@ __device__ __forceinline__ void b_producer(const Smem& s, const Ph& ph, int64_t 
   cur.nct = nct;
   cur.ncols = ncols;
   cur.start();
+  // a second cursor kBPrefetch chunks ahead of the copies: its 16 rows are
+  // prefetched into L2 (one row per thread t < 16) when 16-byte aligned
+  BCursor<Ph> pf = cur;
+  if (kBPrefetch == 0) pf.valid = false;
+  for (int i = 0; i < kBPrefetch && pf.valid; i++) pf.advance();
 #pragma unroll
   for (int i = 0; i < kR - 1; i++) {
     if (cur.valid) {
@@ -315,6 +335,11 @@ __device__ __forceinline__ void b_producer(const Smem& s, const Ph& ph, int64_t 
       cur.advance();
     }
     cp_commit();
+    if (pf.valid) {
+      if (t < kK && pf.vec && (pf.nv & 3) == 0 && pf.k0 + t < pf.sg.K)
+        prefetch_l2(pf.base + (int64_t)(pf.k0 + t) * pf.sg.ld, (uint32_t)pf.nv * 4);
+      pf.advance();
+    }
     const int sb = (int)(g % kSB);
     if (g >= kSB) wait_bar(s, EB + sb, (uint32_t)((g / kSB) - 1) & 1);
     split_b(s.braw((int)(g % kR)), s.bc(sb), t);
@@ -338,6 +363,7 @@ __device__ __forceinline__ void a_producer(const Smem& s, const Ph& ph, int64_t 
       if (g >= kSA && !wait_bar(s, EA + sa, (uint32_t)((g / kSA) - 1) & 1)) return;
       umma::mbar_arrive_expect_tx(&s.bar[FA + sa], kAChunkBytes);
       umma::bulk_g2s(s.a(sa), astream + (a0 + c) * (int64_t)kAChunkBytes, kAChunkBytes, &s.bar[FA + sa]);
+      if (kAPrefetch > 0 && c + kAPrefetch < nch) prefetch_l2(astream + (a0 + c + kAPrefetch) * (int64_t)kAChunkBytes, kAChunkBytes);
     }
   }
 }
@@ -459,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
-  if (warp < 4) {
+  if (warp < kBThreads / 32) {
     b_producer(s, ph, ntiles, nct, ncols);
   } else if (warp == kAWarp) {
     if ((threadIdx.x & 31) == 0) a_producer(s, ph, ntiles, nct, astream);
@@ -562,6 +588,8 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
 fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::vector<TcTile>& tiles) {
   fkf_ctx* ctx = h->ctx;
   std::vector<TcAChunk> ch;
+  // phase-1 items are dealt round-robin to persistent CTAs: longest first
+  std::stable_sort(items.begin(), items.end(), [](const P1Item& a, const P1Item& b) { return a.nr > b.nr; });
   for (P1Item& it : items) {
     it.a_chunk0 = (int64_t)ch.size();
     it.nchunk = (int)cdiv(it.nr, kK);
