@@ -78,6 +78,30 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha
   }
 }
 
+// Matrix-vector form of the FP64 GEMM (N = 1): y_i = sum_k op(A)(i, k) x_k,
+// C[i] = alpha y_i + beta C[i].  Rows of A (not transposed): one warp per
+// output, lanes over k, shuffle reduction; columns (transposed): one thread
+// per output, loop over k (coalesced across outputs).
+__global__ void k_gemv_f64(int M, int K, bool ta, double alpha, const double* __restrict__ A, int64_t lda,
+                           const double* __restrict__ x, int64_t incx, double beta, double* __restrict__ C,
+                           int64_t ldc) {
+  if (!ta) {
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= M) return;
+    const double* a = A + (int64_t)i * lda;
+    double s = 0.0;
+    for (int k = lane; k < K; k += 32) s += a[k] * x[(int64_t)k * incx];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) C[(int64_t)i * ldc] = beta == 0.0 ? alpha * s : alpha * s + beta * C[(int64_t)i * ldc];
+  } else {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double s = 0.0;
+    for (int k = 0; k < K; k++) s += A[(int64_t)k * lda + i] * x[(int64_t)k * incx];
+    C[(int64_t)i * ldc] = beta == 0.0 ? alpha * s : alpha * s + beta * C[(int64_t)i * ldc];
+  }
+}
+
 // Partial Gram: part[z] = A[rows z]^T B[rows z] (A: K x M, B: K x N row-major).
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_gram_part(int M, int N, int64_t K, int64_t chunk,
@@ -146,6 +170,14 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
   if (K <= 0) {
     // C = beta C
     return scale_f64(ctx, M, N, beta, C, ldc);
+  }
+  if (N == 1) {
+    // op(B)(k, 0) = B[k * ldb] (tb = false) or B[k] (tb = true)
+    const int64_t incx = tb ? 1 : ldb;
+    const unsigned grid = ta ? (unsigned)cdiv(M, 256) : (unsigned)cdiv(M * 32, 256);
+    k_gemv_f64<<<grid, 256, 0, ctx->stream>>>((int)M, (int)K, ta, alpha, A, lda, B, incx, beta, C, ldc);
+    FKF_LAUNCHED(ctx);
+    return FKF_OK;
   }
   return gemm_impl<double>(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }

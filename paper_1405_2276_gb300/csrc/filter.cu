@@ -67,32 +67,81 @@ __global__ void k_csc_count(int m, const int64_t* __restrict__ rowptr, const int
   }
 }
 
-// exclusive scan of n ints into n+1 int64 (single CTA of 1024 threads)
-__global__ void k_scan(int64_t n, const int* __restrict__ cnt, int64_t* __restrict__ out) {
-  __shared__ int64_t part[1024];
-  const int t = threadIdx.x;
-  const int64_t per = (n + 1023) / 1024;
-  const int64_t a = t * per < n ? t * per : n;
-  const int64_t b = a + per < n ? a + per : n;
-  int64_t s = 0;
-  for (int64_t i = a; i < b; i++) s += cnt[i];
-  part[t] = s;
+// Exclusive scan of n ints into n + 1 int64 (out[n] = total) in three
+// passes over blocks of 1024: block sums, a scan of the block sums, and the
+// block-local scans plus their offsets.
+constexpr int kScanBlock = 1024;
+
+// exclusive scan of v across the CTA (kScanBlock threads); *total = CTA sum
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
   __syncthreads();
-  if (t == 0) {
-    int64_t run = 0;
-    for (int i = 0; i < 1024; i++) {
-      const int64_t v = part[i];
-      part[i] = run;
-      run += v;
+  if (warp == 0) {
+    int64_t w = sh[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
+    sh[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  int64_t run = part[t];
-  for (int64_t i = a; i < b; i++) {
-    out[i] = run;
-    run += cnt[i];
+  const int64_t before = warp > 0 ? sh[warp - 1] : 0;
+  *total = sh[31];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(int64_t n, const int* __restrict__ cnt,
+                                                          int64_t* __restrict__ bsum) {
+  __shared__ int64_t sh[32];
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  int64_t tot;
+  block_excl_scan(i < n ? cnt[i] : 0, sh, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// exclusive scan of the nb block sums in place; bsum[nb] = total (one CTA)
+__global__ void __launch_bounds__(kScanBlock) k_scan_bsums(int64_t nb, int64_t* __restrict__ bsum) {
+  __shared__ int64_t sh[32];
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanBlock) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < nb ? bsum[i] : 0;
+    int64_t tot;
+    const int64_t e = block_excl_scan(v, sh, &tot);
+    if (i < nb) bsum[i] = carry + e;
+    carry += tot;
   }
-  if (t == 1023) out[n] = run;
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_out(int64_t n, const int* __restrict__ cnt,
+                                                         const int64_t* __restrict__ bsum, int64_t nb,
+                                                         int64_t* __restrict__ out) {
+  __shared__ int64_t sh[32];
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  int64_t tot;
+  const int64_t e = block_excl_scan(i < n ? cnt[i] : 0, sh, &tot);
+  if (i < n) out[i] = bsum[blockIdx.x] + e;
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bsum[nb];
+}
+
+static fkf_status scan_counts(fkf_ctx* ctx, int64_t n, const int* cnt, int64_t* out, DevBuf& ws) {
+  const int64_t nb = std::max<int64_t>(1, cdiv(n, kScanBlock));
+  if (ws.bytes < (size_t)(nb + 1) * 8) FKF_TRY(dev_alloc(ctx, ws, (size_t)(nb + 1) * 8));
+  k_scan_sums<<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(n, cnt, ws.as<int64_t>());
+  FKF_LAUNCHED(ctx);
+  k_scan_bsums<<<1, kScanBlock, 0, ctx->stream>>>(nb, ws.as<int64_t>());
+  FKF_LAUNCHED(ctx);
+  k_scan_out<<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(n, cnt, ws.as<int64_t>(), nb, out);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
 }
 
 // Scatter the entries into their columns (warp per row; the order inside a
@@ -624,7 +673,7 @@ struct fkf_filter {
   DevBuf cnt, cursor, colptr, crow, cval;
   // small FP64 buffers
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
-  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws;
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
   cudaEvent_t ev[7] = {};
   double phase_ms[6] = {};
@@ -828,8 +877,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>(),
                                                                 f->flag.as<int>());
   FKF_LAUNCHED(ctx);
-  k_scan<<<1, 1024, 0, st>>>(n, f->cnt.as<int>(), f->colptr.as<int64_t>());
-  FKF_LAUNCHED(ctx);
+  FKF_TRY(scan_counts(ctx, n, f->cnt.as<int>(), f->colptr.as<int64_t>(), f->scanws));
   k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
                                                                f->cursor.as<int>(), f->crow.as<int>(),
                                                                f->cval.as<double>());
@@ -921,7 +969,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     // innovation covariance S = alpha' A - HW D HW^T + R already factored for
     // the mean (S = HW E HW^T + R up to the new_tol residual A - HW HW^T), and
     // HW D already formed for S: one m x m solve with r right-hand sides and
-    // one r x r x m product, no r x r factorisation.
+    // one symmetric r x r x m product, no r x r factorisation.
     double* Ep = f->Ep.as<double>();
     double* Dn2 = f->Dfn.as<double>();
     double* Kt = f->P.as<double>();  // r x m: K^T
@@ -1743,7 +1791,7 @@ static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, 
   if (gy) FKF_CUDA(ctx, cudaMemcpyAsync(gy, gyd.p, (size_t)K * m * 8, cudaMemcpyDeviceToHost, st));
   if (gs0) {
     // dNLL/ds0 = H^T hbar_0 through a column index of H (deterministic order)
-    DevBuf cnt, cursor, colptr, crow, cval, gc, go;
+    DevBuf cnt, cursor, colptr, crow, cval, gc, go, scanws;
     FKF_TRY(dev_alloc(ctx, cnt, n * 4 + 64));
     FKF_TRY(dev_alloc(ctx, cursor, n * 4 + 64));
     FKF_TRY(dev_alloc(ctx, colptr, (n + 1) * 8));
@@ -1757,8 +1805,7 @@ static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, 
     k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), iperm, n,
                                                                   cnt.as<int>(), flag.as<int>());
     FKF_LAUNCHED(ctx);
-    k_scan<<<1, 1024, 0, st>>>(n, cnt.as<int>(), colptr.as<int64_t>());
-    FKF_LAUNCHED(ctx);
+    FKF_TRY(scan_counts(ctx, n, cnt.as<int>(), colptr.as<int64_t>(), scanws));
     k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>(), iperm,
                                                    n, colptr.as<int64_t>(), cursor.as<int>(), crow.as<int>(),
                                                    cval.as<double>());
