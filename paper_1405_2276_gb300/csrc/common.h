@@ -120,6 +120,9 @@ struct P2Leaf {
 // Tensor-core phase-2 tile: 128 consecutive rows (whole leaves packed) and
 // its merged segment list; a segment covers tile rows [row_lo, row_hi) and
 // a_off addresses the A row of tile row row_lo.
+// Tensor-core phase-2 segment: rows [row_lo, row_hi) of the tile times the
+// segment's A block (a_off, lda) and its B operand: K rows starting at the
+// split-vector chunk b_row (of X if near, else of the slot workspace).
 struct TcSeg {
   int64_t a_off;
   int64_t b_row;
@@ -148,6 +151,28 @@ struct TcAChunk {
   int32_t kv, near;
 };
 
+// One 16-row chunk of the split X operand: rows row0 .. row0 + rows - 1 of X
+// (cluster order), zero rows after them.
+struct TcXChunk {
+  int64_t row0;
+  int32_t rows, pad;
+};
+
+// Host-side tensor-core schedule handed from the upload to happly_tc.cu.
+// Phase-1 items: x_row = first X chunk, nchunk = its chunk count; their
+// operator chunks in item_chunks.  slotmap[g] = position (chunk * 16 + row)
+// of the partner of natural slot g in the split slot workspace.
+struct TcUpload {
+  std::vector<P1Item> items;
+  std::vector<std::vector<TcAChunk>> item_chunks;
+  std::vector<P1Reduce> reduces;
+  std::vector<TcTile> tiles;
+  std::vector<TcSeg> segs;
+  std::vector<TcXChunk> xmap;
+  std::vector<int64_t> slotmap;
+  int64_t nz = 0, part_rows = 0;
+};
+
 struct HostHmat;  // host-side build result (hbuild.cpp)
 
 struct fkf_hmat {
@@ -168,9 +193,11 @@ struct fkf_hmat {
   int32_t max_leaf = 0;
   // tensor-core schedules (FP32 operators)
   DevBuf tcp1, tcred, tctile, tcseg, tc_err;
-  std::vector<TcSeg> tcseg_host;  // phase-2 segments (host copy, for the stream builder)
   DevBuf tca;  // split operator streams: 16 KB per chunk (TF32 hi | lo, tensor-core smem layout)
-  int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0;
+  DevBuf tcxmap, tcslot;  // TcXChunk per X chunk; split-workspace position per natural slot
+  DevBuf xsplit, zsplit;  // split X and slot workspace: 32 KB per (chunk, 256-column tile)
+  int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0, n_tcx = 0, n_tcz = 0;
+  int64_t tc_panel = 0;  // columns per tensor-core pass
   int engine = 0;  // 0: SIMT tile engine, 1: tensor cores (tcgen05, FP32 operators only)
   // workspace
   DevBuf zmix, part, xperm, yperm;
@@ -193,10 +220,9 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
 fkf_status hmat_tc_check(fkf_hmat* h);
 void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector<P2Seg>& segs,
                             std::vector<TcTile>& tiles, std::vector<TcSeg>& tsegs);
-// Split operator streams for the tensor-core engine (after fac/nearv are on
-// the device): numbers the chunks of every phase-1 item and phase-2 tile,
-// writes them to h->tca, uploads the work lists.
-fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::vector<TcTile>& tiles);
+// Uploads the tensor-core schedule and writes the split operator streams
+// (after fac/nearv are on the device).
+fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu);
 
 // hbuild.cpp
 fkf_status hmat_build_host(fkf_ctx* ctx, const double* pts, int64_t n, int dim, fkf_matern k, fkf_hparams hp,

@@ -23,6 +23,7 @@
 // so each row block of Y is written once, by one CTA, with no atomics, and
 // X_c is read once per cluster level instead of once per block.
 #include <algorithm>
+#include <unordered_map>
 #include <cstring>
 #include <mutex>
 
@@ -362,49 +363,109 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
       p2.push_back(lf);
     }
   }
-  // tensor-core schedules (FP32 operators): phase-1 slot tiles of 128, phase-2
-  // tiles of 128 consecutive rows with merged segments
-  std::vector<P1Item> tp1;
-  std::vector<TcTile> tiles;
+  // tensor-core schedules (FP32 operators).  The vector operands are split
+  // into TF32 hi/lo chunks of 16 rows before the products: X per leaf (rows
+  // of a leaf padded to a multiple of 16) and the slot workspace per cluster
+  // (its K_c slots padded to a multiple of 16), so every K-chunk of a product
+  // is one contiguous block.  Phase-1 items cover whole leaves (row groups of
+  // at most 2048 rows of a cluster); phase-2 tiles are 128 consecutive rows
+  // with merged segments.
+  TcUpload tu;
   if (h->prec == FKF_FP32) {
-    std::vector<P1Reduce> tp1r;
+    const int L = (int)leaves.size();
+    std::vector<int64_t> xchunk0(L + 1, 0);
+    std::unordered_map<int64_t, int64_t> leaf_by_begin;
+    for (int l = 0; l < L; l++) {
+      const int c = leaves[l];
+      leaf_by_begin[cl[c].begin] = l;
+      xchunk0[l] = (int64_t)tu.xmap.size();
+      for (int64_t r = 0; r < csize(c); r += 16)
+        tu.xmap.push_back(TcXChunk{cl[c].begin + r, (int32_t)std::min<int64_t>(16, csize(c) - r), 0});
+    }
+    xchunk0[L] = (int64_t)tu.xmap.size();
+    std::vector<int64_t> zchunk0(nc, -1), tcpos(std::max<int64_t>(ktot, 1), 0);
+    std::unordered_map<int64_t, int64_t> z_by_slot_base;
+    int64_t nz = 0;
+    for (int c = 0; c < nc; c++) {
+      if (K[c] == 0) continue;
+      zchunk0[c] = nz;
+      z_by_slot_base[slot_base[c]] = nz;
+      for (int64_t q = 0; q < K[c]; q++) tcpos[slot_base[c] + q] = nz * 16 + q;
+      nz += cdiv(K[c], 16);
+    }
+    tu.nz = nz;
+    tu.slotmap.resize(std::max<int64_t>(ktot, 1), 0);
+    for (int64_t g = 0; g < ktot; g++) tu.slotmap[g] = tcpos[smap[g]];
+    // leaf range of a cluster (its leaves are consecutive in cluster order)
+    auto leaf_range = [&](int c, int& la, int& lb) {
+      int a = c, b = c;
+      while (cl[a].child[0] >= 0) a = cl[a].child[0];
+      while (cl[b].child[1] >= 0) b = cl[b].child[1];
+      la = leaf_id[a];
+      lb = leaf_id[b] + 1;
+    };
     int64_t tparts = 0;
     for (int c = 0; c < nc; c++) {
       if (K[c] == 0) continue;
-      const int64_t nr = csize(c);
-      const int nch = (int)cdiv(nr, kChunkRows);
+      int la, lb;
+      leaf_range(c, la, lb);
+      std::vector<std::pair<int, int>> groups;  // leaf ranges of at most kChunkRows rows
+      for (int l = la; l < lb;) {
+        int e = l;
+        int64_t rows = 0;
+        while (e < lb && (e == l || rows + csize(leaves[e]) <= kChunkRows)) rows += csize(leaves[e++]);
+        groups.push_back({l, e});
+        l = e;
+      }
+      const int ng = (int)groups.size();
       for (int64_t q0 = 0; q0 < K[c]; q0 += 128) {
         const int nq = (int)std::min<int64_t>(128, K[c] - q0);
         const int64_t base = tparts;
-        for (int ch = 0; ch < nch; ch++) {
+        for (int g = 0; g < ng; g++) {
           P1Item it{};
           it.fac_off = fac_off[c];
-          it.r0 = ch * kChunkRows;
-          it.nr = (int)std::min<int64_t>(kChunkRows, nr - it.r0);
-          it.x_row = cl[c].begin + it.r0;
-          it.out_row = nch == 1 ? -1 : base + (int64_t)ch * nq;
+          it.x_row = xchunk0[groups[g].first];  // first X chunk
+          it.nchunk = (int)(xchunk0[groups[g].second] - xchunk0[groups[g].first]);
+          it.out_row = ng == 1 ? -1 : base + (int64_t)g * nq;
           it.map_off = slot_base[c] + q0;
           it.K = (int)K[c];
           it.q0 = (int)q0;
           it.nq = nq;
-          tp1.push_back(it);
+          tu.items.push_back(it);
+          // operator chunks: the item's leaves, 16 rows at a time
+          std::vector<TcAChunk> ch;
+          for (int l = groups[g].first; l < groups[g].second; l++) {
+            const int lc = leaves[l];
+            for (int64_t r = 0; r < csize(lc); r += 16) {
+              TcAChunk a{};
+              a.src_off = fac_off[c] + (cl[lc].begin - cl[c].begin + r) * K[c] + q0;
+              a.si = 1;
+              a.sk = (int32_t)K[c];
+              a.row_lo = 0;
+              a.row_hi = nq;
+              a.kv = (int32_t)std::min<int64_t>(16, csize(lc) - r);
+              a.near = 0;
+              ch.push_back(a);
+            }
+          }
+          tu.item_chunks.push_back(std::move(ch));
         }
-        if (nch > 1) {
-          tp1r.push_back(P1Reduce{base, slot_base[c] + q0, nq, nch});
-          tparts += (int64_t)nch * nq;
+        if (ng > 1) {
+          tu.reduces.push_back(P1Reduce{base, slot_base[c] + q0, nq, ng});
+          tparts += (int64_t)ng * nq;
         }
       }
     }
-    std::vector<TcSeg> tsegs;
-    hmat_build_tc_schedule(p2, segs, tiles, tsegs);
-    if (!tp1r.empty()) FKF_TRY(dev_upload(ctx, h->tcred, tp1r.data(), tp1r.size() * sizeof(P1Reduce)));
-    FKF_TRY(dev_upload(ctx, h->tcseg, tsegs.data(), std::max<size_t>(tsegs.size(), 1) * sizeof(TcSeg)));
-    h->tcseg_host = std::move(tsegs);
-    h->n_tcp1 = (int64_t)tp1.size();
-    h->n_tcred = (int64_t)tp1r.size();
-    h->n_tctile = (int64_t)tiles.size();
-    h->tc_part_rows = std::max(tparts, part_rows);
-    h->engine = 1;
+    hmat_build_tc_schedule(p2, segs, tu.tiles, tu.segs);
+    // B operands of the phase-2 segments as chunk indices
+    for (TcSeg& sg : tu.segs) {
+      if (sg.near) {
+        sg.b_row = xchunk0[leaf_by_begin.at(sg.b_row)];
+      } else {
+        sg.b_row = z_by_slot_base.at(sg.b_row);
+      }
+    }
+    tu.part_rows = std::max(tparts, part_rows);
   }
   // upload
   std::vector<char> tmp;
@@ -419,7 +480,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   FKF_TRY(upload_vals(h->fac, facv));
   FKF_TRY(upload_vals(h->nearv, nearv));
   std::vector<char>().swap(tmp);
-  if (h->prec == FKF_FP32) FKF_TRY(hmat_build_tc_streams(h, tp1, tiles));
+  if (h->prec == FKF_FP32) FKF_TRY(hmat_upload_tc(h, tu));
   FKF_TRY(dev_upload(ctx, h->slotmap, smap.data(), smap.size() * sizeof(int64_t)));
   if (!p1.empty()) FKF_TRY(dev_upload(ctx, h->p1items, p1.data(), p1.size() * sizeof(P1Item)));
   if (!p1r.empty()) FKF_TRY(dev_upload(ctx, h->p1red, p1r.data(), p1r.size() * sizeof(P1Reduce)));

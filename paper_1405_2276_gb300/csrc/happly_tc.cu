@@ -4,25 +4,27 @@
 // hi = tf32(x) and lo = tf32(x - hi), and each product is accumulated as
 // hi*hi + hi*lo + lo*hi (3xTF32), which keeps FP32-level accuracy.
 //
-// The operator side (A) is split once, when the operator is built: every
-// phase-1 item and every phase-2 tile owns a stream of 16 KB chunks (a
-// 128 x 16 TF32 hi block and its lo block, already in the tensor core's
-// shared-memory layout), so a chunk reaches shared memory with one bulk copy.
-// The vector side (B: rows of X or of the slot workspace) is copied as FP32
-// with cp.async and split in shared memory by four producer warps.
+// Both operands reach shared memory already split, in the tensor core's
+// K-major core-matrix layout, one bulk copy per operand and K-chunk of 16:
+//   * the operator (A): split once when the operator is built, as one stream
+//     of 16 KB chunks (128 x 16 TF32 hi block, then lo) per phase-1 item and
+//     per phase-2 tile;
+//   * the vectors (B): X is split per column pass into 16-row chunks per leaf
+//     (rows padded to a multiple of 16), and phase 1 writes its products
+//     straight into the split slot workspace (16-slot chunks per cluster);
+//     a chunk is 32 KB per 256-column tile (hi, then lo).
 //
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-7  B producers: cp.async kR-1 chunks ahead (kR raw stages),
-//              split into three hi/lo stages, arrive on full_b;
-//   warp 8     A producer (one thread): bulk copies into four stages, full_a;
-//   warp 9     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
-//              products), commits to empty_a / empty_b, and to acc_full after
-//              a tile's last chunk; also allocates and frees TMEM;
-//   warps 10-13 epilogue: tcgen05.ld of the finished accumulator, stores,
+//   warp 0     producer (one thread): two bulk copies per chunk into one of
+//              four stages, completion counted in bytes on full[s];
+//   warp 1     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
+//              products), commits to empty[s], and to acc_full after a
+//              tile's last chunk; also allocates and frees TMEM;
+//   warps 2-5  epilogue: tcgen05.ld of the finished accumulator, stores,
 //              arrive on acc_empty.
 // Two accumulators (2 x 256 TMEM columns) let the epilogue of one tile run
 // under the MMAs of the next.  Tiles are dealt round-robin over the CTAs, the
-// column tiles of one work item consecutively (they share its A stream
+// column tiles of one work item consecutively (they share its operator chunks
 // through L2).  Every mbarrier wait is bounded: an expired wait sets a flag,
 // every role leaves its loop, the MMA issuer waits (bounded) for its
 // outstanding MMAs, TMEM is freed and the host sees the error flag.
@@ -32,15 +34,9 @@
 #include "common.h"
 #include "umma.cuh"
 
-// Pipeline depths (compile-time tuning knobs).
-#ifndef FKF_TC_RAW_STAGES
-#define FKF_TC_RAW_STAGES 3
-#endif
-#ifndef FKF_TC_A_PREFETCH
-#define FKF_TC_A_PREFETCH 0
-#endif
-#ifndef FKF_TC_B_PREFETCH
-#define FKF_TC_B_PREFETCH 0
+// Pipeline depth (compile-time tuning knob).
+#ifndef FKF_TC_STAGES
+#define FKF_TC_STAGES 4
 #endif
 
 namespace {
@@ -50,24 +46,20 @@ constexpr int kN = 256;                    // tile columns = MMA N
 constexpr int kK = umma::kChunk;           // 16: K per chunk
 constexpr int kABytes = kM * kK * 4;       // 8 KB: one TF32 half of an A chunk
 constexpr int kAChunkBytes = 2 * kABytes;  // 16 KB: hi | lo
-constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk, or the raw FP32 chunk
-constexpr int kSA = 4;                     // A stages
-constexpr int kSB = 3;                     // split B stages
-constexpr int kR = FKF_TC_RAW_STAGES;      // raw B stages
-constexpr int kAPrefetch = FKF_TC_A_PREFETCH;  // A chunks prefetched into L2 ahead of their copy (0: none)
-constexpr int kBPrefetch = FKF_TC_B_PREFETCH;  // B chunks prefetched into L2 ahead of their copy (0: none)
-constexpr int kSmemBytes = kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes + 256;  // 208.25 KB (kR = 3)
+constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk
+constexpr int kBChunkBytes = 2 * kBBytes;  // 32 KB: hi | lo
+constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;  // 48 KB
+constexpr int kS = FKF_TC_STAGES;
+constexpr int kSmemBytes = kS * kStageBytes + 256;  // 192.25 KB for 4 stages
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
-constexpr int kBThreads = 256;             // warps 0-7: B producers, one column each
-constexpr int kAWarp = 8, kMmaWarp = 9;    // warps 10-13: epilogue
-constexpr int kThreads = 448;
+constexpr int kProdWarp = 0, kMmaWarp = 1;  // warps 2-5: epilogue
+constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kN;
 constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
 
 // barrier indices
-constexpr int FA = 0, EA = FA + kSA, FB = EA + kSA, EB = FB + kSB, AF = EB + kSB, AE = AF + 2, FIN = AE + 2,
-              NBAR = FIN + 1;
+constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, NBAR = FIN + 1;
 static_assert(NBAR * 8 <= 192, "barrier area");
 
 struct Smem {
@@ -75,11 +67,8 @@ struct Smem {
   uint64_t* bar;
   uint32_t* tmem_slot;
   int* fail;
-  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kAChunkBytes; }
-  __device__ __forceinline__ uint8_t* bc(int s) const { return base + kSA * kAChunkBytes + s * 2 * kBBytes; }
-  __device__ __forceinline__ uint8_t* braw(int s) const {
-    return base + kSA * kAChunkBytes + kSB * 2 * kBBytes + s * kBBytes;
-  }
+  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kStageBytes; }
+  __device__ __forceinline__ uint8_t* b(int s) const { return base + s * kStageBytes + kAChunkBytes; }
   __device__ __forceinline__ bool failed() const { return *reinterpret_cast<volatile int*>(fail) != 0; }
   __device__ __forceinline__ void set_fail() const { atomicExch(fail, 1); }
 };
@@ -87,7 +76,7 @@ struct Smem {
 __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   Smem s;
   s.base = base;
-  uint8_t* tail = base + kSA * kAChunkBytes + kSB * 2 * kBBytes + kR * kBBytes;
+  uint8_t* tail = base + kS * kStageBytes;
   s.bar = reinterpret_cast<uint64_t*>(tail);
   s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 192);
   s.fail = reinterpret_cast<int*>(tail + 224);
@@ -100,270 +89,125 @@ __device__ __forceinline__ bool wait_bar(const Smem& s, int i, uint32_t parity) 
   return false;
 }
 
-// ---- B side: cp.async of FP32 chunks, split in shared memory ----------------
-__device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(umma::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// L2 prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global address
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Barrier over the B-producer warps (named barrier 1) that also ORs a
-// predicate across them, so that all of them take the same exit decision.
-__device__ __forceinline__ bool bar_or_b(bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.b32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 256, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)pred)
-      : "memory");
-  return r != 0;
-}
-
-// A quad (4 floats) of `valid` leading elements from src into dst (16 bytes);
-// src is read only where valid, the missing elements are stored as zeros.
-__device__ __forceinline__ void copy_quad(void* dst, const float* src, int valid, bool vec) {
-  if (valid <= 0) {
-    *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-  } else if (vec) {
-    cp16(dst, src, 4 * min(valid, 4));
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      float* d = reinterpret_cast<float*>(dst) + u;
-      if (u < valid)
-        cp4(d, src + u);
-      else
-        *d = 0.f;
-    }
-  }
-}
-
-// Raw B chunk: 16 rows (k) x 256 floats, quad q of row k at byte k * 1024 + q * 16.
-// Copies of P(k, c) = P[(k0 + k) * ld + c] for k0 + k < kv, c < cv; thread t of kBThreads.
-__device__ __forceinline__ void issue_b(uint8_t* raw, const float* P, int64_t ld, int cv, int k0, int kv, bool vec,
-                                        int t) {
-#pragma unroll
-  for (int j = 0; j < (kK * kN / 4) / kBThreads; j++) {
-    const int i = t + j * kBThreads;
-    const int k = i / (kN / 4), q = i % (kN / 4);
-    const bool kvld = k0 + k < kv;
-    const int valid = kvld ? cv - 4 * q : 0;
-    copy_quad(raw + k * (kN * 4) + q * 16, P + (int64_t)(kvld ? k0 + k : 0) * ld + 4 * q, valid, vec);
-  }
+// ---- splitting into the tensor-core layout ----------------------------------
+__device__ __forceinline__ void split4(float v0, float v1, float v2, float v3, uint4& h, uint4& l) {
+  umma::split_tf32(v0, h.x, l.x);
+  umma::split_tf32(v1, h.y, l.y);
+  umma::split_tf32(v2, h.z, l.z);
+  umma::split_tf32(v3, h.w, l.w);
 }
 
 __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
                                      float v3) {
   uint4 h, l;
-  umma::split_tf32(v0, h.x, l.x);
-  umma::split_tf32(v1, h.y, l.y);
-  umma::split_tf32(v2, h.z, l.z);
-  umma::split_tf32(v3, h.w, l.w);
+  split4(v0, v1, v2, v3, h, l);
   const uint32_t off = umma::chunk_offset(row, k);
   *reinterpret_cast<uint4*>(hi_base + off) = h;
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
-// Column t of a raw chunk -> (row = t, k = 0..15) of the split stage.  A
-// warp reads 32 consecutive floats per k and writes 8 distinct rows per
-// quarter-warp (no bank conflicts).
-__device__ __forceinline__ void split_b(const uint8_t* raw, uint8_t* conv, int t) {
-  static_assert(kBThreads == kN, "one B-producer thread per column");
-  uint8_t* hi = conv;
-  uint8_t* lo = conv + kBBytes;
-  const float* r = reinterpret_cast<const float*>(raw) + t;
+// One value into a split B chunk (row = column n of the tile, k = row in chunk).
+__device__ __forceinline__ void put1(uint8_t* chunk, int n, int k, float v) {
+  uint32_t h, l;
+  umma::split_tf32(v, h, l);
+  const uint32_t off = umma::chunk_offset(n, k);
+  *reinterpret_cast<uint32_t*>(chunk + off) = h;
+  *reinterpret_cast<uint32_t*>(chunk + kBBytes + off) = l;
+}
+
+// Split X: chunk x (blockIdx.x) of 16 rows (xmap), column tile ct (blockIdx.y)
+// of 256 columns -> 32 KB at out + (x * nct + ct) * 32 KB.  Thread units are
+// (column n, rows 4kq..4kq+3): a warp reads 32 consecutive floats of a row and
+// writes 512 contiguous bytes per half.
+__global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X, int64_t ldx, int ncols,
+                                                    const TcXChunk* __restrict__ xmap, int nct,
+                                                    uint8_t* __restrict__ out) {
+  const TcXChunk xc = xmap[blockIdx.x];
+  const int ct = blockIdx.y;
+  uint8_t* chunk = out + ((int64_t)blockIdx.x * nct + ct) * kBChunkBytes;
 #pragma unroll
-  for (int q = 0; q < 4; q++)
-    put4(hi, lo, t, 4 * q, r[(4 * q + 0) * kN], r[(4 * q + 1) * kN], r[(4 * q + 2) * kN], r[(4 * q + 3) * kN]);
+  for (int i = 0; i < 4; i++) {
+    const int u = threadIdx.x + 256 * i;
+    const int n = u & (kN - 1), kq = u >> 8;
+    const int col = ct * kN + n;
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int k = 4 * kq + j;
+      v[j] = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] : 0.f;
+    }
+    put4(chunk, chunk + kBBytes, n, 4 * kq, v[0], v[1], v[2], v[3]);
+  }
 }
 
 // ---- the two phases' work items -------------------------------------------
-struct BSeg {
-  const float* p;  // first row of the segment's B rows
-  int64_t ld;
-  int K;
-};
-
-// Phase 2: tiles of 128 consecutive rows; B segments = slot rows of the slot
-// workspace (far) or rows of X (near); output rows of Y.
+// Phase 2: tiles of 128 consecutive rows; B segments = chunks of the split
+// slot workspace (far) or of the split X (near); output rows of Y.
 struct Ph2 {
   const TcTile* tiles;
   const TcSeg* segs;
-  const float* zmix;
-  int64_t ldz;
-  const float* X;
-  int64_t ldx;
+  const uint8_t* zsplit;
+  const uint8_t* xsplit;
   float* Y;
   int64_t ldy;
   __device__ __forceinline__ int nchunk(int64_t w) const { return tiles[w].nchunk; }
   __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return tiles[w].a_chunk0; }
   __device__ __forceinline__ int nseg(int64_t w) const { return tiles[w].nseg; }
-  __device__ __forceinline__ BSeg seg(int64_t w, int j) const {
+  // B chunks of segment j: base array, first chunk, count
+  __device__ __forceinline__ const uint8_t* seg(int64_t w, int j, int64_t& c0, int& nc) const {
     const TcSeg sg = segs[tiles[w].seg0 + j];
-    if (sg.near) return BSeg{X + sg.b_row * ldx, ldx, sg.K};
-    return BSeg{zmix + sg.b_row * ldz, ldz, sg.K};
-  }
-  __device__ __forceinline__ float* row_ptr(int64_t w, int row) const {
-    const TcTile& t = tiles[w];
-    return row < t.rows ? Y + (t.row0 + row) * ldy : nullptr;
+    c0 = sg.b_row;
+    nc = (sg.K + kK - 1) / kK;
+    return sg.near ? xsplit : zsplit;
   }
 };
 
-// Phase 1: items (cluster, 128-slot tile, <= 2048-row chunk); one B segment
-// (the chunk's rows of X); output slot rows scattered through the slot map,
-// or partial rows when the cluster is split into several row chunks.
+// Phase 1: items (cluster, 128-slot tile, group of whole leaves); one B
+// segment (the leaves' X chunks); output slot rows into the split slot
+// workspace through the slot map, or partial rows when the cluster has
+// several leaf groups.
 struct Ph1 {
   const P1Item* items;
-  const float* X;
-  int64_t ldx;
-  const int64_t* slotmap;
-  float* zmix;
+  const uint8_t* xsplit;
+  const int64_t* slotpos;
+  uint8_t* zsplit;
   float* part;
-  int64_t ldz;
+  int64_t ldp;
   __device__ __forceinline__ int nchunk(int64_t w) const { return items[w].nchunk; }
   __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return items[w].a_chunk0; }
   __device__ __forceinline__ int nseg(int64_t) const { return 1; }
-  __device__ __forceinline__ BSeg seg(int64_t w, int) const {
+  __device__ __forceinline__ const uint8_t* seg(int64_t w, int, int64_t& c0, int& nc) const {
     const P1Item& it = items[w];
-    return BSeg{X + it.x_row * ldx, ldx, it.nr};
-  }
-  __device__ __forceinline__ float* row_ptr(int64_t w, int row) const {
-    const P1Item& it = items[w];
-    if (row >= it.nq) return nullptr;
-    return it.out_row < 0 ? zmix + slotmap[it.map_off + row] * ldz : part + (it.out_row + row) * ldz;
-  }
-};
-
-// Walks this CTA's B chunks in order (tiles blockIdx.x, + gridDim.x, ...; in
-// each, its segments' K-chunks), skipping tiles without chunks.
-template <class Ph>
-struct BCursor {
-  const Ph* ph;
-  int64_t ntiles;
-  int nct, ncols;
-  int64_t id, w;
-  int j, nseg, k0, nv;
-  BSeg sg;
-  const float* base;
-  bool vec, valid;
-
-  __device__ __forceinline__ bool find_seg() {
-    for (; j < nseg; j++) {
-      sg = ph->seg(w, j);
-      if (sg.K > 0) {
-        const int n0 = (int)(id % nct) * kN;
-        base = sg.p + n0;
-        vec = (sg.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(base) & 15) == 0);
-        return true;
-      }
-    }
-    return false;
-  }
-  __device__ __forceinline__ void enter() {
-    valid = false;
-    for (; id < ntiles; id += gridDim.x) {
-      w = id / nct;
-      nv = min(kN, ncols - (int)(id % nct) * kN);
-      nseg = ph->nseg(w);
-      j = 0;
-      k0 = 0;
-      if (find_seg()) {
-        valid = true;
-        return;
-      }
-    }
-  }
-  __device__ __forceinline__ void start() {
-    id = blockIdx.x;
-    enter();
-  }
-  __device__ __forceinline__ void advance() {
-    k0 += kK;
-    if (k0 < sg.K) return;
-    k0 = 0;
-    j++;
-    if (find_seg()) return;
-    id += gridDim.x;
-    enter();
+    c0 = it.x_row;
+    nc = it.nchunk;
+    return xsplit;
   }
 };
 
 // ---- roles -----------------------------------------------------------------
 template <class Ph>
-__device__ __forceinline__ void b_producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols) {
-  const int t = threadIdx.x;
-  int64_t total = 0;
-  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) total += ph.nchunk(id / nct);
-  BCursor<Ph> cur;
-  cur.ph = &ph;
-  cur.ntiles = ntiles;
-  cur.nct = nct;
-  cur.ncols = ncols;
-  cur.start();
-  // a second cursor kBPrefetch chunks ahead of the copies: its 16 rows are
-  // prefetched into L2 (one row per thread t < 16) when 16-byte aligned
-  BCursor<Ph> pf = cur;
-  if (kBPrefetch == 0) pf.valid = false;
-  for (int i = 0; i < kBPrefetch && pf.valid; i++) pf.advance();
-#pragma unroll
-  for (int i = 0; i < kR - 1; i++) {
-    if (cur.valid) {
-      issue_b(s.braw(i), cur.base, cur.sg.ld, cur.nv, cur.k0, cur.sg.K, cur.vec, t);
-      cur.advance();
-    }
-    cp_commit();
-  }
-  for (int64_t g = 0; g < total; g++) {
-    cp_wait<kR - 2>();  // this thread's copies of chunk g have landed
-    if (bar_or_b(s.failed())) break;  // everyone's copies of g have landed; raw stage of g-1 is free
-    if (cur.valid) {
-      issue_b(s.braw((int)((g + kR - 1) % kR)), cur.base, cur.sg.ld, cur.nv, cur.k0, cur.sg.K, cur.vec, t);
-      cur.advance();
-    }
-    cp_commit();
-    if (pf.valid) {
-      if (t < kK && pf.vec && (pf.nv & 3) == 0 && pf.k0 + t < pf.sg.K)
-        prefetch_l2(pf.base + (int64_t)(pf.k0 + t) * pf.sg.ld, (uint32_t)pf.nv * 4);
-      pf.advance();
-    }
-    const int sb = (int)(g % kSB);
-    if (g >= kSB) wait_bar(s, EB + sb, (uint32_t)((g / kSB) - 1) & 1);
-    split_b(s.braw((int)(g % kR)), s.bc(sb), t);
-    umma::fence_proxy_async();
-    umma::mbar_arrive(&s.bar[FB + sb]);
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-template <class Ph>
-__device__ __forceinline__ void a_producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct,
-                                           const uint8_t* astream) {
+__device__ __forceinline__ void producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct,
+                                         const uint8_t* astream) {
   int64_t g = 0;
   for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) {
     const int64_t w = id / nct;
-    const int nch = ph.nchunk(w);
-    const int64_t a0 = ph.a_chunk0(w);
-    for (int c = 0; c < nch; c++, g++) {
-      if (s.failed()) return;
-      const int sa = (int)(g % kSA);
-      if (g >= kSA && !wait_bar(s, EA + sa, (uint32_t)((g / kSA) - 1) & 1)) return;
-      umma::mbar_arrive_expect_tx(&s.bar[FA + sa], kAChunkBytes);
-      umma::bulk_g2s(s.a(sa), astream + (a0 + c) * (int64_t)kAChunkBytes, kAChunkBytes, &s.bar[FA + sa]);
-      if (kAPrefetch > 0 && c + kAPrefetch < nch) prefetch_l2(astream + (a0 + c + kAPrefetch) * (int64_t)kAChunkBytes, kAChunkBytes);
+    const int ct = (int)(id % nct);
+    const uint8_t* ap = astream + ph.a_chunk0(w) * (int64_t)kAChunkBytes;
+    const int ns = ph.nseg(w);
+    for (int j = 0; j < ns; j++) {
+      int64_t c0;
+      int nc;
+      const uint8_t* bsrc = ph.seg(w, j, c0, nc);
+      for (int c = 0; c < nc; c++, g++) {
+        if (s.failed()) return;
+        const int st = (int)(g % kS);
+        if (g >= kS && !wait_bar(s, EMPTY + st, (uint32_t)((g / kS) - 1) & 1)) return;
+        umma::mbar_arrive_expect_tx(&s.bar[FULL + st], kStageBytes);
+        umma::bulk_g2s(s.a(st), ap, kAChunkBytes, &s.bar[FULL + st]);
+        umma::bulk_g2s(s.b(st), bsrc + ((c0 + c) * nct + ct) * (int64_t)kBChunkBytes, kBChunkBytes,
+                       &s.bar[FULL + st]);
+        ap += kAChunkBytes;
+      }
     }
   }
 }
@@ -393,16 +237,14 @@ __device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t 
     umma::fence_after_sync();
     const uint32_t acc = tmem + (uint32_t)(b * kN);
     for (int c = 0; c < nch; c++, g++) {
-      const int sa = (int)(g % kSA), sb = (int)(g % kSB);
-      if (s.failed() || !wait_bar(s, FA + sa, (uint32_t)(g / kSA) & 1) ||
-          !wait_bar(s, FB + sb, (uint32_t)(g / kSB) & 1)) {
+      const int st = (int)(g % kS);
+      if (s.failed() || !wait_bar(s, FULL + st, (uint32_t)(g / kS) & 1)) {
         ok = false;
         break;
       }
       umma::fence_after_sync();
-      issue_mma(s.a(sa), s.bc(sb), acc, c == 0);
-      umma::commit(&s.bar[EA + sa]);
-      umma::commit(&s.bar[EB + sb]);
+      issue_mma(s.a(st), s.b(st), acc, c == 0);
+      umma::commit(&s.bar[EMPTY + st]);
     }
     if (!ok) break;
     if (nch > 0)
@@ -415,9 +257,31 @@ __device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t 
   wait_bar(s, FIN, 0);
 }
 
+// Epilogue stores of one row's 32 columns [c0, c0 + 32) of a tile.
+struct RowSinkY {  // phase 2: a row of Y
+  float* dst;
+  __device__ __forceinline__ void put(int c0, int nv, const float (&v)[32]) const {
+    if (!dst) return;
+    if (((reinterpret_cast<uintptr_t>(dst + c0) & 15) == 0) && c0 + 32 <= nv) {
+#pragma unroll
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; i++)
+        if (c0 + i < nv) dst[c0 + i] = v[i];
+    }
+  }
+};
+
 template <class Ph>
 __device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols,
-                                         uint32_t tmem) {
+                                         uint32_t tmem);
+
+// phase 2: rows of Y
+template <>
+__device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int64_t ntiles, int nct, int ncols,
+                                              uint32_t tmem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
   const int row = 32 * quarter + lane;
@@ -430,10 +294,9 @@ __device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t nt
     const int64_t w = id / nct;
     const int n0 = (int)(id % nct) * kN;
     const int nv = min(kN, ncols - n0);
-    const bool zero = ph.nchunk(w) == 0;
-    float* dst = ph.row_ptr(w, row);
-    if (dst) dst += n0;
-    const bool vec4 = dst && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+    const TcTile& t = ph.tiles[w];
+    const bool zero = t.nchunk == 0;
+    const RowSinkY sink{row < t.rows ? ph.Y + (t.row0 + row) * ph.ldy + n0 : nullptr};
 #pragma unroll 1
     for (int j = 0; j < kN / 32; j++) {
       float v[32];
@@ -443,17 +306,59 @@ __device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t nt
       } else {
         umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
       }
-      if (dst) {
-        const int c0 = 32 * j;
-        if (vec4 && c0 + 32 <= nv) {
+      sink.put(32 * j, nv, v);
+    }
+    umma::fence_before_sync();
+    umma::mbar_arrive(&s.bar[AE + b]);
+  }
+}
+
+// phase 1: slot rows into the split slot workspace, or partial rows
+template <>
+__device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int64_t ntiles, int nct, int ncols,
+                                              uint32_t tmem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3;
+  const int row = 32 * quarter + lane;
+  int tl = 0;
+  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
+    const int b = tl & 1;
+    if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    umma::fence_after_sync();
+    if (s.failed()) break;
+    const int64_t w = id / nct;
+    const int ct = (int)(id % nct);
+    const int n0 = ct * kN;
+    const int nv = min(kN, ncols - n0);
+    const P1Item& it = ph.items[w];
+    const bool valid = row < it.nq;
+    RowSinkY psink{nullptr};
+    uint8_t* zchunk = nullptr;
+    int srow = 0;
+    if (valid) {
+      if (it.out_row >= 0) {
+        psink.dst = ph.part + (it.out_row + row) * ph.ldp + n0;
+      } else {
+        const int64_t p = ph.slotpos[it.map_off + row];
+        zchunk = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)kBChunkBytes;
+        srow = (int)(p & 15);
+      }
+    }
+    const bool zero = it.nchunk == 0;
+#pragma unroll 1
+    for (int j = 0; j < kN / 32; j++) {
+      float v[32];
+      if (zero) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else {
+        for (int i = 0; i < 32; i++) v[i] = 0.f;
+      } else {
+        umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
+      }
+      psink.put(32 * j, nv, v);
+      if (zchunk) {
 #pragma unroll
-          for (int i = 0; i < 32; i++)
-            if (c0 + i < nv) dst[c0 + i] = v[i];
-        }
+        for (int i = 0; i < 32; i++)
+          if (32 * j + i < nv) put1(zchunk, 32 * j + i, srow, v[i]);
       }
     }
     umma::fence_before_sync();
@@ -470,10 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5;
   const int64_t ntiles = nwork * nct;
   if (threadIdx.x == 0) {
-    for (int i = FA; i < EA; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = EA; i < FB; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = FB; i < EB; i++) umma::mbar_init(&s.bar[i], kBThreads);
-    for (int i = EB; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = FULL; i < EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = EMPTY; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = AF; i < AE; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 128);
     umma::mbar_init(&s.bar[FIN], 1);
@@ -485,15 +388,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
-  if (warp < kBThreads / 32) {
-    b_producer(s, ph, ntiles, nct, ncols);
-  } else if (warp == kAWarp) {
-    if ((threadIdx.x & 31) == 0) a_producer(s, ph, ntiles, nct, astream);
+  if (warp == kProdWarp) {
+    if ((threadIdx.x & 31) == 0) producer(s, ph, ntiles, nct, astream);
   } else if (warp == kMmaWarp) {
     if ((threadIdx.x & 31) == 0) mma_issuer(s, ph, ntiles, nct, tmem);
     __syncwarp();
   } else {
-    epilogue(s, ph, ntiles, nct, ncols, tmem);
+    epilogue<Ph>(s, ph, ntiles, nct, ncols, tmem);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -528,16 +429,19 @@ __global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const fl
   }
 }
 
-__global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const float* __restrict__ part,
-                                   const int64_t* __restrict__ slotmap, float* __restrict__ zmix, int64_t ldz,
+// Sum the partials of a cluster split into several leaf groups and write the
+// slot rows into the split slot workspace.
+__global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const float* __restrict__ part, int64_t ldp,
+                                   const int64_t* __restrict__ slotpos, uint8_t* __restrict__ zsplit, int nct,
                                    int ncols) {
   const P1Reduce it = items[blockIdx.x];
   const int64_t total = (int64_t)it.nq * ncols;
   for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total; e += (int64_t)blockDim.x * gridDim.y) {
     const int q = (int)(e / ncols), n = (int)(e % ncols);
     float acc = 0.f;
-    for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldz + n];
-    zmix[slotmap[it.map_off + q] * ldz + n] = acc;
+    for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldp + n];
+    const int64_t p = slotpos[it.map_off + q];
+    put1(zsplit + ((p >> 4) * nct + n / kN) * (int64_t)kBChunkBytes, n % kN, (int)(p & 15), acc);
   }
 }
 
@@ -546,9 +450,16 @@ __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const flo
 // Tensor-core apply for an FP32 operator (cluster order).
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
   fkf_ctx* ctx = h->ctx;
-  const int64_t P = h->panel;
-  const size_t zbytes = (size_t)std::max<int64_t>(h->ktot, 1) * P * sizeof(float);
-  if (h->zmix.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zmix, zbytes));
+  const int64_t P = h->tc_panel;
+  const int64_t nct_max = cdiv(P, kN);
+  const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * kBChunkBytes;
+  if (h->xsplit.bytes < xbytes) FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
+  const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * kBChunkBytes;
+  if (h->zsplit.bytes < zbytes) {
+    // padding slots of the split workspace are never written: they start (and stay) zero
+    FKF_TRY(dev_alloc(ctx, h->zsplit, zbytes));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, zbytes, ctx->stream));
+  }
   const size_t pbytes = (size_t)std::max<int64_t>(h->tc_part_rows, 1) * P * sizeof(float);
   if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
   if (h->tc_err.bytes < 64) {
@@ -563,8 +474,13 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
     const int nct = (int)cdiv(nc, kN);
+    if (h->n_tcx > 0) {
+      k_tc_split_x<<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
+          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), nct, h->xsplit.as<uint8_t>());
+      FKF_LAUNCHED(ctx);
+    }
     if (h->n_tcp1 > 0) {
-      const Ph1 ph{h->tcp1.as<P1Item>(), X + c0, ldx, h->slotmap.as<int64_t>(), h->zmix.as<float>(),
+      const Ph1 ph{h->tcp1.as<P1Item>(), h->xsplit.as<uint8_t>(), h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
                    h->part.as<float>(), P};
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
       k_tc_apply<Ph1><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream,
@@ -573,10 +489,11 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     }
     if (h->n_tcred > 0) {
       k_phase1_reduce_tc<<<dim3((unsigned)h->n_tcred, 4), 256, 0, ctx->stream>>>(
-          h->tcred.as<P1Reduce>(), h->part.as<float>(), h->slotmap.as<int64_t>(), h->zmix.as<float>(), P, nc);
+          h->tcred.as<P1Reduce>(), h->part.as<float>(), P, h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(), nct, nc);
       FKF_LAUNCHED(ctx);
     }
-    const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zmix.as<float>(), P, X + c0, ldx, Y + c0, ldy};
+    const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
+                 Y + c0, ldy};
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
     k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream,
                                                                  h->tc_err.as<int>());
@@ -585,31 +502,27 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
   return FKF_OK;
 }
 
-fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::vector<TcTile>& tiles) {
+fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
   fkf_ctx* ctx = h->ctx;
   std::vector<TcAChunk> ch;
   // phase-1 items are dealt round-robin to persistent CTAs: longest first
-  std::stable_sort(items.begin(), items.end(), [](const P1Item& a, const P1Item& b) { return a.nr > b.nr; });
-  for (P1Item& it : items) {
+  std::vector<size_t> order(tu.items.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t b) { return tu.items[a].nchunk > tu.items[b].nchunk; });
+  std::vector<P1Item> items;
+  items.reserve(order.size());
+  for (size_t i : order) {
+    P1Item it = tu.items[i];
     it.a_chunk0 = (int64_t)ch.size();
-    it.nchunk = (int)cdiv(it.nr, kK);
-    for (int c = 0; c < it.nchunk; c++) {
-      TcAChunk a{};
-      a.src_off = it.fac_off + (int64_t)(it.r0 + c * kK) * it.K + it.q0;
-      a.si = 1;
-      a.sk = it.K;
-      a.row_lo = 0;
-      a.row_hi = it.nq;
-      a.kv = std::min(kK, it.nr - c * kK);
-      a.near = 0;
-      ch.push_back(a);
-    }
+    ch.insert(ch.end(), tu.item_chunks[i].begin(), tu.item_chunks[i].end());
+    items.push_back(it);
   }
-  for (TcTile& t : tiles) {
+  for (TcTile& t : tu.tiles) {
     t.a_chunk0 = (int64_t)ch.size();
     int nch = 0;
     for (int j = 0; j < t.nseg; j++) {
-      const TcSeg& sg = h->tcseg_host[t.seg0 + j];
+      const TcSeg& sg = tu.segs[t.seg0 + j];
       for (int k0 = 0; k0 < sg.K; k0 += kK, nch++) {
         TcAChunk a{};
         a.src_off = sg.a_off + k0;
@@ -625,7 +538,22 @@ fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::v
     t.nchunk = nch;
   }
   if (!items.empty()) FKF_TRY(dev_upload(ctx, h->tcp1, items.data(), items.size() * sizeof(P1Item)));
-  if (!tiles.empty()) FKF_TRY(dev_upload(ctx, h->tctile, tiles.data(), tiles.size() * sizeof(TcTile)));
+  if (!tu.reduces.empty())
+    FKF_TRY(dev_upload(ctx, h->tcred, tu.reduces.data(), tu.reduces.size() * sizeof(P1Reduce)));
+  if (!tu.tiles.empty()) FKF_TRY(dev_upload(ctx, h->tctile, tu.tiles.data(), tu.tiles.size() * sizeof(TcTile)));
+  FKF_TRY(dev_upload(ctx, h->tcseg, tu.segs.data(), std::max<size_t>(tu.segs.size(), 1) * sizeof(TcSeg)));
+  if (!tu.xmap.empty()) FKF_TRY(dev_upload(ctx, h->tcxmap, tu.xmap.data(), tu.xmap.size() * sizeof(TcXChunk)));
+  FKF_TRY(dev_upload(ctx, h->tcslot, tu.slotmap.data(), tu.slotmap.size() * sizeof(int64_t)));
+  h->n_tcp1 = (int64_t)items.size();
+  h->n_tcred = (int64_t)tu.reduces.size();
+  h->n_tctile = (int64_t)tu.tiles.size();
+  h->n_tcx = (int64_t)tu.xmap.size();
+  h->n_tcz = tu.nz;
+  h->tc_part_rows = tu.part_rows;
+  // columns per pass: keep the split slot workspace under ~24 GB
+  int64_t panel = 1024;
+  while (panel > kN && (double)h->n_tcz * (panel / kN) * kBChunkBytes > 24e9) panel /= 2;
+  h->tc_panel = panel;
   h->n_tca = (int64_t)ch.size();
   FKF_TRY(dev_alloc(ctx, h->tca, (size_t)std::max<int64_t>(h->n_tca, 1) * kAChunkBytes));
   if (h->n_tca > 0) {
@@ -637,10 +565,10 @@ fkf_status hmat_build_tc_streams(fkf_hmat* h, std::vector<P1Item>& items, std::v
     FKF_LAUNCHED(ctx);
     FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
+  h->engine = 1;
   return FKF_OK;
 }
 
-// Reads (and clears) the tensor-core wait-expiry flag; synchronises.
 fkf_status hmat_tc_check(fkf_hmat* h) {
   if (!h->tc_err.p) return FKF_OK;
   int e = 0;
