@@ -505,11 +505,15 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
 fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
   fkf_ctx* ctx = h->ctx;
   std::vector<TcAChunk> ch;
-  // phase-1 items are dealt round-robin to persistent CTAs: longest first
+  // phase-1 items in the order of their first row (the items of all tree
+  // levels that read the same X chunks run together and share them in L2),
+  // longest first among equal starts
   std::vector<size_t> order(tu.items.size());
   for (size_t i = 0; i < order.size(); i++) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](size_t a, size_t b) { return tu.items[a].nchunk > tu.items[b].nchunk; });
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    const P1Item &x = tu.items[a], &y = tu.items[b];
+    return x.x_row != y.x_row ? x.x_row < y.x_row : x.nchunk > y.nchunk;
+  });
   std::vector<P1Item> items;
   items.reserve(order.size());
   for (size_t i : order) {
