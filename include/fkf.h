@@ -238,10 +238,7 @@ typedef struct {
   int32_t r;          /* rank of the low-rank term */
   int32_t last_path;  /* last step: 0 = new directions merged (GEP, orthonormalisation,
                          merge, rotation); 1 = no information outside span(W): basis kept,
-                         weight updated in information form (Woodbury, full weight);
-                         2 = basis kept with a diagonal weight and HW^T R^-1 HW diagonal
-                         in the basis (a repeated operator in its GEP basis): the per-mode
-                         recursion of Alg. kalmanconstantH, no m x m factorisation */
+                         weight updated in information form */
   int32_t diagonal;   /* 1 if the weight is currently diagonal (the paper's D_k) */
 } fkf_filter_stats;
 fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);

@@ -489,60 +489,6 @@ __global__ void k_add_block(int r, const double* __restrict__ B, double c, doubl
 }
 
 // out = d .* x (n)
-// out[i, j] = rs[i] * A[i*lda + j]  (m x r)
-__global__ void k_scale_rows(int m, int r, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
-                             double* __restrict__ out) {
-  const int64_t total = (int64_t)m * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / r), j = (int)(e % r);
-    out[e] = rs[i] * A[(int64_t)i * lda + j];
-  }
-}
-
-// Diagonal weight recursion (Alg. kalmanconstantH): with the predicted
-// e = alpha' - d and q = Q_ii (Q = HW^T R^-1 HW diagonal), e' = e / (1 + e q)
-// = (1/e + q)^-1 and d' = alpha' - e'.  Also ep = e', and lg[i] =
-// log e - log e' (their sum is log det of I + E Q, the step's part of
-// log det S by the determinant lemma).
-__global__ void k_diag_weight(int r, const double* __restrict__ d, const double* __restrict__ Q, double alpha1,
-                              double* __restrict__ dn, double* __restrict__ ep, double* __restrict__ lg) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= r) return;
-  const double e = alpha1 - d[i];
-  const double q = Q[(int64_t)i * r + i];
-  const double en = e / (1.0 + e * q);
-  dn[i] = alpha1 - en;
-  ep[i] = en;
-  lg[i] = log1p(e * q);
-}
-
-// z = R^-1 nu - R^-1 w (w = HW (e' .* HW^T R^-1 nu)), the Woodbury form of
-// S^-1 nu for S = R + HW E HW^T with E diagonal; z = R^-1 nu when w is null.
-__global__ void k_woodbury_z(int m, const double* __restrict__ nu, const double* __restrict__ rdiag,
-                             const double* __restrict__ w, double* __restrict__ z) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) z[i] = (w ? nu[i] - w[i] : nu[i]) / rdiag[i];
-}
-
-// NLL = (nu^T z + sum log R_ii + sum_j lg_j + m log 2 pi) / 2 (single CTA,
-// fixed summation order)
-__global__ void k_nll_diag(int m, const double* __restrict__ nu, const double* __restrict__ z,
-                           const double* __restrict__ rdiag, int r, const double* __restrict__ lg,
-                           double* __restrict__ out) {
-  __shared__ double sh[32];
-  double a = 0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) a += nu[i] * z[i] + log(rdiag[i]);
-  for (int i = threadIdx.x; i < r; i += blockDim.x) a += lg[i];
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
-    out[0] = 0.5 * (t + m * log(2.0 * 3.14159265358979323846));
-  }
-}
-
 __global__ void k_vmul(int n, const double* __restrict__ d, const double* __restrict__ x, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = d[i] * x[i];
@@ -557,13 +503,13 @@ __global__ void k_vmul(int n, const double* __restrict__ d, const double* __rest
 constexpr int kFrobBlocks = 304;
 
 __global__ void k_frob_part(int64_t n, const double* __restrict__ A, const double* __restrict__ rs, int m,
-                            bool offdiag, double* __restrict__ part) {
+                            double* __restrict__ part) {
   __shared__ double sh[32];
   const int64_t per = (n + kFrobBlocks - 1) / kFrobBlocks;
   const int64_t a = blockIdx.x * per, b = a + per < n ? a + per : n;
   double s = 0;
   for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
-    const double v = (offdiag && e / m == e % m) ? 0.0 : (rs ? A[e] * rs[e / m] * rs[e % m] : A[e]);
+    const double v = rs ? A[e] * rs[e / m] * rs[e % m] : A[e];
     s += v * v;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -584,11 +530,10 @@ __global__ void k_frob_final(const double* __restrict__ part, double* __restrict
   }
 }
 
-// out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs
-// is given; only the entries off the diagonal of the m x m matrix if offdiag)
-static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part, double* out,
-                       bool offdiag = false) {
-  k_frob_part<<<kFrobBlocks, 256, 0, ctx->stream>>>(n, A, rs, m, offdiag, part);
+// out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
+static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part,
+                       double* out) {
+  k_frob_part<<<kFrobBlocks, 256, 0, ctx->stream>>>(n, A, rs, m, part);
   FKF_LAUNCHED(ctx);
   k_frob_final<<<1, 32, 0, ctx->stream>>>(part, out);
   FKF_LAUNCHED(ctx);
@@ -722,14 +667,13 @@ struct fkf_filter {
   bool diag = true;
   DevBuf Df, Dfn, Ep, Qm;
   double new_tol = 0;  // relative information outside span(W) below which the basis is kept
-  double diag_tol = 0;  // relative off-diagonal size of Q = HW^T R^-1 HW below which it counts as diagonal
   int last_path = 0;   // 0: general merge, 1: basis kept (no new directions)
   // step inputs
   DevBuf rowptr, col, val, y, rdiag, rs, flag;
   DevBuf cnt, cursor, colptr, crow, cval;
   // small FP64 buffers
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
-  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws, vm;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws;
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
   cudaEvent_t ev[7] = {};
   double phase_ms[6] = {};
@@ -763,8 +707,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->uz, r));
   FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
   FKF_TRY(A(f->HWD, m * r));
-  FKF_TRY(A(f->nll, 8));
-  FKF_TRY(A(f->vm, 3 * r + m));
+  FKF_TRY(A(f->nll, 4));
   FKF_TRY(A(f->red, kFrobBlocks));
   FKF_TRY(A(f->dbar, r));
   FKF_TRY(A(f->y, m));
@@ -800,9 +743,6 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
   // ||R^-1/2 (A - HW HW^T) R^-1/2||_F / ||R^-1/2 A R^-1/2||_F below new_tol:
   // the step's information lies in span(W) and the basis is kept
   f->new_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-4;
-  // dropping off-diagonal entries of relative size diag_tol changes the
-  // updated weight by about as much: near FP64 resp. FP32 rounding
-  f->diag_tol = h->prec == FKF_FP64 ? 1e-10 : 1e-5;
   f->alpha = alpha0;
   auto fail = [&](fkf_status st) {
     delete f;
@@ -966,109 +906,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   k_sym<<<nblk((int64_t)m * m), 256, 0, st>>>(m, Araw, nm, f->rs.as<double>(), f->rdiag.as<double>(), alpha1,
                                               f->As.as<double>(), f->At.as<double>(), S);
   FKF_LAUNCHED(ctx);
+  // S = alpha' A + R - HW D HW^T   (D diagonal, or the full r x r weight Df)
   const bool diag = f->diag;
   double* Dfc = f->Df.as<double>();
-  const int64_t rr = (int64_t)r * r;
-  // ---- does the step bring information outside span(W)?  The Gamma^-1-Gram
-  // of G's component outside span(W) is A - HW HW^T (X^T G = (HW)^T, X^T W = I);
-  // compared with A in the noise-whitened metric.  With a diagonal weight,
-  // also whether Q = HW^T R^-1 HW is diagonal in the current basis.
-  double ratio = 1.0;
-  bool qdiag = false;
-  {
-    double* nrm = f->nll.as<double>() + 1;
-    if (r > 0) {
-      double* T0 = f->Tm.as<double>();
-      FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
-      FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
-      FKF_TRY(frob(ctx, (int64_t)m * m, T0, f->rs.as<double>(), m, f->red.as<double>(), nrm));
-      FKF_TRY(frob(ctx, (int64_t)m * m, f->At.as<double>(), nullptr, m, f->red.as<double>(), nrm + 1));
-      if (diag) {
-        double* Qm = f->Qm.as<double>();
-        k_scale_rows<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->rs.as<double>(), f->HWD.as<double>());
-        FKF_LAUNCHED(ctx);
-        FKF_TRY(gemm_sym_f64(ctx, true, false, r, m, 1.0, f->HWD.as<double>(), r, f->HWD.as<double>(), r, 0.0, Qm, r));
-        FKF_TRY(frob(ctx, rr, Qm, nullptr, r, f->red.as<double>(), nrm + 2, true));
-        FKF_TRY(frob(ctx, rr, Qm, nullptr, r, f->red.as<double>(), nrm + 3));
-      }
-    }
-    double hv[4] = {1.0, 1.0, 1.0, 0.0};
-    int hflag = 0;
-    if (r > 0) FKF_CUDA(ctx, cudaMemcpyAsync(hv, nrm, (diag ? 4 : 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    FKF_CUDA(ctx, cudaStreamSynchronize(st));
-    if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
-    if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
-    qdiag = r > 0 && diag && hv[3] > 0 && hv[2] <= f->diag_tol * hv[3];
-  }
-  const bool kept = r > 0 && ratio <= f->new_tol;
-  // mean: s' = s + [W G] [-D (HW^T z); alpha' z]  (D diagonal, or the full weight Df)
-  auto mean_update = [&]() -> fkf_status {
-    if (r > 0) {
-      FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
-      if (diag) {
-        k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->uz.as<double>(), f->dbar.as<double>());
-        FKF_LAUNCHED(ctx);
-      } else {
-        FKF_TRY(gemm_f64(ctx, false, false, r, 1, r, 1.0, Dfc, r, f->uz.as<double>(), 1, 0.0, f->dbar.as<double>(), 1));
-      }
-    }
-    k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, nullptr, f->dbar.as<double>(), f->z.as<double>(), alpha1,
-                                                       f->vcoef.as<T>());
-    FKF_LAUNCHED(ctx);
-    k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
-                                                         f->s_new.as<double>());
-    FKF_LAUNCHED(ctx);
-    return FKF_OK;
-  };
-  if (kept && qdiag) {
-    // ---- basis kept, diagonal weight and Q diagonal in this basis (the GEP
-    // basis of a repeated operator): the per-mode recursion of Alg.
-    // kalmanconstantH, e' = (1/e + q)^-1, and the innovation algebra through
-    // the Woodbury identity S^-1 = R^-1 - R^-1 HW E' HW^T R^-1 (S = R + HW E
-    // HW^T up to the new_tol residual) and the determinant lemma
-    // det S = det R prod(1 + e q): no m x m factorisation.
-    double* vm = f->vm.as<double>();
-    double* ep = vm;              // r: e'
-    double* lg = vm + r;          // r: log(1 + e q)
-    double* u = vm + 2 * r;       // m: R^-1 nu, then HW (e' .* HW^T R^-1 nu)
-    double* t = u + m;            // r
-    k_diag_weight<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->Qm.as<double>(), alpha1,
-                                                      f->Dn.as<double>(), ep, lg);
-    FKF_LAUNCHED(ctx);
-    k_woodbury_z<<<(int)cdiv(m, 256), 256, 0, st>>>(m, f->nu.as<double>(), f->rdiag.as<double>(), nullptr, u);
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, u, 1, 0.0, t, 1));
-    k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, ep, t, t);
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(gemm_f64(ctx, false, false, m, 1, r, 1.0, HW, nm, t, 1, 0.0, u, 1));
-    k_woodbury_z<<<(int)cdiv(m, 256), 256, 0, st>>>(m, f->nu.as<double>(), f->rdiag.as<double>(), u,
-                                                    f->z.as<double>());
-    FKF_LAUNCHED(ctx);
-    k_nll_diag<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), f->rdiag.as<double>(), r, lg,
-                                  f->nll.as<double>());
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(mean_update());
-    for (int e = 3; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
-    double nll = 0;
-    FKF_CUDA(ctx, cudaMemcpyAsync(&nll, f->nll.p, 8, cudaMemcpyDeviceToHost, st));
-    FKF_CUDA(ctx, cudaStreamSynchronize(st));
-    FKF_CUDA(ctx, cudaGetLastError());
-    FKF_TRY(hmat_tc_check(h));
-    std::swap(f->s_hat.p, f->s_new.p);
-    std::swap(f->D.p, f->Dn.p);
-    f->alpha = alpha1;
-    f->k++;
-    f->last_path = 2;
-    if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
-    for (int i = 0; i < 6; i++) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, f->ev[i], f->ev[i + 1]);
-      f->phase_ms[i] = ms;
-    }
-    return FKF_OK;
-  }
-  // S = alpha' A + R - HW D HW^T   (D diagonal, or the full r x r weight Df)
   if (r > 0) {
     if (diag) {
       k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
@@ -1083,9 +923,45 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_TRY(chol_solve_f64(ctx, m, S, f->z.as<double>(), 1));
   k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, f->nll.as<double>());
   FKF_LAUNCHED(ctx);
-  FKF_TRY(mean_update());
+  // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
+  if (r > 0) {
+    FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
+    if (diag) {
+      k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->uz.as<double>(), f->dbar.as<double>());
+      FKF_LAUNCHED(ctx);
+    } else {
+      FKF_TRY(gemm_f64(ctx, false, false, r, 1, r, 1.0, Dfc, r, f->uz.as<double>(), 1, 0.0, f->dbar.as<double>(), 1));
+    }
+  }
+  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, nullptr, f->dbar.as<double>(), f->z.as<double>(), alpha1,
+                                                     f->vcoef.as<T>());
+  FKF_LAUNCHED(ctx);
+  k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
+                                                       f->s_new.as<double>());
+  FKF_LAUNCHED(ctx);
   FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
-  if (kept) {
+  // ---- does the step bring information outside span(W)?  The Gamma^-1-Gram
+  // of G's component outside span(W) is A - HW HW^T (X^T G = (HW)^T, X^T W = I);
+  // compared with A in the noise-whitened metric.
+  double ratio = 1.0;
+  {
+    double* nrm = f->nll.as<double>() + 1;
+    if (r > 0) {
+      double* T0 = f->Tm.as<double>();
+      FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
+      FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
+      FKF_TRY(frob(ctx, (int64_t)m * m, T0, f->rs.as<double>(), m, f->red.as<double>(), nrm));
+      FKF_TRY(frob(ctx, (int64_t)m * m, f->At.as<double>(), nullptr, m, f->red.as<double>(), nrm + 1));
+    }
+    double hv[2] = {1.0, 1.0};
+    int hflag = 0;
+    if (r > 0) FKF_CUDA(ctx, cudaMemcpyAsync(hv, nrm, 16, cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
+    if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
+  }
+  if (r > 0 && ratio <= f->new_tol) {
     // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated
     // in information form, E' = (E^-1 + Q)^-1, E = alpha' I - D (predicted),
     // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight)
@@ -1098,6 +974,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     double* Dn2 = f->Dfn.as<double>();
     double* Kt = f->P.as<double>();  // r x m: K^T
     double* Yt = f->J.as<double>();  // r x m: (S^-1 K)^T
+    const int64_t rr = (int64_t)r * r;
     if (diag) {
       k_diag_from<<<nblk(rr), 256, 0, st>>>(r, f->D.as<double>(), alpha1, Ep);
     } else {

@@ -287,12 +287,9 @@ def test_fixed_geometry_rank_stays_at_m(fkf):
 
 def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
     """A repeated operator brings no information outside span(W): the basis is
-    kept.  Right after the first step the basis is the operator's GEP basis, so
-    the weight stays diagonal and the per-mode recursion runs (path 2); a new
-    operator forces the merge path, after which the repeated operator is no
-    longer diagonal in the basis and the full weight is updated in information
-    form (path 1), several steps in a row with no observation in between.
-    Everything against the dense oracle."""
+    kept and the (then non-diagonal) weight is updated in information form,
+    several steps in a row with no observation in between; a new operator
+    then forces the merge path.  Everything against the dense oracle."""
     rng = np.random.default_rng(synth.BASE_SEED + 7)
     nx = ny = 20
     pts = synth.grid_points_2d(nx, ny)
@@ -311,7 +308,7 @@ def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
         nll = fkf.fkf_filter_step(f, ys[k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
         assert abs(nll - ref[k]["nll"]) < 1e-10 * abs(ref[k]["nll"]), k
         paths.append(fkf.fkf_filter_get_stats(f)["last_path"])
-    assert paths == [0, 2, 2, 2, 0, 1, 1, 1]
+    assert paths == [0, 1, 1, 1, 0, 1, 1, 1]
     assert fkf.fkf_filter_get_stats(f)["diagonal"] == 0
     import torch
 
