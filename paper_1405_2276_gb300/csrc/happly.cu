@@ -205,12 +205,19 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   }
   std::vector<int64_t> K(nc, 0), slot_base(nc, 0), fac_off(nc, 0);
   std::vector<std::vector<int64_t>> slot_col(nc);
+  // FP32 operators give every block a multiple of 4 slots (zero columns) on
+  // both sides, so that aligned groups of 4 slots map to aligned groups of 4
+  // (the tensor-core engine writes its slot rows 4 at a time)
+  auto block_width = [&](int b) -> int64_t {
+    const int64_t k = hh.far[b].k;
+    return h->prec == FKF_FP32 ? (k + 3) / 4 * 4 : k;
+  };
   int64_t ktot = 0, facn = 0;
   for (int c = 0; c < nc; c++) {
     int64_t k = 0;
     for (auto [b, side] : slots[c]) {
       slot_col[c].push_back(k);
-      k += hh.far[b].k;
+      k += block_width(b);
     }
     K[c] = (k + 3) / 4 * 4;
     slot_base[c] = ktot;
@@ -218,7 +225,8 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
     ktot += K[c];
     facn += csize(c) * K[c];
   }
-  // slot map (involution between the two sides of each block; padding maps to itself)
+  // slot map (involution between the two sides of each block, the padding
+  // columns of a block included; the padding at the end of a stack maps to itself)
   std::vector<int64_t> smap(std::max<int64_t>(ktot, 1));
   for (int64_t g = 0; g < ktot; g++) smap[g] = g;
   {
@@ -229,7 +237,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
       for (size_t i = 0; i < slots[c].size(); i++)
         side_row[slots[c][i].second][slots[c][i].first] = slot_base[c] + slot_col[c][i];
     for (size_t b = 0; b < hh.far.size(); b++)
-      for (int l = 0; l < hh.far[b].k; l++) {
+      for (int64_t l = 0; l < block_width((int)b); l++) {
         smap[side_row[0][b] + l] = side_row[1][b] + l;
         smap[side_row[1][b] + l] = side_row[0][b] + l;
       }

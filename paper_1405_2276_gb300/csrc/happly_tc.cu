@@ -20,7 +20,8 @@
 //   warp 1     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
 //              products), commits to empty[s], and to acc_full after a
 //              tile's last chunk; also allocates and frees TMEM;
-//   warps 2-5  epilogue: tcgen05.ld of the finished accumulator, stores,
+//   warps 2-9  epilogue: tcgen05.ld of the finished accumulator (two warps
+//              per TMEM lane quarter, one per half of the columns), stores,
 //              arrive on acc_empty.
 // Two accumulators (2 x 256 TMEM columns) let the epilogue of one tile run
 // under the MMAs of the next.  Tiles are dealt round-robin over the CTAs, the
@@ -50,10 +51,13 @@ constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk
 constexpr int kBChunkBytes = 2 * kBBytes;  // 32 KB: hi | lo
 constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;  // 48 KB
 constexpr int kS = FKF_TC_STAGES;
-constexpr int kSmemBytes = kS * kStageBytes + 256;  // 192.25 KB for 4 stages
+constexpr int kEpiWarps = 8;               // warps 2-9: two per TMEM lane quarter, one per column half
+constexpr int kEpiLd = 33;                 // padded row of an epilogue staging tile (32 x 32 floats)
+constexpr int kEpiBytes = kEpiWarps * 32 * kEpiLd * 4;
+constexpr int kSmemBytes = kS * kStageBytes + 256 + kEpiBytes;  // 225.25 KB for 4 stages
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
-constexpr int kProdWarp = 0, kMmaWarp = 1;  // warps 2-5: epilogue
-constexpr int kThreads = 192;
+constexpr int kProdWarp = 0, kMmaWarp = 1;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 2 * kN;
 constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
@@ -67,6 +71,8 @@ struct Smem {
   uint64_t* bar;
   uint32_t* tmem_slot;
   int* fail;
+  float* epi;  // kEpiWarps staging tiles
+
   __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kStageBytes; }
   __device__ __forceinline__ uint8_t* b(int s) const { return base + s * kStageBytes + kAChunkBytes; }
   __device__ __forceinline__ bool failed() const { return *reinterpret_cast<volatile int*>(fail) != 0; }
@@ -80,6 +86,7 @@ __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   s.bar = reinterpret_cast<uint64_t*>(tail);
   s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 192);
   s.fail = reinterpret_cast<int*>(tail + 224);
+  s.epi = reinterpret_cast<float*>(tail + 256);
   return s;
 }
 
@@ -284,6 +291,7 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
                                               uint32_t tmem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
+  const int half = (warp - 2) >> 2;
   const int row = 32 * quarter + lane;
   int tl = 0;
   for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
@@ -298,7 +306,7 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
     const bool zero = t.nchunk == 0;
     const RowSinkY sink{row < t.rows ? ph.Y + (t.row0 + row) * ph.ldy + n0 : nullptr};
 #pragma unroll 1
-    for (int j = 0; j < kN / 32; j++) {
+    for (int j = 4 * half; j < 4 * half + 4; j++) {
       float v[32];
       if (zero) {
 #pragma unroll
@@ -313,13 +321,20 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
   }
 }
 
-// phase 1: slot rows into the split slot workspace, or partial rows
+// phase 1: slot rows into the split slot workspace, or partial rows.  The
+// slots of a tile come in aligned groups of 4 that map to 4 consecutive
+// aligned positions of the split workspace (blocks have a multiple of 4
+// slots), i.e. one 16-byte unit (4 k) per column: each warp stages its
+// 32 rows x 32 columns in shared memory and writes whole units, a warp
+// covering 512 contiguous bytes per hi/lo half.
 template <>
 __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int64_t ntiles, int nct, int ncols,
                                               uint32_t tmem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;
+  const int half = (warp - 2) >> 2;
   const int row = 32 * quarter + lane;
+  float* tile = s.epi + (warp - 2) * 32 * kEpiLd;
   int tl = 0;
   for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
     const int b = tl & 1;
@@ -331,22 +346,25 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
     const int n0 = ct * kN;
     const int nv = min(kN, ncols - n0);
     const P1Item& it = ph.items[w];
-    const bool valid = row < it.nq;
-    RowSinkY psink{nullptr};
-    uint8_t* zchunk = nullptr;
-    int srow = 0;
-    if (valid) {
-      if (it.out_row >= 0) {
-        psink.dst = ph.part + (it.out_row + row) * ph.ldp + n0;
-      } else {
-        const int64_t p = ph.slotpos[it.map_off + row];
-        zchunk = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)kBChunkBytes;
-        srow = (int)(p & 15);
+    const bool zero = it.nchunk == 0;
+    const bool partial = it.out_row >= 0;
+    RowSinkY psink{(partial && row < it.nq) ? ph.part + (it.out_row + row) * ph.ldp + n0 : nullptr};
+    // split-workspace chunk and k of the 8 slot groups of this warp's rows
+    uint8_t* gchunk[8];
+    int gk[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int r4 = 32 * quarter + 4 * q;
+      gchunk[q] = nullptr;
+      gk[q] = 0;
+      if (!partial && r4 < it.nq) {
+        const int64_t p = ph.slotpos[it.map_off + r4];
+        gchunk[q] = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)kBChunkBytes;
+        gk[q] = (int)(p & 12);
       }
     }
-    const bool zero = it.nchunk == 0;
 #pragma unroll 1
-    for (int j = 0; j < kN / 32; j++) {
+    for (int j = 4 * half; j < 4 * half + 4; j++) {
       float v[32];
       if (zero) {
 #pragma unroll
@@ -354,11 +372,20 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
       } else {
         umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
       }
-      psink.put(32 * j, nv, v);
-      if (zchunk) {
+      if (partial) {
+        psink.put(32 * j, nv, v);
+      } else {
 #pragma unroll
-        for (int i = 0; i < 32; i++)
-          if (32 * j + i < nv) put1(zchunk, 32 * j + i, srow, v[i]);
+        for (int i = 0; i < 32; i++) tile[lane * kEpiLd + i] = v[i];
+        __syncwarp();
+        const int n = 32 * j + lane;  // column of this lane
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          if (gchunk[q] && n < nv)
+            put4(gchunk[q], gchunk[q] + kBBytes, n, gk[q], tile[(4 * q + 0) * kEpiLd + lane],
+                 tile[(4 * q + 1) * kEpiLd + lane], tile[(4 * q + 2) * kEpiLd + lane], tile[(4 * q + 3) * kEpiLd + lane]);
+        }
+        __syncwarp();
       }
     }
     umma::fence_before_sync();
@@ -378,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = FULL; i < EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = EMPTY; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = AF; i < AE; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 128);
+    for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 32 * kEpiWarps);
     umma::mbar_init(&s.bar[FIN], 1);
     *s.fail = 0;
     umma::fence_mbar_init();
