@@ -1,0 +1,136 @@
+// Blocked FP64 Cholesky factorisation and forward substitution for the m x m
+// innovation covariance S of the filter step (row-major, S = L L^T with L in
+// the lower triangle).
+//
+// FP64 throughput on this part is about two FMAs per clock per SM, so the
+// design keeps the sequential part short and spreads everything else over
+// the SMs: blocks of 32; a 32 x 32 diagonal block is factored by one CTA
+// (32 rank-1 steps in shared memory); the panel below it is solved row by row
+// (one thread per row, the factor block in shared memory, 32 rows per CTA);
+// the trailing matrix is updated by the symmetric FP64 tile GEMM (lower tiles
+// only).  The forward substitution X <- X L^-T for many right-hand sides uses
+// the same row solve per diagonal block and a GEMM update of the later
+// columns.  Column-major BLAS reads this row-major lower factor as the upper
+// factor U = L^T of S = U^T U.
+#include <algorithm>
+#include <cmath>
+
+#include "common.h"
+#include "dense.h"
+
+namespace {
+
+constexpr int kB = 32;  // block size
+
+// Factor the b x b diagonal block A (ld lda, lower triangle) in place.  A
+// pivot that is not positive sets *flag and is replaced by 1 so that the
+// factorisation completes without NaNs (the caller reports the failure).
+__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int64_t lda, int b,
+                                                    int* __restrict__ flag) {
+  __shared__ double a[kB][kB + 1];
+  const int t = threadIdx.x;
+  for (int e = t; e < kB * kB; e += blockDim.x) {
+    const int i = e / kB, j = e % kB;
+    a[i][j] = (i < b && j <= i) ? A[(int64_t)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < b; j++) {
+    if (t == 0) {
+      double d = a[j][j];
+      if (!(d > 0.0)) {
+        atomicOr(flag, 1);
+        d = 1.0;
+      }
+      a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double inv = 1.0 / a[j][j];
+    if (t > j && t < b) a[t][j] *= inv;
+    __syncthreads();
+    // a[i][l] -= a[i][j] a[l][j] for j < l <= i < b: thread t -> row i = j+1 + t/32, column l = j+1 + t%32
+    for (int e = t; e < kB * kB; e += blockDim.x) {
+      const int i = j + 1 + e / kB, l = j + 1 + e % kB;
+      if (i < b && l <= i) a[i][l] -= a[i][j] * a[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < kB * kB; e += blockDim.x) {
+    const int i = e / kB, j = e % kB;
+    if (i < b && j <= i) A[(int64_t)i * lda + j] = a[i][j];
+  }
+}
+
+// X[r, 0:b] <- X[r, 0:b] Lkk^-T for rows r < rows (forward substitution per
+// row: x_j = (x_j - sum_{l<j} x_l Lkk[j][l]) / Lkk[j][j]); Lkk is the b x b
+// lower factor block at L (ld lda).  One thread per row, 32 rows per CTA.
+__global__ void __launch_bounds__(32) k_trsm_rows(double* __restrict__ X, int64_t ldx, int64_t rows, int b,
+                                                  const double* __restrict__ L, int64_t lda) {
+  __shared__ double l[kB][kB + 1];
+  __shared__ double dinv[kB];
+  const int t = threadIdx.x;
+  for (int e = t; e < kB * kB; e += blockDim.x) {
+    const int i = e / kB, j = e % kB;
+    l[i][j] = (i < b && j <= i) ? L[(int64_t)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  if (t < b) dinv[t] = 1.0 / l[t][t];
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + t;
+  if (r >= rows) return;
+  double* xr = X + r * ldx;
+  double x[kB];
+#pragma unroll
+  for (int j = 0; j < kB; j++) x[j] = j < b ? xr[j] : 0.0;
+#pragma unroll
+  for (int j = 0; j < kB; j++) {
+    double s = x[j];
+#pragma unroll
+    for (int q = 0; q < j; q++) s -= x[q] * l[j][q];
+    x[j] = j < b ? s * dinv[j] : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < kB; j++)
+    if (j < b) xr[j] = x[j];
+}
+
+}  // namespace
+
+fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, DevBuf& ws) {
+  if (n <= 0) return FKF_OK;
+  if (ws.bytes < 256) FKF_TRY(dev_alloc(ctx, ws, 256));
+  int* flag = ws.as<int>();
+  FKF_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  for (int k0 = 0; k0 < n; k0 += kB) {
+    const int b = std::min(kB, n - k0);
+    double* Akk = A + (int64_t)k0 * lda + k0;
+    k_potrf_diag<<<1, 256, 0, ctx->stream>>>(Akk, lda, b, flag);
+    FKF_LAUNCHED(ctx);
+    const int rem = n - k0 - b;
+    if (rem > 0) {
+      double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
+      k_trsm_rows<<<(unsigned)cdiv(rem, 32), 32, 0, ctx->stream>>>(P, lda, rem, b, Akk, lda);
+      FKF_LAUNCHED(ctx);
+      FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, P + b, lda));
+    }
+  }
+  int hflag = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hflag) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d)", n);
+  return FKF_OK;
+}
+
+fkf_status trsm_lt_f64(fkf_ctx* ctx, int n, const double* L, int64_t lda, double* X, int64_t ldx, int64_t rows) {
+  if (n <= 0 || rows <= 0) return FKF_OK;
+  for (int k0 = 0; k0 < n; k0 += kB) {
+    const int b = std::min(kB, n - k0);
+    k_trsm_rows<<<(unsigned)cdiv(rows, 32), 32, 0, ctx->stream>>>(X + k0, ldx, rows, b,
+                                                                 L + (int64_t)k0 * lda + k0, lda);
+    FKF_LAUNCHED(ctx);
+    const int rem = n - k0 - b;
+    if (rem > 0)
+      FKF_TRY(gemm_f64(ctx, false, true, rows, rem, b, -1.0, X + k0, ldx, L + (int64_t)(k0 + b) * lda + k0, lda, 1.0,
+                       X + k0 + b, ldx));
+  }
+  return FKF_OK;
+}

@@ -918,9 +918,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     }
     FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
   }
-  FKF_TRY(chol_f64(ctx, m, S, f->cholws));
+  FKF_TRY(chol_blocked_f64(ctx, m, S, m, f->cholws));
   FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
-  FKF_TRY(chol_solve_f64(ctx, m, S, f->z.as<double>(), 1));
+  FKF_TRY(chol_solve_rowlower_f64(ctx, m, S, f->z.as<double>(), 1));
   k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, f->nll.as<double>());
   FKF_LAUNCHED(ctx);
   // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
@@ -966,14 +966,14 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     // in information form, E' = (E^-1 + Q)^-1, E = alpha' I - D (predicted),
     // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight)
     // Evaluated in the Woodbury form E' = E - K^T S^-1 K, K = HW E, with the
-    // innovation covariance S = alpha' A - HW D HW^T + R already factored for
-    // the mean (S = HW E HW^T + R up to the new_tol residual A - HW HW^T), and
-    // HW D already formed for S: one m x m solve with r right-hand sides and
-    // one symmetric r x r x m product, no r x r factorisation.
+    // innovation covariance S = alpha' A - HW D HW^T + R = L L^T already
+    // factored for the mean (S = HW E HW^T + R up to the new_tol residual
+    // A - HW HW^T), and HW D already formed for S: E' = E - V^T V with
+    // V = L^-1 K (one forward substitution with r right-hand sides and one
+    // symmetric r x r x m product), no r x r factorisation.
     double* Ep = f->Ep.as<double>();
     double* Dn2 = f->Dfn.as<double>();
-    double* Kt = f->P.as<double>();  // r x m: K^T
-    double* Yt = f->J.as<double>();  // r x m: (S^-1 K)^T
+    double* Yt = f->J.as<double>();  // r x m: K^T, then (L^-1 K)^T
     const int64_t rr = (int64_t)r * r;
     if (diag) {
       k_diag_from<<<nblk(rr), 256, 0, st>>>(r, f->D.as<double>(), alpha1, Ep);
@@ -981,11 +981,10 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Dfc, 0.0, nullptr, alpha1, Ep);
     }
     FKF_LAUNCHED(ctx);
-    k_hwe_t<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), alpha1, Kt);
+    k_hwe_t<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), alpha1, Yt);
     FKF_LAUNCHED(ctx);
-    FKF_CUDA(ctx, cudaMemcpyAsync(Yt, Kt, (size_t)m * r * 8, cudaMemcpyDeviceToDevice, st));
-    FKF_TRY(chol_solve_f64(ctx, m, S, Yt, r));
-    FKF_TRY(gemm_sym_f64(ctx, false, true, r, m, -1.0, Kt, m, Yt, m, 1.0, Ep, r));
+    FKF_TRY(trsm_lt_f64(ctx, m, S, m, Yt, m, r));
+    FKF_TRY(gemm_sym_f64(ctx, false, true, r, m, -1.0, Yt, m, Yt, m, 1.0, Ep, r));
     k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Ep, 0.0, nullptr, alpha1, Dn2);  // D' = alpha' I - E'
     FKF_LAUNCHED(ctx);
     for (int e = 4; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
