@@ -177,6 +177,8 @@ def run_gpu(args, rank, world):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     phases = np.zeros(6)
+    # the timed steps are the profiled range (ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     ev0.record(stream)
     t0 = time.time()
     for k in range(args.warmup, total_steps):
@@ -184,6 +186,7 @@ def run_gpu(args, rank, world):
         phases += np.array(fkf.fkf_filter_phase_times(f32))
     ev1.record(stream)
     ev1.synchronize()
+    torch.cuda.profiler.stop()
     wall = time.time() - t0
     ms_dev = ev0.elapsed_time(ev1)
     clk = clocks.stop()
