@@ -24,9 +24,12 @@
 //              per TMEM lane quarter, one per half of the columns), stores,
 //              arrive on acc_empty.
 // Two accumulators (2 x 256 TMEM columns) let the epilogue of one tile run
-// under the MMAs of the next.  Tiles are dealt round-robin over the CTAs, the
-// column tiles of one work item consecutively (they share its operator chunks
-// through L2).  Every mbarrier wait is bounded: an expired wait sets a flag,
+// under the MMAs of the next.  Tiles are taken in order from a global
+// counter (the producer takes the next one and passes its index to the MMA
+// and epilogue roles through a small queue in shared memory): CTAs running at
+// once work on neighbouring tiles, which share operator chunks (the column
+// tiles of one work item) and X or ancestors' slot chunks, in L2, and a CTA
+// that drew short tiles takes more of them.  Every mbarrier wait is bounded: an expired wait sets a flag,
 // every role leaves its loop, the MMA issuer waits (bounded) for its
 // outstanding MMAs, TMEM is freed and the host sees the error flag.
 #include <algorithm>
@@ -54,7 +57,9 @@ constexpr int kS = FKF_TC_STAGES;
 constexpr int kEpiWarps = 8;               // warps 2-9: two per TMEM lane quarter, one per column half
 constexpr int kEpiLd = 33;                 // padded row of an epilogue staging tile (32 x 32 floats)
 constexpr int kEpiBytes = kEpiWarps * 32 * kEpiLd * 4;
-constexpr int kSmemBytes = kS * kStageBytes + 256 + kEpiBytes;  // 225.25 KB for 4 stages
+constexpr int kQ = 8;                      // tile-index queue (producer -> MMA, epilogue)
+constexpr int kTail = 384;                 // barriers, TMEM address, flag, queue
+constexpr int kSmemBytes = kS * kStageBytes + kTail + kEpiBytes;  // 225.4 KB for 4 stages
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 constexpr int kProdWarp = 0, kMmaWarp = 1;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -63,14 +68,16 @@ constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
 
 // barrier indices
-constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, NBAR = FIN + 1;
-static_assert(NBAR * 8 <= 192, "barrier area");
+constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1, QE = QF + kQ,
+              NBAR = QE + kQ;
+static_assert(NBAR * 8 <= 256, "barrier area");
 
 struct Smem {
   uint8_t* base;
   uint64_t* bar;
   uint32_t* tmem_slot;
   int* fail;
+  int64_t* q;  // [kQ] tile indices (-1: no more tiles)
   float* epi;  // kEpiWarps staging tiles
 
   __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kStageBytes; }
@@ -84,9 +91,10 @@ __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   s.base = base;
   uint8_t* tail = base + kS * kStageBytes;
   s.bar = reinterpret_cast<uint64_t*>(tail);
-  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 192);
-  s.fail = reinterpret_cast<int*>(tail + 224);
-  s.epi = reinterpret_cast<float*>(tail + 256);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 256);
+  s.fail = reinterpret_cast<int*>(tail + 264);
+  s.q = reinterpret_cast<int64_t*>(tail + 272);
+  s.epi = reinterpret_cast<float*>(tail + kTail);
   return s;
 }
 
@@ -192,11 +200,28 @@ struct Ph1 {
 };
 
 // ---- roles -----------------------------------------------------------------
+// Next tile of this CTA: taken from the global counter by the producer and
+// published in the queue; every consumer reads each queue entry once.
+__device__ __forceinline__ bool next_tile(const Smem& s, int qi, int64_t& id) {
+  const int slot = qi % kQ;
+  if (!wait_bar(s, QF + slot, (uint32_t)(qi / kQ) & 1)) return false;
+  id = *reinterpret_cast<volatile int64_t*>(&s.q[slot]);
+  umma::mbar_arrive(&s.bar[QE + slot]);
+  return id >= 0;
+}
+
 template <class Ph>
 __device__ __forceinline__ void producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct,
-                                         const uint8_t* astream) {
+                                         const uint8_t* astream, unsigned long long* counter) {
   int64_t g = 0;
-  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) {
+  for (int qi = 0;; qi++) {
+    int64_t id = (int64_t)atomicAdd(counter, 1ull);
+    if (id >= ntiles) id = -1;
+    const int slot = qi % kQ;
+    if (qi >= kQ && !wait_bar(s, QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
+    *reinterpret_cast<volatile int64_t*>(&s.q[slot]) = id;
+    umma::mbar_arrive(&s.bar[QF + slot]);
+    if (id < 0) return;
     const int64_t w = id / nct;
     const int ct = (int)(id % nct);
     const uint8_t* ap = astream + ph.a_chunk0(w) * (int64_t)kAChunkBytes;
@@ -237,7 +262,8 @@ __device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t 
   int64_t g = 0;
   int tl = 0;
   bool ok = true;
-  for (int64_t id = blockIdx.x; ok && id < ntiles; id += gridDim.x, tl++) {
+  int64_t id;
+  for (; ok && next_tile(s, tl, id); tl++) {
     const int nch = ph.nchunk(id / nct);
     const int b = tl & 1;
     if (tl >= 2 && !wait_bar(s, AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
@@ -294,7 +320,8 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
   const int half = (warp - 2) >> 2;
   const int row = 32 * quarter + lane;
   int tl = 0;
-  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
+  int64_t id;
+  for (; next_tile(s, tl, id); tl++) {
     const int b = tl & 1;
     if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
@@ -336,7 +363,8 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
   const int row = 32 * quarter + lane;
   float* tile = s.epi + (warp - 2) * 32 * kEpiLd;
   int tl = 0;
-  for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x, tl++) {
+  int64_t id;
+  for (; next_tile(s, tl, id); tl++) {
     const int b = tl & 1;
     if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
@@ -396,7 +424,7 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
 template <class Ph>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_apply(const Ph ph, int64_t nwork, int nct, int ncols, const uint8_t* __restrict__ astream,
-               int* __restrict__ err) {
+               unsigned long long* __restrict__ counter, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const Smem s = smem_layout(smem_raw);
   const int warp = threadIdx.x >> 5;
@@ -407,6 +435,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = AF; i < AE; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 32 * kEpiWarps);
     umma::mbar_init(&s.bar[FIN], 1);
+    for (int i = QF; i < QE; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = QE; i < NBAR; i++) umma::mbar_init(&s.bar[i], 1 + 32 * kEpiWarps);
     *s.fail = 0;
     umma::fence_mbar_init();
   }
@@ -416,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
   if (warp == kProdWarp) {
-    if ((threadIdx.x & 31) == 0) producer(s, ph, ntiles, nct, astream);
+    if ((threadIdx.x & 31) == 0) producer(s, ph, ntiles, nct, astream, counter);
   } else if (warp == kMmaWarp) {
     if ((threadIdx.x & 31) == 0) mma_issuer(s, ph, ntiles, nct, tmem);
     __syncwarp();
@@ -493,6 +523,8 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     FKF_TRY(dev_alloc(ctx, h->tc_err, 64));
     FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, ctx->stream));
   }
+  // tile counters of the two phases at tc_err + 16, + 24 bytes
+  unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
@@ -501,6 +533,7 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
     const int nct = (int)cdiv(nc, kN);
+    FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
     if (h->n_tcx > 0) {
       k_tc_split_x<<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
           X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), nct, h->xsplit.as<uint8_t>());
@@ -510,7 +543,7 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
       const Ph1 ph{h->tcp1.as<P1Item>(), h->xsplit.as<uint8_t>(), h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
                    h->part.as<float>(), P};
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
-      k_tc_apply<Ph1><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream,
+      k_tc_apply<Ph1><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream, counters,
                                                                    h->tc_err.as<int>());
       FKF_LAUNCHED(ctx);
     }
@@ -522,7 +555,7 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
                  Y + c0, ldy};
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
-    k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream,
+    k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream, counters + 1,
                                                                  h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
   }
