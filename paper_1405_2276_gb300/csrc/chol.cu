@@ -6,7 +6,7 @@
 // design keeps the sequential part short and spreads everything else over
 // the SMs: blocks of 32; a 32 x 32 diagonal block is factored by one CTA
 // (32 rank-1 steps in shared memory); the panel below it is solved row by row
-// (one thread per row, the factor block in shared memory, 32 rows per CTA);
+// (one warp per row, the factor block in shared memory, 8 rows per CTA);
 // the trailing matrix is updated by the symmetric FP64 tile GEMM (lower tiles
 // only).  The forward substitution X <- X L^-T for many right-hand sides uses
 // the same row solve per diagonal block and a GEMM update of the later
@@ -62,9 +62,13 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
 
 // X[r, 0:b] <- X[r, 0:b] Lkk^-T for rows r < rows (forward substitution per
 // row: x_j = (x_j - sum_{l<j} x_l Lkk[j][l]) / Lkk[j][j]); Lkk is the b x b
-// lower factor block at L (ld lda).  One thread per row, 32 rows per CTA.
-__global__ void __launch_bounds__(32) k_trsm_rows(double* __restrict__ X, int64_t ldx, int64_t rows, int b,
-                                                  const double* __restrict__ L, int64_t lda) {
+// lower factor block at L (ld lda).  One warp per row, lane j holding x_j:
+// after x_q is final it is broadcast and every later lane subtracts its term,
+// so a row costs b dependent steps of one FMA per lane (FP64 instructions are
+// slow per warp here; many short rows in flight use all the SMs).
+constexpr int kRowWarps = 8;
+__global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict__ X, int64_t ldx, int64_t rows,
+                                                              int b, const double* __restrict__ L, int64_t lda) {
   __shared__ double l[kB][kB + 1];
   __shared__ double dinv[kB];
   const int t = threadIdx.x;
@@ -75,22 +79,19 @@ __global__ void __launch_bounds__(32) k_trsm_rows(double* __restrict__ X, int64_
   __syncthreads();
   if (t < b) dinv[t] = 1.0 / l[t][t];
   __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + t;
+  const int lane = t & 31;
+  const int64_t r = (int64_t)blockIdx.x * kRowWarps + (t >> 5);
   if (r >= rows) return;
   double* xr = X + r * ldx;
-  double x[kB];
+  double s = lane < b ? xr[lane] : 0.0;
 #pragma unroll
-  for (int j = 0; j < kB; j++) x[j] = j < b ? xr[j] : 0.0;
-#pragma unroll
-  for (int j = 0; j < kB; j++) {
-    double s = x[j];
-#pragma unroll
-    for (int q = 0; q < j; q++) s -= x[q] * l[j][q];
-    x[j] = j < b ? s * dinv[j] : 0.0;
+  for (int q = 0; q < kB; q++) {
+    if (q >= b) break;
+    const double xq = __shfl_sync(0xffffffffu, s * dinv[q], q);
+    if (lane == q) s = xq;
+    if (lane > q) s -= xq * l[lane][q];
   }
-#pragma unroll
-  for (int j = 0; j < kB; j++)
-    if (j < b) xr[j] = x[j];
+  if (lane < b) xr[lane] = s;
 }
 
 }  // namespace
@@ -108,7 +109,7 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, DevBuf&
     const int rem = n - k0 - b;
     if (rem > 0) {
       double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
-      k_trsm_rows<<<(unsigned)cdiv(rem, 32), 32, 0, ctx->stream>>>(P, lda, rem, b, Akk, lda);
+      k_trsm_rows<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, ctx->stream>>>(P, lda, rem, b, Akk, lda);
       FKF_LAUNCHED(ctx);
       FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, P + b, lda));
     }
@@ -124,8 +125,8 @@ fkf_status trsm_lt_f64(fkf_ctx* ctx, int n, const double* L, int64_t lda, double
   if (n <= 0 || rows <= 0) return FKF_OK;
   for (int k0 = 0; k0 < n; k0 += kB) {
     const int b = std::min(kB, n - k0);
-    k_trsm_rows<<<(unsigned)cdiv(rows, 32), 32, 0, ctx->stream>>>(X + k0, ldx, rows, b,
-                                                                 L + (int64_t)k0 * lda + k0, lda);
+    k_trsm_rows<<<(unsigned)cdiv(rows, kRowWarps), 32 * kRowWarps, 0, ctx->stream>>>(X + k0, ldx, rows, b,
+                                                                                    L + (int64_t)k0 * lda + k0, lda);
     FKF_LAUNCHED(ctx);
     const int rem = n - k0 - b;
     if (rem > 0)
