@@ -205,6 +205,24 @@ def run_gpu(args, rank, world):
     log(f"[bench] FP32 path: {res['fp32']['ms_per_step']:.1f} ms/step; phases(ms) "
         + " ".join(f"{p:.1f}" for p in res["fp32"]["phases_ms"]))
 
+    # the same step forced through the merge path (GEP, orthonormalisation,
+    # merge, rotation) although the fixed geometry brings nothing outside span(W)
+    fu_steps = 2
+    fu_phases = np.zeros(6)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(fu_steps):
+        fkf.fkf_filter_step(f32, ys_d[k % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
+                            flags=fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_FULL_UPDATE, want_nll=False)
+        fu_phases += np.array(fkf.fkf_filter_phase_times(f32))
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_fu = ev0.elapsed_time(ev1) / fu_steps
+    res["fp32_full"] = dict(ms_per_step=ms_fu, steps_per_s=1e3 / ms_fu, steps=fu_steps,
+                            phases_ms=(fu_phases / fu_steps).tolist())
+    log(f"[bench] FP32 path, merge forced: {ms_fu:.1f} ms/step; phases(ms) "
+        + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]))
+
     # ---------------- H-apply alone (the dominant kernel), m = 1024 columns ----------------
     def time_apply(hm, info, prec, reps):
         dt = torch.float32 if prec == fkf.FKF_FP32 else torch.float64
@@ -411,11 +429,16 @@ def main():
         "warmup": args.warmup, "ms_per_step": fp32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (N-scale) + f64 (m x m)", "data": "synthetic",
         "config": {"workload": "2D 512x512 cross-well tomography, N=262144, m=1024 (32x32 rays), Matern nu=1/2 "
-                               "ell=0.05, H-matrix leaf 64 eta 1 ACA 1e-8 rank cap 32, R=1e-4 I, general path",
+                               "ell=0.05, H-matrix leaf 64 eta 1 ACA 1e-8 rank cap 32, R=1e-4 I, general step (fixed "
+                               "geometry: the basis is kept once the step brings nothing outside span(W); steps "
+                               "forced through the merge path in fp32_merge_forced)",
                    "global_batch": world, "seq_len": 0, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (H-matrix operator and W exceed 129 MB)"},
         "happly_gbs": ha["gbs"], "happly_ms": ha["ms"], "happly_tflops": ha["tflops"],
         "happly_simt_fp32": {k: res["happly32_simt"][k] for k in ("ms", "gbs", "tflops")},
+        "fp32_merge_forced": {"steps_per_s": res["fp32_full"]["steps_per_s"],
+                              "ms_per_step": res["fp32_full"]["ms_per_step"], "steps": res["fp32_full"]["steps"],
+                              "phases_ms": res["fp32_full"]["phases_ms"]},
         "fp64_path": ({"steps_per_s": res["fp64"]["steps_per_s"], "ms_per_step": res["fp64"]["ms_per_step"],
                        "happly_gbs": res["happly64"]["gbs"], "happly_ms": res["happly64"]["ms"],
                        "happly_tflops": res["happly64"]["tflops"], "phases_ms": res["fp64"]["phases_ms"]}

@@ -192,6 +192,9 @@ void fkf_filter_destroy(fkf_filter* f);
 /* Flags for fkf_filter_step. */
 #define FKF_STEP_INPUTS_ON_DEVICE 1 /* y, H_rowptr, H_col, H_val, R are device pointers */
 #define FKF_STEP_SKIP_MEAN_SYNC 2   /* do not copy the NLL to the host (nll_out ignored) */
+#define FKF_STEP_FULL_UPDATE 4      /* always take the merge path (GEP, orthonormalisation, merge,
+                                       rotation), even when the step brings no information outside
+                                       span(W) and the basis could be kept */
 
 /* One predict + update (Sec. 2.4 / Alg. extkalman without linearisation):
  *   y (m), H_k as CSR m x N (rowptr int64 m+1, col int32 original point

@@ -8,10 +8,10 @@
 // (32 rank-1 steps in shared memory); the panel below it is solved row by row
 // (one warp per row, the factor block in shared memory, 8 rows per CTA);
 // the trailing matrix is updated by the symmetric FP64 tile GEMM (lower tiles
-// only).  The forward substitution X <- X L^-T for many right-hand sides uses
-// the same row solve per diagonal block and a GEMM update of the later
-// columns.  Column-major BLAS reads this row-major lower factor as the upper
-// factor U = L^T of S = U^T U.
+// only).  Stopping after the first nf pivots of a bordered matrix
+// [[S, K], [K^T, E]] leaves the Schur complement E - K^T S^-1 K in the
+// trailing block.  Column-major BLAS reads this row-major lower factor as the
+// upper factor U = L^T of S = U^T U.
 #include <algorithm>
 #include <cmath>
 
@@ -96,13 +96,13 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
 
 }  // namespace
 
-fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, DevBuf& ws) {
-  if (n <= 0) return FKF_OK;
+fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws) {
+  if (n <= 0 || nf <= 0) return FKF_OK;
   if (ws.bytes < 256) FKF_TRY(dev_alloc(ctx, ws, 256));
   int* flag = ws.as<int>();
   FKF_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  for (int k0 = 0; k0 < n; k0 += kB) {
-    const int b = std::min(kB, n - k0);
+  for (int k0 = 0; k0 < nf; k0 += kB) {
+    const int b = std::min(kB, nf - k0);
     double* Akk = A + (int64_t)k0 * lda + k0;
     k_potrf_diag<<<1, 256, 0, ctx->stream>>>(Akk, lda, b, flag);
     FKF_LAUNCHED(ctx);
@@ -117,21 +117,6 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, DevBuf&
   int hflag = 0;
   FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (hflag) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d)", n);
-  return FKF_OK;
-}
-
-fkf_status trsm_lt_f64(fkf_ctx* ctx, int n, const double* L, int64_t lda, double* X, int64_t ldx, int64_t rows) {
-  if (n <= 0 || rows <= 0) return FKF_OK;
-  for (int k0 = 0; k0 < n; k0 += kB) {
-    const int b = std::min(kB, n - k0);
-    k_trsm_rows<<<(unsigned)cdiv(rows, kRowWarps), 32 * kRowWarps, 0, ctx->stream>>>(X + k0, ldx, rows, b,
-                                                                                    L + (int64_t)k0 * lda + k0, lda);
-    FKF_LAUNCHED(ctx);
-    const int rem = n - k0 - b;
-    if (rem > 0)
-      FKF_TRY(gemm_f64(ctx, false, true, rows, rem, b, -1.0, X + k0, ldx, L + (int64_t)(k0 + b) * lda + k0, lda, 1.0,
-                       X + k0 + b, ldx));
-  }
+  if (hflag) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d, %d pivots)", n, nf);
   return FKF_OK;
 }

@@ -23,16 +23,16 @@ fkf_status gram_f32(fkf_ctx* ctx, int64_t M, int64_t N, int64_t K, const float* 
 fkf_status scale_f64(fkf_ctx* ctx, int64_t M, int64_t N, double beta, double* C, int64_t ldc);
 fkf_status scale_f32(fkf_ctx* ctx, int64_t M, int64_t N, float beta, float* C, int64_t ldc);
 
-// Blocked Cholesky factorisation S = L L^T of an SPD n x n matrix (row-major,
-// ld lda; L in the lower triangle, the upper triangle is overwritten with
-// scratch).  Synchronises once; FKF_ENOTSPD if a pivot is not positive.
-fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, DevBuf& ws);
-// X (rows x n, ld ldx) <- X L^-T: row i becomes (L^-1 x_i)^T (forward
-// substitution), L from chol_blocked_f64.
-fkf_status trsm_lt_f64(fkf_ctx* ctx, int n, const double* L, int64_t lda, double* X, int64_t ldx, int64_t rows);
+// Blocked Cholesky factorisation of an SPD n x n matrix (row-major, ld lda),
+// stopped after its first nf pivots: the leading nf x nf block becomes the
+// factor L11 (lower triangle), the rows below it L21, and the trailing block
+// the Schur complement A22 - L21 L21^T (both triangles); the upper triangle of
+// the factored part is overwritten with scratch.  nf = n is the full
+// factorisation.  Synchronises once; FKF_ENOTSPD if a pivot is not positive.
+fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws);
 // Solve S x = b (nrhs contiguous vectors of length n) with the factor of
-// chol_blocked_f64 (ld n).
-fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, double* b, int nrhs);
+// chol_blocked_f64 (ld ldl).
+fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs);
 
 // Symmetric eigensolver (FP64): A (n x n, symmetric, row-major) is replaced
 // by Vt, whose row j is the unit eigenvector of eigenvalue w[j]; eigenvalues

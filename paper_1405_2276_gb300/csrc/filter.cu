@@ -310,14 +310,14 @@ __global__ void k_innovation(int m, const int64_t* __restrict__ rowptr, const in
 // As = (A + A^T)/2, At = diag(rs) As diag(rs); S = alpha' As + diag(R)
 __global__ void k_sym(int m, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
                       const double* __restrict__ rdiag, double alpha1, double* __restrict__ As,
-                      double* __restrict__ At, double* __restrict__ S) {
+                      double* __restrict__ At, double* __restrict__ S, int64_t lds) {
   const int64_t total = (int64_t)m * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / m), j = (int)(e % m);
     const double v = 0.5 * (A[(int64_t)i * lda + j] + A[(int64_t)j * lda + i]);
     As[e] = v;
     At[e] = v * rs[i] * rs[j];
-    S[e] = alpha1 * v + (i == j ? rdiag[i] : 0.0);
+    S[(int64_t)i * lds + j] = alpha1 * v + (i == j ? rdiag[i] : 0.0);
   }
 }
 
@@ -333,12 +333,12 @@ __global__ void k_scale_cols(int m, int r, const double* __restrict__ HW, int64_
 
 // NLL = 1/2 (nu^T z + log det S + m log 2 pi) with S's Cholesky factor on the diagonal
 __global__ void k_nll(int m, const double* __restrict__ nu, const double* __restrict__ z,
-                      const double* __restrict__ L, double* __restrict__ out) {
+                      const double* __restrict__ L, int64_t ldl, double* __restrict__ out) {
   __shared__ double sh[2][32];
   double a = 0, b = 0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     a += nu[i] * z[i];
-    b += log(L[(int64_t)i * m + i]);
+    b += log(L[(int64_t)i * ldl + i]);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -460,24 +460,36 @@ __global__ void k_lincomb(int n, double a, const double* A, double b, const doub
     C[e] = a * A[e] + (B ? b * B[e] : 0.0) + ((e / n == e % n) ? d : 0.0);
 }
 
-// E = diag(alpha1 - d) (r x r)
-// K^T = (alpha' HW - HW D)^T = (HW E)^T, r x m (HW: m x r, ld ldh; HWD: m x r, ld r)
-__global__ void k_hwe_t(int m, int r, const double* __restrict__ HW, int64_t ldh, const double* __restrict__ HWD,
-                        double alpha1, double* __restrict__ Kt) {
-  const int64_t total = (int64_t)m * r;
+// Rows m .. m+r-1 of the augmented matrix [[S, K], [K^T, E]] (ld lda):
+// [K^T | E] with K^T = (alpha' HW - HW D)^T (HW: m x r, ld ldh; HWD: m x r,
+// ld r) and E = alpha' I - D (D = diag(d) if d, else the full weight Df).
+__global__ void k_aug_rows(int m, int r, const double* __restrict__ HW, int64_t ldh, const double* __restrict__ HWD,
+                           const double* __restrict__ d, const double* __restrict__ Df, double alpha1,
+                           double* __restrict__ out, int64_t lda) {
+  const int64_t total = lda * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / m), j = (int)(e % m);
-    Kt[e] = alpha1 * HW[(int64_t)j * ldh + i] - HWD[(int64_t)j * r + i];
+    const int i = (int)(e / lda), j = (int)(e % lda);
+    double v;
+    if (j < m) {
+      v = alpha1 * HW[(int64_t)j * ldh + i] - HWD[(int64_t)j * r + i];
+    } else {
+      const int q = j - m;
+      v = d ? (i == q ? alpha1 - d[i] : 0.0) : (i == q ? alpha1 : 0.0) - Df[(int64_t)i * r + q];
+    }
+    out[(int64_t)i * lda + j] = v;
   }
 }
 
-__global__ void k_diag_from(int r, const double* __restrict__ d, double alpha1, double* __restrict__ E) {
-  const int64_t total = (int64_t)r * r;
+// C (n x n) = a A + d I for A with leading dimension lda
+__global__ void k_lincomb_ld(int n, double a, const double* __restrict__ A, int64_t lda, double d,
+                             double* __restrict__ C) {
+  const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / r), j = (int)(e % r);
-    E[e] = i == j ? alpha1 - d[i] : 0.0;
+    const int i = (int)(e / n), j = (int)(e % n);
+    C[e] = a * A[(int64_t)i * lda + j] + (i == j ? d : 0.0);
   }
 }
+
 
 // M[i, j] += B[i, j] + (i == j ? c : 0) for the leading r x r block of M (ld ldm)
 __global__ void k_add_block(int r, const double* __restrict__ B, double c, double* __restrict__ M, int64_t ldm) {
@@ -686,7 +698,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->HWA, m * nm));
   FKF_TRY(A(f->As, m * m));
   FKF_TRY(A(f->At, m * m));
-  FKF_TRY(A(f->S, m * m));
+  FKF_TRY(A(f->S, (m + r) * (m + r)));  // the augmented matrix [[S, K], [K^T, E]]
   FKF_TRY(A(f->a, m));
   FKF_TRY(A(f->C, m * m));
   FKF_TRY(A(f->lam, m));
@@ -902,44 +914,12 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_LAUNCHED(ctx);
   const double* HW = HWA;       // m x r, ld nm
   const double* Araw = HWA + r;  // m x m, ld nm
+  // S lives in the top-left m x m block of the augmented matrix (ld m + r)
+  const int64_t lda_aug = (int64_t)m + r;
   double* S = f->S.as<double>();
   k_sym<<<nblk((int64_t)m * m), 256, 0, st>>>(m, Araw, nm, f->rs.as<double>(), f->rdiag.as<double>(), alpha1,
-                                              f->As.as<double>(), f->At.as<double>(), S);
+                                              f->As.as<double>(), f->At.as<double>(), S, lda_aug);
   FKF_LAUNCHED(ctx);
-  // S = alpha' A + R - HW D HW^T   (D diagonal, or the full r x r weight Df)
-  const bool diag = f->diag;
-  double* Dfc = f->Df.as<double>();
-  if (r > 0) {
-    if (diag) {
-      k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
-      FKF_LAUNCHED(ctx);
-    } else {
-      FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
-    }
-    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, m));
-  }
-  FKF_TRY(chol_blocked_f64(ctx, m, S, m, f->cholws));
-  FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
-  FKF_TRY(chol_solve_rowlower_f64(ctx, m, S, f->z.as<double>(), 1));
-  k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, f->nll.as<double>());
-  FKF_LAUNCHED(ctx);
-  // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
-  if (r > 0) {
-    FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
-    if (diag) {
-      k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->uz.as<double>(), f->dbar.as<double>());
-      FKF_LAUNCHED(ctx);
-    } else {
-      FKF_TRY(gemm_f64(ctx, false, false, r, 1, r, 1.0, Dfc, r, f->uz.as<double>(), 1, 0.0, f->dbar.as<double>(), 1));
-    }
-  }
-  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, nullptr, f->dbar.as<double>(), f->z.as<double>(), alpha1,
-                                                     f->vcoef.as<T>());
-  FKF_LAUNCHED(ctx);
-  k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
-                                                       f->s_new.as<double>());
-  FKF_LAUNCHED(ctx);
-  FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
   // ---- does the step bring information outside span(W)?  The Gamma^-1-Gram
   // of G's component outside span(W) is A - HW HW^T (X^T G = (HW)^T, X^T W = I);
   // compared with A in the noise-whitened metric.
@@ -961,31 +941,62 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
     if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
   }
-  if (r > 0 && ratio <= f->new_tol) {
+  const bool kept = r > 0 && ratio <= f->new_tol && !(flags & FKF_STEP_FULL_UPDATE);
+  // S = alpha' A + R - HW D HW^T   (D diagonal, or the full r x r weight Df)
+  const bool diag = f->diag;
+  double* Dfc = f->Df.as<double>();
+  if (r > 0) {
+    if (diag) {
+      k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
+      FKF_LAUNCHED(ctx);
+    } else {
+      FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
+    }
+    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, lda_aug));
+  }
+  if (kept) {
     // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated
     // in information form, E' = (E^-1 + Q)^-1, E = alpha' I - D (predicted),
-    // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight)
-    // Evaluated in the Woodbury form E' = E - K^T S^-1 K, K = HW E, with the
-    // innovation covariance S = alpha' A - HW D HW^T + R = L L^T already
-    // factored for the mean (S = HW E HW^T + R up to the new_tol residual
-    // A - HW HW^T), and HW D already formed for S: E' = E - V^T V with
-    // V = L^-1 K (one forward substitution with r right-hand sides and one
-    // symmetric r x r x m product), no r x r factorisation.
-    double* Ep = f->Ep.as<double>();
-    double* Dn2 = f->Dfn.as<double>();
-    double* Yt = f->J.as<double>();  // r x m: K^T, then (L^-1 K)^T
-    const int64_t rr = (int64_t)r * r;
+    // Q = HW^T R^-1 HW  (Alg. kalmanconstantH with a non-diagonal weight),
+    // evaluated in the Woodbury form E' = E - K^T S^-1 K, K = HW E, with the
+    // innovation covariance S = alpha' A - HW D HW^T + R (= HW E HW^T + R up to
+    // the new_tol residual A - HW HW^T).  Both come out of one Cholesky
+    // factorisation of the augmented matrix [[S, K], [K^T, E]] stopped after
+    // its first m pivots: the leading block is S's factor L (for the mean and
+    // the NLL) and the trailing block the Schur complement E - K^T S^-1 K = E'.
+    double* Eaug = S + (int64_t)m * lda_aug;  // rows m.. : [K^T | E]
+    k_aug_rows<<<nblk(lda_aug * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), diag ? f->D.as<double>() : nullptr,
+                                                 diag ? nullptr : Dfc, alpha1, Eaug, lda_aug);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(chol_blocked_f64(ctx, m + r, m, S, lda_aug, f->cholws));
+  } else {
+    FKF_TRY(chol_blocked_f64(ctx, m, m, S, lda_aug, f->cholws));
+  }
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
+  FKF_TRY(chol_solve_rowlower_f64(ctx, m, S, lda_aug, f->z.as<double>(), 1));
+  k_nll<<<1, 256, 0, st>>>(m, f->nu.as<double>(), f->z.as<double>(), S, lda_aug, f->nll.as<double>());
+  FKF_LAUNCHED(ctx);
+  // mean: s' = s + [W G] [-D (HW^T z); alpha' z]
+  if (r > 0) {
+    FKF_TRY(gemm_f64(ctx, true, false, r, 1, m, 1.0, HW, nm, f->z.as<double>(), 1, 0.0, f->uz.as<double>(), 1));
     if (diag) {
-      k_diag_from<<<nblk(rr), 256, 0, st>>>(r, f->D.as<double>(), alpha1, Ep);
+      k_vmul<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), f->uz.as<double>(), f->dbar.as<double>());
+      FKF_LAUNCHED(ctx);
     } else {
-      k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Dfc, 0.0, nullptr, alpha1, Ep);
+      FKF_TRY(gemm_f64(ctx, false, false, r, 1, r, 1.0, Dfc, r, f->uz.as<double>(), 1, 0.0, f->dbar.as<double>(), 1));
     }
-    FKF_LAUNCHED(ctx);
-    k_hwe_t<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), alpha1, Yt);
-    FKF_LAUNCHED(ctx);
-    FKF_TRY(trsm_lt_f64(ctx, m, S, m, Yt, m, r));
-    FKF_TRY(gemm_sym_f64(ctx, false, true, r, m, -1.0, Yt, m, Yt, m, 1.0, Ep, r));
-    k_lincomb<<<nblk(rr), 256, 0, st>>>(r, -1.0, Ep, 0.0, nullptr, alpha1, Dn2);  // D' = alpha' I - E'
+  }
+  k_mean_coef<T><<<(int)cdiv(nm, 256), 256, 0, st>>>(r, m, nullptr, f->dbar.as<double>(), f->z.as<double>(), alpha1,
+                                                     f->vcoef.as<T>());
+  FKF_LAUNCHED(ctx);
+  k_gemv_add<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, nm, Wc, ld, f->vcoef.as<T>(), f->s_hat.as<double>(),
+                                                       f->s_new.as<double>());
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
+  if (kept) {
+    double* Dn2 = f->Dfn.as<double>();
+    // D' = alpha' I - E' (E' = trailing r x r block of the augmented factorisation)
+    k_lincomb_ld<<<nblk((int64_t)r * r), 256, 0, st>>>(r, -1.0, S + (int64_t)m * lda_aug + m, lda_aug, alpha1, Dn2);
     FKF_LAUNCHED(ctx);
     for (int e = 4; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
     double nll = 0;
@@ -1702,7 +1713,7 @@ static fkf_status nll_gradient_impl(fkf_hmat* h, int K, int m, const double* y, 
     FKF_LAUNCHED(ctx);
     FKF_CUDA(ctx, cudaMemcpyAsync(z.p, nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
     FKF_TRY(chol_solve_f64(ctx, m, S.as<double>(), z.as<double>(), 1));
-    k_nll<<<1, 256, 0, st>>>(m, nu.as<double>(), z.as<double>(), S.as<double>(), nll_acc.as<double>());
+    k_nll<<<1, 256, 0, st>>>(m, nu.as<double>(), z.as<double>(), S.as<double>(), m, nll_acc.as<double>());
     FKF_LAUNCHED(ctx);
     double nk = 0;
     FKF_CUDA(ctx, cudaMemcpyAsync(&nk, nll_acc.p, 8, cudaMemcpyDeviceToHost, st));

@@ -79,13 +79,13 @@ fkf_status chol_solve_f64(fkf_ctx* ctx, int n, const double* Afact, double* b, i
   return FKF_OK;
 }
 
-fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, double* b, int nrhs) {
+fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs) {
   if (n == 0 || nrhs == 0) return FKF_OK;
   cusolverDnHandle_t h;
   FKF_TRY(solver(ctx, &h));
   if (ctx->solver_info.bytes < 256) FKF_TRY(dev_alloc(ctx, ctx->solver_info, 256));
   // the row-major lower factor is the column-major upper factor U = L^T, S = U^T U
-  if (cusolverDnDpotrs(h, CUBLAS_FILL_MODE_UPPER, n, nrhs, L, n, b, n, ctx->solver_info.as<int>()) !=
+  if (cusolverDnDpotrs(h, CUBLAS_FILL_MODE_UPPER, n, nrhs, L, (int)ldl, b, n, ctx->solver_info.as<int>()) !=
       CUSOLVER_STATUS_SUCCESS)
     return set_err(ctx, FKF_ECUDA, "potrs failed");
   ctx->lib_calls++;
