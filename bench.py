@@ -205,6 +205,24 @@ def run_gpu(args, rank, world):
     log(f"[bench] FP32 path: {res['fp32']['ms_per_step']:.1f} ms/step; phases(ms) "
         + " ".join(f"{p:.1f}" for p in res["fp32"]["phases_ms"]))
 
+    # the fixed-H fast path (opt-in): the same operator every step, its products
+    # with Gamma reused (Alg. kalmanconstantH); one step to take the kept path
+    fx_steps = 5
+    fx_flags = fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_ALLOW_FIXED_H
+    fkf.fkf_filter_step(f32, ys_d[0], m, rowptr_d, col_d, val_d, None, w["noise"], flags=fx_flags, want_nll=False)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    fx_paths = []
+    for k in range(fx_steps):
+        fkf.fkf_filter_step(f32, ys_d[(k + 1) % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
+                            flags=fx_flags, want_nll=False)
+        fx_paths.append(fkf.fkf_filter_get_stats(f32)["last_path"])
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_fx = ev0.elapsed_time(ev1) / fx_steps
+    res["fp32_fixed_h"] = dict(ms_per_step=ms_fx, steps_per_s=1e3 / ms_fx, steps=fx_steps, paths=fx_paths)
+    log(f"[bench] FP32 fixed-H fast path: {ms_fx:.2f} ms/step, paths {fx_paths}")
+
     # the same step forced through the merge path (GEP, orthonormalisation,
     # merge, rotation) although the fixed geometry brings nothing outside span(W)
     fu_steps = 2
@@ -436,6 +454,11 @@ def main():
                    "l2": "inputs larger than L2 (H-matrix operator and W exceed 129 MB)"},
         "happly_gbs": ha["gbs"], "happly_ms": ha["ms"], "happly_tflops": ha["tflops"],
         "happly_simt_fp32": {k: res["happly32_simt"][k] for k in ("ms", "gbs", "tflops")},
+        "fp32_fixed_h_fast_path": {"steps_per_s": res["fp32_fixed_h"]["steps_per_s"],
+                                   "ms_per_step": res["fp32_fixed_h"]["ms_per_step"],
+                                   "steps": res["fp32_fixed_h"]["steps"],
+                                   "note": "opt-in FKF_STEP_ALLOW_FIXED_H: H_k, R_k unchanged, products with "
+                                           "Gamma reused; not the headline"},
         "fp32_merge_forced": {"steps_per_s": res["fp32_full"]["steps_per_s"],
                               "ms_per_step": res["fp32_full"]["ms_per_step"], "steps": res["fp32_full"]["steps"],
                               "phases_ms": res["fp32_full"]["phases_ms"]},

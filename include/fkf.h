@@ -195,6 +195,10 @@ void fkf_filter_destroy(fkf_filter* f);
 #define FKF_STEP_FULL_UPDATE 4      /* always take the merge path (GEP, orthonormalisation, merge,
                                        rotation), even when the step brings no information outside
                                        span(W) and the basis could be kept */
+#define FKF_STEP_ALLOW_FIXED_H 8    /* fixed-H fast path (Alg. kalmanconstantH): if H_k and R_k are
+                                       byte-identical to the previous step's and that step kept the
+                                       basis, reuse its products G = Gamma_H H^T and H [W G] instead
+                                       of recomputing them (no densify, no H-apply, no gathers) */
 
 /* One predict + update (Sec. 2.4 / Alg. extkalman without linearisation):
  *   y (m), H_k as CSR m x N (rowptr int64 m+1, col int32 original point
@@ -241,7 +245,8 @@ typedef struct {
   int32_t r;          /* rank of the low-rank term */
   int32_t last_path;  /* last step: 0 = new directions merged (GEP, orthonormalisation,
                          merge, rotation); 1 = no information outside span(W): basis kept,
-                         weight updated in information form */
+                         weight updated in information form; 3 = as 1 with the previous
+                         step's products reused (FKF_STEP_ALLOW_FIXED_H, unchanged H_k, R_k) */
   int32_t diagonal;   /* 1 if the weight is currently diagonal (the paper's D_k) */
 } fkf_filter_stats;
 fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);

@@ -183,6 +183,15 @@ __global__ void k_csc_sort(int64_t n, const int64_t* __restrict__ colptr, int* _
   }
 }
 
+// *diff |= (a[i] != b[i]) over n 32-bit words (byte comparison of two arrays)
+__global__ void k_words_differ(int64_t n, const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                               int* __restrict__ diff) {
+  bool d = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d |= a[i] != b[i];
+  if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(diff, 1);
+}
+
 // Bt (n x m, cluster order) += H^T from the sorted CSC form: thread per
 // column of H = row of Bt; duplicates are summed in the sorted order.
 template <typename T>
@@ -679,7 +688,16 @@ struct fkf_filter {
   bool diag = true;
   DevBuf Df, Dfn, Ep, Qm;
   double new_tol = 0;  // relative information outside span(W) below which the basis is kept
-  int last_path = 0;   // 0: general merge, 1: basis kept (no new directions)
+  int last_path = 0;   // 0: general merge, 1: basis kept (no new directions), 3: fixed-H reuse
+  // The last step kept the basis, and G, [HW | A], the dense H^T and its CSC
+  // index still hold that step's products for the current W (prev_*: its H and R).
+  bool products_valid = false;
+  int prev_m = -1;
+  int64_t prev_nnz = -1;
+  std::vector<int64_t> prev_rp;
+  std::vector<double> prev_rdiag;
+  std::vector<int32_t> prev_col;  // host copies, kept for host-side inputs only
+  std::vector<double> prev_val;
   // step inputs
   DevBuf rowptr, col, val, y, rdiag, rs, flag;
   DevBuf cnt, cursor, colptr, crow, cval;
@@ -853,15 +871,46 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       return set_err(ctx, FKF_EINVAL, "filter_step: R[%d] must be finite and > 0", j);
     rs[j] = 1.0 / std::sqrt(rdiag[j]);
   }
+  // ---- fixed-H fast path (opt-in): H and R byte-identical to the previous
+  // step's, which kept the basis, so G = Gamma_H H^T, [HW | A] and the basis
+  // decision are unchanged (Alg. kalmanconstantH: the products with Gamma are
+  // formed once for a constant H)
+  const bool allow_fixed = (flags & FKF_STEP_ALLOW_FIXED_H) && !(flags & FKF_STEP_FULL_UPDATE);
+  bool reuse = false;
+  if (allow_fixed && f->products_valid && m == f->prev_m && nnz == f->prev_nnz && rp == f->prev_rp &&
+      rdiag == f->prev_rdiag) {
+    if (on_dev) {
+      int* diff = f->flag.as<int>() + 8;
+      FKF_CUDA(ctx, cudaMemsetAsync(diff, 0, sizeof(int), st));
+      if (nnz > 0) {
+        k_words_differ<<<nblk(nnz), 256, 0, st>>>(nnz, reinterpret_cast<const uint32_t*>(col_in),
+                                                 f->col.as<uint32_t>(), diff);
+        FKF_LAUNCHED(ctx);
+        k_words_differ<<<nblk(2 * nnz), 256, 0, st>>>(2 * nnz, reinterpret_cast<const uint32_t*>(val_in),
+                                                     f->val.as<uint32_t>(), diff);
+        FKF_LAUNCHED(ctx);
+      }
+      int hd = 1;
+      FKF_CUDA(ctx, cudaMemcpyAsync(&hd, diff, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FKF_CUDA(ctx, cudaStreamSynchronize(st));
+      reuse = hd == 0;
+    } else {
+      reuse = (size_t)nnz == f->prev_col.size() && std::memcmp(col_in, f->prev_col.data(), nnz * 4) == 0 &&
+              std::memcmp(val_in, f->prev_val.data(), nnz * 8) == 0;
+    }
+  }
+  f->products_valid = false;  // set again when this step keeps the basis
   if (f->col.bytes < (size_t)std::max<int64_t>(nnz, 1) * 4) FKF_TRY(dev_alloc(ctx, f->col, std::max<int64_t>(nnz, 1) * 4));
   if (f->val.bytes < (size_t)std::max<int64_t>(nnz, 1) * 8) FKF_TRY(dev_alloc(ctx, f->val, std::max<int64_t>(nnz, 1) * 8));
   if (f->crow.bytes < (size_t)std::max<int64_t>(nnz, 1) * 4) FKF_TRY(dev_alloc(ctx, f->crow, std::max<int64_t>(nnz, 1) * 4));
   if (f->cval.bytes < (size_t)std::max<int64_t>(nnz, 1) * 8) FKF_TRY(dev_alloc(ctx, f->cval, std::max<int64_t>(nnz, 1) * 8));
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  FKF_CUDA(ctx, cudaMemcpyAsync(f->rowptr.p, rowptr_in, (m + 1) * 8, kind, st));
-  if (nnz > 0) {
-    FKF_CUDA(ctx, cudaMemcpyAsync(f->col.p, col_in, nnz * 4, kind, st));
-    FKF_CUDA(ctx, cudaMemcpyAsync(f->val.p, val_in, nnz * 8, kind, st));
+  if (!reuse) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(f->rowptr.p, rowptr_in, (m + 1) * 8, kind, st));
+    if (nnz > 0) {
+      FKF_CUDA(ctx, cudaMemcpyAsync(f->col.p, col_in, nnz * 4, kind, st));
+      FKF_CUDA(ctx, cudaMemcpyAsync(f->val.p, val_in, nnz * 8, kind, st));
+    }
   }
   FKF_CUDA(ctx, cudaMemcpyAsync(f->y.p, y_in, m * 8, kind, st));
   FKF_CUDA(ctx, cudaMemcpyAsync(f->rdiag.p, rdiag.data(), m * 8, cudaMemcpyHostToDevice, st));
@@ -883,32 +932,36 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   const double* val = f->val.as<double>();
 
   FKF_CUDA(ctx, cudaEventRecord(f->ev[0], st));
-  // ---- S1: column index of H (CSC, cluster order) and the dense H^T
-  FKF_CUDA(ctx, cudaMemsetAsync(f->cnt.p, 0, (size_t)n * 4, st));
-  FKF_CUDA(ctx, cudaMemsetAsync(f->cursor.p, 0, (size_t)n * 4, st));
-  k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>(),
-                                                                f->flag.as<int>());
-  FKF_LAUNCHED(ctx);
-  FKF_TRY(scan_counts(ctx, n, f->cnt.as<int>(), f->colptr.as<int64_t>(), f->scanws));
-  k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
-                                                               f->cursor.as<int>(), f->crow.as<int>(),
-                                                               f->cval.as<double>());
-  FKF_LAUNCHED(ctx);
-  k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
-  FKF_LAUNCHED(ctx);
-  FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
-  k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
-                                                      f->cval.as<double>(), f->Bt.as<T>(), m);
-  FKF_LAUNCHED(ctx);
-  FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
-  // ---- S2: G = Gamma_H H^T
-  FKF_TRY(hmat_apply_clustered(h, f->Bt.p, m, G, ld, m));
-  FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
-  // ---- gathers: [HW | A] = H [W G]; innovation
   const int nm = r + m;
   double* HWA = f->HWA.as<double>();
-  csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm, st);
-  FKF_LAUNCHED(ctx);
+  if (!reuse) {
+    // ---- S1: column index of H (CSC, cluster order) and the dense H^T
+    FKF_CUDA(ctx, cudaMemsetAsync(f->cnt.p, 0, (size_t)n * 4, st));
+    FKF_CUDA(ctx, cudaMemsetAsync(f->cursor.p, 0, (size_t)n * 4, st));
+    k_csc_count<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, iperm, n, f->cnt.as<int>(),
+                                                                  f->flag.as<int>());
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(scan_counts(ctx, n, f->cnt.as<int>(), f->colptr.as<int64_t>(), f->scanws));
+    k_csc_fill<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->colptr.as<int64_t>(),
+                                                                 f->cursor.as<int>(), f->crow.as<int>(),
+                                                                 f->cval.as<double>());
+    FKF_LAUNCHED(ctx);
+    k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
+    k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
+                                                        f->cval.as<double>(), f->Bt.as<T>(), m);
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
+    // ---- S2: G = Gamma_H H^T
+    FKF_TRY(hmat_apply_clustered(h, f->Bt.p, m, G, ld, m));
+    FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
+    // ---- gathers: [HW | A] = H [W G]; innovation
+    csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm, st);
+    FKF_LAUNCHED(ctx);
+  } else {
+    for (int e = 1; e < 3; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
+  }
   k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->s_hat.as<double>(),
                                                                f->y.as<double>(), f->nu.as<double>());
   FKF_LAUNCHED(ctx);
@@ -923,8 +976,8 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   // ---- does the step bring information outside span(W)?  The Gamma^-1-Gram
   // of G's component outside span(W) is A - HW HW^T (X^T G = (HW)^T, X^T W = I);
   // compared with A in the noise-whitened metric.
-  double ratio = 1.0;
-  {
+  double ratio = reuse ? 0.0 : 1.0;  // unchanged H, W and G: the previous step's decision stands
+  if (!reuse) {
     double* nrm = f->nll.as<double>() + 1;
     if (r > 0) {
       double* T0 = f->Tm.as<double>();
@@ -1009,7 +1062,22 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     f->diag = false;
     f->alpha = alpha1;
     f->k++;
-    f->last_path = 1;
+    f->last_path = reuse ? 3 : 1;
+    // this step's products stay valid for the next step with the same H and R
+    f->products_valid = true;
+    if (!reuse) {
+      f->prev_m = m;
+      f->prev_nnz = nnz;
+      f->prev_rp = rp;
+      f->prev_rdiag = rdiag;
+      if (allow_fixed && !on_dev) {
+        f->prev_col.assign(col_in, col_in + nnz);
+        f->prev_val.assign(val_in, val_in + nnz);
+      } else {
+        f->prev_col.clear();
+        f->prev_val.clear();
+      }
+    }
     if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
     for (int i = 0; i < 6; i++) {
       float ms = 0;
@@ -1207,6 +1275,7 @@ static fkf_status canonicalize_impl(fkf_filter* f) {
   FKF_CUDA(ctx, cudaGetLastError());
   f->cur = 1 - f->cur;
   f->diag = true;
+  f->products_valid = false;
   return FKF_OK;
 }
 
@@ -1427,6 +1496,7 @@ static fkf_status refresh_impl(fkf_filter* f) {
   FKF_CUDA(ctx, cudaGetLastError());
   std::swap(f->D.p, f->Dn.p);
   f->cur = 1 - f->cur;
+  f->products_valid = false;
   return FKF_OK;
 }
 
@@ -1515,6 +1585,7 @@ fkf_status filter_restore(fkf_filter* f, const char* path) {
   f->k = hd.k;
   f->alpha = hd.alpha;
   f->diag = true;
+  f->products_valid = false;
   return FKF_OK;
 }
 

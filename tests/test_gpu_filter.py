@@ -325,3 +325,56 @@ def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
     fkf.fkf_filter_destroy(f)
     fkf.fkf_hmatrix_destroy(hm)
     fkf.fkf_destroy(ctx)
+
+
+@pytest.mark.parametrize("device_inputs", [False, True])
+def test_fixed_h_fast_path_reuses_products_exactly(fkf, device_inputs):
+    """FKF_STEP_ALLOW_FIXED_H with a repeated operator: after the first
+    kept-basis step the products G = Gamma_H H^T and H [W G] are reused (path
+    3); every result equals the run that recomputes them (the reused arrays
+    are the ones the recomputation would produce bit for bit).  A changed H
+    entry is detected and recomputed."""
+    import torch
+
+    rng = np.random.default_rng(synth.BASE_SEED + 11)
+    nx = ny = 20
+    pts = synth.grid_points_2d(nx, ny)
+    p0, p1 = synth.cross_well_geometry_2d(6, 4)
+    Ha = synth.trace_rays_2d(nx, ny, p0, p1)
+    ys = [rng.standard_normal(Ha.nrows) * 0.3 for _ in range(6)]
+    n = pts.shape[0]
+
+    def arrays(h, y):
+        if not device_inputs:
+            return y, h.rowptr, h.col, h.val
+        return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (y, h.rowptr, h.col, h.val))
+
+    def run(allow, seq):
+        ctx = fkf.fkf_create(0)
+        hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.25, 1.0, leaf=32, eta=1.0, aca_tol=1e-10)
+        f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, 24, 48)
+        flags = (fkf.FKF_STEP_ALLOW_FIXED_H if allow else 0) | (fkf.FKF_STEP_INPUTS_ON_DEVICE if device_inputs else 0)
+        nlls, paths = [], []
+        for y, h in seq:
+            yy, rp, cc, vv = arrays(h, y)
+            nlls.append(fkf.fkf_filter_step(f, yy, h.nrows, rp, cc, vv, None, 1e-4, flags=flags))
+            paths.append(fkf.fkf_filter_get_stats(f)["last_path"])
+        st = fkf.fkf_filter_get(f, n)
+        fkf.fkf_filter_destroy(f)
+        fkf.fkf_hmatrix_destroy(hm)
+        fkf.fkf_destroy(ctx)
+        return nlls, paths, st
+
+    seq = [(y, Ha) for y in ys]
+    a_nll, a_paths, a_st = run(False, seq)
+    b_nll, b_paths, b_st = run(True, seq)
+    assert a_paths == [0, 1, 1, 1, 1, 1]
+    assert b_paths == [0, 1, 3, 3, 3, 3]
+    assert a_nll == b_nll
+    np.testing.assert_array_equal(a_st["s"], b_st["s"])
+    np.testing.assert_array_equal(a_st["D"], b_st["D"])
+    # one changed value in H: no reuse for that step
+    Hc = synth.Csr(Ha.rowptr.copy(), Ha.col.copy(), Ha.val.copy(), Ha.ncols)
+    Hc.val[3] *= 1.0 + 1e-12
+    c_nll, c_paths, _ = run(True, seq[:3] + [(ys[3], Hc)] + seq[4:])
+    assert c_paths[:3] == [0, 1, 3] and c_paths[3] != 3
