@@ -227,19 +227,22 @@ def run_gpu(args, rank, world):
     # merge, rotation) although the fixed geometry brings nothing outside span(W)
     fu_steps = 2
     fu_phases = np.zeros(6)
+    fu_stats = []
     torch.cuda.synchronize()
     ev0.record(stream)
     for k in range(fu_steps):
         fkf.fkf_filter_step(f32, ys_d[k % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
                             flags=fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_FULL_UPDATE, want_nll=False)
         fu_phases += np.array(fkf.fkf_filter_phase_times(f32))
+        st = fkf.fkf_filter_get_stats(f32)
+        fu_stats.append({k2: st[k2] for k2 in ("r", "gep_rank", "new_dirs", "t_eig", "t_lmax")})
     ev1.record(stream)
     ev1.synchronize()
     ms_fu = ev0.elapsed_time(ev1) / fu_steps
     res["fp32_full"] = dict(ms_per_step=ms_fu, steps_per_s=1e3 / ms_fu, steps=fu_steps,
-                            phases_ms=(fu_phases / fu_steps).tolist())
+                            phases_ms=(fu_phases / fu_steps).tolist(), step_stats=fu_stats)
     log(f"[bench] FP32 path, merge forced: {ms_fu:.1f} ms/step; phases(ms) "
-        + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]))
+        + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]) + f"; {fu_stats}")
 
     # ---------------- H-apply alone (the dominant kernel), m = 1024 columns ----------------
     def time_apply(hm, info, prec, reps):

@@ -166,6 +166,20 @@ fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t l
  * Errors: EINVAL (arguments, operator too large for the scratch), ECUDA. */
 fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev,
                                                int64_t ldy, int64_t ncols);
+/* Basis rotation product of the merge step (Alg. lowrankaddition, the
+ * rotation W' = [W G] E of the new factor): C = A E[0:K, 0:ncols] for
+ * row-major FP32 device arrays A (rows x K, leading dimension lda), E
+ * (ke x ncols, lde; ke >= K) and C (rows x ncols, ldc), on the 5th-generation
+ * tensor cores (tcgen05.mma kind::tf32 with a 3xTF32 split, FP32
+ * accumulation in TMEM) -- the kernel the FP32 filter step uses for W' and
+ * X'.  The caller owns the three arrays; C must not overlap A or E.  The
+ * context keeps a workspace (about 8 bytes per element of A plus 8 per
+ * element of E, grown on demand).  The context's stream is synchronised
+ * before return.  Errors: EINVAL (negative sizes, K > ke, a leading
+ * dimension below the row length, C overlapping A or E), ENOMEM, ECUDA,
+ * ETIMEOUT (a tensor-core wait expired). */
+fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t rows, int32_t K, const float* E_dev,
+                          int64_t lde, int64_t ke, int32_t ncols, float* C_dev, int64_t ldc);
 /* Engine of the H-apply for an FP32 operator: 1 (default) = 5th-generation
  * tensor cores (tcgen05.mma kind::tf32 with a 3xTF32 split, FP32
  * accumulation in TMEM); 0 = the FP32 SIMT tile engine.  FP64 operators
@@ -248,6 +262,13 @@ typedef struct {
                          weight updated in information form; 3 = as 1 with the previous
                          step's products reused (FKF_STEP_ALLOW_FIXED_H, unchanged H_k, R_k) */
   int32_t diagonal;   /* 1 if the weight is currently diagonal (the paper's D_k) */
+  /* last merge step (last_path 0): */
+  int32_t gep_rank;   /* data-space GEP eigenvalues kept (above gep_tol * max) */
+  int32_t new_dirs;   /* new Gamma^-1-orthonormal directions merged (T eigenvalues above orth_tol) */
+  int32_t t_eig;      /* 1 if T = I - P^T P was eigendecomposed; 0 if a bound showed
+                         every eigenvalue below orth_tol (Frobenius norm, or a power
+                         iteration estimate below orth_tol / 2) */
+  double t_lmax;      /* largest eigenvalue of T found (or its bound / estimate) */
 } fkf_filter_stats;
 fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);
 

@@ -8,6 +8,7 @@
 #include <new>
 #include <thread>
 #include <algorithm>
+#include <utility>
 
 #include "common.h"
 #include "hmat_host.h"
@@ -201,6 +202,31 @@ FKF_API fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* 
   FKF_TRY(hmat_apply_clustered_noalloc(h, X_dev, ldx, Y_dev, ldy, ncols));
   FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
   return FKF_OK;
+}
+
+FKF_API fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t rows, int32_t K,
+                                  const float* E_dev, int64_t lde, int64_t ke, int32_t ncols, float* C_dev,
+                                  int64_t ldc) {
+  if (!ctx) return FKF_EINVAL;
+  if (rows < 0 || K < 0 || ke < K || ncols < 0 || lda < K || lde < ncols || ldc < ncols)
+    return set_err(ctx, FKF_EINVAL, "fkf_rotate_f32: bad sizes");
+  if (rows == 0 || ncols == 0) return FKF_OK;
+  if (!A_dev || !E_dev || !C_dev) return set_err(ctx, FKF_EINVAL, "fkf_rotate_f32: null pointer");
+  auto span = [](const float* p, int64_t nr, int64_t ld, int64_t nc) {
+    const char* b = reinterpret_cast<const char*>(p);
+    return std::make_pair(b, b + ((nr - 1) * ld + nc) * (int64_t)sizeof(float));
+  };
+  auto overlap = [](std::pair<const char*, const char*> a, std::pair<const char*, const char*> b) {
+    return a.first < b.second && b.first < a.second;
+  };
+  const auto c = span(C_dev, rows, ldc, ncols);
+  if ((K > 0 && overlap(c, span(A_dev, rows, lda, K))) || (K > 0 && overlap(c, span(E_dev, K, lde, ncols))))
+    return set_err(ctx, FKF_EINVAL, "fkf_rotate_f32: C overlaps A or E");
+  const TcGemmProblem p{A_dev, lda, rows, K, C_dev, ldc};
+  FKF_TRY(tc_gemm_f32(ctx, &p, 1, E_dev, lde, ke, ncols, ctx->gemm_ws));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FKF_CUDA(ctx, cudaGetLastError());
+  return tc_gemm_check(ctx, ctx->gemm_ws);
 }
 
 FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,

@@ -33,6 +33,12 @@ struct DevBuf {
 };
 
 
+// Workspace of the tensor-core dense GEMM (split operands, error flag and
+// tile counter).
+struct TcGemmWs {
+  DevBuf asplit, bsplit, ctl;
+};
+
 struct fkf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -42,6 +48,7 @@ struct fkf_ctx {
   std::atomic<int64_t> launches{0};   // kernels of this library
   std::atomic<int64_t> lib_calls{0};  // cuSOLVER routine calls
   DevBuf solver_info;  // status word for cuSOLVER calls
+  TcGemmWs gemm_ws;    // fkf_rotate_f32
 };
 
 // Error plumbing: every internal function returns fkf_status and records a
@@ -223,6 +230,19 @@ void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector
 // Uploads the tensor-core schedule and writes the split operator streams
 // (after fac/nearv are on the device).
 fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu);
+// Dense C_p = A_p B[0:K_p, 0:ncols] for p < np <= 2 (row-major FP32 in and
+// out) on the tensor cores with 3xTF32 products; B has kb >= K_p rows.  The
+// launch is asynchronous: tc_gemm_check reads the error flag after a sync.
+struct TcGemmProblem {
+  const float* A;
+  int64_t lda, rows;
+  int K;
+  float* C;
+  int64_t ldc;
+};
+fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
+                       int ncols, TcGemmWs& ws);
+fkf_status tc_gemm_check(fkf_ctx* ctx, TcGemmWs& ws);
 
 // hbuild.cpp
 fkf_status hmat_build_host(fkf_ctx* ctx, const double* pts, int64_t n, int dim, fkf_matern k, fkf_hparams hp,

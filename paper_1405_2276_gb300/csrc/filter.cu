@@ -551,6 +551,12 @@ __global__ void k_frob_final(const double* __restrict__ part, double* __restrict
   }
 }
 
+__global__ void k_fill_start(int n, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // a fixed start vector with no special structure: 1 + (i mod 7) / 7, alternating sign
+  if (i < n) v[i] = (i & 1 ? -1.0 : 1.0) * (1.0 + (i % 7) / 7.0);
+}
+
 // out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
 static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part,
                        double* out) {
@@ -560,6 +566,36 @@ static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* r
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }
+
+// v = w / nrm[0] (n entries)
+__global__ void k_scale_by(int n, const double* __restrict__ w, const double* __restrict__ nrm,
+                           double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double d = nrm[0];
+  if (i < n) v[i] = d > 0 ? w[i] / d : 0.0;
+}
+
+// Largest |eigenvalue| of a symmetric n x n matrix A by `iters` steps of power
+// iteration from a fixed start (an estimate from below); ws: 2n + 8 doubles,
+// part: the Frobenius partials buffer.  Synchronises once.
+static fkf_status power_lmax(fkf_ctx* ctx, int n, const double* A, double* ws, double* part, int iters,
+                             double* out) {
+  double* v = ws;
+  double* w = ws + n;
+  double* nrm = ws + 2 * n;
+  k_fill_start<<<(int)cdiv(n, 256), 256, 0, ctx->stream>>>(n, v);
+  FKF_LAUNCHED(ctx);
+  for (int it = 0; it < iters; it++) {
+    FKF_TRY(gemm_f64(ctx, false, false, n, 1, n, 1.0, A, n, v, 1, 0.0, w, 1));
+    FKF_TRY(frob(ctx, n, w, nullptr, n, part, nrm));
+    k_scale_by<<<(int)cdiv(n, 256), 256, 0, ctx->stream>>>(n, w, nrm, v);
+    FKF_LAUNCHED(ctx);
+  }
+  FKF_CUDA(ctx, cudaMemcpyAsync(out, nrm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return FKF_OK;
+}
+
 
 // A = (A + A^T) / 2 in place (n x n)
 __global__ void k_symmetrize(int n, double* __restrict__ A) {
@@ -689,6 +725,8 @@ struct fkf_filter {
   DevBuf Df, Dfn, Ep, Qm;
   double new_tol = 0;  // relative information outside span(W) below which the basis is kept
   int last_path = 0;   // 0: general merge, 1: basis kept (no new directions), 3: fixed-H reuse
+  int gep_rank = 0, new_dirs = 0, t_eig = 0;  // last merge step
+  double t_lmax = 0;
   // The last step kept the basis, and G, [HW | A], the dense H^T and its CSC
   // index still hold that step's products for the current W (prev_*: its H and R).
   bool products_valid = false;
@@ -703,8 +741,9 @@ struct fkf_filter {
   DevBuf cnt, cursor, colptr, crow, cval;
   // small FP64 buffers
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
-  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws, vm;
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
+  TcGemmWs rot;  // tensor-core rotation (FP32 state)
   cudaEvent_t ev[7] = {};
   double phase_ms[6] = {};
 };
@@ -738,6 +777,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
   FKF_TRY(A(f->HWD, m * r));
   FKF_TRY(A(f->nll, 4));
+  FKF_TRY(A(f->vm, 2 * m + 8));
   FKF_TRY(A(f->red, kFrobBlocks));
   FKF_TRY(A(f->dbar, r));
   FKF_TRY(A(f->y, m));
@@ -1103,26 +1143,36 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaEventRecord(f->ev[4], st));
   // ---- S4: Gamma^-1-orthonormalisation of U = G C against W (data space)
   double* P = f->P.as<double>();
-  int mp = mlam;
+  int mp = mlam, t_eig = 0;
+  double t_lmax = r > 0 ? 0.0 : 1.0;  // without W, T = I
   if (r > 0 && mlam > 0) {
     FKF_TRY(gemm_f64(ctx, true, false, r, mlam, m, 1.0, HW, nm, C, mlam, 0.0, P, mlam));
     double* Tm = f->Tm.as<double>();
     FKF_TRY(gemm_f64(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
     k_add_identity<<<(int)cdiv(mlam, 256), 256, 0, st>>>(mlam, Tm, mlam, 1.0);
     FKF_LAUNCHED(ctx);
-    // every eigenvalue of T is bounded by ||T||_F: when that is below the
-    // threshold no new direction exists and the eigensolve is skipped
+    // every eigenvalue of T is bounded by ||T||_F; when that is above the
+    // threshold, power iteration estimates the largest eigenvalue (from below:
+    // it must stay under half the threshold) before the eigensolve is paid for
     FKF_TRY(frob(ctx, (int64_t)mlam * mlam, Tm, nullptr, mlam, f->red.as<double>(), f->nll.as<double>() + 1));
     double tfrob = 0;
     FKF_CUDA(ctx, cudaMemcpyAsync(&tfrob, f->nll.as<double>() + 1, 8, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
     mp = 0;
-    if (tfrob > f->orth_tol) {
+    t_lmax = tfrob;
+    bool need_eig = tfrob > f->orth_tol;
+    if (need_eig) {
+      FKF_TRY(power_lmax(ctx, mlam, Tm, f->vm.as<double>(), f->red.as<double>(), 40, &t_lmax));
+      need_eig = t_lmax > 0.5 * f->orth_tol;
+    }
+    if (need_eig) {
       FKF_TRY(eigh_f64(ctx, mlam, Tm, f->th.as<double>(), th_h, f->eigws));
+      t_lmax = th_h.empty() ? 0.0 : th_h.back();
       for (int i = mlam - 1; i >= 0; i--)
         if (th_h[i] > f->orth_tol) mp++;
         else break;
     }
+    t_eig = need_eig ? 1 : 0;
     if (mp > 0) {
       k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 0, f->Po.as<double>(), mlam);
       FKF_LAUNCHED(ctx);
@@ -1205,8 +1255,16 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       FKF_LAUNCHED(ctx);
       Et = f->Ecast.as<T>();
     }
-    FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, nm, 1.0, Wc, ld, Et, rnew, 0.0, Wn, ld));
-    FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, r, 1.0, Xc, rmax, Et, rnew, 0.0, Xn, rmax));
+    if (sizeof(T) == 4) {
+      // both products on the tensor cores in one launch (they share E's split)
+      const TcGemmProblem pr[2] = {
+          {reinterpret_cast<const float*>(Wc), ld, n, (int)nm, reinterpret_cast<float*>(Wn), ld},
+          {reinterpret_cast<const float*>(Xc), rmax, n, r, reinterpret_cast<float*>(Xn), rmax}};
+      FKF_TRY(tc_gemm_f32(ctx, pr, 2, reinterpret_cast<const float*>(Et), rnew, nm, rnew, f->rot));
+    } else {
+      FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, nm, 1.0, Wc, ld, Et, rnew, 0.0, Wn, ld));
+      FKF_TRY(gemm_T<T>(ctx, false, false, n, rnew, r, 1.0, Xc, rmax, Et, rnew, 0.0, Xn, rmax));
+    }
     k_csc_spmm<T><<<(int)cdiv(n * 32, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
                                                           f->cval.as<double>(), E + (int64_t)r * rnew, rnew, Xn, rmax);
     FKF_LAUNCHED(ctx);
@@ -1217,6 +1275,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaStreamSynchronize(st));
   FKF_CUDA(ctx, cudaGetLastError());
   FKF_TRY(hmat_tc_check(h));
+  FKF_TRY(tc_gemm_check(ctx, f->rot));
   // ---- commit
   std::swap(f->s_hat.p, f->s_new.p);
   std::swap(f->D.p, f->Dn.p);
@@ -1226,6 +1285,10 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   f->k++;
   f->diag = true;
   f->last_path = 0;
+  f->gep_rank = mlam;
+  f->new_dirs = mp;
+  f->t_eig = t_eig;
+  f->t_lmax = t_lmax;
   if (nll_out && !(flags & FKF_STEP_SKIP_MEAN_SYNC)) *nll_out = nll;
   for (int i = 0; i < 6; i++) {
     float ms = 0;
@@ -1611,6 +1674,10 @@ void filter_stats(const fkf_filter* f, fkf_filter_stats* s) {
   s->r = f->r;
   s->last_path = f->last_path;
   s->diagonal = f->diag ? 1 : 0;
+  s->gep_rank = f->gep_rank;
+  s->new_dirs = f->new_dirs;
+  s->t_eig = f->t_eig;
+  s->t_lmax = f->t_lmax;
 }
 
 // ---------------------------------------------------------------------------

@@ -130,14 +130,21 @@ __device__ __forceinline__ void put1(uint8_t* chunk, int n, int k, float v) {
   *reinterpret_cast<uint32_t*>(chunk + kBBytes + off) = l;
 }
 
-// Split X: chunk x (blockIdx.x) of 16 rows (xmap), column tile ct (blockIdx.y)
-// of 256 columns -> 32 KB at out + (x * nct + ct) * 32 KB.  Thread units are
-// (column n, rows 4kq..4kq+3): a warp reads 32 consecutive floats of a row and
-// writes 512 contiguous bytes per half.
+// Split X: chunk x (blockIdx.x) of 16 rows (xmap; without a map, rows 16x..
+// of a matrix of urows rows), column tile ct (blockIdx.y) of 256 columns ->
+// 32 KB at out + (x * nct + ct) * 32 KB.  Thread units are (column n, rows
+// 4kq..4kq+3): a warp reads 32 consecutive floats of a row and writes 512
+// contiguous bytes per half.
 __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X, int64_t ldx, int ncols,
-                                                    const TcXChunk* __restrict__ xmap, int nct,
+                                                    const TcXChunk* __restrict__ xmap, int64_t urows, int nct,
                                                     uint8_t* __restrict__ out) {
-  const TcXChunk xc = xmap[blockIdx.x];
+  TcXChunk xc;
+  if (xmap) {
+    xc = xmap[blockIdx.x];
+  } else {
+    xc.row0 = (int64_t)blockIdx.x * kK;
+    xc.rows = (int)min((int64_t)kK, urows - xc.row0);
+  }
   const int ct = blockIdx.y;
   uint8_t* chunk = out + ((int64_t)blockIdx.x * nct + ct) * kBChunkBytes;
 #pragma unroll
@@ -152,6 +159,39 @@ __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X,
       v[j] = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] : 0.f;
     }
     put4(chunk, chunk + kBBytes, n, 4 * kq, v[0], v[1], v[2], v[3]);
+  }
+}
+
+// Split a row-major matrix A (rows x K, ld lda) into operator chunks: tile t
+// (blockIdx.x) of 128 rows, K chunk c (blockIdx.y) of 16 columns -> 16 KB at
+// out + (t * nch + c) * 16 KB; rows >= rows and columns >= K are zero.  Thread
+// units are (row, 4 columns): a warp reads 64-byte runs of 8 rows and writes
+// 512 contiguous bytes per half.
+__global__ void __launch_bounds__(256) k_tc_split_rows(const float* __restrict__ A, int64_t lda, int64_t rows, int K,
+                                                       int nch, uint8_t* __restrict__ out) {
+  const int64_t t = blockIdx.x;
+  const int c = blockIdx.y;
+  uint8_t* hi = out + (t * nch + c) * (int64_t)kAChunkBytes;
+  const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda & 3) == 0;
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int u = threadIdx.x + 256 * i;
+    const int kq = u & 3, row = u >> 2;
+    const int64_t r = t * kM + row;
+    const int k = c * kK + 4 * kq;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < rows) {
+      const float* src = A + r * lda + k;
+      if (vec && k + 4 <= K) {
+        const float4 q = *reinterpret_cast<const float4*>(src);
+        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          if (k + j < K) v[j] = src[j];
+      }
+    }
+    put4(hi, hi + kABytes, row, 4 * kq, v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -175,6 +215,10 @@ struct Ph2 {
     nc = (sg.K + kK - 1) / kK;
     return sg.near ? xsplit : zsplit;
   }
+  __device__ __forceinline__ float* row_dst(int64_t w, int row) const {
+    const TcTile& t = tiles[w];
+    return row < t.rows ? Y + (t.row0 + row) * ldy : nullptr;
+  }
 };
 
 // Phase 1: items (cluster, 128-slot tile, group of whole leaves); one B
@@ -196,6 +240,37 @@ struct Ph1 {
     c0 = it.x_row;
     nc = it.nchunk;
     return xsplit;
+  }
+};
+
+// Dense GEMM C_p = A_p B[0:K_p, :] for up to two problems that share B:
+// row tiles of 128 rows of A_p (split by k_tc_split_rows, tile-major, K
+// chunks consecutive), B split like X in uniform 16-row chunks; tiles of
+// problem 0 first.  Output rows of C_p.
+struct PhGemm {
+  const uint8_t* bsplit;
+  float *C0, *C1;
+  int64_t ldc0, ldc1;
+  int64_t rows0, rows1;
+  int64_t a1;   // first A chunk of problem 1 (problem 0 starts at 0)
+  int64_t nw0;  // row tiles of problem 0
+  int nch0, nch1;  // K chunks per tile
+  // (fields selected, not indexed: a dynamic index into a kernel parameter
+  // array would copy the parameters to local memory)
+  __device__ __forceinline__ int nchunk(int64_t w) const { return w >= nw0 ? nch1 : nch0; }
+  __device__ __forceinline__ int64_t a_chunk0(int64_t w) const {
+    return w >= nw0 ? a1 + (w - nw0) * nch1 : w * nch0;
+  }
+  __device__ __forceinline__ int nseg(int64_t) const { return 1; }
+  __device__ __forceinline__ const uint8_t* seg(int64_t w, int, int64_t& c0, int& nc) const {
+    c0 = 0;
+    nc = nchunk(w);
+    return bsplit;
+  }
+  __device__ __forceinline__ float* row_dst(int64_t w, int row) const {
+    const bool p = w >= nw0;
+    const int64_t r = (p ? w - nw0 : w) * kM + row;
+    return r < (p ? rows1 : rows0) ? (p ? C1 : C0) + r * (p ? ldc1 : ldc0) : nullptr;
   }
 };
 
@@ -311,10 +386,10 @@ template <class Ph>
 __device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols,
                                          uint32_t tmem);
 
-// phase 2: rows of Y
-template <>
-__device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int64_t ntiles, int nct, int ncols,
-                                              uint32_t tmem) {
+// Rows of a row-major output: Ph supplies the destination row (nullptr past
+// the tile's rows) and nchunk (0: the tile is zero).
+template <class Ph>
+__device__ __forceinline__ void epilogue_rows(const Smem& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
   const int half = (warp - 2) >> 2;
@@ -329,9 +404,9 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
     const int64_t w = id / nct;
     const int n0 = (int)(id % nct) * kN;
     const int nv = min(kN, ncols - n0);
-    const TcTile& t = ph.tiles[w];
-    const bool zero = t.nchunk == 0;
-    const RowSinkY sink{row < t.rows ? ph.Y + (t.row0 + row) * ph.ldy + n0 : nullptr};
+    const bool zero = ph.nchunk(w) == 0;
+    float* dst = ph.row_dst(w, row);
+    const RowSinkY sink{dst ? dst + n0 : nullptr};
 #pragma unroll 1
     for (int j = 4 * half; j < 4 * half + 4; j++) {
       float v[32];
@@ -346,6 +421,20 @@ __device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int6
     umma::fence_before_sync();
     umma::mbar_arrive(&s.bar[AE + b]);
   }
+}
+
+// phase 2: rows of Y
+template <>
+__device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int64_t, int nct, int ncols,
+                                              uint32_t tmem) {
+  epilogue_rows(s, ph, nct, ncols, tmem);
+}
+
+// dense GEMM: rows of C
+template <>
+__device__ __forceinline__ void epilogue<PhGemm>(const Smem& s, const PhGemm& ph, int64_t, int nct, int ncols,
+                                                 uint32_t tmem) {
+  epilogue_rows(s, ph, nct, ncols, tmem);
 }
 
 // phase 1: slot rows into the split slot workspace, or partial rows.  The
@@ -536,7 +625,7 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
     if (h->n_tcx > 0) {
       k_tc_split_x<<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
-          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), nct, h->xsplit.as<uint8_t>());
+          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), 0, nct, h->xsplit.as<uint8_t>());
       FKF_LAUNCHED(ctx);
     }
     if (h->n_tcp1 > 0) {
@@ -558,6 +647,71 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream, counters + 1,
                                                                  h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
+                       int ncols, TcGemmWs& ws) {
+  if (np < 1 || np > 2) return set_err(ctx, FKF_EINVAL, "tc_gemm_f32: 1 or 2 problems");
+  if (ncols <= 0) return FKF_OK;
+  PhGemm ph{};
+  int64_t nw[2] = {0, 0}, a0[2] = {0, 0}, achunks = 0;
+  int nch[2] = {0, 0};
+  for (int i = 0; i < np; i++) {
+    if (p[i].K < 0 || p[i].K > kb || p[i].rows < 0) return set_err(ctx, FKF_EINVAL, "tc_gemm_f32: bad shape");
+    nw[i] = cdiv(p[i].rows, kM);
+    nch[i] = (int)cdiv(p[i].K, kK);
+    a0[i] = achunks;
+    achunks += nw[i] * nch[i];
+  }
+  ph.C0 = p[0].C, ph.ldc0 = p[0].ldc, ph.rows0 = p[0].rows, ph.nch0 = nch[0];
+  if (np > 1) ph.C1 = p[1].C, ph.ldc1 = p[1].ldc, ph.rows1 = p[1].rows, ph.nch1 = nch[1], ph.a1 = a0[1];
+  ph.nw0 = nw[0];
+  const int64_t nwork = nw[0] + nw[1];
+  if (nwork == 0) return FKF_OK;
+  const int nct = (int)cdiv(ncols, kN);
+  const int64_t nbx = cdiv(kb, kK);
+  const size_t abytes = (size_t)std::max<int64_t>(achunks, 1) * kAChunkBytes;
+  const size_t bbytes = (size_t)std::max<int64_t>(nbx, 1) * nct * kBChunkBytes;
+  if (ws.asplit.bytes < abytes) FKF_TRY(dev_alloc(ctx, ws.asplit, abytes));
+  if (ws.bsplit.bytes < bbytes) FKF_TRY(dev_alloc(ctx, ws.bsplit, bbytes));
+  if (ws.ctl.bytes < 64) {
+    FKF_TRY(dev_alloc(ctx, ws.ctl, 64));
+    FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, ctx->stream));
+  }
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
+  FKF_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream));
+  if (nbx > 0) {
+    k_tc_split_x<<<dim3((unsigned)nbx, (unsigned)nct), 256, 0, ctx->stream>>>(B, ldb, ncols, nullptr, kb, nct,
+                                                                              ws.bsplit.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+  }
+  for (int i = 0; i < np; i++) {
+    if (nw[i] == 0 || nch[i] == 0) continue;
+    k_tc_split_rows<<<dim3((unsigned)nw[i], (unsigned)nch[i]), 256, 0, ctx->stream>>>(
+        p[i].A, p[i].lda, p[i].rows, p[i].K, nch[i], ws.asplit.as<uint8_t>() + a0[i] * kAChunkBytes);
+    FKF_LAUNCHED(ctx);
+  }
+  ph.bsplit = ws.bsplit.as<uint8_t>();
+  int sms = 0;
+  FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  const int grid = (int)std::min<int64_t>(sms, nwork * nct);
+  k_tc_apply<PhGemm><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, nwork, nct, ncols, ws.asplit.as<uint8_t>(),
+                                                                  counter, ws.ctl.as<int>());
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
+fkf_status tc_gemm_check(fkf_ctx* ctx, TcGemmWs& ws) {
+  if (!ws.ctl.p) return FKF_OK;
+  int e = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&e, ws.ctl.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, ctx->stream));
+    return set_err(ctx, FKF_ETIMEOUT, "tensor-core GEMM: an mbarrier wait expired");
   }
   return FKF_OK;
 }

@@ -62,7 +62,8 @@ class fkf_step_desc(C.Structure):
 
 class fkf_filter_stats(C.Structure):
     _fields_ = [("k", C.c_int64), ("alpha", C.c_double), ("r", C.c_int32), ("last_path", C.c_int32),
-                ("diagonal", C.c_int32)]
+                ("diagonal", C.c_int32), ("gep_rank", C.c_int32), ("new_dirs", C.c_int32), ("t_eig", C.c_int32),
+                ("t_lmax", C.c_double)]
 
 
 class FkfError(RuntimeError):
@@ -87,6 +88,8 @@ _sigs = {
     "fkf_hmatrix_apply": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_hmatrix_apply_clustered": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_hmatrix_apply_clustered_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_rotate_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, C.c_int64, C.c_int64, C.c_int32, _P,
+                                 C.c_int64]),
     "fkf_hmatrix_permutation": (C.c_int, [_P, _P]),
     "fkf_hmatrix_densify": (C.c_int, [_P, _P]),
     "fkf_hmatrix_destroy": (None, [_P]),
@@ -209,6 +212,15 @@ def fkf_hmatrix_apply_clustered_noalloc(h, X, Y, ncols=None, ldx=None, ldy=None)
     ldx = X.stride(0) if ldx is None else ldx
     ldy = Y.stride(0) if ldy is None else ldy
     _check(_lib.fkf_hmatrix_apply_clustered_noalloc(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
+
+
+def fkf_rotate_f32(ctx, A, E, C, K=None, ncols=None):
+    """C[:, :ncols] = A[:, :K] @ E[:K, :ncols] on the tensor cores (FP32
+    row-major CUDA tensors, any leading dimensions)."""
+    K = A.shape[1] if K is None else K
+    ncols = C.shape[1] if ncols is None else ncols
+    _check(_lib.fkf_rotate_f32(ctx.ptr, _ptr(A), A.stride(0), A.shape[0], K, _ptr(E), E.stride(0), E.shape[0], ncols,
+                               _ptr(C), C.stride(0)), ctx)
 
 
 def fkf_hmatrix_set_engine(h, engine: int) -> None:
