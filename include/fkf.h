@@ -180,13 +180,19 @@ fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, i
  * ETIMEOUT (a tensor-core wait expired). */
 fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t rows, int32_t K, const float* E_dev,
                           int64_t lde, int64_t ke, int32_t ncols, float* C_dev, int64_t ldc);
-/* Engine of the H-apply for an FP32 operator: 1 (default) = 5th-generation
- * tensor cores (tcgen05.mma kind::tf32 with a 3xTF32 split, FP32
- * accumulation in TMEM); 0 = the FP32 SIMT tile engine.  FP64 operators
- * always use the FP64 SIMT engine.  Errors: EINVAL (engine not 0/1, or 1 for
- * an FP64 operator).  A tensor-core wait that expires makes the apply (or the
- * filter step) return FKF_ETIMEOUT. */
+/* Engine of the H-apply for an FP32 operator: 2 (default) = 5th-generation
+ * tensor cores, tcgen05.mma kind::f16 with a two-term FP16 split of
+ * power-of-two scaled operands (hi*hi + hi*lo + lo*hi at twice the TF32
+ * rate; scales per slot, point and X column keep FP32-level accuracy);
+ * 1 = tensor cores, kind::tf32 with a 3xTF32 split; both accumulate in FP32
+ * in TMEM.  0 = the FP32 SIMT tile engine.  FP64 operators always use the FP64
+ * SIMT engine.  Selecting another tensor-core format rewrites the operator's
+ * split stream (device work, synchronous).  Errors: EINVAL (engine not 0-2,
+ * or 1-2 for an FP64 operator).  A tensor-core wait that expires makes the
+ * apply (or the filter step) return FKF_ETIMEOUT. */
 fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
+/* Current engine of the H-apply (see fkf_hmatrix_set_engine).  Errors: EINVAL (null). */
+fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine);
 /* Permutation: perm[i] = original index of the i-th point in cluster order. */
 fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host);
 /* Dense copy of Gamma_H (host, N x N row-major, original order); N <= 8192. */

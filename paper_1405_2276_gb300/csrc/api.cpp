@@ -185,13 +185,18 @@ FKF_API fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, i
   return hmat_tc_check(h);
 }
 
+FKF_API fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine) {
+  if (!h || !engine) return FKF_EINVAL;
+  *engine = h->engine;
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine) {
   if (!h) return FKF_EINVAL;
-  if (engine != 0 && engine != 1) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0 or 1");
-  if (engine == 1 && h->prec != FKF_FP32)
-    return set_err(h->ctx, FKF_EINVAL, "set_engine: the tensor-core engine needs an FP32 operator");
-  h->engine = engine;
-  return FKF_OK;
+  if (engine < 0 || engine > 2) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0, 1 or 2");
+  if (engine != 0 && h->prec != FKF_FP32)
+    return set_err(h->ctx, FKF_EINVAL, "set_engine: the tensor-core engines need an FP32 operator");
+  return hmat_set_engine(h, engine);
 }
 
 // Variant that never allocates device memory (static scratch; see fkf.h).

@@ -151,11 +151,17 @@ struct TcTile {
 // One 128 x 16 chunk of a split operator stream: element (i, k) is
 // src[src_off + (i - row_lo) * si + k * sk] for row_lo <= i < row_hi and
 // k < kv, zero elsewhere (src = the far factors, or the near blocks if near).
+// For the scaled FP16 format, row i is scaled by the scale of natural slot
+// s_off + i (phase 1) or of point s_off + i (phase 2), and column k of a far
+// phase-2 chunk by the inverse scale of slot-workspace position k_off + k.
 struct TcAChunk {
   int64_t src_off;
+  int64_t s_off;
+  int64_t k_off;   // -1: no column scale
   int32_t si, sk;
   int32_t row_lo, row_hi;
   int32_t kv, near;
+  int32_t phase, pad;
 };
 
 // One 16-row chunk of the split X operand: rows row0 .. row0 + rows - 1 of X
@@ -200,12 +206,18 @@ struct fkf_hmat {
   int32_t max_leaf = 0;
   // tensor-core schedules (FP32 operators)
   DevBuf tcp1, tcred, tctile, tcseg, tc_err;
-  DevBuf tca;  // split operator streams: 16 KB per chunk (TF32 hi | lo, tensor-core smem layout)
+  DevBuf tca;  // split operator streams: one chunk per 128 x 16 block (hi | lo, tensor-core smem layout)
+  DevBuf tcadesc;  // TcAChunk per chunk of tca
   DevBuf tcxmap, tcslot;  // TcXChunk per X chunk; split-workspace position per natural slot
-  DevBuf xsplit, zsplit;  // split X and slot workspace: 32 KB per (chunk, 256-column tile)
+  DevBuf xsplit, zsplit;  // split X and slot workspace, per (chunk, 256-column tile)
+  // scaled FP16 format: power-of-two scales per natural slot (phase-1 rows),
+  // per slot-workspace position, per point (phase-2 rows); column scales of X
+  DevBuf tc_qslot, tc_qpos, tc_rpt, tc_col;
   int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0, n_tcx = 0, n_tcz = 0;
   int64_t tc_panel = 0;  // columns per tensor-core pass
-  int engine = 0;  // 0: SIMT tile engine, 1: tensor cores (tcgen05, FP32 operators only)
+  int tca_fmt = 0;       // format the split operator stream holds (1, 2)
+  int zsplit_fmt = 0;    // format last written to the split slot workspace
+  int engine = 0;  // 0: SIMT tile engine; tensor cores (FP32 operators only): 1 = 3xTF32, 2 = scaled 2xFP16
   // workspace
   DevBuf zmix, part, xperm, yperm;
   int64_t panel = 256;
@@ -230,6 +242,9 @@ void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector
 // Uploads the tensor-core schedule and writes the split operator streams
 // (after fac/nearv are on the device).
 fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu);
+// Selects the engine (0, 1, 2); rewrites the split operator stream when the
+// tensor-core format changes.
+fkf_status hmat_set_engine(fkf_hmat* h, int engine);
 // Dense C_p = A_p B[0:K_p, 0:ncols] for p < np <= 2 (row-major FP32 in and
 // out) on the tensor cores with 3xTF32 products; B has kb >= K_p rows.  The
 // launch is asynchronous: tc_gemm_check reads the error flag after a sync.

@@ -164,7 +164,7 @@ fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y
   if (ncols <= 0) return FKF_OK;
   if (h->prec == FKF_FP64)
     return apply_impl<double>(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
-  if (h->engine == 1) return hmat_apply_clustered_tc(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
+  if (h->engine != 0) return hmat_apply_clustered_tc(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
   return apply_impl<float>(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
 }
 
@@ -453,6 +453,9 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
               a.row_hi = nq;
               a.kv = (int32_t)std::min<int64_t>(16, csize(lc) - r);
               a.near = 0;
+              a.phase = 1;
+              a.s_off = slot_base[c] + q0;
+              a.k_off = -1;
               ch.push_back(a);
             }
           }
@@ -488,6 +491,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   FKF_TRY(upload_vals(h->fac, facv));
   FKF_TRY(upload_vals(h->nearv, nearv));
   std::vector<char>().swap(tmp);
+  h->ktot = ktot;  // the tensor-core upload sizes its per-slot scales by it
   if (h->prec == FKF_FP32) FKF_TRY(hmat_upload_tc(h, tu));
   FKF_TRY(dev_upload(ctx, h->slotmap, smap.data(), smap.size() * sizeof(int64_t)));
   if (!p1.empty()) FKF_TRY(dev_upload(ctx, h->p1items, p1.data(), p1.size() * sizeof(P1Item)));

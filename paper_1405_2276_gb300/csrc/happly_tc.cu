@@ -1,25 +1,35 @@
 // H-apply on the 5th-generation tensor cores (FP32 operators).  Both phases
-// of the two-phase apply run as 128 x 256 output tiles of tcgen05.mma
-// kind::tf32 with FP32 accumulators in TMEM.  Every FP32 value x is split into
-// hi = tf32(x) and lo = tf32(x - hi), and each product is accumulated as
-// hi*hi + hi*lo + lo*hi (3xTF32), which keeps FP32-level accuracy.
+// of the two-phase apply run as 128 x 256 output tiles of tcgen05.mma with
+// FP32 accumulators in TMEM.  Every FP32 value is split into two terms and
+// each product is accumulated as hi*hi + hi*lo + lo*hi, in one of two
+// element formats:
+//   F = 1 (3xTF32, kind::tf32): hi = tf32(x), lo = tf32(x - hi);
+//   F = 2 (scaled 2xFP16, kind::f16, twice the MMA rate): x is first scaled
+//     by a power of two (exact), hi = fp16(x s), lo = fp16(x s - hi).  The
+//     scales keep every operand inside FP16's range with room for lo:
+//     operator rows (per slot in phase 1, per point in phase 2), the slot
+//     columns of phase 2 (inverse of the slot's phase-1 scale, so that the
+//     slot products pass between the phases without rescaling), and the
+//     columns of X (per apply); the phase-2 epilogue removes the point and
+//     column scales.  Each term then carries 11 significant bits, the pair
+//     22, as in 3xTF32, down to 2^-17 of its row's (column's) scale; smaller
+//     elements keep an absolute error below 2^-25 of that scale.
 //
 // Both operands reach shared memory already split, in the tensor core's
 // K-major core-matrix layout, one bulk copy per operand and K-chunk of 16:
-//   * the operator (A): split once when the operator is built, as one stream
-//     of 16 KB chunks (128 x 16 TF32 hi block, then lo) per phase-1 item and
-//     per phase-2 tile;
+//   * the operator (A): split once when the operator is built (or the
+//     format changes), as one stream of chunks (128 x 16 hi block, then lo)
+//     per phase-1 item and per phase-2 tile;
 //   * the vectors (B): X is split per column pass into 16-row chunks per leaf
 //     (rows padded to a multiple of 16), and phase 1 writes its products
-//     straight into the split slot workspace (16-slot chunks per cluster);
-//     a chunk is 32 KB per 256-column tile (hi, then lo).
+//     straight into the split slot workspace (16-slot chunks per cluster).
 //
 // One persistent CTA per SM, warp-specialised:
 //   warp 0     producer (one thread): two bulk copies per chunk into one of
-//              four stages, completion counted in bytes on full[s];
-//   warp 1     MMA issuer (one thread): six MMAs per chunk (2 K-steps x 3
-//              products), commits to empty[s], and to acc_full after a
-//              tile's last chunk; also allocates and frees TMEM;
+//              the stages, completion counted in bytes on full[s];
+//   warp 1     MMA issuer (one thread): three products per K-step, commits
+//              to empty[s], and to acc_full after a tile's last chunk; also
+//              allocates and frees TMEM;
 //   warps 2-9  epilogue: tcgen05.ld of the finished accumulator (two warps
 //              per TMEM lane quarter, one per half of the columns), stores,
 //              arrive on acc_empty.
@@ -29,49 +39,84 @@
 // and epilogue roles through a small queue in shared memory): CTAs running at
 // once work on neighbouring tiles, which share operator chunks (the column
 // tiles of one work item) and X or ancestors' slot chunks, in L2, and a CTA
-// that drew short tiles takes more of them.  Every mbarrier wait is bounded: an expired wait sets a flag,
-// every role leaves its loop, the MMA issuer waits (bounded) for its
-// outstanding MMAs, TMEM is freed and the host sees the error flag.
+// that drew short tiles takes more of them.  Every mbarrier wait is bounded:
+// an expired wait sets a flag, every role leaves its loop, the MMA issuer
+// waits (bounded) for its outstanding MMAs, TMEM is freed and the host sees
+// the error flag.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.h"
 #include "umma.cuh"
 
-// Pipeline depth (compile-time tuning knob).
-#ifndef FKF_TC_STAGES
-#define FKF_TC_STAGES 4
+// Chunks per pipeline stage and stage counts of the two formats
+// (compile-time tuning knobs).  A stage's MMAs end with one commit, and each
+// commit costs the MMA pipe a gap: fewer, larger stages keep it busier.
+#ifndef FKF_TC_TF32_CHUNKS_PER_STAGE
+#define FKF_TC_TF32_CHUNKS_PER_STAGE 1
+#endif
+#ifndef FKF_TC_STAGES_TF32
+#define FKF_TC_STAGES_TF32 (4 / FKF_TC_TF32_CHUNKS_PER_STAGE)
+#endif
+// tcgen05 fence after each stage's full-barrier wait (the bulk copies and
+// the MMAs are both async-proxy operations ordered by the mbarrier)
+#ifndef FKF_TC_STAGE_FENCE
+#define FKF_TC_STAGE_FENCE 1
+#endif
+#ifndef FKF_TC_F16_CHUNKS_PER_STAGE
+#define FKF_TC_F16_CHUNKS_PER_STAGE 4
+#endif
+#ifndef FKF_TC_STAGES_F16
+#define FKF_TC_STAGES_F16 (8 / FKF_TC_F16_CHUNKS_PER_STAGE)
 #endif
 
 namespace {
 
-constexpr int kM = 128;                    // tile rows = TMEM lanes
-constexpr int kN = 256;                    // tile columns = MMA N
-constexpr int kK = umma::kChunk;           // 16: K per chunk
-constexpr int kABytes = kM * kK * 4;       // 8 KB: one TF32 half of an A chunk
-constexpr int kAChunkBytes = 2 * kABytes;  // 16 KB: hi | lo
-constexpr int kBBytes = kN * kK * 4;       // 16 KB: one TF32 half of a B chunk
-constexpr int kBChunkBytes = 2 * kBBytes;  // 32 KB: hi | lo
-constexpr int kStageBytes = kAChunkBytes + kBChunkBytes;  // 48 KB
-constexpr int kS = FKF_TC_STAGES;
-constexpr int kEpiWarps = 8;               // warps 2-9: two per TMEM lane quarter, one per column half
-constexpr int kEpiLd = 33;                 // padded row of an epilogue staging tile (32 x 32 floats)
+constexpr int kM = 128;           // tile rows = TMEM lanes
+constexpr int kN = 256;           // tile columns = MMA N
+constexpr int kK = umma::kChunk;  // 16: K per chunk
+constexpr int kEpiWarps = 8;      // warps 2-9: two per TMEM lane quarter, one per column half
+constexpr int kEpiLd = 33;        // padded row of an epilogue staging tile (32 x 32 floats)
 constexpr int kEpiBytes = kEpiWarps * 32 * kEpiLd * 4;
-constexpr int kQ = 8;                      // tile-index queue (producer -> MMA, epilogue)
-constexpr int kTail = 384;                 // barriers, TMEM address, flag, queue
-constexpr int kSmemBytes = kS * kStageBytes + kTail + kEpiBytes;  // 225.4 KB for 4 stages
-static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+constexpr int kQ = 8;             // tile-index queue (producer -> MMA, epilogue)
+constexpr int kBarBytes = 384;
+constexpr int kTail = 512;        // barriers, TMEM address, flag, queue
 constexpr int kProdWarp = 0, kMmaWarp = 1;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 2 * kN;
 constexpr uint32_t kMaxPolls = 1u << 22;
-constexpr uint32_t kIdesc = umma::idesc_tf32(kM, kN);
 
-// barrier indices
-constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1, QE = QF + kQ,
-              NBAR = QE + kQ;
-static_assert(NBAR * 8 <= 256, "barrier area");
+// Geometry of format F's split chunks.
+template <int F>
+struct Geo {
+  static constexpr int kEl = F == 1 ? 4 : 2;       // bytes per element
+  static constexpr int kPer = 16 / kEl;            // elements of one core-matrix row (16 bytes)
+  static constexpr int kMmaK = F == 1 ? 8 : 16;    // K per MMA
+  static constexpr int kABytes = kM * kK * kEl;    // one half (hi or lo) of an A chunk
+  static constexpr int kAChunk = 2 * kABytes;
+  static constexpr int kBBytes = kN * kK * kEl;    // one half of a B chunk (256 columns)
+  static constexpr int kBChunk = 2 * kBBytes;
+  static constexpr int kCPS = F == 1 ? FKF_TC_TF32_CHUNKS_PER_STAGE : FKF_TC_F16_CHUNKS_PER_STAGE;  // chunks per stage
+  static constexpr int kStage = kCPS * (kAChunk + kBChunk);
+  static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : FKF_TC_STAGES_F16;  // pipeline stages
+  static constexpr uint32_t kSBO = (kK / kPer) * 128;  // next 8-row group
+  static constexpr uint32_t kIdesc = F == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
+  static constexpr int kSmem = kS * kStage + kTail + kEpiBytes;
+  // barrier indices
+  static constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1,
+                       QE = QF + kQ, NBAR = QE + kQ;
+  static_assert(kSmem <= 232448, "shared memory per CTA");
+  static_assert(NBAR * 8 <= kBarBytes, "barrier area");
+  // byte offset of element (row, k) in a K-major no-swizzle chunk of kK columns
+  __device__ static __forceinline__ uint32_t off(int row, int k) {
+    return (uint32_t)((row >> 3) * kSBO + (k / kPer) * 128 + (row & 7) * 16 + (k % kPer) * kEl);
+  }
+};
 
+template <int F>
 struct Smem {
   uint8_t* base;
   uint64_t* bar;
@@ -80,64 +125,124 @@ struct Smem {
   int64_t* q;  // [kQ] tile indices (-1: no more tiles)
   float* epi;  // kEpiWarps staging tiles
 
-  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kStageBytes; }
-  __device__ __forceinline__ uint8_t* b(int s) const { return base + s * kStageBytes + kAChunkBytes; }
+  // stage s: the A chunks of its kCPS chunks (consecutive), then their B chunks
+  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * Geo<F>::kStage; }
+  __device__ __forceinline__ uint8_t* b(int s) const {
+    return base + s * Geo<F>::kStage + Geo<F>::kCPS * Geo<F>::kAChunk;
+  }
   __device__ __forceinline__ bool failed() const { return *reinterpret_cast<volatile int*>(fail) != 0; }
   __device__ __forceinline__ void set_fail() const { atomicExch(fail, 1); }
 };
 
-__device__ __forceinline__ Smem smem_layout(uint8_t* base) {
-  Smem s;
+template <int F>
+__device__ __forceinline__ Smem<F> smem_layout(uint8_t* base) {
+  Smem<F> s;
   s.base = base;
-  uint8_t* tail = base + kS * kStageBytes;
+  uint8_t* tail = base + Geo<F>::kS * Geo<F>::kStage;
   s.bar = reinterpret_cast<uint64_t*>(tail);
-  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + 256);
-  s.fail = reinterpret_cast<int*>(tail + 264);
-  s.q = reinterpret_cast<int64_t*>(tail + 272);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + kBarBytes);
+  s.fail = reinterpret_cast<int*>(tail + kBarBytes + 8);
+  s.q = reinterpret_cast<int64_t*>(tail + kBarBytes + 16);
   s.epi = reinterpret_cast<float*>(tail + kTail);
   return s;
 }
 
-__device__ __forceinline__ bool wait_bar(const Smem& s, int i, uint32_t parity) {
+template <int F>
+__device__ __forceinline__ bool wait_bar(const Smem<F>& s, int i, uint32_t parity) {
   if (umma::mbar_wait(&s.bar[i], parity, kMaxPolls)) return true;
   s.set_fail();
   return false;
 }
 
 // ---- splitting into the tensor-core layout ----------------------------------
-__device__ __forceinline__ void split4(float v0, float v1, float v2, float v3, uint4& h, uint4& l) {
-  umma::split_tf32(v0, h.x, l.x);
-  umma::split_tf32(v1, h.y, l.y);
-  umma::split_tf32(v2, h.z, l.z);
-  umma::split_tf32(v3, h.w, l.w);
+__device__ __forceinline__ void split_f16(float x, uint32_t& h, uint32_t& l) {
+  const __half hh = __float2half_rn(x);
+  const __half ll = __float2half_rn(x - __half2float(hh));
+  h = __half_as_ushort(hh);
+  l = __half_as_ushort(ll);
 }
 
-__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
-                                     float v3) {
+// kPer consecutive elements v[0..kPer) of one row, starting at k (a multiple
+// of kPer): one 16-byte store per half.
+template <int F>
+__device__ __forceinline__ void put_unit(uint8_t* hi_base, uint8_t* lo_base, int row, int k, const float* v) {
   uint4 h, l;
-  split4(v0, v1, v2, v3, h, l);
-  const uint32_t off = umma::chunk_offset(row, k);
+  if constexpr (F == 1) {
+    umma::split_tf32(v[0], h.x, l.x);
+    umma::split_tf32(v[1], h.y, l.y);
+    umma::split_tf32(v[2], h.z, l.z);
+    umma::split_tf32(v[3], h.w, l.w);
+  } else {
+    uint32_t a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) split_f16(v[i], a[i], b[i]);
+    h = make_uint4(a[0] | a[1] << 16, a[2] | a[3] << 16, a[4] | a[5] << 16, a[6] | a[7] << 16);
+    l = make_uint4(b[0] | b[1] << 16, b[2] | b[3] << 16, b[4] | b[5] << 16, b[6] | b[7] << 16);
+  }
+  const uint32_t off = Geo<F>::off(row, k);
   *reinterpret_cast<uint4*>(hi_base + off) = h;
   *reinterpret_cast<uint4*>(lo_base + off) = l;
 }
 
+// Four consecutive elements of one row starting at k (a multiple of 4).
+template <int F>
+__device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
+                                     float v3) {
+  const uint32_t off = Geo<F>::off(row, k);
+  if constexpr (F == 1) {
+    uint4 h, l;
+    umma::split_tf32(v0, h.x, l.x);
+    umma::split_tf32(v1, h.y, l.y);
+    umma::split_tf32(v2, h.z, l.z);
+    umma::split_tf32(v3, h.w, l.w);
+    *reinterpret_cast<uint4*>(hi_base + off) = h;
+    *reinterpret_cast<uint4*>(lo_base + off) = l;
+  } else {
+    uint32_t a[4], b[4];
+    split_f16(v0, a[0], b[0]);
+    split_f16(v1, a[1], b[1]);
+    split_f16(v2, a[2], b[2]);
+    split_f16(v3, a[3], b[3]);
+    *reinterpret_cast<uint2*>(hi_base + off) = make_uint2(a[0] | a[1] << 16, a[2] | a[3] << 16);
+    *reinterpret_cast<uint2*>(lo_base + off) = make_uint2(b[0] | b[1] << 16, b[2] | b[3] << 16);
+  }
+}
+
 // One value into a split B chunk (row = column n of the tile, k = row in chunk).
+template <int F>
 __device__ __forceinline__ void put1(uint8_t* chunk, int n, int k, float v) {
+  const uint32_t off = Geo<F>::off(n, k);
   uint32_t h, l;
-  umma::split_tf32(v, h, l);
-  const uint32_t off = umma::chunk_offset(n, k);
-  *reinterpret_cast<uint32_t*>(chunk + off) = h;
-  *reinterpret_cast<uint32_t*>(chunk + kBBytes + off) = l;
+  if constexpr (F == 1) {
+    umma::split_tf32(v, h, l);
+    *reinterpret_cast<uint32_t*>(chunk + off) = h;
+    *reinterpret_cast<uint32_t*>(chunk + Geo<F>::kBBytes + off) = l;
+  } else {
+    split_f16(v, h, l);
+    *reinterpret_cast<uint16_t*>(chunk + off) = (uint16_t)h;
+    *reinterpret_cast<uint16_t*>(chunk + Geo<F>::kBBytes + off) = (uint16_t)l;
+  }
+}
+
+// Largest power of two <= x, limited to [2^-100, 2^100]; 1 for x that is not
+// a positive finite number.
+__device__ __forceinline__ float pow2_floor(float x) {
+  if (!(x > 0.f) || isinf(x)) return 1.f;
+  int e;
+  frexpf(x, &e);  // x = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, min(max(e - 1, -100), 100));
 }
 
 // Split X: chunk x (blockIdx.x) of 16 rows (xmap; without a map, rows 16x..
 // of a matrix of urows rows), column tile ct (blockIdx.y) of 256 columns ->
-// 32 KB at out + (x * nct + ct) * 32 KB.  Thread units are (column n, rows
-// 4kq..4kq+3): a warp reads 32 consecutive floats of a row and writes 512
-// contiguous bytes per half.
+// out + (x * nct + ct) * kBChunk; columns scaled by cscale (F = 2).  Thread
+// units are (column n, kPer rows): a warp reads 32 consecutive floats of a
+// row and writes 512 contiguous bytes per half.
+template <int F>
 __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X, int64_t ldx, int ncols,
                                                     const TcXChunk* __restrict__ xmap, int64_t urows, int nct,
-                                                    uint8_t* __restrict__ out) {
+                                                    const float* __restrict__ cscale, uint8_t* __restrict__ out) {
+  using G = Geo<F>;
   TcXChunk xc;
   if (xmap) {
     xc = xmap[blockIdx.x];
@@ -146,32 +251,59 @@ __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X,
     xc.rows = (int)min((int64_t)kK, urows - xc.row0);
   }
   const int ct = blockIdx.y;
-  uint8_t* chunk = out + ((int64_t)blockIdx.x * nct + ct) * kBChunkBytes;
+  uint8_t* chunk = out + ((int64_t)blockIdx.x * nct + ct) * G::kBChunk;
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < kK / G::kPer; i++) {
     const int u = threadIdx.x + 256 * i;
     const int n = u & (kN - 1), kq = u >> 8;
     const int col = ct * kN + n;
-    float v[4];
+    const float sc = (F == 2 && col < ncols) ? cscale[col] : 1.f;
+    float v[G::kPer];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int k = 4 * kq + j;
-      v[j] = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] : 0.f;
+    for (int j = 0; j < G::kPer; j++) {
+      const int k = G::kPer * kq + j;
+      v[j] = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] * sc : 0.f;
     }
-    put4(chunk, chunk + kBBytes, n, 4 * kq, v[0], v[1], v[2], v[3]);
+    put_unit<F>(chunk, chunk + G::kBBytes, n, G::kPer * kq, v);
   }
 }
 
-// Split a row-major matrix A (rows x K, ld lda) into operator chunks: tile t
-// (blockIdx.x) of 128 rows, K chunk c (blockIdx.y) of 16 columns -> 16 KB at
-// out + (t * nch + c) * 16 KB; rows >= rows and columns >= K are zero.  Thread
-// units are (row, 4 columns): a warp reads 64-byte runs of 8 rows and writes
-// 512 contiguous bytes per half.
+// Column maxima of |X| (rows x ncols, ld ldx) as ordered float bits; grid
+// (column blocks of 256, row blocks).
+__global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ X, int64_t ldx, int64_t rows, int ncols,
+                                                int64_t rows_per_block, unsigned* __restrict__ cmax) {
+  const int col = blockIdx.x * 256 + threadIdx.x;
+  if (col >= ncols) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = min(rows, r0 + rows_per_block);
+  float m = 0.f;
+  for (int64_t r = r0; r < r1; r++) m = fmaxf(m, fabsf(X[r * ldx + col]));
+  atomicMax(&cmax[col], __float_as_uint(m));
+}
+
+// X column scales: the largest power of two with max |X_j| * s_j <= 1/2 (so
+// that a phase-1 slot value, bounded by its operator row's scaled L1 bound
+// 2^15 times max |X_j s_j|, stays below FP16's 65504); inverse scales after
+// them.
+__global__ void k_colscale(const unsigned* __restrict__ cmax, int ncols, float* __restrict__ cs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  const float s = pow2_floor(0.5f / __uint_as_float(cmax[j]));
+  cs[j] = s;
+  cs[ncols + j] = 1.f / s;
+}
+
+// Split a row-major matrix A (rows x K, ld lda) into 3xTF32 operator chunks:
+// tile t (blockIdx.x) of 128 rows, K chunk c (blockIdx.y) of 16 columns ->
+// out + (t * nch + c) * kAChunk; rows >= rows and columns >= K are zero.
+// Thread units are (row, 4 columns): a warp reads 64-byte runs of 8 rows and
+// writes 512 contiguous bytes per half.
 __global__ void __launch_bounds__(256) k_tc_split_rows(const float* __restrict__ A, int64_t lda, int64_t rows, int K,
                                                        int nch, uint8_t* __restrict__ out) {
+  using G = Geo<1>;
   const int64_t t = blockIdx.x;
   const int c = blockIdx.y;
-  uint8_t* hi = out + (t * nch + c) * (int64_t)kAChunkBytes;
+  uint8_t* hi = out + (t * nch + c) * (int64_t)G::kAChunk;
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda & 3) == 0;
 #pragma unroll
   for (int i = 0; i < 2; i++) {
@@ -191,13 +323,15 @@ __global__ void __launch_bounds__(256) k_tc_split_rows(const float* __restrict__
           if (k + j < K) v[j] = src[j];
       }
     }
-    put4(hi, hi + kABytes, row, 4 * kq, v[0], v[1], v[2], v[3]);
+    put_unit<1>(hi, hi + G::kABytes, row, 4 * kq, v);
   }
 }
 
-// ---- the two phases' work items -------------------------------------------
+// ---- the work items ----------------------------------------------------------
 // Phase 2: tiles of 128 consecutive rows; B segments = chunks of the split
-// slot workspace (far) or of the split X (near); output rows of Y.
+// slot workspace (far) or of the split X (near); output rows of Y, with the
+// point and column scales removed (F = 2: rpt = point scales, cinv = inverse
+// column scales of the pass).
 struct Ph2 {
   const TcTile* tiles;
   const TcSeg* segs;
@@ -205,6 +339,8 @@ struct Ph2 {
   const uint8_t* xsplit;
   float* Y;
   int64_t ldy;
+  const float* rpt;
+  const float* cinv;
   __device__ __forceinline__ int nchunk(int64_t w) const { return tiles[w].nchunk; }
   __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return tiles[w].a_chunk0; }
   __device__ __forceinline__ int nseg(int64_t w) const { return tiles[w].nseg; }
@@ -215,9 +351,11 @@ struct Ph2 {
     nc = (sg.K + kK - 1) / kK;
     return sg.near ? xsplit : zsplit;
   }
-  __device__ __forceinline__ float* row_dst(int64_t w, int row) const {
+  __device__ __forceinline__ float* row_dst(int64_t w, int row, float& rinv) const {
     const TcTile& t = tiles[w];
-    return row < t.rows ? Y + (t.row0 + row) * ldy : nullptr;
+    if (row >= t.rows) return nullptr;
+    rinv = rpt ? 1.f / rpt[t.row0 + row] : 1.f;
+    return Y + (t.row0 + row) * ldy;
   }
 };
 
@@ -252,9 +390,10 @@ struct PhGemm {
   float *C0, *C1;
   int64_t ldc0, ldc1;
   int64_t rows0, rows1;
-  int64_t a1;   // first A chunk of problem 1 (problem 0 starts at 0)
-  int64_t nw0;  // row tiles of problem 0
+  int64_t a1;      // first A chunk of problem 1 (problem 0 starts at 0)
+  int64_t nw0;     // row tiles of problem 0
   int nch0, nch1;  // K chunks per tile
+  const float* cinv;  // unused (unscaled format)
   // (fields selected, not indexed: a dynamic index into a kernel parameter
   // array would copy the parameters to local memory)
   __device__ __forceinline__ int nchunk(int64_t w) const { return w >= nw0 ? nch1 : nch0; }
@@ -267,9 +406,10 @@ struct PhGemm {
     nc = nchunk(w);
     return bsplit;
   }
-  __device__ __forceinline__ float* row_dst(int64_t w, int row) const {
+  __device__ __forceinline__ float* row_dst(int64_t w, int row, float& rinv) const {
     const bool p = w >= nw0;
     const int64_t r = (p ? w - nw0 : w) * kM + row;
+    rinv = 1.f;
     return r < (p ? rows1 : rows0) ? (p ? C1 : C0) + r * (p ? ldc1 : ldc0) : nullptr;
   }
 };
@@ -277,63 +417,89 @@ struct PhGemm {
 // ---- roles -----------------------------------------------------------------
 // Next tile of this CTA: taken from the global counter by the producer and
 // published in the queue; every consumer reads each queue entry once.
-__device__ __forceinline__ bool next_tile(const Smem& s, int qi, int64_t& id) {
+template <int F>
+__device__ __forceinline__ bool next_tile(const Smem<F>& s, int qi, int64_t& id) {
+  using G = Geo<F>;
   const int slot = qi % kQ;
-  if (!wait_bar(s, QF + slot, (uint32_t)(qi / kQ) & 1)) return false;
+  if (!wait_bar(s, G::QF + slot, (uint32_t)(qi / kQ) & 1)) return false;
   id = *reinterpret_cast<volatile int64_t*>(&s.q[slot]);
-  umma::mbar_arrive(&s.bar[QE + slot]);
+  umma::mbar_arrive(&s.bar[G::QE + slot]);
   return id >= 0;
 }
 
-template <class Ph>
-__device__ __forceinline__ void producer(const Smem& s, const Ph& ph, int64_t ntiles, int nct,
+// A tile's chunks go kCPS to a stage (the last stage of a tile may hold
+// fewer): one bulk copy for their A chunks (consecutive in the operator
+// stream), one per B chunk.
+template <int F, class Ph>
+__device__ __forceinline__ void producer(const Smem<F>& s, const Ph& ph, int64_t ntiles, int nct,
                                          const uint8_t* astream, unsigned long long* counter) {
-  int64_t g = 0;
+  using G = Geo<F>;
+  int64_t g = 0;  // stages issued
   for (int qi = 0;; qi++) {
     int64_t id = (int64_t)atomicAdd(counter, 1ull);
     if (id >= ntiles) id = -1;
     const int slot = qi % kQ;
-    if (qi >= kQ && !wait_bar(s, QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
+    if (qi >= kQ && !wait_bar(s, G::QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
     *reinterpret_cast<volatile int64_t*>(&s.q[slot]) = id;
-    umma::mbar_arrive(&s.bar[QF + slot]);
+    umma::mbar_arrive(&s.bar[G::QF + slot]);
     if (id < 0) return;
     const int64_t w = id / nct;
     const int ct = (int)(id % nct);
-    const uint8_t* ap = astream + ph.a_chunk0(w) * (int64_t)kAChunkBytes;
+    const int nch = ph.nchunk(w);
+    const uint8_t* ap = astream + ph.a_chunk0(w) * (int64_t)G::kAChunk;
     const int ns = ph.nseg(w);
-    for (int j = 0; j < ns; j++) {
+    int t = 0, j = 0, nin = 0, st = 0;  // chunk of the tile, chunk within the stage, chunks in the stage
+    for (int sg = 0; sg < ns; sg++) {
       int64_t c0;
       int nc;
-      const uint8_t* bsrc = ph.seg(w, j, c0, nc);
-      for (int c = 0; c < nc; c++, g++) {
-        if (s.failed()) return;
-        const int st = (int)(g % kS);
-        if (g >= kS && !wait_bar(s, EMPTY + st, (uint32_t)((g / kS) - 1) & 1)) return;
-        umma::mbar_arrive_expect_tx(&s.bar[FULL + st], kStageBytes);
-        umma::bulk_g2s(s.a(st), ap, kAChunkBytes, &s.bar[FULL + st]);
-        umma::bulk_g2s(s.b(st), bsrc + ((c0 + c) * nct + ct) * (int64_t)kBChunkBytes, kBChunkBytes,
-                       &s.bar[FULL + st]);
-        ap += kAChunkBytes;
+      const uint8_t* bsrc = ph.seg(w, sg, c0, nc);
+      for (int c = 0; c < nc; c++, t++) {
+        if (j == 0) {
+          if (s.failed()) return;
+          st = (int)(g % G::kS);
+          if (g >= G::kS && !wait_bar(s, G::EMPTY + st, (uint32_t)((g / G::kS) - 1) & 1)) return;
+          nin = min(G::kCPS, nch - t);
+          umma::mbar_arrive_expect_tx(&s.bar[G::FULL + st], (uint32_t)(nin * (G::kAChunk + G::kBChunk)));
+          umma::bulk_g2s(s.a(st), ap, (uint32_t)(nin * G::kAChunk), &s.bar[G::FULL + st]);
+          ap += nin * G::kAChunk;
+        }
+        umma::bulk_g2s(s.b(st) + j * G::kBChunk, bsrc + ((c0 + c) * nct + ct) * (int64_t)G::kBChunk, G::kBChunk,
+                       &s.bar[G::FULL + st]);
+        if (++j == nin) {
+          j = 0;
+          g++;
+        }
       }
     }
   }
 }
 
+template <int F>
 __device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, uint32_t acc, bool first) {
-  const uint32_t a_hi = umma::smem_u32(a), a_lo = a_hi + kABytes;
-  const uint32_t b_hi = umma::smem_u32(b), b_lo = b_hi + kBBytes;
+  using G = Geo<F>;
+  const uint32_t a_hi = umma::smem_u32(a), a_lo = a_hi + G::kABytes;
+  const uint32_t b_hi = umma::smem_u32(b), b_lo = b_hi + G::kBBytes;
 #pragma unroll
-  for (int kk = 0; kk < kK / 8; kk++) {
+  for (int kk = 0; kk < kK / G::kMmaK; kk++) {
     const uint32_t koff = kk * 2 * umma::kLBO;  // two core matrices along K per MMA
-    umma::mma_tf32(acc, umma::smem_desc(a_hi + koff), umma::smem_desc(b_hi + koff), kIdesc,
-                   (first && kk == 0) ? 0u : 1u);
-    umma::mma_tf32(acc, umma::smem_desc(a_hi + koff), umma::smem_desc(b_lo + koff), kIdesc, 1u);
-    umma::mma_tf32(acc, umma::smem_desc(a_lo + koff), umma::smem_desc(b_hi + koff), kIdesc, 1u);
+    const uint64_t ah = umma::smem_desc(a_hi + koff, G::kSBO), al = umma::smem_desc(a_lo + koff, G::kSBO);
+    const uint64_t bh = umma::smem_desc(b_hi + koff, G::kSBO), bl = umma::smem_desc(b_lo + koff, G::kSBO);
+    const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+    if constexpr (F == 1) {
+      umma::mma_tf32(acc, ah, bh, G::kIdesc, acc0);
+      umma::mma_tf32(acc, ah, bl, G::kIdesc, 1u);
+      umma::mma_tf32(acc, al, bh, G::kIdesc, 1u);
+    } else {
+      umma::mma_f16(acc, ah, bh, G::kIdesc, acc0);
+      umma::mma_f16(acc, ah, bl, G::kIdesc, 1u);
+      umma::mma_f16(acc, al, bh, G::kIdesc, 1u);
+    }
   }
 }
 
-template <class Ph>
-__device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t ntiles, int nct, uint32_t tmem) {
+template <int F, class Ph>
+__device__ __forceinline__ void mma_issuer(const Smem<F>& s, const Ph& ph, int nct, uint32_t tmem) {
+  using G = Geo<F>;
   int64_t g = 0;
   int tl = 0;
   bool ok = true;
@@ -341,35 +507,44 @@ __device__ __forceinline__ void mma_issuer(const Smem& s, const Ph& ph, int64_t 
   for (; ok && next_tile(s, tl, id); tl++) {
     const int nch = ph.nchunk(id / nct);
     const int b = tl & 1;
-    if (tl >= 2 && !wait_bar(s, AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
+    if (tl >= 2 && !wait_bar(s, G::AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
     umma::fence_after_sync();
     const uint32_t acc = tmem + (uint32_t)(b * kN);
-    for (int c = 0; c < nch; c++, g++) {
-      const int st = (int)(g % kS);
-      if (s.failed() || !wait_bar(s, FULL + st, (uint32_t)(g / kS) & 1)) {
+    for (int c = 0; c < nch; g++) {
+      const int st = (int)(g % G::kS);
+      const int nin = min(G::kCPS, nch - c);
+      if (s.failed() || !wait_bar(s, G::FULL + st, (uint32_t)(g / G::kS) & 1)) {
         ok = false;
         break;
       }
+#if FKF_TC_STAGE_FENCE
       umma::fence_after_sync();
-      issue_mma(s.a(st), s.b(st), acc, c == 0);
-      umma::commit(&s.bar[EMPTY + st]);
+#endif
+      for (int j = 0; j < nin; j++, c++)
+        issue_mma<F>(s.a(st) + j * G::kAChunk, s.b(st) + j * G::kBChunk, acc, c == 0);
+      umma::commit(&s.bar[G::EMPTY + st]);
     }
     if (!ok) break;
     if (nch > 0)
-      umma::commit(&s.bar[AF + b]);
+      umma::commit(&s.bar[G::AF + b]);
     else
-      umma::mbar_arrive(&s.bar[AF + b]);
+      umma::mbar_arrive(&s.bar[G::AF + b]);
   }
   // every MMA issued here has completed before TMEM is released
-  umma::commit(&s.bar[FIN]);
-  wait_bar(s, FIN, 0);
+  umma::commit(&s.bar[G::FIN]);
+  wait_bar(s, G::FIN, 0);
 }
 
-// Epilogue stores of one row's 32 columns [c0, c0 + 32) of a tile.
-struct RowSinkY {  // phase 2: a row of Y
+// Epilogue stores of one row's 32 columns [c0, c0 + 32) of a tile, times
+// rinv * cinv[c] when cinv is given.
+struct RowSinkY {
   float* dst;
-  __device__ __forceinline__ void put(int c0, int nv, const float (&v)[32]) const {
+  __device__ __forceinline__ void put(int c0, int nv, float (&v)[32], float rinv, const float* cinv) const {
     if (!dst) return;
+    if (cinv) {
+#pragma unroll
+      for (int i = 0; i < 32; i++) v[i] *= rinv * (c0 + i < nv ? cinv[c0 + i] : 0.f);
+    }
     if (((reinterpret_cast<uintptr_t>(dst + c0) & 15) == 0) && c0 + 32 <= nv) {
 #pragma unroll
       for (int i = 0; i < 32; i += 4)
@@ -382,14 +557,11 @@ struct RowSinkY {  // phase 2: a row of Y
   }
 };
 
-template <class Ph>
-__device__ __forceinline__ void epilogue(const Smem& s, const Ph& ph, int64_t ntiles, int nct, int ncols,
-                                         uint32_t tmem);
-
 // Rows of a row-major output: Ph supplies the destination row (nullptr past
-// the tile's rows) and nchunk (0: the tile is zero).
-template <class Ph>
-__device__ __forceinline__ void epilogue_rows(const Smem& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
+// the tile's rows) and its inverse scale, and nchunk (0: the tile is zero).
+template <int F, class Ph>
+__device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
+  using G = Geo<F>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
   const int half = (warp - 2) >> 2;
@@ -398,15 +570,17 @@ __device__ __forceinline__ void epilogue_rows(const Smem& s, const Ph& ph, int n
   int64_t id;
   for (; next_tile(s, tl, id); tl++) {
     const int b = tl & 1;
-    if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
     if (s.failed()) break;
     const int64_t w = id / nct;
     const int n0 = (int)(id % nct) * kN;
     const int nv = min(kN, ncols - n0);
     const bool zero = ph.nchunk(w) == 0;
-    float* dst = ph.row_dst(w, row);
+    float rinv = 1.f;
+    float* dst = ph.row_dst(w, row, rinv);
     const RowSinkY sink{dst ? dst + n0 : nullptr};
+    const float* cinv = ph.cinv ? ph.cinv + n0 : nullptr;
 #pragma unroll 1
     for (int j = 4 * half; j < 4 * half + 4; j++) {
       float v[32];
@@ -416,36 +590,23 @@ __device__ __forceinline__ void epilogue_rows(const Smem& s, const Ph& ph, int n
       } else {
         umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
       }
-      sink.put(32 * j, nv, v);
+      sink.put(32 * j, nv, v, rinv, cinv);
     }
     umma::fence_before_sync();
-    umma::mbar_arrive(&s.bar[AE + b]);
+    umma::mbar_arrive(&s.bar[G::AE + b]);
   }
 }
 
-// phase 2: rows of Y
-template <>
-__device__ __forceinline__ void epilogue<Ph2>(const Smem& s, const Ph2& ph, int64_t, int nct, int ncols,
-                                              uint32_t tmem) {
-  epilogue_rows(s, ph, nct, ncols, tmem);
-}
-
-// dense GEMM: rows of C
-template <>
-__device__ __forceinline__ void epilogue<PhGemm>(const Smem& s, const PhGemm& ph, int64_t, int nct, int ncols,
-                                                 uint32_t tmem) {
-  epilogue_rows(s, ph, nct, ncols, tmem);
-}
-
-// phase 1: slot rows into the split slot workspace, or partial rows.  The
+// Phase 1: slot rows into the split slot workspace, or partial rows.  The
 // slots of a tile come in aligned groups of 4 that map to 4 consecutive
 // aligned positions of the split workspace (blocks have a multiple of 4
-// slots), i.e. one 16-byte unit (4 k) per column: each warp stages its
-// 32 rows x 32 columns in shared memory and writes whole units, a warp
-// covering 512 contiguous bytes per hi/lo half.
-template <>
-__device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int64_t ntiles, int nct, int ncols,
-                                              uint32_t tmem) {
+// slots), i.e. 4 k of one column: each warp stages its 32 rows x 32 columns
+// in shared memory and writes whole groups, a warp covering a contiguous
+// run per hi/lo half.  (Slot values stay scaled: phase 2's operator columns
+// carry the inverse scales.)
+template <int F>
+__device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const Ph1& ph, int nct, int ncols, uint32_t tmem) {
+  using G = Geo<F>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;
   const int half = (warp - 2) >> 2;
@@ -455,7 +616,7 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
   int64_t id;
   for (; next_tile(s, tl, id); tl++) {
     const int b = tl & 1;
-    if (!wait_bar(s, AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
     if (s.failed()) break;
     const int64_t w = id / nct;
@@ -476,7 +637,7 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
       gk[q] = 0;
       if (!partial && r4 < it.nq) {
         const int64_t p = ph.slotpos[it.map_off + r4];
-        gchunk[q] = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)kBChunkBytes;
+        gchunk[q] = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)G::kBChunk;
         gk[q] = (int)(p & 12);
       }
     }
@@ -490,7 +651,7 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
         umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
       }
       if (partial) {
-        psink.put(32 * j, nv, v);
+        psink.put(32 * j, nv, v, 1.f, nullptr);
       } else {
 #pragma unroll
         for (int i = 0; i < 32; i++) tile[lane * kEpiLd + i] = v[i];
@@ -499,33 +660,43 @@ __device__ __forceinline__ void epilogue<Ph1>(const Smem& s, const Ph1& ph, int6
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           if (gchunk[q] && n < nv)
-            put4(gchunk[q], gchunk[q] + kBBytes, n, gk[q], tile[(4 * q + 0) * kEpiLd + lane],
-                 tile[(4 * q + 1) * kEpiLd + lane], tile[(4 * q + 2) * kEpiLd + lane], tile[(4 * q + 3) * kEpiLd + lane]);
+            put4<F>(gchunk[q], gchunk[q] + G::kBBytes, n, gk[q], tile[(4 * q + 0) * kEpiLd + lane],
+                    tile[(4 * q + 1) * kEpiLd + lane], tile[(4 * q + 2) * kEpiLd + lane],
+                    tile[(4 * q + 3) * kEpiLd + lane]);
         }
         __syncwarp();
       }
     }
     umma::fence_before_sync();
-    umma::mbar_arrive(&s.bar[AE + b]);
+    umma::mbar_arrive(&s.bar[G::AE + b]);
   }
 }
 
-template <class Ph>
+template <int F, class Ph>
+__device__ __forceinline__ void epilogue(const Smem<F>& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
+  if constexpr (std::is_same<Ph, Ph1>::value)
+    epilogue_p1<F>(s, ph, nct, ncols, tmem);
+  else
+    epilogue_rows<F>(s, ph, nct, ncols, tmem);
+}
+
+template <int F, class Ph>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_apply(const Ph ph, int64_t nwork, int nct, int ncols, const uint8_t* __restrict__ astream,
                unsigned long long* __restrict__ counter, int* __restrict__ err) {
+  using G = Geo<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem s = smem_layout(smem_raw);
+  const Smem<F> s = smem_layout<F>(smem_raw);
   const int warp = threadIdx.x >> 5;
   const int64_t ntiles = nwork * nct;
   if (threadIdx.x == 0) {
-    for (int i = FULL; i < EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = EMPTY; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = AF; i < AE; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = AE; i < FIN; i++) umma::mbar_init(&s.bar[i], 32 * kEpiWarps);
-    umma::mbar_init(&s.bar[FIN], 1);
-    for (int i = QF; i < QE; i++) umma::mbar_init(&s.bar[i], 1);
-    for (int i = QE; i < NBAR; i++) umma::mbar_init(&s.bar[i], 1 + 32 * kEpiWarps);
+    for (int i = G::FULL; i < G::EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = G::EMPTY; i < G::AF; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = G::AF; i < G::AE; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = G::AE; i < G::FIN; i++) umma::mbar_init(&s.bar[i], 32 * kEpiWarps);
+    umma::mbar_init(&s.bar[G::FIN], 1);
+    for (int i = G::QF; i < G::QE; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = G::QE; i < G::NBAR; i++) umma::mbar_init(&s.bar[i], 1 + 32 * kEpiWarps);
     *s.fail = 0;
     umma::fence_mbar_init();
   }
@@ -535,12 +706,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
   if (warp == kProdWarp) {
-    if ((threadIdx.x & 31) == 0) producer(s, ph, ntiles, nct, astream, counter);
+    if ((threadIdx.x & 31) == 0) producer<F>(s, ph, ntiles, nct, astream, counter);
   } else if (warp == kMmaWarp) {
-    if ((threadIdx.x & 31) == 0) mma_issuer(s, ph, ntiles, nct, tmem);
+    if ((threadIdx.x & 31) == 0) mma_issuer<F>(s, ph, nct, tmem);
     __syncwarp();
   } else {
-    epilogue<Ph>(s, ph, ntiles, nct, ncols, tmem);
+    epilogue<F>(s, ph, nct, ncols, tmem);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -551,32 +722,98 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Writes the split operator chunks: element (i, k) of chunk c (see TcAChunk)
-// into its hi and lo blocks in the tensor-core layout.
-__global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const float* __restrict__ fac,
-                             const float* __restrict__ nearv, uint8_t* __restrict__ out) {
+// ---- operator stream ---------------------------------------------------------
+// Element (i, k) of chunk ch, unscaled (0 outside the chunk's rows and kv).
+__device__ __forceinline__ float chunk_elem(const TcAChunk& ch, const float* fac, const float* nearv, int i, int k) {
+  if (i < ch.row_lo || i >= ch.row_hi || k >= ch.kv) return 0.f;
+  const float* src = ch.near ? nearv : fac;
+  return src[ch.src_off + (int64_t)(i - ch.row_lo) * ch.si + (int64_t)k * ch.sk];
+}
+
+// Scale passes of format 2 over the chunks of one phase: per scale row (a
+// natural slot in phase 1, a point in phase 2) the max |element| (phase 2:
+// with the slot columns' inverse scales applied), and in phase 1 the number
+// of columns.  One thread per chunk row.
+__global__ void __launch_bounds__(128) k_tc_rowmax(const TcAChunk* __restrict__ d, int64_t n, int phase,
+                                                   const float* __restrict__ fac, const float* __restrict__ nearv,
+                                                   const float* __restrict__ qpos, unsigned* __restrict__ rmax,
+                                                   int* __restrict__ cnt) {
+  const int i = threadIdx.x;
   for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
     const TcAChunk ch = d[c];
-    const float* src = ch.near ? nearv : fac;
-    uint8_t* hi = out + c * kAChunkBytes;
-    uint8_t* lo = hi + kABytes;
-    for (int e = threadIdx.x; e < kM * kK / 4; e += blockDim.x) {
-      const int i = e >> 2, kq = e & 3;
-      float v[4];
+    if (ch.phase != phase || i < ch.row_lo || i >= ch.row_hi) continue;
+    float m = 0.f;
+    for (int k = 0; k < ch.kv; k++) {
+      float a = fabsf(chunk_elem(ch, fac, nearv, i, k));
+      if (ch.k_off >= 0) a /= qpos[ch.k_off + k];
+      m = fmaxf(m, a);
+    }
+    atomicMax(&rmax[ch.s_off + i], __float_as_uint(m));
+    if (cnt) atomicAdd(&cnt[ch.s_off + i], ch.kv);
+  }
+}
+
+// Slot scales: q_g = largest power of two with q_g * cnt_g * max|V_g| <= 2^15
+// (so that q_g |V_g . x| <= 2^15 * max|x| <= 2^14 for column-scaled x),
+// stored per natural slot and at the slot's workspace position.
+__global__ void k_tc_qscale(int64_t nslots, const unsigned* __restrict__ vmax, const int* __restrict__ cnt,
+                            const int64_t* __restrict__ slotpos, float* __restrict__ qslot,
+                            float* __restrict__ qpos) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nslots) return;
+  const float q = pow2_floor(32768.f / ((float)max(cnt[g], 1) * __uint_as_float(vmax[g])));
+  qslot[g] = q;
+  qpos[slotpos[g]] = q;
+}
+
+// Point scales: largest power of two with the row's max |element| <= 2^14.
+__global__ void k_tc_rscale(int64_t n, const unsigned* __restrict__ rmax, float* __restrict__ r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = pow2_floor(16384.f / __uint_as_float(rmax[i]));
+}
+
+__global__ void k_fill_f32(int64_t n, float v, float* __restrict__ p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Writes the split operator chunks in format F: element (i, k) of chunk c
+// (see TcAChunk; format 2 with its row and column scales) into its hi and lo
+// blocks in the tensor-core layout.
+template <int F>
+__global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const float* __restrict__ fac,
+                             const float* __restrict__ nearv, const float* __restrict__ qslot,
+                             const float* __restrict__ rpt, const float* __restrict__ qpos,
+                             uint8_t* __restrict__ out) {
+  using G = Geo<F>;
+  constexpr int NU = kK / G::kPer;
+  for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+    const TcAChunk ch = d[c];
+    uint8_t* hi = out + c * G::kAChunk;
+    uint8_t* lo = hi + G::kABytes;
+    for (int e = threadIdx.x; e < kM * NU; e += blockDim.x) {
+      const int i = e / NU, kq = e % NU;
+      float rs = 1.f;
+      if (F == 2 && i >= ch.row_lo && i < ch.row_hi) rs = ch.phase == 1 ? qslot[ch.s_off + i] : rpt[ch.s_off + i];
+      float v[G::kPer];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int k = 4 * kq + u;
-        v[u] = (i >= ch.row_lo && i < ch.row_hi && k < ch.kv)
-                   ? src[ch.src_off + (int64_t)(i - ch.row_lo) * ch.si + (int64_t)k * ch.sk]
-                   : 0.f;
+      for (int u = 0; u < G::kPer; u++) {
+        const int k = G::kPer * kq + u;
+        float x = chunk_elem(ch, fac, nearv, i, k);
+        if (F == 2 && x != 0.f) {
+          x *= rs;
+          if (ch.k_off >= 0) x /= qpos[ch.k_off + k];
+        }
+        v[u] = x;
       }
-      put4(hi, lo, i, 4 * kq, v[0], v[1], v[2], v[3]);
+      put_unit<F>(hi, lo, i, G::kPer * kq, v);
     }
   }
 }
 
 // Sum the partials of a cluster split into several leaf groups and write the
 // slot rows into the split slot workspace.
+template <int F>
 __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const float* __restrict__ part, int64_t ldp,
                                    const int64_t* __restrict__ slotpos, uint8_t* __restrict__ zsplit, int nct,
                                    int ncols) {
@@ -587,24 +824,24 @@ __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const flo
     float acc = 0.f;
     for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldp + n];
     const int64_t p = slotpos[it.map_off + q];
-    put1(zsplit + ((p >> 4) * nct + n / kN) * (int64_t)kBChunkBytes, n % kN, (int)(p & 15), acc);
+    put1<F>(zsplit + ((p >> 4) * nct + n / kN) * (int64_t)Geo<F>::kBChunk, n % kN, (int)(p & 15), acc);
   }
 }
 
-}  // namespace
-
-// Tensor-core apply for an FP32 operator (cluster order).
-fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+template <int F>
+fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+  using G = Geo<F>;
   fkf_ctx* ctx = h->ctx;
   const int64_t P = h->tc_panel;
   const int64_t nct_max = cdiv(P, kN);
-  const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * kBChunkBytes;
+  const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * G::kBChunk;
   if (h->xsplit.bytes < xbytes) FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
-  const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * kBChunkBytes;
-  if (h->zsplit.bytes < zbytes) {
+  const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * G::kBChunk;
+  if (h->zsplit.bytes < zbytes || h->zsplit_fmt != F) {
     // padding slots of the split workspace are never written: they start (and stay) zero
-    FKF_TRY(dev_alloc(ctx, h->zsplit, zbytes));
-    FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, zbytes, ctx->stream));
+    if (h->zsplit.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zsplit, zbytes));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, h->zsplit.bytes, ctx->stream));
+    h->zsplit_fmt = F;
   }
   const size_t pbytes = (size_t)std::max<int64_t>(h->tc_part_rows, 1) * P * sizeof(float);
   if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
@@ -612,47 +849,130 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
     FKF_TRY(dev_alloc(ctx, h->tc_err, 64));
     FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, ctx->stream));
   }
+  // column maxima and scales of one pass (format 2)
+  if (F == 2 && h->tc_col.bytes < (size_t)P * 12) FKF_TRY(dev_alloc(ctx, h->tc_col, (size_t)P * 12));
   // tile counters of the two phases at tc_err + 16, + 24 bytes
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
   const uint8_t* astream = h->tca.as<uint8_t>();
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
     const int nct = (int)cdiv(nc, kN);
     FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    float* cs = nullptr;
+    if (F == 2) {
+      unsigned* cmax = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
+      cs = h->tc_col.as<float>();
+      FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned), ctx->stream));
+      const int64_t rpb = 2048;
+      k_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, ctx->stream>>>(X + c0, ldx, h->n,
+                                                                                                 nc, rpb, cmax);
+      FKF_LAUNCHED(ctx);
+      k_colscale<<<(unsigned)cdiv(nc, 256), 256, 0, ctx->stream>>>(cmax, nc, cs);
+      FKF_LAUNCHED(ctx);
+    }
     if (h->n_tcx > 0) {
-      k_tc_split_x<<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
-          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), 0, nct, h->xsplit.as<uint8_t>());
+      k_tc_split_x<F><<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
+          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), 0, nct, cs, h->xsplit.as<uint8_t>());
       FKF_LAUNCHED(ctx);
     }
     if (h->n_tcp1 > 0) {
       const Ph1 ph{h->tcp1.as<P1Item>(), h->xsplit.as<uint8_t>(), h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
                    h->part.as<float>(), P};
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
-      k_tc_apply<Ph1><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream, counters,
-                                                                   h->tc_err.as<int>());
+      k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream, counters,
+                                                                     h->tc_err.as<int>());
       FKF_LAUNCHED(ctx);
     }
     if (h->n_tcred > 0) {
-      k_phase1_reduce_tc<<<dim3((unsigned)h->n_tcred, 4), 256, 0, ctx->stream>>>(
+      k_phase1_reduce_tc<F><<<dim3((unsigned)h->n_tcred, 4), 256, 0, ctx->stream>>>(
           h->tcred.as<P1Reduce>(), h->part.as<float>(), P, h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(), nct, nc);
       FKF_LAUNCHED(ctx);
     }
     const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
-                 Y + c0, ldy};
+                 Y + c0, ldy, F == 2 ? h->tc_rpt.as<float>() : nullptr, F == 2 ? cs + nc : nullptr};
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
-    k_tc_apply<Ph2><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream, counters + 1,
-                                                                 h->tc_err.as<int>());
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream, counters + 1,
+                                                                   h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
   }
   return FKF_OK;
 }
 
+// Rewrites the split operator stream in format F (format 2: scales first).
+fkf_status build_stream(fkf_hmat* h, int F) {
+  fkf_ctx* ctx = h->ctx;
+  if (h->n_tca == 0) {
+    h->tca_fmt = F;
+    return FKF_OK;
+  }
+  const int grid = (int)std::min<int64_t>(h->n_tca, 152 * 8);
+  const TcAChunk* d = h->tcadesc.as<TcAChunk>();
+  if (F == 2) {
+    // every natural slot (phase-1 row) has a scale: the slot count must be known
+    if (h->n_tcp1 > 0 && h->ktot <= 0) return set_err(ctx, FKF_ESTATE, "tensor-core stream: slot count not set");
+    const int64_t ns = std::max<int64_t>(h->ktot, 1), npos = std::max<int64_t>(h->n_tcz, 1) * 16;
+    FKF_TRY(dev_alloc(ctx, h->tc_qslot, (size_t)ns * sizeof(float)));
+    FKF_TRY(dev_alloc(ctx, h->tc_qpos, (size_t)npos * sizeof(float)));
+    FKF_TRY(dev_alloc(ctx, h->tc_rpt, (size_t)std::max<int64_t>(h->n, 1) * sizeof(float)));
+    DevBuf mx, cnt;
+    FKF_TRY(dev_alloc(ctx, mx, (size_t)std::max(ns, h->n) * sizeof(unsigned)));
+    FKF_TRY(dev_alloc(ctx, cnt, (size_t)ns * sizeof(int)));
+    FKF_CUDA(ctx, cudaMemsetAsync(mx.p, 0, mx.bytes, ctx->stream));
+    FKF_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, cnt.bytes, ctx->stream));
+    k_fill_f32<<<(unsigned)cdiv(npos, 256), 256, 0, ctx->stream>>>(npos, 1.f, h->tc_qpos.as<float>());
+    FKF_LAUNCHED(ctx);
+    k_tc_rowmax<<<grid, 128, 0, ctx->stream>>>(d, h->n_tca, 1, h->fac.as<float>(), h->nearv.as<float>(), nullptr,
+                                              mx.as<unsigned>(), cnt.as<int>());
+    FKF_LAUNCHED(ctx);
+    if (h->ktot > 0) {
+      k_tc_qscale<<<(unsigned)cdiv(h->ktot, 256), 256, 0, ctx->stream>>>(
+          h->ktot, mx.as<unsigned>(), cnt.as<int>(), h->tcslot.as<int64_t>(), h->tc_qslot.as<float>(),
+          h->tc_qpos.as<float>());
+      FKF_LAUNCHED(ctx);
+    }
+    FKF_CUDA(ctx, cudaMemsetAsync(mx.p, 0, mx.bytes, ctx->stream));
+    k_tc_rowmax<<<grid, 128, 0, ctx->stream>>>(d, h->n_tca, 2, h->fac.as<float>(), h->nearv.as<float>(),
+                                              h->tc_qpos.as<float>(), mx.as<unsigned>(), nullptr);
+    FKF_LAUNCHED(ctx);
+    k_tc_rscale<<<(unsigned)cdiv(h->n, 256), 256, 0, ctx->stream>>>(h->n, mx.as<unsigned>(), h->tc_rpt.as<float>());
+    FKF_LAUNCHED(ctx);
+    k_tc_build_a<2><<<grid, 256, 0, ctx->stream>>>(d, h->n_tca, h->fac.as<float>(), h->nearv.as<float>(),
+                                                   h->tc_qslot.as<float>(), h->tc_rpt.as<float>(),
+                                                   h->tc_qpos.as<float>(), h->tca.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // before mx, cnt are freed
+  } else {
+    k_tc_build_a<1><<<grid, 256, 0, ctx->stream>>>(d, h->n_tca, h->fac.as<float>(), h->nearv.as<float>(), nullptr,
+                                                   nullptr, nullptr, h->tca.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  h->tca_fmt = F;
+  return FKF_OK;
+}
+
+}  // namespace
+
+// Tensor-core apply for an FP32 operator (cluster order).
+fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+  if (h->tca_fmt != h->engine) FKF_TRY(build_stream(h, h->engine));
+  if (h->engine == 2) return apply_tc<2>(h, X, ldx, Y, ldy, ncols);
+  return apply_tc<1>(h, X, ldx, Y, ldy, ncols);
+}
+
+fkf_status hmat_set_engine(fkf_hmat* h, int engine) {
+  if (engine != 0 && h->tca_fmt != engine) FKF_TRY(build_stream(h, engine));
+  h->engine = engine;
+  return FKF_OK;
+}
+
 fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
                        int ncols, TcGemmWs& ws) {
+  using G = Geo<1>;
   if (np < 1 || np > 2) return set_err(ctx, FKF_EINVAL, "tc_gemm_f32: 1 or 2 problems");
   if (ncols <= 0) return FKF_OK;
   PhGemm ph{};
@@ -672,8 +992,8 @@ fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float
   if (nwork == 0) return FKF_OK;
   const int nct = (int)cdiv(ncols, kN);
   const int64_t nbx = cdiv(kb, kK);
-  const size_t abytes = (size_t)std::max<int64_t>(achunks, 1) * kAChunkBytes;
-  const size_t bbytes = (size_t)std::max<int64_t>(nbx, 1) * nct * kBChunkBytes;
+  const size_t abytes = (size_t)std::max<int64_t>(achunks, 1) * G::kAChunk;
+  const size_t bbytes = (size_t)std::max<int64_t>(nbx, 1) * nct * G::kBChunk;
   if (ws.asplit.bytes < abytes) FKF_TRY(dev_alloc(ctx, ws.asplit, abytes));
   if (ws.bsplit.bytes < bbytes) FKF_TRY(dev_alloc(ctx, ws.bsplit, bbytes));
   if (ws.ctl.bytes < 64) {
@@ -683,23 +1003,23 @@ fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
   FKF_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream));
   if (nbx > 0) {
-    k_tc_split_x<<<dim3((unsigned)nbx, (unsigned)nct), 256, 0, ctx->stream>>>(B, ldb, ncols, nullptr, kb, nct,
-                                                                              ws.bsplit.as<uint8_t>());
+    k_tc_split_x<1><<<dim3((unsigned)nbx, (unsigned)nct), 256, 0, ctx->stream>>>(B, ldb, ncols, nullptr, kb, nct,
+                                                                                 nullptr, ws.bsplit.as<uint8_t>());
     FKF_LAUNCHED(ctx);
   }
   for (int i = 0; i < np; i++) {
     if (nw[i] == 0 || nch[i] == 0) continue;
     k_tc_split_rows<<<dim3((unsigned)nw[i], (unsigned)nch[i]), 256, 0, ctx->stream>>>(
-        p[i].A, p[i].lda, p[i].rows, p[i].K, nch[i], ws.asplit.as<uint8_t>() + a0[i] * kAChunkBytes);
+        p[i].A, p[i].lda, p[i].rows, p[i].K, nch[i], ws.asplit.as<uint8_t>() + a0[i] * G::kAChunk);
     FKF_LAUNCHED(ctx);
   }
   ph.bsplit = ws.bsplit.as<uint8_t>();
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<1, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
   const int grid = (int)std::min<int64_t>(sms, nwork * nct);
-  k_tc_apply<PhGemm><<<grid, kThreads, kSmemBytes, ctx->stream>>>(ph, nwork, nct, ncols, ws.asplit.as<uint8_t>(),
-                                                                  counter, ws.ctl.as<int>());
+  k_tc_apply<1, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, nwork, nct, ncols, ws.asplit.as<uint8_t>(),
+                                                                   counter, ws.ctl.as<int>());
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }
@@ -750,6 +1070,9 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
         a.row_hi = sg.row_hi;
         a.kv = std::min(kK, sg.K - k0);
         a.near = sg.near;
+        a.phase = 2;
+        a.s_off = t.row0;
+        a.k_off = sg.near ? -1 : sg.b_row * kK + k0;
         ch.push_back(a);
       }
     }
@@ -770,20 +1093,14 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
   h->tc_part_rows = tu.part_rows;
   // columns per pass: keep the split slot workspace under ~24 GB
   int64_t panel = 1024;
-  while (panel > kN && (double)h->n_tcz * (panel / kN) * kBChunkBytes > 24e9) panel /= 2;
+  while (panel > kN && (double)h->n_tcz * (panel / kN) * Geo<1>::kBChunk > 24e9) panel /= 2;
   h->tc_panel = panel;
   h->n_tca = (int64_t)ch.size();
-  FKF_TRY(dev_alloc(ctx, h->tca, (size_t)std::max<int64_t>(h->n_tca, 1) * kAChunkBytes));
-  if (h->n_tca > 0) {
-    DevBuf desc;
-    FKF_TRY(dev_upload(ctx, desc, ch.data(), ch.size() * sizeof(TcAChunk)));
-    const int grid = (int)std::min<int64_t>(h->n_tca, 152 * 8);
-    k_tc_build_a<<<grid, 256, 0, ctx->stream>>>(desc.as<TcAChunk>(), h->n_tca, h->fac.as<float>(),
-                                                h->nearv.as<float>(), h->tca.as<uint8_t>());
-    FKF_LAUNCHED(ctx);
-    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  }
-  h->engine = 1;
+  // the stream holds either format (format 1 chunks are the larger)
+  FKF_TRY(dev_alloc(ctx, h->tca, (size_t)std::max<int64_t>(h->n_tca, 1) * Geo<1>::kAChunk));
+  if (h->n_tca > 0) FKF_TRY(dev_upload(ctx, h->tcadesc, ch.data(), ch.size() * sizeof(TcAChunk)));
+  FKF_TRY(build_stream(h, 2));
+  h->engine = 2;
   return FKF_OK;
 }
 

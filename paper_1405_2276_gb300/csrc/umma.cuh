@@ -1,5 +1,5 @@
 // Blackwell (sm_103a) 5th-generation tensor-core building blocks, written as
-// inline PTX: TMEM allocation, tcgen05.mma kind::tf32 with shared-memory
+// inline PTX: TMEM allocation, tcgen05.mma kind::tf32 / kind::f16 with shared-memory
 // matrix descriptors, tcgen05.commit to an mbarrier, tcgen05.ld of the
 // accumulator, and bounded mbarrier waits.
 //
@@ -34,11 +34,11 @@ __device__ __forceinline__ uint32_t chunk_offset(int row, int k) {
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
 // stride byte offsets (all >> 4), fixed version bits 46..48 = 0b001,
 // base offset 0, relative LBO mode, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo = kSBO) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -47,6 +47,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 // N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16 (format 0), both
+// K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -77,6 +83,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 

@@ -111,6 +111,7 @@ _sigs = {
     "fkf_filter_step_batched": (C.c_int, [C.POINTER(fkf_step_desc), C.c_int32, C.c_int32]),
     "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
     "fkf_hmatrix_set_engine": (C.c_int, [_P, C.c_int32]),
+    "fkf_hmatrix_get_engine": (C.c_int, [_P, C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -224,8 +225,15 @@ def fkf_rotate_f32(ctx, A, E, C, K=None, ncols=None):
 
 
 def fkf_hmatrix_set_engine(h, engine: int) -> None:
-    """1 = tensor cores (tcgen05, 3xTF32; FP32 operators), 0 = SIMT tile engine."""
+    """FP32 operators: 2 = tensor cores with scaled 2xFP16 (default), 1 = tensor
+    cores with 3xTF32, 0 = SIMT tile engine."""
     _check(_lib.fkf_hmatrix_set_engine(h.ptr, engine), h.ctx)
+
+
+def fkf_hmatrix_get_engine(h) -> int:
+    e = C.c_int32()
+    _check(_lib.fkf_hmatrix_get_engine(h.ptr, C.byref(e)), h.ctx)
+    return e.value
 
 
 def fkf_hmatrix_permutation(h, n):

@@ -83,7 +83,7 @@ def test_compressed_operator_exactly_symmetric(fkf, ctx):
     pts = synth.grid_points_2d(40, 30)
     n = pts.shape[0]
     G = covariance.dense_gamma(pts, 0.5, 0.1, 1.0)
-    for prec, engine in ((0, 0), (1, 0), (1, 1)):
+    for prec, engine in ((0, 0), (1, 0), (1, 1), (1, 2)):
         hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.1, 1.0, leaf=32, eta=1.0, aca_tol=1e-6, precision=prec)
         fkf.fkf_hmatrix_set_engine(hm, engine)
         D = fkf.fkf_hmatrix_densify(hm, n)
@@ -147,17 +147,43 @@ def test_invalid_arguments(fkf, ctx):
     X = torch.zeros((64, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(fkf.FkfError):  # X and Y overlap
         fkf.fkf_hmatrix_apply(hm, X, X)
-    with pytest.raises(fkf.FkfError):  # tensor-core engine needs an FP32 operator
-        fkf.fkf_hmatrix_set_engine(hm, 1)
+    for engine in (1, 2):  # tensor-core engines need an FP32 operator
+        with pytest.raises(fkf.FkfError):
+            fkf.fkf_hmatrix_set_engine(hm, engine)
+    with pytest.raises(fkf.FkfError):
+        fkf.fkf_hmatrix_set_engine(hm, 3)
     fkf.fkf_hmatrix_destroy(hm)
 
 
+def test_engine_switch_round_trip(fkf, ctx):
+    """Switching the tensor-core format rewrites the operator stream and
+    clears the slot workspace: 1 -> 2 -> 1 -> 2 repeats each format's result
+    bit for bit."""
+    import torch
+
+    pts = synth.grid_points_2d(96, 80)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.1, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, k_cap=32, precision=1)
+    X = torch.from_numpy(np.random.default_rng(21).standard_normal((n, 300))).to("cuda", torch.float32)
+    out = {}
+    for engine in (1, 2, 1, 2):
+        fkf.fkf_hmatrix_set_engine(hm, engine)
+        Y = torch.empty_like(X)
+        fkf.fkf_hmatrix_apply_clustered(hm, X, Y)
+        if engine in out:
+            assert torch.equal(out[engine], Y), engine
+        out[engine] = Y
+    assert (out[1] - out[2]).abs().max().item() < 1e-5 * out[1].abs().max().item()
+    fkf.fkf_hmatrix_destroy(hm)
+
+
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("grid,leaf,ncols", [((37, 23), 16, 300), ((64, 48), 32, 130), ((256, 256), 64, 260)])
-def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
-    """The tcgen05 3xTF32 engine against the FP64 apply of the same H-matrix
-    (same cluster tree, block tree and ACA pivots): its error must be of the
-    FP32 SIMT engine's size (both accumulate in FP32), and against the exact
-    product on small grids."""
+def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols, engine):
+    """The tcgen05 engines (1: 3xTF32, 2: scaled 2xFP16) against the FP64
+    apply of the same H-matrix (same cluster tree, block tree and ACA
+    pivots): the error must be of the FP32 SIMT engine's size (all accumulate
+    in FP32), and against the exact product on small grids."""
     import torch
 
     pts = synth.grid_points_2d(*grid)
@@ -169,7 +195,7 @@ def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
     X = torch.from_numpy(Xn).to("cuda", torch.float32)
     Y_tc = torch.empty_like(X)
     Y_simt = torch.empty_like(X)
-    fkf.fkf_hmatrix_set_engine(hm, 1)
+    fkf.fkf_hmatrix_set_engine(hm, engine)
     fkf.fkf_hmatrix_apply_clustered(hm, X, Y_tc)
     fkf.fkf_hmatrix_set_engine(hm, 0)
     fkf.fkf_hmatrix_apply_clustered(hm, X, Y_simt)
@@ -182,7 +208,7 @@ def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
     assert np.isfinite(a).all()
     e_tc = np.abs(a - c).max() / np.abs(c).max()
     e_simt = np.abs(b - c).max() / np.abs(c).max()
-    print(f"grid {grid}: tensor-core error {e_tc:.2e}, SIMT error {e_simt:.2e} (vs FP64 apply)")
+    print(f"grid {grid} engine {engine}: tensor-core error {e_tc:.2e}, SIMT error {e_simt:.2e} (vs FP64 apply)")
     # 3xTF32 drops the lo*lo term (2^-22 relative per product) and accumulates in
     # the tensor core's FP32: FP32-level error, a small multiple of the SIMT engine's
     assert e_tc < max(10 * e_simt, 1e-5) and e_tc < 1e-4
@@ -193,3 +219,22 @@ def test_tensor_core_engine_matches_simt_and_dense(fkf, ctx, grid, leaf, ncols):
         assert np.abs(a - ref).max() / np.abs(ref).max() < 2e-5
     fkf.fkf_hmatrix_destroy(hm)
     fkf.fkf_hmatrix_destroy(h64)
+
+
+def test_default_engine_as_built(fkf, ctx):
+    """An FP32 operator starts on the scaled-FP16 tensor-core engine with the
+    stream written at build time (no engine switch before the first apply)."""
+    import torch
+
+    pts = synth.grid_points_2d(48, 40)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.2, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, k_cap=32, precision=1)
+    assert fkf.fkf_hmatrix_get_engine(hm) == 2
+    X = torch.from_numpy(np.random.default_rng(4).standard_normal((n, 40))).to("cuda", torch.float32)
+    Y = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y)
+    fkf.fkf_hmatrix_set_engine(hm, 0)
+    Y0 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y0)
+    assert (Y - Y0).abs().max().item() < 2e-5 * Y0.abs().max().item()
+    fkf.fkf_hmatrix_destroy(hm)
