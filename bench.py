@@ -38,6 +38,20 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 
 
+def workload_name():
+    w = WORKLOAD
+    gx, gy = w["grid"]
+    return (f"2D {gx}x{gy} cross-well tomography, N={gx * gy}, m={w['src'] * w['rec']} ({w['src']}x{w['rec']} rays), "
+            f"Matern nu={w['nu']} ell={w['ell']}, H-matrix leaf {w['leaf']} eta {w['eta']:g} ACA {w['aca_tol']:g} "
+            f"rank cap {w['k_cap']}, R={w['noise']:g} I, general step (fixed geometry: the basis is kept once the "
+            "step brings nothing outside span(W); steps forced through the merge path in fp32_merge_forced)")
+
+
+def bench_config(world):
+    return {"workload": workload_name(), "global_batch": world, "seq_len": 0, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (H-matrix operator and W exceed 129 MB)"}
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -399,8 +413,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * cb["seconds_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "2D 512x512 cross-well tomography, N=262144, m=1024, Matern nu=1/2 ell=0.05",
-                           "global_batch": 1, "seq_len": 0, "parallelism": "none (CPU oracle)"},
+                "config": bench_config(1),
                 "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
                 "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -462,12 +475,7 @@ def main():
         "metric": METRIC, "value": fp32["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": fp32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (N-scale) + f64 (m x m)", "data": "synthetic",
-        "config": {"workload": "2D 512x512 cross-well tomography, N=262144, m=1024 (32x32 rays), Matern nu=1/2 "
-                               "ell=0.05, H-matrix leaf 64 eta 1 ACA 1e-8 rank cap 32, R=1e-4 I, general step (fixed "
-                               "geometry: the basis is kept once the step brings nothing outside span(W); steps "
-                               "forced through the merge path in fp32_merge_forced)",
-                   "global_batch": world, "seq_len": 0, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (H-matrix operator and W exceed 129 MB)"},
+        "config": bench_config(world),
         "happly_gbs": ha["gbs"], "happly_ms": ha["ms"], "happly_tflops": ha["tflops"],
         "happly_simt_fp32": {k: res["happly32_simt"][k] for k in ("ms", "gbs", "tflops")},
         "happly_3xtf32": {k: res["happly32_tf32"][k] for k in ("ms", "gbs", "tflops")},
