@@ -97,8 +97,24 @@ FKF_API fkf_status fkf_create(fkf_ctx** out, int32_t device, void* cuda_stream) 
   return FKF_OK;
 }
 
+fkf_status ctx_side(fkf_ctx* ctx, size_t n_events) {
+  if (!ctx->side) {
+    int least = 0, greatest = 0;
+    FKF_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    FKF_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest));
+  }
+  while (ctx->side_ev.size() < n_events) {
+    cudaEvent_t e;
+    FKF_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->side_ev.push_back(e);
+  }
+  return FKF_OK;
+}
+
 FKF_API void fkf_destroy(fkf_ctx* ctx) {
   if (!ctx) return;
+  for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->solver) cusolverDnDestroy(reinterpret_cast<cusolverDnHandle_t>(ctx->solver));
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

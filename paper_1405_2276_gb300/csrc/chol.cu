@@ -2,9 +2,9 @@
 // innovation covariance S of the filter step (row-major, S = L L^T with L in
 // the lower triangle).
 //
-// FP64 throughput on this part is about two FMAs per clock per SM, so the
-// design keeps the sequential part short and spreads everything else over
-// the SMs: blocks of 32; a 32 x 32 diagonal block is factored by one CTA
+// FP64 throughput on this part is a small fraction of FP32's and a warp-wide
+// FP64 instruction holds its sub-partition for many clocks, so the design
+// keeps the sequential part short and spreads everything else over the SMs: blocks of 32; a 32 x 32 diagonal block is factored by one CTA
 // (32 rank-1 steps in shared memory); the panel below it is solved row by row
 // (one warp per row, the factor block in shared memory, 8 rows per CTA);
 // the trailing matrix is updated by the symmetric FP64 tile GEMM (lower tiles
@@ -96,27 +96,89 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
 
 }  // namespace
 
+namespace {
+// Runs the library's launches of its scope on stream s (the context is used
+// by one host thread at a time).
+struct OnStream {
+  fkf_ctx* c;
+  cudaStream_t saved;
+  OnStream(fkf_ctx* ctx, cudaStream_t s) : c(ctx), saved(ctx->stream) { c->stream = s; }
+  ~OnStream() { c->stream = saved; }
+};
+}  // namespace
+
+// With look-ahead (several blocks): the critical chain -- diagonal block k,
+// its panel, and the update of the next block column k+1 by panel k -- runs
+// on the context's high-priority second stream, while the rest of panel k's
+// trailing update (rows and columns from block k+2 on, the bulk of the flops)
+// runs on the context stream; the block scheduler serves the chain first.
+// Ordering: the trailing update of panel k waits for panel k; the update of
+// block column k+1 by panel k waits for the trailing update of panel k-1
+// (which also wrote block column k+1).  Every other pair of concurrent
+// launches touches disjoint blocks.
 fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws) {
   if (n <= 0 || nf <= 0) return FKF_OK;
   if (ws.bytes < 256) FKF_TRY(dev_alloc(ctx, ws, 256));
   int* flag = ws.as<int>();
   FKF_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  for (int k0 = 0; k0 < nf; k0 += kB) {
-    const int b = std::min(kB, nf - k0);
-    double* Akk = A + (int64_t)k0 * lda + k0;
-    k_potrf_diag<<<1, 256, 0, ctx->stream>>>(Akk, lda, b, flag);
-    FKF_LAUNCHED(ctx);
-    const int rem = n - k0 - b;
-    if (rem > 0) {
-      double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
-      k_trsm_rows<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, ctx->stream>>>(P, lda, rem, b, Akk, lda);
-      FKF_LAUNCHED(ctx);
-      FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, P + b, lda));
-    }
+  const int nb = (int)cdiv(nf, kB);
+  const bool la = nb >= 2 && n - kB > 2 * kB;
+  cudaStream_t bs = ctx->stream, cs = ctx->stream;  // bulk, chain
+  cudaEvent_t* evT = nullptr;
+  cudaEvent_t* evS = nullptr;
+  if (la) {
+    FKF_TRY(ctx_side(ctx, 2 * (size_t)nb + 1));
+    cs = ctx->side;
+    evT = ctx->side_ev.data();
+    evS = evT + nb;
+    // the chain starts after everything queued so far
+    FKF_CUDA(ctx, cudaEventRecord(evS[nb], bs));
+    FKF_CUDA(ctx, cudaStreamWaitEvent(cs, evS[nb], 0));
   }
+  auto factor = [&]() -> fkf_status {
+    for (int k = 0; k < nb; k++) {
+      const int k0 = k * kB;
+      const int b = std::min(kB, nf - k0);
+      double* Akk = A + (int64_t)k0 * lda + k0;
+      k_potrf_diag<<<1, 256, 0, cs>>>(Akk, lda, b, flag);
+      FKF_LAUNCHED(ctx);
+      const int rem = n - k0 - b;
+      if (rem <= 0) continue;
+      double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
+      k_trsm_rows<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, cs>>>(P, lda, rem, b, Akk, lda);
+      FKF_LAUNCHED(ctx);
+      double* C = P + b;  // trailing block at (k0 + b, k0 + b)
+      if (!la) {
+        FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, C, lda, true));
+        continue;
+      }
+      FKF_CUDA(ctx, cudaEventRecord(evT[k], cs));
+      const int b1 = k + 1 < nb ? std::min(kB, nf - (k0 + b)) : 0;  // next block column (critical chain)
+      if (b1 > 0) {
+        if (k >= 1) FKF_CUDA(ctx, cudaStreamWaitEvent(cs, evS[k - 1], 0));
+        OnStream on(ctx, cs);
+        FKF_TRY(gemm_f64(ctx, false, true, rem, b1, b, -1.0, P, lda, P, lda, 1.0, C, lda));
+      }
+      const int rem2 = rem - b1;
+      FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evT[k], 0));
+      if (rem2 > 0)
+        FKF_TRY(gemm_sym_f64(ctx, false, true, rem2, b, -1.0, P + (int64_t)b1 * lda, lda, P + (int64_t)b1 * lda, lda,
+                             1.0, C + (int64_t)b1 * lda + b1, lda, true));
+      FKF_CUDA(ctx, cudaEventRecord(evS[k], bs));
+    }
+    return FKF_OK;
+  };
+  const fkf_status st = factor();
+  if (la) {
+    // join: the context stream continues after all of the chain's work (also when a launch
+    // failed part-way)
+    FKF_CUDA(ctx, cudaEventRecord(evS[nb], cs));
+    FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evS[nb], 0));
+  }
+  FKF_TRY(st);
   int hflag = 0;
-  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, bs));
+  FKF_CUDA(ctx, cudaStreamSynchronize(bs));
   if (hflag) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d, %d pivots)", n, nf);
   return FKF_OK;
 }

@@ -49,7 +49,12 @@ struct fkf_ctx {
   std::atomic<int64_t> lib_calls{0};  // cuSOLVER routine calls
   DevBuf solver_info;  // status word for cuSOLVER calls
   TcGemmWs gemm_ws;    // fkf_rotate_f32
+  cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
+  std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
 };
+
+// Second stream of the context and at least n events (created on first use).
+fkf_status ctx_side(fkf_ctx* ctx, size_t n_events);
 
 // Error plumbing: every internal function returns fkf_status and records a
 // message on the context.

@@ -40,9 +40,10 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm(int M, int N, int K, T al
 // Symmetric result C = alpha op(A) op(B) + beta C (N x N) when op(A) op(B) is
 // symmetric: only the tiles on and below the diagonal are computed (tile t of
 // the lower triangle, row-major order), and each computed entry (i >= j) is
-// written to both (i, j) and (j, i).  C must be symmetric on entry when beta
-// is not zero.
-template <typename T, bool A_KC, bool B_KC>
+// written to (i, j) and, with MIRROR, to (j, i) as well (without it the upper
+// triangle is left as it was).  With MIRROR, C must be symmetric on entry
+// when beta is not zero.
+template <typename T, bool A_KC, bool B_KC, bool MIRROR>
 __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha, const T* __restrict__ A,
                                                            int64_t lda, const T* __restrict__ B, int64_t ldb,
                                                            T beta, T* __restrict__ C, int64_t ldc) {
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha
       T* dst = C + (int64_t)gi * ldc + gj;
       const T v = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *dst;
       *dst = v;
-      if (gi != gj) C[(int64_t)gj * ldc + gi] = v;
+      if (MIRROR && gi != gj) C[(int64_t)gj * ldc + gi] = v;
     }
   }
 }
@@ -183,20 +184,30 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
 }
 
 fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, double alpha, const double* A,
-                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                        bool lower_only) {
   if (N <= 0) return FKF_OK;
   if (K <= 0) return scale_f64(ctx, N, N, beta, C, ldc);
   constexpr int BM = TileCfg<double>::BM;
   const int64_t nb = cdiv(N, BM);
   const unsigned grid = (unsigned)(nb * (nb + 1) / 2);
-  if (!ta && !tb)
-    k_gemm_sym<double, true, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!ta && tb)
-    k_gemm_sym<double, true, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (ta && !tb)
-    k_gemm_sym<double, false, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else
-    k_gemm_sym<double, false, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+#define FKF_SYM_LAUNCH(AK, BK)                                                                                    \
+  if (lower_only)                                                                                                  \
+    k_gemm_sym<double, AK, BK, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, \
+                                                                              ldb, beta, C, ldc);               \
+  else                                                                                                             \
+    k_gemm_sym<double, AK, BK, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B,  \
+                                                                             ldb, beta, C, ldc);
+  if (!ta && !tb) {
+    FKF_SYM_LAUNCH(true, false)
+  } else if (!ta && tb) {
+    FKF_SYM_LAUNCH(true, true)
+  } else if (ta && !tb) {
+    FKF_SYM_LAUNCH(false, false)
+  } else {
+    FKF_SYM_LAUNCH(false, true)
+  }
+#undef FKF_SYM_LAUNCH
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }

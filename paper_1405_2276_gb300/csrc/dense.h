@@ -10,9 +10,11 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
                     int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc);
 // gemm_f64 for a symmetric N x N result (op(A) op(B) symmetric, C symmetric
 // when beta != 0): computes the lower tiles and mirrors them, so C comes out
-// exactly symmetric.
+// exactly symmetric; lower_only: the lower triangle alone is written (for
+// consumers that read only it, such as the blocked Cholesky).
 fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, double alpha, const double* A,
-                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc);
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                        bool lower_only = false);
 fkf_status gemm_f32(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                     int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
 // C (M x N, FP64) = A^T B with A: K x M, B: K x N (row-major), K long.

@@ -489,13 +489,14 @@ __global__ void k_aug_rows(int m, int r, const double* __restrict__ HW, int64_t 
   }
 }
 
-// C (n x n) = a A + d I for A with leading dimension lda
+// C (n x n) = a A + d I for a symmetric A given by its lower triangle
+// (leading dimension lda); C comes out exactly symmetric
 __global__ void k_lincomb_ld(int n, double a, const double* __restrict__ A, int64_t lda, double d,
                              double* __restrict__ C) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    C[e] = a * A[(int64_t)i * lda + j] + (i == j ? d : 0.0);
+    C[e] = a * A[(int64_t)max(i, j) * lda + min(i, j)] + (i == j ? d : 0.0);
   }
 }
 
@@ -558,6 +559,38 @@ __global__ void k_fill_start(int n, double* __restrict__ v) {
 }
 
 // out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
+// Partial sums of ((A - C)_ij rs_i rs_j)^2 over m x m arrays, A in FP64 and C in FP32.
+__global__ void k_frob_diff_part(int64_t n, const double* __restrict__ A, const float* __restrict__ C,
+                                 const double* __restrict__ rs, int m, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t per = (n + kFrobBlocks - 1) / kFrobBlocks;
+  const int64_t a = blockIdx.x * per, b = a + per < n ? a + per : n;
+  double s = 0;
+  for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+    const double v = (A[e] - (double)C[e]) * rs[e / m] * rs[e % m];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// HW (m x r, ld ldh, FP64) in FP32, row-major (ld r) and transposed (r x m).
+__global__ void k_hw_f32(int m, int r, const double* __restrict__ HW, int64_t ldh, float* __restrict__ hw,
+                         float* __restrict__ hwt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * r) return;
+  const int i = (int)(e / r), j = (int)(e % r);
+  const float v = (float)HW[(int64_t)i * ldh + j];
+  hw[e] = v;
+  hwt[(int64_t)j * m + i] = v;
+}
+
 static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part,
                        double* out) {
   k_frob_part<<<kFrobBlocks, 256, 0, ctx->stream>>>(n, A, rs, m, part);
@@ -743,7 +776,8 @@ struct fkf_filter {
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
   DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws, vm;
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
-  TcGemmWs rot;  // tensor-core rotation (FP32 state)
+  TcGemmWs rot;       // tensor-core products (FP32 state): the rotation and the basis test
+  DevBuf hw32, c32;   // basis test of the FP32 state: HW and HW^T in FP32, HW HW^T
   cudaEvent_t ev[7] = {};
   double phase_ms[6] = {};
 };
@@ -789,6 +823,10 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->Dfn, r * r));
   FKF_TRY(A(f->Ep, r * r));
   FKF_TRY(A(f->Qm, r * r));
+  if (f->w == 4) {
+    FKF_TRY(A(f->hw32, m * r));        // 2 m r floats
+    FKF_TRY(A(f->c32, m * m / 2 + 1));  // m^2 floats
+  }
   return FKF_OK;
 }
 
@@ -1019,11 +1057,29 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   double ratio = reuse ? 0.0 : 1.0;  // unchanged H, W and G: the previous step's decision stands
   if (!reuse) {
     double* nrm = f->nll.as<double>() + 1;
+    int tc_fail = 0;
     if (r > 0) {
-      double* T0 = f->Tm.as<double>();
-      FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
-      FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
-      FKF_TRY(frob(ctx, (int64_t)m * m, T0, f->rs.as<double>(), m, f->red.as<double>(), nrm));
+      if (sizeof(T) == 4) {
+        // FP32 state: the test threshold (1e-4) is three orders above FP32 rounding of HW, so
+        // HW HW^T runs on the tensor cores (3xTF32) and A - HW HW^T is formed in FP64
+        float* hw = f->hw32.as<float>();
+        float* hwt = hw + (int64_t)m * r;
+        k_hw_f32<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, hw, hwt);
+        FKF_LAUNCHED(ctx);
+        const TcGemmProblem pr{hw, r, m, r, f->c32.as<float>(), m};
+        FKF_TRY(tc_gemm_f32(ctx, &pr, 1, hwt, m, r, m, f->rot));
+        k_frob_diff_part<<<kFrobBlocks, 256, 0, st>>>((int64_t)m * m, f->As.as<double>(), f->c32.as<float>(),
+                                                     f->rs.as<double>(), m, f->red.as<double>());
+        FKF_LAUNCHED(ctx);
+        k_frob_final<<<1, 32, 0, st>>>(f->red.as<double>(), nrm);
+        FKF_LAUNCHED(ctx);
+        FKF_CUDA(ctx, cudaMemcpyAsync(&tc_fail, f->rot.ctl.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      } else {
+        double* T0 = f->Tm.as<double>();
+        FKF_CUDA(ctx, cudaMemcpyAsync(T0, f->As.p, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st));
+        FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, HW, nm, HW, nm, 1.0, T0, m));
+        FKF_TRY(frob(ctx, (int64_t)m * m, T0, f->rs.as<double>(), m, f->red.as<double>(), nrm));
+      }
       FKF_TRY(frob(ctx, (int64_t)m * m, f->At.as<double>(), nullptr, m, f->red.as<double>(), nrm + 1));
     }
     double hv[2] = {1.0, 1.0};
@@ -1031,6 +1087,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     if (r > 0) FKF_CUDA(ctx, cudaMemcpyAsync(hv, nrm, 16, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (tc_fail) FKF_TRY(tc_gemm_check(ctx, f->rot));
     if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
     if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
   }
@@ -1045,7 +1102,8 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     } else {
       FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
     }
-    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, lda_aug));
+    // S is read only through its lower triangle (blocked Cholesky)
+    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, lda_aug, true));
   }
   if (kept) {
     // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated

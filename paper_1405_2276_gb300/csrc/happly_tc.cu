@@ -657,12 +657,27 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const Ph1& ph, int
         for (int i = 0; i < 32; i++) tile[lane * kEpiLd + i] = v[i];
         __syncwarp();
         const int n = 32 * j + lane;  // column of this lane
+        if (n < nv) {
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-          if (gchunk[q] && n < nv)
-            put4<F>(gchunk[q], gchunk[q] + G::kBBytes, n, gk[q], tile[(4 * q + 0) * kEpiLd + lane],
-                    tile[(4 * q + 1) * kEpiLd + lane], tile[(4 * q + 2) * kEpiLd + lane],
-                    tile[(4 * q + 3) * kEpiLd + lane]);
+          for (int q = 0; q < 8; q += 2) {
+            // FP16: two groups that fill one 16-byte unit (positions p, p + 4 with p % 8 == 0) go
+            // out as one store per half
+            if (F == 2 && gchunk[q] && gchunk[q + 1] == gchunk[q] && gk[q + 1] == gk[q] + 4 && (gk[q] & 7) == 0) {
+              float v[8];
+#pragma unroll
+              for (int i = 0; i < 8; i++) v[i] = tile[(4 * q + i) * kEpiLd + lane];
+              put_unit<F>(gchunk[q], gchunk[q] + G::kBBytes, n, gk[q], v);
+              continue;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const int qq = q + h;
+              if (gchunk[qq])
+                put4<F>(gchunk[qq], gchunk[qq] + G::kBBytes, n, gk[qq], tile[(4 * qq + 0) * kEpiLd + lane],
+                        tile[(4 * qq + 1) * kEpiLd + lane], tile[(4 * qq + 2) * kEpiLd + lane],
+                        tile[(4 * qq + 3) * kEpiLd + lane]);
+            }
+          }
         }
         __syncwarp();
       }
