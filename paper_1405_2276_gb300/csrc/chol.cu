@@ -94,17 +94,30 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
   if (lane < b) xr[lane] = s;
 }
 
-}  // namespace
+// C[r, 0:nc] -= P[r, 0:b] Q^T for rows r < rows, with Q = P[0:nc, 0:b] (the
+// rows of the next diagonal block): the update of the next block column by
+// the current panel.  One warp per row, lane j accumulating column j; Q in
+// shared memory, P's row broadcast by shuffles.
+__global__ void __launch_bounds__(32 * kRowWarps) k_next_column(double* __restrict__ C, int64_t ldc, int64_t rows,
+                                                                int nc, const double* __restrict__ P, int64_t ldp,
+                                                                int b) {
+  __shared__ double q[kB][kB + 1];
+  const int t = threadIdx.x;
+  for (int e = t; e < kB * kB; e += blockDim.x) {
+    const int i = e / kB, l = e % kB;
+    q[i][l] = (i < nc && l < b) ? P[(int64_t)i * ldp + l] : 0.0;
+  }
+  __syncthreads();
+  const int lane = t & 31;
+  const int64_t r = (int64_t)blockIdx.x * kRowWarps + (t >> 5);
+  if (r >= rows) return;
+  const double pl = lane < b ? P[r * ldp + lane] : 0.0;
+  double acc = 0.0;
+#pragma unroll
+  for (int l = 0; l < kB; l++) acc += __shfl_sync(0xffffffffu, pl, l) * q[lane][l];
+  if (lane < nc) C[r * ldc + lane] -= acc;
+}
 
-namespace {
-// Runs the library's launches of its scope on stream s (the context is used
-// by one host thread at a time).
-struct OnStream {
-  fkf_ctx* c;
-  cudaStream_t saved;
-  OnStream(fkf_ctx* ctx, cudaStream_t s) : c(ctx), saved(ctx->stream) { c->stream = s; }
-  ~OnStream() { c->stream = saved; }
-};
 }  // namespace
 
 // With look-ahead (several blocks): the critical chain -- diagonal block k,
@@ -156,8 +169,8 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       const int b1 = k + 1 < nb ? std::min(kB, nf - (k0 + b)) : 0;  // next block column (critical chain)
       if (b1 > 0) {
         if (k >= 1) FKF_CUDA(ctx, cudaStreamWaitEvent(cs, evS[k - 1], 0));
-        OnStream on(ctx, cs);
-        FKF_TRY(gemm_f64(ctx, false, true, rem, b1, b, -1.0, P, lda, P, lda, 1.0, C, lda));
+        k_next_column<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, cs>>>(C, lda, rem, b1, P, lda, b);
+        FKF_LAUNCHED(ctx);
       }
       const int rem2 = rem - b1;
       FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evT[k], 0));
