@@ -242,16 +242,22 @@ typedef struct {
   double r_scalar;
   double nll;        /* out: innovation NLL of this step */
   int32_t status;    /* out: fkf_status of this filter's step */
+  int32_t merged;    /* out: 1 if this step's H-apply ran in the batch's merged launches */
 } fkf_step_desc;
 
 /* Step many independent filters at once (uneven N, m, kernels).  Every
  * filter must belong to a different context (each context owns one CUDA
- * stream); the steps are issued concurrently, one host worker per context,
- * so the GPU overlaps the filters' kernels.  Each filter's step is
- * transactional on its own; descs[i].status reports it.  Returns FKF_OK when
- * every step succeeded, else the status of the first failing entry.  flags as
- * for fkf_filter_step (applied to every entry).  Errors: EINVAL (nb < 1,
- * a context used twice), or the per-filter errors. */
+ * stream); each step runs on its own host thread.  The steps' H-applies (S2)
+ * of FP32 operators on the same tensor-core engine and device are merged:
+ * one persistent launch per apply phase serves all of them (a step waits in
+ * its H-apply until every step of the batch has reached its own or finished
+ * without one); the rest of each step runs on its own context's stream, so
+ * the GPU overlaps the filters' kernels.  Results are bitwise those of
+ * stepping the filters one at a time.  Each filter's step is transactional
+ * on its own; descs[i].status reports it.  Returns FKF_OK when every step
+ * succeeded, else the status of the first failing entry.  flags as for
+ * fkf_filter_step (applied to every entry).  Errors: EINVAL (nb < 1, a
+ * context used twice), or the per-filter errors. */
 fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int32_t flags);
 
 /* Current state: s_hat (host, N, original order; nullable), alpha, rank r,

@@ -8,6 +8,8 @@
 #include <new>
 #include <thread>
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
 #include <utility>
 
 #include "common.h"
@@ -326,6 +328,117 @@ FKF_API fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, co
   return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out);
 }
 
+// ---- merged H-applies of a batch of steps ------------------------------------
+// Every step of fkf_filter_step_batched runs on its own host thread.  A step
+// that reaches its H-apply (S2) registers the request here and waits; a step
+// that ends without one (an error, or the products reused) withdraws.  When
+// every step has registered or withdrawn, the last thread issues one merged
+// launch per phase for all registered applies on the first requester's
+// stream (after each requester's stream reached its apply), and every
+// requester's stream then waits for it.  Operators that cannot be merged are
+// applied one by one on their own streams.
+namespace {
+struct ApplyBatch {
+  struct Req {
+    fkf_hmat* h;
+    const float* X;
+    int64_t ldx;
+    float* Y;
+    int64_t ldy;
+    int64_t ncols;
+    cudaEvent_t ready;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  int expected = 0, arrived = 0, left = 0;
+  bool finished = false;
+  fkf_status status = FKF_OK;
+  std::vector<Req> reqs;
+  std::vector<cudaEvent_t> evs;  // one per step (ready) + done
+  cudaEvent_t done = nullptr;
+  bool merged = false;
+
+  // with mu held, once every step has registered or withdrawn
+  void run() {
+    if (reqs.empty()) {
+      finished = true;
+      return;
+    }
+    std::vector<fkf_hmat*> hs;
+    std::vector<const float*> X;
+    std::vector<float*> Y;
+    std::vector<int64_t> ldx, ldy, nc;
+    for (const Req& r : reqs) {
+      hs.push_back(r.h);
+      X.push_back(r.X);
+      Y.push_back(r.Y);
+      ldx.push_back(r.ldx);
+      ldy.push_back(r.ldy);
+      nc.push_back(r.ncols);
+    }
+    merged = hmat_tc_multi_ok(hs.data(), (int)hs.size(), nc.data());
+    fkf_status st = FKF_OK;
+    if (merged) {
+      fkf_ctx* lctx = reqs[0].h->ctx;
+      if (cudaSetDevice(lctx->device) != cudaSuccess) st = set_err(lctx, FKF_ECUDA, "cudaSetDevice failed");
+      for (const Req& r : reqs)
+        if (st == FKF_OK && cudaStreamWaitEvent(lctx->stream, r.ready, 0) != cudaSuccess)
+          st = set_err(lctx, FKF_ECUDA, "batched apply: stream wait failed");
+      if (st == FKF_OK)
+        st = hmat_apply_tc_multi(lctx, hs.data(), (int)hs.size(), X.data(), ldx.data(), Y.data(), ldy.data(),
+                                 nc.data());
+      if (st == FKF_OK && cudaEventRecord(done, lctx->stream) != cudaSuccess)
+        st = set_err(lctx, FKF_ECUDA, "batched apply: event record failed");
+    } else {
+      for (const Req& r : reqs)
+        if (st == FKF_OK) st = hmat_apply_clustered(r.h, r.X, r.ldx, r.Y, r.ldy, r.ncols);
+    }
+    status = st;
+    finished = true;
+  }
+
+  fkf_status apply(const Req& req) {
+    std::unique_lock<std::mutex> lk(mu);
+    reqs.push_back(req);
+    arrived++;
+    if (arrived + left == expected)
+      run();
+    else
+      cv.wait(lk, [&] { return finished; });
+    lk.unlock();
+    cv.notify_all();
+    return status;
+  }
+
+  void withdraw() {
+    std::unique_lock<std::mutex> lk(mu);
+    left++;
+    if (arrived + left == expected && !finished) run();
+    lk.unlock();
+    cv.notify_all();
+  }
+};
+
+thread_local ApplyBatch* tls_batch = nullptr;
+thread_local int tls_batch_index = -1;
+thread_local bool tls_batch_arrived = false;
+}  // namespace
+
+fkf_status hmat_apply_step(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols) {
+  ApplyBatch* b = tls_batch;
+  if (!b || tls_batch_arrived || h->prec != FKF_FP32 || h->engine == 0)
+    return hmat_apply_clustered(h, X, ldx, Y, ldy, ncols);
+  tls_batch_arrived = true;
+  fkf_ctx* ctx = h->ctx;
+  const cudaEvent_t ready = b->evs[tls_batch_index];
+  FKF_CUDA(ctx, cudaEventRecord(ready, ctx->stream));
+  const fkf_status st =
+      b->apply({h, static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, ncols, ready});
+  if (st != FKF_OK) return set_err(ctx, st, "batched H-apply failed");
+  if (b->merged) FKF_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, b->done, 0));
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int32_t flags) {
   if (!descs || nb < 1) return FKF_EINVAL;
   std::vector<fkf_ctx*> ctxs(nb);
@@ -335,24 +448,36 @@ FKF_API fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int
     for (int j = 0; j < i; j++)
       if (ctxs[j] == ctxs[i]) return set_err(ctxs[i], FKF_EINVAL, "step_batched: filters %d and %d share a context", j, i);
   }
-  const int nthreads = (int)std::min<int64_t>(nb, std::max(1u, std::thread::hardware_concurrency()));
-  std::atomic<int> next{0};
-  auto worker = [&]() {
-    while (true) {
-      const int i = next.fetch_add(1);
-      if (i >= nb) break;
-      fkf_step_desc& d = descs[i];
-      fkf_ctx* ctx = ctxs[i];
-      fkf_status st = FKF_OK;
-      if (cudaSetDevice(ctx->device) != cudaSuccess) st = set_err(ctx, FKF_ECUDA, "cudaSetDevice failed");
-      if (st == FKF_OK) st = fkf_filter_step(d.filter, d.y, d.m, d.H_rowptr, d.H_col, d.H_val, d.R, d.r_scalar, flags,
-                                             &d.nll);
-      d.status = st;
+  ApplyBatch batch;
+  batch.expected = nb;
+  batch.evs.resize(nb + 1, nullptr);
+  for (int i = 0; i <= nb; i++)
+    if (cudaSetDevice(ctxs[std::min(i, nb - 1)]->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&batch.evs[i], cudaEventDisableTiming) != cudaSuccess) {
+      for (int j = 0; j < i; j++) cudaEventDestroy(batch.evs[j]);
+      return set_err(ctxs[0], FKF_ECUDA, "step_batched: event creation failed");
     }
+  batch.done = batch.evs[nb];
+  // one host thread per step: a step waits in its H-apply for the others
+  auto worker = [&](int i) {
+    fkf_step_desc& d = descs[i];
+    fkf_ctx* ctx = ctxs[i];
+    tls_batch = &batch;
+    tls_batch_index = i;
+    tls_batch_arrived = false;
+    fkf_status st = FKF_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) st = set_err(ctx, FKF_ECUDA, "cudaSetDevice failed");
+    if (st == FKF_OK)
+      st = fkf_filter_step(d.filter, d.y, d.m, d.H_rowptr, d.H_col, d.H_val, d.R, d.r_scalar, flags, &d.nll);
+    if (!tls_batch_arrived) batch.withdraw();
+    d.merged = tls_batch_arrived && batch.merged ? 1 : 0;
+    tls_batch = nullptr;
+    d.status = st;
   };
   std::vector<std::thread> pool;
-  for (int t = 0; t < nthreads; t++) pool.emplace_back(worker);
+  for (int i = 0; i < nb; i++) pool.emplace_back(worker, i);
   for (auto& t : pool) t.join();
+  for (cudaEvent_t e : batch.evs) cudaEventDestroy(e);
   for (int i = 0; i < nb; i++)
     if (descs[i].status != FKF_OK) return (fkf_status)descs[i].status;
   return FKF_OK;

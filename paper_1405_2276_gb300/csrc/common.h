@@ -39,6 +39,19 @@ struct TcGemmWs {
   DevBuf asplit, bsplit, ctl;
 };
 
+// Workspace of the merged multi-operator H-apply (job lists and their host
+// staging, tile counters and error flag).
+struct TcMultiWs {
+  DevBuf jobs, ctl;
+  void* staging = nullptr;  // pinned host copy of the job lists
+  size_t staging_bytes = 0;
+  cudaEvent_t staged = nullptr;  // the last upload from the staging buffer completed
+  ~TcMultiWs() {
+    if (staging) cudaFreeHost(staging);
+    if (staged) cudaEventDestroy(staged);
+  }
+};
+
 struct fkf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -51,6 +64,7 @@ struct fkf_ctx {
   TcGemmWs gemm_ws;    // fkf_rotate_f32
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
   std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
+  TcMultiWs multi_ws;                 // merged H-applies of batched steps launched on this context
 };
 
 // Second stream of the context and at least n events (created on first use).
@@ -250,6 +264,18 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu);
 // Selects the engine (0, 1, 2); rewrites the split operator stream when the
 // tensor-core format changes.
 fkf_status hmat_set_engine(fkf_hmat* h, int engine);
+// Y_f = Gamma_f X_f (cluster order) for nb FP32 operators on the same
+// tensor-core format, each in one column pass (ncols_f <= its panel), with
+// one persistent launch per phase for all of them, on ctx's stream; the
+// caller orders that stream after the producers of every X_f.  A failed wait
+// is reported through every operator's tensor-core error flag.
+fkf_status hmat_apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float* const* X, const int64_t* ldx,
+                               float* const* Y, const int64_t* ldy, const int64_t* ncols);
+// True when hmat_apply_tc_multi can run these operators together.
+bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols);
+// The step's H-apply (S2): through the batch of the calling host thread when
+// it takes part in one (fkf_filter_step_batched), else a plain apply.
+fkf_status hmat_apply_step(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
 // Dense C_p = A_p B[0:K_p, 0:ncols] for p < np <= 2 (row-major FP32 in and
 // out) on the tensor cores with 3xTF32 products; B has kb >= K_p rows.  The
 // launch is asynchronous: tc_gemm_check reads the error flag after a sync.

@@ -1032,7 +1032,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_LAUNCHED(ctx);
     FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
     // ---- S2: G = Gamma_H H^T
-    FKF_TRY(hmat_apply_clustered(h, f->Bt.p, m, G, ld, m));
+    FKF_TRY(hmat_apply_step(h, f->Bt.p, m, G, ld, m));
     FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
     // ---- gathers: [HW | A] = H [W G]; innovation
     csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm, st);

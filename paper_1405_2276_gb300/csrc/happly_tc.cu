@@ -341,6 +341,8 @@ struct Ph2 {
   int64_t ldy;
   const float* rpt;
   const float* cinv;
+  const uint8_t* astream;  // split operator stream
+  int nct, ncols;          // column tiles and columns of the pass
   __device__ __forceinline__ int nchunk(int64_t w) const { return tiles[w].nchunk; }
   __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return tiles[w].a_chunk0; }
   __device__ __forceinline__ int nseg(int64_t w) const { return tiles[w].nseg; }
@@ -370,6 +372,8 @@ struct Ph1 {
   uint8_t* zsplit;
   float* part;
   int64_t ldp;
+  const uint8_t* astream;
+  int nct, ncols;
   __device__ __forceinline__ int nchunk(int64_t w) const { return items[w].nchunk; }
   __device__ __forceinline__ int64_t a_chunk0(int64_t w) const { return items[w].a_chunk0; }
   __device__ __forceinline__ int nseg(int64_t) const { return 1; }
@@ -394,6 +398,8 @@ struct PhGemm {
   int64_t nw0;     // row tiles of problem 0
   int nch0, nch1;  // K chunks per tile
   const float* cinv;  // unused (unscaled format)
+  const uint8_t* astream;
+  int nct, ncols;
   // (fields selected, not indexed: a dynamic index into a kernel parameter
   // array would copy the parameters to local memory)
   __device__ __forceinline__ int nchunk(int64_t w) const { return w >= nw0 ? nch1 : nch0; }
@@ -414,6 +420,34 @@ struct PhGemm {
   }
 };
 
+// A set of jobs of one phase run by one persistent launch: one job (a
+// filter's apply, passed by value) or a device list of jobs whose tiles are
+// numbered consecutively (t0[j] = first global tile of job j).  Queue entries
+// carry (job, tile within the job).
+constexpr int kJobShift = 44;
+constexpr int64_t kLocalMask = (int64_t(1) << kJobShift) - 1;
+
+template <class Ph>
+struct JobSet {
+  Ph one;
+  const Ph* list;
+  const int64_t* t0;
+  int nj;  // 0: the single job `one`
+  __device__ __forceinline__ Ph get(int j) const { return nj ? list[j] : one; }
+  __device__ __forceinline__ int64_t pack(int64_t id) const {
+    if (!nj) return id;
+    int lo = 0, hi = nj - 1;  // largest j with t0[j] <= id
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (t0[mid] <= id)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    return ((int64_t)lo << kJobShift) | (id - t0[lo]);
+  }
+};
+
 // ---- roles -----------------------------------------------------------------
 // Next tile of this CTA: taken from the global counter by the producer and
 // published in the queue; every consumer reads each queue entry once.
@@ -431,22 +465,25 @@ __device__ __forceinline__ bool next_tile(const Smem<F>& s, int qi, int64_t& id)
 // fewer): one bulk copy for their A chunks (consecutive in the operator
 // stream), one per B chunk.
 template <int F, class Ph>
-__device__ __forceinline__ void producer(const Smem<F>& s, const Ph& ph, int64_t ntiles, int nct,
-                                         const uint8_t* astream, unsigned long long* counter) {
+__device__ __forceinline__ void producer(const Smem<F>& s, const JobSet<Ph>& js, int64_t ntiles,
+                                         unsigned long long* counter) {
   using G = Geo<F>;
   int64_t g = 0;  // stages issued
   for (int qi = 0;; qi++) {
-    int64_t id = (int64_t)atomicAdd(counter, 1ull);
-    if (id >= ntiles) id = -1;
+    const int64_t id = (int64_t)atomicAdd(counter, 1ull);
+    const int64_t packed = id < ntiles ? js.pack(id) : -1;
     const int slot = qi % kQ;
     if (qi >= kQ && !wait_bar(s, G::QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
-    *reinterpret_cast<volatile int64_t*>(&s.q[slot]) = id;
+    *reinterpret_cast<volatile int64_t*>(&s.q[slot]) = packed;
     umma::mbar_arrive(&s.bar[G::QF + slot]);
-    if (id < 0) return;
-    const int64_t w = id / nct;
-    const int ct = (int)(id % nct);
+    if (packed < 0) return;
+    const Ph ph = js.get((int)(packed >> kJobShift));
+    const int64_t lid = packed & kLocalMask;
+    const int nct = ph.nct;
+    const int64_t w = lid / nct;
+    const int ct = (int)(lid % nct);
     const int nch = ph.nchunk(w);
-    const uint8_t* ap = astream + ph.a_chunk0(w) * (int64_t)G::kAChunk;
+    const uint8_t* ap = ph.astream + ph.a_chunk0(w) * (int64_t)G::kAChunk;
     const int ns = ph.nseg(w);
     int t = 0, j = 0, nin = 0, st = 0;  // chunk of the tile, chunk within the stage, chunks in the stage
     for (int sg = 0; sg < ns; sg++) {
@@ -498,14 +535,15 @@ __device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, ui
 }
 
 template <int F, class Ph>
-__device__ __forceinline__ void mma_issuer(const Smem<F>& s, const Ph& ph, int nct, uint32_t tmem) {
+__device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& js, uint32_t tmem) {
   using G = Geo<F>;
   int64_t g = 0;
   int tl = 0;
   bool ok = true;
   int64_t id;
   for (; ok && next_tile(s, tl, id); tl++) {
-    const int nch = ph.nchunk(id / nct);
+    const Ph ph = js.get((int)(id >> kJobShift));
+    const int nch = ph.nchunk((id & kLocalMask) / ph.nct);
     const int b = tl & 1;
     if (tl >= 2 && !wait_bar(s, G::AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
     umma::fence_after_sync();
@@ -560,7 +598,7 @@ struct RowSinkY {
 // Rows of a row-major output: Ph supplies the destination row (nullptr past
 // the tile's rows) and its inverse scale, and nchunk (0: the tile is zero).
 template <int F, class Ph>
-__device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
+__device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const JobSet<Ph>& js, uint32_t tmem) {
   using G = Geo<F>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;  // TMEM lanes 32*quarter.. are this warp's
@@ -573,9 +611,11 @@ __device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const Ph& ph, in
     if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
     if (s.failed()) break;
-    const int64_t w = id / nct;
-    const int n0 = (int)(id % nct) * kN;
-    const int nv = min(kN, ncols - n0);
+    const Ph ph = js.get((int)(id >> kJobShift));
+    const int64_t lid = id & kLocalMask;
+    const int64_t w = lid / ph.nct;
+    const int n0 = (int)(lid % ph.nct) * kN;
+    const int nv = min(kN, ph.ncols - n0);
     const bool zero = ph.nchunk(w) == 0;
     float rinv = 1.f;
     float* dst = ph.row_dst(w, row, rinv);
@@ -605,7 +645,7 @@ __device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const Ph& ph, in
 // run per hi/lo half.  (Slot values stay scaled: phase 2's operator columns
 // carry the inverse scales.)
 template <int F>
-__device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const Ph1& ph, int nct, int ncols, uint32_t tmem) {
+__device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>& js, uint32_t tmem) {
   using G = Geo<F>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;
@@ -619,10 +659,13 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const Ph1& ph, int
     if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
     umma::fence_after_sync();
     if (s.failed()) break;
-    const int64_t w = id / nct;
-    const int ct = (int)(id % nct);
+    const Ph1 ph = js.get((int)(id >> kJobShift));
+    const int64_t lid = id & kLocalMask;
+    const int nct = ph.nct;
+    const int64_t w = lid / nct;
+    const int ct = (int)(lid % nct);
     const int n0 = ct * kN;
-    const int nv = min(kN, ncols - n0);
+    const int nv = min(kN, ph.ncols - n0);
     const P1Item& it = ph.items[w];
     const bool zero = it.nchunk == 0;
     const bool partial = it.out_row >= 0;
@@ -688,22 +731,20 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const Ph1& ph, int
 }
 
 template <int F, class Ph>
-__device__ __forceinline__ void epilogue(const Smem<F>& s, const Ph& ph, int nct, int ncols, uint32_t tmem) {
+__device__ __forceinline__ void epilogue(const Smem<F>& s, const JobSet<Ph>& js, uint32_t tmem) {
   if constexpr (std::is_same<Ph, Ph1>::value)
-    epilogue_p1<F>(s, ph, nct, ncols, tmem);
+    epilogue_p1<F>(s, js, tmem);
   else
-    epilogue_rows<F>(s, ph, nct, ncols, tmem);
+    epilogue_rows<F>(s, js, tmem);
 }
 
 template <int F, class Ph>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_apply(const Ph ph, int64_t nwork, int nct, int ncols, const uint8_t* __restrict__ astream,
-               unsigned long long* __restrict__ counter, int* __restrict__ err) {
+    k_tc_apply(const JobSet<Ph> js, int64_t ntiles, unsigned long long* __restrict__ counter, int* __restrict__ err) {
   using G = Geo<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const Smem<F> s = smem_layout<F>(smem_raw);
   const int warp = threadIdx.x >> 5;
-  const int64_t ntiles = nwork * nct;
   if (threadIdx.x == 0) {
     for (int i = G::FULL; i < G::EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
     for (int i = G::EMPTY; i < G::AF; i++) umma::mbar_init(&s.bar[i], 1);
@@ -721,12 +762,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
   if (warp == kProdWarp) {
-    if ((threadIdx.x & 31) == 0) producer<F>(s, ph, ntiles, nct, astream, counter);
+    if ((threadIdx.x & 31) == 0) producer<F>(s, js, ntiles, counter);
   } else if (warp == kMmaWarp) {
-    if ((threadIdx.x & 31) == 0) mma_issuer<F>(s, ph, nct, tmem);
+    if ((threadIdx.x & 31) == 0) mma_issuer<F>(s, js, tmem);
     __syncwarp();
   } else {
-    epilogue<F>(s, ph, nct, ncols, tmem);
+    epilogue<F>(s, js, tmem);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -843,8 +884,12 @@ __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const flo
   }
 }
 
+fkf_status build_stream(fkf_hmat* h, int F);
+
+// Buffers of an apply of up to one panel of columns per pass (allocated or
+// grown on first use; the slot workspace is cleared when its format changes).
 template <int F>
-fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+fkf_status tc_buffers(fkf_hmat* h, cudaStream_t st) {
   using G = Geo<F>;
   fkf_ctx* ctx = h->ctx;
   const int64_t P = h->tc_panel;
@@ -855,65 +900,190 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
   if (h->zsplit.bytes < zbytes || h->zsplit_fmt != F) {
     // padding slots of the split workspace are never written: they start (and stay) zero
     if (h->zsplit.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zsplit, zbytes));
-    FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, h->zsplit.bytes, ctx->stream));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, h->zsplit.bytes, st));
     h->zsplit_fmt = F;
   }
   const size_t pbytes = (size_t)std::max<int64_t>(h->tc_part_rows, 1) * P * sizeof(float);
   if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
   if (h->tc_err.bytes < 64) {
     FKF_TRY(dev_alloc(ctx, h->tc_err, 64));
-    FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, ctx->stream));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, st));
   }
   // column maxima and scales of one pass (format 2)
   if (F == 2 && h->tc_col.bytes < (size_t)P * 12) FKF_TRY(dev_alloc(ctx, h->tc_col, (size_t)P * 12));
+  return FKF_OK;
+}
+
+// Split X of one pass (nc columns) on stream st; format 2 first computes the
+// column scales (returned in cs: scales, then inverse scales).
+template <int F>
+fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaStream_t st, float*& cs) {
+  fkf_ctx* ctx = h->ctx;
+  const int64_t P = h->tc_panel;
+  const int nct = (int)cdiv(nc, kN);
+  cs = nullptr;
+  if (F == 2) {
+    unsigned* cmax = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
+    cs = h->tc_col.as<float>();
+    FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned), st));
+    const int64_t rpb = 2048;
+    k_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, st>>>(X, ldx, h->n, nc, rpb, cmax);
+    FKF_LAUNCHED(ctx);
+    k_colscale<<<(unsigned)cdiv(nc, 256), 256, 0, st>>>(cmax, nc, cs);
+    FKF_LAUNCHED(ctx);
+  }
+  if (h->n_tcx > 0) {
+    k_tc_split_x<F><<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, st>>>(X, ldx, nc, h->tcxmap.as<TcXChunk>(), 0,
+                                                                             nct, cs, h->xsplit.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+template <int F>
+Ph1 tc_ph1(fkf_hmat* h, int nc) {
+  return Ph1{h->tcp1.as<P1Item>(), h->xsplit.as<uint8_t>(), h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
+             h->part.as<float>(), h->tc_panel, h->tca.as<uint8_t>(), (int)cdiv(nc, kN), nc};
+}
+
+template <int F>
+Ph2 tc_ph2(fkf_hmat* h, float* Y, int64_t ldy, int nc, const float* cs) {
+  return Ph2{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
+             Y, ldy, F == 2 ? h->tc_rpt.as<float>() : nullptr, F == 2 ? cs + nc : nullptr, h->tca.as<uint8_t>(),
+             (int)cdiv(nc, kN), nc};
+}
+
+template <int F>
+fkf_status tc_reduce(fkf_hmat* h, int nc, cudaStream_t st) {
+  if (h->n_tcred == 0) return FKF_OK;
+  k_phase1_reduce_tc<F><<<dim3((unsigned)h->n_tcred, 4), 256, 0, st>>>(
+      h->tcred.as<P1Reduce>(), h->part.as<float>(), h->tc_panel, h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
+      (int)cdiv(nc, kN), nc);
+  FKF_LAUNCHED(h->ctx);
+  return FKF_OK;
+}
+
+template <int F>
+fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
+  using G = Geo<F>;
+  fkf_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t P = h->tc_panel;
+  FKF_TRY(tc_buffers<F>(h, st));
   // tile counters of the two phases at tc_err + 16, + 24 bytes
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
-  const uint8_t* astream = h->tca.as<uint8_t>();
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
     const int nct = (int)cdiv(nc, kN);
-    FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     float* cs = nullptr;
-    if (F == 2) {
-      unsigned* cmax = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
-      cs = h->tc_col.as<float>();
-      FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned), ctx->stream));
-      const int64_t rpb = 2048;
-      k_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, ctx->stream>>>(X + c0, ldx, h->n,
-                                                                                                 nc, rpb, cmax);
-      FKF_LAUNCHED(ctx);
-      k_colscale<<<(unsigned)cdiv(nc, 256), 256, 0, ctx->stream>>>(cmax, nc, cs);
-      FKF_LAUNCHED(ctx);
-    }
-    if (h->n_tcx > 0) {
-      k_tc_split_x<F><<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, ctx->stream>>>(
-          X + c0, ldx, nc, h->tcxmap.as<TcXChunk>(), 0, nct, cs, h->xsplit.as<uint8_t>());
-      FKF_LAUNCHED(ctx);
-    }
+    FKF_TRY(tc_split_pass<F>(h, X + c0, ldx, nc, st, cs));
     if (h->n_tcp1 > 0) {
-      const Ph1 ph{h->tcp1.as<P1Item>(), h->xsplit.as<uint8_t>(), h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(),
-                   h->part.as<float>(), P};
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
-      k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, h->n_tcp1, nct, nc, astream, counters,
-                                                                     h->tc_err.as<int>());
+      k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph1>{tc_ph1<F>(h, nc), nullptr, nullptr, 0},
+                                                            h->n_tcp1 * nct, counters, h->tc_err.as<int>());
       FKF_LAUNCHED(ctx);
     }
-    if (h->n_tcred > 0) {
-      k_phase1_reduce_tc<F><<<dim3((unsigned)h->n_tcred, 4), 256, 0, ctx->stream>>>(
-          h->tcred.as<P1Reduce>(), h->part.as<float>(), P, h->tcslot.as<int64_t>(), h->zsplit.as<uint8_t>(), nct, nc);
-      FKF_LAUNCHED(ctx);
-    }
-    const Ph2 ph{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
-                 Y + c0, ldy, F == 2 ? h->tc_rpt.as<float>() : nullptr, F == 2 ? cs + nc : nullptr};
+    FKF_TRY(tc_reduce<F>(h, nc, st));
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
-    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, h->n_tctile, nct, nc, astream, counters + 1,
-                                                                   h->tc_err.as<int>());
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph2>{tc_ph2<F>(h, Y + c0, ldy, nc, cs), nullptr,
+                                                                      nullptr, 0},
+                                                          h->n_tctile * nct, counters + 1, h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
   }
+  return FKF_OK;
+}
+
+// err -> every operator's tensor-core error flag
+__global__ void k_err_fanout(const int* __restrict__ err, int* const* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && *err) atomicExch(dst[i], 1);
+}
+
+template <int F>
+fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float* const* X, const int64_t* ldx,
+                          float* const* Y, const int64_t* ldy, const int64_t* ncols) {
+  using G = Geo<F>;
+  cudaStream_t st = ctx->stream;
+  TcMultiWs& ws = ctx->multi_ws;
+  std::vector<Ph1> p1;
+  std::vector<Ph2> p2;
+  std::vector<int64_t> t1{0}, t2{0};
+  std::vector<int*> errs;
+  std::vector<int> active;
+  for (int f = 0; f < nb; f++) {
+    fkf_hmat* h = hs[f];
+    if (ncols[f] <= 0) continue;
+    if (h->tca_fmt != F) FKF_TRY(build_stream(h, F));
+    FKF_TRY(tc_buffers<F>(h, st));
+    const int nc = (int)ncols[f];
+    const int nct = (int)cdiv(nc, kN);
+    float* cs = nullptr;
+    FKF_TRY(tc_split_pass<F>(h, X[f], ldx[f], nc, st, cs));
+    if (h->n_tcp1 > 0) {
+      p1.push_back(tc_ph1<F>(h, nc));
+      t1.push_back(t1.back() + h->n_tcp1 * nct);
+    }
+    if (h->n_tctile > 0) {
+      p2.push_back(tc_ph2<F>(h, Y[f], ldy[f], nc, cs));
+      t2.push_back(t2.back() + h->n_tctile * nct);
+    }
+    errs.push_back(h->tc_err.as<int>());
+    active.push_back(f);
+  }
+  if (active.empty()) return FKF_OK;
+  // job lists: Ph1[], Ph2[], t1[], t2[], error flags[] (8-byte aligned pieces)
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  const size_t o1 = 0, o2 = al(o1 + p1.size() * sizeof(Ph1)), ot1 = al(o2 + p2.size() * sizeof(Ph2)),
+               ot2 = al(ot1 + t1.size() * 8), oe = al(ot2 + t2.size() * 8), total = al(oe + errs.size() * 8);
+  if (!ws.staged) FKF_CUDA(ctx, cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming));
+  FKF_CUDA(ctx, cudaEventSynchronize(ws.staged));  // the previous upload has left the staging buffer
+  if (ws.staging_bytes < total) {
+    if (ws.staging) cudaFreeHost(ws.staging);
+    ws.staging = nullptr;
+    ws.staging_bytes = 0;
+    FKF_CUDA(ctx, cudaMallocHost(&ws.staging, total));
+    ws.staging_bytes = total;
+  }
+  if (ws.jobs.bytes < total) FKF_TRY(dev_alloc(ctx, ws.jobs, total));
+  if (ws.ctl.bytes < 64) FKF_TRY(dev_alloc(ctx, ws.ctl, 64));
+  char* hb = static_cast<char*>(ws.staging);
+  std::memcpy(hb + o1, p1.data(), p1.size() * sizeof(Ph1));
+  std::memcpy(hb + o2, p2.data(), p2.size() * sizeof(Ph2));
+  std::memcpy(hb + ot1, t1.data(), t1.size() * 8);
+  std::memcpy(hb + ot2, t2.data(), t2.size() * 8);
+  std::memcpy(hb + oe, errs.data(), errs.size() * 8);
+  FKF_CUDA(ctx, cudaMemcpyAsync(ws.jobs.p, hb, total, cudaMemcpyHostToDevice, st));
+  FKF_CUDA(ctx, cudaEventRecord(ws.staged, st));
+  char* db = ws.jobs.as<char>();
+  int* err = ws.ctl.as<int>();
+  unsigned long long* counters = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
+  FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, st));
+  int sms = 0;
+  FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  if (!p1.empty()) {
+    const JobSet<Ph1> js{p1[0], reinterpret_cast<const Ph1*>(db + o1), reinterpret_cast<const int64_t*>(db + ot1),
+                         (int)p1.size()};
+    const int grid = (int)std::min<int64_t>(sms, t1.back());
+    k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(js, t1.back(), counters, err);
+    FKF_LAUNCHED(ctx);
+  }
+  for (int f : active) FKF_TRY(tc_reduce<F>(hs[f], (int)ncols[f], st));
+  if (!p2.empty()) {
+    const JobSet<Ph2> js{p2[0], reinterpret_cast<const Ph2*>(db + o2), reinterpret_cast<const int64_t*>(db + ot2),
+                         (int)p2.size()};
+    const int grid = (int)std::min<int64_t>(sms, t2.back());
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, st>>>(js, t2.back(), counters + 1, err);
+    FKF_LAUNCHED(ctx);
+  }
+  k_err_fanout<<<1, 64, 0, st>>>(err, reinterpret_cast<int* const*>(db + oe), (int)errs.size());
+  FKF_LAUNCHED(ctx);
   return FKF_OK;
 }
 
@@ -979,6 +1149,27 @@ fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, flo
   return apply_tc<1>(h, X, ldx, Y, ldy, ncols);
 }
 
+bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols) {
+  if (nb < 1) return false;
+  const int F = hs[0]->engine;
+  for (int f = 0; f < nb; f++) {
+    const fkf_hmat* h = hs[f];
+    if (h->prec != FKF_FP32 || h->engine != F || (F != 1 && F != 2) || ncols[f] > h->tc_panel ||
+        h->ctx->device != hs[0]->ctx->device)
+      return false;
+    for (int g = 0; g < f; g++)
+      if (hs[g] == h) return false;  // one operator's buffers serve one apply at a time
+  }
+  return true;
+}
+
+fkf_status hmat_apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float* const* X, const int64_t* ldx,
+                               float* const* Y, const int64_t* ldy, const int64_t* ncols) {
+  if (!hmat_tc_multi_ok(hs, nb, ncols)) return set_err(ctx, FKF_EINVAL, "merged apply: operators not compatible");
+  if (hs[0]->engine == 2) return apply_tc_multi<2>(ctx, hs, nb, X, ldx, Y, ldy, ncols);
+  return apply_tc_multi<1>(ctx, hs, nb, X, ldx, Y, ldy, ncols);
+}
+
 fkf_status hmat_set_engine(fkf_hmat* h, int engine) {
   if (engine != 0 && h->tca_fmt != engine) FKF_TRY(build_stream(h, engine));
   h->engine = engine;
@@ -1029,12 +1220,15 @@ fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float
     FKF_LAUNCHED(ctx);
   }
   ph.bsplit = ws.bsplit.as<uint8_t>();
+  ph.astream = ws.asplit.as<uint8_t>();
+  ph.nct = nct;
+  ph.ncols = ncols;
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<1, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
   const int grid = (int)std::min<int64_t>(sms, nwork * nct);
-  k_tc_apply<1, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(ph, nwork, nct, ncols, ws.asplit.as<uint8_t>(),
-                                                                   counter, ws.ctl.as<int>());
+  k_tc_apply<1, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
+                                                                   nwork * nct, counter, ws.ctl.as<int>());
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }

@@ -56,7 +56,7 @@ class fkf_step_desc(C.Structure):
     _fields_ = [
         ("filter", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int32), ("H_rowptr", C.c_void_p),
         ("H_col", C.c_void_p), ("H_val", C.c_void_p), ("R", C.c_void_p), ("r_scalar", C.c_double),
-        ("nll", C.c_double), ("status", C.c_int32),
+        ("nll", C.c_double), ("status", C.c_int32), ("merged", C.c_int32),
     ]
 
 
@@ -277,10 +277,11 @@ def fkf_filter_step(f, y, m, rowptr, col, val, R=None, r_scalar=0.0, flags=0, wa
     return nll.value
 
 
-def fkf_filter_step_batched(entries, flags=0):
+def fkf_filter_step_batched(entries, flags=0, return_merged=False):
     """entries: list of (filter, y, rowptr, col, val, R or None, r_scalar), each
-    filter on its own context.  Returns the list of per-filter NLLs; raises
-    FkfError (with the first failing status) if any step failed."""
+    filter on its own context.  Returns the list of per-filter NLLs (and, with
+    return_merged, whether each step's H-apply ran in the merged launches);
+    raises FkfError (with the first failing status) if any step failed."""
     nb = len(entries)
     descs = (fkf_step_desc * nb)()
     keep = []
@@ -299,7 +300,10 @@ def fkf_filter_step_batched(entries, flags=0):
         bad = next(i for i in range(nb) if descs[i].status != FKF_OK) if any(
             descs[i].status != FKF_OK for i in range(nb)) else 0
         _check(st, entries[bad][0].ctx)
-    return [descs[i].nll for i in range(nb)]
+    nlls = [descs[i].nll for i in range(nb)]
+    if return_merged:
+        return nlls, [bool(descs[i].merged) for i in range(nb)]
+    return nlls
 
 
 def fkf_filter_get(f, n, want_s=True, want_D=True, W=None):

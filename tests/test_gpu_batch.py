@@ -101,3 +101,58 @@ def test_batched_rejects_shared_context_and_reports_per_filter_status(fkf):
     fkf.fkf_filter_destroy(f2)
     del ctx
     _free(fkf, objs)
+
+
+SPECS32 = [  # uneven FP32 filters: grid, n_src, n_rec, nu, ell
+    ((24, 24), 3, 4, 0.5, 0.1),
+    ((64, 48), 8, 8, 1.5, 0.2),
+    ((40, 40), 6, 10, 0.5, 0.05),
+    ((96, 80), 12, 10, 1.5, 0.08),
+    ((32, 56), 4, 6, 0.5, 0.3),
+    ((72, 72), 10, 12, 1.5, 0.12),
+]
+
+
+def _make32(fkf, steps, engine=None):
+    out = []
+    for i, (grid, ns, nr, nu, ell) in enumerate(SPECS32):
+        wl = synth.tomography_workload(grid, ns, nr, steps, ell, 1.0, 1e-4, seed=synth.BASE_SEED + 1000 * 4 + i)
+        ctx = fkf.fkf_create(0)
+        hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, precision=1)
+        if engine is not None and i == 1:
+            fkf.fkf_hmatrix_set_engine(hm, engine)
+        m = wl["H"].nrows
+        f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)
+        out.append(dict(wl=wl, ctx=ctx, hm=hm, f=f))
+    return out
+
+
+@pytest.mark.parametrize("engine", [None, 1])
+def test_fp32_batch_merged_apply_bitwise(fkf, engine):
+    """FP32 filters of uneven N and m: with one tensor-core format the batch's
+    H-applies run as one merged launch per phase (engine None: all on the
+    default engine); with one filter on another format (engine 1) they run one
+    by one.  Either way every result equals stepping the filters alone, bit
+    for bit."""
+    steps = 3
+    a = _make32(fkf, steps, engine)
+    b = _make32(fkf, steps, engine)
+    for k in range(steps):
+        entries = []
+        for o in a:
+            h = o["wl"]["H"]
+            entries.append((o["f"], o["wl"]["y"][k], h.rowptr, h.col, h.val, None, 1e-4))
+        nll_b, merged = fkf.fkf_filter_step_batched(entries, return_merged=True)
+        assert all(merged) if engine is None else not any(merged)
+        nll_s = []
+        for o in b:
+            h = o["wl"]["H"]
+            nll_s.append(fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4))
+        assert nll_b == nll_s
+    for oa, ob in zip(a, b):
+        n = oa["wl"]["points"].shape[0]
+        sa, sb = fkf.fkf_filter_get(oa["f"], n), fkf.fkf_filter_get(ob["f"], n)
+        np.testing.assert_array_equal(sa["s"], sb["s"])
+        np.testing.assert_array_equal(sa["D"], sb["D"])
+    _free(fkf, a)
+    _free(fkf, b)
