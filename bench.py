@@ -83,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -350,6 +350,71 @@ def run_gpu(args, rank, world):
     return res, wl
 
 
+def batch_bench(nb, steps, warmup):
+    """nb independent FP32 filters of uneven size (N log-uniform in [16384, 131072] on square
+    grids, m = n_src x n_rec in [64, 512], nu in {1/2, 3/2}, ell in [0.02, 0.3]; seeded):
+    filter steps/s summed over the batch, stepped one at a time vs fkf_filter_step_batched
+    (merged H-apply launches)."""
+    import torch
+
+    import synth
+    from paper_1405_2276_gb300 import fkf
+
+    rng = np.random.default_rng(synth.BASE_SEED + 77)
+    specs = []
+    for i in range(nb):
+        n_target = int(np.exp(rng.uniform(np.log(16384), np.log(131072))))
+        g = max(16, int(round(np.sqrt(n_target))))
+        ns, nr = int(rng.integers(8, 24)), int(rng.integers(8, 24))
+        specs.append(((g, g), ns, nr, float(rng.choice([0.5, 1.5])), float(rng.uniform(0.02, 0.3))))
+    sets = []
+    for rep in range(2):
+        objs = []
+        for i, (grid, ns, nr, nu, ell) in enumerate(specs):
+            wl = synth.tomography_workload(grid, ns, nr, warmup + steps, ell, 1.0, 1e-4,
+                                           seed=synth.BASE_SEED + 5000 + i)
+            ctx = fkf.fkf_create(0)
+            hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32,
+                                       precision=fkf.FKF_FP32)
+            m = wl["H"].nrows
+            objs.append(dict(wl=wl, ctx=ctx, hm=hm, f=fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)))
+        sets.append(objs)
+
+    def entries(objs, k):
+        return [(o["f"], o["wl"]["y"][k], o["wl"]["H"].rowptr, o["wl"]["H"].col, o["wl"]["H"].val, None, 1e-4)
+                for o in objs]
+
+    seq, bat = sets
+    for k in range(warmup):
+        for o in seq:
+            h = o["wl"]["H"]
+            fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
+        fkf.fkf_filter_step_batched(entries(bat, k))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(warmup, warmup + steps):
+        for o in seq:
+            h = o["wl"]["H"]
+            fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
+    torch.cuda.synchronize()
+    t_seq = time.time() - t0
+    merged = []
+    t0 = time.time()
+    for k in range(warmup, warmup + steps):
+        _, merged = fkf.fkf_filter_step_batched(entries(bat, k), return_merged=True)
+    torch.cuda.synchronize()
+    t_bat = time.time() - t0
+    out = dict(filters=nb, steps=steps, n=[s[0][0] * s[0][1] for s in specs], m=[s[1] * s[2] for s in specs],
+               sequential_steps_per_s=nb * steps / t_seq, batched_steps_per_s=nb * steps / t_bat,
+               merged=all(merged), timing="host wall clock around the steps (each step synchronises its stream)")
+    for objs in sets:
+        for o in objs:
+            fkf.fkf_filter_destroy(o["f"])
+            fkf.fkf_hmatrix_destroy(o["hm"])
+            fkf.fkf_destroy(o["ctx"])
+    return out
+
+
 def cpu_oracle_baseline(wl, sample_rows=2048, steps=3):
     """The oracle as it stands (O2: exact cross-covariance Kalman recursion for a
     fixed H, FP64 NumPy) on a bounded sample of the workload: all m x m work
@@ -395,6 +460,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
                     help="medium = 256x256, m=400: for profiler captures only")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time a batch of this many uneven FP32 filters (sequential vs merged batched steps)")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload == "medium":
@@ -423,6 +490,9 @@ def main():
         return
 
     res, wl = run_gpu(args, rank, world)
+    if args.batch > 0 and rank == 0:
+        res["batch"] = batch_bench(args.batch, steps=5, warmup=3)
+        log(f"[bench] batch of {args.batch} uneven FP32 filters: {res['batch']}")
     if world > 1:
         import torch.distributed as dist
 
@@ -514,6 +584,7 @@ def main():
         "e2e": {k: res["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
         "gpu_launches": fp32["launches"], "library_calls": fp32["lib_calls"],
         "clocks": fp32["clocks"],
+        "batch": res.get("batch"),
     }
     print(json.dumps(line), flush=True)
 

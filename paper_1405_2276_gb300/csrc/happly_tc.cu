@@ -886,14 +886,15 @@ __global__ void k_phase1_reduce_tc(const P1Reduce* __restrict__ items, const flo
 
 fkf_status build_stream(fkf_hmat* h, int F);
 
-// Buffers of an apply of up to one panel of columns per pass (allocated or
-// grown on first use; the slot workspace is cleared when its format changes).
+// Buffers of an apply whose passes have up to nc columns (allocated or grown
+// on first use; the slot workspace is cleared when it grows or its format
+// changes).
 template <int F>
-fkf_status tc_buffers(fkf_hmat* h, cudaStream_t st) {
+fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
   using G = Geo<F>;
   fkf_ctx* ctx = h->ctx;
   const int64_t P = h->tc_panel;
-  const int64_t nct_max = cdiv(P, kN);
+  const int64_t nct_max = cdiv(std::min(nc, P), kN);
   const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * G::kBChunk;
   if (h->xsplit.bytes < xbytes) FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
   const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * G::kBChunk;
@@ -969,7 +970,7 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
   fkf_ctx* ctx = h->ctx;
   cudaStream_t st = ctx->stream;
   const int64_t P = h->tc_panel;
-  FKF_TRY(tc_buffers<F>(h, st));
+  FKF_TRY(tc_buffers<F>(h, ncols, st));
   // tile counters of the two phases at tc_err + 16, + 24 bytes
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
   int sms = 0;
@@ -1019,7 +1020,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     fkf_hmat* h = hs[f];
     if (ncols[f] <= 0) continue;
     if (h->tca_fmt != F) FKF_TRY(build_stream(h, F));
-    FKF_TRY(tc_buffers<F>(h, st));
+    FKF_TRY(tc_buffers<F>(h, ncols[f], st));
     const int nc = (int)ncols[f];
     const int nct = (int)cdiv(nc, kN);
     float* cs = nullptr;
