@@ -621,8 +621,10 @@ __device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const JobSet<Ph>
     float* dst = ph.row_dst(w, row, rinv);
     const RowSinkY sink{dst ? dst + n0 : nullptr};
     const float* cinv = ph.cinv ? ph.cinv + n0 : nullptr;
+    // a warp whose 32 rows are all past the tile's rows has nothing to store
+    const int jend = __any_sync(0xffffffffu, dst != nullptr) ? 4 * half + 4 : 4 * half;
 #pragma unroll 1
-    for (int j = 4 * half; j < 4 * half + 4; j++) {
+    for (int j = 4 * half; j < jend; j++) {
       float v[32];
       if (zero) {
 #pragma unroll
@@ -684,8 +686,11 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
         gk[q] = (int)(p & 12);
       }
     }
+    // slot tiles are often shorter than 128: warps whose rows are all past the
+    // item's slots skip the accumulator loads and stores
+    const int jend = 32 * quarter < it.nq ? 4 * half + 4 : 4 * half;
 #pragma unroll 1
-    for (int j = 4 * half; j < 4 * half + 4; j++) {
+    for (int j = 4 * half; j < jend; j++) {
       float v[32];
       if (zero) {
 #pragma unroll
