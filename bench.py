@@ -261,6 +261,35 @@ def run_gpu(args, rank, world):
     log(f"[bench] FP32 path, merge forced: {ms_fu:.1f} ms/step; phases(ms) "
         + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]) + f"; {fu_stats}")
 
+    # time-varying geometry: m new random rays every step (the general step with new
+    # directions: GEP, orthonormalisation, merge with truncation at r_max, rotation)
+    import synth
+
+    vr_rng = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 31))
+    vr_steps = 3
+    gx, gy = w["grid"]
+    ops = synth.varying_ray_operators(vr_rng, gx, gy, [m] * (vr_steps + 1))
+    truth = wl["truth"]
+    vys = [synth.measurements(vr_rng, ops[k], truth[min(k, truth.shape[0] - 1)], w["noise"])
+           for k in range(vr_steps + 1)]
+    fkf.fkf_filter_step(f32, vys[0], m, ops[0].rowptr, ops[0].col, ops[0].val, None, w["noise"])
+    vr_stats = []
+    torch.cuda.synchronize()
+    t0 = time.time()
+    vr_phases = np.zeros(6)
+    for k in range(1, vr_steps + 1):
+        fkf.fkf_filter_step(f32, vys[k], m, ops[k].rowptr, ops[k].col, ops[k].val, None, w["noise"])
+        vr_phases += np.array(fkf.fkf_filter_phase_times(f32))
+        st = fkf.fkf_filter_get_stats(f32)
+        vr_stats.append({k2: st[k2] for k2 in ("r", "last_path", "gep_rank", "new_dirs", "t_eig")})
+    torch.cuda.synchronize()
+    ms_vr = (time.time() - t0) * 1e3 / vr_steps
+    res["fp32_varying"] = dict(ms_per_step=ms_vr, steps_per_s=1e3 / ms_vr, steps=vr_steps,
+                               phases_ms=(vr_phases / vr_steps).tolist(), step_stats=vr_stats,
+                               note="host inputs, a new random ray set each step; host wall clock")
+    log(f"[bench] FP32 path, new rays every step: {ms_vr:.1f} ms/step; phases(ms) "
+        + " ".join(f"{p:.1f}" for p in res["fp32_varying"]["phases_ms"]) + f"; {vr_stats}")
+
     # ---------------- H-apply alone (the dominant kernel), m = 1024 columns ----------------
     def time_apply(hm, info, prec, reps):
         dt = torch.float32 if prec == fkf.FKF_FP32 else torch.float64
@@ -568,6 +597,8 @@ def main():
                                    "steps": res["fp32_fixed_h"]["steps"],
                                    "note": "opt-in FKF_STEP_ALLOW_FIXED_H: H_k, R_k unchanged, products with "
                                            "Gamma reused; not the headline"},
+        "fp32_varying_geometry": {k: res["fp32_varying"][k] for k in ("steps_per_s", "ms_per_step", "steps",
+                                                                         "phases_ms", "note")},
         "fp32_merge_forced": {"steps_per_s": res["fp32_full"]["steps_per_s"],
                               "ms_per_step": res["fp32_full"]["ms_per_step"], "steps": res["fp32_full"]["steps"],
                               "phases_ms": res["fp32_full"]["phases_ms"]},

@@ -277,10 +277,9 @@ typedef struct {
   /* last merge step (last_path 0): */
   int32_t gep_rank;   /* data-space GEP eigenvalues kept (above gep_tol * max) */
   int32_t new_dirs;   /* new Gamma^-1-orthonormal directions merged (T eigenvalues above orth_tol) */
-  int32_t t_eig;      /* 1 if T = I - P^T P was eigendecomposed; 0 if a bound showed
-                         every eigenvalue below orth_tol (Frobenius norm, or a power
-                         iteration estimate below orth_tol / 2) */
-  double t_lmax;      /* largest eigenvalue of T found (or its bound / estimate) */
+  int32_t t_eig;      /* 1 if T = I - P^T P was factored (pivoted Cholesky, pivots above
+                         orth_tol); 0 if ||T||_F <= orth_tol showed nothing new */
+  double t_lmax;      /* ||T||_F, a bound on every eigenvalue of T */
 } fkf_filter_stats;
 fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);
 

@@ -118,7 +118,111 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_next_column(double* __restri
   if (lane < nc) C[r * ldc + lane] -= acc;
 }
 
+// One panel of a pivoted (rank-revealing) Cholesky factorisation, one CTA:
+// up to maxc pivots, each the index with the largest remaining diagonal
+// among those not yet pivoted; stops when that diagonal is <= tol.  A
+// (symmetric, lower triangle valid) already carries the updates of the
+// previous panels; column k0 + j of Lp (n x ., ld ldl) becomes
+// (A(:, p) - sum_{jj < j} Lp(:, k0 + jj) Lp(p, k0 + jj)) / sqrt(d_p), zero on
+// rows pivoted earlier; diag and pivoted are updated; *count = columns made.
+constexpr int kPcholThreads = 1024;
+__global__ void __launch_bounds__(kPcholThreads) k_pchol_panel(int n, const double* __restrict__ A, int64_t lda,
+                                                               double* __restrict__ diag, int* __restrict__ pivoted,
+                                                               double* __restrict__ Lp, int64_t ldl, int k0, int maxc,
+                                                               double tol, int* __restrict__ count) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ double prow[kB];  // Lp(p, k0 .. k0 + j - 1) of the current pivot
+  __shared__ int sp;
+  __shared__ double sd;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int j = 0;
+  for (; j < maxc; j++) {
+    // argmax of the remaining diagonal (ties: smallest index)
+    double v = -1.0;
+    int vi = n;
+    for (int i = t; i < n; i += kPcholThreads)
+      if (!pivoted[i] && diag[i] > v) v = diag[i], vi = i;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+      if (ov > v || (ov == v && oi < vi)) v = ov, vi = oi;
+    }
+    if (lane == 0) bv[warp] = v, bi[warp] = vi;
+    __syncthreads();
+    if (t == 0) {
+      double b = -1.0;
+      int p = n;
+      for (int w = 0; w < kPcholThreads / 32; w++)
+        if (bv[w] > b || (bv[w] == b && bi[w] < p)) b = bv[w], p = bi[w];
+      sp = p;
+      sd = b;
+    }
+    __syncthreads();
+    const int p = sp;
+    const double dp = sd;
+    if (!(dp > tol) || p >= n) break;
+    if (t < j) prow[t] = Lp[(int64_t)p * ldl + k0 + t];
+    __syncthreads();
+    const double rp = sqrt(dp);
+    for (int i = t; i < n; i += kPcholThreads) {
+      double l = 0.0;
+      if (i == p) {
+        l = rp;
+      } else if (!pivoted[i]) {
+        double c = A[(int64_t)max(i, p) * lda + min(i, p)];
+        for (int jj = 0; jj < j; jj++) c -= Lp[(int64_t)i * ldl + k0 + jj] * prow[jj];
+        l = c / rp;
+        diag[i] -= l * l;
+      }
+      Lp[(int64_t)i * ldl + k0 + j] = l;
+    }
+    __syncthreads();
+    if (t == 0) {
+      pivoted[p] = 1;
+      diag[p] = 0.0;
+    }
+    __syncthreads();
+  }
+  if (t == 0) *count = j;
+}
+
+__global__ void k_diag_of(int n, const double* __restrict__ A, int64_t lda, double* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = A[(int64_t)i * lda + i];
+}
+
 }  // namespace
+
+fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, int max_rank, double* Lp, int64_t ldl,
+                     DevBuf& ws, int* rank_out) {
+  *rank_out = 0;
+  if (n <= 0 || max_rank <= 0) return FKF_OK;
+  const size_t need = (size_t)n * (sizeof(double) + sizeof(int)) + 256;
+  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
+  double* diag = ws.as<double>();
+  int* pivoted = reinterpret_cast<int*>(diag + n);
+  int* count = reinterpret_cast<int*>(ws.as<char>() + need - 64);
+  cudaStream_t st = ctx->stream;
+  k_diag_of<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, A, lda, diag);
+  FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaMemsetAsync(pivoted, 0, (size_t)n * sizeof(int), st));
+  int rank = 0;
+  while (rank < max_rank) {
+    const int maxc = std::min(kB, max_rank - rank);
+    k_pchol_panel<<<1, kPcholThreads, 0, st>>>(n, A, lda, diag, pivoted, Lp, ldl, rank, maxc, tol, count);
+    FKF_LAUNCHED(ctx);
+    int c = 0;
+    FKF_CUDA(ctx, cudaMemcpyAsync(&c, count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (c > 0)  // the rest of the matrix loses this panel's contribution
+      FKF_TRY(gemm_sym_f64(ctx, false, true, n, c, -1.0, Lp + rank, ldl, Lp + rank, ldl, 1.0, A, lda, true));
+    rank += c;
+    if (c < maxc) break;
+  }
+  *rank_out = rank;
+  return FKF_OK;
+}
 
 // With look-ahead (several blocks): the critical chain -- diagonal block k,
 // its panel, and the update of the next block column k+1 by panel k -- runs

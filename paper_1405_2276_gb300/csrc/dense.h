@@ -31,6 +31,14 @@ fkf_status scale_f32(fkf_ctx* ctx, int64_t M, int64_t N, float beta, float* C, i
 // the Schur complement A22 - L21 L21^T (both triangles); the upper triangle of
 // the factored part is overwritten with scratch.  nf = n is the full
 // factorisation.  Synchronises once; FKF_ENOTSPD if a pivot is not positive.
+// Pivoted (rank-revealing) Cholesky of a symmetric positive semidefinite
+// n x n matrix A (row-major, lower triangle read; A is overwritten by the
+// updates): A ~= Lp Lp^T with Lp = Pi L (L lower triangular in pivot order),
+// pivots the largest remaining diagonal, stopping when it is <= tol or after
+// max_rank pivots.  Lp: n x rank (ld ldl >= max_rank), row i of column k zero
+// when i was pivoted before k.  Synchronises once per 32 pivots.
+fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, int max_rank, double* Lp, int64_t ldl,
+                     DevBuf& ws, int* rank_out);
 fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws);
 // Solve S x = b (nrhs contiguous vectors of length n) with the factor of
 // chol_blocked_f64 (ld ldl).

@@ -15,7 +15,10 @@
 //     H^T R^-1 H (Eq. geneigendecomposition restricted to its range).
 //   Gamma^-1-orthonormalisation against W (Alg. lowrankaddition steps 1-2),
 //     with W^T Gamma^-1 U = HW^T C =: P and the Gram of U - W P equal to
-//     T = I - P^T P (no N-scale Gram needed); T = Q_T Theta Q_T^T.
+//     T = I - P^T P (no N-scale Gram needed); a rank-revealing pivoted
+//     Cholesky T ~= Lp Lp^T gives the new directions (U - W P) Y,
+//     Y = Lp (Lp^T Lp)^-1 (written Q_T Theta^-1/2 below, Lp^T as Theta^1/2 Q_T^T:
+//     what an eigendecomposition T = Q_T Theta Q_T^T would give).
 //   Merge (step 3-4): M = diag(Dbar, 0) + [P; Theta^1/2 Q_T^T] Lam [...]^T,
 //     Dbar = D / (alpha' (alpha' - D))  (the sign-consistent form of the SMW
 //     expansion of Sigma_pred^-1, as in Alg. extkalman); M = S Dhat S^T,
@@ -552,13 +555,7 @@ __global__ void k_frob_final(const double* __restrict__ part, double* __restrict
   }
 }
 
-__global__ void k_fill_start(int n, double* __restrict__ v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // a fixed start vector with no special structure: 1 + (i mod 7) / 7, alternating sign
-  if (i < n) v[i] = (i & 1 ? -1.0 : 1.0) * (1.0 + (i % 7) / 7.0);
-}
 
-// out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
 // Partial sums of ((A - C)_ij rs_i rs_j)^2 over m x m arrays, A in FP64 and C in FP32.
 __global__ void k_frob_diff_part(int64_t n, const double* __restrict__ A, const float* __restrict__ C,
                                  const double* __restrict__ rs, int m, double* __restrict__ part) {
@@ -591,6 +588,7 @@ __global__ void k_hw_f32(int m, int r, const double* __restrict__ HW, int64_t ld
   hwt[(int64_t)j * m + i] = v;
 }
 
+// out[0] = ||A||_F (n entries; scaled by rs[i] rs[j] as an m x m matrix when rs is given)
 static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* rs, int m, double* part,
                        double* out) {
   k_frob_part<<<kFrobBlocks, 256, 0, ctx->stream>>>(n, A, rs, m, part);
@@ -600,34 +598,6 @@ static fkf_status frob(fkf_ctx* ctx, int64_t n, const double* A, const double* r
   return FKF_OK;
 }
 
-// v = w / nrm[0] (n entries)
-__global__ void k_scale_by(int n, const double* __restrict__ w, const double* __restrict__ nrm,
-                           double* __restrict__ v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double d = nrm[0];
-  if (i < n) v[i] = d > 0 ? w[i] / d : 0.0;
-}
-
-// Largest |eigenvalue| of a symmetric n x n matrix A by `iters` steps of power
-// iteration from a fixed start (an estimate from below); ws: 2n + 8 doubles,
-// part: the Frobenius partials buffer.  Synchronises once.
-static fkf_status power_lmax(fkf_ctx* ctx, int n, const double* A, double* ws, double* part, int iters,
-                             double* out) {
-  double* v = ws;
-  double* w = ws + n;
-  double* nrm = ws + 2 * n;
-  k_fill_start<<<(int)cdiv(n, 256), 256, 0, ctx->stream>>>(n, v);
-  FKF_LAUNCHED(ctx);
-  for (int it = 0; it < iters; it++) {
-    FKF_TRY(gemm_f64(ctx, false, false, n, 1, n, 1.0, A, n, v, 1, 0.0, w, 1));
-    FKF_TRY(frob(ctx, n, w, nullptr, n, part, nrm));
-    k_scale_by<<<(int)cdiv(n, 256), 256, 0, ctx->stream>>>(n, w, nrm, v);
-    FKF_LAUNCHED(ctx);
-  }
-  FKF_CUDA(ctx, cudaMemcpyAsync(out, nrm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return FKF_OK;
-}
 
 
 // A = (A + A^T) / 2 in place (n x n)
@@ -774,7 +744,8 @@ struct fkf_filter {
   DevBuf cnt, cursor, colptr, crow, cval;
   // small FP64 buffers
   DevBuf HWA, As, At, S, a, C, lam, P, Tm, th, Po, F1t, ZL, M, thM, Sk, J, E, Ecast;
-  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws, vm;
+  DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws;
+  DevBuf Lpv, Gm, F1c, pcws;  // pivoted Cholesky of T: factor, its Gram, the solved factor, workspace
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
   TcGemmWs rot;       // tensor-core products (FP32 state): the rotation and the basis test
   DevBuf hw32, c32;   // basis test of the FP32 state: HW and HW^T in FP32, HW HW^T
@@ -811,7 +782,9 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
   FKF_TRY(A(f->HWD, m * r));
   FKF_TRY(A(f->nll, 4));
-  FKF_TRY(A(f->vm, 2 * m + 8));
+  FKF_TRY(A(f->Lpv, m * m));
+  FKF_TRY(A(f->Gm, m * m));
+  FKF_TRY(A(f->F1c, m * m));
   FKF_TRY(A(f->red, kFrobBlocks));
   FKF_TRY(A(f->dbar, r));
   FKF_TRY(A(f->y, m));
@@ -1185,7 +1158,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     return FKF_OK;
   }
   // ---- S3: data-space GEP  R^-1/2 A R^-1/2 = Q diag(a) Q^T
-  std::vector<double> a_h, th_h, thM_h;
+  std::vector<double> a_h, thM_h;
   FKF_TRY(eigh_f64(ctx, m, f->At.as<double>(), f->a.as<double>(), a_h, f->eigws));
   const double amax = a_h.empty() ? 0.0 : a_h.back();
   int mlam = 0;
@@ -1209,34 +1182,39 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_TRY(gemm_f64(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
     k_add_identity<<<(int)cdiv(mlam, 256), 256, 0, st>>>(mlam, Tm, mlam, 1.0);
     FKF_LAUNCHED(ctx);
-    // every eigenvalue of T is bounded by ||T||_F; when that is above the
-    // threshold, power iteration estimates the largest eigenvalue (from below:
-    // it must stay under half the threshold) before the eigensolve is paid for
+    // every eigenvalue of T is bounded by ||T||_F: below the threshold there
+    // is nothing new to factor
     FKF_TRY(frob(ctx, (int64_t)mlam * mlam, Tm, nullptr, mlam, f->red.as<double>(), f->nll.as<double>() + 1));
     double tfrob = 0;
     FKF_CUDA(ctx, cudaMemcpyAsync(&tfrob, f->nll.as<double>() + 1, 8, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
     mp = 0;
     t_lmax = tfrob;
-    bool need_eig = tfrob > f->orth_tol;
-    if (need_eig) {
-      FKF_TRY(power_lmax(ctx, mlam, Tm, f->vm.as<double>(), f->red.as<double>(), 40, &t_lmax));
-      need_eig = t_lmax > 0.5 * f->orth_tol;
+    const bool factor_t = tfrob > f->orth_tol;
+    if (factor_t) {
+      // rank-revealing pivoted Cholesky T ~= Lp Lp^T (Lp = Pi L, mlam x mp), pivots above
+      // orth_tol.  With Y = Lp (Lp^T Lp)^-1 the new directions V = (U - W P) Y are
+      // Gamma^-1-orthonormal (Y^T T Y = I) and U - W P = V Lp^T up to the dropped
+      // pivots, so Po = Lp^T and F1 = Y take the places of Theta^1/2 Q_T^T and
+      // Q_T Theta^-1/2 of an eigendecomposition.
+      double* Lp = f->Lpv.as<double>();
+      FKF_TRY(pchol_f64(ctx, mlam, Tm, mlam, f->orth_tol, mlam, Lp, mlam, f->pcws, &mp));
+      if (mp > 0) {
+        k_transpose<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mp, mlam, Lp, mlam, f->Po.as<double>(), mlam);
+        FKF_LAUNCHED(ctx);
+        double* Gm = f->Gm.as<double>();
+        double* F1 = f->F1c.as<double>();  // mlam x mp
+        FKF_TRY(gemm_f64(ctx, true, false, mp, mp, mlam, 1.0, Lp, mlam, Lp, mlam, 0.0, Gm, mp));
+        FKF_CUDA(ctx, cudaMemcpy2DAsync(F1, (size_t)mp * 8, Lp, (size_t)mlam * 8, (size_t)mp * 8, mlam,
+                                        cudaMemcpyDeviceToDevice, st));
+        FKF_TRY(chol_f64(ctx, mp, Gm, f->cholws));
+        // column-major, F1 is the mp x mlam right-hand side Lp^T: F1 <- Lp (Lp^T Lp)^-1
+        FKF_TRY(chol_solve_f64(ctx, mp, Gm, F1, mlam));
+        k_transpose<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mp, mlam, F1, mp, f->F1t.as<double>(), mlam);
+        FKF_LAUNCHED(ctx);
+      }
     }
-    if (need_eig) {
-      FKF_TRY(eigh_f64(ctx, mlam, Tm, f->th.as<double>(), th_h, f->eigws));
-      t_lmax = th_h.empty() ? 0.0 : th_h.back();
-      for (int i = mlam - 1; i >= 0; i--)
-        if (th_h[i] > f->orth_tol) mp++;
-        else break;
-    }
-    t_eig = need_eig ? 1 : 0;
-    if (mp > 0) {
-      k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 0, f->Po.as<double>(), mlam);
-      FKF_LAUNCHED(ctx);
-      k_top_rows<<<nblk((int64_t)mp * mlam), 256, 0, st>>>(mlam, mp, Tm, f->th.as<double>(), 1, f->F1t.as<double>(), mlam);
-      FKF_LAUNCHED(ctx);
-    }
+    t_eig = factor_t ? 1 : 0;
   } else if (mlam > 0) {
     k_identity<<<nblk((int64_t)mlam * mlam), 256, 0, st>>>(mlam, f->Po.as<double>(), mlam);
     FKF_LAUNCHED(ctx);
