@@ -48,6 +48,11 @@ fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t
 // by Vt, whose row j is the unit eigenvector of eigenvalue w[j]; eigenvalues
 // ascending.  The eigenvalues are also copied to w_host (synchronises).
 fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws);
+// The k largest eigenpairs of a symmetric n x n A (cuSOLVER syevdx, range by
+// index; all of them through eigh_f64 when k >= n): on return *meig pairs,
+// eigenvalues ascending in w, eigenvector i in row i of A (row-major view).
+fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
+                        int* meig);
 // Cholesky factorisation of an SPD n x n matrix in place; returns
 // FKF_ENOTSPD when a pivot is not positive (synchronises to read the status).
 fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws);

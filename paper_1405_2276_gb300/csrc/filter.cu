@@ -408,11 +408,13 @@ __global__ void k_build_C(int m, int mlam, const double* __restrict__ Vt, const 
 
 // out[p, :] = Vt[n-1-p, :] * f(w[n-1-p]) for p < cnt; mode 0: sqrt(w), 1: 1/sqrt(w), 2: 1
 __global__ void k_top_rows(int n, int cnt, const double* __restrict__ Vt, const double* __restrict__ w, int mode,
-                           double* __restrict__ out, int64_t ldo) {
+                           double* __restrict__ out, int64_t ldo, int nv = -1) {
+  // nv: eigenpairs held (rows of Vt, entries of w), the largest last; all n by default
+  const int top = (nv < 0 ? n : nv) - 1;
   const int64_t total = (int64_t)cnt * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / n), j = (int)(e % n);
-    const int src = n - 1 - p;
+    const int src = top - p;
     const double f = mode == 0 ? sqrt(w[src]) : (mode == 1 ? 1.0 / sqrt(w[src]) : 1.0);
     out[(int64_t)p * ldo + j] = Vt[(int64_t)src * n + j] * f;
   }
@@ -1224,7 +1226,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   // ---- S5: merge  M = diag(Dbar, 0) + Z Lam Z^T, Z = [P; Po]
   const int nM = r + mp;
   double* M = f->M.as<double>();
-  int rnew = 0;
+  int rnew = 0, meig = 0;
   if (nM > 0) {
     if (mlam > 0) {
       k_stack_scale<<<nblk((int64_t)nM * mlam), 256, 0, st>>>(r, mp, mlam, P, f->Po.as<double>(), f->lam.as<double>(),
@@ -1248,19 +1250,21 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       k_add_block<<<nblk(rr), 256, 0, st>>>(r, f->Qm.as<double>(), -1.0 / alpha1, M, nM);
       FKF_LAUNCHED(ctx);
     }
-    FKF_TRY(eigh_f64(ctx, nM, M, f->thM.as<double>(), thM_h, f->eigws));
-    const double tmax = thM_h.back();
-    for (int i = nM - 1; i >= 0 && rnew < rmax; i--)
+    // only the r_max largest eigenpairs can be kept
+    FKF_TRY(eigh_top_f64(ctx, nM, rmax, M, f->thM.as<double>(), thM_h, f->eigws, &meig));
+    const double tmax = thM_h.empty() ? 0.0 : thM_h.back();
+    for (int i = meig - 1; i >= 0 && rnew < rmax; i--)
       if (tmax > 0 && thM_h[i] > f->trunc_tol * tmax && thM_h[i] > 0) rnew++;
       else break;
   }
   double* Dn = f->Dn.as<double>();
   double* E = f->E.as<double>();
   if (rnew > 0) {
-    k_new_D<<<(int)cdiv(rnew, 256), 256, 0, st>>>(nM, rnew, f->thM.as<double>(), alpha1, Dn);
+    k_new_D<<<(int)cdiv(rnew, 256), 256, 0, st>>>(meig, rnew, f->thM.as<double>(), alpha1, Dn);
     FKF_LAUNCHED(ctx);
     // Sk (rnew x nM): rows = kept eigenvectors of M (descending)
-    k_top_rows<<<nblk((int64_t)rnew * nM), 256, 0, st>>>(nM, rnew, M, f->thM.as<double>(), 2, f->Sk.as<double>(), nM);
+    k_top_rows<<<nblk((int64_t)rnew * nM), 256, 0, st>>>(nM, rnew, M, f->thM.as<double>(), 2, f->Sk.as<double>(), nM,
+                                                        meig);
     FKF_LAUNCHED(ctx);
     double* EW = E;                       // r x rnew
     double* EG = E + (int64_t)r * rnew;   // m x rnew

@@ -46,6 +46,41 @@ fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   return FKF_OK;
 }
 
+fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
+                        int* meig_out) {
+  *meig_out = 0;
+  w_host.clear();
+  if (n == 0 || k <= 0) return FKF_OK;
+  if (k >= n) {
+    FKF_TRY(eigh_f64(ctx, n, A, w_dev, w_host, ws));
+    *meig_out = n;
+    return FKF_OK;
+  }
+  cusolverDnHandle_t h;
+  FKF_TRY(solver(ctx, &h));
+  int lwork = 0, meig = 0;
+  const int il = n - k + 1, iu = n;
+  if (cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n, A, n,
+                                   0.0, 0.0, il, iu, &meig, w_dev, &lwork) != CUSOLVER_STATUS_SUCCESS)
+    return set_err(ctx, FKF_ECUDA, "syevdx_bufferSize failed (n=%d)", n);
+  const size_t need = (size_t)lwork * sizeof(double) + 256;
+  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
+  int* info = reinterpret_cast<int*>(ws.as<char>() + (size_t)lwork * sizeof(double));
+  if (cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0,
+                        il, iu, &meig, w_dev, ws.as<double>(), lwork, info) != CUSOLVER_STATUS_SUCCESS)
+    return set_err(ctx, FKF_ECUDA, "syevdx failed (n=%d)", n);
+  ctx->lib_calls++;
+  int hinfo = 0;
+  w_host.assign(std::max(meig, 0), 0.0);
+  FKF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (meig > 0)
+    FKF_CUDA(ctx, cudaMemcpyAsync(w_host.data(), w_dev, meig * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0) return set_err(ctx, FKF_ENOCONV, "symmetric eigensolver did not converge (n=%d, info=%d)", n, hinfo);
+  *meig_out = meig;
+  return FKF_OK;
+}
+
 fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws) {
   if (n == 0) return FKF_OK;
   cusolverDnHandle_t h;
