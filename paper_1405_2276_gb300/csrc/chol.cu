@@ -4,9 +4,10 @@
 //
 // FP64 throughput on this part is a small fraction of FP32's and a warp-wide
 // FP64 instruction holds its sub-partition for many clocks, so the design
-// keeps the sequential part short and spreads everything else over the SMs: blocks of 32; a 32 x 32 diagonal block is factored by one CTA
-// (32 rank-1 steps in shared memory); the panel below it is solved row by row
-// (one warp per row, the factor block in shared memory, 8 rows per CTA);
+// keeps the sequential part short and spreads everything else over the SMs:
+// blocks of kB; a diagonal block is factored by one CTA (kB rank-1 steps in
+// shared memory); the panel below it is solved row by row (one warp per row,
+// kB / 32 columns per lane, the factor block in shared memory, 8 rows per CTA);
 // the trailing matrix is updated by the symmetric FP64 tile GEMM (lower tiles
 // only).  Stopping after the first nf pivots of a bordered matrix
 // [[S, K], [K^T, E]] leaves the Schur complement E - K^T S^-1 K in the
@@ -18,9 +19,15 @@
 #include "common.h"
 #include "dense.h"
 
+#ifndef FKF_CHOL_BLOCK
+#define FKF_CHOL_BLOCK 32
+#endif
+
 namespace {
 
-constexpr int kB = 32;  // block size
+constexpr int kB = FKF_CHOL_BLOCK;  // block size (a multiple of 32, at most 64)
+constexpr int kV = kB / 32;         // columns per lane in the row kernels
+constexpr int kPB = 32;             // pivots per panel of the pivoted Cholesky
 
 // Factor the b x b diagonal block A (ld lda, lower triangle) in place.  A
 // pivot that is not positive sets *flag and is replaced by 1 so that the
@@ -62,9 +69,9 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
 
 // X[r, 0:b] <- X[r, 0:b] Lkk^-T for rows r < rows (forward substitution per
 // row: x_j = (x_j - sum_{l<j} x_l Lkk[j][l]) / Lkk[j][j]); Lkk is the b x b
-// lower factor block at L (ld lda).  One warp per row, lane j holding x_j:
-// after x_q is final it is broadcast and every later lane subtracts its term,
-// so a row costs b dependent steps of one FMA per lane (FP64 instructions are
+// lower factor block at L (ld lda).  One warp per row, lane j holding x_j,
+// x_{j+32}, ...: after x_q is final it is broadcast and every later column
+// subtracts its term, so a row costs b dependent steps (FP64 instructions are
 // slow per warp here; many short rows in flight use all the SMs).
 constexpr int kRowWarps = 8;
 __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict__ X, int64_t ldx, int64_t rows,
@@ -83,21 +90,30 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
   const int64_t r = (int64_t)blockIdx.x * kRowWarps + (t >> 5);
   if (r >= rows) return;
   double* xr = X + r * ldx;
-  double s = lane < b ? xr[lane] : 0.0;
+  double s[kV];
+#pragma unroll
+  for (int v = 0; v < kV; v++) s[v] = 32 * v + lane < b ? xr[32 * v + lane] : 0.0;
 #pragma unroll
   for (int q = 0; q < kB; q++) {
     if (q >= b) break;
-    const double xq = __shfl_sync(0xffffffffu, s * dinv[q], q);
-    if (lane == q) s = xq;
-    if (lane > q) s -= xq * l[lane][q];
+    const int qv = q >> 5, ql = q & 31;
+    const double xq = __shfl_sync(0xffffffffu, s[qv] * dinv[q], ql);
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      const int c = 32 * v + lane;
+      if (c == q) s[v] = xq;
+      if (c > q) s[v] -= xq * l[c][q];
+    }
   }
-  if (lane < b) xr[lane] = s;
+#pragma unroll
+  for (int v = 0; v < kV; v++)
+    if (32 * v + lane < b) xr[32 * v + lane] = s[v];
 }
 
 // C[r, 0:nc] -= P[r, 0:b] Q^T for rows r < rows, with Q = P[0:nc, 0:b] (the
 // rows of the next diagonal block): the update of the next block column by
-// the current panel.  One warp per row, lane j accumulating column j; Q in
-// shared memory, P's row broadcast by shuffles.
+// the current panel.  One warp per row, lane j accumulating columns j,
+// j + 32, ...; Q in shared memory, P's row broadcast by shuffles.
 __global__ void __launch_bounds__(32 * kRowWarps) k_next_column(double* __restrict__ C, int64_t ldc, int64_t rows,
                                                                 int nc, const double* __restrict__ P, int64_t ldp,
                                                                 int b) {
@@ -111,11 +127,21 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_next_column(double* __restri
   const int lane = t & 31;
   const int64_t r = (int64_t)blockIdx.x * kRowWarps + (t >> 5);
   if (r >= rows) return;
-  const double pl = lane < b ? P[r * ldp + lane] : 0.0;
-  double acc = 0.0;
+  double pl[kV], acc[kV];
 #pragma unroll
-  for (int l = 0; l < kB; l++) acc += __shfl_sync(0xffffffffu, pl, l) * q[lane][l];
-  if (lane < nc) C[r * ldc + lane] -= acc;
+  for (int v = 0; v < kV; v++) {
+    pl[v] = 32 * v + lane < b ? P[r * ldp + 32 * v + lane] : 0.0;
+    acc[v] = 0.0;
+  }
+#pragma unroll
+  for (int l = 0; l < kB; l++) {
+    const double p = __shfl_sync(0xffffffffu, pl[l >> 5], l & 31);
+#pragma unroll
+    for (int v = 0; v < kV; v++) acc[v] += p * q[32 * v + lane][l];
+  }
+#pragma unroll
+  for (int v = 0; v < kV; v++)
+    if (32 * v + lane < nc) C[r * ldc + 32 * v + lane] -= acc[v];
 }
 
 // One panel of a pivoted (rank-revealing) Cholesky factorisation, one CTA:
@@ -132,7 +158,7 @@ __global__ void __launch_bounds__(kPcholThreads) k_pchol_panel(int n, const doub
                                                                double tol, int* __restrict__ count) {
   __shared__ double bv[32];
   __shared__ int bi[32];
-  __shared__ double prow[kB];  // Lp(p, k0 .. k0 + j - 1) of the current pivot
+  __shared__ double prow[kPB];  // Lp(p, k0 .. k0 + j - 1) of the current pivot
   __shared__ int sp;
   __shared__ double sd;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -209,7 +235,7 @@ fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, in
   FKF_CUDA(ctx, cudaMemsetAsync(pivoted, 0, (size_t)n * sizeof(int), st));
   int rank = 0;
   while (rank < max_rank) {
-    const int maxc = std::min(kB, max_rank - rank);
+    const int maxc = std::min(kPB, max_rank - rank);
     k_pchol_panel<<<1, kPcholThreads, 0, st>>>(n, A, lda, diag, pivoted, Lp, ldl, rank, maxc, tol, count);
     FKF_LAUNCHED(ctx);
     int c = 0;

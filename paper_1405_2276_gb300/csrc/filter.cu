@@ -1233,7 +1233,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
                                                             f->ZL.as<double>());
       FKF_LAUNCHED(ctx);
     }
-    FKF_TRY(gemm_f64(ctx, false, true, nM, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0, M, nM));
+    FKF_TRY(gemm_sym_f64(ctx, false, true, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0, M, nM));
     if (r > 0 && diag) {
       k_add_dbar<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), alpha1, M, nM);
       FKF_LAUNCHED(ctx);
