@@ -173,6 +173,9 @@ def run_gpu(args, rank, world):
 
     # ---------------- FP32 path (the headline) ----------------
     hm32, info32 = build_hmat(fkf.FKF_FP32)
+    # the project's autotuner picks the tensor-core pipeline shape for this operator
+    res["autotune"] = dict(zip(("variant", "ms_per_apply"), fkf.fkf_hmatrix_autotune(hm32, m)))
+    log(f"[bench] autotuned tensor-core pipeline: {res['autotune']}")
     f32 = fkf.fkf_filter_create(hm32, None, 0.0, 1e-12, m, 2 * m)
     snap32 = None
     cmp_step = min(3, args.warmup)
@@ -616,6 +619,7 @@ def main():
         "gpu_launches": fp32["launches"], "library_calls": fp32["lib_calls"],
         "clocks": fp32["clocks"],
         "batch": res.get("batch"),
+        "autotune": res.get("autotune"),
     }
     print(json.dumps(line), flush=True)
 

@@ -193,6 +193,16 @@ fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t
 fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
 /* Current engine of the H-apply (see fkf_hmatrix_set_engine).  Errors: EINVAL (null). */
 fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine);
+/* Autotuner of the tensor-core pipeline shape (engine 2): times the FP16
+ * kernels with four K-chunks per stage and two stages (variant 0) and with two
+ * chunks per stage and four stages (variant 1) on an apply of ncols columns
+ * (deterministic test vectors, CUDA events on the context stream) and keeps
+ * the faster for this operator; the results do not depend on the shape.
+ * variant (nullable): the shape kept; ms (nullable): its time per apply (0
+ * when the engine is not 2, where nothing is tuned).  Allocates two N x ncols
+ * FP32 buffers for the duration of the call.  Errors: EINVAL, ENOMEM, ECUDA,
+ * ETIMEOUT. */
+fkf_status fkf_hmatrix_autotune(fkf_hmat* h, int64_t ncols, int32_t* variant, double* ms);
 /* Permutation: perm[i] = original index of the i-th point in cluster order. */
 fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host);
 /* Dense copy of Gamma_H (host, N x N row-major, original order); N <= 8192. */

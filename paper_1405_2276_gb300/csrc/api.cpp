@@ -209,6 +209,17 @@ FKF_API fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine) {
   return FKF_OK;
 }
 
+FKF_API fkf_status fkf_hmatrix_autotune(fkf_hmat* h, int64_t ncols, int32_t* variant, double* ms) {
+  if (!h) return FKF_EINVAL;
+  if (ncols < 1) return set_err(h->ctx, FKF_EINVAL, "autotune: ncols >= 1 required");
+  int v = 0;
+  double t = 0.0;
+  FKF_TRY(hmat_autotune(h, ncols, &v, &t));
+  if (variant) *variant = v;
+  if (ms) *ms = t;
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine) {
   if (!h) return FKF_EINVAL;
   if (engine < 0 || engine > 2) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0, 1 or 2");

@@ -235,6 +235,7 @@ struct fkf_hmat {
   int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0, n_tcx = 0, n_tcz = 0;
   int64_t tc_panel = 0;  // columns per tensor-core pass
   int tca_fmt = 0;       // format the split operator stream holds (1, 2)
+  int tc_variant = 0;    // pipeline shape of the FP16 engine (0: 4 chunks x 2 stages, 1: 2 x 4; hmat_autotune)
   int zsplit_fmt = 0;    // format last written to the split slot workspace
   int engine = 0;  // 0: SIMT tile engine; tensor cores (FP32 operators only): 1 = 3xTF32, 2 = scaled 2xFP16
   // workspace
@@ -271,6 +272,9 @@ fkf_status hmat_set_engine(fkf_hmat* h, int engine);
 // is reported through every operator's tensor-core error flag.
 fkf_status hmat_apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float* const* X, const int64_t* ldx,
                                float* const* Y, const int64_t* ldy, const int64_t* ncols);
+// Times the FP16 engine's pipeline shapes on an apply of ncols columns and
+// keeps the faster one for this operator (no-op for other engines).
+fkf_status hmat_autotune(fkf_hmat* h, int64_t ncols, int* variant, double* ms_best);
 // True when hmat_apply_tc_multi can run these operators together.
 bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols);
 // The step's H-apply (S2): through the batch of the calling host thread when

@@ -89,21 +89,29 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 2 * kN;
 constexpr uint32_t kMaxPolls = 1u << 22;
 
-// Geometry of format F's split chunks.
+// Kernel codes F: 1 = 3xTF32; 2 and 3 = the scaled 2xFP16 format with two
+// pipeline shapes (2: four K-chunks per stage, two stages; 3: two chunks per
+// stage, four stages), chosen per operator by hmat_autotune.  fmt_of(F) is
+// the element format (1 or 2) of the split operands.
+__host__ __device__ constexpr int fmt_of(int F) { return F == 1 ? 1 : 2; }
+
+// Geometry of kernel code F's split chunks and pipeline.
 template <int F>
 struct Geo {
-  static constexpr int kEl = F == 1 ? 4 : 2;       // bytes per element
+  static constexpr int kFmt = fmt_of(F);
+  static constexpr int kEl = kFmt == 1 ? 4 : 2;    // bytes per element
   static constexpr int kPer = 16 / kEl;            // elements of one core-matrix row (16 bytes)
-  static constexpr int kMmaK = F == 1 ? 8 : 16;    // K per MMA
+  static constexpr int kMmaK = kFmt == 1 ? 8 : 16; // K per MMA
   static constexpr int kABytes = kM * kK * kEl;    // one half (hi or lo) of an A chunk
   static constexpr int kAChunk = 2 * kABytes;
   static constexpr int kBBytes = kN * kK * kEl;    // one half of a B chunk (256 columns)
   static constexpr int kBChunk = 2 * kBBytes;
-  static constexpr int kCPS = F == 1 ? FKF_TC_TF32_CHUNKS_PER_STAGE : FKF_TC_F16_CHUNKS_PER_STAGE;  // chunks per stage
+  static constexpr int kCPS = F == 1 ? FKF_TC_TF32_CHUNKS_PER_STAGE
+                                     : (F == 2 ? FKF_TC_F16_CHUNKS_PER_STAGE : 2);  // chunks per stage
   static constexpr int kStage = kCPS * (kAChunk + kBChunk);
-  static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : FKF_TC_STAGES_F16;  // pipeline stages
+  static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : (F == 2 ? FKF_TC_STAGES_F16 : 4);  // pipeline stages
   static constexpr uint32_t kSBO = (kK / kPer) * 128;  // next 8-row group
-  static constexpr uint32_t kIdesc = F == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
+  static constexpr uint32_t kIdesc = kFmt == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
   static constexpr int kSmem = kS * kStage + kTail + kEpiBytes;
   // barrier indices
   static constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1,
@@ -167,7 +175,7 @@ __device__ __forceinline__ void split_f16(float x, uint32_t& h, uint32_t& l) {
 template <int F>
 __device__ __forceinline__ void put_unit(uint8_t* hi_base, uint8_t* lo_base, int row, int k, const float* v) {
   uint4 h, l;
-  if constexpr (F == 1) {
+  if constexpr (fmt_of(F) == 1) {
     umma::split_tf32(v[0], h.x, l.x);
     umma::split_tf32(v[1], h.y, l.y);
     umma::split_tf32(v[2], h.z, l.z);
@@ -189,7 +197,7 @@ template <int F>
 __device__ __forceinline__ void put4(uint8_t* hi_base, uint8_t* lo_base, int row, int k, float v0, float v1, float v2,
                                      float v3) {
   const uint32_t off = Geo<F>::off(row, k);
-  if constexpr (F == 1) {
+  if constexpr (fmt_of(F) == 1) {
     uint4 h, l;
     umma::split_tf32(v0, h.x, l.x);
     umma::split_tf32(v1, h.y, l.y);
@@ -213,7 +221,7 @@ template <int F>
 __device__ __forceinline__ void put1(uint8_t* chunk, int n, int k, float v) {
   const uint32_t off = Geo<F>::off(n, k);
   uint32_t h, l;
-  if constexpr (F == 1) {
+  if constexpr (fmt_of(F) == 1) {
     umma::split_tf32(v, h, l);
     *reinterpret_cast<uint32_t*>(chunk + off) = h;
     *reinterpret_cast<uint32_t*>(chunk + Geo<F>::kBBytes + off) = l;
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X,
     const int u = threadIdx.x + 256 * i;
     const int n = u & (kN - 1), kq = u >> 8;
     const int col = ct * kN + n;
-    const float sc = (F == 2 && col < ncols) ? cscale[col] : 1.f;
+    const float sc = (fmt_of(F) == 2 && col < ncols) ? cscale[col] : 1.f;
     float v[G::kPer];
 #pragma unroll
     for (int j = 0; j < G::kPer; j++) {
@@ -522,7 +530,7 @@ __device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, ui
     const uint64_t ah = umma::smem_desc(a_hi + koff, G::kSBO), al = umma::smem_desc(a_lo + koff, G::kSBO);
     const uint64_t bh = umma::smem_desc(b_hi + koff, G::kSBO), bl = umma::smem_desc(b_lo + koff, G::kSBO);
     const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
-    if constexpr (F == 1) {
+    if constexpr (fmt_of(F) == 1) {
       umma::mma_tf32(acc, ah, bh, G::kIdesc, acc0);
       umma::mma_tf32(acc, ah, bl, G::kIdesc, 1u);
       umma::mma_tf32(acc, al, bh, G::kIdesc, 1u);
@@ -710,7 +718,8 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
           for (int q = 0; q < 8; q += 2) {
             // FP16: two groups that fill one 16-byte unit (positions p, p + 4 with p % 8 == 0) go
             // out as one store per half
-            if (F == 2 && gchunk[q] && gchunk[q + 1] == gchunk[q] && gk[q + 1] == gk[q] + 4 && (gk[q] & 7) == 0) {
+            if (fmt_of(F) == 2 && gchunk[q] && gchunk[q + 1] == gchunk[q] && gk[q + 1] == gk[q] + 4 &&
+                (gk[q] & 7) == 0) {
               float v[8];
 #pragma unroll
               for (int i = 0; i < 8; i++) v[i] = tile[(4 * q + i) * kEpiLd + lane];
@@ -855,13 +864,14 @@ __global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const fl
     for (int e = threadIdx.x; e < kM * NU; e += blockDim.x) {
       const int i = e / NU, kq = e % NU;
       float rs = 1.f;
-      if (F == 2 && i >= ch.row_lo && i < ch.row_hi) rs = ch.phase == 1 ? qslot[ch.s_off + i] : rpt[ch.s_off + i];
+      if (fmt_of(F) == 2 && i >= ch.row_lo && i < ch.row_hi)
+        rs = ch.phase == 1 ? qslot[ch.s_off + i] : rpt[ch.s_off + i];
       float v[G::kPer];
 #pragma unroll
       for (int u = 0; u < G::kPer; u++) {
         const int k = G::kPer * kq + u;
         float x = chunk_elem(ch, fac, nearv, i, k);
-        if (F == 2 && x != 0.f) {
+        if (fmt_of(F) == 2 && x != 0.f) {
           x *= rs;
           if (ch.k_off >= 0) x /= qpos[ch.k_off + k];
         }
@@ -903,11 +913,11 @@ fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
   const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * G::kBChunk;
   if (h->xsplit.bytes < xbytes) FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
   const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * G::kBChunk;
-  if (h->zsplit.bytes < zbytes || h->zsplit_fmt != F) {
+  if (h->zsplit.bytes < zbytes || h->zsplit_fmt != fmt_of(F)) {
     // padding slots of the split workspace are never written: they start (and stay) zero
     if (h->zsplit.bytes < zbytes) FKF_TRY(dev_alloc(ctx, h->zsplit, zbytes));
     FKF_CUDA(ctx, cudaMemsetAsync(h->zsplit.p, 0, h->zsplit.bytes, st));
-    h->zsplit_fmt = F;
+    h->zsplit_fmt = fmt_of(F);
   }
   const size_t pbytes = (size_t)std::max<int64_t>(h->tc_part_rows, 1) * P * sizeof(float);
   if (h->part.bytes < pbytes) FKF_TRY(dev_alloc(ctx, h->part, pbytes));
@@ -916,7 +926,7 @@ fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
     FKF_CUDA(ctx, cudaMemsetAsync(h->tc_err.p, 0, 64, st));
   }
   // column maxima and scales of one pass (format 2)
-  if (F == 2 && h->tc_col.bytes < (size_t)P * 12) FKF_TRY(dev_alloc(ctx, h->tc_col, (size_t)P * 12));
+  if (fmt_of(F) == 2 && h->tc_col.bytes < (size_t)P * 12) FKF_TRY(dev_alloc(ctx, h->tc_col, (size_t)P * 12));
   return FKF_OK;
 }
 
@@ -928,7 +938,7 @@ fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaS
   const int64_t P = h->tc_panel;
   const int nct = (int)cdiv(nc, kN);
   cs = nullptr;
-  if (F == 2) {
+  if (fmt_of(F) == 2) {
     unsigned* cmax = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
     cs = h->tc_col.as<float>();
     FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned), st));
@@ -955,7 +965,8 @@ Ph1 tc_ph1(fkf_hmat* h, int nc) {
 template <int F>
 Ph2 tc_ph2(fkf_hmat* h, float* Y, int64_t ldy, int nc, const float* cs) {
   return Ph2{h->tctile.as<TcTile>(), h->tcseg.as<TcSeg>(), h->zsplit.as<uint8_t>(), h->xsplit.as<uint8_t>(),
-             Y, ldy, F == 2 ? h->tc_rpt.as<float>() : nullptr, F == 2 ? cs + nc : nullptr, h->tca.as<uint8_t>(),
+             Y, ldy, fmt_of(F) == 2 ? h->tc_rpt.as<float>() : nullptr, fmt_of(F) == 2 ? cs + nc : nullptr,
+             h->tca.as<uint8_t>(),
              (int)cdiv(nc, kN), nc};
 }
 
@@ -1024,7 +1035,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
   for (int f = 0; f < nb; f++) {
     fkf_hmat* h = hs[f];
     if (ncols[f] <= 0) continue;
-    if (h->tca_fmt != F) FKF_TRY(build_stream(h, F));
+    if (h->tca_fmt != fmt_of(F)) FKF_TRY(build_stream(h, fmt_of(F)));
     FKF_TRY(tc_buffers<F>(h, ncols[f], st));
     const int nc = (int)ncols[f];
     const int nct = (int)cdiv(nc, kN);
@@ -1151,8 +1162,65 @@ fkf_status build_stream(fkf_hmat* h, int F) {
 // Tensor-core apply for an FP32 operator (cluster order).
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {
   if (h->tca_fmt != h->engine) FKF_TRY(build_stream(h, h->engine));
-  if (h->engine == 2) return apply_tc<2>(h, X, ldx, Y, ldy, ncols);
+  if (h->engine == 2)
+    return h->tc_variant ? apply_tc<3>(h, X, ldx, Y, ldy, ncols) : apply_tc<2>(h, X, ldx, Y, ldy, ncols);
   return apply_tc<1>(h, X, ldx, Y, ldy, ncols);
+}
+
+namespace {
+// deterministic test vectors in [-1, 1) (a 32-bit integer hash of the index)
+__global__ void k_fill_hash(int64_t n, float* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = (uint32_t)i * 2654435761u;
+    v ^= v >> 16;
+    v *= 2246822519u;
+    v ^= v >> 13;
+    x[i] = (float)(v >> 8) * (2.0f / 16777216.0f) - 1.0f;
+  }
+}
+}  // namespace
+
+fkf_status hmat_autotune(fkf_hmat* h, int64_t ncols, int* variant, double* ms_best) {
+  fkf_ctx* ctx = h->ctx;
+  *variant = h->tc_variant;
+  *ms_best = 0.0;
+  if (h->prec != FKF_FP32 || h->engine != 2) return FKF_OK;
+  const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(ncols, h->tc_panel));
+  DevBuf X, Y;
+  FKF_TRY(dev_alloc(ctx, X, (size_t)h->n * nc * sizeof(float)));
+  FKF_TRY(dev_alloc(ctx, Y, (size_t)h->n * nc * sizeof(float)));
+  k_fill_hash<<<152 * 8, 256, 0, ctx->stream>>>(h->n * nc, X.as<float>());
+  FKF_LAUNCHED(ctx);
+  cudaEvent_t e0, e1;
+  FKF_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_err(ctx, FKF_ECUDA, "autotune: event creation failed");
+  }
+  double best = -1.0;
+  int vbest = 0;
+  fkf_status st = FKF_OK;
+  for (int v = 0; v < 2 && st == FKF_OK; v++) {
+    h->tc_variant = v;
+    st = hmat_apply_clustered_tc(h, X.as<float>(), nc, Y.as<float>(), nc, nc);  // warm
+    if (st != FKF_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    for (int k = 0; k < 3 && st == FKF_OK; k++)
+      st = hmat_apply_clustered_tc(h, X.as<float>(), nc, Y.as<float>(), nc, nc);
+    cudaEventRecord(e1, ctx->stream);
+    float ms = 0.f;
+    if (st == FKF_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = set_err(ctx, FKF_ECUDA, "autotune: timing failed");
+    if (st == FKF_OK && (best < 0 || ms / 3.0 < best)) best = ms / 3.0, vbest = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FKF_TRY(st);
+  FKF_TRY(hmat_tc_check(h));
+  h->tc_variant = vbest;
+  *variant = vbest;
+  *ms_best = best;
+  return FKF_OK;
 }
 
 bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols) {
@@ -1161,7 +1229,7 @@ bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols) {
   for (int f = 0; f < nb; f++) {
     const fkf_hmat* h = hs[f];
     if (h->prec != FKF_FP32 || h->engine != F || (F != 1 && F != 2) || ncols[f] > h->tc_panel ||
-        h->ctx->device != hs[0]->ctx->device)
+        h->ctx->device != hs[0]->ctx->device || h->tc_variant != hs[0]->tc_variant)
       return false;
     for (int g = 0; g < f; g++)
       if (hs[g] == h) return false;  // one operator's buffers serve one apply at a time
@@ -1172,7 +1240,9 @@ bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols) {
 fkf_status hmat_apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float* const* X, const int64_t* ldx,
                                float* const* Y, const int64_t* ldy, const int64_t* ncols) {
   if (!hmat_tc_multi_ok(hs, nb, ncols)) return set_err(ctx, FKF_EINVAL, "merged apply: operators not compatible");
-  if (hs[0]->engine == 2) return apply_tc_multi<2>(ctx, hs, nb, X, ldx, Y, ldy, ncols);
+  if (hs[0]->engine == 2)
+    return hs[0]->tc_variant ? apply_tc_multi<3>(ctx, hs, nb, X, ldx, Y, ldy, ncols)
+                             : apply_tc_multi<2>(ctx, hs, nb, X, ldx, Y, ldy, ncols);
   return apply_tc_multi<1>(ctx, hs, nb, X, ldx, Y, ldy, ncols);
 }
 

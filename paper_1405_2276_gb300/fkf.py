@@ -112,6 +112,7 @@ _sigs = {
     "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
     "fkf_hmatrix_set_engine": (C.c_int, [_P, C.c_int32]),
     "fkf_hmatrix_get_engine": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "fkf_hmatrix_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -228,6 +229,15 @@ def fkf_hmatrix_set_engine(h, engine: int) -> None:
     """FP32 operators: 2 = tensor cores with scaled 2xFP16 (default), 1 = tensor
     cores with 3xTF32, 0 = SIMT tile engine."""
     _check(_lib.fkf_hmatrix_set_engine(h.ptr, engine), h.ctx)
+
+
+def fkf_hmatrix_autotune(h, ncols: int):
+    """Pick the faster tensor-core pipeline shape for this operator; returns
+    (variant, ms per apply of ncols columns)."""
+    v = C.c_int32()
+    ms = C.c_double()
+    _check(_lib.fkf_hmatrix_autotune(h.ptr, ncols, C.byref(v), C.byref(ms)), h.ctx)
+    return v.value, ms.value
 
 
 def fkf_hmatrix_get_engine(h) -> int:

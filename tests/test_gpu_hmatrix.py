@@ -238,3 +238,24 @@ def test_default_engine_as_built(fkf, ctx):
     fkf.fkf_hmatrix_apply_clustered(hm, X, Y0)
     assert (Y - Y0).abs().max().item() < 2e-5 * Y0.abs().max().item()
     fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_autotune_keeps_results(fkf, ctx):
+    """The autotuner picks a pipeline shape; both shapes give the same
+    product bit for bit (the same MMAs in the same order per tile)."""
+    import torch
+
+    pts = synth.grid_points_2d(80, 72)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 0.5, 0.1, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, k_cap=32, precision=1)
+    X = torch.from_numpy(np.random.default_rng(8).standard_normal((n, 300))).to("cuda", torch.float32)
+    Y0 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y0)
+    v, ms = fkf.fkf_hmatrix_autotune(hm, 300)
+    assert v in (0, 1) and ms > 0
+    Y1 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y1)
+    assert torch.equal(Y0, Y1)
+    fkf.fkf_hmatrix_set_engine(hm, 1)
+    assert fkf.fkf_hmatrix_autotune(hm, 300) == (v, 0.0)  # nothing to tune on engine 1
+    fkf.fkf_hmatrix_destroy(hm)
