@@ -37,7 +37,7 @@ MEDIUM = dict(grid=(256, 256), src=20, rec=20, nu=1.5, ell=0.1, sigma2=1.0, nois
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes of one H-apply (both k_tc_apply launches, engine 2) on the 512 x 512 workload, from
 # the ncu capture summarised in profiles/happly_tc_dram_large.md (kernel unchanged since)
-HAPPLY_F2_DRAM_BYTES = 34.71e9
+HAPPLY_F2_DRAM_BYTES = 34.73e9
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 
 

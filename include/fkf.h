@@ -170,11 +170,11 @@ fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, i
  * rotation W' = [W G] E of the new factor): C = A E[0:K, 0:ncols] for
  * row-major FP32 device arrays A (rows x K, leading dimension lda), E
  * (ke x ncols, lde; ke >= K) and C (rows x ncols, ldc), on the 5th-generation
- * tensor cores (tcgen05.mma kind::tf32 with a 3xTF32 split, FP32
- * accumulation in TMEM) -- the kernel the FP32 filter step uses for W' and
- * X'.  The caller owns the three arrays; C must not overlap A or E.  The
- * context keeps a workspace (about 8 bytes per element of A plus 8 per
- * element of E, grown on demand).  The context's stream is synchronised
+ * tensor cores (tcgen05.mma kind::f16 with a two-term FP16 split of operands
+ * scaled by powers of two per row of A and per column of E, FP32 accumulation
+ * in TMEM) -- the kernel the FP32 filter step uses for W' and X'.  The
+ * caller owns the three arrays; C must not overlap A or E.  The context keeps
+ * a workspace (about 4 bytes per element of A and of E, grown on demand).  The context's stream is synchronised
  * before return.  Errors: EINVAL (negative sizes, K > ke, a leading
  * dimension below the row length, C overlapping A or E), ENOMEM, ECUDA,
  * ETIMEOUT (a tensor-core wait expired). */

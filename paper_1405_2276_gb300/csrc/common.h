@@ -36,7 +36,7 @@ struct DevBuf {
 // Workspace of the tensor-core dense GEMM (split operands, error flag and
 // tile counter).
 struct TcGemmWs {
-  DevBuf asplit, bsplit, ctl;
+  DevBuf asplit, bsplit, ctl, scales;
 };
 
 // Workspace of the merged multi-operator H-apply (job lists and their host
@@ -281,7 +281,7 @@ bool hmat_tc_multi_ok(fkf_hmat* const* hs, int nb, const int64_t* ncols);
 // it takes part in one (fkf_filter_step_batched), else a plain apply.
 fkf_status hmat_apply_step(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
 // Dense C_p = A_p B[0:K_p, 0:ncols] for p < np <= 2 (row-major FP32 in and
-// out) on the tensor cores with 3xTF32 products; B has kb >= K_p rows.  The
+// out) on the tensor cores with two-term split products; B has kb >= K_p rows.  The
 // launch is asynchronous: tc_gemm_check reads the error flag after a sync.
 struct TcGemmProblem {
   const float* A;
@@ -290,8 +290,9 @@ struct TcGemmProblem {
   float* C;
   int64_t ldc;
 };
+// fmt: 2 = scaled two-term FP16 split (kind::f16, default), 1 = 3xTF32.
 fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
-                       int ncols, TcGemmWs& ws);
+                       int ncols, TcGemmWs& ws, int fmt = 2);
 fkf_status tc_gemm_check(fkf_ctx* ctx, TcGemmWs& ws);
 
 // hbuild.cpp

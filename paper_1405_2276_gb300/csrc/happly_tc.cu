@@ -301,38 +301,61 @@ __global__ void k_colscale(const unsigned* __restrict__ cmax, int ncols, float* 
   cs[ncols + j] = 1.f / s;
 }
 
-// Split a row-major matrix A (rows x K, ld lda) into 3xTF32 operator chunks:
-// tile t (blockIdx.x) of 128 rows, K chunk c (blockIdx.y) of 16 columns ->
-// out + (t * nch + c) * kAChunk; rows >= rows and columns >= K are zero.
-// Thread units are (row, 4 columns): a warp reads 64-byte runs of 8 rows and
-// writes 512 contiguous bytes per half.
+// Split a row-major matrix A (rows x K, ld lda) into operator chunks of
+// kernel code F: tile t (blockIdx.x) of 128 rows, K chunk c (blockIdx.y) of 16
+// columns -> out + (t * nch + c) * kAChunk; rows >= rows and columns >= K are
+// zero; the FP16 format scales row r by rs[r].  Thread units are (row, kPer
+// columns): a warp reads runs of 8 (TF32) or 4 (FP16) rows and writes 512
+// contiguous bytes per half.
+template <int F>
 __global__ void __launch_bounds__(256) k_tc_split_rows(const float* __restrict__ A, int64_t lda, int64_t rows, int K,
-                                                       int nch, uint8_t* __restrict__ out) {
-  using G = Geo<1>;
+                                                       int nch, const float* __restrict__ rs,
+                                                       uint8_t* __restrict__ out) {
+  using G = Geo<F>;
+  constexpr int P = G::kPer, NU = kK / P;
   const int64_t t = blockIdx.x;
   const int c = blockIdx.y;
   uint8_t* hi = out + (t * nch + c) * (int64_t)G::kAChunk;
   const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda & 3) == 0;
 #pragma unroll
-  for (int i = 0; i < 2; i++) {
+  for (int i = 0; i < kM * NU / 256; i++) {
     const int u = threadIdx.x + 256 * i;
-    const int kq = u & 3, row = u >> 2;
+    const int kq = u % NU, row = u / NU;
     const int64_t r = t * kM + row;
-    const int k = c * kK + 4 * kq;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    const int k = c * kK + P * kq;
+    float v[P];
+#pragma unroll
+    for (int j = 0; j < P; j++) v[j] = 0.f;
     if (r < rows) {
       const float* src = A + r * lda + k;
-      if (vec && k + 4 <= K) {
-        const float4 q = *reinterpret_cast<const float4*>(src);
-        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-      } else {
+      const float sc = (fmt_of(F) == 2 && rs) ? rs[r] : 1.f;
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-          if (k + j < K) v[j] = src[j];
+      for (int j0 = 0; j0 < P; j0 += 4) {
+        if (vec && k + j0 + 4 <= K) {
+          const float4 q = *reinterpret_cast<const float4*>(src + j0);
+          v[j0] = q.x * sc, v[j0 + 1] = q.y * sc, v[j0 + 2] = q.z * sc, v[j0 + 3] = q.w * sc;
+        } else {
+#pragma unroll
+          for (int j = j0; j < j0 + 4; j++)
+            if (k + j < K) v[j] = src[j] * sc;
+        }
       }
     }
-    put_unit<1>(hi, hi + G::kABytes, row, 4 * kq, v);
+    put_unit<F>(hi, hi + G::kABytes, row, P * kq, v);
   }
+}
+
+// Row scales of the FP16 format: the largest power of two with the row's max
+// |element| <= 2^14 (one warp per row).
+__global__ void __launch_bounds__(256) k_rowscale(const float* __restrict__ A, int64_t lda, int64_t rows, int K,
+                                                  float* __restrict__ rs) {
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float m = 0.f;
+  for (int k = lane; k < K; k += 32) m = fmaxf(m, fabsf(A[r * lda + k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) rs[r] = pow2_floor(16384.f / m);
 }
 
 // ---- the work items ----------------------------------------------------------
@@ -405,9 +428,10 @@ struct PhGemm {
   int64_t a1;      // first A chunk of problem 1 (problem 0 starts at 0)
   int64_t nw0;     // row tiles of problem 0
   int nch0, nch1;  // K chunks per tile
-  const float* cinv;  // unused (unscaled format)
+  const float* cinv;  // inverse column scales of B (FP16 format), else null
   const uint8_t* astream;
   int nct, ncols;
+  const float *rs0, *rs1;  // row scales of A_0, A_1 (FP16 format), else null
   // (fields selected, not indexed: a dynamic index into a kernel parameter
   // array would copy the parameters to local memory)
   __device__ __forceinline__ int nchunk(int64_t w) const { return w >= nw0 ? nch1 : nch0; }
@@ -423,8 +447,10 @@ struct PhGemm {
   __device__ __forceinline__ float* row_dst(int64_t w, int row, float& rinv) const {
     const bool p = w >= nw0;
     const int64_t r = (p ? w - nw0 : w) * kM + row;
-    rinv = 1.f;
-    return r < (p ? rows1 : rows0) ? (p ? C1 : C0) + r * (p ? ldc1 : ldc0) : nullptr;
+    if (r >= (p ? rows1 : rows0)) return nullptr;
+    const float* rs = p ? rs1 : rs0;
+    rinv = rs ? 1.f / rs[r] : 1.f;
+    return (p ? C1 : C0) + r * (p ? ldc1 : ldc0);
   }
 };
 
@@ -1252,11 +1278,11 @@ fkf_status hmat_set_engine(fkf_hmat* h, int engine) {
   return FKF_OK;
 }
 
-fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
-                       int ncols, TcGemmWs& ws) {
-  using G = Geo<1>;
-  if (np < 1 || np > 2) return set_err(ctx, FKF_EINVAL, "tc_gemm_f32: 1 or 2 problems");
-  if (ncols <= 0) return FKF_OK;
+namespace {
+template <int F>
+fkf_status tc_gemm_impl(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
+                        int ncols, TcGemmWs& ws) {
+  using G = Geo<F>;
   PhGemm ph{};
   int64_t nw[2] = {0, 0}, a0[2] = {0, 0}, achunks = 0;
   int nch[2] = {0, 0};
@@ -1284,15 +1310,43 @@ fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float
   }
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
   FKF_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream));
+  float* rs[2] = {nullptr, nullptr};
+  float* cs = nullptr;
+  if (fmt_of(F) == 2) {
+    // row scales of A_0, A_1, then scales, inverse scales and maxima of B's columns
+    const size_t sbytes = (size_t)(p[0].rows + (np > 1 ? p[1].rows : 0) + 3 * (int64_t)ncols + 4) * sizeof(float);
+    if (ws.scales.bytes < sbytes) FKF_TRY(dev_alloc(ctx, ws.scales, sbytes));
+    rs[0] = ws.scales.as<float>();
+    rs[1] = rs[0] + p[0].rows;
+    cs = rs[1] + (np > 1 ? p[1].rows : 0);
+    unsigned* cmax = reinterpret_cast<unsigned*>(cs + 2 * ncols);
+    for (int i = 0; i < np; i++)
+      if (p[i].rows > 0) {
+        k_rowscale<<<(unsigned)cdiv(p[i].rows, 8), 256, 0, ctx->stream>>>(p[i].A, p[i].lda, p[i].rows, p[i].K, rs[i]);
+        FKF_LAUNCHED(ctx);
+      }
+    FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)ncols * sizeof(unsigned), ctx->stream));
+    if (kb > 0) {
+      const int64_t rpb = 2048;
+      k_colmax<<<dim3((unsigned)cdiv(ncols, 256), (unsigned)cdiv(kb, rpb)), 256, 0, ctx->stream>>>(B, ldb, kb, ncols,
+                                                                                                    rpb, cmax);
+      FKF_LAUNCHED(ctx);
+    }
+    k_colscale<<<(unsigned)cdiv(ncols, 256), 256, 0, ctx->stream>>>(cmax, ncols, cs);
+    FKF_LAUNCHED(ctx);
+    ph.rs0 = rs[0];
+    ph.rs1 = np > 1 ? rs[1] : nullptr;
+    ph.cinv = cs + ncols;
+  }
   if (nbx > 0) {
-    k_tc_split_x<1><<<dim3((unsigned)nbx, (unsigned)nct), 256, 0, ctx->stream>>>(B, ldb, ncols, nullptr, kb, nct,
-                                                                                 nullptr, ws.bsplit.as<uint8_t>());
+    k_tc_split_x<F><<<dim3((unsigned)nbx, (unsigned)nct), 256, 0, ctx->stream>>>(B, ldb, ncols, nullptr, kb, nct, cs,
+                                                                                 ws.bsplit.as<uint8_t>());
     FKF_LAUNCHED(ctx);
   }
   for (int i = 0; i < np; i++) {
     if (nw[i] == 0 || nch[i] == 0) continue;
-    k_tc_split_rows<<<dim3((unsigned)nw[i], (unsigned)nch[i]), 256, 0, ctx->stream>>>(
-        p[i].A, p[i].lda, p[i].rows, p[i].K, nch[i], ws.asplit.as<uint8_t>() + a0[i] * G::kAChunk);
+    k_tc_split_rows<F><<<dim3((unsigned)nw[i], (unsigned)nch[i]), 256, 0, ctx->stream>>>(
+        p[i].A, p[i].lda, p[i].rows, p[i].K, nch[i], rs[i], ws.asplit.as<uint8_t>() + a0[i] * G::kAChunk);
     FKF_LAUNCHED(ctx);
   }
   ph.bsplit = ws.bsplit.as<uint8_t>();
@@ -1301,12 +1355,21 @@ fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float
   ph.ncols = ncols;
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<1, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
   const int grid = (int)std::min<int64_t>(sms, nwork * nct);
-  k_tc_apply<1, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
+  k_tc_apply<F, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
                                                                    nwork * nct, counter, ws.ctl.as<int>());
   FKF_LAUNCHED(ctx);
   return FKF_OK;
+}
+}  // namespace
+
+fkf_status tc_gemm_f32(fkf_ctx* ctx, const TcGemmProblem* p, int np, const float* B, int64_t ldb, int64_t kb,
+                       int ncols, TcGemmWs& ws, int fmt) {
+  if (np < 1 || np > 2) return set_err(ctx, FKF_EINVAL, "tc_gemm_f32: 1 or 2 problems");
+  if (ncols <= 0) return FKF_OK;
+  if (fmt == 1) return tc_gemm_impl<1>(ctx, p, np, B, ldb, kb, ncols, ws);
+  return tc_gemm_impl<2>(ctx, p, np, B, ldb, kb, ncols, ws);
 }
 
 fkf_status tc_gemm_check(fkf_ctx* ctx, TcGemmWs& ws) {
