@@ -378,3 +378,35 @@ def test_fixed_h_fast_path_reuses_products_exactly(fkf, device_inputs):
     Hc.val[3] *= 1.0 + 1e-12
     c_nll, c_paths, _ = run(True, seq[:3] + [(ys[3], Hc)] + seq[4:])
     assert c_paths[:3] == [0, 1, 3] and c_paths[3] != 3
+
+
+@pytest.mark.parametrize("precision,eta,bound", [(0, 0.0, 1e-10), (1, 1.0, 5e-3)])
+def test_3d_voxels_and_rays_match_dense_kf(fkf, precision, eta, bound):
+    """A 3D voxel grid (12 x 10 x 14) with straight rays between lattices on
+    two opposite faces (the 3D workload's geometry, small enough for the dense
+    oracle): the octree H-matrix and the filter against the dense KF, and 16
+    conditional realizations per step through the same path."""
+    import torch
+
+    wl = synth.tomography_workload((12, 10, 14), (3, 4), (4, 3), 4, 0.3, 1.0, 1e-4, seed=synth.BASE_SEED + 91)
+    pts = wl["points"]
+    kern = (0.5, 0.3, 1.0)
+    G = covariance.dense_gamma(pts, *kern)
+    Hd = synth.csr_to_dense(wl["H"])
+    ref = kalman.kf_dense(G, [(wl["y"][k], Hd, 1e-4) for k in range(4)])
+    sg = [(wl["y"][k], wl["H"], 1e-4) for k in range(4)]
+    got, ctx, hm, f = run_filter(pts, kern, sg, precision=precision, leaf=40, eta=eta, aca_tol=1e-10)
+    for a, b in zip(got, ref):
+        assert rel_err(a["s"], b["s"]) < bound
+        assert rel_err(a["var"], b["var"]) < bound
+    n = pts.shape[0]
+    L = np.linalg.cholesky(G)
+    a = L @ np.random.default_rng(4).standard_normal((n, 16))
+    a_t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.empty_like(a_t)
+    fkf.fkf_conditional_realization(f, a_t, out)
+    x_ref = uq.realization(ref[-1]["s"], ref[-1]["Sigma"], G, got[-1]["alpha"], a)
+    assert rel_err(out.cpu().numpy(), x_ref) < (1e-9 if precision == 0 else 5e-3)
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
