@@ -57,7 +57,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # a value-returning function (or lambda) that can fall off its end is an error,
+    # not a warning: the optimiser treats that path as unreachable
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Werror=return-type",
+              "--diag-error=940", "-I", INCLUDE, "-I", CSRC]
     jobs = []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
