@@ -113,8 +113,18 @@ fkf_status ctx_side(fkf_ctx* ctx, size_t n_events) {
   return FKF_OK;
 }
 
+fkf_status ctx_side_lo(fkf_ctx* ctx) {
+  if (!ctx->side_lo) {
+    int least = 0, greatest = 0;
+    FKF_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    FKF_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side_lo, cudaStreamNonBlocking, least));
+  }
+  return FKF_OK;
+}
+
 FKF_API void fkf_destroy(fkf_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->side_lo) cudaStreamDestroy(ctx->side_lo);
   for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->solver) cusolverDnDestroy(reinterpret_cast<cusolverDnHandle_t>(ctx->solver));

@@ -63,12 +63,15 @@ struct fkf_ctx {
   DevBuf solver_info;  // status word for cuSOLVER calls
   TcGemmWs gemm_ws;    // fkf_rotate_f32
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
+  cudaStream_t side_lo = nullptr;     // low-priority stream for work that fills SMs beside a persistent kernel
   std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
   TcMultiWs multi_ws;                 // merged H-applies of batched steps launched on this context
 };
 
 // Second stream of the context and at least n events (created on first use).
 fkf_status ctx_side(fkf_ctx* ctx, size_t n_events);
+// The context's low-priority stream (created on first use).
+fkf_status ctx_side_lo(fkf_ctx* ctx);
 
 // Error plumbing: every internal function returns fkf_status and records a
 // message on the context.

@@ -752,6 +752,10 @@ struct fkf_filter {
   TcGemmWs rot;       // tensor-core products (FP32 state): the rotation and the basis test
   DevBuf hw32, c32;   // basis test of the FP32 state: HW and HW^T in FP32, HW HW^T
   cudaEvent_t ev[7] = {};
+  // HW gathered (main stream) -> HWD and the product HWD HW^T on the
+  // low-priority stream, beside the H-apply -> consumed on the main stream
+  cudaEvent_t ev_hw = nullptr, ev_p = nullptr;
+  DevBuf Pw;  // HWD HW^T (m x m, lower triangle)
   double phase_ms[6] = {};
 };
 
@@ -783,6 +787,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->uz, r));
   FKF_TRY(dev_alloc(ctx, f->vcoef, (size_t)std::max<int64_t>(nm, 1) * f->w));
   FKF_TRY(A(f->HWD, m * r));
+  FKF_TRY(A(f->Pw, m * m));
   FKF_TRY(A(f->nll, 4));
   FKF_TRY(A(f->Lpv, m * m));
   FKF_TRY(A(f->Gm, m * m));
@@ -856,6 +861,8 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
     return fail(set_err(ctx, FKF_ECUDA, "memset s0"));
   }
   for (int i = 0; i < 7; i++) cudaEventCreate(&f->ev[i]);
+  cudaEventCreateWithFlags(&f->ev_hw, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&f->ev_p, cudaEventDisableTiming);
   *out = f;
   return FKF_OK;
 }
@@ -864,6 +871,8 @@ void filter_destroy(fkf_filter* f) {
   if (!f) return;
   for (int i = 0; i < 7; i++)
     if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+  if (f->ev_hw) cudaEventDestroy(f->ev_hw);
+  if (f->ev_p) cudaEventDestroy(f->ev_p);
   delete f;
 }
 
@@ -887,6 +896,55 @@ static fkf_status gram_T(fkf_ctx* ctx, size_t w, int64_t M, int64_t N, int64_t K
                          const void* B, int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
   if (w == 8) return gram_f64(ctx, M, N, K, (const double*)A, lda, (const double*)B, ldb, C, ldc, ws);
   return gram_f32(ctx, M, N, K, (const float*)A, lda, (const float*)B, ldb, C, ldc, ws);
+}
+
+// C[i][j] -= P[i][j] for j <= i < m (lower triangles).
+__global__ void k_sub_lower(int m, const double* __restrict__ P, int64_t ldp, double* __restrict__ C, int64_t ldc) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / m, j = e % m;
+    if (j <= i) C[i * ldc + j] -= P[i * ldp + j];
+  }
+}
+
+namespace {
+// Runs the library's stream-ordered helpers on another stream for its scope.
+struct OnStream {
+  fkf_ctx* ctx;
+  cudaStream_t saved;
+  OnStream(fkf_ctx* c, cudaStream_t s) : ctx(c), saved(c->stream) { ctx->stream = s; }
+  ~OnStream() { ctx->stream = saved; }
+};
+}  // namespace
+
+// The products of the step that involve the low-rank weight and HW only,
+// HWD = HW D (D diagonal, or the full weight Df) and Pw = HWD HW^T (lower
+// triangle), once HW = H W is in HWA (m x r, ld ldh) on the context stream.
+// They go to the context's low-priority stream, so that on an FP32 state they
+// run on the SMs' FP64 units beside the tensor-core H-apply (which leaves room
+// for one FP64 tile CTA per SM) instead of after it; the step's main stream
+// waits for ev_p before it uses HWD or Pw.  Nothing to do when r = 0.
+static fkf_status weight_products(fkf_filter* f, int m, const double* HW, int64_t ldh) {
+  fkf_ctx* ctx = f->ctx;
+  const int r = f->r;
+  if (r <= 0) return FKF_OK;
+  FKF_TRY(ctx_side_lo(ctx));
+  cudaStream_t lo = ctx->side_lo;
+  FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamWaitEvent(lo, f->ev_hw, 0));
+  {
+    OnStream on(ctx, lo);
+    if (f->diag) {
+      k_scale_cols<<<nblk((int64_t)m * r), 256, 0, lo>>>(m, r, HW, ldh, f->D.as<double>(), f->HWD.as<double>());
+      FKF_LAUNCHED(ctx);
+    } else {
+      FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, ldh, f->Df.as<double>(), r, 0.0, f->HWD.as<double>(), r));
+    }
+    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, 1.0, f->HWD.as<double>(), r, HW, ldh, 0.0, f->Pw.as<double>(), m,
+                         true));
+  }
+  FKF_CUDA(ctx, cudaEventRecord(f->ev_p, lo));
+  return FKF_OK;
 }
 
 template <typename T>
@@ -1005,14 +1063,19 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
                                                         f->cval.as<double>(), f->Bt.as<T>(), m);
     FKF_LAUNCHED(ctx);
+    // ---- gather HW = H W (needs no product with Gamma)
+    csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, r, HWA, nm, st);
+    FKF_LAUNCHED(ctx);
+    FKF_TRY(weight_products(f, m, HWA, nm));
     FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
     // ---- S2: G = Gamma_H H^T
     FKF_TRY(hmat_apply_step(h, f->Bt.p, m, G, ld, m));
     FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
-    // ---- gathers: [HW | A] = H [W G]; innovation
-    csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, nm, HWA, nm, st);
+    // ---- gather A = H G; innovation
+    csr_gather<T>(m, rowptr, col, val, iperm, n, G, ld, m, HWA + r, nm, st);
     FKF_LAUNCHED(ctx);
   } else {
+    FKF_TRY(weight_products(f, m, HWA, nm));
     for (int e = 1; e < 3; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
   }
   k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->s_hat.as<double>(),
@@ -1071,14 +1134,11 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   const bool diag = f->diag;
   double* Dfc = f->Df.as<double>();
   if (r > 0) {
-    if (diag) {
-      k_scale_cols<<<nblk((int64_t)m * r), 256, 0, st>>>(m, r, HW, nm, f->D.as<double>(), f->HWD.as<double>());
-      FKF_LAUNCHED(ctx);
-    } else {
-      FKF_TRY(gemm_f64(ctx, false, false, m, r, r, 1.0, HW, nm, Dfc, r, 0.0, f->HWD.as<double>(), r));
-    }
-    // S is read only through its lower triangle (blocked Cholesky)
-    FKF_TRY(gemm_sym_f64(ctx, false, true, m, r, -1.0, f->HWD.as<double>(), r, HW, nm, 1.0, S, lda_aug, true));
+    // S -= HWD HW^T (formed beside the H-apply; S is read only through its
+    // lower triangle by the blocked Cholesky)
+    FKF_CUDA(ctx, cudaStreamWaitEvent(st, f->ev_p, 0));
+    k_sub_lower<<<nblk((int64_t)m * m), 256, 0, st>>>(m, f->Pw.as<double>(), m, S, lda_aug);
+    FKF_LAUNCHED(ctx);
   }
   if (kept) {
     // ---- basis kept: Sigma+ = alpha' Gamma - W D' W^T with the weight updated
