@@ -64,6 +64,10 @@ struct fkf_ctx {
   TcGemmWs gemm_ws;    // fkf_rotate_f32
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
   cudaStream_t side_lo = nullptr;     // low-priority stream for work that fills SMs beside a persistent kernel
+  // When set, the tensor-core H-apply on this context records ph2_mark on the
+  // context stream just before its last phase-2 launch and sets ph2_marked.
+  cudaEvent_t ph2_mark = nullptr;
+  bool ph2_marked = false;
   std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
   TcMultiWs multi_ws;                 // merged H-applies of batched steps launched on this context
 };

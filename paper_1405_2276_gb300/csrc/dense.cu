@@ -3,12 +3,34 @@
 // row chunks, summed in a fixed order in FP64), and the small FP64 products of
 // the data-space algebra.
 #include <algorithm>
+#include <atomic>
+#include <type_traits>
 
 #include "common.h"
 #include "dense.h"
 #include "tile.cuh"
 
 namespace {
+
+// The FP64 tile kernels ask for the largest shared-memory carveout: an SM
+// that runs a persistent tensor-core kernel with a large shared-memory
+// footprint (phase 2 of the H-apply) then also takes one of their CTAs beside
+// it, instead of draining first to switch configurations.  Set once per
+// kernel and device (a hint: a refusal is ignored).
+template <typename Kern>
+void prefer_max_shared(Kern kernel, std::atomic<uint32_t>& done, int device) {
+  const uint32_t bit = 1u << (device & 31);
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+      cudaSuccess)
+    cudaGetLastError();
+  done.fetch_or(bit);
+}
+#define FKF_MAXSHARED(kern)                          \
+  do {                                               \
+    static std::atomic<uint32_t> done_{0};           \
+    prefer_max_shared(kern, done_, ctx->device);     \
+  } while (0)
 
 // C = alpha op(A) op(B) + beta C, all row-major.
 template <typename T, bool A_KC, bool B_KC>
@@ -152,14 +174,20 @@ fkf_status gemm_impl(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64
   dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM));
   // op(A)(m,k): ta=false -> A[m*lda+k] (k-contiguous); ta=true -> A[k*lda+m]
   // op(B)(k,n): tb=false -> B[k*ldb+n]; tb=true -> B[n*ldb+k] (k-contiguous)
-  if (!ta && !tb)
+  constexpr bool f64 = std::is_same<T, double>::value;
+  if (!ta && !tb) {
+    if (f64) FKF_MAXSHARED((k_gemm<T, true, false>));
     k_gemm<T, true, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!ta && tb)
+  } else if (!ta && tb) {
+    if (f64) FKF_MAXSHARED((k_gemm<T, true, true>));
     k_gemm<T, true, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (ta && !tb)
+  } else if (ta && !tb) {
+    if (f64) FKF_MAXSHARED((k_gemm<T, false, false>));
     k_gemm<T, false, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else
+  } else {
+    if (f64) FKF_MAXSHARED((k_gemm<T, false, true>));
     k_gemm<T, false, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+  }
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }
@@ -192,12 +220,15 @@ fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, do
   const int64_t nb = cdiv(N, BM);
   const unsigned grid = (unsigned)(nb * (nb + 1) / 2);
 #define FKF_SYM_LAUNCH(AK, BK)                                                                                    \
-  if (lower_only)                                                                                                  \
+  if (lower_only) {                                                                                                \
+    FKF_MAXSHARED((k_gemm_sym<double, AK, BK, false>));                                                            \
     k_gemm_sym<double, AK, BK, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, \
                                                                               ldb, beta, C, ldc);               \
-  else                                                                                                             \
+  } else {                                                                                                         \
+    FKF_MAXSHARED((k_gemm_sym<double, AK, BK, true>));                                                             \
     k_gemm_sym<double, AK, BK, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B,  \
-                                                                             ldb, beta, C, ldc);
+                                                                             ldb, beta, C, ldc);                \
+  }
   if (!ta && !tb) {
     FKF_SYM_LAUNCH(true, false)
   } else if (!ta && tb) {

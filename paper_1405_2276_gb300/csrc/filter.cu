@@ -919,18 +919,18 @@ struct OnStream {
 
 // The products of the step that involve the low-rank weight and HW only,
 // HWD = HW D (D diagonal, or the full weight Df) and Pw = HWD HW^T (lower
-// triangle), once HW = H W is in HWA (m x r, ld ldh) on the context stream.
-// They go to the context's low-priority stream, so that on an FP32 state they
-// run on the SMs' FP64 units beside the tensor-core H-apply (which leaves room
-// for one FP64 tile CTA per SM) instead of after it; the step's main stream
-// waits for ev_p before it uses HWD or Pw.  Nothing to do when r = 0.
+// triangle), once HW = H W is in HWA (m x r, ld ldh) and ev_hw has been
+// recorded after it on the context stream.  They go to the context's
+// low-priority stream, so that on an FP32 state they run on the SMs' FP64
+// units beside the tensor-core H-apply's phase 2 (which leaves room for one
+// FP64 tile CTA per SM) instead of after it; the step's main stream waits for
+// ev_p before it uses HWD or Pw.  Nothing to do when r = 0.
 static fkf_status weight_products(fkf_filter* f, int m, const double* HW, int64_t ldh) {
   fkf_ctx* ctx = f->ctx;
   const int r = f->r;
   if (r <= 0) return FKF_OK;
   FKF_TRY(ctx_side_lo(ctx));
   cudaStream_t lo = ctx->side_lo;
-  FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, ctx->stream));
   FKF_CUDA(ctx, cudaStreamWaitEvent(lo, f->ev_hw, 0));
   {
     OnStream on(ctx, lo);
@@ -1066,15 +1066,24 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     // ---- gather HW = H W (needs no product with Gamma)
     csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, r, HWA, nm, st);
     FKF_LAUNCHED(ctx);
-    FKF_TRY(weight_products(f, m, HWA, nm));
     FKF_CUDA(ctx, cudaEventRecord(f->ev[1], st));
-    // ---- S2: G = Gamma_H H^T
-    FKF_TRY(hmat_apply_step(h, f->Bt.p, m, G, ld, m));
+    // ---- S2: G = Gamma_H H^T; the weight products start with its phase 2
+    // (or after it, when the apply sets no mark)
+    ctx->ph2_mark = r > 0 ? f->ev_hw : nullptr;
+    ctx->ph2_marked = false;
+    const fkf_status ast = hmat_apply_step(h, f->Bt.p, m, G, ld, m);
+    const bool marked = ctx->ph2_marked;
+    ctx->ph2_mark = nullptr;
+    ctx->ph2_marked = false;
+    FKF_TRY(ast);
+    if (r > 0 && !marked) FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, st));
+    FKF_TRY(weight_products(f, m, HWA, nm));
     FKF_CUDA(ctx, cudaEventRecord(f->ev[2], st));
     // ---- gather A = H G; innovation
     csr_gather<T>(m, rowptr, col, val, iperm, n, G, ld, m, HWA + r, nm, st);
     FKF_LAUNCHED(ctx);
   } else {
+    if (r > 0) FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, st));
     FKF_TRY(weight_products(f, m, HWA, nm));
     for (int e = 1; e < 3; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
   }

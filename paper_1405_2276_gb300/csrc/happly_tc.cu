@@ -112,7 +112,10 @@ struct Geo {
   static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : (F == 2 ? FKF_TC_STAGES_F16 : 4);  // pipeline stages
   static constexpr uint32_t kSBO = (kK / kPer) * 128;  // next 8-row group
   static constexpr uint32_t kIdesc = kFmt == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
-  static constexpr int kSmem = kS * kStage + kTail + kEpiBytes;
+  static constexpr int kSmem = kS * kStage + kTail + kEpiBytes;  // phase 1 (its epilogue stages tiles)
+  // phase 2 and the GEMMs store rows straight from TMEM and take no staging
+  // tiles: the room left on the SM holds one FP64 tile CTA of concurrent work
+  static constexpr int kSmemRows = kS * kStage + kTail;
   // barrier indices
   static constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1,
                        QE = QF + kQ, NBAR = QE + kQ;
@@ -1018,7 +1021,10 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
+  // the largest carveout (not the smallest that fits phase 2): the SM keeps room for one FP64 tile CTA
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
   for (int64_t c0 = 0; c0 < ncols; c0 += P) {
     const int nc = (int)std::min<int64_t>(P, ncols - c0);
     const int nct = (int)cdiv(nc, kN);
@@ -1032,8 +1038,12 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
       FKF_LAUNCHED(ctx);
     }
     FKF_TRY(tc_reduce<F>(h, nc, st));
+    if (ctx->ph2_mark && c0 + P >= ncols) {  // the last phase 2 of this apply starts here
+      FKF_CUDA(ctx, cudaEventRecord(ctx->ph2_mark, st));
+      ctx->ph2_marked = true;
+    }
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
-    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph2>{tc_ph2<F>(h, Y + c0, ldy, nc, cs), nullptr,
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmemRows, st>>>(JobSet<Ph2>{tc_ph2<F>(h, Y + c0, ldy, nc, cs), nullptr,
                                                                       nullptr, 0},
                                                           h->n_tctile * nct, counters + 1, h->tc_err.as<int>());
     FKF_LAUNCHED(ctx);
@@ -1109,7 +1119,10 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
+  // the largest carveout (not the smallest that fits phase 2): the SM keeps room for one FP64 tile CTA
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
   if (!p1.empty()) {
     const JobSet<Ph1> js{p1[0], reinterpret_cast<const Ph1*>(db + o1), reinterpret_cast<const int64_t*>(db + ot1),
                          (int)p1.size()};
@@ -1122,7 +1135,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     const JobSet<Ph2> js{p2[0], reinterpret_cast<const Ph2*>(db + o2), reinterpret_cast<const int64_t*>(db + ot2),
                          (int)p2.size()};
     const int grid = (int)std::min<int64_t>(sms, t2.back());
-    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmem, st>>>(js, t2.back(), counters + 1, err);
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmemRows, st>>>(js, t2.back(), counters + 1, err);
     FKF_LAUNCHED(ctx);
   }
   k_err_fanout<<<1, 64, 0, st>>>(err, reinterpret_cast<int* const*>(db + oe), (int)errs.size());
@@ -1355,9 +1368,9 @@ fkf_status tc_gemm_impl(fkf_ctx* ctx, const TcGemmProblem* p, int np, const floa
   ph.ncols = ncols;
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   const int grid = (int)std::min<int64_t>(sms, nwork * nct);
-  k_tc_apply<F, PhGemm><<<grid, kThreads, G::kSmem, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
+  k_tc_apply<F, PhGemm><<<grid, kThreads, G::kSmemRows, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
                                                                    nwork * nct, counter, ws.ctl.as<int>());
   FKF_LAUNCHED(ctx);
   return FKF_OK;
