@@ -1131,6 +1131,13 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     FKF_LAUNCHED(ctx);
   }
   for (int f : active) FKF_TRY(tc_reduce<F>(hs[f], (int)ncols[f], st));
+  for (int f : active) {  // each operator's context may ask to hear when phase 2 starts
+    fkf_ctx* c = hs[f]->ctx;
+    if (c->ph2_mark) {
+      FKF_CUDA(ctx, cudaEventRecord(c->ph2_mark, st));
+      c->ph2_marked = true;
+    }
+  }
   if (!p2.empty()) {
     const JobSet<Ph2> js{p2[0], reinterpret_cast<const Ph2*>(db + o2), reinterpret_cast<const int64_t*>(db + ot2),
                          (int)p2.size()};
