@@ -68,6 +68,10 @@ struct fkf_ctx {
   // context stream just before its last phase-2 launch and sets ph2_marked.
   cudaEvent_t ph2_mark = nullptr;
   bool ph2_marked = false;
+  // When set, the column maxima of |X| for the tensor-core H-apply's split of
+  // X (ncols unsigned, ordered float bits), already computed on the context
+  // stream by the caller: the apply uses them instead of scanning X.
+  const unsigned* x_colmax = nullptr;
   std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
   TcMultiWs multi_ws;                 // merged H-applies of batched steps launched on this context
 };

@@ -199,11 +199,17 @@ __global__ void k_words_differ(int64_t n, const uint32_t* __restrict__ a, const 
 // column of H = row of Bt; duplicates are summed in the sorted order.
 template <typename T>
 __global__ void k_densify_csc(int64_t n, const int64_t* __restrict__ colptr, const int* __restrict__ crow,
-                              const double* __restrict__ cval, T* __restrict__ Bt, int64_t ldb) {
+                              const double* __restrict__ cval, T* __restrict__ Bt, int64_t ldb,
+                              unsigned* __restrict__ cmax) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   T* row = Bt + i * ldb;
   for (int64_t p = colptr[i]; p < colptr[i + 1]; p++) row[crow[p]] += (T)cval[p];
+  // column maxima of |Bt| (ordered bits of non-negative floats), from the
+  // final values (repeated entries summed); zero columns keep 0
+  if (cmax)
+    for (int64_t p = colptr[i]; p < colptr[i + 1]; p++)
+      atomicMax(&cmax[crow[p]], __float_as_uint(fabsf((float)row[crow[p]])));
 }
 
 // out (m x ncols, FP64) = H * src[:, 0:ncols]  (src rows in cluster order)
@@ -756,6 +762,7 @@ struct fkf_filter {
   // low-priority stream, beside the H-apply -> consumed on the main stream
   cudaEvent_t ev_hw = nullptr, ev_p = nullptr;
   DevBuf Pw;  // HWD HW^T (m x m, lower triangle)
+  DevBuf xcmax;  // column maxima of the dense H^T (FP32 state), for the H-apply's split
   double phase_ms[6] = {};
 };
 
@@ -804,6 +811,7 @@ static fkf_status alloc_small(fkf_filter* f) {
   FKF_TRY(A(f->Ep, r * r));
   FKF_TRY(A(f->Qm, r * r));
   if (f->w == 4) {
+    FKF_TRY(dev_alloc(ctx, f->xcmax, (size_t)std::max<int64_t>(m, 1) * sizeof(unsigned)));
     FKF_TRY(A(f->hw32, m * r));        // 2 m r floats
     FKF_TRY(A(f->c32, m * m / 2 + 1));  // m^2 floats
   }
@@ -1060,8 +1068,10 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
     FKF_LAUNCHED(ctx);
     FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
+    unsigned* xcmax = sizeof(T) == 4 ? f->xcmax.as<unsigned>() : nullptr;  // the FP32 split's column scales
+    if (xcmax) FKF_CUDA(ctx, cudaMemsetAsync(xcmax, 0, (size_t)m * sizeof(unsigned), st));
     k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
-                                                        f->cval.as<double>(), f->Bt.as<T>(), m);
+                                                        f->cval.as<double>(), f->Bt.as<T>(), m, xcmax);
     FKF_LAUNCHED(ctx);
     // ---- gather HW = H W (needs no product with Gamma)
     csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, r, HWA, nm, st);
@@ -1071,10 +1081,12 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     // (or after it, when the apply sets no mark)
     ctx->ph2_mark = r > 0 ? f->ev_hw : nullptr;
     ctx->ph2_marked = false;
+    ctx->x_colmax = xcmax;
     const fkf_status ast = hmat_apply_step(h, f->Bt.p, m, G, ld, m);
     const bool marked = ctx->ph2_marked;
     ctx->ph2_mark = nullptr;
     ctx->ph2_marked = false;
+    ctx->x_colmax = nullptr;
     FKF_TRY(ast);
     if (r > 0 && !marked) FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, st));
     FKF_TRY(weight_products(f, m, HWA, nm));

@@ -960,20 +960,26 @@ fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
 }
 
 // Split X of one pass (nc columns) on stream st; format 2 first computes the
-// column scales (returned in cs: scales, then inverse scales).
+// column scales (returned in cs: scales, then inverse scales) from the column
+// maxima of |X|, scanned here unless the caller supplies them (cmax_in).
 template <int F>
-fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaStream_t st, float*& cs) {
+fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaStream_t st, float*& cs,
+                         const unsigned* cmax_in) {
   fkf_ctx* ctx = h->ctx;
   const int64_t P = h->tc_panel;
   const int nct = (int)cdiv(nc, kN);
   cs = nullptr;
   if (fmt_of(F) == 2) {
-    unsigned* cmax = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
+    const unsigned* cmax = cmax_in;
     cs = h->tc_col.as<float>();
-    FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned), st));
-    const int64_t rpb = 2048;
-    k_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, st>>>(X, ldx, h->n, nc, rpb, cmax);
-    FKF_LAUNCHED(ctx);
+    if (!cmax) {
+      unsigned* cm = reinterpret_cast<unsigned*>(h->tc_col.as<float>() + 2 * P);
+      FKF_CUDA(ctx, cudaMemsetAsync(cm, 0, (size_t)nc * sizeof(unsigned), st));
+      const int64_t rpb = 2048;
+      k_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, st>>>(X, ldx, h->n, nc, rpb, cm);
+      FKF_LAUNCHED(ctx);
+      cmax = cm;
+    }
     k_colscale<<<(unsigned)cdiv(nc, 256), 256, 0, st>>>(cmax, nc, cs);
     FKF_LAUNCHED(ctx);
   }
@@ -1030,7 +1036,7 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
     const int nct = (int)cdiv(nc, kN);
     FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
     float* cs = nullptr;
-    FKF_TRY(tc_split_pass<F>(h, X + c0, ldx, nc, st, cs));
+    FKF_TRY(tc_split_pass<F>(h, X + c0, ldx, nc, st, cs, ctx->x_colmax ? ctx->x_colmax + c0 : nullptr));
     if (h->n_tcp1 > 0) {
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
       k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph1>{tc_ph1<F>(h, nc), nullptr, nullptr, 0},
@@ -1076,7 +1082,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     const int nc = (int)ncols[f];
     const int nct = (int)cdiv(nc, kN);
     float* cs = nullptr;
-    FKF_TRY(tc_split_pass<F>(h, X[f], ldx[f], nc, st, cs));
+    FKF_TRY(tc_split_pass<F>(h, X[f], ldx[f], nc, st, cs, h->ctx->x_colmax));
     if (h->n_tcp1 > 0) {
       p1.push_back(tc_ph1<F>(h, nc));
       t1.push_back(t1.back() + h->n_tcp1 * nct);
