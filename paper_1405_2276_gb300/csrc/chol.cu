@@ -259,8 +259,13 @@ fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, in
 // block column k+1 by panel k waits for the trailing update of panel k-1
 // (which also wrote block column k+1).  Every other pair of concurrent
 // launches touches disjoint blocks.
-fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws) {
+// A bordered matrix (nf < n): the panels' trailing updates leave the block
+// A22 = A[nf:, nf:] alone, and it becomes the Schur complement in one
+// rank-nf product A22 -= L21 L21^T at the end (a long reduction that runs
+// near the FP64 tile GEMM's rate, instead of nf / kB rank-kB updates).
+fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws, cudaEvent_t schur_done) {
   if (n <= 0 || nf <= 0) return FKF_OK;
+  nf = std::min(nf, n);
   if (ws.bytes < 256) FKF_TRY(dev_alloc(ctx, ws, 256));
   int* flag = ws.as<int>();
   FKF_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
@@ -269,8 +274,8 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
   cudaStream_t bs = ctx->stream, cs = ctx->stream;  // bulk, chain
   cudaEvent_t* evT = nullptr;
   cudaEvent_t* evS = nullptr;
+  if (la || nf < n) FKF_TRY(ctx_side(ctx, 2 * (size_t)nb + 2));
   if (la) {
-    FKF_TRY(ctx_side(ctx, 2 * (size_t)nb + 1));
     cs = ctx->side;
     evT = ctx->side_ev.data();
     evS = evT + nb;
@@ -291,8 +296,10 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       k_trsm_rows<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, cs>>>(P, lda, rem, b, Akk, lda);
       FKF_LAUNCHED(ctx);
       double* C = P + b;  // trailing block at (k0 + b, k0 + b)
+      // entries of the trailing block in A22 (relative index >= skip) wait for the final product
+      const int64_t skip = nf < n ? nf - (k0 + b) : -1;
       if (!la) {
-        FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, C, lda, true));
+        if (skip != 0) FKF_TRY(gemm_sym_f64(ctx, false, true, rem, b, -1.0, P, lda, P, lda, 1.0, C, lda, true, skip));
         continue;
       }
       FKF_CUDA(ctx, cudaEventRecord(evT[k], cs));
@@ -304,9 +311,10 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       }
       const int rem2 = rem - b1;
       FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evT[k], 0));
-      if (rem2 > 0)
+      const int64_t skip2 = nf < n ? nf - (k0 + b + b1) : -1;
+      if (rem2 > 0 && skip2 != 0)
         FKF_TRY(gemm_sym_f64(ctx, false, true, rem2, b, -1.0, P + (int64_t)b1 * lda, lda, P + (int64_t)b1 * lda, lda,
-                             1.0, C + (int64_t)b1 * lda + b1, lda, true));
+                             1.0, C + (int64_t)b1 * lda + b1, lda, true, skip2));
       FKF_CUDA(ctx, cudaEventRecord(evS[k], bs));
     }
     return FKF_OK;
@@ -319,9 +327,30 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
     FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evS[nb], 0));
   }
   FKF_TRY(st);
+  if (nf < n) {  // A22 -= L21 L21^T
+    const double* L21 = A + (int64_t)nf * lda;
+    double* A22 = A + (int64_t)nf * lda + nf;
+    if (schur_done) {
+      FKF_TRY(ctx_side_lo(ctx));
+      cudaEvent_t fac = ctx->side_ev[2 * (size_t)nb + 1];
+      FKF_CUDA(ctx, cudaEventRecord(fac, bs));
+      FKF_CUDA(ctx, cudaStreamWaitEvent(ctx->side_lo, fac, 0));
+      const cudaStream_t saved = ctx->stream;
+      ctx->stream = ctx->side_lo;
+      const fkf_status ss = gemm_sym_f64(ctx, false, true, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda, true);
+      ctx->stream = saved;
+      FKF_TRY(ss);
+      FKF_CUDA(ctx, cudaEventRecord(schur_done, ctx->side_lo));
+    } else {
+      FKF_TRY(gemm_sym_f64(ctx, false, true, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda, true));
+    }
+  }
   int hflag = 0;
   FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, bs));
   FKF_CUDA(ctx, cudaStreamSynchronize(bs));
-  if (hflag) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d, %d pivots)", n, nf);
+  if (hflag) {
+    if (nf < n && schur_done) FKF_CUDA(ctx, cudaStreamWaitEvent(bs, schur_done, 0));  // nothing left in flight
+    return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (n=%d, %d pivots)", n, nf);
+  }
   return FKF_OK;
 }

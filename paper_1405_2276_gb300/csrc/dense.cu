@@ -64,11 +64,12 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm(int M, int N, int K, T al
 // the lower triangle, row-major order), and each computed entry (i >= j) is
 // written to (i, j) and, with MIRROR, to (j, i) as well (without it the upper
 // triangle is left as it was).  With MIRROR, C must be symmetric on entry
-// when beta is not zero.
+// when beta is not zero.  Entries with i, j >= skip are left untouched (tiles
+// entirely among them are not computed).
 template <typename T, bool A_KC, bool B_KC, bool MIRROR>
 __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha, const T* __restrict__ A,
                                                            int64_t lda, const T* __restrict__ B, int64_t ldb,
-                                                           T beta, T* __restrict__ C, int64_t ldc) {
+                                                           T beta, T* __restrict__ C, int64_t ldc, int skip) {
   static_assert(TileCfg<T>::BM == TileCfg<T>::BN, "square tiles");
   __shared__ TileSmem<T> sm;
   constexpr int BM = TileCfg<T>::BM;
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha
   while (bi * (bi + 1) / 2 > t) bi--;
   const int bj = t - bi * (bi + 1) / 2;
   const int m0 = bi * BM, n0 = bj * BM;
+  if (n0 >= skip) return;  // every entry has i >= j >= skip (uniform over the CTA)
   const int mv = min(BM, N - m0), nv = min(BM, N - n0);
   T acc[TileCfg<T>::TM][TileCfg<T>::TN];
   tile_zero<T>(acc);
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha
     for (int j = 0; j < TileCfg<T>::TN; j++) {
       const int c = tile_col<T>(j);
       const int gi = m0 + r, gj = n0 + c;
-      if (c >= nv || gi < gj) continue;
+      if (c >= nv || gi < gj || gj >= skip) continue;
       T* dst = C + (int64_t)gi * ldc + gj;
       const T v = beta == T(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *dst;
       *dst = v;
@@ -213,9 +215,11 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
 
 fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                        bool lower_only) {
+                        bool lower_only, int64_t skip) {
   if (N <= 0) return FKF_OK;
   if (K <= 0) return scale_f64(ctx, N, N, beta, C, ldc);
+  if (skip >= 0 && skip < N && !lower_only) return set_err(ctx, FKF_EINVAL, "gemm_sym_f64: skip needs lower_only");
+  const int sk = (skip < 0 || skip >= N) ? (int)N : (int)skip;
   constexpr int BM = TileCfg<double>::BM;
   const int64_t nb = cdiv(N, BM);
   const unsigned grid = (unsigned)(nb * (nb + 1) / 2);
@@ -223,11 +227,11 @@ fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, do
   if (lower_only) {                                                                                                \
     FKF_MAXSHARED((k_gemm_sym<double, AK, BK, false>));                                                            \
     k_gemm_sym<double, AK, BK, false><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B, \
-                                                                              ldb, beta, C, ldc);               \
+                                                                              ldb, beta, C, ldc, sk);           \
   } else {                                                                                                         \
     FKF_MAXSHARED((k_gemm_sym<double, AK, BK, true>));                                                             \
     k_gemm_sym<double, AK, BK, true><<<grid, kTileThreads, 0, ctx->stream>>>((int)N, (int)K, alpha, A, lda, B,  \
-                                                                             ldb, beta, C, ldc);                \
+                                                                             ldb, beta, C, ldc, sk);            \
   }
   if (!ta && !tb) {
     FKF_SYM_LAUNCH(true, false)

@@ -11,10 +11,12 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
 // gemm_f64 for a symmetric N x N result (op(A) op(B) symmetric, C symmetric
 // when beta != 0): computes the lower tiles and mirrors them, so C comes out
 // exactly symmetric; lower_only: the lower triangle alone is written (for
-// consumers that read only it, such as the blocked Cholesky).
+// consumers that read only it, such as the blocked Cholesky).  skip in
+// [0, N) (lower_only only): entries (i, j) with i, j >= skip are left as they
+// were.
 fkf_status gemm_sym_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t N, int64_t K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                        bool lower_only = false);
+                        bool lower_only = false, int64_t skip = -1);
 fkf_status gemm_f32(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                     int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
 // C (M x N, FP64) = A^T B with A: K x M, B: K x N (row-major), K long.
@@ -39,7 +41,12 @@ fkf_status scale_f32(fkf_ctx* ctx, int64_t M, int64_t N, float beta, float* C, i
 // when i was pivoted before k.  Synchronises once per 32 pivots.
 fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, int max_rank, double* Lp, int64_t ldl,
                      DevBuf& ws, int* rank_out);
-fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws);
+// schur_done (nf < n): the Schur complement is formed by one product
+// A22 -= L21 L21^T on the context's low-priority stream after the
+// factorisation and schur_done is recorded after it; the caller waits on it
+// before reading A22 (the factor itself is complete on return).
+fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws,
+                            cudaEvent_t schur_done = nullptr);
 // Solve S x = b (nrhs contiguous vectors of length n) with the factor of
 // chol_blocked_f64 (ld ldl).
 fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs);

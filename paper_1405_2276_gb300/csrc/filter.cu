@@ -761,6 +761,7 @@ struct fkf_filter {
   // HW gathered (main stream) -> HWD and the product HWD HW^T on the
   // low-priority stream, beside the H-apply -> consumed on the main stream
   cudaEvent_t ev_hw = nullptr, ev_p = nullptr;
+  cudaEvent_t ev_schur = nullptr;  // the kept-basis weight E' (Schur complement) is formed
   DevBuf Pw;  // HWD HW^T (m x m, lower triangle)
   DevBuf xcmax;  // column maxima of the dense H^T (FP32 state), for the H-apply's split
   double phase_ms[6] = {};
@@ -871,6 +872,7 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
   for (int i = 0; i < 7; i++) cudaEventCreate(&f->ev[i]);
   cudaEventCreateWithFlags(&f->ev_hw, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&f->ev_p, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&f->ev_schur, cudaEventDisableTiming);
   *out = f;
   return FKF_OK;
 }
@@ -881,6 +883,7 @@ void filter_destroy(fkf_filter* f) {
     if (f->ev[i]) cudaEventDestroy(f->ev[i]);
   if (f->ev_hw) cudaEventDestroy(f->ev_hw);
   if (f->ev_p) cudaEventDestroy(f->ev_p);
+  if (f->ev_schur) cudaEventDestroy(f->ev_schur);
   delete f;
 }
 
@@ -1050,6 +1053,10 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   const int32_t* col = f->col.as<int32_t>();
   const double* val = f->val.as<double>();
 
+  // work a previous step left on the low-priority stream (if it failed part-way)
+  // is finished before this step touches the buffers it reads or writes
+  FKF_CUDA(ctx, cudaStreamWaitEvent(st, f->ev_p, 0));
+  FKF_CUDA(ctx, cudaStreamWaitEvent(st, f->ev_schur, 0));
   FKF_CUDA(ctx, cudaEventRecord(f->ev[0], st));
   const int nm = r + m;
   double* HWA = f->HWA.as<double>();
@@ -1175,7 +1182,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     k_aug_rows<<<nblk(lda_aug * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), diag ? f->D.as<double>() : nullptr,
                                                  diag ? nullptr : Dfc, alpha1, Eaug, lda_aug);
     FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_blocked_f64(ctx, m + r, m, S, lda_aug, f->cholws));
+    FKF_TRY(chol_blocked_f64(ctx, m + r, m, S, lda_aug, f->cholws, f->ev_schur));
   } else {
     FKF_TRY(chol_blocked_f64(ctx, m, m, S, lda_aug, f->cholws));
   }
@@ -1202,7 +1209,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaEventRecord(f->ev[3], st));
   if (kept) {
     double* Dn2 = f->Dfn.as<double>();
-    // D' = alpha' I - E' (E' = trailing r x r block of the augmented factorisation)
+    // D' = alpha' I - E' (E' = trailing r x r block of the augmented factorisation,
+    // formed beside the solve for z and the mean update)
+    FKF_CUDA(ctx, cudaStreamWaitEvent(st, f->ev_schur, 0));
     k_lincomb_ld<<<nblk((int64_t)r * r), 256, 0, st>>>(r, -1.0, S + (int64_t)m * lda_aug + m, lda_aug, alpha1, Dn2);
     FKF_LAUNCHED(ctx);
     for (int e = 4; e < 7; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
