@@ -35,10 +35,22 @@ constexpr int kPB = 32;             // pivots per panel of the pivoted Cholesky
 __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int64_t lda, int b,
                                                     int* __restrict__ flag) {
   __shared__ double a[kB][kB + 1];
+  // the lower triangle's entries ordered by column, last column first:
+  // entry t = (row, column) packed as row << 8 | column, so that the entries
+  // right of column j are the first (b-j-1)(b-j)/2 (the update of step j
+  // issues no FP64 instruction for entries it leaves alone)
+  __shared__ unsigned short tri[kB * (kB + 1) / 2];
   const int t = threadIdx.x;
   for (int e = t; e < kB * kB; e += blockDim.x) {
     const int i = e / kB, j = e % kB;
     a[i][j] = (i < b && j <= i) ? A[(int64_t)i * lda + j] : 0.0;
+  }
+  for (int e = t; e < b * (b + 1) / 2; e += blockDim.x) {
+    int u = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);  // columns b-u.. hold the first u(u+1)/2
+    while (u * (u - 1) / 2 > e) u--;
+    while (u * (u + 1) / 2 <= e) u++;
+    const int c = b - u, i = c + (e - u * (u - 1) / 2);
+    tri[e] = (unsigned short)(i << 8 | c);
   }
   __syncthreads();
   for (int j = 0; j < b; j++) {
@@ -54,10 +66,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
     const double inv = 1.0 / a[j][j];
     if (t > j && t < b) a[t][j] *= inv;
     __syncthreads();
-    // a[i][l] -= a[i][j] a[l][j] for j < l <= i < b: thread t -> row i = j+1 + t/32, column l = j+1 + t%32
-    for (int e = t; e < kB * kB; e += blockDim.x) {
-      const int i = j + 1 + e / kB, l = j + 1 + e % kB;
-      if (i < b && l <= i) a[i][l] -= a[i][j] * a[l][j];
+    // a[i][l] -= a[i][j] a[l][j] for j < l <= i < b
+    const int cnt = (b - j - 1) * (b - j) / 2;
+    for (int e = t; e < cnt; e += blockDim.x) {
+      const int i = tri[e] >> 8, l = tri[e] & 255;
+      a[i][l] -= a[i][j] * a[l][j];
     }
     __syncthreads();
   }
