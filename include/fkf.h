@@ -24,6 +24,11 @@
  *  - Pointers named *_dev are device pointers on the context's device; all
  *    others are host pointers unless a flag says otherwise.  Device work is
  *    issued on the context's stream; host outputs are complete on return.
+ *    Inside a call the library may also run work on two streams of its own
+ *    (a high-priority one for the Cholesky's critical chain, a low-priority
+ *    one for FP64 products that share the SMs with the tensor-core H-apply),
+ *    ordered against the context's stream by events: seen from the context's
+ *    stream, every call's work is complete where the call's own work is.
  *  - Point order: all N-indexed inputs/outputs use the caller's original
  *    point order (the library permutes internally to cluster order).
  *  - Dense N x n blocks of vectors are row-major: element (i, j) at
@@ -104,7 +109,9 @@ typedef struct {
 
 /* ---- context -------------------------------------------------------------
  * fkf_create: bind to CUDA device `device` and the CUDA stream `cuda_stream`
- * (a cudaStream_t, or NULL for a library-created stream).  */
+ * (a cudaStream_t, or NULL for a library-created stream).  The context
+ * creates its internal streams on first use and destroys them in
+ * fkf_destroy.  */
 fkf_status fkf_create(fkf_ctx** out, int32_t device, void* cuda_stream);
 void fkf_destroy(fkf_ctx* ctx);
 const char* fkf_last_error(const fkf_ctx* ctx);
