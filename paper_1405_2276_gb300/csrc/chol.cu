@@ -41,16 +41,19 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
   // issues no FP64 instruction for entries it leaves alone)
   __shared__ unsigned short tri[kB * (kB + 1) / 2];
   const int t = threadIdx.x;
-  for (int e = t; e < kB * kB; e += blockDim.x) {
-    const int i = e / kB, j = e % kB;
-    a[i][j] = (i < b && j <= i) ? A[(int64_t)i * lda + j] : 0.0;
-  }
   for (int e = t; e < b * (b + 1) / 2; e += blockDim.x) {
     int u = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);  // columns b-u.. hold the first u(u+1)/2
     while (u * (u - 1) / 2 > e) u--;
     while (u * (u + 1) / 2 <= e) u++;
     const int c = b - u, i = c + (e - u * (u - 1) / 2);
     tri[e] = (unsigned short)(i << 8 | c);
+  }
+  // launched early behind the previous kernel of the stream (programmatic
+  // dependent launch): its results are visible after this wait
+  cudaGridDependencySynchronize();
+  for (int e = t; e < kB * kB; e += blockDim.x) {
+    const int i = e / kB, j = e % kB;
+    a[i][j] = (i < b && j <= i) ? A[(int64_t)i * lda + j] : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < b; j++) {
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
   __shared__ double l[kB][kB + 1];
   __shared__ double dinv[kB];
   const int t = threadIdx.x;
+  cudaGridDependencySynchronize();  // launched early behind the diagonal block's kernel
   for (int e = t; e < kB * kB; e += blockDim.x) {
     const int i = e / kB, j = e % kB;
     l[i][j] = (i < b && j <= i) ? L[(int64_t)i * lda + j] : 0.0;
@@ -231,6 +235,24 @@ __global__ void k_diag_of(int n, const double* __restrict__ A, int64_t lda, doub
   if (i < n) d[i] = A[(int64_t)i * lda + i];
 }
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream finishes and waits for it on the device
+// (cudaGridDependencySynchronize), which hides the launch gap of the chain.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), unsigned grid, unsigned block, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<P>(args)...);
+}
+
 }  // namespace
 
 fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, int max_rank, double* Lp, int64_t ldl,
@@ -301,12 +323,13 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       const int k0 = k * kB;
       const int b = std::min(kB, nf - k0);
       double* Akk = A + (int64_t)k0 * lda + k0;
-      k_potrf_diag<<<1, 256, 0, cs>>>(Akk, lda, b, flag);
+      FKF_CUDA(ctx, launch_pdl(k_potrf_diag, 1, 256, cs, Akk, lda, b, flag));
       FKF_LAUNCHED(ctx);
       const int rem = n - k0 - b;
       if (rem <= 0) continue;
       double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
-      k_trsm_rows<<<(unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, 0, cs>>>(P, lda, rem, b, Akk, lda);
+      FKF_CUDA(ctx, launch_pdl(k_trsm_rows, (unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, cs, P, lda,
+                               (int64_t)rem, b, (const double*)Akk, lda));
       FKF_LAUNCHED(ctx);
       double* C = P + b;  // trailing block at (k0 + b, k0 + b)
       // entries of the trailing block in A22 (relative index >= skip) wait for the final product
