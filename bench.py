@@ -119,13 +119,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_seed(rank):
+    """Seed of rank `rank`'s synthetic workload: every replica filters its own data."""
+    import synth
+
+    return synth.BASE_SEED + 2 + 1000 * rank
+
+
+def max_over_ranks(t_local, world, device="cuda"):
+    """The slowest rank's time (every rank calls this; world 1: t_local)."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(steps_per_rank, t_max, world):
+    """Job throughput of `world` replicas that each ran `steps_per_rank` steps, timed by the slowest."""
+    return world * steps_per_rank / t_max
+
+
 def make_workload(steps, seed_offset=0):
     import synth
 
     w = WORKLOAD
     t0 = time.time()
     wl = synth.tomography_workload(w["grid"], w["src"], w["rec"], steps, w["ell"], w["sigma2"], w["noise"],
-                                   seed=synth.BASE_SEED + 2 + 1000 * seed_offset)
+                                   seed=replica_seed(seed_offset))
     log(f"[bench] workload: N={wl['points'].shape[0]} m={wl['H'].nrows} nnz={wl['H'].nnz} "
         f"steps={steps} ({time.time() - t0:.1f}s)")
     return wl
@@ -212,14 +236,8 @@ def run_gpu(args, rank, world):
     clk = clocks.stop()
     launches = fkf.fkf_launch_count(ctx) - l0
     libcalls = fkf.fkf_library_call_count(ctx) - c0
-    t_local = ms_dev / 1e3
-    if world > 1:
-        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_local
-    res["fp32"] = dict(ms_per_step=1e3 * t_max / args.steps, steps_per_s=world * args.steps / t_max,
+    t_max = max_over_ranks(ms_dev / 1e3, world)
+    res["fp32"] = dict(ms_per_step=1e3 * t_max / args.steps, steps_per_s=replica_value(args.steps, t_max, world),
                        wall_s=wall, phases_ms=(phases / args.steps).tolist(), launches=launches,
                        lib_calls=libcalls, clocks=clk)
     log(f"[bench] FP32 path: {res['fp32']['ms_per_step']:.1f} ms/step; phases(ms) "
@@ -235,16 +253,18 @@ def run_gpu(args, rank, world):
     s_host = np.zeros(n)
     nll = 0.0
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.time()
     for k in range(e2e_steps):
         kk = (args.warmup + args.steps + k) % total_steps
         nll = fkf.fkf_filter_step(f32, ys_p[kk], m, rowptr_p, col_p, val_p, None, w["noise"])
         st = fkf.fkf_filter_get(f32, n, want_D=False)
         s_host = st["s"]
-    e2e_t = time.time() - t0
+    e2e_t = max_over_ranks(time.time() - t0, world)
     h2d = ys_p[0].nbytes + rowptr_p.nbytes + col_p.nbytes + val_p.nbytes
     d2h = 8 + s_host.nbytes
-    res["e2e"] = dict(value=world * e2e_steps / e2e_t, unit="steps/s", h2d_bytes_per_step=int(h2d),
+    res["e2e"] = dict(value=replica_value(e2e_steps, e2e_t, world), unit="steps/s", h2d_bytes_per_step=int(h2d),
                       d2h_bytes_per_step=int(d2h), steps=e2e_steps, nll_last=nll,
                       path=fkf.fkf_filter_get_stats(f32)["last_path"])
     log(f"[bench] FP32 path end to end (host buffers): {res['e2e']}")
