@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(kTileThreads) k_gemm_sym(int N, int K, T alpha
 
 // Matrix-vector form of the FP64 GEMM (N = 1): y_i = sum_k op(A)(i, k) x_k,
 // C[i] = alpha y_i + beta C[i].  Rows of A (not transposed): one warp per
-// output, lanes over k, shuffle reduction; columns (transposed): one thread
-// per output, loop over k (coalesced across outputs).
+// output, lanes over k, shuffle reduction; columns (transposed): a CTA per 32
+// outputs, lanes over outputs (coalesced), its warps splitting k.
+constexpr int kGemvTThreads = 1024;  // CTA of the transposed GEMV
 __global__ void k_gemv_f64(int M, int K, bool ta, double alpha, const double* __restrict__ A, int64_t lda,
                            const double* __restrict__ x, int64_t incx, double beta, double* __restrict__ C,
                            int64_t ldc) {
@@ -119,11 +120,22 @@ __global__ void k_gemv_f64(int M, int K, bool ta, double alpha, const double* __
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) C[(int64_t)i * ldc] = beta == 0.0 ? alpha * s : alpha * s + beta * C[(int64_t)i * ldc];
   } else {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
+    // 32 outputs per CTA of kGemvTThreads (lanes over outputs: coalesced
+    // rows of A); warp w sums k = w, w + nw, ...; the warps' partial sums of an
+    // output are added in warp order (deterministic)
+    __shared__ double part[kGemvTThreads / 32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
     double s = 0.0;
-    for (int k = 0; k < K; k++) s += A[(int64_t)k * lda + i] * x[(int64_t)k * incx];
-    C[(int64_t)i * ldc] = beta == 0.0 ? alpha * s : alpha * s + beta * C[(int64_t)i * ldc];
+    if (i < M)
+      for (int k = w; k < K; k += nw) s += A[(int64_t)k * lda + i] * x[(int64_t)k * incx];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < M) {
+      double t = 0.0;
+      for (int q = 0; q < nw; q++) t += part[q][lane];
+      C[(int64_t)i * ldc] = beta == 0.0 ? alpha * t : alpha * t + beta * C[(int64_t)i * ldc];
+    }
   }
 }
 
@@ -205,8 +217,9 @@ fkf_status gemm_f64(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
   if (N == 1) {
     // op(B)(k, 0) = B[k * ldb] (tb = false) or B[k] (tb = true)
     const int64_t incx = tb ? 1 : ldb;
-    const unsigned grid = ta ? (unsigned)cdiv(M, 256) : (unsigned)cdiv(M * 32, 256);
-    k_gemv_f64<<<grid, 256, 0, ctx->stream>>>((int)M, (int)K, ta, alpha, A, lda, B, incx, beta, C, ldc);
+    const unsigned grid = ta ? (unsigned)cdiv(M, 32) : (unsigned)cdiv(M * 32, 256);
+    k_gemv_f64<<<grid, ta ? kGemvTThreads : 256, 0, ctx->stream>>>((int)M, (int)K, ta, alpha, A, lda, B, incx,
+                                                                  beta, C, ldc);
     FKF_LAUNCHED(ctx);
     return FKF_OK;
   }
