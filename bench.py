@@ -9,8 +9,9 @@ merge, rotation of W and X) on device-resident inputs.  Prints ONE JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica of the filter
-(the path does not shard without an all-to-all), the timing
-is the max over ranks and `value` sums all ranks' steps.
+(one filter step does not shard without an all-to-all that moves the
+column-sharded Gamma H^T into row layout), the timing is the max over ranks
+and `value` sums all ranks' steps.
 """
 
 from __future__ import annotations
