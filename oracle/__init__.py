@@ -13,7 +13,13 @@ Contents (each function cites the passage it follows):
   kalman      -- O1: the textbook Kalman filter with F = I (Alg. standard and
                  the random-walk assumption of Sec. 2.1); O2: the exact
                  cross-covariance recursion for a fixed H, evaluated on sampled
-                 rows (same Kalman algebra, tracking Sigma H^T)
+                 rows (same Kalman algebra, tracking Sigma H^T); O1t: O1 with
+                 the rank control of Alg. lowrankaddition step 4 (rank cap and
+                 relative truncation) applied densely; O1e: the extended filter
+                 of Sec. 4.2 (Alg. extkalman) with the Box-Cox map of Eq.
+                 nonlinear
+  ghep        -- Eq. ghep solved exactly (the definition) and by the randomized
+                 algorithm of App. B (Alg. randomizedghepuncert)
   uq          -- variance, relative entropy and conditional realizations
                  (Sec. 3) computed densely from a covariance matrix, and the
                  paper's low-rank representation (Eq. sigmakk) recovered

@@ -19,6 +19,25 @@ be run for any subset of rows; H s is tracked as its own m-vector.  Per step
     C = C- - C- S^-1 T-, T = T- - T- S^-1 T-, c = c- - rowsum(C- S^-1 * C-)
 with G = Gamma H^T and A = H Gamma H^T.
 
+O1t `kf_dense_truncated`: O1 followed, after every update, by the rank control
+of Alg. lowrankaddition step 4 applied to the dense posterior: the correction
+alpha_k Gamma - Sigma_k|k is written as W D W^T with W^T Gamma^-1 W = I
+(Eq. sigmakk, recovered densely), and only the modes that the low-rank filter
+keeps survive: at most r_max of them, the largest merged eigenvalues theta,
+and only those with theta > trunc_tol * max(theta).  theta is the eigenvalue
+of the merged information term (Sec. 2.4), related to the kept weight by
+D = alpha^2 theta / (1 + alpha theta), i.e. theta = d / (alpha (alpha - d)),
+which is increasing in d.  The mean update of the next step uses the truncated
+covariance, as the low-rank filter does.
+
+O1e `ekf_dense`: the extended Kalman filter of Sec. 4.2 (Alg. extkalman) for the
+measurement map y = h(x) + v, h(x) = H s(x), where x is the filtered
+(transformed) field and s(x) = ((x + a) / a)^a inverts the Box-Cox transform
+x = a (s^(1/a) - 1) of Eq. nonlinear.  Each step linearises h at the predicted
+mean: H_k = H diag(s'(x_pred)), s'(x) = ((x + a) / a)^(a - 1); innovation
+nu = y - h(x_pred); then the O1 update with H_k (optionally followed by the
+truncation of O1t).
+
 Readings (the paper's wording is at odds with itself on these):
   * time index: at step k the filter predicts from k-1 to k and updates with
     y_k (the algorithms use y_k with H s_k);
@@ -64,6 +83,100 @@ def kf_dense(Gamma, steps, s0=None, alpha0=0.0, keep_cov=True):
         rec = dict(s=s.copy(), var=np.diag(Sigma).copy(), nll=float(nll))
         if keep_cov:
             rec["Sigma"] = Sigma.copy()
+        out.append(rec)
+    return out
+
+
+def truncate_lowrank(Sigma, Gamma, alpha, r_max=None, trunc_tol=0.0):
+    """Rank control of Alg. lowrankaddition step 4 on a dense posterior.
+
+    alpha Gamma - Sigma = W diag(d) W^T with W^T Gamma^-1 W = I is found densely
+    (Gamma = L L^T, L^-1 (alpha Gamma - Sigma) L^-T = Q diag(d) Q^T, W = L Q).
+    Modes are ranked by theta = d / (alpha (alpha - d)) (the merged eigenvalue);
+    the r_max largest with theta > trunc_tol * max(theta) and theta > 0 are kept.
+    Returns (truncated Sigma, kept d (descending), number kept)."""
+    L = linalg.cholesky(Gamma, lower=True)
+    Mt = linalg.solve_triangular(L, alpha * Gamma - Sigma, lower=True)
+    Mt = linalg.solve_triangular(L, Mt.T, lower=True).T
+    Mt = 0.5 * (Mt + Mt.T)
+    d, Q = np.linalg.eigh(Mt)
+    order = np.argsort(d)[::-1]
+    d, Q = d[order], Q[:, order]
+    theta = np.where(d < alpha, d / (alpha * np.maximum(alpha - d, 1e-300)), np.inf)
+    tmax = theta[0] if theta.size else 0.0
+    keep = 0
+    limit = theta.size if r_max is None else min(r_max, theta.size)
+    while keep < limit and theta[keep] > 0 and theta[keep] > trunc_tol * tmax:
+        keep += 1
+    W = L @ Q[:, :keep]
+    Sig = alpha * Gamma - (W * d[:keep]) @ W.T
+    return 0.5 * (Sig + Sig.T), d[:keep].copy(), keep
+
+
+def _kf_update(s, Sigma_p, H, R, y_minus_h):
+    m = H.shape[0]
+    PHt = Sigma_p @ H.T
+    S = H @ PHt + np.diag(_as_rvec(R, m))
+    cf = linalg.cho_factor(S, lower=True)
+    z = linalg.cho_solve(cf, y_minus_h)
+    K = linalg.cho_solve(cf, PHt.T).T
+    s = s + K @ y_minus_h
+    Sigma = Sigma_p - K @ PHt.T
+    Sigma = 0.5 * (Sigma + Sigma.T)
+    logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+    nll = 0.5 * (y_minus_h @ z + logdet + m * np.log(2.0 * np.pi))
+    return s, Sigma, float(nll)
+
+
+def kf_dense_truncated(Gamma, steps, r_max=None, trunc_tol=0.0, s0=None, alpha0=0.0):
+    """Run O1t: O1 with the rank control of `truncate_lowrank` after every
+    update.  steps: iterable of (y, H dense, R).  Returns per-step dicts with
+    s, Sigma, var, nll, r (modes kept) and d (kept weights, descending)."""
+    N = Gamma.shape[0]
+    s = np.zeros(N) if s0 is None else np.array(s0, dtype=np.float64)
+    alpha = alpha0
+    Sigma = alpha0 * Gamma.copy()
+    out = []
+    for y, H, R in steps:
+        alpha = alpha + 1.0
+        Sigma_p = Sigma + Gamma
+        s, Sigma, nll = _kf_update(s, Sigma_p, H, R, y - H @ s)
+        Sigma, d, r = truncate_lowrank(Sigma, Gamma, alpha, r_max, trunc_tol)
+        out.append(dict(s=s.copy(), Sigma=Sigma.copy(), var=np.diag(Sigma).copy(), nll=nll, r=r, d=d))
+    return out
+
+
+def boxcox_state(x, a):
+    """Eq. nonlinear, inverse direction: s = ((x + a) / a)^a."""
+    return np.power((np.asarray(x, dtype=np.float64) + a) / a, a)
+
+
+def boxcox_state_derivative(x, a):
+    """ds/dx of `boxcox_state`: ((x + a) / a)^(a - 1)."""
+    return np.power((np.asarray(x, dtype=np.float64) + a) / a, a - 1.0)
+
+
+def ekf_dense(Gamma, steps, a, s0=None, alpha0=0.0, r_max=None, trunc_tol=None):
+    """Run O1e (Alg. extkalman written densely).  steps: iterable of
+    (y, H dense (m x N), R) with y = H s(x_k) + v.  With r_max / trunc_tol the
+    O1t rank control follows every update.  Returns per-step dicts with s (the
+    filtered field x), Sigma, var, nll and, when truncating, r and d."""
+    N = Gamma.shape[0]
+    x = np.zeros(N) if s0 is None else np.array(s0, dtype=np.float64)
+    alpha = alpha0
+    Sigma = alpha0 * Gamma.copy()
+    out = []
+    for y, H, R in steps:
+        alpha = alpha + 1.0
+        Sigma_p = Sigma + Gamma
+        Hk = H * boxcox_state_derivative(x, a)[None, :]  # H diag(s'(x_pred))
+        nu = y - H @ boxcox_state(x, a)
+        x, Sigma, nll = _kf_update(x, Sigma_p, Hk, R, nu)
+        rec = dict(nll=nll)
+        if r_max is not None or trunc_tol is not None:
+            Sigma, d, r = truncate_lowrank(Sigma, Gamma, alpha, r_max, trunc_tol or 0.0)
+            rec.update(r=r, d=d)
+        rec.update(s=x.copy(), Sigma=Sigma.copy(), var=np.diag(Sigma).copy())
         out.append(rec)
     return out
 

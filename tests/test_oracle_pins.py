@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 from scipy import linalg, special, stats
 
-from oracle import covariance, kalman, matern, uq
+from oracle import covariance, ghep, kalman, matern, uq
 import synth
 
 
@@ -267,3 +267,194 @@ def test_batch_gradients_match_central_differences_of_dense_kf():
         sm_[i] -= h
         fd = (total(sigma2, rho, ys, sp) - total(sigma2, rho, ys, sm_)) / (2 * h)
         assert abs(fd - gs0[i]) < 1e-6 * max(1, abs(fd))
+
+
+# ----------------------------------------------------------------------------
+# O1t: rank control of the low-rank posterior (Alg. lowrankaddition step 4)
+# ----------------------------------------------------------------------------
+def test_truncation_equals_generalized_eigen_truncation():
+    """truncate_lowrank keeps the leading generalized eigenpairs of
+    (alpha Gamma - Sigma) u = d Gamma u (scipy's generalized eigensolver, an
+    independent route), and the whitened error equals the first dropped d
+    (best rank-r approximation in the Gamma^-1 metric)."""
+    rng = np.random.default_rng(21)
+    Gamma, steps = _random_problem(rng, 25, [4, 5, 3])
+    res = kalman.kf_dense(Gamma, steps)
+    alpha = float(len(steps))
+    Sigma = res[-1]["Sigma"]
+    Delta = alpha * Gamma - Sigma
+    d_all, U = linalg.eigh(0.5 * (Delta + Delta.T), Gamma)  # U^T Gamma U = I
+    d_all, U = d_all[::-1], U[:, ::-1]
+    for r_max in (3, 7, 11):
+        St, d, r = kalman.truncate_lowrank(Sigma, Gamma, alpha, r_max=r_max)
+        assert r == r_max
+        np.testing.assert_allclose(d, d_all[:r_max], rtol=1e-9, atol=1e-12)
+        W = Gamma @ U[:, :r_max]
+        ref = alpha * Gamma - (W * d_all[:r_max]) @ W.T
+        np.testing.assert_allclose(St, ref, rtol=1e-9, atol=1e-11)
+        L = np.linalg.cholesky(Gamma)
+        E = linalg.solve_triangular(L, St - Sigma, lower=True)
+        E = linalg.solve_triangular(L, E.T, lower=True).T
+        assert abs(np.linalg.norm(E, 2) - d_all[r_max]) < 1e-8 * d_all[0]
+    # rank of the correction after 3 steps is at most sum m_k = 12
+    assert np.sum(d_all > 1e-10 * d_all[0]) <= 12
+
+
+def test_truncated_filter_without_cap_is_o1_and_caps_rank():
+    rng = np.random.default_rng(22)
+    Gamma, steps = _random_problem(rng, 20, [3, 4, 2, 5])
+    a = kalman.kf_dense(Gamma, steps)
+    b = kalman.kf_dense_truncated(Gamma, steps, r_max=None, trunc_tol=0.0)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y["Sigma"], x["Sigma"], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(y["s"], x["s"], rtol=1e-10, atol=1e-12)
+        assert abs(x["nll"] - y["nll"]) < 1e-10 * abs(x["nll"])
+    c = kalman.kf_dense_truncated(Gamma, steps, r_max=5, trunc_tol=1e-12)
+    assert [q["r"] for q in c] == [3, 5, 5, 5]
+    # every truncated posterior stays symmetric positive definite
+    for q in c:
+        assert np.linalg.eigvalsh(q["Sigma"]).min() > 0
+    # trunc_tol: theta = d / (alpha (alpha - d)) of every kept mode above tol * max
+    e = kalman.kf_dense_truncated(Gamma, steps, trunc_tol=1e-2)
+    for k, q in enumerate(e):
+        al = k + 1.0
+        th = q["d"] / (al * (al - q["d"]))
+        assert np.all(th > 1e-2 * th[0])
+
+
+# ----------------------------------------------------------------------------
+# O1e: extended Kalman filter with the Box-Cox map (Sec. 4.2, Alg. extkalman)
+# ----------------------------------------------------------------------------
+def test_boxcox_map_inverse_derivative_and_log_limit():
+    """s(x) inverts Eq. nonlinear's x = a (s^(1/a) - 1); its derivative matches
+    central differences; a -> infinity gives s = exp(x) (the log-transform
+    limit the paper names)."""
+    x = np.linspace(-0.9, 2.0, 37)
+    for a in (1.0, 2.0, 4.0, 6.0, 2.5):
+        s = kalman.boxcox_state(x, a)
+        np.testing.assert_allclose(a * (s ** (1.0 / a) - 1.0), x, rtol=1e-12, atol=1e-13)
+        h = 1e-6
+        fd = (kalman.boxcox_state(x + h, a) - kalman.boxcox_state(x - h, a)) / (2 * h)
+        np.testing.assert_allclose(kalman.boxcox_state_derivative(x, a), fd, rtol=1e-7)
+    np.testing.assert_allclose(kalman.boxcox_state(x, 1e8), np.exp(x), rtol=1e-6)
+
+
+def test_ekf_with_identity_map_is_the_linear_filter():
+    """a = 1: s(x) = x + 1 is affine with unit Jacobian, so the EKF equals O1
+    on the measurements y - H 1."""
+    rng = np.random.default_rng(23)
+    Gamma, steps = _random_problem(rng, 15, [3, 4, 2])
+    a = kalman.ekf_dense(Gamma, steps, 1.0)
+    b = kalman.kf_dense(Gamma, [(y - H @ np.ones(15), H, R) for y, H, R in steps])
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x["s"], y["s"], rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(x["Sigma"], y["Sigma"], rtol=1e-11, atol=1e-12)
+        assert abs(x["nll"] - y["nll"]) < 1e-11 * abs(y["nll"])
+
+
+def test_ekf_step_is_one_gauss_newton_step():
+    """One EKF step from (x0, Sigma-) equals one Gauss-Newton step of the MAP
+    objective 1/2 |y - h(x)|^2_R^-1 + 1/2 |x - x0|^2_Sigma-^-1 started at x0,
+    solved as a stacked whitened least-squares problem (numpy lstsq)."""
+    rng = np.random.default_rng(24)
+    N, m, a = 18, 5, 4.0
+    Gamma, _ = _random_problem(rng, N, [])
+    H = np.abs(rng.standard_normal((m, N)))
+    R = rng.uniform(0.05, 0.2, m)
+    x0 = 0.3 * rng.standard_normal(N)
+    Sig0 = 0.5 * Gamma
+    y = H @ kalman.boxcox_state(x0 + 0.1 * rng.standard_normal(N), a)
+    out = kalman.ekf_dense(Gamma, [(y, H, R)], a, s0=x0, alpha0=0.5)
+    J = H * kalman.boxcox_state_derivative(x0, a)[None, :]
+    Lp = np.linalg.cholesky(Sig0 + Gamma)
+    top = J / np.sqrt(R)[:, None]
+    bot = linalg.solve_triangular(Lp, np.eye(N), lower=True)
+    rhs = np.concatenate([(y - H @ kalman.boxcox_state(x0, a)) / np.sqrt(R), np.zeros(N)])
+    delta = np.linalg.lstsq(np.vstack([top, bot]), rhs, rcond=None)[0]
+    np.testing.assert_allclose(out[0]["s"], x0 + delta, rtol=1e-9, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------
+# Eq. ghep: exact and randomized (App. B, Alg. randomizedghepuncert)
+# ----------------------------------------------------------------------------
+def _ghep_problem(rng, N=40, m=9):
+    pts = rng.uniform(size=(N, 2))
+    Gamma = covariance.dense_gamma(pts, 1.5, 0.3, 1.0)
+    H = rng.standard_normal((m, N))
+    R = rng.uniform(0.05, 0.2, m)
+    return Gamma, H, R
+
+
+def test_ghep_exact_identities_and_data_space_spectrum():
+    """U^T Gamma^-1 U = I, Gamma^-1 U Lambda U^T Gamma^-1 = H^T R^-1 H
+    (Eq. geneigendecomposition), and the nonzero eigenvalues are those of the
+    data-space matrix R^-1/2 H Gamma H^T R^-1/2 (numpy eigvalsh)."""
+    rng = np.random.default_rng(31)
+    Gamma, H, R = _ghep_problem(rng)
+    lam, U = ghep.ghep_exact(H, R, Gamma)
+    assert lam.shape[0] == H.shape[0]
+    Gi = np.linalg.inv(Gamma)
+    np.testing.assert_allclose(U.T @ Gi @ U, np.eye(lam.shape[0]), atol=1e-9)
+    A = H.T @ (H / R[:, None])
+    np.testing.assert_allclose(Gi @ (U * lam) @ U.T @ Gi, A, rtol=0, atol=1e-8 * np.abs(A).max())
+    rs = 1.0 / np.sqrt(R)
+    ds = np.linalg.eigvalsh((rs[:, None] * (H @ Gamma @ H.T)) * rs[None, :])[::-1]
+    np.testing.assert_allclose(lam, ds, rtol=1e-9)
+
+
+def test_mgs_qr_in_weighted_inner_product():
+    rng = np.random.default_rng(32)
+    Gamma, _, _ = _ghep_problem(rng)
+    Y = rng.standard_normal((Gamma.shape[0], 7))
+    Qh, Rm = ghep.mgs_qr_weighted(Y, Gamma)
+    np.testing.assert_allclose(Qh.T @ Gamma @ Qh, np.eye(7), atol=1e-12)
+    np.testing.assert_allclose(Qh @ Rm, Y, rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.tril(Rm, -1), 0)
+
+
+def test_randomized_ghep_exact_when_sketch_spans_range():
+    """k + p = rank(A): the sketch spans the range of B^-1 A, so the randomized
+    algorithm returns the exact nonzero spectrum; also for an A of exact rank
+    k < m (a rank-deficient H).  (A sketch wider than the rank would ask the
+    Gram-Schmidt step to normalise rounding noise.)"""
+    rng = np.random.default_rng(33)
+    Gamma, H, R = _ghep_problem(rng)
+    lam, U = ghep.ghep_exact(H, R, Gamma)
+    Om = rng.standard_normal((Gamma.shape[0], H.shape[0]))
+    lr, Ur = ghep.ghep_randomized(H, R, Gamma, Om, H.shape[0])
+    np.testing.assert_allclose(lr, lam, rtol=1e-9)
+    Gi = np.linalg.inv(Gamma)
+    A = H.T @ (H / R[:, None])
+    np.testing.assert_allclose(Gi @ (Ur * lr) @ Ur.T @ Gi, A, rtol=0, atol=1e-8 * np.abs(A).max())
+    np.testing.assert_allclose(Ur.T @ Gi @ Ur, np.eye(lr.shape[0]), atol=1e-9)
+    # rank-4 operator, sketch of 4 columns
+    H4 = rng.standard_normal((9, 4)) @ rng.standard_normal((4, Gamma.shape[0]))
+    l4, _ = ghep.ghep_exact(H4, R, Gamma, rel_tol=1e-10)
+    assert l4.shape[0] == 4
+    lr4, _ = ghep.ghep_randomized(H4, R, Gamma, rng.standard_normal((Gamma.shape[0], 4)), 4)
+    np.testing.assert_allclose(lr4, l4, rtol=1e-8)
+
+
+def test_randomized_ghep_ritz_bounds():
+    """k + p < rank: Rayleigh-Ritz values are lower bounds of the exact
+    eigenvalues and, with eps = |(I - Q Q^T B) B^-1 A|_B, |lam - lam~| <= 2 eps
+    (App. B's bound)."""
+    rng = np.random.default_rng(34)
+    Gamma, H, R = _ghep_problem(rng, N=60, m=30)
+    lam, _ = ghep.ghep_exact(H, R, Gamma)
+    k, p = 6, 4
+    Om = rng.standard_normal((Gamma.shape[0], k + p))
+    lr, Ur = ghep.ghep_randomized(H, R, Gamma, Om, k)
+    assert np.all(lr <= lam[:k] * (1 + 1e-12))
+    # eps from the B-orthonormal basis of the sketch (Q = Gamma Qhat, Q^T B Q = I)
+    A = H.T @ (H / R[:, None])
+    Qh, _ = ghep.mgs_qr_weighted(A @ Om, Gamma)
+    Q = Gamma @ Qh
+    B = np.linalg.inv(Gamma)
+    C = Gamma @ A
+    Eop = (np.eye(Gamma.shape[0]) - Q @ Q.T @ B) @ C
+    ev, V = np.linalg.eigh(B)
+    Bh = (V * np.sqrt(ev)) @ V.T
+    Bmh = (V / np.sqrt(ev)) @ V.T
+    eps = np.linalg.norm(Bh @ Eop @ Bmh, 2)
+    assert np.all(np.abs(lam[:k] - lr) <= 2 * eps * (1 + 1e-9))
