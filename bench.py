@@ -2,9 +2,17 @@
 workload (N = 262,144 cells, m = 1024 rays = 32 x 32 source/receiver pairs,
 Matern nu = 1/2, ell = 0.05, R = 1e-4 I), FP32 path vs FP64 path.
 
-One step = one general-path filter step (densify H^T, H-apply Gamma_H H^T,
-gathers, innovation and mean update, data-space GEP, Gamma^-1-orthonormal
-merge, rotation of W and X) on device-resident inputs.  Prints ONE JSON line.
+The headline `value` times the filter step as the library takes it on this
+workload's fixed ray geometry, on device-resident inputs: densify H^T, the
+H-apply Gamma_H H^T, the gathers, the basis test and, because a repeated
+geometry brings no information outside span(W) after the first step, the
+kept-basis update (one bordered Cholesky: innovation, mean, NLL and the new
+weight) -- the data-space GEP, the merge eigensolve and the rotation do not
+run in these steps.  The general (merge) step is timed separately with CUDA
+events over the same number of steps, twice: forced through the merge path on
+the fixed geometry (`general_step_merge`), and with a new random ray set every
+step so that new directions really arrive and the rank cap truncates
+(`general_step_new_rays`).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,10 +44,10 @@ WORKLOAD = dict(grid=(512, 512), src=32, rec=32, nu=0.5, ell=0.05, sigma2=1.0, n
 MEDIUM = dict(grid=(256, 256), src=20, rec=20, nu=1.5, ell=0.1, sigma2=1.0, noise=1e-4, leaf=64, eta=1.0,
               aca_tol=1e-8, k_cap=32)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-# DRAM bytes of one H-apply (both k_tc_apply launches, engine 2) on the 512 x 512 workload, from
-# the ncu capture summarised in profiles/happly_tc_dram_large.md (kernel unchanged since)
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, summed over both k_tc_apply launches)
+# of one m = 1024 H-apply of the 512 x 512 operator with the FP16-split engine; None when the kernel
+# has changed since that capture
 HAPPLY_F2_DRAM_BYTES = 34.73e9
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (recipe table)
 
 
 def workload_name():
@@ -248,7 +256,7 @@ def run_gpu(args, rank, world):
     # the same steady-state step as the timed loop above (taken right after it, on the
     # same filter state), its inputs copied from pinned host memory by the library
     # and the mean read back every step
-    e2e_steps = min(args.steps, 5)
+    e2e_steps = args.steps
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     ys_p, rowptr_p, col_p, val_p = pin(ys), pin(h.rowptr), pin(h.col), pin(h.val)
     s_host = np.zeros(n)
@@ -288,55 +296,59 @@ def run_gpu(args, rank, world):
     res["fp32_fixed_h"] = dict(ms_per_step=ms_fx, steps_per_s=1e3 / ms_fx, steps=fx_steps, paths=fx_paths)
     log(f"[bench] FP32 fixed-H fast path: {ms_fx:.2f} ms/step, paths {fx_paths}")
 
-    # the same step forced through the merge path (GEP, orthonormalisation,
-    # merge, rotation) although the fixed geometry brings nothing outside span(W)
-    fu_steps = 2
-    fu_phases = np.zeros(6)
-    fu_stats = []
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for k in range(fu_steps):
-        fkf.fkf_filter_step(f32, ys_d[k % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
-                            flags=fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_FULL_UPDATE, want_nll=False)
-        fu_phases += np.array(fkf.fkf_filter_phase_times(f32))
-        st = fkf.fkf_filter_get_stats(f32)
-        fu_stats.append({k2: st[k2] for k2 in ("r", "gep_rank", "new_dirs", "t_eig", "t_lmax")})
-    ev1.record(stream)
-    ev1.synchronize()
-    ms_fu = ev0.elapsed_time(ev1) / fu_steps
-    res["fp32_full"] = dict(ms_per_step=ms_fu, steps_per_s=1e3 / ms_fu, steps=fu_steps,
-                            phases_ms=(fu_phases / fu_steps).tolist(), step_stats=fu_stats)
-    log(f"[bench] FP32 path, merge forced: {ms_fu:.1f} ms/step; phases(ms) "
-        + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]) + f"; {fu_stats}")
+    # the general (merge) step, timed like the headline: CUDA events on the library stream around
+    # `general` steps.  (1) The fixed geometry forced through the merge path (GEP, orthonormalisation,
+    # merge eigensolve, rotation) although it brings nothing outside span(W).
+    general = max(args.general_steps, 1)
 
-    # time-varying geometry: m new random rays every step (the general step with new
-    # directions: GEP, orthonormalisation, merge with truncation at r_max, rotation)
+    def timed_steps(step_fn, nsteps, stat_keys):
+        phases = np.zeros(6)
+        stats = []
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(nsteps):
+            step_fn(k)
+            phases += np.array(fkf.fkf_filter_phase_times(f32))
+            st = fkf.fkf_filter_get_stats(f32)
+            stats.append({k2: st[k2] for k2 in stat_keys})
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / nsteps
+        return dict(ms_per_step=ms, steps_per_s=1e3 / ms, steps=nsteps, phases_ms=(phases / nsteps).tolist(),
+                    step_stats=stats[-2:], timing="CUDA events on the library stream around the steps")
+
+    res["fp32_full"] = timed_steps(
+        lambda k: fkf.fkf_filter_step(f32, ys_d[k % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
+                                      flags=fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_FULL_UPDATE, want_nll=False),
+        general, ("r", "last_path", "gep_rank", "new_dirs", "t_eig", "t_lmax"))
+    log(f"[bench] FP32 general step, merge forced: {res['fp32_full']['ms_per_step']:.1f} ms/step; phases(ms) "
+        + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]) + f"; {res['fp32_full']['step_stats']}")
+
+    # (2) a new random ray set (m rays) every step: new directions arrive, the rank reaches the cap
+    # r_max = 2m and the merge truncates to it every step (device-resident operators)
     import synth
 
     vr_rng = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 31))
-    vr_steps = 3
     gx, gy = w["grid"]
-    ops = synth.varying_ray_operators(vr_rng, gx, gy, [m] * (vr_steps + 1))
+    ops = synth.varying_ray_operators(vr_rng, gx, gy, [m] * (general + 1))
     truth = wl["truth"]
     vys = [synth.measurements(vr_rng, ops[k], truth[min(k, truth.shape[0] - 1)], w["noise"])
-           for k in range(vr_steps + 1)]
-    fkf.fkf_filter_step(f32, vys[0], m, ops[0].rowptr, ops[0].col, ops[0].val, None, w["noise"])
-    vr_stats = []
-    torch.cuda.synchronize()
-    t0 = time.time()
-    vr_phases = np.zeros(6)
-    for k in range(1, vr_steps + 1):
-        fkf.fkf_filter_step(f32, vys[k], m, ops[k].rowptr, ops[k].col, ops[k].val, None, w["noise"])
-        vr_phases += np.array(fkf.fkf_filter_phase_times(f32))
-        st = fkf.fkf_filter_get_stats(f32)
-        vr_stats.append({k2: st[k2] for k2 in ("r", "last_path", "gep_rank", "new_dirs", "t_eig")})
-    torch.cuda.synchronize()
-    ms_vr = (time.time() - t0) * 1e3 / vr_steps
-    res["fp32_varying"] = dict(ms_per_step=ms_vr, steps_per_s=1e3 / ms_vr, steps=vr_steps,
-                               phases_ms=(vr_phases / vr_steps).tolist(), step_stats=vr_stats,
-                               note="host inputs, a new random ray set each step; host wall clock")
-    log(f"[bench] FP32 path, new rays every step: {ms_vr:.1f} ms/step; phases(ms) "
-        + " ".join(f"{p:.1f}" for p in res["fp32_varying"]["phases_ms"]) + f"; {vr_stats}")
+           for k in range(general + 1)]
+    ops_d = [tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (vys[k], o.rowptr, o.col, o.val))
+             for k, o in enumerate(ops)]
+
+    def vr_step(k):
+        yv, rp, cc, vv = ops_d[k]
+        fkf.fkf_filter_step(f32, yv, m, rp, cc, vv, None, w["noise"], flags=fkf.FKF_STEP_INPUTS_ON_DEVICE,
+                            want_nll=False)
+
+    vr_step(0)
+    res["fp32_varying"] = timed_steps(lambda k: vr_step(k + 1), general,
+                                      ("r", "last_path", "gep_rank", "new_dirs", "t_eig"))
+    log(f"[bench] FP32 general step, new rays every step: {res['fp32_varying']['ms_per_step']:.1f} ms/step; "
+        "phases(ms) " + " ".join(f"{p:.1f}" for p in res["fp32_varying"]["phases_ms"])
+        + f"; {res['fp32_varying']['step_stats']}")
+    del ops_d
 
     # ---------------- H-apply alone (the dominant kernel), m = 1024 columns ----------------
     def time_apply(hm, info, prec, reps):
@@ -476,10 +488,13 @@ def batch_bench(nb, steps, warmup):
     return out
 
 
-def cpu_oracle_baseline(wl, sample_rows=2048, steps=3):
+def cpu_oracle_baseline(wl, sample_rows=2048, steps=3, warmup=0):
     """The oracle as it stands (O2: exact cross-covariance Kalman recursion for a
-    fixed H, FP64 NumPy) on a bounded sample of the workload: all m x m work
-    plus `sample_rows` of the N state rows; the per-row cost is scaled to N."""
+    fixed H, FP64 NumPy) on a bounded sample of the workload.  Every one of the
+    `warmup` + `steps` steps runs in full on the sample: all m x m work of the
+    step plus `sample_rows` of the N state rows.  The timed steps are run twice,
+    with the sampled rows and with none, and the per-row part of the step time
+    is scaled to all N rows."""
     from oracle import covariance, kalman
     import synth
 
@@ -495,19 +510,27 @@ def cpu_oracle_baseline(wl, sample_rows=2048, steps=3):
     t_setup = time.time() - t0
     rng = np.random.default_rng(1)
     rows = np.sort(rng.choice(n, sample_rows, replace=False))
-    ys = [(wl["y"][k], w["noise"]) for k in range(steps)]
+    total = warmup + steps
+    ys = [(wl["y"][k % wl["y"].shape[0]], w["noise"]) for k in range(total)]
     t1 = time.time()
-    out_rows = kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys)
-    t_rows = (time.time() - t1) / steps
+    out_rows = kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys[:max(warmup, 3)])
+    if steps > 0:
+        # timed: `steps` steps continuing the same recursion would need its state; the oracle restarts
+        # from the prior, which costs the same per step
+        t1 = time.time()
+        kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys[warmup:])
+    t_rows = (time.time() - t1) / max(steps, 1)
     t2 = time.time()
-    kalman.kf_crosscov_rows(G[rows[:0]], A, np.zeros(0), ys)
-    t_glob = (time.time() - t2) / steps
+    kalman.kf_crosscov_rows(G[rows[:0]], A, np.zeros(0), ys[warmup:])
+    t_glob = (time.time() - t2) / max(steps, 1)
     t_step = t_glob + max(t_rows - t_glob, 0.0) * n / sample_rows
     return dict(value=1.0 / t_step, unit="steps/s", cores=os.cpu_count(), kind="oracle",
-                sample=f"O2 (exact cross-covariance KF, FP64 NumPy) for {steps} steps on {sample_rows} of {n} rows "
-                       f"plus all m x m work; per-row time scaled to N; one-time exact Gamma H^T by FFT "
-                       f"({t_setup:.1f}s) not counted",
-                seconds_per_step=t_step, rows=rows, out_rows=out_rows, setup_s=t_setup)
+                sample=f"O2 (exact cross-covariance KF, FP64 NumPy): {steps} timed steps after {warmup} untimed, "
+                       f"each running all m x m work plus {sample_rows} of the {n} state rows; the per-row "
+                       f"time is scaled to all {n} rows; the one-time exact Gamma H^T by FFT ({t_setup:.1f}s) "
+                       "is not counted",
+                seconds_per_step=t_step, rows=rows, out_rows=out_rows, setup_s=t_setup, steps_run=steps,
+                sample_rows=sample_rows)
 
 
 def main():
@@ -517,6 +540,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--general-steps", type=int, default=None,
+                    help="steps timed for each general-step field (default: --steps)")
     ap.add_argument("--cpu-rows", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
@@ -528,6 +553,8 @@ def main():
     if args.workload == "medium":
         WORKLOAD = MEDIUM
     assert args.warmup >= 3, "at least 3 warm-up steps"
+    if args.general_steps is None:
+        args.general_steps = args.steps
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
@@ -539,9 +566,10 @@ def main():
         if rank != 0:
             return
         wl = make_workload(args.warmup + args.steps)
-        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=min(args.steps, 3))
+        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=args.steps, warmup=args.warmup)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "n_gpus": args.gpus, "steps": cb["steps_run"], "warmup": args.warmup,
+                "extrapolated_rows": {"rows_run": cb["sample_rows"], "rows_scaled_to": int(wl["points"].shape[0])},
                 "ms_per_step": 1e3 * cb["seconds_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": bench_config(1),
@@ -564,7 +592,7 @@ def main():
     cpu = None
     err_oracle = None
     if not args.no_cpu:
-        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=3)
+        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=3, warmup=0)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         err_oracle = {}
         ref = cb["out_rows"][2]
@@ -622,7 +650,10 @@ def main():
     line = {
         "metric": METRIC, "value": fp32["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": fp32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (N-scale) + f64 (m x m)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 via a two-term fp16 split on the tensor cores (N-scale) + f64 (m x m)",
+        "data": "synthetic",
+        "headline_step": "the library's step on the fixed geometry: after step 1 the basis is kept (no GEP, "
+                         "merge eigensolve or rotation run); the general step is general_step_merge / _new_rays",
         "config": bench_config(world),
         "happly_gbs": res["happly32"]["gbs"], "happly_ms": res["happly32"]["ms"],
         "happly_tflops": res["happly32"]["tflops"], "happly_in_step_ms": step_apply_ms,
@@ -633,11 +664,10 @@ def main():
                                    "steps": res["fp32_fixed_h"]["steps"],
                                    "note": "opt-in FKF_STEP_ALLOW_FIXED_H: H_k, R_k unchanged, products with "
                                            "Gamma reused; not the headline"},
-        "fp32_varying_geometry": {k: res["fp32_varying"][k] for k in ("steps_per_s", "ms_per_step", "steps",
-                                                                         "phases_ms", "note")},
-        "fp32_merge_forced": {"steps_per_s": res["fp32_full"]["steps_per_s"],
-                              "ms_per_step": res["fp32_full"]["ms_per_step"], "steps": res["fp32_full"]["steps"],
-                              "phases_ms": res["fp32_full"]["phases_ms"]},
+        "general_step_merge": dict(res["fp32_full"], note="FP32 path, the fixed geometry forced through the "
+                                   "merge path (FKF_STEP_FULL_UPDATE): GEP, orthonormalisation, merge, rotation"),
+        "general_step_new_rays": dict(res["fp32_varying"], note="FP32 path, a new random set of m rays every "
+                                      "step (device inputs); rank at the cap r_max = 2m, merge truncates"),
         "fp64_path": ({"steps_per_s": res["fp64"]["steps_per_s"], "ms_per_step": res["fp64"]["ms_per_step"],
                        "happly_gbs": res["happly64"]["gbs"], "happly_ms": res["happly64"]["ms"],
                        "happly_tflops": res["happly64"]["tflops"], "phases_ms": res["fp64"]["phases_ms"]}

@@ -133,6 +133,16 @@ fkf_status fkf_hmatrix_info(const fkf_hmat* h, fkf_hmat_info* info);
  * X_dev / Y_dev hold doubles for FKF_FP64 and floats for FKF_FP32; they
  * must not overlap.  ldx, ldy >= ncols.  Errors: EINVAL, ENOMEM, ECUDA. */
 fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy, int64_t ncols);
+/* Adjoint of Y = Gamma_H X for reverse-mode differentiation: gX = Gamma_H^T gY
+ * = Gamma_H gY (every far block and near tile is stored once and serves both
+ * (t, s) and (s, t), so the adjoint is the same sweep), and, with Y the forward
+ * result, grad_sigma2 = <gY, Y> / sigma2, the derivative with respect to the
+ * Matern variance (Gamma_H = sigma2 Gamma_1,H, so dY/dsigma2 = Y / sigma2).
+ * gY_dev, Y_dev, gX_dev: device, N x ncols row-major, original point order,
+ * the operator's element type; grad_sigma2 (host, nullable; Y_dev may be NULL
+ * then).  Errors: as fkf_hmatrix_apply. */
+fkf_status fkf_hmatrix_apply_adjoint(fkf_hmat* h, const void* gY_dev, int64_t ldg, const void* Y_dev, int64_t ldy,
+                                     void* gX_dev, int64_t ldgx, int64_t ncols, double* grad_sigma2);
 /* Same product with X and Y already in cluster order (no permutation). */
 fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
                                        int64_t ncols);
@@ -152,9 +162,12 @@ fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t l
  * would fail or fragment it.  The regular apply grows library-owned
  * workspaces with cudaMalloc on first use; this one never allocates.
  *
- * Same arguments, layout and result as fkf_hmatrix_apply_clustered (X, Y in
- * cluster order, row-major, precision's element type; the caller passes and
- * owns both).  The slot workspace and the split-reduction partials live in a
+ * Same arguments and layout as fkf_hmatrix_apply_clustered (X, Y in cluster
+ * order, row-major, precision's element type; the caller passes and owns
+ * both), and the same product: for an FP64 operator the same result up to
+ * summation order; an FP32 operator always runs the FP32 SIMT tile engine here,
+ * whatever fkf_hmatrix_set_engine chose, so against the default tensor-core
+ * apply it agrees to FP32 rounding (about 1e-5 relative).  The slot workspace and the split-reduction partials live in a
  * library-wide static device array of FKF_NOALLOC_SCRATCH_BYTES bytes; the
  * columns are processed in panels as wide as that array allows (at least one
  * column).  An operator that needs more than FKF_NOALLOC_SCRATCH_BYTES for a
@@ -198,6 +211,17 @@ fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t
  * or 1-2 for an FP64 operator).  A tensor-core wait that expires makes the
  * apply (or the filter step) return FKF_ETIMEOUT. */
 fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
+/* Poll limit of the tensor-core H-apply's pipeline waits (producer -> MMA ->
+ * epilogue mbarrier hand-offs inside a CTA).  A wait that is not satisfied
+ * within `polls` polls gives up: the CTA marks itself failed, every role
+ * unwinds (the MMA thread waits for its issued MMAs, the producer for its
+ * issued bulk copies, both with the full default limit, and TMEM is freed),
+ * and the apply -- or the filter step that ran it -- returns FKF_ETIMEOUT with
+ * the outputs undefined; the operator stays usable.  polls < 0 restores the
+ * default 2^22; 0 makes every wait that is not already satisfied give up at
+ * once (the way to exercise the time-out path).  Errors: EINVAL (polls >
+ * 2^32 - 1). */
+fkf_status fkf_hmatrix_set_wait_limit(fkf_hmat* h, int64_t polls);
 /* Current engine of the H-apply (see fkf_hmatrix_set_engine).  Errors: EINVAL (null). */
 fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine);
 /* Autotuner of the tensor-core pipeline shape (engine 2): times the FP16
@@ -246,6 +270,27 @@ void fkf_filter_destroy(fkf_filter* f);
  * SPD), ENOCONV, ECUDA; the filter state is unchanged on error. */
 fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr, const int32_t* H_col,
                            const double* H_val, const double* R, double r_scalar, int32_t flags, double* nll_out);
+
+/* Extended Kalman filter step with the Box-Cox measurement map (Sec. 4.2,
+ * Eq. nonlinear, Alg. extkalman).  The filtered field x is the Box-Cox
+ * transform of the physical field s, x = a (s^(1/a) - 1), and the
+ * measurements are y = H s(x) + v with s(x) = ((x + a)/a)^a.  The step
+ * predicts (alpha += 1, mean unchanged), linearises at the predicted mean
+ * x_pred: innovation nu = y - H s(x_pred), Jacobian
+ * H_k = H diag(s'(x_pred)), s'(x) = ((x + a)/a)^(a - 1), and updates with H_k
+ * through the general path (data-space GEP, Gamma^-1-orthonormal merge with
+ * the filter's truncation, rotation) exactly as fkf_filter_step does for a
+ * linear operator; the Jacobian changes every step, so the rank grows until
+ * the truncation (trunc_tol, r_max) bounds it.  One linearisation per step.
+ * Arguments as for fkf_filter_step (H is the linear operator H of h(x) =
+ * H s(x), CSR over original point indices); boxcox_a > 0.  For a non-integer
+ * a the map needs x > -a at every cell the rays cross (the power of a negative
+ * base is undefined); a = 1 is the linear filter on y - H 1.  The fixed-H fast
+ * path does not apply (FKF_STEP_ALLOW_FIXED_H is ignored).
+ * Errors: as fkf_filter_step, and EINVAL for boxcox_a <= 0. */
+fkf_status fkf_filter_step_ekf(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr,
+                               const int32_t* H_col, const double* H_val, const double* R, double r_scalar,
+                               double boxcox_a, int32_t flags, double* nll_out);
 
 /* One filter's inputs and outputs for fkf_filter_step_batched. */
 typedef struct {
@@ -313,10 +358,20 @@ fkf_status fkf_conditional_realization(fkf_filter* f, const double* a_dev, int32
 fkf_status fkf_uncertainty_scalars(fkf_filter* f, double* rel_entropy, double* trace_sigma);
 /* Orthonormality drift max |X^T W - I| with X = Gamma^-1 W carried alongside W. */
 fkf_status fkf_filter_orthonormality(fkf_filter* f, double* max_abs_err);
-/* Re-establish W = Gamma_H X and W^T Gamma^-1 W = I (one H-apply of r columns,
- * a Gram and a small Cholesky/eigen rotation); the covariance it represents
- * is kept. */
+/* Re-establish W = Gamma_H X and W^T Gamma^-1 W = I (the invariant of
+ * Eq. sigmakk, which FP32 storage of W and X lets drift): one H-apply of r
+ * columns (the Gamma_sys W_k product), the Gram Q = X^T Gamma_H X,
+ * W <- (Gamma_H X) Q^-1/2 and the weight re-diagonalised in that basis; the
+ * covariance it represents is kept.  Works for any r <= r_max (a scratch of
+ * N x r elements is allocated on first use when r exceeds m_max).
+ * Errors: ENOTSPD (Q not positive definite), ENOMEM, ECUDA. */
 fkf_status fkf_filter_refresh(fkf_filter* f);
+/* Schedule fkf_filter_refresh after every `every`-th step (k % every == 0,
+ * counted over the filter's lifetime) of fkf_filter_step / _ekf; 0 (the
+ * default) never refreshes.  A scheduled refresh runs after the step has
+ * committed; if it fails, the step's status is the refresh's error and the
+ * state is the step's result.  Errors: EINVAL (every < 0). */
+fkf_status fkf_filter_set_refresh(fkf_filter* f, int32_t every);
 /* Checkpoint / restore of (k, alpha, r, s_hat, D, W, X) to a binary file. */
 fkf_status fkf_filter_checkpoint(fkf_filter* f, const char* path);
 fkf_status fkf_filter_restore(fkf_filter* f, const char* path);

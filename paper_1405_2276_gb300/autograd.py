@@ -1,17 +1,17 @@
 """torch.autograd wrappers over the C-ABI (hand-written adjoints).
 
-HApply     Y = Gamma_H X (original point order).  Backward: the adjoint
-           apply Gamma_H^T dY is the same sweep (every far block and near tile
-           is stored once and serves both (t, s) and (s, t), so Gamma_H is
-           exactly symmetric); d/dsigma2 = <dY, Y> / sigma2 because
-           Gamma_H = sigma2 * Gamma_1,H.
+HApply     Y = Gamma_H X (original point order).  Backward:
+           fkf_hmatrix_apply_adjoint, i.e. the adjoint apply Gamma_H^T dY (the
+           same sweep: Gamma_H is exactly symmetric) and d/dsigma2 =
+           <dY, Y> / sigma2 (Gamma_H = sigma2 * Gamma_1,H), both in the library.
 FilterNLL  summed innovation NLL of K filter steps with a fixed H and its
            gradient with respect to the measurements, the prior mean, the
            Matern variance and the noise variance, from fkf_nll_gradient
            (reverse-mode data-space recursion in the library).
 
-All products run in libfkf.so; this module only moves tensors across the
-C-ABI and applies the chain rule with the incoming scalar/tensor gradient.
+All products and reductions run in libfkf.so; this module only moves tensors
+across the C-ABI and scales the library's gradients by the incoming scalar
+gradient of FilterNLL.
 """
 
 from __future__ import annotations
@@ -38,9 +38,8 @@ class HApply(torch.autograd.Function):
         (Y,) = ctx.saved_tensors
         gYc = gY.contiguous()
         gX = torch.empty_like(gYc)
-        fkf.fkf_hmatrix_apply(ctx.hmat, gYc, gX)  # Gamma_H^T = Gamma_H
-        g_sigma2 = torch.sum(gYc * Y) / ctx.sigma2
-        return gX, g_sigma2.to(torch.float64), None
+        g_sigma2 = fkf.fkf_hmatrix_apply_adjoint(ctx.hmat, gYc, Y, gX)
+        return gX, torch.tensor(g_sigma2, dtype=torch.float64), None
 
 
 class FilterNLL(torch.autograd.Function):
@@ -51,14 +50,12 @@ class FilterNLL(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, y, s0, sigma2, rho, hmat, H, alpha0=0.0):
-        built = fkf.fkf_hmatrix_info(hmat)
         y_np = np.ascontiguousarray(y.detach().cpu().numpy(), dtype=np.float64)
         s0_np = np.ascontiguousarray(s0.detach().cpu().numpy(), dtype=np.float64)
         nll, gy, gs0, gsig, grho = fkf.fkf_nll_gradient(hmat, y_np, H.rowptr, H.col, H.val, float(rho), s0_np,
                                                         float(alpha0))
         ctx.grads = (torch.from_numpy(gy).to(y.device), torch.from_numpy(gs0).to(s0.device),
                      torch.tensor(gsig, dtype=torch.float64), torch.tensor(grho, dtype=torch.float64))
-        del built
         return torch.tensor(nll, dtype=torch.float64)
 
     @staticmethod

@@ -21,7 +21,9 @@ fkf_status filter_create(fkf_hmat* h, const double* s0, double alpha0, double tr
                          fkf_filter** out);
 void filter_destroy(fkf_filter* f);
 fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* rowptr, const int32_t* col,
-                       const double* val, const double* R, double r_scalar, int flags, double* nll_out);
+                       const double* val, const double* R, double r_scalar, int flags, double* nll_out,
+                       double boxcox_a);
+fkf_status filter_set_refresh(fkf_filter* f, int every);
 fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, double* D, void* W_dev, int64_t ldw);
 fkf_status filter_variance(fkf_filter* f, double* var_dev);
 fkf_status filter_realization(fkf_filter* f, const double* a_dev, int ns, double* out_dev);
@@ -290,6 +292,27 @@ FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx
   return hmat_tc_check(h);
 }
 
+FKF_API fkf_status fkf_hmatrix_apply_adjoint(fkf_hmat* h, const void* gY_dev, int64_t ldg, const void* Y_dev,
+                                             int64_t ldy, void* gX_dev, int64_t ldgx, int64_t ncols,
+                                             double* grad_sigma2) {
+  if (!h) return FKF_EINVAL;
+  FKF_TRY(fkf_hmatrix_apply(h, gY_dev, ldg, gX_dev, ldgx, ncols));
+  if (grad_sigma2) {
+    if (!Y_dev || ldy < ncols) return set_err(h->ctx, FKF_EINVAL, "hmatrix_apply_adjoint: Y_dev, ldy >= ncols required");
+    double dot = 0;
+    if (ncols > 0) FKF_TRY(hmat_dot(h, gY_dev, ldg, Y_dev, ldy, h->n, ncols, &dot));
+    *grad_sigma2 = dot / h->kernel.sigma2;
+  }
+  return FKF_OK;
+}
+
+FKF_API fkf_status fkf_hmatrix_set_wait_limit(fkf_hmat* h, int64_t polls) {
+  if (!h) return FKF_EINVAL;
+  if (polls > 0xffffffffLL) return set_err(h->ctx, FKF_EINVAL, "set_wait_limit: polls <= 2^32 - 1 required");
+  h->tc_polls = polls < 0 ? (1u << 22) : (uint32_t)polls;
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_hmatrix_permutation(const fkf_hmat* h, int64_t* perm_host) {
   if (!h || !perm_host) return FKF_EINVAL;
   std::memcpy(perm_host, h->perm.data(), h->n * sizeof(int64_t));
@@ -346,7 +369,22 @@ FKF_API fkf_status fkf_filter_step(fkf_filter* f, const double* y, int32_t m, co
   if (!f) return FKF_EINVAL;
   if (!y || !H_rowptr || (!H_col && m > 0) || (!H_val && m > 0))
     return set_err(filter_ctx(f), FKF_EINVAL, "filter_step: null input pointer");
-  return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out);
+  return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out, 0.0);
+}
+
+FKF_API fkf_status fkf_filter_step_ekf(fkf_filter* f, const double* y, int32_t m, const int64_t* H_rowptr,
+                                       const int32_t* H_col, const double* H_val, const double* R, double r_scalar,
+                                       double boxcox_a, int32_t flags, double* nll_out) {
+  if (!f) return FKF_EINVAL;
+  if (!y || !H_rowptr || (!H_col && m > 0) || (!H_val && m > 0))
+    return set_err(filter_ctx(f), FKF_EINVAL, "filter_step_ekf: null input pointer");
+  if (!(boxcox_a > 0.0)) return set_err(filter_ctx(f), FKF_EINVAL, "filter_step_ekf: Box-Cox parameter a > 0 required");
+  return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out, boxcox_a);
+}
+
+FKF_API fkf_status fkf_filter_set_refresh(fkf_filter* f, int32_t every) {
+  if (!f) return FKF_EINVAL;
+  return filter_set_refresh(f, every);
 }
 
 // ---- merged H-applies of a batch of steps ------------------------------------

@@ -245,6 +245,7 @@ struct fkf_hmat {
   DevBuf tc_qslot, tc_qpos, tc_rpt, tc_col;
   int64_t n_tcp1 = 0, n_tcred = 0, n_tctile = 0, tc_part_rows = 0, n_tca = 0, n_tcx = 0, n_tcz = 0;
   int64_t tc_panel = 0;  // columns per tensor-core pass
+  uint32_t tc_polls = 1u << 22;  // poll limit of the tensor-core kernels' pipeline waits
   int tca_fmt = 0;       // format the split operator stream holds (1, 2)
   int tc_variant = 0;    // pipeline shape of the FP16 engine (0: 4 chunks x 2 stages, 1: 2 x 4; hmat_autotune)
   int zsplit_fmt = 0;    // format last written to the split slot workspace
@@ -257,6 +258,10 @@ struct fkf_hmat {
 // happly.cu
 fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh);
 fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
+// <A, B> = sum_ij A_ij B_ij over nrows x ncols blocks of the operator's
+// element type (FP64 accumulation, fixed order; synchronises).
+fkf_status hmat_dot(fkf_hmat* h, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows, int64_t ncols,
+                    double* out);
 fkf_status hmat_apply_clustered_noalloc(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy,
                                         int64_t ncols);
 // dst[i, :] = src[idx[i], :] for i < nrows (element type = precision / FP64)

@@ -325,6 +325,33 @@ __global__ void k_innovation(int m, const int64_t* __restrict__ rowptr, const in
   if (lane == 0) nu[w] = y[w] - acc;
 }
 
+// Extended filter with the Box-Cox map (Sec. 4.2, Eq. nonlinear, Alg.
+// extkalman): the state x is the transformed field, the measurement map is
+// h(x) = H s(x) with s(x) = ((x + a)/a)^a.  At the predicted mean (= the
+// previous posterior mean, F = I) this kernel forms the innovation
+// nu = y - H s(x) and replaces H's values in place by those of the Jacobian
+// H_k = H diag(s'(x)), s'(x) = ((x + a)/a)^(a - 1).  Warp per row; each
+// warp reads its row's values before it rewrites them.
+__global__ void k_boxcox_linearize(int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   double* __restrict__ val, const int64_t* __restrict__ iperm, int64_t n,
+                                   const double* __restrict__ x, double a, const double* __restrict__ y,
+                                   double* __restrict__ nu) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= m) return;
+  double acc = 0;
+  for (int64_t p = rowptr[w] + lane; p < rowptr[w + 1]; p += 32) {
+    const int64_t c = col[p];
+    if (c >= 0 && c < n) {
+      const double b = (x[iperm[c]] + a) / a;
+      const double sp = pow(b, a - 1.0);  // s'(x)
+      acc += val[p] * (sp * b);            // s(x) = b^a = b^(a-1) b
+      val[p] *= sp;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) nu[w] = y[w] - acc;
+}
+
 // As = (A + A^T)/2, At = diag(rs) As diag(rs); S = alpha' As + diag(R)
 __global__ void k_sym(int m, const double* __restrict__ A, int64_t lda, const double* __restrict__ rs,
                       const double* __restrict__ rdiag, double alpha1, double* __restrict__ As,
@@ -764,6 +791,8 @@ struct fkf_filter {
   cudaEvent_t ev_schur = nullptr;  // the kept-basis weight E' (Schur complement) is formed
   DevBuf Pw;  // HWD HW^T (m x m, lower triangle)
   DevBuf xcmax;  // column maxima of the dense H^T (FP32 state), for the H-apply's split
+  int refresh_every = 0;  // scheduled refresh (W <- Gamma_H X) after every refresh_every-th step; 0: never
+  DevBuf refw;            // Gamma_H X when r exceeds the spare buffer's m_max columns
   double phase_ms[6] = {};
 };
 
@@ -961,7 +990,7 @@ static fkf_status weight_products(fkf_filter* f, int m, const double* HW, int64_
 template <typename T>
 static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int64_t* rowptr_in,
                             const int32_t* col_in, const double* val_in, const double* R_in, double r_scalar,
-                            int flags, double* nll_out) {
+                            int flags, double* nll_out, double bc) {
   fkf_ctx* ctx = f->ctx;
   fkf_hmat* h = f->h;
   cudaStream_t st = ctx->stream;
@@ -997,7 +1026,8 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   // step's, which kept the basis, so G = Gamma_H H^T, [HW | A] and the basis
   // decision are unchanged (Alg. kalmanconstantH: the products with Gamma are
   // formed once for a constant H)
-  const bool allow_fixed = (flags & FKF_STEP_ALLOW_FIXED_H) && !(flags & FKF_STEP_FULL_UPDATE);
+  // the extended filter re-linearises every step: its Jacobian changes with the mean
+  const bool allow_fixed = (flags & FKF_STEP_ALLOW_FIXED_H) && !(flags & FKF_STEP_FULL_UPDATE) && bc == 0.0;
   bool reuse = false;
   if (allow_fixed && f->products_valid && m == f->prev_m && nnz == f->prev_nnz && rp == f->prev_rp &&
       rdiag == f->prev_rdiag) {
@@ -1038,6 +1068,13 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaMemcpyAsync(f->rdiag.p, rdiag.data(), m * 8, cudaMemcpyHostToDevice, st));
   FKF_CUDA(ctx, cudaMemcpyAsync(f->rs.p, rs.data(), m * 8, cudaMemcpyHostToDevice, st));
   FKF_CUDA(ctx, cudaMemsetAsync(f->flag.p, 0, 64, st));
+  if (bc > 0.0) {
+    // EKF: nu = y - H s(x_pred) and H <- H_k = H diag(s'(x_pred)) before anything reads H
+    k_boxcox_linearize<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(
+        m, f->rowptr.as<int64_t>(), f->col.as<int32_t>(), f->val.as<double>(), h->iperm_d.as<int64_t>(), n,
+        f->s_hat.as<double>(), bc, f->y.as<double>(), f->nu.as<double>());
+    FKF_LAUNCHED(ctx);
+  }
 
   const int r = f->r, rmax = f->r_max;
   const double alpha1 = f->alpha + 1.0;  // predict
@@ -1106,9 +1143,12 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_TRY(weight_products(f, m, HWA, nm));
     for (int e = 1; e < 3; e++) FKF_CUDA(ctx, cudaEventRecord(f->ev[e], st));
   }
-  k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n, f->s_hat.as<double>(),
-                                                               f->y.as<double>(), f->nu.as<double>());
-  FKF_LAUNCHED(ctx);
+  if (bc == 0.0) {
+    k_innovation<<<(int)cdiv((int64_t)m * 32, 256), 256, 0, st>>>(m, rowptr, col, val, iperm, n,
+                                                                 f->s_hat.as<double>(), f->y.as<double>(),
+                                                                 f->nu.as<double>());
+    FKF_LAUNCHED(ctx);
+  }
   const double* HW = HWA;       // m x r, ld nm
   const double* Araw = HWA + r;  // m x m, ld nm
   // S lives in the top-left m x m block of the augmented matrix (ld m + r)
@@ -1149,10 +1189,13 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       FKF_TRY(frob(ctx, (int64_t)m * m, f->At.as<double>(), nullptr, m, f->red.as<double>(), nrm + 1));
     }
     double hv[2] = {1.0, 1.0};
-    int hflag = 0;
+    int hflag = 0, apply_fail = 0;
     if (r > 0) FKF_CUDA(ctx, cudaMemcpyAsync(hv, nrm, 16, cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaMemcpyAsync(&hflag, f->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // a tensor-core wait of the H-apply that gave up: stop before G is used
+    if (h->tc_err.p) FKF_CUDA(ctx, cudaMemcpyAsync(&apply_fail, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (apply_fail) FKF_TRY(hmat_tc_check(h));
     if (tc_fail) FKF_TRY(tc_gemm_check(ctx, f->rot));
     if (hflag) return set_err(ctx, FKF_EINVAL, "filter_step: H column index outside [0, N)");
     if (r > 0) ratio = hv[1] > 0 ? hv[0] / hv[1] : 0.0;
@@ -1227,7 +1270,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     f->k++;
     f->last_path = reuse ? 3 : 1;
     // this step's products stay valid for the next step with the same H and R
-    f->products_valid = true;
+    f->products_valid = bc == 0.0;
     if (!reuse) {
       f->prev_m = m;
       f->prev_nnz = nnz;
@@ -1428,10 +1471,27 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   return FKF_OK;
 }
 
+fkf_status filter_refresh(fkf_filter* f);
+
 fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* rowptr, const int32_t* col,
-                       const double* val, const double* R, double r_scalar, int flags, double* nll_out) {
-  if (f->w == 8) return step_impl<double>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out);
-  return step_impl<float>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out);
+                       const double* val, const double* R, double r_scalar, int flags, double* nll_out,
+                       double boxcox_a) {
+  if (!(boxcox_a >= 0.0) || !std::isfinite(boxcox_a))
+    return set_err(f->ctx, FKF_EINVAL, "filter_step: Box-Cox parameter must be finite and >= 0 (0: linear)");
+  const fkf_status st =
+      f->w == 8 ? step_impl<double>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out, boxcox_a)
+                : step_impl<float>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out, boxcox_a);
+  if (st != FKF_OK) return st;
+  // S10: the scheduled refresh W <- Gamma_H X (after the step has committed;
+  // the refresh is transactional on its own and keeps the covariance)
+  if (f->refresh_every > 0 && f->k % f->refresh_every == 0 && f->r > 0) return filter_refresh(f);
+  return FKF_OK;
+}
+
+fkf_status filter_set_refresh(fkf_filter* f, int every) {
+  if (every < 0) return set_err(f->ctx, FKF_EINVAL, "set_refresh: every >= 0 required");
+  f->refresh_every = every;
+  return FKF_OK;
 }
 
 // Bring the state to the paper's form (Eq. sigmakk with D diagonal): with the
@@ -1638,8 +1698,16 @@ static fkf_status refresh_impl(fkf_filter* f) {
   if (r == 0) return FKF_OK;
   const int64_t n = f->n, ld = f->ldwg, rr = (int64_t)r * r;
   T* Xc = f->Xb[f->cur].as<T>();
-  T* Wtmp = f->WG[1 - f->cur].as<T>() + rmax;  // G columns of the spare buffer as scratch (ld)
-  FKF_TRY(hmat_apply_clustered(f->h, Xc, rmax, Wtmp, ld, r));
+  // Gamma_H X goes to the G columns of the spare buffer when r fits in them,
+  // else to a scratch of its own (N x r, kept for later refreshes)
+  T* Wtmp = f->WG[1 - f->cur].as<T>() + rmax;
+  int64_t ldt = ld;
+  if (r > f->m_max) {
+    FKF_TRY(dev_alloc(ctx, f->refw, (size_t)n * r * sizeof(T)));
+    Wtmp = f->refw.as<T>();
+    ldt = r;
+  }
+  FKF_TRY(hmat_apply_clustered(f->h, Xc, rmax, Wtmp, ldt, r));
   FKF_TRY(dev_alloc(ctx, f->tmp3, (size_t)rr * 8 * 6));
   double* Q = f->tmp3.as<double>();
   double* B1 = Q + rr;
@@ -1647,7 +1715,7 @@ static fkf_status refresh_impl(fkf_filter* f) {
   double* Qh = Bm1 + rr;
   double* Qmh = Qh + rr;
   double* E = Qmh + rr;
-  FKF_TRY(gram_T(ctx, f->w, r, r, n, Xc, rmax, Wtmp, ld, Q, r, f->gramws));
+  FKF_TRY(gram_T(ctx, f->w, r, r, n, Xc, rmax, Wtmp, ldt, Q, r, f->gramws));
   k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Q);
   FKF_LAUNCHED(ctx);
   std::vector<double> w_h;
@@ -1683,7 +1751,7 @@ static fkf_status refresh_impl(fkf_filter* f) {
     Et = f->Ecast.as<T>();
   }
   T* Wn = f->WG[1 - f->cur].as<T>() + (rmax - r);  // columns [rmax - r, rmax): disjoint from Wtmp
-  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Wtmp, ld, Et, r, 0.0, Wn, ld));
+  FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Wtmp, ldt, Et, r, 0.0, Wn, ld));
   FKF_TRY(gemm_T<T>(ctx, false, false, n, r, r, 1.0, Xc, rmax, Et, r, 0.0, f->Xb[1 - f->cur].as<T>(), rmax));
   FKF_CUDA(ctx, cudaStreamSynchronize(st));
   FKF_CUDA(ctx, cudaGetLastError());
@@ -1695,10 +1763,6 @@ static fkf_status refresh_impl(fkf_filter* f) {
 
 fkf_status filter_refresh(fkf_filter* f) {
   FKF_TRY(canonicalize(f));
-  if (f->r > f->m_max) {
-    // refresh uses the G columns of the spare buffer as scratch for Gamma X (r columns)
-    return set_err(f->ctx, FKF_ESTATE, "refresh: rank %d exceeds the scratch width m_max=%d", f->r, f->m_max);
-  }
   if (f->w == 8) return refresh_impl<double>(f);
   return refresh_impl<float>(f);
 }

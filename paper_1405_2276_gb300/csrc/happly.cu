@@ -185,6 +185,48 @@ fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const in
   return permute_rows<float>(h->ctx, (const float*)src, lds, idx_dev, (float*)dst, ldd, nrows, ncols);
 }
 
+// Per-block partial sums of <A, B> (FP64 accumulation, fixed order).
+template <typename T>
+__global__ void k_dot_part(int64_t nrows, int64_t ncols, const T* __restrict__ A, int64_t lda,
+                           const T* __restrict__ B, int64_t ldb, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc = 0;
+  const int64_t total = nrows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols, j = e % ncols;
+    acc += (double)A[i * lda + j] * (double)B[i * ldb + j];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+fkf_status hmat_dot(fkf_hmat* h, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows, int64_t ncols,
+                    double* out) {
+  fkf_ctx* ctx = h->ctx;
+  constexpr int kBlocks = 304;
+  DevBuf part;
+  FKF_TRY(dev_alloc(ctx, part, kBlocks * sizeof(double)));
+  if (h->prec == FKF_FP64)
+    k_dot_part<double><<<kBlocks, 256, 0, ctx->stream>>>(nrows, ncols, (const double*)A, lda, (const double*)B, ldb,
+                                                          part.as<double>());
+  else
+    k_dot_part<float><<<kBlocks, 256, 0, ctx->stream>>>(nrows, ncols, (const float*)A, lda, (const float*)B, ldb,
+                                                         part.as<double>());
+  FKF_LAUNCHED(ctx);
+  double hp[kBlocks];
+  FKF_CUDA(ctx, cudaMemcpyAsync(hp, part.p, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double s = 0;
+  for (int b = 0; b < kBlocks; b++) s += hp[b];
+  *out = s;
+  return FKF_OK;
+}
+
 fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, const int64_t* idx_dev, double* dst,
                                  int64_t ldd, int64_t nrows, int64_t ncols) {
   return permute_rows<double>(ctx, src, lds, idx_dev, dst, ldd, nrows, ncols);

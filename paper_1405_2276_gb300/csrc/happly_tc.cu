@@ -133,6 +133,7 @@ struct Smem {
   uint64_t* bar;
   uint32_t* tmem_slot;
   int* fail;
+  uint32_t polls;  // poll limit of the pipeline waits (kMaxPolls unless a caller lowered it)
   int64_t* q;  // [kQ] tile indices (-1: no more tiles)
   float* epi;  // kEpiWarps staging tiles
 
@@ -158,8 +159,19 @@ __device__ __forceinline__ Smem<F> smem_layout(uint8_t* base) {
   return s;
 }
 
+// A pipeline wait (stages, accumulators, tile queue): gives up after s.polls
+// polls and marks the CTA failed, which makes every role unwind.
 template <int F>
 __device__ __forceinline__ bool wait_bar(const Smem<F>& s, int i, uint32_t parity) {
+  if (umma::mbar_wait(&s.bar[i], parity, s.polls)) return true;
+  s.set_fail();
+  return false;
+}
+
+// An unwind wait (MMA completion before TMEM is released, bulk copies landed
+// before the CTA exits): always the full kMaxPolls, whatever s.polls is.
+template <int F>
+__device__ __forceinline__ bool wait_bar_unwind(const Smem<F>& s, int i, uint32_t parity) {
   if (umma::mbar_wait(&s.bar[i], parity, kMaxPolls)) return true;
   s.set_fail();
   return false;
@@ -501,11 +513,13 @@ __device__ __forceinline__ bool next_tile(const Smem<F>& s, int qi, int64_t& id)
 // A tile's chunks go kCPS to a stage (the last stage of a tile may hold
 // fewer): one bulk copy for their A chunks (consecutive in the operator
 // stream), one per B chunk.
+// Returns through g the number of stages whose bulk copies it issued (each
+// stage is issued whole: every exit is at a stage boundary).
 template <int F, class Ph>
 __device__ __forceinline__ void producer(const Smem<F>& s, const JobSet<Ph>& js, int64_t ntiles,
-                                         unsigned long long* counter) {
+                                         unsigned long long* counter, int64_t& g) {
   using G = Geo<F>;
-  int64_t g = 0;  // stages issued
+  g = 0;  // stages issued
   for (int qi = 0;; qi++) {
     const int64_t id = (int64_t)atomicAdd(counter, 1ull);
     const int64_t packed = id < ntiles ? js.pack(id) : -1;
@@ -607,7 +621,7 @@ __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& j
   }
   // every MMA issued here has completed before TMEM is released
   umma::commit(&s.bar[G::FIN]);
-  wait_bar(s, G::FIN, 0);
+  wait_bar_unwind(s, G::FIN, 0);
 }
 
 // Epilogue stores of one row's 32 columns [c0, c0 + 32) of a tile, times
@@ -783,10 +797,12 @@ __device__ __forceinline__ void epilogue(const Smem<F>& s, const JobSet<Ph>& js,
 
 template <int F, class Ph>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_apply(const JobSet<Ph> js, int64_t ntiles, unsigned long long* __restrict__ counter, int* __restrict__ err) {
+    k_tc_apply(const JobSet<Ph> js, int64_t ntiles, unsigned long long* __restrict__ counter, int* __restrict__ err,
+               uint32_t max_polls) {
   using G = Geo<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const Smem<F> s = smem_layout<F>(smem_raw);
+  Smem<F> s = smem_layout<F>(smem_raw);
+  s.polls = max_polls;
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int i = G::FULL; i < G::EMPTY; i++) umma::mbar_init(&s.bar[i], 1);
@@ -805,7 +821,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = *s.tmem_slot;
   if (warp == kProdWarp) {
-    if ((threadIdx.x & 31) == 0) producer<F>(s, js, ntiles, counter);
+    if ((threadIdx.x & 31) == 0) {
+      int64_t g = 0;
+      producer<F>(s, js, ntiles, counter, g);
+      // the CTA does not exit (nor does a failed one unwind) while a bulk copy
+      // into its shared memory is in flight: wait for the last phase issued to
+      // each stage (a phase the MMA thread already consumed reads as complete)
+      for (int64_t i = g > G::kS ? g - G::kS : 0; i < g; i++)
+        wait_bar_unwind(s, G::FULL + (int)(i % G::kS), (uint32_t)(i / G::kS) & 1);
+    }
   } else if (warp == kMmaWarp) {
     if ((threadIdx.x & 31) == 0) mma_issuer<F>(s, js, tmem);
     __syncwarp();
@@ -1040,7 +1064,8 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
     if (h->n_tcp1 > 0) {
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
       k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph1>{tc_ph1<F>(h, nc), nullptr, nullptr, 0},
-                                                            h->n_tcp1 * nct, counters, h->tc_err.as<int>());
+                                                            h->n_tcp1 * nct, counters, h->tc_err.as<int>(),
+                                                            h->tc_polls);
       FKF_LAUNCHED(ctx);
     }
     FKF_TRY(tc_reduce<F>(h, nc, st));
@@ -1051,7 +1076,8 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
     const int grid = (int)std::min<int64_t>(sms, h->n_tctile * nct);
     k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmemRows, st>>>(JobSet<Ph2>{tc_ph2<F>(h, Y + c0, ldy, nc, cs), nullptr,
                                                                       nullptr, 0},
-                                                          h->n_tctile * nct, counters + 1, h->tc_err.as<int>());
+                                                          h->n_tctile * nct, counters + 1, h->tc_err.as<int>(),
+                                                          h->tc_polls);
     FKF_LAUNCHED(ctx);
   }
   return FKF_OK;
@@ -1121,6 +1147,8 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
   char* db = ws.jobs.as<char>();
   int* err = ws.ctl.as<int>();
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
+  uint32_t polls = kMaxPolls;  // the smallest limit any operator of the batch asks for
+  for (int f : active) polls = std::min(polls, hs[f]->tc_polls);
   FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, st));
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -1133,7 +1161,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     const JobSet<Ph1> js{p1[0], reinterpret_cast<const Ph1*>(db + o1), reinterpret_cast<const int64_t*>(db + ot1),
                          (int)p1.size()};
     const int grid = (int)std::min<int64_t>(sms, t1.back());
-    k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(js, t1.back(), counters, err);
+    k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(js, t1.back(), counters, err, polls);
     FKF_LAUNCHED(ctx);
   }
   for (int f : active) FKF_TRY(tc_reduce<F>(hs[f], (int)ncols[f], st));
@@ -1148,7 +1176,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     const JobSet<Ph2> js{p2[0], reinterpret_cast<const Ph2*>(db + o2), reinterpret_cast<const int64_t*>(db + ot2),
                          (int)p2.size()};
     const int grid = (int)std::min<int64_t>(sms, t2.back());
-    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmemRows, st>>>(js, t2.back(), counters + 1, err);
+    k_tc_apply<F, Ph2><<<grid, kThreads, G::kSmemRows, st>>>(js, t2.back(), counters + 1, err, polls);
     FKF_LAUNCHED(ctx);
   }
   k_err_fanout<<<1, 64, 0, st>>>(err, reinterpret_cast<int* const*>(db + oe), (int)errs.size());
@@ -1384,7 +1412,7 @@ fkf_status tc_gemm_impl(fkf_ctx* ctx, const TcGemmProblem* p, int np, const floa
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, PhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   const int grid = (int)std::min<int64_t>(sms, nwork * nct);
   k_tc_apply<F, PhGemm><<<grid, kThreads, G::kSmemRows, ctx->stream>>>(JobSet<PhGemm>{ph, nullptr, nullptr, 0},
-                                                                   nwork * nct, counter, ws.ctl.as<int>());
+                                                                   nwork * nct, counter, ws.ctl.as<int>(), kMaxPolls);
   FKF_LAUNCHED(ctx);
   return FKF_OK;
 }

@@ -87,6 +87,8 @@ _sigs = {
     "fkf_hmatrix_info": (C.c_int, [_P, C.POINTER(fkf_hmat_info)]),
     "fkf_hmatrix_apply": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_hmatrix_apply_clustered": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_hmatrix_apply_adjoint": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64,
+                                            C.POINTER(C.c_double)]),
     "fkf_hmatrix_apply_clustered_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
     "fkf_rotate_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, C.c_int64, C.c_int64, C.c_int32, _P,
                                  C.c_int64]),
@@ -96,6 +98,8 @@ _sigs = {
     "fkf_filter_create": (C.c_int, [_P, _P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_P)]),
     "fkf_filter_destroy": (None, [_P]),
     "fkf_filter_step": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.c_double, C.c_int32, _P]),
+    "fkf_filter_step_ekf": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.c_double, C.c_double, C.c_int32, _P]),
+    "fkf_filter_set_refresh": (C.c_int, [_P, C.c_int32]),
     "fkf_filter_get": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64]),
     "fkf_variance": (C.c_int, [_P, _P]),
     "fkf_conditional_realization": (C.c_int, [_P, _P, C.c_int32, _P]),
@@ -111,6 +115,7 @@ _sigs = {
     "fkf_filter_step_batched": (C.c_int, [C.POINTER(fkf_step_desc), C.c_int32, C.c_int32]),
     "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
     "fkf_hmatrix_set_engine": (C.c_int, [_P, C.c_int32]),
+    "fkf_hmatrix_set_wait_limit": (C.c_int, [_P, C.c_int64]),
     "fkf_hmatrix_get_engine": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "fkf_hmatrix_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
 }
@@ -199,6 +204,15 @@ def fkf_hmatrix_apply(h, X, Y, ncols=None, ldx=None, ldy=None):
     _check(_lib.fkf_hmatrix_apply(h.ptr, _ptr(X), ldx, _ptr(Y), ldy, ncols), h.ctx)
 
 
+def fkf_hmatrix_apply_adjoint(h, gY, Y, gX):
+    """gX = Gamma_H gY; returns dL/dsigma2 = <gY, Y> / sigma2 (Y the forward result)."""
+    ncols = gY.shape[1] if gY.dim() > 1 else 1
+    g = C.c_double(0.0)
+    _check(_lib.fkf_hmatrix_apply_adjoint(h.ptr, _ptr(gY), ncols, _ptr(Y), ncols, _ptr(gX), ncols, ncols,
+                                          C.byref(g)), h.ctx)
+    return g.value
+
+
 def fkf_hmatrix_apply_clustered(h, X, Y, ncols=None, ldx=None, ldy=None):
     ncols = X.shape[1] if ncols is None else ncols
     ldx = X.stride(0) if ldx is None else ldx
@@ -238,6 +252,10 @@ def fkf_hmatrix_autotune(h, ncols: int):
     ms = C.c_double()
     _check(_lib.fkf_hmatrix_autotune(h.ptr, ncols, C.byref(v), C.byref(ms)), h.ctx)
     return v.value, ms.value
+
+
+def fkf_hmatrix_set_wait_limit(h, polls: int) -> None:
+    _check(_lib.fkf_hmatrix_set_wait_limit(h.ptr, int(polls)), h.ctx)
 
 
 def fkf_hmatrix_get_engine(h) -> int:
@@ -283,6 +301,16 @@ def fkf_filter_step(f, y, m, rowptr, col, val, R=None, r_scalar=0.0, flags=0, wa
     nll = C.c_double(0.0)
     st = _lib.fkf_filter_step(f.ptr, _ptr(y), m, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(R), r_scalar, flags,
                               C.byref(nll) if want_nll else None)
+    _check(st, f.ctx)
+    return nll.value
+
+
+def fkf_filter_step_ekf(f, y, m, rowptr, col, val, boxcox_a, R=None, r_scalar=0.0, flags=0, want_nll=True):
+    """Extended filter step with the Box-Cox map s(x) = ((x + a)/a)^a:
+    y = H s(x) + v; arguments as fkf_filter_step plus a = boxcox_a."""
+    nll = C.c_double(0.0)
+    st = _lib.fkf_filter_step_ekf(f.ptr, _ptr(y), m, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(R), r_scalar,
+                                  float(boxcox_a), flags, C.byref(nll) if want_nll else None)
     _check(st, f.ctx)
     return nll.value
 
@@ -358,6 +386,10 @@ def fkf_filter_orthonormality(f) -> float:
 
 def fkf_filter_refresh(f) -> None:
     _check(_lib.fkf_filter_refresh(f.ptr), f.ctx)
+
+
+def fkf_filter_set_refresh(f, every: int) -> None:
+    _check(_lib.fkf_filter_set_refresh(f.ptr, int(every)), f.ctx)
 
 
 def fkf_filter_checkpoint(f, path: str) -> None:

@@ -49,6 +49,8 @@ def run_filter(points, kernel, steps, precision=0, leaf=64, eta=1.0, aca_tol=1e-
     m_max = m_max or max(h.nrows for _, h, _ in steps)
     r_max = r_max or 2 * m_max
     f = fkf.fkf_filter_create(hmat, None, 0.0, trunc_tol, m_max, r_max)
+    if refresh_every:
+        fkf.fkf_filter_set_refresh(f, refresh_every)  # S10 scheduled by the library
     out = []
     dt = torch.float64 if precision == fkf.FKF_FP64 else torch.float32
     for k, (y, h, R) in enumerate(steps):
@@ -70,8 +72,6 @@ def run_filter(points, kernel, steps, precision=0, leaf=64, eta=1.0, aca_tol=1e-
             W = torch.empty((n, st["r"]), dtype=dt, device="cuda")
             fkf.fkf_filter_get(f, n, want_s=False, want_D=False, W=W)
             rec["W"] = W.double().cpu().numpy()
-        if refresh_every and (k + 1) % refresh_every == 0:
-            fkf.fkf_filter_refresh(f)
         out.append(rec)
     return out, ctx, hmat, f
 

@@ -7,8 +7,9 @@ diag(Sigma) on those rows are compared with it step by step.
 
 - 256 x 256 grid, m = 400, nu = 3/2, ell = 0.1, 50 steps, FP64 path, 4096 rows.
 - 512 x 512 grid, m = 1024, nu = 1/2, ell = 0.05: the benchmark's workload and
-  launch configuration (FP32 path, tensor-core H-apply engine as built) and the
-  FP64 path, 3 steps, 2048 rows.
+  launch configuration (FP32 path, tensor-core H-apply engine as built) over
+  the workload's 100 steps, without and with the scheduled refresh
+  (W <- Gamma_H X every 10 steps), and the FP64 path over 3 steps; 2048 rows.
 
 Both operators are ACA-compressed (tolerance 1e-8), so the FP64 path differs
 from the exact-Gamma oracle by the compression times the filter's sensitivity
@@ -57,10 +58,11 @@ def _worst(got, ref, rows):
     return es, ev
 
 
-def _run(fkf, cfg, wl, steps, precision):
+def _run(fkf, cfg, wl, steps, precision, refresh_every=0):
     kern = (cfg["nu"], cfg["ell"], cfg["sigma2"])
     sg = [(wl["y"][k], wl["H"], cfg["noise"]) for k in range(steps)]
-    got, ctx, hm, f = run_filter(wl["points"], kern, sg, precision=precision, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32)
+    got, ctx, hm, f = run_filter(wl["points"], kern, sg, precision=precision, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32,
+                                 refresh_every=refresh_every)
     engine = fkf.fkf_hmatrix_get_engine(hm)
     fkf.fkf_filter_destroy(f)
     fkf.fkf_hmatrix_destroy(hm)
@@ -78,15 +80,24 @@ def test_medium_grid_fp64_path_50_steps(fkf):
     assert es < 1e-6 and ev < 1e-6
 
 
-@pytest.mark.parametrize("precision,bound", [(1, 2e-4), (0, 1e-6)])
-def test_large_grid_bench_workload(fkf, precision, bound):
-    steps = 3
-    wl = workload(LARGE, steps)
-    rows, ref = _oracle_rows(LARGE, wl, steps, 2048, seed=1)
-    got, engine = _run(fkf, LARGE, wl, steps, precision)
+_LARGE_CACHE = {}
+
+
+def _large_oracle(steps):
+    if steps not in _LARGE_CACHE:
+        wl = workload(LARGE, steps)
+        _LARGE_CACHE[steps] = (wl,) + _oracle_rows(LARGE, wl, steps, 2048, seed=1)
+    return _LARGE_CACHE[steps]
+
+
+@pytest.mark.parametrize("precision,steps,refresh,bound", [(1, 100, 0, 2e-4), (1, 100, 10, 2e-4), (0, 3, 0, 1e-6)])
+def test_large_grid_bench_workload(fkf, precision, steps, refresh, bound):
+    wl, rows, ref = _large_oracle(steps)
+    got, engine = _run(fkf, LARGE, wl, steps, precision, refresh_every=refresh)
     if precision == 1:
         assert engine == 2  # the engine the benchmark times
     es, ev = _worst(got, ref, rows)
-    print(f"512x512 {'FP32' if precision else 'FP64'} path, {steps} steps vs O2 on 2048 rows: "
-          f"s_hat {es:.2e}, var {ev:.2e}")
+    late = _worst(got[-10:], ref[-10:], rows)
+    print(f"512x512 {'FP32' if precision else 'FP64'} path, {steps} steps (refresh every {refresh or 'never'}) "
+          f"vs O2 on 2048 rows: s_hat {es:.2e}, var {ev:.2e}; last 10 steps s_hat {late[0]:.2e}, var {late[1]:.2e}")
     assert es < bound and ev < bound
