@@ -488,13 +488,12 @@ def batch_bench(nb, steps, warmup):
     return out
 
 
-def cpu_oracle_baseline(wl, sample_rows=2048, steps=3, warmup=0):
+def cpu_oracle_baseline(wl, steps=3, warmup=0):
     """The oracle as it stands (O2: exact cross-covariance Kalman recursion for a
-    fixed H, FP64 NumPy) on a bounded sample of the workload.  Every one of the
-    `warmup` + `steps` steps runs in full on the sample: all m x m work of the
-    step plus `sample_rows` of the N state rows.  The timed steps are run twice,
-    with the sampled rows and with none, and the per-row part of the step time
-    is scaled to all N rows."""
+    fixed H, FP64 NumPy) on the bench workload: all N state rows and all m x m
+    work, `steps` timed steps from the prior after an untimed warm-up of
+    `warmup` steps on a few rows (BLAS thread start-up).  The one-time exact
+    Gamma H^T (FFT on the grid) is not timed."""
     from oracle import covariance, kalman
     import synth
 
@@ -508,29 +507,17 @@ def cpu_oracle_baseline(wl, sample_rows=2048, steps=3, warmup=0):
     A = Ht.T @ G
     A = 0.5 * (A + A.T)
     t_setup = time.time() - t0
-    rng = np.random.default_rng(1)
-    rows = np.sort(rng.choice(n, sample_rows, replace=False))
-    total = warmup + steps
-    ys = [(wl["y"][k % wl["y"].shape[0]], w["noise"]) for k in range(total)]
+    ys = [(wl["y"][k % wl["y"].shape[0]], w["noise"]) for k in range(max(steps, warmup, 1))]
+    if warmup > 0:
+        kalman.kf_crosscov_rows(G[:256], A, np.full(256, w["sigma2"]), ys[:warmup])
     t1 = time.time()
-    out_rows = kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys[:max(warmup, 3)])
-    if steps > 0:
-        # timed: `steps` steps continuing the same recursion would need its state; the oracle restarts
-        # from the prior, which costs the same per step
-        t1 = time.time()
-        kalman.kf_crosscov_rows(G[rows], A, np.full(sample_rows, w["sigma2"]), ys[warmup:])
-    t_rows = (time.time() - t1) / max(steps, 1)
-    t2 = time.time()
-    kalman.kf_crosscov_rows(G[rows[:0]], A, np.zeros(0), ys[warmup:])
-    t_glob = (time.time() - t2) / max(steps, 1)
-    t_step = t_glob + max(t_rows - t_glob, 0.0) * n / sample_rows
+    out_rows = kalman.kf_crosscov_rows(G, A, np.full(n, w["sigma2"]), ys[:steps])
+    t_step = (time.time() - t1) / steps
     return dict(value=1.0 / t_step, unit="steps/s", cores=os.cpu_count(), kind="oracle",
-                sample=f"O2 (exact cross-covariance KF, FP64 NumPy): {steps} timed steps after {warmup} untimed, "
-                       f"each running all m x m work plus {sample_rows} of the {n} state rows; the per-row "
-                       f"time is scaled to all {n} rows; the one-time exact Gamma H^T by FFT ({t_setup:.1f}s) "
-                       "is not counted",
-                seconds_per_step=t_step, rows=rows, out_rows=out_rows, setup_s=t_setup, steps_run=steps,
-                sample_rows=sample_rows)
+                sample=f"O2 (exact cross-covariance KF, FP64 NumPy) on all {n} state rows and all m x m work: "
+                       f"{steps} timed steps from the prior (after {warmup} untimed warm-up steps on 256 rows); "
+                       f"the one-time exact Gamma H^T by FFT ({t_setup:.1f}s) is not timed",
+                seconds_per_step=t_step, rows=np.arange(n), out_rows=out_rows, setup_s=t_setup, steps_run=steps)
 
 
 def main():
@@ -542,7 +529,6 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--general-steps", type=int, default=None,
                     help="steps timed for each general-step field (default: --steps)")
-    ap.add_argument("--cpu-rows", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
                     help="medium = 256x256, m=400: for profiler captures only")
@@ -566,10 +552,9 @@ def main():
         if rank != 0:
             return
         wl = make_workload(args.warmup + args.steps)
-        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=args.steps, warmup=args.warmup)
+        cb = cpu_oracle_baseline(wl, steps=args.steps, warmup=args.warmup)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
                 "n_gpus": args.gpus, "steps": cb["steps_run"], "warmup": args.warmup,
-                "extrapolated_rows": {"rows_run": cb["sample_rows"], "rows_scaled_to": int(wl["points"].shape[0])},
                 "ms_per_step": 1e3 * cb["seconds_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": bench_config(1),
@@ -592,7 +577,7 @@ def main():
     cpu = None
     err_oracle = None
     if not args.no_cpu:
-        cb = cpu_oracle_baseline(wl, sample_rows=args.cpu_rows, steps=3, warmup=0)
+        cb = cpu_oracle_baseline(wl, steps=3, warmup=1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         err_oracle = {}
         ref = cb["out_rows"][2]

@@ -117,8 +117,22 @@ void fkf_destroy(fkf_ctx* ctx);
 const char* fkf_last_error(const fkf_ctx* ctx);
 /* Kernels of this library launched by this context since creation. */
 int64_t fkf_launch_count(const fkf_ctx* ctx);
-/* cuSOLVER dense-routine calls (syevd, potrf, potrs) issued by this context. */
+/* cuSOLVER dense-routine calls (potrf, potrs) issued by this context. */
 int64_t fkf_library_call_count(const fkf_ctx* ctx);
+
+/* Symmetric eigendecomposition in FP64 on the device: the solver the filter
+ * uses for the data-space generalized eigenproblem (Eq. ghep, solved as the
+ * standard problem of R^-1/2 H Gamma H^T R^-1/2) and for the merge eigenproblem
+ * of Alg. lowrankaddition (step 4).  Householder reduction to tridiagonal form,
+ * divide and conquer on the tridiagonal, back-transformation of the wanted
+ * eigenvectors.  A_dev: n x n symmetric (the mean of A and A^T is used),
+ * row-major doubles, overwritten: rows 0..want-1 receive the eigenvectors of
+ * the `want` largest eigenvalues, ascending (row q belongs to w[n - want + q]).
+ * w_dev: all n eigenvalues, ascending.  Device workspace of about
+ * 5 n^2 + n want doubles is allocated for the call.  Synchronises the
+ * context's stream.  Errors: EINVAL, ENOMEM, ENOCONV (an iteration or a
+ * bounded device wait did not finish), ECUDA. */
+fkf_status fkf_eigh(fkf_ctx* ctx, int32_t n, double* A_dev, double* w_dev, int32_t want);
 
 /* ---- H-matrix (Sec. 2.2.1) ----------------------------------------------
  * fkf_hmatrix_build: points (host, N x dim row-major, dim 2 or 3) -> Gamma_H.
@@ -366,6 +380,21 @@ fkf_status fkf_filter_orthonormality(fkf_filter* f, double* max_abs_err);
  * N x r elements is allocated on first use when r exceeds m_max).
  * Errors: ENOTSPD (Q not positive definite), ENOMEM, ECUDA. */
 fkf_status fkf_filter_refresh(fkf_filter* f);
+/* Randomized generalized eigensolver for the merge steps (App. B, Alg.
+ * randomizedghepuncert, with A = H_k^T R^-1 H_k and B = Gamma^-1): instead of
+ * the exact data-space GEP (an m x m eigendecomposition), each merge step
+ * keeps the k dominant modes of the sketch Ybar = A Omega of l = k + p
+ * Gaussian columns: a Gamma-orthonormal basis of Ybar (rank-revealing), the
+ * Rayleigh-Ritz matrix T = Q^T A Q (l x l) and its k largest eigenpairs.  All
+ * of it runs in data space (O(m^2 l) instead of O(m^3)); the mean update and
+ * the innovation covariance stay exact, the covariance update uses the k
+ * modes (the approximation App. B bounds).  omega_dev: device, N x (k + p)
+ * row-major FP64 in original point order, the caller's Gaussian draws (the
+ * algorithm's input Omega), copied by the call (the caller may free it) and
+ * used by every later merge step until changed.  k = 0 restores the exact
+ * GEP (omega_dev ignored).  Errors: EINVAL (k < 0, p < 0, k + p > m_max,
+ * omega_dev NULL with k > 0), ENOMEM, ECUDA. */
+fkf_status fkf_filter_set_randomized_ghep(fkf_filter* f, int32_t k, int32_t p, const double* omega_dev);
 /* Schedule fkf_filter_refresh after every `every`-th step (k % every == 0,
  * counted over the filter's lifetime) of fkf_filter_step / _ekf; 0 (the
  * default) never refreshes.  A scheduled refresh runs after the step has

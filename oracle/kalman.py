@@ -181,6 +181,36 @@ def ekf_dense(Gamma, steps, a, s0=None, alpha0=0.0, r_max=None, trunc_tol=None):
     return out
 
 
+def kf_dense_randomized_ghep(Gamma, steps, Omega, k, s0=None, alpha0=0.0):
+    """The filter of Alg. kalman with the measurement information taken from
+    the randomized GHEP of App. B: each step's H^T R^-1 H is replaced by its
+    rank-k approximation Gamma^-1 U Lambda U^T Gamma^-1 from
+    `ghep.ghep_randomized(H, R, Gamma, Omega, k)` in the covariance update,
+    Sigma+ = (Sigma-^-1 + Gamma^-1 U Lambda U^T Gamma^-1)^-1 (written by the
+    Woodbury identity, F = Gamma^-1 U:
+    Sigma+ = Sigma- - Sigma- F (Lambda^-1 + F^T Sigma- F)^-1 F^T Sigma-),
+    while the mean, the innovation covariance and the NLL use the exact
+    Kalman update with Sigma- (Alg. kalman computes the gain from
+    Sigma H^T directly).  Returns per-step dicts with s, Sigma, var, nll."""
+    from . import ghep
+
+    N = Gamma.shape[0]
+    s = np.zeros(N) if s0 is None else np.array(s0, dtype=np.float64)
+    Sigma = alpha0 * Gamma.copy()
+    out = []
+    for y, H, R in steps:
+        Sigma_p = Sigma + Gamma
+        s, _, nll = _kf_update(s, Sigma_p, H, R, y - H @ s)
+        lam, U = ghep.ghep_randomized(H, R, Gamma, Omega, k)
+        F = np.linalg.solve(Gamma, U)
+        SF = Sigma_p @ F
+        inner = np.diag(1.0 / lam) + F.T @ SF
+        Sigma = Sigma_p - SF @ np.linalg.solve(inner, SF.T)
+        Sigma = 0.5 * (Sigma + Sigma.T)
+        out.append(dict(s=s.copy(), Sigma=Sigma.copy(), var=np.diag(Sigma).copy(), nll=nll))
+    return out
+
+
 def kf_information_form(Gamma, steps, alpha0=0.0):
     """Covariances only, via Eq. filtering: Sigma+ = (Sigma-^-1 + H^T R^-1 H)^-1.
     Used to pin O1 by a second, independent algebra (requires Sigma- SPD, i.e.

@@ -24,6 +24,7 @@ fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* row
                        const double* val, const double* R, double r_scalar, int flags, double* nll_out,
                        double boxcox_a);
 fkf_status filter_set_refresh(fkf_filter* f, int every);
+fkf_status filter_set_randomized_ghep(fkf_filter* f, int k, int p, const double* omega_dev);
 fkf_status filter_get(fkf_filter* f, double* s_hat, double* alpha, int* r, double* D, void* W_dev, int64_t ldw);
 fkf_status filter_variance(fkf_filter* f, double* var_dev);
 fkf_status filter_realization(fkf_filter* f, const double* a_dev, int ns, double* out_dev);
@@ -306,6 +307,19 @@ FKF_API fkf_status fkf_hmatrix_apply_adjoint(fkf_hmat* h, const void* gY_dev, in
   return FKF_OK;
 }
 
+fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
+                    int want);
+
+FKF_API fkf_status fkf_eigh(fkf_ctx* ctx, int32_t n, double* A_dev, double* w_dev, int32_t want) {
+  if (!ctx) return FKF_EINVAL;
+  if (n < 0 || !A_dev || !w_dev || want < 0 || want > n)
+    return set_err(ctx, FKF_EINVAL, "eigh: n >= 0, 0 <= want <= n and device pointers required");
+  FKF_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<double> w;
+  DevBuf ws;
+  return eigh_own(ctx, n, A_dev, w_dev, w, ws, want);
+}
+
 FKF_API fkf_status fkf_hmatrix_set_wait_limit(fkf_hmat* h, int64_t polls) {
   if (!h) return FKF_EINVAL;
   if (polls > 0xffffffffLL) return set_err(h->ctx, FKF_EINVAL, "set_wait_limit: polls <= 2^32 - 1 required");
@@ -380,6 +394,11 @@ FKF_API fkf_status fkf_filter_step_ekf(fkf_filter* f, const double* y, int32_t m
     return set_err(filter_ctx(f), FKF_EINVAL, "filter_step_ekf: null input pointer");
   if (!(boxcox_a > 0.0)) return set_err(filter_ctx(f), FKF_EINVAL, "filter_step_ekf: Box-Cox parameter a > 0 required");
   return filter_step(f, y, m, H_rowptr, H_col, H_val, R, r_scalar, flags, nll_out, boxcox_a);
+}
+
+FKF_API fkf_status fkf_filter_set_randomized_ghep(fkf_filter* f, int32_t k, int32_t p, const double* omega_dev) {
+  if (!f) return FKF_EINVAL;
+  return filter_set_randomized_ghep(f, k, p, omega_dev);
 }
 
 FKF_API fkf_status fkf_filter_set_refresh(fkf_filter* f, int32_t every) {

@@ -88,9 +88,11 @@ fkf_status set_err(fkf_ctx* ctx, fkf_status st, const char* fmt, ...);
 #define FKF_CUDA(ctx, expr)                                                                             \
   do {                                                                                                  \
     cudaError_t e_ = (expr);                                                                            \
-    if (e_ != cudaSuccess)                                                                              \
+    if (e_ != cudaSuccess) {                                                                            \
+      cudaGetLastError(); /* a failed call's error must not surface again at a later launch check */    \
       return set_err((ctx), e_ == cudaErrorMemoryAllocation ? FKF_ENOMEM : FKF_ECUDA, "%s: %s (%s:%d)", \
                      #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+    }                                                                                                   \
   } while (0)
 
 #define FKF_TRY(expr)               \

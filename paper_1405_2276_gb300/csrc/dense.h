@@ -51,12 +51,18 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
 // chol_blocked_f64 (ld ldl).
 fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs);
 
+// The library's own symmetric eigensolver (eigh.cu): all n eigenvalues
+// ascending into w_dev and w_host; the eigenvectors of the `want` largest into
+// rows 0..want-1 of A (row q = eigenvector of w[n - want + q]).  A must be
+// symmetric; ws grows to about 5 n^2 + n want doubles.  Synchronises.
+fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
+                    int want);
 // Symmetric eigensolver (FP64): A (n x n, symmetric, row-major) is replaced
 // by Vt, whose row j is the unit eigenvector of eigenvalue w[j]; eigenvalues
 // ascending.  The eigenvalues are also copied to w_host (synchronises).
 fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws);
-// The k largest eigenpairs of a symmetric n x n A (cuSOLVER syevdx, range by
-// index; all of them through eigh_f64 when k >= n): on return *meig pairs,
+// The k largest eigenpairs of a symmetric n x n A (w_dev must hold n values):
+// on return *meig pairs,
 // eigenvalues ascending in w, eigenvector i in row i of A (row-major view).
 fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
                         int* meig);

@@ -453,6 +453,16 @@ __global__ void k_top_rows(int n, int cnt, const double* __restrict__ Vt, const 
   }
 }
 
+// A[i, :] *= d[i] * d[i] (sq) or d[i]
+__global__ void k_scale_rows(int rows, int cols, double* __restrict__ A, int64_t lda, const double* __restrict__ d,
+                             int sq) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols);
+    A[(int64_t)i * lda + e % cols] *= sq ? d[i] * d[i] : d[i];
+  }
+}
+
 __global__ void k_identity(int n, double* __restrict__ out, int64_t ldo) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
@@ -792,6 +802,11 @@ struct fkf_filter {
   DevBuf Pw;  // HWD HW^T (m x m, lower triangle)
   DevBuf xcmax;  // column maxima of the dense H^T (FP32 state), for the H-apply's split
   int refresh_every = 0;  // scheduled refresh (W <- Gamma_H X) after every refresh_every-th step; 0: never
+  // randomized GHEP (App. B): k modes from a sketch of l = k + p Gaussian columns
+  // (Omega, N x l, cluster order, FP64); rk = 0: the exact data-space GEP
+  int rk = 0, rl = 0;
+  DevBuf omega, rZ, rAZ, rGram, rLp, rGm, rY, rB, rV, rT, rSk;
+  std::vector<double> rlam_h;
   DevBuf refw;            // Gamma_H X when r exceeds the spare buffer's m_max columns
   double phase_ms[6] = {};
 };
@@ -984,6 +999,115 @@ static fkf_status weight_products(fkf_filter* f, int m, const double* HW, int64_
                          true));
   }
   FKF_CUDA(ctx, cudaEventRecord(f->ev_p, lo));
+  return FKF_OK;
+}
+
+// Randomized GHEP (App. B, Alg. randomizedghepuncert) for A = H^T R^-1 H and
+// B = Gamma^-1, written in data space: with the Gaussian sketch Omega (N x l)
+// and Z = R^-1 H Omega (m x l),
+//   step 1  Ybar = A Omega = H^T Z;
+//   step 2  the Gamma-orthonormal basis of Ybar: its Gram Ybar^T Gamma Ybar =
+//           Z^T (H Gamma H^T) Z = Z^T As Z (l x l, data space) is factored by
+//           the rank-revealing pivoted Cholesky Gram ~= Lp Lp^T, and
+//           Qhat = Ybar Y with Y = Lp (Lp^T Lp)^-1 (Y^T Gram Y = I);
+//   step 3  Q = Gamma Qhat = G B with B = Z Y (G = Gamma H^T), Q^T Gamma^-1 Q = I;
+//   step 4  T = Q^T A Q = V^T R^-1 V with V = H Q = As B = (As Z) Y;
+//   step 5  T = S Lambda S^T, the k largest modes kept: U = Q S_k = G C with
+//           C = B S_k (m x k), Lambda_k in lam.
+// C and lam take the place of the exact GEP's (U = G C, U^T Gamma^-1 U =
+// C^T As C = I), so the orthonormalisation and merge that follow are
+// unchanged.  Cost O(m^2 l) instead of the O(m^3) eigensolve.
+static fkf_status randomized_gep(fkf_filter* f, int m, int* mlam_out) {
+  fkf_ctx* ctx = f->ctx;
+  cudaStream_t st = ctx->stream;
+  const int l = f->rl, k = f->rk;
+  const int64_t n = f->n;
+  *mlam_out = 0;
+  double* Z = f->rZ.as<double>();
+  double* AZ = f->rAZ.as<double>();
+  double* Gram = f->rGram.as<double>();
+  // step 1: H Omega (gather of Omega's rows at H's columns), then Z = R^-1 H Omega
+  csr_gather<double>(m, f->rowptr.as<int64_t>(), f->col.as<int32_t>(), f->val.as<double>(),
+                     f->h->iperm_d.as<int64_t>(), n, f->omega.as<double>(), l, l, Z, l, st);
+  FKF_LAUNCHED(ctx);
+  k_scale_rows<<<nblk((int64_t)m * l), 256, 0, st>>>(m, l, Z, l, f->rs.as<double>(), 1);
+  FKF_LAUNCHED(ctx);
+  // step 2: Gram = Z^T As Z, pivoted Cholesky relative to its largest diagonal entry
+  FKF_TRY(gemm_f64(ctx, false, false, m, l, m, 1.0, f->As.as<double>(), m, Z, l, 0.0, AZ, l));
+  FKF_TRY(gemm_sym_f64(ctx, true, false, l, m, 1.0, Z, l, AZ, l, 0.0, Gram, l));
+  std::vector<double> gdiag(l);
+  FKF_CUDA(ctx, cudaMemcpy2DAsync(gdiag.data(), 8, Gram, (size_t)(l + 1) * 8, 8, l, cudaMemcpyDeviceToHost, st));
+  FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  double gmax = 0;
+  for (double v : gdiag) gmax = std::max(gmax, v);
+  if (!(gmax > 0)) return FKF_OK;  // H Omega = 0: no information
+  int rank = 0;
+  double* Lp = f->rLp.as<double>();
+  FKF_TRY(pchol_f64(ctx, l, Gram, l, f->gep_tol * gmax, l, Lp, l, f->pcws, &rank));
+  if (rank == 0) return FKF_OK;
+  double* Gm = f->rGm.as<double>();
+  double* Y = f->rY.as<double>();  // l x rank
+  FKF_TRY(gemm_f64(ctx, true, false, rank, rank, l, 1.0, Lp, l, Lp, l, 0.0, Gm, rank));
+  FKF_CUDA(ctx, cudaMemcpy2DAsync(Y, (size_t)rank * 8, Lp, (size_t)l * 8, (size_t)rank * 8, l,
+                                  cudaMemcpyDeviceToDevice, st));
+  FKF_TRY(chol_f64(ctx, rank, Gm, f->cholws));
+  FKF_TRY(chol_solve_f64(ctx, rank, Gm, Y, l));  // rows of Y: Lp (Lp^T Lp)^-1
+  // step 3: B = Z Y;  step 4: V = (As Z) Y, T = V^T R^-1 V
+  double* B = f->rB.as<double>();
+  double* V = f->rV.as<double>();
+  double* T = f->rT.as<double>();
+  FKF_TRY(gemm_f64(ctx, false, false, m, rank, l, 1.0, Z, l, Y, rank, 0.0, B, rank));
+  FKF_TRY(gemm_f64(ctx, false, false, m, rank, l, 1.0, AZ, l, Y, rank, 0.0, V, rank));
+  k_scale_rows<<<nblk((int64_t)m * rank), 256, 0, st>>>(m, rank, V, rank, f->rs.as<double>(), 0);
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(gemm_sym_f64(ctx, true, false, rank, m, 1.0, V, rank, V, rank, 0.0, T, rank));
+  // step 5: eigenpairs of T, the k largest above the GEP threshold
+  std::vector<double> w_h;
+  FKF_TRY(eigh_f64(ctx, rank, T, f->a.as<double>(), w_h, f->eigws));
+  const double wmax = w_h.empty() ? 0.0 : w_h.back();
+  int kk = 0;
+  for (int i = rank - 1; i >= 0 && kk < k; i--)
+    if (wmax > 0 && w_h[i] > f->gep_tol * wmax) kk++;
+    else break;
+  if (kk == 0) return FKF_OK;
+  double* Sk = f->rSk.as<double>();  // kk x rank, rows = eigenvectors, largest first
+  k_top_rows<<<nblk((int64_t)kk * rank), 256, 0, st>>>(rank, kk, T, f->a.as<double>(), 2, Sk, rank);
+  FKF_LAUNCHED(ctx);
+  FKF_TRY(gemm_f64(ctx, false, true, m, kk, rank, 1.0, B, rank, Sk, rank, 0.0, f->C.as<double>(), kk));
+  f->rlam_h.assign(kk, 0.0);
+  for (int q = 0; q < kk; q++) f->rlam_h[q] = w_h[rank - 1 - q];
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->lam.p, f->rlam_h.data(), kk * 8, cudaMemcpyHostToDevice, st));
+  *mlam_out = kk;
+  return FKF_OK;
+}
+
+fkf_status filter_set_randomized_ghep(fkf_filter* f, int k, int p, const double* omega_dev) {
+  fkf_ctx* ctx = f->ctx;
+  if (k == 0) {
+    f->rk = f->rl = 0;
+    return FKF_OK;
+  }
+  const int l = k + p;
+  if (k < 0 || p < 0 || l > f->m_max || !omega_dev)
+    return set_err(ctx, FKF_EINVAL, "set_randomized_ghep: k >= 1, p >= 0, k + p <= m_max and a sketch required");
+  const int64_t n = f->n, m = f->m_max;
+  auto A = [&](DevBuf& b, int64_t elems) { return dev_alloc(ctx, b, (size_t)std::max<int64_t>(elems, 1) * 8); };
+  FKF_TRY(A(f->omega, n * l));
+  FKF_TRY(A(f->rZ, m * l));
+  FKF_TRY(A(f->rAZ, m * l));
+  FKF_TRY(A(f->rGram, (int64_t)l * l));
+  FKF_TRY(A(f->rLp, (int64_t)l * l));
+  FKF_TRY(A(f->rGm, (int64_t)l * l));
+  FKF_TRY(A(f->rY, (int64_t)l * l));
+  FKF_TRY(A(f->rB, m * l));
+  FKF_TRY(A(f->rV, m * l));
+  FKF_TRY(A(f->rT, (int64_t)l * l));
+  FKF_TRY(A(f->rSk, (int64_t)l * l));
+  // cluster order: row i of the stored sketch is the caller's row perm[i]
+  FKF_TRY(hmat_permute_rows_f64(ctx, omega_dev, l, f->h->perm_d.as<int64_t>(), f->omega.as<double>(), l, n, l));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  f->rk = k;
+  f->rl = l;
   return FKF_OK;
 }
 
@@ -1294,17 +1418,21 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   }
   // ---- S3: data-space GEP  R^-1/2 A R^-1/2 = Q diag(a) Q^T
   std::vector<double> a_h, thM_h;
-  FKF_TRY(eigh_f64(ctx, m, f->At.as<double>(), f->a.as<double>(), a_h, f->eigws));
-  const double amax = a_h.empty() ? 0.0 : a_h.back();
   int mlam = 0;
-  for (int i = m - 1; i >= 0; i--)
-    if (amax > 0 && a_h[i] > f->gep_tol * amax) mlam++;
-    else break;
   double* C = f->C.as<double>();
-  if (mlam > 0) {
-    k_build_C<<<nblk((int64_t)m * mlam), 256, 0, st>>>(m, mlam, f->At.as<double>(), f->a.as<double>(),
-                                                       f->rs.as<double>(), C, f->lam.as<double>());
-    FKF_LAUNCHED(ctx);
+  if (f->rk > 0) {
+    FKF_TRY(randomized_gep(f, m, &mlam));
+  } else {
+    FKF_TRY(eigh_f64(ctx, m, f->At.as<double>(), f->a.as<double>(), a_h, f->eigws));
+    const double amax = a_h.empty() ? 0.0 : a_h.back();
+    for (int i = m - 1; i >= 0; i--)
+      if (amax > 0 && a_h[i] > f->gep_tol * amax) mlam++;
+      else break;
+    if (mlam > 0) {
+      k_build_C<<<nblk((int64_t)m * mlam), 256, 0, st>>>(m, mlam, f->At.as<double>(), f->a.as<double>(),
+                                                         f->rs.as<double>(), C, f->lam.as<double>());
+      FKF_LAUNCHED(ctx);
+    }
   }
   FKF_CUDA(ctx, cudaEventRecord(f->ev[4], st));
   // ---- S4: Gamma^-1-orthonormalisation of U = G C against W (data space)
@@ -1719,13 +1847,14 @@ static fkf_status refresh_impl(fkf_filter* f) {
   k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Q);
   FKF_LAUNCHED(ctx);
   std::vector<double> w_h;
-  FKF_TRY(eigh_f64(ctx, r, Q, f->th.as<double>(), w_h, f->eigws));  // Q -> Vt
+  double* thr = f->thM.as<double>();  // r eigenvalues (r <= r_max)
+  FKF_TRY(eigh_f64(ctx, r, Q, thr, w_h, f->eigws));  // Q -> Vt
   if (!(w_h[0] > 0)) return set_err(ctx, FKF_ENOTSPD, "refresh: X^T Gamma X not positive definite");
-  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 0, B1, r);   // diag(sqrt th) Vt
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, thr, 0, B1, r);   // diag(sqrt th) Vt
   FKF_LAUNCHED(ctx);
-  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 1, Bm1, r);  // diag(1/sqrt th) Vt
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, thr, 1, Bm1, r);  // diag(1/sqrt th) Vt
   FKF_LAUNCHED(ctx);
-  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 2, E, r);    // Vt (same order)
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, thr, 2, E, r);    // Vt (same order)
   FKF_LAUNCHED(ctx);
   FKF_TRY(gemm_f64(ctx, true, false, r, r, r, 1.0, E, r, B1, r, 0.0, Qh, r));    // Q^1/2
   FKF_TRY(gemm_f64(ctx, true, false, r, r, r, 1.0, E, r, Bm1, r, 0.0, Qmh, r));  // Q^-1/2
@@ -1735,8 +1864,8 @@ static fkf_status refresh_impl(fkf_filter* f) {
   FKF_TRY(gemm_f64(ctx, false, false, r, r, r, 1.0, B1, r, Qh, r, 0.0, Q, r));
   k_symmetrize<<<nblk(rr), 256, 0, st>>>(r, Q);
   FKF_LAUNCHED(ctx);
-  FKF_TRY(eigh_f64(ctx, r, Q, f->th.as<double>(), w_h, f->eigws));
-  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, f->th.as<double>(), 2, f->Sk.as<double>(), r);  // S^T (desc)
+  FKF_TRY(eigh_f64(ctx, r, Q, thr, w_h, f->eigws));
+  k_top_rows<<<nblk(rr), 256, 0, st>>>(r, r, Q, thr, 2, f->Sk.as<double>(), r);  // S^T (desc)
   FKF_LAUNCHED(ctx);
   FKF_TRY(gemm_f64(ctx, false, true, r, r, r, 1.0, Qmh, r, f->Sk.as<double>(), r, 0.0, E, r));  // E = Q^-1/2 S
   std::vector<double> dn(r);

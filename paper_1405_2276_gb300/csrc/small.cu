@@ -1,8 +1,10 @@
 // Small dense FP64 factorisations for the m x m and r x r data-space algebra:
-// symmetric eigendecomposition and Cholesky.  These run on the GPU through
-// cuSOLVER's dense routines (syevd, potrf, potrs) on the context stream.
+// the symmetric eigendecompositions (the library's own solver, eigh.cu) and
+// the Cholesky factorisation and solves of small SPD systems (cuSOLVER's
+// potrf/potrs on the context stream).
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "dense.h"
@@ -20,30 +22,10 @@ static fkf_status solver(fkf_ctx* ctx, cusolverDnHandle_t* out) {
   return FKF_OK;
 }
 
+// The symmetric eigenproblems (data-space GEP, merge, re-diagonalisations)
+// run on the library's own eigensolver (eigh.cu).
 fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws) {
-  w_host.assign(n, 0.0);
-  if (n == 0) return FKF_OK;
-  cusolverDnHandle_t h;
-  FKF_TRY(solver(ctx, &h));
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n, w_dev, &lwork) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "syevd_bufferSize failed (n=%d)", n);
-  const size_t need = (size_t)lwork * sizeof(double) + 256;
-  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
-  int* info = reinterpret_cast<int*>(ws.as<char>() + (size_t)lwork * sizeof(double));
-  // Row-major symmetric A is the same matrix in column-major order; on exit
-  // column j (column-major) = row j (row-major) holds eigenvector j.
-  if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n, w_dev, ws.as<double>(), lwork,
-                       info) != CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "syevd failed (n=%d)", n);
-  ctx->lib_calls++;
-  int hinfo = 0;
-  FKF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaMemcpyAsync(w_host.data(), w_dev, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (hinfo != 0) return set_err(ctx, FKF_ENOCONV, "symmetric eigensolver did not converge (n=%d, info=%d)", n, hinfo);
-  return FKF_OK;
+  return eigh_own(ctx, n, A, w_dev, w_host, ws, n);
 }
 
 fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
@@ -51,33 +33,16 @@ fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, st
   *meig_out = 0;
   w_host.clear();
   if (n == 0 || k <= 0) return FKF_OK;
-  if (k >= n) {
-    FKF_TRY(eigh_f64(ctx, n, A, w_dev, w_host, ws));
-    *meig_out = n;
-    return FKF_OK;
+  k = std::min(k, n);
+  std::vector<double> all;
+  FKF_TRY(eigh_own(ctx, n, A, w_dev, all, ws, k));
+  // the k largest, ascending, at the front of w
+  if (k < n) {
+    FKF_CUDA(ctx, cudaMemcpyAsync(w_dev, all.data() + (n - k), (size_t)k * 8, cudaMemcpyHostToDevice, ctx->stream));
+    FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
-  cusolverDnHandle_t h;
-  FKF_TRY(solver(ctx, &h));
-  int lwork = 0, meig = 0;
-  const int il = n - k + 1, iu = n;
-  if (cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n, A, n,
-                                   0.0, 0.0, il, iu, &meig, w_dev, &lwork) != CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "syevdx_bufferSize failed (n=%d)", n);
-  const size_t need = (size_t)lwork * sizeof(double) + 256;
-  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
-  int* info = reinterpret_cast<int*>(ws.as<char>() + (size_t)lwork * sizeof(double));
-  if (cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0,
-                        il, iu, &meig, w_dev, ws.as<double>(), lwork, info) != CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "syevdx failed (n=%d)", n);
-  ctx->lib_calls++;
-  int hinfo = 0;
-  w_host.assign(std::max(meig, 0), 0.0);
-  FKF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  if (meig > 0)
-    FKF_CUDA(ctx, cudaMemcpyAsync(w_host.data(), w_dev, meig * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (hinfo != 0) return set_err(ctx, FKF_ENOCONV, "symmetric eigensolver did not converge (n=%d, info=%d)", n, hinfo);
-  *meig_out = meig;
+  w_host.assign(all.end() - k, all.end());
+  *meig_out = k;
   return FKF_OK;
 }
 

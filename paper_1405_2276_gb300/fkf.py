@@ -100,6 +100,7 @@ _sigs = {
     "fkf_filter_step": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.c_double, C.c_int32, _P]),
     "fkf_filter_step_ekf": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.c_double, C.c_double, C.c_int32, _P]),
     "fkf_filter_set_refresh": (C.c_int, [_P, C.c_int32]),
+    "fkf_filter_set_randomized_ghep": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "fkf_filter_get": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64]),
     "fkf_variance": (C.c_int, [_P, _P]),
     "fkf_conditional_realization": (C.c_int, [_P, _P, C.c_int32, _P]),
@@ -116,6 +117,7 @@ _sigs = {
     "fkf_filter_get_stats": (C.c_int, [_P, C.POINTER(fkf_filter_stats)]),
     "fkf_hmatrix_set_engine": (C.c_int, [_P, C.c_int32]),
     "fkf_hmatrix_set_wait_limit": (C.c_int, [_P, C.c_int64]),
+    "fkf_eigh": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32]),
     "fkf_hmatrix_get_engine": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "fkf_hmatrix_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
 }
@@ -254,6 +256,15 @@ def fkf_hmatrix_autotune(h, ncols: int):
     return v.value, ms.value
 
 
+def fkf_eigh(ctx, A, w, want=None) -> None:
+    """Symmetric eigendecomposition on the device: A (n x n torch CUDA float64,
+    overwritten: rows 0..want-1 = eigenvectors of the want largest eigenvalues,
+    ascending), w (n, float64): all eigenvalues ascending."""
+    n = A.shape[0]
+    want = n if want is None else int(want)
+    _check(_lib.fkf_eigh(ctx.ptr, n, _ptr(A), _ptr(w), want), ctx)
+
+
 def fkf_hmatrix_set_wait_limit(h, polls: int) -> None:
     _check(_lib.fkf_hmatrix_set_wait_limit(h.ptr, int(polls)), h.ctx)
 
@@ -386,6 +397,12 @@ def fkf_filter_orthonormality(f) -> float:
 
 def fkf_filter_refresh(f) -> None:
     _check(_lib.fkf_filter_refresh(f.ptr), f.ctx)
+
+
+def fkf_filter_set_randomized_ghep(f, k: int, p: int = 0, omega=None) -> None:
+    """k modes from a sketch of k + p Gaussian columns omega (torch CUDA float64,
+    N x (k + p), original point order); k = 0: the exact GEP."""
+    _check(_lib.fkf_filter_set_randomized_ghep(f.ptr, int(k), int(p), _ptr(omega)), f.ctx)
 
 
 def fkf_filter_set_refresh(f, every: int) -> None:

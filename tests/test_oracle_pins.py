@@ -458,3 +458,26 @@ def test_randomized_ghep_ritz_bounds():
     Bmh = (V / np.sqrt(ev)) @ V.T
     eps = np.linalg.norm(Bh @ Eop @ Bmh, 2)
     assert np.all(np.abs(lam[:k] - lr) <= 2 * eps * (1 + 1e-9))
+
+
+def test_randomized_ghep_filter_is_o1_when_sketch_spans_and_information_form_otherwise():
+    """The filter with the randomized GHEP equals O1 when the sketch spans the
+    range of H^T R^-1 H (k + p = m); with fewer modes its covariance equals
+    the information form with the rank-k data term (scipy inverse), and its
+    mean is O1's mean given the same predicted covariance."""
+    rng = np.random.default_rng(35)
+    N, ms = 30, [6, 6, 6]
+    Gamma, steps = _random_problem(rng, N, ms)
+    Om = rng.standard_normal((N, 6))
+    a = kalman.kf_dense(Gamma, steps)
+    b = kalman.kf_dense_randomized_ghep(Gamma, steps, Om, 6)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y["Sigma"], x["Sigma"], rtol=1e-8, atol=1e-10)
+        np.testing.assert_allclose(y["s"], x["s"], rtol=1e-8, atol=1e-10)
+    k = 3
+    c = kalman.kf_dense_randomized_ghep(Gamma, steps[:1], Om[:, :5], k)
+    lam, U = ghep.ghep_randomized(steps[0][1], steps[0][2], Gamma, Om[:, :5], k)
+    Gi = np.linalg.inv(Gamma)
+    info = np.linalg.inv(Gamma) + Gi @ (U * lam) @ U.T @ Gi
+    np.testing.assert_allclose(c[0]["Sigma"], np.linalg.inv(info), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(c[0]["s"], a[0]["s"], rtol=1e-12, atol=1e-14)
