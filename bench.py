@@ -605,9 +605,12 @@ def main():
                 "bound": "tensor", "achieved": ha["tflops"], "peak": f16_peak, "unit": "TFLOP/s",
                 "frac": ha["tflops"] / f16_peak,
                 "traffic": HAPPLY_F2_DRAM_BYTES if args.workload == "large" else None,
-                "traffic_note": "dram bytes read + written by both k_tc_apply launches of one apply (ncu, "
-                                "profiles/happly_tc_dram_large.md); includes the slot products V^T X written "
-                                "by phase 1 and read by phase 2 (2 x 8.6 GB)",
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of both k_tc_apply launches "
+                                "of one m = 1024 apply; includes the slot products V^T X written by phase 1 "
+                                "and read by phase 2 (2 x 8.6 GB)",
+                "hbm_target_note": "the apply is tensor-bound in this design (about 600 flop per algorithmic "
+                                   "byte); its algorithmic HBM rate is hbm_frac_of_measured of the measured copy "
+                                   "bandwidth, well below a 60% HBM target",
                 "peak_source": f"{src} bf16 dense {peaks['bf16_tflops']} TFLOP/s (fp16 dense rate = bf16)",
                 "frac_of_split_ceiling": 3.0 * ha["tflops"] / f16_peak,
                 "hbm_gbs_algorithmic": ha["gbs"], "hbm_frac_of_measured": ha["gbs"] / peaks["hbm_gbs"],

@@ -37,7 +37,10 @@ namespace {
 
 constexpr int kNB = 32;                  // panel width of the reduction and the back-transformation
 constexpr int kLeaf = 32;                // largest leaf of the divide and conquer (one warp)
-constexpr int kTrdThreads = 256;
+constexpr int kBT = 128;
+constexpr size_t kPrepSmem = 216 * 1024;  // shared memory of the merge preparation (s <= 3949)                 // reflectors per block of the back-transformation
+constexpr int kTrdThreads = 512;
+constexpr int kTrdSmemV = 6144;            // reflector entries staged in shared memory (48 KB)
 constexpr uint32_t kBarPolls = 1u << 24;  // bounded grid-barrier spin
 constexpr double kEps = DBL_EPSILON;
 
@@ -62,25 +65,39 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident): a
-// monotonic arrival counter; the wait is bounded and records a failure.
-__device__ void grid_barrier(unsigned* bar, unsigned& gen, int* err) {
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): an
+// arrival counter (monotonic: count = gen * gridDim.x after generation gen) and
+// a generation flag that the last CTA to arrive publishes; the others spin on
+// the flag.  The spin is bounded and records a failure in err.
+__device__ void grid_barrier(unsigned* count, unsigned* flag, unsigned& gen, int* err) {
   __syncthreads();
-  gen += gridDim.x;
   if (threadIdx.x == 0) {
+    gen++;
     __threadfence();
-    atomicAdd(bar, 1u);
-    uint32_t polls = 0;
-    while (*reinterpret_cast<volatile unsigned*>(bar) < gen) {
-      if (++polls > kBarPolls) {
-        atomicExch(err, 1);
-        break;
+    const unsigned prev = atomicAdd(count, 1u);
+    if (prev == gen * gridDim.x - 1) {
+      atomicExch(flag, gen);
+    } else {
+      uint32_t polls = 0;
+      while (*reinterpret_cast<volatile unsigned*>(flag) < gen) {
+        if (++polls > kBarPolls) {
+          atomicExch(err, 1);
+          break;
+        }
       }
-      __nanosleep(32);
     }
     __threadfence();
   }
   __syncthreads();
+}
+
+// Sum over the grid's CTAs of a per-CTA partial (part[0..G)), by the whole
+// block (one load per thread, then a block reduction); every CTA obtains the
+// same value (fixed order).
+__device__ double grid_partials_sum(const double* part, int G, double* sh) {
+  double v = 0;
+  for (int q = threadIdx.x; q < G; q += blockDim.x) v += part[q];
+  return block_sum(v, sh);
 }
 
 struct TrdArgs {
@@ -96,79 +113,106 @@ struct TrdArgs {
   double* col;   // n: current column
   double* vg;    // n: reflector
   double* pg;    // n: A v
-  double* part;  // gridDim.x * (1 + 2 kNB) partial sums
-  unsigned* bar;
+  double* part;  // 3 * gridDim.x + gridDim.x * 2 kNB partial sums (one region per phase)
+  unsigned* bar; // [0] arrival count, [1] generation flag
   int* err;
 };
 
-// One panel of the Householder reduction (lower form).  Column j of the panel
+// One panel of the Householder reduction (lower form), by every SM (the
+// column's symmetric product is FP64-FMA bound).  Column j of the panel
 // (c = j - j0):
 //   a = A[j:, j] - V[j:, :c] W[j, :c]^T - W[j:, :c] V[j, :c]^T   (current column)
 //   d_j = a_0; reflector H = I - tau v v^T with H a[1:] = beta e_1, v_0 = 1
 //   p = A[j+1:, j+1:] v - V (W^T v) - W (V^T v)                    (current matrix times v)
 //   w = tau p - tau^2/2 (p^T v) v;  V[:, c] = v, W[:, c] = w
-// The reflector (below its leading 1) is stored in A[j+2:, j].
+// The reflector (below its leading 1) is stored in A[j+2:, j].  Three grid
+// barriers per column: the correction w of column c is formed at the start of
+// column c + 1 by the CTA that owns each row there (every CTA forms the entry
+// w_{j+1} that all of them need), and after the loop for the last column.
+// Partial sums go to one region per phase, so a region is rewritten only after
+// every CTA has passed a later barrier.
 __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
   __shared__ double sh[33];
-  __shared__ double red[4][2 * kNB];
   __shared__ double wv[2 * kNB];
   __shared__ double bc[4];
+  extern __shared__ double vs[];  // v[j+1..n) when it fits
   const int64_t n = a.n;
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
   constexpr int L = 2 * kNB;
+  double* partA = a.part;
+  double* partC = a.part + G;
+  double* partB = a.part + 2 * G;  // G x 2 kNB
   unsigned gen = 0;
-  double* part2 = a.part + G;
+  double tau_prev = 0, k2_prev = 0;  // column c - 1: w = tau p - k2 v
+  int64_t s0 = 0, s1 = 0;            // rows [j+1, n) of this CTA (phases B and C)
   for (int c = 0; c < a.nbp; c++) {
     const int64_t j = a.j0 + c;
     if (j >= n) break;
-    // ---- phase A: current column on rows [j, n), this CTA's chunk
+    // ---- phase A: w of column c - 1 on this CTA's rows of [j, n), then the current column
     {
       const int64_t rows = n - j, R = (rows + G - 1) / G;
       const int64_t r0 = j + b * R, r1 = min(n, r0 + R);
+      if (c > 0) {
+        for (int64_t i = r0 + t; i < r1; i += blockDim.x) {
+          const double w = tau_prev * a.pg[i] - k2_prev * a.vg[i];
+          a.VW[i * L + kNB + c - 1] = w;
+          a.WV[i * L + c - 1] = w;
+        }
+      }
       const double* Vj = a.VW + j * L;
+      const double wjc = c > 0 ? tau_prev * a.pg[j] - k2_prev * a.vg[j] : 0.0;
+      __syncthreads();
+      // a warp per row; lane q < c forms the correction terms of column q
+      const double vjq = lane < c ? (lane == c - 1 ? wjc : Vj[kNB + lane]) : 0.0;  // W[j][q]
+      const double vjv = lane < c ? Vj[lane] : 0.0;                                // V[j][q]
       double ss = 0;
-      for (int64_t i = r0 + t; i < r1; i += blockDim.x) {
-        double v = a.A[j * n + i];  // A[i][j] = A[j][i]
+      for (int64_t i = r0 + warp; i < r1; i += nw) {
         const double* Vi = a.VW + i * L;
-        for (int q = 0; q < c; q++) v -= Vi[q] * Vj[kNB + q] + Vi[kNB + q] * Vj[q];
-        a.col[i] = v;
-        if (i >= j + 2) ss += v * v;
+        double corr = lane < c ? Vi[lane] * vjq + Vi[kNB + lane] * vjv : 0.0;
+        corr = warp_sum(corr);
+        if (lane == 0) {
+          const double v = a.A[j * n + i] - corr;  // A[i][j] = A[j][i]
+          a.col[i] = v;
+          if (i >= j + 2) ss += v * v;
+        }
       }
       ss = block_sum(ss, sh);
-      if (t == 0) a.part[b] = ss;
+      if (t == 0) partA[b] = ss;
     }
-    grid_barrier(a.bar, gen, a.err);
+    grid_barrier(a.bar, a.bar + 1, gen, a.err);
     // ---- phase B: the reflector (every CTA computes it from the same partials)
-    if (t == 0) {
-      double s2 = 0;
-      for (int q = 0; q < G; q++) s2 += a.part[q];
-      double beta = 0, tau = 0, scale = 0;
-      if (j + 1 < n) {
-        const double alpha = a.col[j + 1];
-        if (s2 == 0.0) {
-          beta = alpha;
-        } else {
-          beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-          tau = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
-        }
-      }
-      bc[0] = tau;
-      bc[1] = scale;
-      if (b == 0) {
-        a.d[j] = a.col[j];
+    {
+      const double s2 = grid_partials_sum(partA, G, sh);
+      if (t == 0) {
+        double beta = 0, tau = 0, scale = 0;
         if (j + 1 < n) {
-          a.e[j] = beta;
-          a.tau[j] = tau;
+          const double alpha = a.col[j + 1];
+          if (s2 == 0.0) {
+            beta = alpha;
+          } else {
+            beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+          }
+        }
+        bc[0] = tau;
+        bc[1] = scale;
+        if (b == 0) {
+          a.d[j] = a.col[j];
+          if (j + 1 < n) {
+            a.e[j] = beta;
+            a.tau[j] = tau;
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
     if (j + 1 >= n) break;  // the last diagonal entry has no reflector (uniform over the grid)
     const double tau = bc[0], scale = bc[1];
     const int64_t rows1 = n - j - 1, R1 = (rows1 + G - 1) / G;
-    const int64_t s0 = j + 1 + b * R1, s1 = min(n, s0 + R1);
+    s0 = j + 1 + b * R1;
+    s1 = min(n, s0 + R1);
     for (int64_t i = s0 + t; i < s1; i += blockDim.x) {
       const double v = (i == j + 1) ? 1.0 : a.col[i] * scale;
       a.vg[i] = v;
@@ -177,56 +221,64 @@ __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
       if (i >= j + 2) a.A[i * n + j] = v;
     }
     __syncthreads();
-    if (c > 0) {
-      // partial W^T v (entries 0..c-1) and V^T v (c..2c-1) over this CTA's rows
-      const int ql = t % L, rl = t / L;  // 4 row lanes x 64 entry lanes
+    // partial W^T v (entries 0..c-1) and V^T v (c..2c-1) over this CTA's rows
+    for (int qq = warp; qq < 2 * c; qq += nw) {
+      const int colofs = qq < c ? kNB + qq : qq - c;
       double acc = 0;
-      if (ql < 2 * c) {
-        const int colofs = ql < c ? kNB + ql : ql - c;
-        for (int64_t i = s0 + rl; i < s1; i += 4) acc += a.VW[i * L + colofs] * a.vg[i];
-      }
-      red[rl][ql] = acc;
-      __syncthreads();
-      if (t < 2 * c) part2[(int64_t)b * L + t] = red[0][t] + red[1][t] + red[2][t] + red[3][t];
+      for (int64_t i = s0 + lane; i < s1; i += 32) acc += a.VW[i * L + colofs] * a.vg[i];
+      acc = warp_sum(acc);
+      if (lane == 0) partB[(int64_t)b * L + qq] = acc;
     }
-    grid_barrier(a.bar, gen, a.err);
+    grid_barrier(a.bar, a.bar + 1, gen, a.err);
     // ---- phase C: p = A v - V (W^T v) - W (V^T v), a warp per row of this CTA's chunk
-    if (t < 2 * c) {
-      double s = 0;
-      for (int q = 0; q < G; q++) s += part2[(int64_t)q * L + t];
-      wv[t] = s;
+    for (int qq = warp; qq < 2 * c; qq += nw) {
+      double acc = 0;
+      for (int q = lane; q < G; q += 32) acc += partB[(int64_t)q * L + qq];
+      acc = warp_sum(acc);
+      if (lane == 0) wv[qq] = acc;
     }
+    const int64_t nv = n - j - 1;
+    const bool vsm = nv <= kTrdSmemV;
+    if (vsm)
+      for (int64_t k = t; k < nv; k += blockDim.x) vs[k] = a.vg[j + 1 + k];
     __syncthreads();
     double pv = 0;
     for (int64_t i = s0 + warp; i < s1; i += nw) {
-      const double* Ai = a.A + i * n;
-      double acc = 0;
-      for (int64_t k = j + 1 + lane; k < n; k += 32) acc += Ai[k] * a.vg[k];
-      acc = warp_sum(acc);
+      const double* Ai = a.A + i * n + j + 1;
+      const double* vv = vsm ? vs : a.vg + j + 1;
+      double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+      int64_t k = lane;
+      for (; k + 96 < nv; k += 128) {
+        acc0 += Ai[k] * vv[k];
+        acc1 += Ai[k + 32] * vv[k + 32];
+        acc2 += Ai[k + 64] * vv[k + 64];
+        acc3 += Ai[k + 96] * vv[k + 96];
+      }
+      for (; k < nv; k += 32) acc0 += Ai[k] * vv[k];
+      const double* Vi = a.VW + i * L;
+      const double corr = lane < c ? Vi[lane] * wv[lane] + Vi[kNB + lane] * wv[c + lane] : 0.0;
+      const double acc = warp_sum((acc0 + acc1) + (acc2 + acc3) - corr);
       if (lane == 0) {
-        const double* Vi = a.VW + i * L;
-        for (int q = 0; q < c; q++) acc -= Vi[q] * wv[q] + Vi[kNB + q] * wv[c + q];
         a.pg[i] = acc;
         pv += acc * a.vg[i];
       }
     }
     pv = block_sum(pv, sh);
-    if (t == 0) a.part[b] = pv;
-    grid_barrier(a.bar, gen, a.err);
-    // ---- phase D: w = tau p - tau^2/2 (p^T v) v
-    if (t == 0) {
-      double s = 0;
-      for (int q = 0; q < G; q++) s += a.part[q];
-      bc[2] = s;
-    }
-    __syncthreads();
-    const double k2 = 0.5 * tau * tau * bc[2];
+    if (t == 0) partC[b] = pv;
+    grid_barrier(a.bar, a.bar + 1, gen, a.err);
+    // w = tau p - tau^2/2 (p^T v) v, formed at the start of the next column (or below)
+    const double ptv = grid_partials_sum(partC, G, sh);
+    tau_prev = tau;
+    k2_prev = 0.5 * tau * tau * ptv;
+  }
+  // the panel's last correction column, on this CTA's rows of [j_last + 1, n)
+  const int64_t jl = a.j0 + a.nbp - 1;
+  if (jl + 1 < n) {
     for (int64_t i = s0 + t; i < s1; i += blockDim.x) {
-      const double w = tau * a.pg[i] - k2 * a.vg[i];
-      a.VW[i * L + kNB + c] = w;
-      a.WV[i * L + c] = w;
+      const double w = tau_prev * a.pg[i] - k2_prev * a.vg[i];
+      a.VW[i * L + kNB + a.nbp - 1] = w;
+      a.WV[i * L + a.nbp - 1] = w;
     }
-    grid_barrier(a.bar, gen, a.err);
   }
 }
 
@@ -361,103 +413,230 @@ struct DcMerge {
   int* ctl;     // [0] K, [1] number of rotations, [2] deflated count, [3] error
   int* src;     // final position -> source (>= 0: non-deflated root, < 0: -1 - deflated index)
   double* rho;  // [0]
+  int* iscr;    // 4 n ints of preparation scratch (when shared memory is too small)
+  double* dscr; // n words of preparation scratch
 };
 
-// Merge preparation (one CTA; the sequential scans on thread 0): z from the
-// children's eigenvectors, the children's sorted eigenvalue lists merged,
-// deflation, the remaining poles and z compacted.
-__global__ void k_dc_prep(int64_t off, int s, int m, int64_t bidx, const double* __restrict__ e,
-                          const double* __restrict__ D, const double* __restrict__ Q, int64_t ldq, DcMerge mg,
-                          double* __restrict__ zc) {
+// Order-preserving integer key of a double (compares of keys are integer
+// compares; the serial scans below avoid long FP64 dependency chains).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+
+// Exclusive prefix sums of flags[0..s) into pos (block-wide; thread t takes a
+// contiguous chunk); returns the total.
+__device__ int block_scan_flags(const int* flags, int s, int* pos, int* cnt) {
+  const int T = blockDim.x, t = threadIdx.x;
+  const int chunk = (s + T - 1) / T, lo = min(s, t * chunk), hi = min(s, lo + chunk);
+  int c = 0;
+  for (int p = lo; p < hi; p++) c += flags[p];
+  cnt[t] = c;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int u = 0; u < T; u++) {
+      const int x = cnt[u];
+      cnt[u] = acc;
+      acc += x;
+    }
+    cnt[T] = acc;
+  }
+  __syncthreads();
+  int o = cnt[t];
+  for (int p = lo; p < hi; p++) {
+    pos[p] = o;
+    o += flags[p];
+  }
+  const int total = cnt[T];
+  __syncthreads();
+  return total;
+}
+
+constexpr int kPrepThreads = 512;
+
+// Merge preparation (one CTA; copies in shared memory when they fit): z from
+// the children's eigenvectors, the children's sorted eigenvalue lists merged
+// (on integer keys), deflation, the remaining poles and z compacted.
+// Deflation (scan in ascending order of d): a pole with rho |z_j| <= tol is
+// deflated; otherwise, with i the previous surviving pole, the rotation in the
+// (i, j) plane that zeroes z_i is taken when |(d_j - d_i) c s| <= tol, which
+// deflates i.  The tests of consecutive survivors are formed in parallel from
+// the merged values; the serial walk recomputes a test only after a rotation
+// changed its left pole.  Dynamic shared memory: kPrepWords(s) words of 8 bytes.
+__global__ void __launch_bounds__(kPrepThreads) k_dc_prep(int64_t off, int s, int m, int64_t bidx,
+                                                          const double* __restrict__ e,
+                                                          const double* __restrict__ D,
+                                                          const double* __restrict__ Q, int64_t ldq, DcMerge mg,
+                                                          double* __restrict__ zc, int use_smem) {
+  extern __shared__ double psm[];
+  __shared__ int cnt[kPrepThreads + 1];
+  __shared__ double shr[33];
+  // shared memory (or the global scratch of the merge): Dp, zp, key (s words
+  // each), then eight int arrays of s entries
+  double* Dp = use_smem ? psm : mg.Dp;   // merged, then rotated
+  double* zp = use_smem ? psm + s : mg.zp;
+  long long* key = reinterpret_cast<long long*>(use_smem ? psm + 2 * s : mg.dscr);
+  int* ib = use_smem ? reinterpret_cast<int*>(psm + 3 * s) : nullptr;
+  int* perm = use_smem ? ib : mg.perm;
+  int* defl = use_smem ? ib + s : mg.src;
+  int* nd = use_smem ? ib + 2 * s : mg.nd;
+  int* df = use_smem ? ib + 3 * s : mg.df;
+  int* sv = use_smem ? ib + 4 * s : mg.iscr;        // survivors, in order
+  int* flg = use_smem ? ib + 5 * s : mg.iscr + s;   // flags
+  int* pos = use_smem ? ib + 6 * s : mg.iscr + 2 * s;
+  int* rot = use_smem ? ib + 7 * s : mg.iscr + 3 * s;  // pair u (survivors u-1, u) rotates
+  const int t = threadIdx.x, T = blockDim.x;
   const double beta = e[bidx];
   const double sgn = beta < 0 ? -1.0 : 1.0;
   const double inv2 = 0.70710678118654752440;
-  for (int p = threadIdx.x; p < s; p += blockDim.x)
-    zc[p] = (p < m ? Q[(off + m - 1) * ldq + off + p] : sgn * Q[(off + m) * ldq + off + p]) * inv2;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
   const double rho = 2.0 * fabs(beta);
-  mg.rho[0] = rho;
-  // merge the two ascending lists
-  int a = 0, b2 = m, q = 0;
-  while (a < m || b2 < s) {
-    int pick;
-    if (b2 >= s || (a < m && D[off + a] <= D[off + b2])) pick = a++;
-    else pick = b2++;
-    mg.perm[q] = pick;
-    mg.Dp[q] = D[off + pick];
-    mg.zp[q] = zc[pick];
-    q++;
+  for (int p = t; p < s; p += T) {
+    zc[p] = (p < m ? Q[(off + m - 1) * ldq + off + p] : sgn * Q[(off + m) * ldq + off + p]) * inv2;
+    key[p] = dkey(D[off + p]);
   }
+  __syncthreads();
+  // merge the two ascending lists (integer keys)
+  if (t == 0) {
+    mg.rho[0] = rho;
+    int a = 0, b2 = m, q = 0;
+    while (a < m || b2 < s) perm[q++] = (b2 >= s || (a < m && key[a] <= key[b2])) ? a++ : b2++;
+  }
+  __syncthreads();
   double dmax = 0, zmax = 0;
-  for (int p = 0; p < s; p++) {
-    dmax = fmax(dmax, fabs(mg.Dp[p]));
-    zmax = fmax(zmax, fabs(mg.zp[p]));
+  for (int q = t; q < s; q += T) {
+    Dp[q] = D[off + perm[q]];
+    zp[q] = zc[perm[q]];
+    dmax = fmax(dmax, fabs(Dp[q]));
+    zmax = fmax(zmax, fabs(zp[q]));
   }
-  const double tol = 8.0 * kEps * fmax(dmax, rho * zmax);
-  // deflation scan: flag 1 = deflated; mg.src doubles as the flag array here
-  int* defl = mg.src;
-  int ng = 0, pend = -1;
-  for (int j = 0; j < s; j++) {
-    defl[j] = 0;
-    if (rho * fabs(mg.zp[j]) <= tol) {
-      defl[j] = 1;
-      continue;
+  // block maxima (the partial maxima are non-negative: reuse block_sum's shape)
+  {
+    const int lane = t & 31, warp = t >> 5, nw = T >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
     }
-    if (pend < 0) {
-      pend = j;
-      continue;
+    if (lane == 0) {
+      shr[warp] = dmax;
+      shr[16 + warp] = zmax;
     }
-    const int i = pend;
-    const double r = hypot(mg.zp[i], mg.zp[j]);
-    const double c = mg.zp[j] / r, sn = -mg.zp[i] / r;
-    const double tdiff = mg.Dp[j] - mg.Dp[i];
-    if (fabs(tdiff * c * sn) <= tol) {
-      mg.zp[j] = r;
-      mg.zp[i] = 0.0;
-      mg.gi[ng] = i;
-      mg.gj[ng] = j;
-      mg.gc[ng] = c;
-      mg.gs[ng] = sn;
-      ng++;
-      const double di = mg.Dp[i], dj = mg.Dp[j];
-      mg.Dp[i] = di * c * c + dj * sn * sn;
-      mg.Dp[j] = di * sn * sn + dj * c * c;
-      defl[i] = 1;
+    __syncthreads();
+    if (t == 0) {
+      double a = 0, b = 0;
+      for (int w = 0; w < nw; w++) {
+        a = fmax(a, shr[w]);
+        b = fmax(b, shr[16 + w]);
+      }
+      shr[32] = 8.0 * kEps * fmax(a, rho * b);
     }
-    pend = j;
+    __syncthreads();
   }
-  int K = 0, nf = 0;
-  for (int p = 0; p < s; p++) {
-    if (defl[p]) mg.df[nf++] = p;
-    else mg.nd[K++] = p;
+  const double tol = shr[32];
+  // survivors of the small-z test, compacted in order
+  for (int q = t; q < s; q += T) flg[q] = rho * fabs(zp[q]) <= tol ? 0 : 1;
+  __syncthreads();
+  const int nsv = block_scan_flags(flg, s, pos, cnt);
+  for (int q = t; q < s; q += T)
+    if (flg[q]) sv[pos[q]] = q;
+  __syncthreads();
+  // the rotation test of each consecutive pair of survivors, from the merged values
+  for (int u = t + 1; u < nsv; u += T) {
+    const int i = sv[u - 1], j = sv[u];
+    const double r = sqrt(zp[i] * zp[i] + zp[j] * zp[j]);
+    rot[u] = fabs((Dp[j] - Dp[i]) * (zp[j] / r) * (zp[i] / r)) <= tol ? 1 : 0;
   }
-  // both lists by ascending Dp (the rotations may have moved a value slightly)
-  for (int u = 1; u < K; u++) {
-    const int x = mg.nd[u];
-    int v = u - 1;
-    while (v >= 0 && mg.Dp[mg.nd[v]] > mg.Dp[x]) {
-      mg.nd[v + 1] = mg.nd[v];
-      v--;
+  for (int q = t; q < s; q += T) defl[q] = flg[q] ? 0 : 1;
+  __syncthreads();
+  // serial walk over the survivors: rotations (recomputing a pair's test only
+  // when the previous rotation changed its left pole)
+  if (t == 0) {
+    int ng = 0;
+    bool changed = false;
+    for (int u = 1; u < nsv; u++) {
+      const int i = sv[u - 1], j = sv[u];
+      bool take = rot[u] != 0;
+      double r = 0, c = 0, sn = 0;
+      if (take || changed) {
+        r = sqrt(zp[i] * zp[i] + zp[j] * zp[j]);
+        c = zp[j] / r;
+        sn = -zp[i] / r;
+        if (changed) take = fabs((Dp[j] - Dp[i]) * c * sn) <= tol;
+      }
+      changed = false;
+      if (take) {
+        zp[j] = r;
+        zp[i] = 0.0;
+        mg.gi[ng] = i;
+        mg.gj[ng] = j;
+        mg.gc[ng] = c;
+        mg.gs[ng] = sn;
+        ng++;
+        const double di = Dp[i], dj = Dp[j];
+        Dp[i] = di * c * c + dj * sn * sn;
+        Dp[j] = di * sn * sn + dj * c * c;
+        defl[i] = 1;
+        changed = true;
+      }
     }
-    mg.nd[v + 1] = x;
+    cnt[0] = ng;
   }
-  for (int u = 1; u < nf; u++) {
-    const int x = mg.df[u];
-    int v = u - 1;
-    while (v >= 0 && mg.Dp[mg.df[v]] > mg.Dp[x]) {
-      mg.df[v + 1] = mg.df[v];
-      v--;
+  __syncthreads();
+  const int ng = cnt[0];
+  __syncthreads();
+  // non-deflated and deflated positions, each in position order, then by
+  // ascending Dp (the rotations may have moved a value slightly)
+  for (int q = t; q < s; q += T) flg[q] = defl[q] ? 0 : 1;
+  __syncthreads();
+  const int K = block_scan_flags(flg, s, pos, cnt);
+  for (int q = t; q < s; q += T) {
+    if (flg[q]) nd[pos[q]] = q;
+    else df[q - pos[q]] = q;
+    key[q] = dkey(Dp[q]);
+  }
+  __syncthreads();
+  const int nf = s - K;
+  if (t == 0) {
+    for (int u = 1; u < K; u++) {
+      const int x = nd[u];
+      const long long kx = key[x];
+      int v = u - 1;
+      while (v >= 0 && key[nd[v]] > kx) {
+        nd[v + 1] = nd[v];
+        v--;
+      }
+      nd[v + 1] = x;
     }
-    mg.df[v + 1] = x;
+  } else if (t == 32) {
+    for (int u = 1; u < nf; u++) {
+      const int x = df[u];
+      const long long kx = key[x];
+      int v = u - 1;
+      while (v >= 0 && key[df[v]] > kx) {
+        df[v + 1] = df[v];
+        v--;
+      }
+      df[v + 1] = x;
+    }
   }
-  for (int u = 0; u < K; u++) {
-    mg.dk[u] = mg.Dp[mg.nd[u]];
-    mg.zk[u] = mg.zp[mg.nd[u]];
+  if (t == 64) {
+    mg.ctl[0] = K;
+    mg.ctl[1] = ng;
+    mg.ctl[2] = nf;
   }
-  mg.ctl[0] = K;
-  mg.ctl[1] = ng;
-  mg.ctl[2] = nf;
+  __syncthreads();
+  for (int u = t; u < K; u += T) {
+    mg.dk[u] = Dp[nd[u]];
+    mg.zk[u] = zp[nd[u]];
+  }
+  if (use_smem) {
+    for (int p = t; p < s; p += T) {
+      mg.perm[p] = perm[p];
+      mg.Dp[p] = Dp[p];
+    }
+    for (int u = t; u < K; u += T) mg.nd[u] = nd[u];
+    for (int u = t; u < nf; u += T) mg.df[u] = df[u];
+  }
 }
 
 // QsT[q][r] = column perm[q] of the node's block (row r), then the deflation
@@ -485,10 +664,11 @@ __global__ void k_dc_gather_rotate(int64_t off, int s, const double* __restrict_
 // accurate.  Each iteration fits the poles left of the interval by
 // c1 + s1/(d_j - l) and those right of it by c2 + s2/(d_j+1 - l) (value and
 // derivative matched at the current point) and takes the root of the fit in
-// the interval, falling back to bisection of the bracket.
+// the interval, falling back to bisection of the bracket.  One warp per root:
+// the lanes split the sums over the poles.
 __global__ void k_dc_secular(DcMerge mg, int* __restrict__ err) {
   const int K = mg.ctl[0];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= K) return;
   const double rho = mg.rho[0];
   const double* dk = mg.dk;
@@ -497,8 +677,9 @@ __global__ void k_dc_secular(DcMerge mg, int* __restrict__ err) {
   double lo, hi;
   if (j < K - 1) {
     const double mid = 0.5 * (dk[j + 1] - dk[j]);
-    double f = 1.0 / rho;
-    for (int i = 0; i < K; i++) f += zk[i] * zk[i] / ((dk[i] - dk[j]) - mid);
+    double f = 0;
+    for (int i = lane; i < K; i += 32) f += zk[i] * zk[i] / ((dk[i] - dk[j]) - mid);
+    f = warp_sum(f) + 1.0 / rho;
     if (f >= 0) {
       o = j;
       lo = 0.0;
@@ -511,7 +692,8 @@ __global__ void k_dc_secular(DcMerge mg, int* __restrict__ err) {
   } else {
     o = j;
     double z2 = 0;
-    for (int i = 0; i < K; i++) z2 += zk[i] * zk[i];
+    for (int i = lane; i < K; i += 32) z2 += zk[i] * zk[i];
+    z2 = warp_sum(z2);
     lo = 0.0;
     hi = rho * z2;
   }
@@ -519,20 +701,26 @@ __global__ void k_dc_secular(DcMerge mg, int* __restrict__ err) {
   double tau = 0.5 * (lo + hi);
   bool conv = false;
   for (int it = 0; it < 200; it++) {
-    double F = 1.0 / rho, aF = 1.0 / rho, p1 = 0, dp1 = 0, p2 = 0, dp2 = 0;
-    for (int i = 0; i < K; i++) {
-      const double del = (dk[i] - dor) - tau;
-      const double tm = zk[i] * zk[i] / del;
+    double F = 0, aF = 0, p1 = 0, dp1 = 0, p2 = 0, dp2 = 0;
+    for (int i = lane; i < K; i += 32) {
+      const double rdel = 1.0 / ((dk[i] - dor) - tau);
+      const double tm = zk[i] * zk[i] * rdel;
       F += tm;
       aF += fabs(tm);
       if (i <= j) {
         p1 += tm;
-        dp1 += tm / del;
+        dp1 += tm * rdel;
       } else {
         p2 += tm;
-        dp2 += tm / del;
+        dp2 += tm * rdel;
       }
     }
+    F = warp_sum(F) + 1.0 / rho;
+    aF = warp_sum(aF) + 1.0 / rho;
+    p1 = warp_sum(p1);
+    dp1 = warp_sum(dp1);
+    p2 = warp_sum(p2);
+    dp2 = warp_sum(dp2);
     if (fabs(F) <= 8.0 * kEps * aF) {
       conv = true;
       break;
@@ -571,51 +759,58 @@ __global__ void k_dc_secular(DcMerge mg, int* __restrict__ err) {
     }
     tau = nt;
   }
-  if (!conv) atomicExch(err, 3);
-  mg.orig[j] = o;
-  mg.taus[j] = tau;
-  mg.lam[j] = dor + tau;
+  if (lane == 0) {
+    if (!conv) atomicExch(err, 3);
+    mg.orig[j] = o;
+    mg.taus[j] = tau;
+    mg.lam[j] = dor + tau;
+  }
 }
 
 // Loewner: zh_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)),
-// as a product of ratios of order one; sign of z_i.
+// as a product of ratios of order one; sign of z_i.  Warp per i: each lane
+// multiplies a strided subset, the partial products are combined.
 __global__ void k_dc_lowner(DcMerge mg) {
   const int K = mg.ctl[0];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= K) return;
   const double* dk = mg.dk;
   const double di = dk[i];
-  auto lmd = [&](int j) { return (dk[mg.orig[j]] - di) + mg.taus[j]; };
-  double prod = lmd(K - 1) / mg.rho[0];
-  for (int j = 0; j < K - 1; j++) prod *= lmd(j) / ((j < i ? dk[j] : dk[j + 1]) - di);
-  mg.zh[i] = copysign(sqrt(fmax(prod, 0.0)), mg.zk[i]);
+  double prod = 1.0;
+  for (int j = lane; j < K; j += 32) {
+    const double lmd = (dk[mg.orig[j]] - di) + mg.taus[j];
+    prod *= j == K - 1 ? lmd / mg.rho[0] : lmd / ((j < i ? dk[j] : dk[j + 1]) - di);
+  }
+  for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, o);
+  if (lane == 0) mg.zh[i] = copysign(sqrt(fmax(prod, 0.0)), mg.zk[i]);
 }
 
-// Column norms of u_j = zh / (d - lambda_j) (thread per column).
+// Column norms of u_j = zh / (d - lambda_j) (warp per column).
 __global__ void k_dc_colnorm(DcMerge mg) {
   const int K = mg.ctl[0];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= K) return;
   const double dor = mg.dk[mg.orig[j]], tj = mg.taus[j];
   double s = 0;
-  for (int i = 0; i < K; i++) {
+  for (int i = lane; i < K; i += 32) {
     const double u = mg.zh[i] / ((mg.dk[i] - dor) - tj);
     s += u * u;
   }
-  mg.cnrm[j] = sqrt(s);
+  s = warp_sum(s);
+  if (lane == 0) mg.cnrm[j] = sqrt(s);
 }
 
-// U[i][j] = zh_i / (d_i - lambda_j) / |u_j| (K x K, row-major), and the
+// UT[j][i] = zh_i / (d_i - lambda_j) / |u_j| (K x K, row j = u_j), and the
 // non-deflated columns of QsT gathered: QselT[q][r] = QsT[nd[q]][r].
-__global__ void k_dc_vectors(int s, DcMerge mg, double* __restrict__ U, const double* __restrict__ QsT,
+__global__ void k_dc_vectors(int s, DcMerge mg, double* __restrict__ UT, const double* __restrict__ QsT,
                              double* __restrict__ QselT) {
   const int K = mg.ctl[0];
   const int64_t tot = (int64_t)K * K, tot2 = (int64_t)K * s;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot + tot2;
        e += (int64_t)gridDim.x * blockDim.x) {
     if (e < tot) {
-      const int i = (int)(e / K), j = (int)(e % K);
-      U[e] = mg.zh[i] / ((mg.dk[i] - mg.dk[mg.orig[j]]) - mg.taus[j]) / mg.cnrm[j];
+      const int j = (int)(e / K), i = (int)(e % K);
+      UT[e] = mg.zh[i] / ((mg.dk[i] - mg.dk[mg.orig[j]]) - mg.taus[j]) / mg.cnrm[j];
     } else {
       const int64_t f = e - tot;
       const int q = (int)(f / s), r = (int)(f % s);
@@ -643,16 +838,15 @@ __global__ void k_dc_order(int64_t off, DcMerge mg, double* __restrict__ D) {
   }
 }
 
-// Q block column t <- its source: row r of Qn (s x K) or of column df[.] of QsT.
-__global__ void k_dc_assemble(int64_t off, int s, DcMerge mg, const double* __restrict__ Qn,
+// Q block column t <- its source: QnT[q] (the q-th new eigenvector, K x s) or
+// QsT[df[.]] (a deflated column).
+__global__ void k_dc_assemble(int64_t off, int s, DcMerge mg, const double* __restrict__ QnT,
                               const double* __restrict__ QsT, double* __restrict__ Q, int64_t ldq) {
-  const int K = mg.ctl[0];
   const int64_t tot = (int64_t)s * s;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / s), t = (int)(e % s);
     const int sc = mg.src[t];
-    Q[(off + r) * ldq + off + t] =
-        sc >= 0 ? Qn[(int64_t)r * K + sc] : QsT[(int64_t)mg.df[-1 - sc] * s + r];
+    Q[(off + r) * ldq + off + t] = sc >= 0 ? QnT[(int64_t)sc * s + r] : QsT[(int64_t)mg.df[-1 - sc] * s + r];
   }
 }
 
@@ -670,19 +864,41 @@ __global__ void k_bt_vp(int64_t n, int64_t j0, int nbp, const double* __restrict
 }
 
 // Triangular factor of the compact WY form H_j0 ... H_j0+nbp-1 = I - V T V^T:
-// T[c][c] = tau_c, T[0:c, c] = -tau_c T[0:c, 0:c] (V^T V)[0:c, c].
+// T[c][c] = tau_c, T[0:c, c] = -tau_c T[0:c, 0:c] (V^T V)[0:c, c].  Row r of T
+// depends only on row r and V^T V, so thread r forms its row; both triangles
+// are kept packed in shared memory (G[q][c] for q < c at c(c-1)/2 + q, T[r][c]
+// for r <= c at c(c+1)/2 + r).
 __global__ void k_bt_tfactor(int nbp, const double* __restrict__ VtV, const double* __restrict__ tau,
                              double* __restrict__ T) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int e = 0; e < nbp * nbp; e++) T[e] = 0.0;
-  for (int c = 0; c < nbp; c++) {
-    const double tc = tau[c];
-    T[c * nbp + c] = tc;
-    for (int r = 0; r < c; r++) {
-      double s = 0;
-      for (int q = r; q < c; q++) s += T[r * nbp + q] * VtV[q * nbp + c];
-      T[r * nbp + c] = -tc * s;
+  extern __shared__ double smt[];
+  double* Gu = smt;                          // nbp (nbp - 1) / 2
+  double* Tp = smt + nbp * (nbp - 1) / 2;    // nbp (nbp + 1) / 2
+  const int r = threadIdx.x;
+  for (int e = r; e < nbp * nbp; e += blockDim.x) {
+    const int q = e / nbp, c = e % nbp;
+    if (q < c) Gu[c * (c - 1) / 2 + q] = VtV[e];
+  }
+  __syncthreads();
+  if (r < nbp) {
+    Tp[r * (r + 1) / 2 + r] = tau[r];
+    for (int c = r + 1; c < nbp; c++) {
+      const double* gc = Gu + c * (c - 1) / 2;
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // independent chains (FP64 latency)
+      int q = r;
+      for (; q + 3 < c; q += 4) {
+        a0 += Tp[q * (q + 1) / 2 + r] * gc[q];
+        a1 += Tp[(q + 1) * (q + 2) / 2 + r] * gc[q + 1];
+        a2 += Tp[(q + 2) * (q + 3) / 2 + r] * gc[q + 2];
+        a3 += Tp[(q + 3) * (q + 4) / 2 + r] * gc[q + 3];
+      }
+      for (; q < c; q++) a0 += Tp[q * (q + 1) / 2 + r] * gc[q];
+      Tp[c * (c + 1) / 2 + r] = -tau[c] * ((a0 + a1) + (a2 + a3));
     }
+  }
+  __syncthreads();
+  for (int e = r; e < nbp * nbp; e += blockDim.x) {
+    const int rr = e / nbp, c = e % nbp;
+    T[e] = rr <= c ? Tp[c * (c + 1) / 2 + rr] : 0.0;
   }
 }
 
@@ -748,6 +964,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   want = std::max(0, std::min(want, n));
   const int64_t N = n, nn = N * N;
   const int64_t L = 2 * kNB;
+  DevBuf gws;  // partial sums of the back-transformation's long products
   // workspace layout (doubles)
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -756,10 +973,10 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   const int64_t w_X = N * std::max(want, 1);
   const int64_t w_VW = N * L, w_WV = N * L;
   const int64_t w_vec = 20 * N + 64;                       // d, e, tau, col, vg, pg, zc, the merge arrays
-  const int64_t w_part = (int64_t)gmax * (1 + L) + 64;
-  const int64_t w_small = 4 * kNB * kNB + 2 * N * kNB + 64;  // back-transformation
+  const int64_t w_part = (int64_t)gmax * (3 + L) + 64;
+  const int64_t w_small = 2 * kBT * kBT + N * kBT + kBT * std::max<int64_t>(want, 1) + 64;  // back-transformation
   const int64_t total = w_Q + w_QsT + w_QselT + w_U + w_Qn + w_X + w_VW + w_WV + w_vec + w_part + w_small;
-  const size_t ints = (size_t)12 * N + 64;
+  const size_t ints = (size_t)15 * N + 128;
   const size_t need = (size_t)total * 8 + ints * 4 + 256;
   if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
   double* p = ws.as<double>();
@@ -795,11 +1012,12 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   mg.cnrm = take(N);
   mg.rho = take(8);
   double* zc = take(N);
+  mg.dscr = take(N);
   double* part = take(w_part);
-  double* Vp = take(N * kNB);
-  double* Y1 = take(N * kNB);
-  double* VtV = take(kNB * kNB);
-  double* Tf = take(kNB * kNB);
+  double* Vp = take(N * kBT);
+  double* Y1 = take(kBT * std::max<int64_t>(want, 1));
+  double* VtV = take(kBT * kBT);
+  double* Tf = take(kBT * kBT);
   int* ip = reinterpret_cast<int*>(p + 8);
   mg.perm = ip;
   mg.gi = ip + N;
@@ -812,7 +1030,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   int* lsize_d = ip + 8 * N;
   int* splits_d = ip + 9 * N;
   mg.ctl = ip + 10 * N;   // 8 ints
-  unsigned* bar = reinterpret_cast<unsigned*>(ip + 10 * N + 8);
+  mg.iscr = ip + 10 * N + 64;  // 4 N ints
   int* err = ip + 10 * N + 16;
   FKF_CUDA(ctx, cudaMemsetAsync(err, 0, 4 * sizeof(int), st));
   FKF_CUDA(ctx, cudaMemsetAsync(e, 0, N * 8, st));
@@ -820,16 +1038,20 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   k_symmetrize_full<<<grid_for(nn), 256, 0, st>>>(N, A);
   FKF_LAUNCHED(ctx);
 
-  // ---- 1. tridiagonal reduction
+  // ---- 1. tridiagonal reduction: one cooperative panel kernel over every SM per panel
+  unsigned* bar = reinterpret_cast<unsigned*>(ip + 10 * N + 8);
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kTrdSmemV * sizeof(double))));
   for (int64_t j0 = 0; j0 < N; j0 += kNB) {
     const int nbp = (int)std::min<int64_t>(kNB, N - j0);
     FKF_CUDA(ctx, cudaMemsetAsync(VW, 0, w_VW * 8, st));
     FKF_CUDA(ctx, cudaMemsetAsync(WV, 0, w_WV * 8, st));
-    FKF_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(gmax, (N - j0) / 16));
+    FKF_CUDA(ctx, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(gmax, (N - j0) / 8));
     TrdArgs ta{A, N, j0, nbp, VW, WV, d, e, tau, col, vg, pg, part, bar, err};
     void* args[] = {&ta};
-    FKF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_trd_panel, dim3(G), dim3(kTrdThreads), args, 0, st));
+    const size_t vsm = (size_t)std::min<int64_t>(N, kTrdSmemV) * sizeof(double);
+    FKF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_trd_panel, dim3(G), dim3(kTrdThreads), args, vsm, st));
     ctx->launches++;
     const int64_t j1 = j0 + nbp;
     if (j1 < N) {
@@ -854,9 +1076,13 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   double* Dv = w_dev;  // eigenvalues of the nodes, in place
   k_dc_leaf<<<(unsigned)loff.size(), 32, 0, st>>>(loff_d, lsize_d, d, e, Dv, Q, N, err);
   FKF_LAUNCHED(ctx);
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem));
   for (const Node& nd : merges) {
     const int s = nd.s;
-    k_dc_prep<<<1, 256, 0, st>>>(nd.off, s, nd.m, nd.off + nd.m - 1, e, Dv, Q, N, mg, zc);
+    const size_t psm = (size_t)s * (3 * sizeof(double) + 8 * sizeof(int));
+    const int use_smem = psm <= kPrepSmem ? 1 : 0;
+    k_dc_prep<<<1, kPrepThreads, use_smem ? psm : 0, st>>>(nd.off, s, nd.m, nd.off + nd.m - 1, e, Dv, Q, N, mg, zc,
+                                                           use_smem);
     FKF_LAUNCHED(ctx);
     int hc[3] = {0, 0, 0};
     FKF_CUDA(ctx, cudaMemcpyAsync(hc, mg.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -865,16 +1091,17 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     FKF_CUDA(ctx, cudaStreamSynchronize(st));
     const int K = hc[0];
     if (K > 0) {
-      k_dc_secular<<<(unsigned)cdiv(K, 64), 64, 0, st>>>(mg, err);
+      const unsigned wb = (unsigned)cdiv((int64_t)K * 32, 128);  // a warp per root / index
+      k_dc_secular<<<wb, 128, 0, st>>>(mg, err);
       FKF_LAUNCHED(ctx);
-      k_dc_lowner<<<(unsigned)cdiv(K, 64), 64, 0, st>>>(mg);
+      k_dc_lowner<<<wb, 128, 0, st>>>(mg);
       FKF_LAUNCHED(ctx);
-      k_dc_colnorm<<<(unsigned)cdiv(K, 64), 64, 0, st>>>(mg);
+      k_dc_colnorm<<<wb, 128, 0, st>>>(mg);
       FKF_LAUNCHED(ctx);
       k_dc_vectors<<<grid_for((int64_t)K * K + (int64_t)K * s), 256, 0, st>>>(s, mg, U, QsT, QselT);
       FKF_LAUNCHED(ctx);
-      // Qn (s x K) = QselT^T U
-      FKF_TRY(gemm_f64(ctx, true, false, s, K, K, 1.0, QselT, s, U, K, 0.0, Qn, K));
+      // QnT (K x s) = UT QselT: row q = the q-th new eigenvector in the node's basis
+      FKF_TRY(gemm_f64(ctx, false, false, K, s, K, 1.0, U, K, QselT, s, 0.0, Qn, s));
     }
     k_dc_order<<<1, 32, 0, st>>>(nd.off, mg, Dv);
     FKF_LAUNCHED(ctx);
@@ -887,18 +1114,21 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     const int64_t k = want;
     k_copy_cols<<<grid_for(N * k), 256, 0, st>>>(N, k, Q + (N - k), N, X, k);
     FKF_LAUNCHED(ctx);
-    const int64_t nref = N - 1;  // reflectors 0 .. n-2 (the last has tau = 0 when n - 2 < 0)
-    for (int64_t j0 = ((nref - 1) / kNB) * kNB; nref > 0 && j0 >= 0; j0 -= kNB) {
-      const int nbp = (int)std::min<int64_t>(kNB, nref - j0);
+    const int64_t nref = N - 1;  // reflectors 0 .. n-2
+    FKF_CUDA(ctx, cudaFuncSetAttribute(k_bt_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kBT * kBT * (int)sizeof(double) + 64));
+    for (int64_t j0 = nref > 0 ? ((nref - 1) / kBT) * kBT : -1; j0 >= 0; j0 -= kBT) {
+      const int nbp = (int)std::min<int64_t>(kBT, nref - j0);
       const int64_t rows = N - j0 - 1;
       if (rows <= 0 || nbp <= 0) continue;
       k_bt_vp<<<grid_for(rows * nbp), 256, 0, st>>>(N, j0, nbp, A, Vp);
       FKF_LAUNCHED(ctx);
-      FKF_TRY(gemm_f64(ctx, true, false, nbp, nbp, rows, 1.0, Vp, nbp, Vp, nbp, 0.0, VtV, nbp));
-      k_bt_tfactor<<<1, 32, 0, st>>>(nbp, VtV, tau + j0, Tf);
+      FKF_TRY(gram_f64(ctx, nbp, nbp, rows, Vp, nbp, Vp, nbp, VtV, nbp, gws));
+      k_bt_tfactor<<<1, kBT, (size_t)nbp * nbp * sizeof(double) + 64, st>>>(nbp, VtV, tau + j0, Tf);
       FKF_LAUNCHED(ctx);
       double* Xs = X + (j0 + 1) * k;
-      FKF_TRY(gemm_f64(ctx, true, false, nbp, k, rows, 1.0, Vp, nbp, Xs, k, 0.0, Y1, k));
+      // X[j0+1:] -= V (T (V^T X[j0+1:]))
+      FKF_TRY(gram_f64(ctx, nbp, k, rows, Vp, nbp, Xs, k, Y1, k, gws));
       FKF_TRY(gemm_f64(ctx, false, false, nbp, k, nbp, 1.0, Tf, nbp, Y1, k, 0.0, QselT, k));
       FKF_TRY(gemm_f64(ctx, false, false, rows, k, nbp, -1.0, Vp, nbp, QselT, k, 1.0, Xs, k));
     }
