@@ -423,68 +423,80 @@ def run_gpu(args, rank, world):
     return res, wl
 
 
-def batch_bench(nb, steps, warmup):
-    """nb independent FP32 filters of uneven size (N log-uniform in [16384, 131072] on square
-    grids, m = n_src x n_rec in [64, 512], nu in {1/2, 3/2}, ell in [0.02, 0.3]; seeded):
-    filter steps/s summed over the batch, stepped one at a time vs fkf_filter_step_batched
-    (merged H-apply launches)."""
+def batch_spec(nb, seed):
+    """Uneven filters of the batch workload: N log-uniform in [16384, 262144] on square grids, m
+    log-uniform in [64, 1024] as n_src x n_rec rays, nu in {1/2, 3/2}, ell uniform in [0.02, 0.3]."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(nb):
+        g = int(round(np.sqrt(np.exp(rng.uniform(np.log(16384), np.log(262144))))))
+        m = np.exp(rng.uniform(np.log(64), np.log(1024)))
+        ns = max(2, int(round(np.sqrt(m))))
+        nr = max(2, int(round(m / ns)))
+        specs.append(((g, g), ns, nr, float(rng.choice([0.5, 1.5])), float(rng.uniform(0.02, 0.3))))
+    return specs
+
+
+def batch_bench(nb, steps, warmup, mem_reserve_gb=24.0):
+    """The batch workload: nb independent FP32 filters of uneven size (batch_spec), created while
+    device memory allows (mem_reserve_gb kept free); filter steps/s summed over the batch, the same
+    filters stepped one at a time and through fkf_filter_step_batched (merged H-apply launches),
+    host wall clock around the steps (every step synchronises its own stream)."""
     import torch
 
     import synth
     from paper_1405_2276_gb300 import fkf
 
-    rng = np.random.default_rng(synth.BASE_SEED + 77)
-    specs = []
-    for i in range(nb):
-        n_target = int(np.exp(rng.uniform(np.log(16384), np.log(131072))))
-        g = max(16, int(round(np.sqrt(n_target))))
-        ns, nr = int(rng.integers(8, 24)), int(rng.integers(8, 24))
-        specs.append(((g, g), ns, nr, float(rng.choice([0.5, 1.5])), float(rng.uniform(0.02, 0.3))))
-    sets = []
-    for rep in range(2):
-        objs = []
-        for i, (grid, ns, nr, nu, ell) in enumerate(specs):
-            wl = synth.tomography_workload(grid, ns, nr, warmup + steps, ell, 1.0, 1e-4,
-                                           seed=synth.BASE_SEED + 5000 + i)
-            ctx = fkf.fkf_create(0)
-            hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32,
-                                       precision=fkf.FKF_FP32)
-            m = wl["H"].nrows
-            objs.append(dict(wl=wl, ctx=ctx, hm=hm, f=fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, 2 * m)))
-        sets.append(objs)
+    specs = batch_spec(nb, synth.BASE_SEED + 77)
+    objs = []
+    t_build = time.time()
+    for i, (grid, ns, nr, nu, ell) in enumerate(specs):
+        free, _ = torch.cuda.mem_get_info()
+        if free < mem_reserve_gb * 2**30:
+            break
+        wl = synth.tomography_workload(grid, ns, nr, warmup + 2 * steps, ell, 1.0, 1e-4, seed=synth.BASE_SEED + 5000 + i)
+        ctx = fkf.fkf_create(0)
+        hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32,
+                                   precision=fkf.FKF_FP32)
+        m = wl["H"].nrows
+        # a fixed geometry keeps the rank at m: r_max = m bounds the state's memory
+        objs.append(dict(wl=wl, ctx=ctx, hm=hm, f=fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, m)))
+    t_build = time.time() - t_build
+    nf = len(objs)
 
-    def entries(objs, k):
+    def entries(k):
         return [(o["f"], o["wl"]["y"][k], o["wl"]["H"].rowptr, o["wl"]["H"].col, o["wl"]["H"].val, None, 1e-4)
                 for o in objs]
 
-    seq, bat = sets
     for k in range(warmup):
-        for o in seq:
-            h = o["wl"]["H"]
-            fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
-        fkf.fkf_filter_step_batched(entries(bat, k))
+        fkf.fkf_filter_step_batched(entries(k))
     torch.cuda.synchronize()
     t0 = time.time()
     for k in range(warmup, warmup + steps):
-        for o in seq:
+        for o in objs:
             h = o["wl"]["H"]
             fkf.fkf_filter_step(o["f"], o["wl"]["y"][k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
     torch.cuda.synchronize()
     t_seq = time.time() - t0
     merged = []
     t0 = time.time()
-    for k in range(warmup, warmup + steps):
-        _, merged = fkf.fkf_filter_step_batched(entries(bat, k), return_merged=True)
+    for k in range(warmup + steps, warmup + 2 * steps):
+        _, merged = fkf.fkf_filter_step_batched(entries(k), return_merged=True)
     torch.cuda.synchronize()
     t_bat = time.time() - t0
-    out = dict(filters=nb, steps=steps, n=[s[0][0] * s[0][1] for s in specs], m=[s[1] * s[2] for s in specs],
-               sequential_steps_per_s=nb * steps / t_seq, batched_steps_per_s=nb * steps / t_bat,
-               merged=all(merged), timing="host wall clock around the steps (each step synchronises its stream)")
-    for objs in sets:
-        for o in objs:
-            fkf.fkf_filter_destroy(o["f"])
-            fkf.fkf_hmatrix_destroy(o["hm"])
-            fkf.fkf_destroy(o["ctx"])
+    ns_ = [o["wl"]["points"].shape[0] for o in objs]
+    ms_ = [o["wl"]["H"].nrows for o in objs]
+    out = dict(filters=nf, filters_requested=nb, steps=steps, n_min=min(ns_), n_max=max(ns_), m_min=min(ms_),
+               m_max=max(ms_), n_sum=int(sum(ns_)), sequential_steps_per_s=nf * steps / t_seq,
+               batched_steps_per_s=nf * steps / t_bat, merged=all(merged), build_s=t_build,
+               timing="host wall clock around the steps (each step synchronises its stream)",
+               note=("stopped at the device-memory reserve" if nf < nb else "all requested filters") +
+                    "; merged phase-1 and phase-2 H-apply launches, the rest of each step on its own stream; "
+                    "no CUDA graph (steps take host decisions on device results)")
+    for o in objs:
+        fkf.fkf_filter_destroy(o["f"])
+        fkf.fkf_hmatrix_destroy(o["hm"])
+        fkf.fkf_destroy(o["ctx"])
     return out
 
 
@@ -532,8 +544,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
                     help="medium = 256x256, m=400: for profiler captures only")
-    ap.add_argument("--batch", type=int, default=0,
-                    help="also time a batch of this many uneven FP32 filters (sequential vs merged batched steps)")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="also time a batch of this many uneven FP32 filters (sequential vs merged batched steps); "
+                         "0 skips it")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload == "medium":
@@ -565,7 +578,10 @@ def main():
 
     res, wl = run_gpu(args, rank, world)
     if args.batch > 0 and rank == 0:
-        res["batch"] = batch_bench(args.batch, steps=5, warmup=3)
+        try:
+            res["batch"] = batch_bench(args.batch, steps=5, warmup=3)
+        except Exception as ex:  # the batch is an extra field: its failure must not lose the line
+            res["batch"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
         log(f"[bench] batch of {args.batch} uneven FP32 filters: {res['batch']}")
     if world > 1:
         import torch.distributed as dist

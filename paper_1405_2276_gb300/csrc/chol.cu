@@ -390,3 +390,70 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
   }
   return FKF_OK;
 }
+
+namespace {
+// Triangular solves of one diagonal block for every right-hand side (thread
+// per RHS row q of B): forward L_kk y = b (in place), or backward L_kk^T x = y.
+__global__ void k_trsv_block_fwd(int nrhs, int b, const double* __restrict__ Lkk, int64_t ldl, double* B,
+                                 int64_t ldb) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nrhs) return;
+  double* Bq = B + (int64_t)q * ldb;
+  for (int i = 0; i < b; i++) {
+    double y0 = Bq[i], y1 = 0;
+    int j = 0;
+    for (; j + 1 < i; j += 2) {
+      y0 -= Lkk[(int64_t)i * ldl + j] * Bq[j];
+      y1 -= Lkk[(int64_t)i * ldl + j + 1] * Bq[j + 1];
+    }
+    for (; j < i; j++) y0 -= Lkk[(int64_t)i * ldl + j] * Bq[j];
+    Bq[i] = (y0 + y1) / Lkk[(int64_t)i * ldl + i];
+  }
+}
+
+__global__ void k_trsv_block_bwd(int nrhs, int b, const double* __restrict__ Lkk, int64_t ldl, double* B,
+                                 int64_t ldb) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nrhs) return;
+  double* Bq = B + (int64_t)q * ldb;
+  for (int i = b - 1; i >= 0; i--) {
+    double x0 = Bq[i], x1 = 0;
+    int j = i + 1;
+    for (; j + 1 < b; j += 2) {
+      x0 -= Lkk[(int64_t)j * ldl + i] * Bq[j];
+      x1 -= Lkk[(int64_t)(j + 1) * ldl + i] * Bq[j + 1];
+    }
+    for (; j < b; j++) x0 -= Lkk[(int64_t)j * ldl + i] * Bq[j];
+    Bq[i] = (x0 + x1) / Lkk[(int64_t)i * ldl + i];
+  }
+}
+}  // namespace
+
+// Solve L L^T x = b for nrhs right-hand sides, the rows of B (nrhs x n,
+// leading dimension ldb), with the lower factor L of chol_blocked_f64 (n x n
+// row-major, ld ldl; only its lower triangle is read).  Row form: the
+// forward substitution is Y = B L^-T, the backward one X = Y L^-1, both by
+// blocks of kB columns: a triangular solve of the diagonal block per
+// right-hand side, then one GEMM update of the remaining columns.
+fkf_status chol_solve_rows_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* B, int nrhs, int64_t ldb) {
+  if (n <= 0 || nrhs <= 0) return FKF_OK;
+  cudaStream_t st = ctx->stream;
+  const unsigned g = (unsigned)cdiv(nrhs, 128);
+  for (int k0 = 0; k0 < n; k0 += kB) {
+    const int b = std::min(kB, n - k0);
+    k_trsv_block_fwd<<<g, 128, 0, st>>>(nrhs, b, L + (int64_t)k0 * ldl + k0, ldl, B + k0, ldb);
+    FKF_LAUNCHED(ctx);
+    const int rest = n - k0 - b;
+    if (rest > 0)
+      FKF_TRY(gemm_f64(ctx, false, true, nrhs, rest, b, -1.0, B + k0, ldb, L + (int64_t)(k0 + b) * ldl + k0, ldl, 1.0,
+                       B + k0 + b, ldb));
+  }
+  for (int k0 = ((n - 1) / kB) * kB; k0 >= 0; k0 -= kB) {
+    const int b = std::min(kB, n - k0);
+    k_trsv_block_bwd<<<g, 128, 0, st>>>(nrhs, b, L + (int64_t)k0 * ldl + k0, ldl, B + k0, ldb);
+    FKF_LAUNCHED(ctx);
+    if (k0 > 0)
+      FKF_TRY(gemm_f64(ctx, false, false, nrhs, k0, b, -1.0, B + k0, ldb, L + (int64_t)k0 * ldl, ldl, 1.0, B, ldb));
+  }
+  return FKF_OK;
+}

@@ -47,6 +47,10 @@ fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, in
 // before reading A22 (the factor itself is complete on return).
 fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws,
                             cudaEvent_t schur_done = nullptr);
+// Solve L L^T x = b for the nrhs rows of B (nrhs x n, ld ldb), in place, with
+// the lower factor of chol_blocked_f64 (ld ldl); the library's own blocked
+// triangular solves.
+fkf_status chol_solve_rows_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* B, int nrhs, int64_t ldb);
 // Solve S x = b (nrhs contiguous vectors of length n) with the factor of
 // chol_blocked_f64 (ld ldl).
 fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs);
@@ -66,8 +70,9 @@ fkf_status eigh_f64(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
 // eigenvalues ascending in w, eigenvector i in row i of A (row-major view).
 fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
                         int* meig);
-// Cholesky factorisation of an SPD n x n matrix in place; returns
-// FKF_ENOTSPD when a pivot is not positive (synchronises to read the status).
+// Cholesky factorisation of an SPD n x n matrix in place (the library's
+// blocked factorisation; lower factor, row-major); FKF_ENOTSPD when a pivot is
+// not positive.
 fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws);
 // Solve A x = b for nrhs right-hand sides stored as nrhs contiguous vectors
 // of length n, with A factored by chol_f64.

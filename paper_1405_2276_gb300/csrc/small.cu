@@ -1,7 +1,8 @@
 // Small dense FP64 factorisations for the m x m and r x r data-space algebra:
-// the symmetric eigendecompositions (the library's own solver, eigh.cu) and
-// the Cholesky factorisation and solves of small SPD systems (cuSOLVER's
-// potrf/potrs on the context stream).
+// the symmetric eigendecompositions (the library's own solver, eigh.cu), the
+// Cholesky factorisation and solves of small SPD systems (the library's own,
+// chol.cu), and the one-right-hand-side solve of the step's innovation system
+// (cuSOLVER's potrs on the context stream).
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -46,37 +47,12 @@ fkf_status eigh_top_f64(fkf_ctx* ctx, int n, int k, double* A, double* w_dev, st
   return FKF_OK;
 }
 
-fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws) {
-  if (n == 0) return FKF_OK;
-  cusolverDnHandle_t h;
-  FKF_TRY(solver(ctx, &h));
-  int lwork = 0;
-  if (cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_LOWER, n, A, n, &lwork) != CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "potrf_bufferSize failed");
-  const size_t need = (size_t)lwork * sizeof(double) + 256;
-  if (ws.bytes < need) FKF_TRY(dev_alloc(ctx, ws, need));
-  int* info = reinterpret_cast<int*>(ws.as<char>() + (size_t)lwork * sizeof(double));
-  if (cusolverDnDpotrf(h, CUBLAS_FILL_MODE_LOWER, n, A, n, ws.as<double>(), lwork, info) != CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "potrf failed");
-  ctx->lib_calls++;
-  int hinfo = 0;
-  FKF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (hinfo > 0) return set_err(ctx, FKF_ENOTSPD, "matrix not positive definite (leading minor %d of %d)", hinfo, n);
-  if (hinfo < 0) return set_err(ctx, FKF_ECUDA, "potrf argument %d invalid", -hinfo);
-  return FKF_OK;
-}
+// Cholesky factorisation and solves of small SPD systems: the library's own
+// blocked factorisation (chol.cu) and blocked triangular solves.
+fkf_status chol_f64(fkf_ctx* ctx, int n, double* A, DevBuf& ws) { return chol_blocked_f64(ctx, n, n, A, n, ws); }
 
 fkf_status chol_solve_f64(fkf_ctx* ctx, int n, const double* Afact, double* b, int nrhs) {
-  if (n == 0 || nrhs == 0) return FKF_OK;
-  cusolverDnHandle_t h;
-  FKF_TRY(solver(ctx, &h));
-  if (ctx->solver_info.bytes < 256) FKF_TRY(dev_alloc(ctx, ctx->solver_info, 256));
-  if (cusolverDnDpotrs(h, CUBLAS_FILL_MODE_LOWER, n, nrhs, Afact, n, b, n, ctx->solver_info.as<int>()) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return set_err(ctx, FKF_ECUDA, "potrs failed");
-  ctx->lib_calls++;
-  return FKF_OK;
+  return chol_solve_rows_f64(ctx, n, Afact, n, b, nrhs, n);
 }
 
 fkf_status chol_solve_rowlower_f64(fkf_ctx* ctx, int n, const double* L, int64_t ldl, double* b, int nrhs) {

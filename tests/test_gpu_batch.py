@@ -1,6 +1,8 @@
 """Batched steps of independent filters with uneven sizes (fkf_filter_step_batched)
-against the same filters stepped one at a time, and one of them against the
-dense oracle."""
+against the same filters stepped one at a time (bitwise), and every member of
+the batch against the dense oracle: the FP64 members against O1 run on their
+own compressed covariance Gamma_H (exported densely) at 1e-10, the FP32
+members against O1 with the exact Matern covariance at 2e-4."""
 
 import numpy as np
 import pytest
@@ -69,14 +71,22 @@ def test_batched_equals_sequential(fkf):
         sa, sb = fkf.fkf_filter_get(oa["f"], n), fkf.fkf_filter_get(ob["f"], n)
         np.testing.assert_array_equal(sa["s"], sb["s"])
         np.testing.assert_array_equal(sa["D"], sb["D"])
-    # first filter (FP64) against the dense oracle
-    o = a[0]
-    grid, ns, nr, nu, ell, prec = o["spec"]
-    G = covariance.dense_gamma(o["wl"]["points"], nu, ell, 1.0)
-    Hd = synth.csr_to_dense(o["wl"]["H"])
-    ref = kalman.kf_dense(G, [(o["wl"]["y"][k], Hd, 1e-4) for k in range(steps)], keep_cov=False)
-    st = fkf.fkf_filter_get(o["f"], o["wl"]["points"].shape[0])
-    assert rel_err(st["s"], ref[-1]["s"]) < 1e-6
+    # every member against the dense oracle
+    import torch
+
+    for o in a:
+        grid, ns, nr, nu, ell, prec = o["spec"]
+        pts = o["wl"]["points"]
+        n = pts.shape[0]
+        G = fkf.fkf_hmatrix_densify(o["hm"], n) if prec == 0 else covariance.dense_gamma(pts, nu, ell, 1.0)
+        Hd = synth.csr_to_dense(o["wl"]["H"])
+        ref = kalman.kf_dense(G, [(o["wl"]["y"][k], Hd, 1e-4) for k in range(steps)], keep_cov=False)
+        st = fkf.fkf_filter_get(o["f"], n)
+        v = torch.empty(n, dtype=torch.float64, device="cuda")
+        fkf.fkf_variance(o["f"], v)
+        bound = 1e-10 if prec == 0 else 2e-4
+        es, ev = rel_err(st["s"], ref[-1]["s"]), rel_err(v.cpu().numpy(), ref[-1]["var"])
+        assert es < bound and ev < bound, (o["spec"], es, ev)
     _free(fkf, a)
     _free(fkf, b)
 

@@ -6,7 +6,7 @@ The measurements are y_k = H s(x_k) + v_k with s(x) = ((x + a)/a)^a (Eq.
 nonlinear), x_k a random walk of the transformed field.  The Jacobian
 H_k = H diag(s'(x_pred)) changes every step, so every step runs the general
 path (GEP, orthonormalisation, merge, rotation) and the rank grows until the
-truncation bounds it.  FP64 path: relative 1e-10 with no truncation (trunc_tol = 0), relative 1e-9: a Jacobian that changes by a
+truncation bounds it.  FP64 path: relative 1e-10 with no truncation (the 1e-12 rounding floor of trunc_tol), relative 1e-9: a Jacobian that changes by a
 rescaling of H's columns brings new directions whose Gamma^-1-norm outside
 span(W) is small, and the orthonormalisation's rank-revealing threshold
 (1e-10, which keeps X^T W = I to working precision) drops information of that
@@ -75,7 +75,7 @@ def _run(fkf, pts, H, ys, kern, noise, a, trunc_tol, r_max, precision=0):
 def test_ekf_matches_dense_extended_filter(fkf, a):
     pts, H, Hd, ys, G, kern, noise = _problem(a)
     ref = kalman.ekf_dense(G, [(y, Hd, noise) for y in ys], a)
-    got, orth = _run(fkf, pts, H, ys, kern, noise, a, 0.0, H.nrows * len(ys))
+    got, orth = _run(fkf, pts, H, ys, kern, noise, a, 1e-12, H.nrows * len(ys))
     worst = 0.0
     for k, (g, b) in enumerate(zip(got, ref)):
         Sig = g["alpha"] * G - (g["W"] * g["D"]) @ g["W"].T
@@ -86,6 +86,7 @@ def test_ekf_matches_dense_extended_filter(fkf, a):
         assert e < 1e-9, (k, parts)
         assert g["path"] == 0  # a new Jacobian every step: the merge path
     assert got[-1]["r"] > H.nrows  # the rank grew past one step's measurements
+    print(f"EKF a={a:g}: orthonormality {orth:.1e}")
     assert orth < 1e-9
     print(f"EKF a={a:g}: worst rel err vs O1e {worst:.2e}, ranks {[g['r'] for g in got]}")
 
