@@ -86,8 +86,10 @@ def test_ekf_matches_dense_extended_filter(fkf, a):
         assert e < 1e-9, (k, parts)
         assert g["path"] == 0  # a new Jacobian every step: the merge path
     assert got[-1]["r"] > H.nrows  # the rank grew past one step's measurements
+    # directions accepted just above the orthonormalisation's threshold tau_o = 1e-10 carry a
+    # Gamma^-1-orthonormality error of order eps / tau_o (observed 2e-7 to 3e-7)
     print(f"EKF a={a:g}: orthonormality {orth:.1e}")
-    assert orth < 1e-9
+    assert orth < 1e-5
     print(f"EKF a={a:g}: worst rel err vs O1e {worst:.2e}, ranks {[g['r'] for g in got]}")
 
 
