@@ -423,6 +423,38 @@ def run_gpu(args, rank, world):
     return res, wl
 
 
+def eigh_bench(sizes, profile=False):
+    """The library's FP64 symmetric eigensolver (fkf_eigh, all eigenvectors) on seeded random
+    symmetric matrices: device ms per call (CUDA events, second call; the first warms up).
+    profile: the timed calls are bracketed by cudaProfilerStart/Stop."""
+    import torch
+
+    from paper_1405_2276_gb300 import fkf
+
+    ctx = fkf.fkf_create(0)
+    out = {}
+    for n in sizes:
+        rng = np.random.default_rng(n)
+        B = rng.standard_normal((n, n))
+        A = torch.from_numpy(B + B.T).cuda()
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        fkf.fkf_eigh(ctx, A.clone(), w)
+        X = A.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if profile:
+            torch.cuda.profiler.start()
+        e0.record()
+        fkf.fkf_eigh(ctx, X, w)
+        e1.record()
+        e1.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
+        out[str(n)] = e0.elapsed_time(e1)
+    fkf.fkf_destroy(ctx)
+    return out
+
+
 def batch_spec(nb, seed):
     """Uneven filters of the batch workload: N log-uniform in [16384, 262144] on square grids, m
     log-uniform in [64, 1024] as n_src x n_rec rays, nu in {1/2, 3/2}, ell uniform in [0.02, 0.3]."""
@@ -549,6 +581,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
                     help="medium = 256x256, m=400: for profiler captures only")
+    ap.add_argument("--eigh", type=int, nargs="*", default=None,
+                    help="only time the FP64 eigensolver on these sizes (profiler range around the timed calls)")
     ap.add_argument("--batch", type=int, default=64,
                     help="also time a batch of this many uneven FP32 filters (sequential vs merged batched steps); "
                          "0 skips it")
@@ -566,6 +600,13 @@ def main():
 
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
 
+    if args.eigh:
+        from paper_1405_2276_gb300 import build
+
+        build()
+        print(json.dumps({"eigh_ms": eigh_bench(args.eigh, profile=True)}), flush=True)
+        return
+
     if args.impl == "reference":
         if rank != 0:
             return
@@ -582,6 +623,9 @@ def main():
         return
 
     res, wl = run_gpu(args, rank, world)
+    if rank == 0:
+        res["eigh"] = eigh_bench([1024, 3072])
+        log(f"[bench] FP64 eigensolver (ms per call, all eigenvectors): {res['eigh']}")
     if args.batch > 0 and rank == 0:
         try:
             res["batch"] = batch_bench(args.batch, steps=5, warmup=3)
@@ -691,6 +735,7 @@ def main():
         "gpu_launches": fp32["launches"], "library_calls": fp32["lib_calls"],
         "clocks": fp32["clocks"],
         "batch": res.get("batch"),
+        "eigh_fp64_ms": res.get("eigh"),
         "autotune": res.get("autotune"),
     }
     print(json.dumps(line), flush=True)

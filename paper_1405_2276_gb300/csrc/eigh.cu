@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kNB = 32;                  // panel width of the reduction and the back-transformation
 constexpr int kLeaf = 32;                // largest leaf of the divide and conquer (one warp)
-constexpr int kBT = 64;                  // reflectors per block of the back-transformation
+constexpr int kBT = 128;                 // reflectors per block of the back-transformation
 constexpr size_t kPrepSmem = 216 * 1024;  // shared memory of the merge preparation (s <= 3949)                 // reflectors per block of the back-transformation
 constexpr int kTrdThreads = 512;
 constexpr int kTrdSmemV = 6144;            // reflector entries staged in shared memory (48 KB)
