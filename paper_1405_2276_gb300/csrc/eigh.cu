@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(32) k_dc_leaf(const int* __restrict__ loff, co
   __shared__ double dd[kLeaf], ee[kLeaf], cs[2][kLeaf];
   __shared__ int lo_sh, perm[kLeaf];
   const int off = loff[blockIdx.x], s = lsize[blockIdx.x], lane = threadIdx.x;
-  for (int q = 0; q < s; q++) Z[lane][q] = (lane == q) ? 1.0 : 0.0;
+  if (lane < s)
+    for (int q = 0; q < s; q++) Z[lane][q] = (lane == q) ? 1.0 : 0.0;
   if (lane < s) {
     dd[lane] = d[off + lane];
     ee[lane] = lane < s - 1 ? e[off + lane] : 0.0;
@@ -865,41 +866,35 @@ __global__ void k_bt_vp(int64_t n, int64_t j0, int nbp, const double* __restrict
 
 // Triangular factor of the compact WY form H_j0 ... H_j0+nbp-1 = I - V T V^T:
 // T[c][c] = tau_c, T[0:c, c] = -tau_c T[0:c, 0:c] (V^T V)[0:c, c].  Row r of T
-// depends only on row r and V^T V, so thread r forms its row; both triangles
-// are kept packed in shared memory (G[q][c] for q < c at c(c-1)/2 + q, T[r][c]
-// for r <= c at c(c+1)/2 + r).
-__global__ void k_bt_tfactor(int nbp, const double* __restrict__ VtV, const double* __restrict__ tau,
-                             double* __restrict__ T) {
+// depends only on row r and V^T V: a warp per row, its lanes splitting each
+// sum (V^T V's strictly upper triangle packed in shared memory, G[q][c] at
+// c(c-1)/2 + q; the warp's row of T in shared memory).
+constexpr int kTfWarps = 16;
+__global__ void __launch_bounds__(32 * kTfWarps) k_bt_tfactor(int nbp, const double* __restrict__ VtV,
+                                                             const double* __restrict__ tau, double* __restrict__ T) {
   extern __shared__ double smt[];
-  double* Gu = smt;                          // nbp (nbp - 1) / 2
-  double* Tp = smt + nbp * (nbp - 1) / 2;    // nbp (nbp + 1) / 2
-  const int r = threadIdx.x;
-  for (int e = r; e < nbp * nbp; e += blockDim.x) {
+  double* Gu = smt;                               // nbp (nbp - 1) / 2
+  double* rows = smt + nbp * (nbp - 1) / 2;       // kTfWarps x nbp
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int e = t; e < nbp * nbp; e += blockDim.x) {
     const int q = e / nbp, c = e % nbp;
     if (q < c) Gu[c * (c - 1) / 2 + q] = VtV[e];
   }
   __syncthreads();
-  if (r < nbp) {
-    Tp[r * (r + 1) / 2 + r] = tau[r];
-    for (int c = r + 1; c < nbp; c++) {
-      const double* gc = Gu + c * (c - 1) / 2;
-      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // independent chains (FP64 latency)
-      int q = r;
-      for (; q + 3 < c; q += 4) {
-        a0 += Tp[q * (q + 1) / 2 + r] * gc[q];
-        a1 += Tp[(q + 1) * (q + 2) / 2 + r] * gc[q + 1];
-        a2 += Tp[(q + 2) * (q + 3) / 2 + r] * gc[q + 2];
-        a3 += Tp[(q + 3) * (q + 4) / 2 + r] * gc[q + 3];
-      }
-      for (; q < c; q++) a0 += Tp[q * (q + 1) / 2 + r] * gc[q];
-      Tp[c * (c + 1) / 2 + r] = -tau[c] * ((a0 + a1) + (a2 + a3));
-    }
+  const int r = blockIdx.x * kTfWarps + w;
+  if (r >= nbp) return;
+  double* Tr = rows + w * nbp;
+  for (int c = lane; c < nbp; c += 32) Tr[c] = c == r ? tau[r] : 0.0;
+  __syncwarp();
+  for (int c = r + 1; c < nbp; c++) {
+    const double* gc = Gu + c * (c - 1) / 2;
+    double acc = 0;
+    for (int q = r + lane; q < c; q += 32) acc += Tr[q] * gc[q];
+    acc = warp_sum(acc);
+    if (lane == 0) Tr[c] = -tau[c] * acc;
+    __syncwarp();
   }
-  __syncthreads();
-  for (int e = r; e < nbp * nbp; e += blockDim.x) {
-    const int rr = e / nbp, c = e % nbp;
-    T[e] = rr <= c ? Tp[c * (c + 1) / 2 + rr] : 0.0;
-  }
+  for (int c = lane; c < nbp; c += 32) T[(int64_t)r * nbp + c] = Tr[c];
 }
 
 __global__ void k_copy_cols(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
@@ -1047,7 +1042,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     FKF_CUDA(ctx, cudaMemsetAsync(VW, 0, w_VW * 8, st));
     FKF_CUDA(ctx, cudaMemsetAsync(WV, 0, w_WV * 8, st));
     FKF_CUDA(ctx, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(gmax, (N - j0) / 8));
+    const int G = (int)std::max<int64_t>(4, std::min<int64_t>(gmax, (N - j0) / 8));
     TrdArgs ta{A, N, j0, nbp, VW, WV, d, e, tau, col, vg, pg, part, bar, err};
     void* args[] = {&ta};
     const size_t vsm = (size_t)std::min<int64_t>(N, kTrdSmemV) * sizeof(double);
@@ -1116,7 +1111,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     FKF_LAUNCHED(ctx);
     const int64_t nref = N - 1;  // reflectors 0 .. n-2
     FKF_CUDA(ctx, cudaFuncSetAttribute(k_bt_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kBT * kBT * (int)sizeof(double) + 64));
+                                       (kBT * (kBT - 1) / 2 + kTfWarps * kBT) * (int)sizeof(double)));
     for (int64_t j0 = nref > 0 ? ((nref - 1) / kBT) * kBT : -1; j0 >= 0; j0 -= kBT) {
       const int nbp = (int)std::min<int64_t>(kBT, nref - j0);
       const int64_t rows = N - j0 - 1;
@@ -1124,7 +1119,8 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
       k_bt_vp<<<grid_for(rows * nbp), 256, 0, st>>>(N, j0, nbp, A, Vp);
       FKF_LAUNCHED(ctx);
       FKF_TRY(gram_f64(ctx, nbp, nbp, rows, Vp, nbp, Vp, nbp, VtV, nbp, gws));
-      k_bt_tfactor<<<1, kBT, (size_t)nbp * nbp * sizeof(double) + 64, st>>>(nbp, VtV, tau + j0, Tf);
+      k_bt_tfactor<<<(unsigned)cdiv(nbp, kTfWarps), 32 * kTfWarps,
+                     (size_t)(nbp * (nbp - 1) / 2 + kTfWarps * nbp) * sizeof(double), st>>>(nbp, VtV, tau + j0, Tf);
       FKF_LAUNCHED(ctx);
       double* Xs = X + (j0 + 1) * k;
       // X[j0+1:] -= V (T (V^T X[j0+1:]))
