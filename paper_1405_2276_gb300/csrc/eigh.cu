@@ -120,22 +120,26 @@ struct TrdArgs {
 
 // One panel of the Householder reduction (lower form), by every SM (the
 // column's symmetric product is FP64-FMA bound).  Column j of the panel
-// (c = j - j0):
+// (c = j - j0), with x = a[1:] the part below the diagonal:
 //   a = A[j:, j] - V[j:, :c] W[j, :c]^T - W[j:, :c] V[j, :c]^T   (current column)
-//   d_j = a_0; reflector H = I - tau v v^T with H a[1:] = beta e_1, v_0 = 1
+//   d_j = a_0; reflector H = I - tau v v^T with H x = beta e_1,
+//   v = (x - beta e_1) / (alpha - beta), alpha = x_0
 //   p = A[j+1:, j+1:] v - V (W^T v) - W (V^T v)                    (current matrix times v)
 //   w = tau p - tau^2/2 (p^T v) v;  V[:, c] = v, W[:, c] = w
-// The reflector (below its leading 1) is stored in A[j+2:, j].  Three grid
-// barriers per column: the correction w of column c is formed at the start of
-// column c + 1 by the CTA that owns each row there (every CTA forms the entry
-// w_{j+1} that all of them need), and after the loop for the last column.
-// Partial sums go to one region per phase, so a region is rewritten only after
-// every CTA has passed a later barrier.
+// Two grid barriers per column: the product starts from x as soon as the
+// column is complete, A v = (A x - beta A e_1) / (alpha - beta), and W^T v,
+// V^T v follow from W^T x, V^T x in the same way, so the reflector's scalars
+// (from the column's norm) are formed after the same barrier.  The correction
+// w of column c is formed at the start of column c + 1 by the CTA that owns
+// each row there (every CTA forms the entry w_{j+1} that all of them need), and
+// after the loop for the last column.  Partial sums go to one region per phase,
+// so a region is rewritten only after every CTA has passed a later barrier.
+// The reflector (below its leading 1) is stored in A[j+2:, j].
 __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
   __shared__ double sh[33];
   __shared__ double wv[2 * kNB];
   __shared__ double bc[4];
-  extern __shared__ double vs[];  // v[j+1..n) when it fits
+  extern __shared__ double vs[];  // x[0..n-j-1) when it fits
   const int64_t n = a.n;
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
@@ -145,11 +149,12 @@ __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
   double* partB = a.part + 2 * G;  // G x 2 kNB
   unsigned gen = 0;
   double tau_prev = 0, k2_prev = 0;  // column c - 1: w = tau p - k2 v
-  int64_t s0 = 0, s1 = 0;            // rows [j+1, n) of this CTA (phases B and C)
+  int64_t s0 = 0, s1 = 0;            // rows [j+1, n) of this CTA (the product phase)
   for (int c = 0; c < a.nbp; c++) {
     const int64_t j = a.j0 + c;
     if (j >= n) break;
-    // ---- phase A: w of column c - 1 on this CTA's rows of [j, n), then the current column
+    // ---- phase A: w of column c - 1 and the current column on this CTA's rows
+    // of [j, n); partial sums of |x[1:]|^2, W^T x and V^T x
     {
       const int64_t rows = n - j, R = (rows + G - 1) / G;
       const int64_t r0 = j + b * R, r1 = min(n, r0 + R);
@@ -167,49 +172,76 @@ __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
       const double vjq = lane < c ? (lane == c - 1 ? wjc : Vj[kNB + lane]) : 0.0;  // W[j][q]
       const double vjv = lane < c ? Vj[lane] : 0.0;                                // V[j][q]
       double ss = 0;
+      double px = 0;  // lane q: W[:, q]^T x (q < c) or V[:, q - c]^T x (c <= q < 2c), this warp's rows
+      double px2 = 0;  // the same for lane q + 32 (2c may reach 64)
       for (int64_t i = r0 + warp; i < r1; i += nw) {
         const double* Vi = a.VW + i * L;
         double corr = lane < c ? Vi[lane] * vjq + Vi[kNB + lane] * vjv : 0.0;
         corr = warp_sum(corr);
+        const double v = a.A[j * n + i] - corr;  // A[i][j] = A[j][i]
         if (lane == 0) {
-          const double v = a.A[j * n + i] - corr;  // A[i][j] = A[j][i]
           a.col[i] = v;
           if (i >= j + 2) ss += v * v;
+        }
+        if (i >= j + 1) {
+          // W[i][q] for q < c sits at Vi[kNB + q], V[i][q] at Vi[q]
+          if (lane < 2 * c) px += (lane < c ? Vi[kNB + lane] : Vi[lane - c]) * v;
+          if (lane + 32 < 2 * c) px2 += (lane + 32 < c ? Vi[kNB + lane + 32] : Vi[lane + 32 - c]) * v;
         }
       }
       ss = block_sum(ss, sh);
       if (t == 0) partA[b] = ss;
+      // combine the warps' W^T x / V^T x partials in shared memory
+      __shared__ double pxw[kTrdThreads / 32][2 * kNB];
+      if (lane < 2 * c) pxw[warp][lane] = px;
+      if (lane + 32 < 2 * c) pxw[warp][lane + 32] = px2;
+      __syncthreads();
+      if (t < 2 * c) {
+        double acc = 0;
+        for (int w2 = 0; w2 < nw; w2++) acc += pxw[w2][t];
+        partB[(int64_t)b * L + t] = acc;
+      }
     }
     grid_barrier(a.bar, a.bar + 1, gen, a.err);
-    // ---- phase B: the reflector (every CTA computes it from the same partials)
-    {
-      const double s2 = grid_partials_sum(partA, G, sh);
-      if (t == 0) {
-        double beta = 0, tau = 0, scale = 0;
-        if (j + 1 < n) {
-          const double alpha = a.col[j + 1];
-          if (s2 == 0.0) {
-            beta = alpha;
-          } else {
-            beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
-          }
-        }
-        bc[0] = tau;
-        bc[1] = scale;
-        if (b == 0) {
-          a.d[j] = a.col[j];
-          if (j + 1 < n) {
-            a.e[j] = beta;
-            a.tau[j] = tau;
-          }
+    // ---- phase B: the reflector's scalars (every CTA, same partials, same order)
+    const double s2 = grid_partials_sum(partA, G, sh);
+    if (t == 0) {
+      double beta = 0, tau = 0, scale = 0;
+      if (j + 1 < n) {
+        const double alpha = a.col[j + 1];
+        if (s2 == 0.0) {
+          beta = alpha;
+        } else {
+          beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+          tau = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
         }
       }
-      __syncthreads();
+      bc[0] = tau;
+      bc[1] = scale;
+      bc[3] = beta;
+      if (b == 0) {
+        a.d[j] = a.col[j];
+        if (j + 1 < n) {
+          a.e[j] = beta;
+          a.tau[j] = tau;
+        }
+      }
     }
+    __syncthreads();
     if (j + 1 >= n) break;  // the last diagonal entry has no reflector (uniform over the grid)
-    const double tau = bc[0], scale = bc[1];
+    const double tau = bc[0], scale = bc[1], beta = bc[3];
+    // W^T v = scale (W^T x - beta W[j+1, :]), V^T v likewise
+    const double* Vn = a.VW + (j + 1) * L;
+    for (int qq = warp; qq < 2 * c; qq += nw) {
+      double acc = 0;
+      for (int q = lane; q < G; q += 32) acc += partB[(int64_t)q * L + qq];
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double e1 = qq < c ? Vn[kNB + qq] : Vn[qq - c];
+        wv[qq] = scale * (acc - beta * e1);
+      }
+    }
     const int64_t rows1 = n - j - 1, R1 = (rows1 + G - 1) / G;
     s0 = j + 1 + b * R1;
     s1 = min(n, s0 + R1);
@@ -220,47 +252,34 @@ __global__ void __launch_bounds__(kTrdThreads) k_trd_panel(TrdArgs a) {
       a.WV[i * L + kNB + c] = v;
       if (i >= j + 2) a.A[i * n + j] = v;
     }
-    __syncthreads();
-    // partial W^T v (entries 0..c-1) and V^T v (c..2c-1) over this CTA's rows
-    for (int qq = warp; qq < 2 * c; qq += nw) {
-      const int colofs = qq < c ? kNB + qq : qq - c;
-      double acc = 0;
-      for (int64_t i = s0 + lane; i < s1; i += 32) acc += a.VW[i * L + colofs] * a.vg[i];
-      acc = warp_sum(acc);
-      if (lane == 0) partB[(int64_t)b * L + qq] = acc;
-    }
-    grid_barrier(a.bar, a.bar + 1, gen, a.err);
-    // ---- phase C: p = A v - V (W^T v) - W (V^T v), a warp per row of this CTA's chunk
-    for (int qq = warp; qq < 2 * c; qq += nw) {
-      double acc = 0;
-      for (int q = lane; q < G; q += 32) acc += partB[(int64_t)q * L + qq];
-      acc = warp_sum(acc);
-      if (lane == 0) wv[qq] = acc;
-    }
+    // x = col[j+1..n) staged in shared memory when it fits
     const int64_t nv = n - j - 1;
     const bool vsm = nv <= kTrdSmemV;
     if (vsm)
-      for (int64_t k = t; k < nv; k += blockDim.x) vs[k] = a.vg[j + 1 + k];
+      for (int64_t k = t; k < nv; k += blockDim.x) vs[k] = a.col[j + 1 + k];
     __syncthreads();
+    // ---- phase C: p = scale (A x - beta A e_1) - V (W^T v) - W (V^T v), a warp per row
     double pv = 0;
     for (int64_t i = s0 + warp; i < s1; i += nw) {
       const double* Ai = a.A + i * n + j + 1;
-      const double* vv = vsm ? vs : a.vg + j + 1;
+      const double* xv = vsm ? vs : a.col + j + 1;
       double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
       int64_t k = lane;
       for (; k + 96 < nv; k += 128) {
-        acc0 += Ai[k] * vv[k];
-        acc1 += Ai[k + 32] * vv[k + 32];
-        acc2 += Ai[k + 64] * vv[k + 64];
-        acc3 += Ai[k + 96] * vv[k + 96];
+        acc0 += Ai[k] * xv[k];
+        acc1 += Ai[k + 32] * xv[k + 32];
+        acc2 += Ai[k + 64] * xv[k + 64];
+        acc3 += Ai[k + 96] * xv[k + 96];
       }
-      for (; k < nv; k += 32) acc0 += Ai[k] * vv[k];
+      for (; k < nv; k += 32) acc0 += Ai[k] * xv[k];
       const double* Vi = a.VW + i * L;
       const double corr = lane < c ? Vi[lane] * wv[lane] + Vi[kNB + lane] * wv[c + lane] : 0.0;
-      const double acc = warp_sum((acc0 + acc1) + (acc2 + acc3) - corr);
+      const double ax = warp_sum((acc0 + acc1) + (acc2 + acc3));
+      const double cs = warp_sum(corr);
       if (lane == 0) {
-        a.pg[i] = acc;
-        pv += acc * a.vg[i];
+        const double pi = scale * (ax - beta * Ai[0]) - cs;
+        a.pg[i] = pi;
+        pv += pi * ((i == j + 1) ? 1.0 : a.col[i] * scale);
       }
     }
     pv = block_sum(pv, sh);
