@@ -157,11 +157,14 @@ struct P2Leaf {
 };
 
 // Tensor-core phase-2 tile: 128 consecutive rows (whole leaves packed) and
-// its merged segment list; a segment covers tile rows [row_lo, row_hi) and
-// a_off addresses the A row of tile row row_lo.
+// its merged segment list.
 // Tensor-core phase-2 segment: rows [row_lo, row_hi) of the tile times the
-// segment's A block (a_off, lda) and its B operand: K rows starting at the
-// split-vector chunk b_row (of X if near, else of the slot workspace).
+// segment's A block (a_off addresses the A row of tile row row_lo, row
+// stride lda) and its B operand: K rows starting at the split-vector chunk
+// b_row (of X if near, else of the slot workspace).  A near segment may hold
+// a second row range [row_lo2, row_hi2) with its own A block (a_off2, lda2):
+// two leaves of a tile that share a near partner read its X chunks once, and
+// the rows of a leaf without that partner stay zero.
 struct TcSeg {
   int64_t a_off;
   int64_t b_row;
@@ -169,7 +172,9 @@ struct TcSeg {
   int32_t K;
   int32_t near;
   int32_t row_lo, row_hi;
-  int32_t pad;
+  int32_t lda2;
+  int64_t a_off2;
+  int32_t row_lo2, row_hi2;  // empty when equal
 };
 
 struct TcTile {
@@ -181,8 +186,10 @@ struct TcTile {
 };
 
 // One 128 x 16 chunk of a split operator stream: element (i, k) is
-// src[src_off + (i - row_lo) * si + k * sk] for row_lo <= i < row_hi and
-// k < kv, zero elsewhere (src = the far factors, or the near blocks if near).
+// src[src_off + (i - row_lo) * si + k * sk] for row_lo <= i < row_hi,
+// src[src_off2 + (i - row_lo2) * si2 + k * sk] for row_lo2 <= i < row_hi2,
+// and k < kv, zero elsewhere (src = the far factors, or the near blocks if
+// near).
 // For the scaled FP16 format, row i is scaled by the scale of natural slot
 // s_off + i (phase 1) or of point s_off + i (phase 2), and column k of a far
 // phase-2 chunk by the inverse scale of slot-workspace position k_off + k.
@@ -193,7 +200,9 @@ struct TcAChunk {
   int32_t si, sk;
   int32_t row_lo, row_hi;
   int32_t kv, near;
-  int32_t phase, pad;
+  int32_t phase, si2;
+  int64_t src_off2;
+  int32_t row_lo2, row_hi2;  // second row range (empty when equal)
 };
 
 // One 16-row chunk of the split X operand: rows row0 .. row0 + rows - 1 of X

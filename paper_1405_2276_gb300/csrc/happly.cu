@@ -468,8 +468,12 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
         l = e;
       }
       const int ng = (int)groups.size();
-      for (int64_t q0 = 0; q0 < K[c]; q0 += 128) {
-        const int nq = (int)std::min<int64_t>(128, K[c] - q0);
+      // slot tiles of at most 128 (the MMA's N), balanced: N is the tile's
+      // slot count rounded up to 16, so equal tiles waste the least
+      const int64_t ntq = cdiv(K[c], 128);
+      const int64_t tq = (cdiv(K[c], ntq) + 3) / 4 * 4;
+      for (int64_t q0 = 0; q0 < K[c]; q0 += tq) {
+        const int nq = (int)std::min<int64_t>(tq, K[c] - q0);
         const int64_t base = tparts;
         for (int g = 0; g < ng; g++) {
           P1Item it{};

@@ -23,6 +23,9 @@
 //   * the vectors (B): X is split per column pass into 16-row chunks per leaf
 //     (rows padded to a multiple of 16), and phase 1 writes its products
 //     straight into the split slot workspace (16-slot chunks per cluster).
+// Phase 1 swaps the roles inside the MMA: the two 128-column halves of an X
+// chunk are A and the operator chunk (slots) is B, with N = the item's slot
+// count rounded up to 16, so that the accumulator lanes are vector columns.
 //
 // One persistent CTA per SM, warp-specialised:
 //   warp 0     producer (one thread): two bulk copies per chunk into one of
@@ -79,8 +82,6 @@ constexpr int kM = 128;           // tile rows = TMEM lanes
 constexpr int kN = 256;           // tile columns = MMA N
 constexpr int kK = umma::kChunk;  // 16: K per chunk
 constexpr int kEpiWarps = 8;      // warps 2-9: two per TMEM lane quarter, one per column half
-constexpr int kEpiLd = 33;        // padded row of an epilogue staging tile (32 x 32 floats)
-constexpr int kEpiBytes = kEpiWarps * 32 * kEpiLd * 4;
 constexpr int kQ = 8;             // tile-index queue (producer -> MMA, epilogue)
 constexpr int kBarBytes = 384;
 constexpr int kTail = 512;        // barriers, TMEM address, flag, queue
@@ -112,14 +113,13 @@ struct Geo {
   static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : (F == 2 ? FKF_TC_STAGES_F16 : 4);  // pipeline stages
   static constexpr uint32_t kSBO = (kK / kPer) * 128;  // next 8-row group
   static constexpr uint32_t kIdesc = kFmt == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
-  static constexpr int kSmem = kS * kStage + kTail + kEpiBytes;  // phase 1 (its epilogue stages tiles)
-  // phase 2 and the GEMMs store rows straight from TMEM and take no staging
-  // tiles: the room left on the SM holds one FP64 tile CTA of concurrent work
+  // every epilogue stores straight from TMEM (no staging tiles): the room
+  // left on the SM holds one FP64 tile CTA of concurrent work
   static constexpr int kSmemRows = kS * kStage + kTail;
   // barrier indices
   static constexpr int FULL = 0, EMPTY = FULL + kS, AF = EMPTY + kS, AE = AF + 2, FIN = AE + 2, QF = FIN + 1,
                        QE = QF + kQ, NBAR = QE + kQ;
-  static_assert(kSmem <= 232448, "shared memory per CTA");
+  static_assert(kSmemRows <= 232448, "shared memory per CTA");
   static_assert(NBAR * 8 <= kBarBytes, "barrier area");
   // byte offset of element (row, k) in a K-major no-swizzle chunk of kK columns
   __device__ static __forceinline__ uint32_t off(int row, int k) {
@@ -135,7 +135,6 @@ struct Smem {
   int* fail;
   uint32_t polls;  // poll limit of the pipeline waits (kMaxPolls unless a caller lowered it)
   int64_t* q;  // [kQ] tile indices (-1: no more tiles)
-  float* epi;  // kEpiWarps staging tiles
 
   // stage s: the A chunks of its kCPS chunks (consecutive), then their B chunks
   __device__ __forceinline__ uint8_t* a(int s) const { return base + s * Geo<F>::kStage; }
@@ -155,7 +154,6 @@ __device__ __forceinline__ Smem<F> smem_layout(uint8_t* base) {
   s.tmem_slot = reinterpret_cast<uint32_t*>(tail + kBarBytes);
   s.fail = reinterpret_cast<int*>(tail + kBarBytes + 8);
   s.q = reinterpret_cast<int64_t*>(tail + kBarBytes + 16);
-  s.epi = reinterpret_cast<float*>(tail + kTail);
   return s;
 }
 
@@ -585,6 +583,44 @@ __device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, ui
   }
 }
 
+// Phase 1 with the roles swapped: the 128-row halves of the split X chunk
+// (rows = vector columns) are A (M = 128), the operator chunk (rows = slots)
+// is B with N = the item's slot count rounded up to 16, and half h
+// accumulates at TMEM column offset 128 h.  The accumulator lanes are then
+// vector columns, so the epilogue writes the K-major split slot workspace
+// without a transpose, and short slot tiles cost no padded MMA rows.
+template <int F>
+__device__ __forceinline__ void issue_mma_p1(const uint8_t* op, const uint8_t* x, uint32_t acc, bool first, int nh,
+                                             uint32_t idesc) {
+  using G = Geo<F>;
+  const uint32_t b_hi = umma::smem_u32(op), b_lo = b_hi + G::kABytes;
+  for (int h = 0; h < nh; h++) {
+    const uint32_t a_hi = umma::smem_u32(x) + (uint32_t)h * (G::kBBytes / 2), a_lo = a_hi + G::kBBytes;
+    const uint32_t d = acc + (uint32_t)(h * (kN / 2));
+#pragma unroll
+    for (int kk = 0; kk < kK / G::kMmaK; kk++) {
+      const uint32_t koff = kk * 2 * umma::kLBO;
+      const uint64_t ah = umma::smem_desc(a_hi + koff, G::kSBO), al = umma::smem_desc(a_lo + koff, G::kSBO);
+      const uint64_t bh = umma::smem_desc(b_hi + koff, G::kSBO), bl = umma::smem_desc(b_lo + koff, G::kSBO);
+      const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+      if constexpr (fmt_of(F) == 1) {
+        umma::mma_tf32(d, ah, bh, idesc, acc0);
+        umma::mma_tf32(d, ah, bl, idesc, 1u);
+        umma::mma_tf32(d, al, bh, idesc, 1u);
+      } else {
+        umma::mma_f16(d, ah, bh, idesc, acc0);
+        umma::mma_f16(d, ah, bl, idesc, 1u);
+        umma::mma_f16(d, al, bh, idesc, 1u);
+      }
+    }
+  }
+}
+
+// Slot count of a phase-1 item rounded up to the MMA's N granularity.
+__device__ __forceinline__ int p1_n(int nq) { return (nq + 15) & ~15; }
+// Halves of column tile ct that hold vector columns (the other is all zero).
+__device__ __forceinline__ int p1_halves(int ncols, int ct) { return ncols - ct * kN > kN / 2 ? 2 : 1; }
+
 template <int F, class Ph>
 __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& js, uint32_t tmem) {
   using G = Geo<F>;
@@ -594,7 +630,15 @@ __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& j
   int64_t id;
   for (; ok && next_tile(s, tl, id); tl++) {
     const Ph ph = js.get((int)(id >> kJobShift));
-    const int nch = ph.nchunk((id & kLocalMask) / ph.nct);
+    const int64_t lw = (id & kLocalMask) / ph.nct;
+    const int nch = ph.nchunk(lw);
+    int nh = 0;
+    uint32_t idesc1 = 0;
+    if constexpr (std::is_same<Ph, Ph1>::value) {
+      nh = p1_halves(ph.ncols, (int)((id & kLocalMask) % ph.nct));
+      const int n = p1_n(ph.items[lw].nq);
+      idesc1 = fmt_of(F) == 1 ? umma::idesc_tf32(kM, n) : umma::idesc_f16(kM, n);
+    }
     const int b = tl & 1;
     if (tl >= 2 && !wait_bar(s, G::AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
     umma::fence_after_sync();
@@ -609,8 +653,12 @@ __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& j
 #if FKF_TC_STAGE_FENCE
       umma::fence_after_sync();
 #endif
-      for (int j = 0; j < nin; j++, c++)
-        issue_mma<F>(s.a(st) + j * G::kAChunk, s.b(st) + j * G::kBChunk, acc, c == 0);
+      for (int j = 0; j < nin; j++, c++) {
+        if constexpr (std::is_same<Ph, Ph1>::value)
+          issue_mma_p1<F>(s.a(st) + j * G::kAChunk, s.b(st) + j * G::kBChunk, acc, c == 0, nh, idesc1);
+        else
+          issue_mma<F>(s.a(st) + j * G::kAChunk, s.b(st) + j * G::kBChunk, acc, c == 0);
+      }
       umma::commit(&s.bar[G::EMPTY + st]);
     }
     if (!ok) break;
@@ -690,21 +738,24 @@ __device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const JobSet<Ph>
   }
 }
 
-// Phase 1: slot rows into the split slot workspace, or partial rows.  The
-// slots of a tile come in aligned groups of 4 that map to 4 consecutive
-// aligned positions of the split workspace (blocks have a multiple of 4
-// slots), i.e. 4 k of one column: each warp stages its 32 rows x 32 columns
-// in shared memory and writes whole groups, a warp covering a contiguous
-// run per hi/lo half.  (Slot values stay scaled: phase 2's operator columns
-// carry the inverse scales.)
+// Phase 1: slot values into the split slot workspace, or partial rows.  The
+// accumulator of half h holds (vector column, slot): lane = column
+// 128 h + 32 quarter + lane of the column tile, TMEM column = slot of the
+// item.  A lane loads 32 slots of its column and stores them as the 16-row
+// K-major chunks of the workspace: the slots of a tile come in aligned
+// groups of 4 that map to 4 consecutive aligned positions (blocks have a
+// multiple of 4 slots), i.e. 4 k of one workspace row; two groups that
+// fill one 16-byte FP16 unit go out as one store per half.  Partial rows
+// (clusters split over several leaf groups) are FP32 rows of the partial
+// buffer.  (Slot values stay scaled: phase 2's operator columns carry the
+// inverse scales.)
 template <int F>
 __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>& js, uint32_t tmem) {
   using G = Geo<F>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3;
   const int half = (warp - 2) >> 2;
-  const int row = 32 * quarter + lane;
-  float* tile = s.epi + (warp - 2) * 32 * kEpiLd;
+  const int nl = half * (kN / 2) + 32 * quarter + lane;  // column within the column tile
   int tl = 0;
   int64_t id;
   for (; next_tile(s, tl, id); tl++) {
@@ -718,68 +769,49 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
     const int64_t w = lid / nct;
     const int ct = (int)(lid % nct);
     const int n0 = ct * kN;
-    const int nv = min(kN, ph.ncols - n0);
+    const bool col_ok = n0 + nl < ph.ncols;
     const P1Item& it = ph.items[w];
     const bool zero = it.nchunk == 0;
     const bool partial = it.out_row >= 0;
-    RowSinkY psink{(partial && row < it.nq) ? ph.part + (it.out_row + row) * ph.ldp + n0 : nullptr};
-    // split-workspace chunk and k of the 8 slot groups of this warp's rows
-    uint8_t* gchunk[8];
-    int gk[8];
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int r4 = 32 * quarter + 4 * q;
-      gchunk[q] = nullptr;
-      gk[q] = 0;
-      if (!partial && r4 < it.nq) {
-        const int64_t p = ph.slotpos[it.map_off + r4];
-        gchunk[q] = ph.zsplit + ((p >> 4) * nct + ct) * (int64_t)G::kBChunk;
-        gk[q] = (int)(p & 12);
-      }
-    }
-    // slot tiles are often shorter than 128: warps whose rows are all past the
-    // item's slots skip the accumulator loads and stores
-    const int jend = 32 * quarter < it.nq ? 4 * half + 4 : 4 * half;
+    // the warps of an all-zero half (past the pass's columns) have nothing to load
+    const bool active = half < p1_halves(ph.ncols, ct);
+    const uint32_t tbase = tmem + (uint32_t)(b * kN + half * (kN / 2)) + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll 1
-    for (int j = 4 * half; j < jend; j++) {
+    for (int j = 0; active && 32 * j < it.nq; j++) {
       float v[32];
       if (zero) {
 #pragma unroll
         for (int i = 0; i < 32; i++) v[i] = 0.f;
       } else {
-        umma::tmem_ld32(tmem + (uint32_t)(b * kN) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * j), v);
+        umma::tmem_ld32(tbase + (uint32_t)(32 * j), v);
       }
+      if (!col_ok) continue;
+      const int q0 = 32 * j;
       if (partial) {
-        psink.put(32 * j, nv, v, 1.f, nullptr);
-      } else {
+        float* dst = ph.part + (it.out_row + q0) * ph.ldp + n0 + nl;
 #pragma unroll
-        for (int i = 0; i < 32; i++) tile[lane * kEpiLd + i] = v[i];
-        __syncwarp();
-        const int n = 32 * j + lane;  // column of this lane
-        if (n < nv) {
+        for (int i = 0; i < 32; i++)
+          if (q0 + i < it.nq) dst[(int64_t)i * ph.ldp] = v[i];
+        continue;
+      }
+      int64_t p[8];
 #pragma unroll
-          for (int q = 0; q < 8; q += 2) {
-            // FP16: two groups that fill one 16-byte unit (positions p, p + 4 with p % 8 == 0) go
-            // out as one store per half
-            if (fmt_of(F) == 2 && gchunk[q] && gchunk[q + 1] == gchunk[q] && gk[q + 1] == gk[q] + 4 &&
-                (gk[q] & 7) == 0) {
-              float v[8];
+      for (int u = 0; u < 8; u++) p[u] = q0 + 4 * u < it.nq ? ph.slotpos[it.map_off + q0 + 4 * u] : -1;
 #pragma unroll
-              for (int i = 0; i < 8; i++) v[i] = tile[(4 * q + i) * kEpiLd + lane];
-              put_unit<F>(gchunk[q], gchunk[q] + G::kBBytes, n, gk[q], v);
-              continue;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-              const int qq = q + h;
-              if (gchunk[qq])
-                put4<F>(gchunk[qq], gchunk[qq] + G::kBBytes, n, gk[qq], tile[(4 * qq + 0) * kEpiLd + lane],
-                        tile[(4 * qq + 1) * kEpiLd + lane], tile[(4 * qq + 2) * kEpiLd + lane],
-                        tile[(4 * qq + 3) * kEpiLd + lane]);
-            }
-          }
+      for (int u = 0; u < 8; u += 2) {
+        if (p[u] < 0) continue;
+        uint8_t* ch = ph.zsplit + ((p[u] >> 4) * nct + ct) * (int64_t)G::kBChunk;
+        // FP16: two groups that fill one 16-byte unit (positions p, p + 4 with p % 8 == 0)
+        if (fmt_of(F) == 2 && p[u + 1] == p[u] + 4 && (p[u] & 7) == 0) {
+          put_unit<F>(ch, ch + G::kBBytes, nl, (int)(p[u] & 12), &v[4 * u]);
+          continue;
         }
-        __syncwarp();
+        put4<F>(ch, ch + G::kBBytes, nl, (int)(p[u] & 12), v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        if (p[u + 1] >= 0) {
+          uint8_t* ch1 = ph.zsplit + ((p[u + 1] >> 4) * nct + ct) * (int64_t)G::kBChunk;
+          put4<F>(ch1, ch1 + G::kBBytes, nl, (int)(p[u + 1] & 12), v[4 * u + 4], v[4 * u + 5], v[4 * u + 6],
+                  v[4 * u + 7]);
+        }
       }
     }
     umma::fence_before_sync();
@@ -847,10 +879,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---- operator stream ---------------------------------------------------------
 // Element (i, k) of chunk ch, unscaled (0 outside the chunk's rows and kv).
+__device__ __forceinline__ bool chunk_row(const TcAChunk& ch, int i) {
+  return (i >= ch.row_lo && i < ch.row_hi) || (i >= ch.row_lo2 && i < ch.row_hi2);
+}
 __device__ __forceinline__ float chunk_elem(const TcAChunk& ch, const float* fac, const float* nearv, int i, int k) {
-  if (i < ch.row_lo || i >= ch.row_hi || k >= ch.kv) return 0.f;
+  if (k >= ch.kv) return 0.f;
   const float* src = ch.near ? nearv : fac;
-  return src[ch.src_off + (int64_t)(i - ch.row_lo) * ch.si + (int64_t)k * ch.sk];
+  if (i >= ch.row_lo && i < ch.row_hi) return src[ch.src_off + (int64_t)(i - ch.row_lo) * ch.si + (int64_t)k * ch.sk];
+  if (i >= ch.row_lo2 && i < ch.row_hi2)
+    return src[ch.src_off2 + (int64_t)(i - ch.row_lo2) * ch.si2 + (int64_t)k * ch.sk];
+  return 0.f;
 }
 
 // Scale passes of format 2 over the chunks of one phase: per scale row (a
@@ -864,7 +902,7 @@ __global__ void __launch_bounds__(128) k_tc_rowmax(const TcAChunk* __restrict__ 
   const int i = threadIdx.x;
   for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
     const TcAChunk ch = d[c];
-    if (ch.phase != phase || i < ch.row_lo || i >= ch.row_hi) continue;
+    if (ch.phase != phase || !chunk_row(ch, i)) continue;
     float m = 0.f;
     for (int k = 0; k < ch.kv; k++) {
       float a = fabsf(chunk_elem(ch, fac, nearv, i, k));
@@ -917,7 +955,7 @@ __global__ void k_tc_build_a(const TcAChunk* __restrict__ d, int64_t n, const fl
     for (int e = threadIdx.x; e < kM * NU; e += blockDim.x) {
       const int i = e / NU, kq = e % NU;
       float rs = 1.f;
-      if (fmt_of(F) == 2 && i >= ch.row_lo && i < ch.row_hi)
+      if (fmt_of(F) == 2 && chunk_row(ch, i))
         rs = ch.phase == 1 ? qslot[ch.s_off + i] : rpt[ch.s_off + i];
       float v[G::kPer];
 #pragma unroll
@@ -1050,7 +1088,7 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   // the largest carveout (not the smallest that fits phase 2): the SM keeps room for one FP64 tile CTA
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1063,7 +1101,7 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
     FKF_TRY(tc_split_pass<F>(h, X + c0, ldx, nc, st, cs, ctx->x_colmax ? ctx->x_colmax + c0 : nullptr));
     if (h->n_tcp1 > 0) {
       const int grid = (int)std::min<int64_t>(sms, h->n_tcp1 * nct);
-      k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(JobSet<Ph1>{tc_ph1<F>(h, nc), nullptr, nullptr, 0},
+      k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmemRows, st>>>(JobSet<Ph1>{tc_ph1<F>(h, nc), nullptr, nullptr, 0},
                                                             h->n_tcp1 * nct, counters, h->tc_err.as<int>(),
                                                             h->tc_polls);
       FKF_LAUNCHED(ctx);
@@ -1152,7 +1190,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
   FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, st));
   int sms = 0;
   FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph1>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemRows));
   // the largest carveout (not the smallest that fits phase 2): the SM keeps room for one FP64 tile CTA
   FKF_CUDA(ctx, cudaFuncSetAttribute(k_tc_apply<F, Ph2>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1161,7 +1199,7 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
     const JobSet<Ph1> js{p1[0], reinterpret_cast<const Ph1*>(db + o1), reinterpret_cast<const int64_t*>(db + ot1),
                          (int)p1.size()};
     const int grid = (int)std::min<int64_t>(sms, t1.back());
-    k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmem, st>>>(js, t1.back(), counters, err, polls);
+    k_tc_apply<F, Ph1><<<grid, kThreads, G::kSmemRows, st>>>(js, t1.back(), counters, err, polls);
     FKF_LAUNCHED(ctx);
   }
   for (int f : active) FKF_TRY(tc_reduce<F>(hs[f], (int)ncols[f], st));
@@ -1470,6 +1508,10 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
         a.sk = 1;
         a.row_lo = sg.row_lo;
         a.row_hi = sg.row_hi;
+        a.src_off2 = sg.a_off2 + k0;
+        a.si2 = sg.lda2;
+        a.row_lo2 = sg.row_lo2;
+        a.row_hi2 = sg.row_hi2;
         a.kv = std::min(kK, sg.K - k0);
         a.near = sg.near;
         a.phase = 2;
@@ -1535,13 +1577,25 @@ void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector
         const P2Seg& sg = segs[lf.seg0 + k];
         const int64_t a_off = sg.a_off + (int64_t)lf.pad * sg.lda;
         bool merged = false;
-        for (size_t q = t.seg0; q < tsegs.size(); q++) {
+        for (size_t q = t.seg0; q < tsegs.size() && !merged; q++) {
           TcSeg& e = tsegs[q];
-          if (e.near == sg.near && e.b_row == sg.b_row && e.K == sg.K && e.lda == sg.lda && e.row_hi == ro &&
-              e.a_off + (int64_t)(e.row_hi - e.row_lo) * e.lda == a_off) {
-            e.row_hi = ro + lf.rows;
+          if (e.near != sg.near || e.b_row != sg.b_row || e.K != sg.K) continue;
+          const bool two = e.row_hi2 > e.row_lo2;
+          if (!two && e.lda == sg.lda && e.row_hi == ro && e.a_off + (int64_t)(e.row_hi - e.row_lo) * e.lda == a_off) {
+            e.row_hi = ro + lf.rows;  // the rows continue the segment's A block
             merged = true;
-            break;
+          } else if (two && e.lda2 == sg.lda && e.row_hi2 == ro &&
+                     e.a_off2 + (int64_t)(e.row_hi2 - e.row_lo2) * e.lda2 == a_off) {
+            e.row_hi2 = ro + lf.rows;  // the rows continue its second A block
+            merged = true;
+          } else if (!two && sg.near && e.row_hi <= ro) {
+            // the same near partner for a later leaf of the tile: its A block
+            // becomes the segment's second row range (the B chunks are shared)
+            e.a_off2 = a_off;
+            e.lda2 = sg.lda;
+            e.row_lo2 = ro;
+            e.row_hi2 = ro + lf.rows;
+            merged = true;
           }
         }
         if (!merged) {
