@@ -760,9 +760,8 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
   int64_t id;
   for (; next_tile(s, tl, id); tl++) {
     const int b = tl & 1;
-    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
-    umma::fence_after_sync();
-    if (s.failed()) break;
+    // the tile's descriptors and slot positions are loaded while its MMAs
+    // run: lane L holds the workspace position of slot group L (slots 4L..)
     const Ph1 ph = js.get((int)(id >> kJobShift));
     const int64_t lid = id & kLocalMask;
     const int nct = ph.nct;
@@ -770,9 +769,13 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
     const int ct = (int)(lid % nct);
     const int n0 = ct * kN;
     const bool col_ok = n0 + nl < ph.ncols;
-    const P1Item& it = ph.items[w];
+    const P1Item it = ph.items[w];
     const bool zero = it.nchunk == 0;
     const bool partial = it.out_row >= 0;
+    const int64_t pl = (!partial && 4 * lane < it.nq) ? ph.slotpos[it.map_off + 4 * lane] : -1;
+    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    umma::fence_after_sync();
+    if (s.failed()) break;
     // the warps of an all-zero half (past the pass's columns) have nothing to load
     const bool active = half < p1_halves(ph.ncols, ct);
     const uint32_t tbase = tmem + (uint32_t)(b * kN + half * (kN / 2)) + ((uint32_t)(32 * quarter) << 16);
@@ -785,6 +788,9 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
       } else {
         umma::tmem_ld32(tbase + (uint32_t)(32 * j), v);
       }
+      int64_t p[8];  // workspace positions of this j's 8 slot groups (-1: none)
+#pragma unroll
+      for (int u = 0; u < 8; u++) p[u] = __shfl_sync(0xffffffffu, pl, 8 * j + u);
       if (!col_ok) continue;
       const int q0 = 32 * j;
       if (partial) {
@@ -794,9 +800,6 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
           if (q0 + i < it.nq) dst[(int64_t)i * ph.ldp] = v[i];
         continue;
       }
-      int64_t p[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) p[u] = q0 + 4 * u < it.nq ? ph.slotpos[it.map_off + q0 + 4 * u] : -1;
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         if (p[u] < 0) continue;
@@ -1229,6 +1232,11 @@ fkf_status build_stream(fkf_hmat* h, int F) {
     h->tca_fmt = F;
     return FKF_OK;
   }
+  const size_t need = (size_t)h->n_tca * (F == 1 ? Geo<1>::kAChunk : Geo<2>::kAChunk);
+  if (h->tca.bytes < need) {
+    h->tca_fmt = 0;  // the old stream is gone
+    FKF_TRY(dev_alloc(ctx, h->tca, need));
+  }
   const int grid = (int)std::min<int64_t>(h->n_tca, 152 * 8);
   const TcAChunk* d = h->tcadesc.as<TcAChunk>();
   if (F == 2) {
@@ -1540,8 +1548,9 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
   while (panel > kN && (double)h->n_tcz * (panel / kN) * Geo<1>::kBChunk > 24e9) panel /= 2;
   h->tc_panel = panel;
   h->n_tca = (int64_t)ch.size();
-  // the stream holds either format (format 1 chunks are the larger)
-  FKF_TRY(dev_alloc(ctx, h->tca, (size_t)std::max<int64_t>(h->n_tca, 1) * Geo<1>::kAChunk));
+  // the stream is sized for the format it holds (build_stream grows it for
+  // the larger 3xTF32 chunks)
+  h->tca.release();
   if (h->n_tca > 0) FKF_TRY(dev_upload(ctx, h->tcadesc, ch.data(), ch.size() * sizeof(TcAChunk)));
   FKF_TRY(build_stream(h, 2));
   h->engine = 2;
