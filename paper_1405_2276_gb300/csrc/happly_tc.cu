@@ -75,6 +75,13 @@
 #ifndef FKF_TC_STAGES_F16
 #define FKF_TC_STAGES_F16 (8 / FKF_TC_F16_CHUNKS_PER_STAGE)
 #endif
+// the second FP16 pipeline shape (kernel code 3) that the autotuner tries
+#ifndef FKF_TC_F16_ALT_CHUNKS_PER_STAGE
+#define FKF_TC_F16_ALT_CHUNKS_PER_STAGE 2
+#endif
+#ifndef FKF_TC_STAGES_F16_ALT
+#define FKF_TC_STAGES_F16_ALT 4
+#endif
 
 namespace {
 
@@ -84,7 +91,7 @@ constexpr int kK = umma::kChunk;  // 16: K per chunk
 constexpr int kEpiWarps = 8;      // warps 2-9: two per TMEM lane quarter, one per column half
 constexpr int kQ = 8;             // tile-index queue (producer -> MMA, epilogue)
 constexpr int kBarBytes = 384;
-constexpr int kTail = 512;        // barriers, TMEM address, flag, queue
+constexpr int kTail = 640;        // barriers, TMEM address, flag, queue
 constexpr int kProdWarp = 0, kMmaWarp = 1;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 2 * kN;
@@ -108,9 +115,11 @@ struct Geo {
   static constexpr int kBBytes = kN * kK * kEl;    // one half of a B chunk (256 columns)
   static constexpr int kBChunk = 2 * kBBytes;
   static constexpr int kCPS = F == 1 ? FKF_TC_TF32_CHUNKS_PER_STAGE
-                                     : (F == 2 ? FKF_TC_F16_CHUNKS_PER_STAGE : 2);  // chunks per stage
+                                     : (F == 2 ? FKF_TC_F16_CHUNKS_PER_STAGE
+                                               : FKF_TC_F16_ALT_CHUNKS_PER_STAGE);  // chunks per stage
   static constexpr int kStage = kCPS * (kAChunk + kBChunk);
-  static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32 : (F == 2 ? FKF_TC_STAGES_F16 : 4);  // pipeline stages
+  static constexpr int kS = F == 1 ? FKF_TC_STAGES_TF32
+                                   : (F == 2 ? FKF_TC_STAGES_F16 : FKF_TC_STAGES_F16_ALT);  // pipeline stages
   static constexpr uint32_t kSBO = (kK / kPer) * 128;  // next 8-row group
   static constexpr uint32_t kIdesc = kFmt == 1 ? umma::idesc_tf32(kM, kN) : umma::idesc_f16(kM, kN);
   // every epilogue stores straight from TMEM (no staging tiles): the room
@@ -127,6 +136,13 @@ struct Geo {
   }
 };
 
+// Tile queue entry (producer -> MMA issuer, epilogue).
+struct TileQ {
+  int64_t id;  // packed (job, tile), -1: no more tiles
+  int32_t nch; // K-chunks of the tile
+  int32_t n;   // phase 1: MMA N (the item's slots rounded up to 16)
+};
+
 template <int F>
 struct Smem {
   uint8_t* base;
@@ -134,7 +150,7 @@ struct Smem {
   uint32_t* tmem_slot;
   int* fail;
   uint32_t polls;  // poll limit of the pipeline waits (kMaxPolls unless a caller lowered it)
-  int64_t* q;  // [kQ] tile indices (-1: no more tiles)
+  TileQ* q;  // [kQ] tile entries (id -1: no more tiles)
 
   // stage s: the A chunks of its kCPS chunks (consecutive), then their B chunks
   __device__ __forceinline__ uint8_t* a(int s) const { return base + s * Geo<F>::kStage; }
@@ -153,7 +169,7 @@ __device__ __forceinline__ Smem<F> smem_layout(uint8_t* base) {
   s.bar = reinterpret_cast<uint64_t*>(tail);
   s.tmem_slot = reinterpret_cast<uint32_t*>(tail + kBarBytes);
   s.fail = reinterpret_cast<int*>(tail + kBarBytes + 8);
-  s.q = reinterpret_cast<int64_t*>(tail + kBarBytes + 16);
+  s.q = reinterpret_cast<TileQ*>(tail + kBarBytes + 16);
   return s;
 }
 
@@ -496,14 +512,22 @@ struct JobSet {
 };
 
 // ---- roles -----------------------------------------------------------------
+// Slot count of a phase-1 item rounded up to the MMA's N granularity.
+__device__ __forceinline__ int p1_n(int nq) { return (nq + 15) & ~15; }
+// Halves of column tile ct that hold vector columns (the other is all zero).
+__device__ __forceinline__ int p1_halves(int ncols, int ct) { return ncols - ct * kN > kN / 2 ? 2 : 1; }
 // Next tile of this CTA: taken from the global counter by the producer and
 // published in the queue; every consumer reads each queue entry once.
 template <int F>
-__device__ __forceinline__ bool next_tile(const Smem<F>& s, int qi, int64_t& id) {
+__device__ __forceinline__ bool next_tile(const Smem<F>& s, int qi, int64_t& id, int* nch = nullptr,
+                                          int* n = nullptr) {
   using G = Geo<F>;
   const int slot = qi % kQ;
   if (!wait_bar(s, G::QF + slot, (uint32_t)(qi / kQ) & 1)) return false;
-  id = *reinterpret_cast<volatile int64_t*>(&s.q[slot]);
+  volatile TileQ* e = &s.q[slot];
+  id = e->id;
+  if (nch) *nch = e->nch;
+  if (n) *n = e->n;
   umma::mbar_arrive(&s.bar[G::QE + slot]);
   return id >= 0;
 }
@@ -522,16 +546,27 @@ __device__ __forceinline__ void producer(const Smem<F>& s, const JobSet<Ph>& js,
     const int64_t id = (int64_t)atomicAdd(counter, 1ull);
     const int64_t packed = id < ntiles ? js.pack(id) : -1;
     const int slot = qi % kQ;
+    // the tile's chunk count (and phase 1's MMA N) travel with its index, so
+    // the MMA issuer reads nothing from global memory between tiles
+    Ph ph{};
+    int64_t w = 0;
+    int ct = 0, nch = 0, nn = 0;
+    if (packed >= 0) {
+      ph = js.get((int)(packed >> kJobShift));
+      const int64_t lid = packed & kLocalMask;
+      w = lid / ph.nct;
+      ct = (int)(lid % ph.nct);
+      nch = ph.nchunk(w);
+      if constexpr (std::is_same<Ph, Ph1>::value) nn = p1_n(ph.items[w].nq);
+    }
     if (qi >= kQ && !wait_bar(s, G::QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
-    *reinterpret_cast<volatile int64_t*>(&s.q[slot]) = packed;
+    volatile TileQ* e = &s.q[slot];
+    e->id = packed;
+    e->nch = nch;
+    e->n = nn;
     umma::mbar_arrive(&s.bar[G::QF + slot]);
     if (packed < 0) return;
-    const Ph ph = js.get((int)(packed >> kJobShift));
-    const int64_t lid = packed & kLocalMask;
     const int nct = ph.nct;
-    const int64_t w = lid / nct;
-    const int ct = (int)(lid % nct);
-    const int nch = ph.nchunk(w);
     const uint8_t* ap = ph.astream + ph.a_chunk0(w) * (int64_t)G::kAChunk;
     const int ns = ph.nseg(w);
     int t = 0, j = 0, nin = 0, st = 0;  // chunk of the tile, chunk within the stage, chunks in the stage
@@ -616,10 +651,6 @@ __device__ __forceinline__ void issue_mma_p1(const uint8_t* op, const uint8_t* x
   }
 }
 
-// Slot count of a phase-1 item rounded up to the MMA's N granularity.
-__device__ __forceinline__ int p1_n(int nq) { return (nq + 15) & ~15; }
-// Halves of column tile ct that hold vector columns (the other is all zero).
-__device__ __forceinline__ int p1_halves(int ncols, int ct) { return ncols - ct * kN > kN / 2 ? 2 : 1; }
 
 template <int F, class Ph>
 __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& js, uint32_t tmem) {
@@ -628,16 +659,14 @@ __device__ __forceinline__ void mma_issuer(const Smem<F>& s, const JobSet<Ph>& j
   int tl = 0;
   bool ok = true;
   int64_t id;
-  for (; ok && next_tile(s, tl, id); tl++) {
-    const Ph ph = js.get((int)(id >> kJobShift));
-    const int64_t lw = (id & kLocalMask) / ph.nct;
-    const int nch = ph.nchunk(lw);
+  int nch = 0, nn = 0;
+  for (; ok && next_tile(s, tl, id, &nch, &nn); tl++) {
     int nh = 0;
     uint32_t idesc1 = 0;
     if constexpr (std::is_same<Ph, Ph1>::value) {
+      const Ph ph = js.get((int)(id >> kJobShift));  // a kernel parameter unless the launch has a job list
       nh = p1_halves(ph.ncols, (int)((id & kLocalMask) % ph.nct));
-      const int n = p1_n(ph.items[lw].nq);
-      idesc1 = fmt_of(F) == 1 ? umma::idesc_tf32(kM, n) : umma::idesc_f16(kM, n);
+      idesc1 = fmt_of(F) == 1 ? umma::idesc_tf32(kM, nn) : umma::idesc_f16(kM, nn);
     }
     const int b = tl & 1;
     if (tl >= 2 && !wait_bar(s, G::AE + b, (uint32_t)((tl >> 1) - 1) & 1)) break;
@@ -705,21 +734,23 @@ __device__ __forceinline__ void epilogue_rows(const Smem<F>& s, const JobSet<Ph>
   const int row = 32 * quarter + lane;
   int tl = 0;
   int64_t id;
-  for (; next_tile(s, tl, id); tl++) {
+  int nch = 0;
+  for (; next_tile(s, tl, id, &nch); tl++) {
     const int b = tl & 1;
-    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
-    umma::fence_after_sync();
-    if (s.failed()) break;
+    // the tile's destination rows and scales are loaded while its MMAs run
     const Ph ph = js.get((int)(id >> kJobShift));
     const int64_t lid = id & kLocalMask;
     const int64_t w = lid / ph.nct;
     const int n0 = (int)(lid % ph.nct) * kN;
     const int nv = min(kN, ph.ncols - n0);
-    const bool zero = ph.nchunk(w) == 0;
+    const bool zero = nch == 0;
     float rinv = 1.f;
     float* dst = ph.row_dst(w, row, rinv);
     const RowSinkY sink{dst ? dst + n0 : nullptr};
     const float* cinv = ph.cinv ? ph.cinv + n0 : nullptr;
+    if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
+    umma::fence_after_sync();
+    if (s.failed()) break;
     // a warp whose 32 rows are all past the tile's rows has nothing to store
     const int jend = __any_sync(0xffffffffu, dst != nullptr) ? 4 * half + 4 : 4 * half;
 #pragma unroll 1
@@ -758,7 +789,8 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
   const int nl = half * (kN / 2) + 32 * quarter + lane;  // column within the column tile
   int tl = 0;
   int64_t id;
-  for (; next_tile(s, tl, id); tl++) {
+  int nch = 0;
+  for (; next_tile(s, tl, id, &nch); tl++) {
     const int b = tl & 1;
     // the tile's descriptors and slot positions are loaded while its MMAs
     // run: lane L holds the workspace position of slot group L (slots 4L..)
@@ -770,7 +802,7 @@ __device__ __forceinline__ void epilogue_p1(const Smem<F>& s, const JobSet<Ph1>&
     const int n0 = ct * kN;
     const bool col_ok = n0 + nl < ph.ncols;
     const P1Item it = ph.items[w];
-    const bool zero = it.nchunk == 0;
+    const bool zero = nch == 0;
     const bool partial = it.out_row >= 0;
     const int64_t pl = (!partial && 4 * lane < it.nq) ? ph.slotpos[it.map_off + 4 * lane] : -1;
     if (!wait_bar(s, G::AF + b, (uint32_t)(tl >> 1) & 1)) break;
