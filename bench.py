@@ -414,6 +414,43 @@ def run_gpu(args, rank, world):
             ev = float(np.abs(snap32["var"] - snap64["var"]).max() / np.abs(snap64["var"]).max())
             res["err_fp32_vs_fp64"] = {"step": cmp_step, "s_hat_rel_max": es, "var_rel_max": ev}
         fkf.fkf_filter_destroy(f64)
+
+        # the same FP64 path with its products on the tensor cores (engine 3: 7-bit integer
+        # slices, exact FP32 sums per block); CUDA events around the steps after the first
+        fkf.fkf_hmatrix_set_engine(hm64, 3)
+        f64t = fkf.fkf_filter_create(hm64, None, 0.0, 1e-12, m, 2 * m)
+        nt = max(args.fp64_steps + 2, cmp_step)
+        snap64t = None
+        ev_t0 = torch.cuda.Event(enable_timing=True)
+        ev_t1 = torch.cuda.Event(enable_timing=True)
+        for k in range(nt):
+            if k == 1:
+                torch.cuda.synchronize()
+                ev_t0.record(stream)
+            step_dev(f64t, k)
+            if k + 1 == cmp_step:
+                ev_t1.record(stream)  # (the snapshot below is outside the timed steps)
+                ev_t1.synchronize()
+                t_part = ev_t0.elapsed_time(ev_t1) if k >= 1 else 0.0
+                snap64t = fkf.fkf_filter_get(f64t, n)
+                v = torch.empty(n, dtype=torch.float64, device="cuda")
+                fkf.fkf_variance(f64t, v)
+                snap64t["var"] = v.cpu().numpy()
+                torch.cuda.synchronize()
+                ev_t0.record(stream)
+        ev_t1.record(stream)
+        ev_t1.synchronize()
+        ms_t = (t_part + ev_t0.elapsed_time(ev_t1)) / (nt - 1)
+        res["fp64_tc"] = dict(ms_per_step=ms_t, steps_per_s=1e3 / ms_t, steps=nt - 1,
+                              phases_ms=fkf.fkf_filter_phase_times(f64t))
+        res["happly64_tc"] = time_apply(hm64, info64, fkf.FKF_FP64, 3)
+        if snap64 is not None and snap64t is not None:
+            res["fp64_tc"]["err_vs_fp64"] = {
+                "step": cmp_step,
+                "s_hat_rel_max": float(np.abs(snap64t["s"] - snap64["s"]).max() / np.abs(snap64["s"]).max()),
+                "var_rel_max": float(np.abs(snap64t["var"] - snap64["var"]).max() / np.abs(snap64["var"]).max())}
+        log(f"[bench] FP64 path on the tensor cores (engine 3): {res['fp64_tc']}  H-apply {res['happly64_tc']}")
+        fkf.fkf_filter_destroy(f64t)
         fkf.fkf_hmatrix_destroy(hm64)
     fkf.fkf_destroy(ctx)
     res["snap32"] = snap32 if cmp_step == 3 else None
@@ -725,6 +762,15 @@ def main():
                        "happly_gbs": res["happly64"]["gbs"], "happly_ms": res["happly64"]["ms"],
                        "happly_tflops": res["happly64"]["tflops"], "phases_ms": res["fp64"]["phases_ms"]}
                       if "fp64" in res else None),
+        "fp64_path_tensor_cores": ({"steps_per_s": res["fp64_tc"]["steps_per_s"],
+                                    "ms_per_step": res["fp64_tc"]["ms_per_step"], "steps": res["fp64_tc"]["steps"],
+                                    "happly_ms": res["happly64_tc"]["ms"], "happly_tflops": res["happly64_tc"]["tflops"],
+                                    "phases_ms": res["fp64_tc"]["phases_ms"],
+                                    "err_vs_fp64_path": res["fp64_tc"].get("err_vs_fp64"),
+                                    "engine": "3: FP64 products from 7-bit integer slices on the FP16 tensor cores "
+                                              "(Ozaki's error-free splitting, exact FP32 sums per 512-K block)",
+                                    "timing": "CUDA events on the library stream around the steps after the first"}
+                                   if "fp64_tc" in res else None),
         "err_fp32_vs_fp64": res.get("err_fp32_vs_fp64"),
         "err_vs_oracle": err_oracle,
         "phases_ms": dict(zip(["densify", "h_apply", "gather_innov_mean", "gep", "orth_merge", "rotation"],

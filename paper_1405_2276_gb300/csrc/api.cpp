@@ -235,9 +235,11 @@ FKF_API fkf_status fkf_hmatrix_autotune(fkf_hmat* h, int64_t ncols, int32_t* var
 
 FKF_API fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine) {
   if (!h) return FKF_EINVAL;
-  if (engine < 0 || engine > 2) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0, 1 or 2");
-  if (engine != 0 && h->prec != FKF_FP32)
-    return set_err(h->ctx, FKF_EINVAL, "set_engine: the tensor-core engines need an FP32 operator");
+  if (engine < 0 || engine > 3) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0, 1, 2 or 3");
+  if ((engine == 1 || engine == 2) && h->prec != FKF_FP32)
+    return set_err(h->ctx, FKF_EINVAL, "set_engine: engines 1 and 2 need an FP32 operator");
+  if (engine == 3 && h->prec != FKF_FP64)
+    return set_err(h->ctx, FKF_EINVAL, "set_engine: engine 3 needs an FP64 operator");
   return hmat_set_engine(h, engine);
 }
 

@@ -227,6 +227,58 @@ struct TcUpload {
   int64_t nz = 0, part_rows = 0;
 };
 
+// ---- FP64 operators on the tensor cores (engine 3, happly_oz.cu) ----------
+// Products of FP64 values from exact products of 7-bit integer slices (FP16
+// MMAs, FP32 accumulation that stays exact per K-block).  The vector
+// operand (X, or the slot workspace) is the MMA's A: 128 vector columns x 16
+// K per chunk; the operator is B: 64 rows (slots in phase 1, points in phase
+// 2) x 16 K per chunk.  Vector chunks are indexed chunk * nct + column tile.
+struct OzItem {      // phase 1: slots [q0, q0 + nq) of a cluster times the X rows of a leaf group
+  int64_t x_chunk0;  // first X chunk of the group
+  int64_t b_chunk0;  // first operator chunk of the item
+  int64_t map_off;   // natural slot of slot q0
+  int64_t out_row;   // -1: the slot workspace; else first row of the FP64 partials
+  int32_t nchunk;    // K-chunks
+  int32_t nq;        // slots (<= 64)
+};
+struct OzTile {      // phase 2: up to 64 consecutive points of one leaf
+  int64_t row0;
+  int64_t b_chunk0;
+  int32_t rows, seg0, nseg, nchunk;
+};
+struct OzSeg {       // phase-2 segment: nch vector chunks from chunk a0 (of X if near, else of the workspace)
+  int64_t a0;
+  int32_t nch, near;
+};
+// One operator chunk: element (n, k) = src[src_off + n * si + k * sk] for
+// n < rows, k < kv (src = the far factors, or the near blocks if near), times
+// the workspace-position bound of column k (k_off + k) for far phase-2
+// chunks, over the power-of-two scale of row n (natural slot s_off + n in
+// phase 1, point s_off + n in phase 2); zero elsewhere.
+struct OzBChunk {
+  int64_t src_off;
+  int64_t s_off;
+  int64_t k_off;  // -1: no column factor
+  int32_t si, sk;
+  int32_t rows, kv;
+  int32_t near, phase;
+};
+// Host-side schedule and scales of engine 3, handed from the upload.
+struct OzUpload {
+  std::vector<OzItem> items;
+  std::vector<P1Reduce> reduces;
+  std::vector<OzTile> tiles;
+  std::vector<OzSeg> segs;
+  std::vector<OzBChunk> bchunks;
+  std::vector<TcXChunk> xmap;
+  std::vector<int64_t> slotpos;      // natural slot -> workspace position of its partner
+  std::vector<double> sig_slot;      // per natural slot: power of two >= max |V| of its column
+  std::vector<double> q_slot;        // per natural slot: power of two >= the column's L1 norm
+  std::vector<double> q_pos;         // per workspace position: q_slot of the slot whose product lands there
+  std::vector<double> sig_pt;        // per point: power of two >= max |phase-2 operator row element|
+  int64_t nz = 0, part_rows = 0;
+};
+
 struct HostHmat;  // host-side build result (hbuild.cpp)
 
 struct fkf_hmat {
@@ -260,7 +312,15 @@ struct fkf_hmat {
   int tca_fmt = 0;       // format the split operator stream holds (1, 2)
   int tc_variant = 0;    // pipeline shape of the FP16 engine (0: 4 chunks x 2 stages, 1: 2 x 4; hmat_autotune)
   int zsplit_fmt = 0;    // format last written to the split slot workspace
-  int engine = 0;  // 0: SIMT tile engine; tensor cores (FP32 operators only): 1 = 3xTF32, 2 = scaled 2xFP16
+  int engine = 0;  // 0: SIMT tile engine; tensor cores: 1 = 3xTF32, 2 = scaled 2xFP16 (FP32 operators),
+                   // 3 = integer slices (FP64 operators)
+  // engine 3 (FP64 operators): schedule, scales, sliced operator stream,
+  // sliced X and slot workspace per column pass, FP64 partials
+  DevBuf ozitem, ozred, oztile, ozseg, ozbdesc, ozxmap, ozslot, oz_sigslot, oz_qslot, oz_qpos, oz_sigpt;
+  DevBuf ozb, ozx, ozz, ozpart, oz_col, oz_err;
+  int64_t n_ozitem = 0, n_ozred = 0, n_oztile = 0, n_ozb = 0, n_ozx = 0, n_ozz = 0, oz_part_rows = 0;
+  int64_t oz_panel = 0;
+  bool ozb_built = false;
   // workspace
   DevBuf zmix, part, xperm, yperm;
   int64_t panel = 256;
@@ -280,6 +340,14 @@ fkf_status hmat_permute_rows(fkf_hmat* h, const void* src, int64_t lds, const in
                              int64_t ldd, int64_t nrows, int64_t ncols);
 fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, const int64_t* idx_dev, double* dst,
                                  int64_t ldd, int64_t nrows, int64_t ncols);
+
+// happly_oz.cu
+fkf_status hmat_upload_oz(fkf_hmat* h, OzUpload& ou);
+fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                                   int64_t ncols);
+fkf_status hmat_oz_check(fkf_hmat* h);
+// Writes the sliced operator stream of engine 3 if it is not there yet.
+fkf_status hmat_oz_prepare(fkf_hmat* h);
 
 // happly_tc.cu
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols);

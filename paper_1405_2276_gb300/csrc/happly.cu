@@ -23,6 +23,7 @@
 // so each row block of Y is written once, by one CTA, with no atomics, and
 // X_c is read once per cluster level instead of once per block.
 #include <algorithm>
+#include <cmath>
 #include <unordered_map>
 #include <cstring>
 #include <mutex>
@@ -162,8 +163,10 @@ void fill_typed(void* dst, const double* src, size_t n) {
 
 fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols) {
   if (ncols <= 0) return FKF_OK;
-  if (h->prec == FKF_FP64)
+  if (h->prec == FKF_FP64) {
+    if (h->engine == 3) return hmat_apply_clustered_oz(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
     return apply_impl<double>(h, (const double*)X, ldx, (double*)Y, ldy, ncols);
+  }
   if (h->engine != 0) return hmat_apply_clustered_tc(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
   return apply_impl<float>(h, (const float*)X, ldx, (float*)Y, ldy, ncols);
 }
@@ -247,12 +250,12 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   }
   std::vector<int64_t> K(nc, 0), slot_base(nc, 0), fac_off(nc, 0);
   std::vector<std::vector<int64_t>> slot_col(nc);
-  // FP32 operators give every block a multiple of 4 slots (zero columns) on
-  // both sides, so that aligned groups of 4 slots map to aligned groups of 4
-  // (the tensor-core engine writes its slot rows 4 at a time)
+  // every block gets a multiple of 4 slots (zero columns) on both sides, so
+  // that aligned groups of 4 slots map to aligned groups of 4 (the
+  // tensor-core engines write their slot values 4 at a time)
   auto block_width = [&](int b) -> int64_t {
     const int64_t k = hh.far[b].k;
-    return h->prec == FKF_FP32 ? (k + 3) / 4 * 4 : k;
+    return (k + 3) / 4 * 4;
   };
   int64_t ktot = 0, facn = 0;
   for (int c = 0; c < nc; c++) {
@@ -524,6 +527,168 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
     }
     tu.part_rows = std::max(tparts, part_rows);
   }
+  // FP64 operators: the schedule of the integer-slice tensor-core engine
+  // (engine 3).  Vector chunks as above (X per leaf, the slot workspace per
+  // cluster, 16 rows each); phase-1 items of at most 64 slots over leaf
+  // groups of at most kChunkRows rows; phase-2 tiles of at most 64 points of
+  // one leaf, whose segments are the leaf's ancestors' factor rows and its
+  // near blocks.
+  OzUpload ou;
+  if (h->prec == FKF_FP64) {
+    const int L = (int)leaves.size();
+    std::vector<int64_t> xchunk0(L + 1, 0);
+    for (int l = 0; l < L; l++) {
+      const int c = leaves[l];
+      xchunk0[l] = (int64_t)ou.xmap.size();
+      for (int64_t r = 0; r < csize(c); r += 16)
+        ou.xmap.push_back(TcXChunk{cl[c].begin + r, (int32_t)std::min<int64_t>(16, csize(c) - r), 0});
+    }
+    xchunk0[L] = (int64_t)ou.xmap.size();
+    std::unordered_map<int64_t, int64_t> leaf_by_begin;
+    for (int l = 0; l < L; l++) leaf_by_begin[cl[leaves[l]].begin] = l;
+    std::vector<int64_t> zchunk0(nc, -1), pos(std::max<int64_t>(ktot, 1), 0);
+    int64_t nz = 0;
+    for (int c = 0; c < nc; c++) {
+      if (K[c] == 0) continue;
+      zchunk0[c] = nz;
+      for (int64_t q = 0; q < K[c]; q++) pos[slot_base[c] + q] = nz * 16 + q;
+      nz += cdiv(K[c], 16);
+    }
+    ou.nz = nz;
+    ou.slotpos.resize(std::max<int64_t>(ktot, 1), 0);
+    for (int64_t g = 0; g < ktot; g++) ou.slotpos[g] = pos[smap[g]];
+    // scales of the slices (powers of two, so that every scaling is exact)
+    auto pow2ceil = [](double x) { return x > 0 ? std::ldexp(1.0, std::ilogb(x) + 1) : 1.0; };
+    ou.sig_slot.assign(std::max<int64_t>(ktot, 1), 1.0);
+    ou.q_slot.assign(std::max<int64_t>(ktot, 1), 1.0);
+    for (int c = 0; c < nc; c++)
+      for (int64_t q = 0; q < K[c]; q++) {
+        double mx = 0, l1 = 0;
+        for (int64_t r = 0; r < csize(c); r++) {
+          const double v = std::fabs(facv[fac_off[c] + r * K[c] + q]);
+          mx = std::max(mx, v);
+          l1 += v;
+        }
+        ou.sig_slot[slot_base[c] + q] = pow2ceil(mx);
+        ou.q_slot[slot_base[c] + q] = pow2ceil(l1);
+      }
+    ou.q_pos.assign((size_t)std::max<int64_t>(nz, 1) * 16, 1.0);
+    for (int64_t g = 0; g < ktot; g++) ou.q_pos[ou.slotpos[g]] = ou.q_slot[g];
+    // phase-1 items
+    int64_t parts = 0;
+    for (int c = 0; c < nc; c++) {
+      if (K[c] == 0) continue;
+      int a = c, b = c;
+      while (cl[a].child[0] >= 0) a = cl[a].child[0];
+      while (cl[b].child[1] >= 0) b = cl[b].child[1];
+      const int la = leaf_id[a], lb = leaf_id[b] + 1;
+      std::vector<std::pair<int, int>> groups;
+      for (int l = la; l < lb;) {
+        int e = l;
+        int64_t rows = 0;
+        while (e < lb && (e == l || rows + csize(leaves[e]) <= kChunkRows)) rows += csize(leaves[e++]);
+        groups.push_back({l, e});
+        l = e;
+      }
+      const int ng = (int)groups.size();
+      const int64_t ntq = cdiv(K[c], 64);
+      const int64_t tq = (cdiv(K[c], ntq) + 3) / 4 * 4;
+      for (int64_t q0 = 0; q0 < K[c]; q0 += tq) {
+        const int nq = (int)std::min<int64_t>(tq, K[c] - q0);
+        const int64_t base = parts;
+        for (int g = 0; g < ng; g++) {
+          OzItem it{};
+          it.x_chunk0 = xchunk0[groups[g].first];
+          it.nchunk = (int)(xchunk0[groups[g].second] - xchunk0[groups[g].first]);
+          it.b_chunk0 = (int64_t)ou.bchunks.size();
+          it.map_off = slot_base[c] + q0;
+          it.out_row = ng == 1 ? -1 : base + (int64_t)g * nq;
+          it.nq = nq;
+          ou.items.push_back(it);
+          for (int l = groups[g].first; l < groups[g].second; l++) {
+            const int lc = leaves[l];
+            for (int64_t r = 0; r < csize(lc); r += 16) {
+              OzBChunk bc{};
+              bc.src_off = fac_off[c] + (cl[lc].begin - cl[c].begin + r) * K[c] + q0;
+              bc.si = 1;
+              bc.sk = (int32_t)K[c];
+              bc.rows = nq;
+              bc.kv = (int32_t)std::min<int64_t>(16, csize(lc) - r);
+              bc.phase = 1;
+              bc.s_off = slot_base[c] + q0;
+              bc.k_off = -1;
+              ou.bchunks.push_back(bc);
+            }
+          }
+        }
+        if (ng > 1) {
+          ou.reduces.push_back(P1Reduce{base, slot_base[c] + q0, nq, ng});
+          parts += (int64_t)ng * nq;
+        }
+      }
+    }
+    ou.part_rows = parts;
+    // phase-2 tiles and the point scales
+    ou.sig_pt.assign((size_t)std::max<int64_t>(hh.n, 1), 1.0);
+    for (int l = 0; l < L; l++) {
+      const int tau = leaves[l];
+      const int64_t nt = csize(tau);
+      for (int64_t r0 = 0; r0 < nt; r0 += 64) {
+        OzTile t{};
+        t.row0 = cl[tau].begin + r0;
+        t.rows = (int)std::min<int64_t>(64, nt - r0);
+        t.seg0 = (int)ou.segs.size();
+        t.b_chunk0 = (int64_t)ou.bchunks.size();
+        std::vector<double> rmax((size_t)t.rows, 0.0);
+        for (int c = tau; c >= 0; c = cl[c].parent) {
+          if (K[c] == 0) continue;
+          const int64_t a_row = t.row0 - cl[c].begin;
+          ou.segs.push_back(OzSeg{zchunk0[c], (int32_t)cdiv(K[c], 16), 0});
+          for (int64_t k0 = 0; k0 < K[c]; k0 += 16) {
+            OzBChunk bc{};
+            bc.src_off = fac_off[c] + a_row * K[c] + k0;
+            bc.si = (int32_t)K[c];
+            bc.sk = 1;
+            bc.rows = t.rows;
+            bc.kv = (int32_t)std::min<int64_t>(16, K[c] - k0);
+            bc.phase = 2;
+            bc.s_off = t.row0;
+            bc.k_off = zchunk0[c] * 16 + k0;
+            ou.bchunks.push_back(bc);
+          }
+          for (int i = 0; i < t.rows; i++)
+            for (int64_t q = 0; q < K[c]; q++)
+              rmax[i] = std::max(rmax[i], std::fabs(facv[fac_off[c] + (a_row + i) * K[c] + q]) *
+                                              ou.q_pos[zchunk0[c] * 16 + q]);
+        }
+        for (size_t i = 0; i < partners[l].size(); i++) {
+          const int sg = partners[l][i].sigma;
+          const int64_t ns = csize(sg);
+          ou.segs.push_back(OzSeg{xchunk0[leaf_by_begin.at(cl[sg].begin)], (int32_t)cdiv(ns, 16), 1});
+          for (int64_t k0 = 0; k0 < ns; k0 += 16) {
+            OzBChunk bc{};
+            bc.src_off = near_off[l] + r0 * kn[l] + pcol[l][i] + k0;
+            bc.si = (int32_t)kn[l];
+            bc.sk = 1;
+            bc.rows = t.rows;
+            bc.kv = (int32_t)std::min<int64_t>(16, ns - k0);
+            bc.near = 1;
+            bc.phase = 2;
+            bc.s_off = t.row0;
+            bc.k_off = -1;
+            ou.bchunks.push_back(bc);
+          }
+          for (int ii = 0; ii < t.rows; ii++)
+            for (int64_t b = 0; b < ns; b++)
+              rmax[ii] = std::max(rmax[ii], std::fabs(nearv[near_off[l] + (r0 + ii) * kn[l] + pcol[l][i] + b]));
+        }
+        t.nseg = (int)ou.segs.size() - t.seg0;
+        t.nchunk = (int)((int64_t)ou.bchunks.size() - t.b_chunk0);
+        for (int i = 0; i < t.rows; i++) ou.sig_pt[t.row0 + i] = pow2ceil(rmax[i]);
+        ou.tiles.push_back(t);
+      }
+    }
+  }
   // upload
   std::vector<char> tmp;
   auto upload_vals = [&](DevBuf& dst, const std::vector<double>& src) -> fkf_status {
@@ -539,6 +704,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   std::vector<char>().swap(tmp);
   h->ktot = ktot;  // the tensor-core upload sizes its per-slot scales by it
   if (h->prec == FKF_FP32) FKF_TRY(hmat_upload_tc(h, tu));
+  if (h->prec == FKF_FP64) FKF_TRY(hmat_upload_oz(h, ou));
   FKF_TRY(dev_upload(ctx, h->slotmap, smap.data(), smap.size() * sizeof(int64_t)));
   if (!p1.empty()) FKF_TRY(dev_upload(ctx, h->p1items, p1.data(), p1.size() * sizeof(P1Item)));
   if (!p1r.empty()) FKF_TRY(dev_upload(ctx, h->p1red, p1r.data(), p1r.size() * sizeof(P1Reduce)));
@@ -576,7 +742,9 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   in.operator_bytes = (fe + in.near_entries) * (int64_t)w;
   in.device_bytes = (int64_t)(h->fac.bytes + h->nearv.bytes + h->slotmap.bytes + h->p1items.bytes +
                               h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes + h->tca.bytes + h->tcp1.bytes +
-                              h->tctile.bytes + h->tcseg.bytes + h->tcred.bytes);
+                              h->tctile.bytes + h->tcseg.bytes + h->tcred.bytes + h->ozb.bytes + h->ozbdesc.bytes +
+                              h->ozitem.bytes + h->oztile.bytes + h->ozseg.bytes + h->ozx.bytes + h->ozz.bytes +
+                              h->ozpart.bytes);
   in.build_seconds = hh.build_seconds;
   return FKF_OK;
 }

@@ -1,0 +1,678 @@
+// H-apply of FP64 operators on the 5th-generation tensor cores (engine 3):
+// FP64 products assembled from exact products of small integer slices, the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump ("Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012), run as
+// FP16 MMAs whose FP32 sums stay exact.
+//
+// Slices.  Every value is first scaled by a power of two (exact) into
+// [-1, 1]: operator rows by a scale per row, vector columns by a scale per
+// column.  A value x in [-1, 1] is then
+//     x = sum_{i<7} d_i 2^(-7(i+1)) + r,   d_0 in [-128, 128], d_i in [-64, 64],
+// with d_i = rint(2^7 t_i), t_0 = x, t_{i+1} = 2^7 t_i - d_i and |r| <= 2^-50:
+// every d_i is an integer held exactly by FP16.  A dot product sum_k a_k b_k
+// of two such values is sum_{i,j} 2^(-7(i+j+2)) S_ij with integer
+// S_ij = sum_k d^a_{k,i} d^b_{k,j}.  The 28 products with i + j <= 6 are
+// kept (the dropped ones lie below 2^-56 of the scales); those of one weight
+// w = i + j accumulate in one FP32 TMEM accumulator.  Over a block of 512 K
+// (32 chunks of 16) every partial sum of weight w <= 5 is an integer of
+// magnitude <= 2^24, hence exact in FP32 (the MMA multiplies FP16 integers
+// exactly); weight 6 lies 2^-42 below weight 0, where FP32 rounding is far
+// below FP64's.  After each block the epilogue moves the sums of weights
+// 0..5 into one 64-bit integer accumulator per output (sum_w T_w 2^(7(5-w)),
+// below 2^58 per block) and weight 6 into an FP32 one, and frees TMEM for the
+// next block; at the end of a tile it combines them in FP64 with the scales.
+//
+// The products run in the tensor-core layout of happly_tc.cu, with the MMA
+// roles of its phase 1 in both phases: the vector operand (X or the slot
+// workspace; rows = 128 vector columns, K-major) is A, the operator (rows =
+// 64 slots in phase 1, 64 points of one leaf in phase 2) is B, so the
+// accumulator lanes are vector columns and every epilogue store is a row of
+// consecutive vector columns.
+//   phase 1  Z[n, g] = sum_{k in c} X[k, n] V[k, g]   for the slots g of a
+//            cluster c, written (sliced, over the bound tau_n Q_g, with Q_g
+//            >= the L1 norm of V's column) at the workspace position of the
+//            partner slot, or as FP64 partial rows when the cluster's rows
+//            are split over several leaf groups;
+//   phase 2  Y[i, n] = sum_{far} U[i, g] Q_g Z'[n, g] + sum_{near} G[i, k] X'[k, n]
+//            times tau_n and the row scale.
+// One persistent CTA per SM, warp-specialised as in happly_tc.cu: a
+// producer thread (two bulk copies per chunk), an MMA thread (28 MMAs per
+// chunk), eight epilogue warps (two per TMEM lane quarter, one per half of
+// the 64 operator rows).  Every mbarrier wait is bounded; an expired wait
+// sets a flag, every role unwinds and the host reports FKF_ETIMEOUT.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "common.h"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int kSl = 7;                   // slices per value
+constexpr int kW = 7;                    // weights w = i + j kept (0 .. 6)
+constexpr int kM = 128;                  // vector columns per tile (MMA M, TMEM lanes)
+constexpr int kN = 64;                   // operator rows per tile (MMA N)
+constexpr int kK = 16;                   // K per chunk = one kind::f16 MMA
+constexpr int kAPlane = kM * kK * 2;     // one slice plane of a vector chunk (4 KB)
+constexpr int kBPlane = kN * kK * 2;     // one slice plane of an operator chunk (2 KB)
+constexpr int kAChunk = kSl * kAPlane;   // 28 KB
+constexpr int kBChunk = kSl * kBPlane;   // 14 KB
+constexpr int kStage = kAChunk + kBChunk;
+constexpr int kStages = 4;
+constexpr int kKBlock = 32;              // chunks per exact block (512 K)
+constexpr uint32_t kSBO = 256;           // K-major FP16 core matrices: next 8-row group
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kQ = 8;
+constexpr uint32_t kTmemCols = 512;      // 7 weights x 64 columns used
+constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr uint32_t kIdesc = umma::idesc_f16(kM, kN);
+constexpr int FULL = 0, EMPTY = FULL + kStages, AF = EMPTY + kStages, AE = AF + 1, FIN = AE + 1, QF = FIN + 1,
+              QE = QF + kQ, NBAR = QE + kQ;
+constexpr int kBarBytes = 256;
+constexpr int kTail = 512;
+constexpr int kSmem = kStages * kStage + kTail;
+static_assert(NBAR * 8 <= kBarBytes, "barrier area");
+static_assert(kSmem <= 232448, "shared memory per CTA");
+
+struct OzQ {
+  int64_t id;   // tile index, -1: no more tiles
+  int32_t nch;  // K-chunks of the tile
+  int32_t pad;
+};
+
+struct OzSmem {
+  uint8_t* base;
+  uint64_t* bar;
+  uint32_t* tmem_slot;
+  int* fail;
+  OzQ* q;
+  uint32_t polls;
+  __device__ __forceinline__ uint8_t* a(int s) const { return base + s * kStage; }
+  __device__ __forceinline__ uint8_t* b(int s) const { return base + s * kStage + kAChunk; }
+  __device__ __forceinline__ bool failed() const { return *reinterpret_cast<volatile int*>(fail) != 0; }
+  __device__ __forceinline__ void set_fail() const { atomicExch(fail, 1); }
+};
+
+__device__ __forceinline__ bool wait_bar(const OzSmem& s, int i, uint32_t parity) {
+  if (umma::mbar_wait(&s.bar[i], parity, s.polls)) return true;
+  s.set_fail();
+  return false;
+}
+__device__ __forceinline__ bool wait_unwind(const OzSmem& s, int i, uint32_t parity) {
+  if (umma::mbar_wait(&s.bar[i], parity, kMaxPolls)) return true;
+  s.set_fail();
+  return false;
+}
+
+// byte offset of element (row, k) of one slice plane, K-major, no swizzle
+__device__ __forceinline__ uint32_t off16(int row, int k) {
+  return (uint32_t)((row >> 3) * kSBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// power of two >= |x| (1 for 0): the scale that maps a row or column into [-1, 1]
+__device__ __forceinline__ double pow2_ceil(double x) {
+  if (!(x > 0.0) || isinf(x)) return 1.0;
+  int e;
+  frexp(x, &e);  // x = f 2^e, f in [0.5, 1)
+  return ldexp(1.0, e);
+}
+
+// The seven slices of x in [-1, 1] as FP16 bit patterns.
+__device__ __forceinline__ void slice7(double x, uint16_t (&d)[kSl]) {
+#pragma unroll
+  for (int i = 0; i < kSl; i++) {
+    const double t = x * 128.0;
+    const double r = rint(t);
+    d[i] = __half_as_ushort(__double2half((float)r));
+    x = t - r;
+  }
+}
+
+// ---- work descriptions ----------------------------------------------------
+struct OzPh1 {
+  const OzItem* items;
+  const uint8_t* xs;  // sliced X of the pass
+  const uint8_t* ops; // sliced operator stream
+  uint8_t* zs;        // sliced slot workspace of the pass
+  double* part;       // FP64 partial rows (clusters over several leaf groups)
+  int64_t ldp;
+  const int64_t* slotpos;
+  const double* sig;  // per natural slot: row scale of its operator column
+  const double* qs;   // per natural slot: bound of its products
+  int nct, ncols;
+};
+
+struct OzPh2 {
+  const OzTile* tiles;
+  const OzSeg* segs;
+  const uint8_t* xs;
+  const uint8_t* zs;
+  const uint8_t* ops;
+  double* Y;
+  int64_t ldy;
+  const double* sig;  // per point
+  const double* tau;  // per column of the pass
+  int nct, ncols;
+};
+
+__device__ __forceinline__ int tile_nch(const OzPh1& p, int64_t w) { return p.items[w].nchunk; }
+__device__ __forceinline__ int tile_nch(const OzPh2& p, int64_t w) { return p.tiles[w].nchunk; }
+
+// ---- roles ----------------------------------------------------------------
+__device__ __forceinline__ bool next_tile(const OzSmem& s, int qi, int64_t& id, int& nch) {
+  const int slot = qi % kQ;
+  if (!wait_bar(s, QF + slot, (uint32_t)(qi / kQ) & 1)) return false;
+  volatile OzQ* e = &s.q[slot];
+  id = e->id;
+  nch = e->nch;
+  umma::mbar_arrive(&s.bar[QE + slot]);
+  return id >= 0;
+}
+
+// One chunk (vector chunk a, operator chunk b) into stage st of the g-th
+// chunk overall.  Returns false when the CTA failed.
+__device__ __forceinline__ bool load_chunk(const OzSmem& s, int64_t& g, const uint8_t* a, const uint8_t* b) {
+  const int st = (int)(g % kStages);
+  if (s.failed()) return false;
+  if (g >= kStages && !wait_bar(s, EMPTY + st, (uint32_t)((g / kStages) - 1) & 1)) return false;
+  umma::mbar_arrive_expect_tx(&s.bar[FULL + st], (uint32_t)kStage);
+  umma::bulk_g2s(s.a(st), a, (uint32_t)kAChunk, &s.bar[FULL + st]);
+  umma::bulk_g2s(s.b(st), b, (uint32_t)kBChunk, &s.bar[FULL + st]);
+  g++;
+  return true;
+}
+
+template <class Ph>
+__device__ __forceinline__ void producer(const OzSmem& s, const Ph& ph, int64_t ntiles, unsigned long long* counter,
+                                         int64_t& g) {
+  g = 0;
+  for (int qi = 0;; qi++) {
+    const int64_t raw = (int64_t)atomicAdd(counter, 1ull);
+    const int64_t id = raw < ntiles ? raw : -1;
+    const int64_t w = id >= 0 ? id / ph.nct : 0;
+    const int ct = id >= 0 ? (int)(id % ph.nct) : 0;
+    const int nch = id >= 0 ? tile_nch(ph, w) : 0;
+    const int slot = qi % kQ;
+    if (qi >= kQ && !wait_bar(s, QE + slot, (uint32_t)((qi / kQ) - 1) & 1)) return;
+    volatile OzQ* e = &s.q[slot];
+    e->id = id;
+    e->nch = nch;
+    umma::mbar_arrive(&s.bar[QF + slot]);
+    if (id < 0) return;
+    if constexpr (std::is_same<Ph, OzPh1>::value) {
+      const OzItem it = ph.items[w];
+      for (int c = 0; c < nch; c++)
+        if (!load_chunk(s, g, ph.xs + ((it.x_chunk0 + c) * ph.nct + ct) * (int64_t)kAChunk,
+                        ph.ops + (it.b_chunk0 + c) * (int64_t)kBChunk))
+          return;
+    } else {
+      const OzTile t = ph.tiles[w];
+      int64_t bc = t.b_chunk0;
+      for (int j = 0; j < t.nseg; j++) {
+        const OzSeg sg = ph.segs[t.seg0 + j];
+        const uint8_t* base = sg.near ? ph.xs : ph.zs;
+        for (int c = 0; c < sg.nch; c++, bc++)
+          if (!load_chunk(s, g, base + ((sg.a0 + c) * ph.nct + ct) * (int64_t)kAChunk,
+                          ph.ops + bc * (int64_t)kBChunk))
+            return;
+      }
+    }
+  }
+}
+
+// The 28 products of one chunk: weight w accumulates at TMEM column 64 w;
+// the first chunk of a block starts every weight afresh.
+__device__ __forceinline__ void issue_chunk(const uint8_t* a, const uint8_t* b, uint32_t tmem, bool first) {
+  const uint32_t a0 = umma::smem_u32(a), b0 = umma::smem_u32(b);
+#pragma unroll
+  for (int w = 0; w < kW; w++) {
+#pragma unroll
+    for (int i = 0; i <= w; i++) {
+      const int j = w - i;
+      const uint64_t ad = umma::smem_desc(a0 + (uint32_t)(i * kAPlane), kSBO);
+      const uint64_t bd = umma::smem_desc(b0 + (uint32_t)(j * kBPlane), kSBO);
+      umma::mma_f16(tmem + (uint32_t)(w * kN), ad, bd, kIdesc, (first && i == 0) ? 0u : 1u);
+    }
+  }
+}
+
+__device__ __forceinline__ void mma_issuer(const OzSmem& s, uint32_t tmem) {
+  int64_t g = 0;  // chunks consumed
+  int64_t fl = 0; // blocks handed to the epilogue
+  int tl = 0, nch = 0;
+  int64_t id;
+  bool ok = true;
+  for (; ok && next_tile(s, tl, id, nch); tl++) {
+    if (nch == 0) {  // nothing to multiply: the epilogue writes zeros
+      if (fl > 0 && !wait_bar(s, AE, (uint32_t)((fl - 1) & 1))) break;
+      umma::mbar_arrive(&s.bar[AF]);
+      fl++;
+      continue;
+    }
+    for (int c = 0; c < nch; c++) {
+      if (c % kKBlock == 0) {  // the epilogue has read the previous block's sums
+        if (fl > 0 && !wait_bar(s, AE, (uint32_t)((fl - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+      }
+      const int st = (int)(g % kStages);
+      if (s.failed() || !wait_bar(s, FULL + st, (uint32_t)(g / kStages) & 1)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      issue_chunk(s.a(st), s.b(st), tmem, c % kKBlock == 0);
+      umma::commit(&s.bar[EMPTY + st]);
+      g++;
+      if (c % kKBlock == kKBlock - 1 || c == nch - 1) {
+        umma::commit(&s.bar[AF]);
+        fl++;
+      }
+    }
+  }
+  // every MMA issued here has completed before TMEM is released
+  umma::commit(&s.bar[FIN]);
+  wait_unwind(s, FIN, 0);
+}
+
+// Epilogue: warp (quarter q, half h) owns TMEM lanes 32 q .. (vector columns
+// of the tile) and operator rows 32 h .. 32 h + 31 of every weight.
+template <class Ph>
+__device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t tmem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = (warp - 2) >> 2;
+  const int vcol = 32 * quarter + lane;  // vector column within the column tile
+  int64_t fl = 0;
+  int tl = 0, nch = 0;
+  int64_t id;
+  for (; next_tile(s, tl, id, nch); tl++) {
+    const int64_t w = id / ph.nct;
+    const int ct = (int)(id % ph.nct);
+    const int col = ct * kM + vcol;
+    // weights 0..5: exact integers, summed as sum_w T_w 2^(7(5-w)) in 64 bits
+    // (units of 2^-35; at most 2^58 per block); weight 6 in FP32 (units of 2^-42)
+    int64_t acc[32];
+    float acc6[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+      acc[i] = 0;
+      acc6[i] = 0.f;
+    }
+    const int nblk = nch > 0 ? (nch + kKBlock - 1) / kKBlock : 1;
+    bool ok = true;
+    for (int blk = 0; blk < nblk; blk++, fl++) {
+      if (!wait_bar(s, AF, (uint32_t)(fl & 1))) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      if (s.failed()) {
+        ok = false;
+        break;
+      }
+      if (nch > 0) {
+#pragma unroll
+        for (int wt = 0; wt < kW; wt++) {
+#pragma unroll
+          for (int hh = 0; hh < 2; hh++) {
+            float v[16];
+            umma::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(wt * kN + 32 * half + 16 * hh), v);
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              if (wt < kW - 1)
+                acc[16 * hh + i] += (int64_t)__float2int_rn(v[i]) << (7 * (kW - 2 - wt));
+              else
+                acc6[16 * hh + i] += v[i];
+            }
+          }
+        }
+      }
+      umma::fence_before_sync();
+      umma::mbar_arrive(&s.bar[AE]);
+    }
+    if (!ok) break;
+    if (col >= ph.ncols) continue;
+    if constexpr (std::is_same<Ph, OzPh2>::value) {
+      const OzTile t = ph.tiles[w];
+      const double sc = ph.tau[col] * 0x1p-14;
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const int n = 32 * half + i;
+        if (n < t.rows) {
+          const double r = (double)acc[i] * 0x1p-35 + (double)acc6[i] * 0x1p-42;
+          ph.Y[(t.row0 + n) * ph.ldy + col] = sc * ph.sig[t.row0 + n] * r;
+        }
+      }
+    } else {
+      const OzItem it = ph.items[w];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {  // aligned groups of 4 slots
+        const int n0 = 32 * half + 4 * u;
+        if (n0 >= it.nq) continue;
+        double z[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const int64_t g = it.map_off + n0 + e;
+          const double r = (double)acc[4 * u + e] * 0x1p-35 + (double)acc6[4 * u + e] * 0x1p-42;
+          z[e] = ph.sig[g] * 0x1p-14 * r;  // Z / tau_n
+          if (it.out_row < 0) z[e] /= ph.qs[g];
+        }
+        if (it.out_row >= 0) {
+#pragma unroll
+          for (int e = 0; e < 4; e++) ph.part[(it.out_row + n0 + e) * ph.ldp + col] = z[e];
+          continue;
+        }
+        const int64_t p = ph.slotpos[it.map_off + n0];  // 4 consecutive aligned positions
+        uint8_t* ch = ph.zs + ((p >> 4) * ph.nct + ct) * (int64_t)kAChunk + off16(vcol, (int)(p & 15));
+        // slice plane by plane (the same steps as slice7), 4 values at a time
+#pragma unroll
+        for (int i = 0; i < kSl; i++) {
+          uint32_t h[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const double t = z[e] * 128.0;
+            const double r = rint(t);
+            h[e] = __half_as_ushort(__double2half((float)r));
+            z[e] = t - r;
+          }
+          *reinterpret_cast<uint2*>(ch + i * kAPlane) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        }
+      }
+    }
+  }
+}
+
+template <class Ph>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_oz_apply(const Ph ph, int64_t ntiles, unsigned long long* __restrict__ counter, int* __restrict__ err,
+               uint32_t max_polls) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  OzSmem s;
+  s.base = smem_raw;
+  uint8_t* tail = smem_raw + kStages * kStage;
+  s.bar = reinterpret_cast<uint64_t*>(tail);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(tail + kBarBytes);
+  s.fail = reinterpret_cast<int*>(tail + kBarBytes + 8);
+  s.q = reinterpret_cast<OzQ*>(tail + kBarBytes + 16);
+  s.polls = max_polls;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int i = FULL; i < AF; i++) umma::mbar_init(&s.bar[i], 1);
+    umma::mbar_init(&s.bar[AF], 1);
+    umma::mbar_init(&s.bar[AE], 32 * kEpiWarps);
+    umma::mbar_init(&s.bar[FIN], 1);
+    for (int i = QF; i < QE; i++) umma::mbar_init(&s.bar[i], 1);
+    for (int i = QE; i < NBAR; i++) umma::mbar_init(&s.bar[i], 1 + 32 * kEpiWarps);
+    *s.fail = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 1) umma::tmem_alloc(s.tmem_slot, kTmemCols);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *s.tmem_slot;
+  if (warp == 0) {
+    if ((threadIdx.x & 31) == 0) {
+      int64_t g = 0;
+      producer<Ph>(s, ph, ntiles, counter, g);
+      // no exit (nor unwind) while a bulk copy into this CTA's shared memory is in flight
+      for (int64_t i = g > kStages ? g - kStages : 0; i < g; i++)
+        wait_unwind(s, FULL + (int)(i % kStages), (uint32_t)(i / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if ((threadIdx.x & 31) == 0) mma_issuer(s, tmem);
+    __syncwarp();
+  } else {
+    epilogue<Ph>(s, ph, tmem);
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0 && s.failed()) atomicExch(err, 1);
+  if (warp == 1) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---- slicing ----------------------------------------------------------------
+// Operator chunks: thread (row n, 8 k) of chunk c; 7 planes of 64 x 16.
+__global__ void __launch_bounds__(128) k_oz_build_b(const OzBChunk* __restrict__ d, int64_t n,
+                                                    const double* __restrict__ fac, const double* __restrict__ nearv,
+                                                    const double* __restrict__ sig_slot,
+                                                    const double* __restrict__ sig_pt,
+                                                    const double* __restrict__ q_pos, uint8_t* __restrict__ out) {
+  const int row = threadIdx.x & 63, kg = threadIdx.x >> 6;
+  for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+    const OzBChunk ch = d[c];
+    const double* src = ch.near ? nearv : fac;
+    const double rs = row < ch.rows ? 1.0 / (ch.phase == 1 ? sig_slot[ch.s_off + row] : sig_pt[ch.s_off + row]) : 0.0;
+    uint16_t sl[8][kSl];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int k = 8 * kg + u;
+      double x = 0.0;
+      if (row < ch.rows && k < ch.kv) {
+        x = src[ch.src_off + (int64_t)row * ch.si + (int64_t)k * ch.sk] * rs;
+        if (ch.k_off >= 0) x *= q_pos[ch.k_off + k];
+      }
+      slice7(x, sl[u]);
+    }
+    uint8_t* base = out + c * (int64_t)kBChunk + off16(row, 8 * kg);
+#pragma unroll
+    for (int i = 0; i < kSl; i++)
+      *reinterpret_cast<uint4*>(base + i * kBPlane) =
+          make_uint4((uint32_t)sl[0][i] | ((uint32_t)sl[1][i] << 16), (uint32_t)sl[2][i] | ((uint32_t)sl[3][i] << 16),
+                     (uint32_t)sl[4][i] | ((uint32_t)sl[5][i] << 16), (uint32_t)sl[6][i] | ((uint32_t)sl[7][i] << 16));
+  }
+}
+
+// Column maxima of |X| (bit patterns of non-negative doubles order like the values).
+__global__ void __launch_bounds__(256) k_oz_colmax(const double* __restrict__ X, int64_t ldx, int64_t rows, int ncols,
+                                                   int64_t rows_per_block, unsigned long long* __restrict__ cmax) {
+  const int col = blockIdx.x * 256 + threadIdx.x;
+  if (col >= ncols) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = min(rows, r0 + rows_per_block);
+  double m = 0.0;
+  for (int64_t r = r0; r < r1; r++) m = fmax(m, fabs(X[r * ldx + col]));
+  atomicMax(&cmax[col], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_oz_tau(const unsigned long long* __restrict__ cmax, int ncols, double* __restrict__ tau) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ncols) tau[j] = pow2_ceil(__longlong_as_double((long long)cmax[j]));
+}
+
+// Sliced X of one pass: chunk x (blockIdx.x) of 16 rows, column tile ct
+// (blockIdx.y) of 128 columns; thread (column n, 8 rows).
+__global__ void __launch_bounds__(256) k_oz_split_x(const double* __restrict__ X, int64_t ldx, int ncols,
+                                                    const TcXChunk* __restrict__ xmap, int nct,
+                                                    const double* __restrict__ tau, uint8_t* __restrict__ out) {
+  const TcXChunk xc = xmap[blockIdx.x];
+  const int ct = blockIdx.y;
+  const int n = threadIdx.x & 127, kg = threadIdx.x >> 7;
+  const int col = ct * kM + n;
+  const double inv = col < ncols ? 1.0 / tau[col] : 0.0;
+  uint16_t sl[8][kSl];
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const int k = 8 * kg + u;
+    const double x = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] * inv : 0.0;
+    slice7(x, sl[u]);
+  }
+  uint8_t* base = out + ((int64_t)blockIdx.x * nct + ct) * kAChunk + off16(n, 8 * kg);
+#pragma unroll
+  for (int i = 0; i < kSl; i++)
+    *reinterpret_cast<uint4*>(base + i * kAPlane) =
+        make_uint4((uint32_t)sl[0][i] | ((uint32_t)sl[1][i] << 16), (uint32_t)sl[2][i] | ((uint32_t)sl[3][i] << 16),
+                   (uint32_t)sl[4][i] | ((uint32_t)sl[5][i] << 16), (uint32_t)sl[6][i] | ((uint32_t)sl[7][i] << 16));
+}
+
+// Sum the FP64 partial rows of a cluster split over several leaf groups
+// (Z / tau, fixed order), divide by the slot bound and write the slices into
+// the workspace position of the partner slot.
+__global__ void k_oz_reduce(const P1Reduce* __restrict__ items, const double* __restrict__ part, int64_t ldp,
+                            const int64_t* __restrict__ slotpos, const double* __restrict__ qs, uint8_t* __restrict__ zs,
+                            int nct, int ncols) {
+  const P1Reduce it = items[blockIdx.x];
+  const int64_t total = (int64_t)it.nq * ncols;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total; e += (int64_t)blockDim.x * gridDim.y) {
+    const int q = (int)(e / ncols), n = (int)(e % ncols);
+    double acc = 0.0;
+    for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldp + n];
+    uint16_t d[kSl];
+    slice7(acc / qs[it.map_off + q], d);
+    const int64_t p = slotpos[it.map_off + q];
+    uint8_t* ch = zs + ((p >> 4) * nct + n / kM) * (int64_t)kAChunk + off16(n % kM, (int)(p & 15));
+#pragma unroll
+    for (int i = 0; i < kSl; i++) *reinterpret_cast<uint16_t*>(ch + i * kAPlane) = d[i];
+  }
+}
+
+fkf_status build_oz_stream(fkf_hmat* h) {
+  fkf_ctx* ctx = h->ctx;
+  if (h->n_ozb > 0) {
+    FKF_TRY(dev_alloc(ctx, h->ozb, (size_t)h->n_ozb * kBChunk));
+    const int grid = (int)std::min<int64_t>(h->n_ozb, 152 * 16);
+    k_oz_build_b<<<grid, 128, 0, ctx->stream>>>(h->ozbdesc.as<OzBChunk>(), h->n_ozb, h->fac.as<double>(),
+                                               h->nearv.as<double>(), h->oz_sigslot.as<double>(),
+                                               h->oz_sigpt.as<double>(), h->oz_qpos.as<double>(),
+                                               h->ozb.as<uint8_t>());
+    FKF_LAUNCHED(ctx);
+  }
+  h->ozb_built = true;
+  return FKF_OK;
+}
+
+}  // namespace
+
+fkf_status hmat_upload_oz(fkf_hmat* h, OzUpload& ou) {
+  fkf_ctx* ctx = h->ctx;
+  auto up = [&](DevBuf& b, const void* p, size_t bytes) -> fkf_status {
+    if (bytes == 0) return FKF_OK;
+    return dev_upload(ctx, b, p, bytes);
+  };
+  FKF_TRY(up(h->ozitem, ou.items.data(), ou.items.size() * sizeof(OzItem)));
+  FKF_TRY(up(h->ozred, ou.reduces.data(), ou.reduces.size() * sizeof(P1Reduce)));
+  FKF_TRY(up(h->oztile, ou.tiles.data(), ou.tiles.size() * sizeof(OzTile)));
+  FKF_TRY(up(h->ozseg, ou.segs.data(), ou.segs.size() * sizeof(OzSeg)));
+  FKF_TRY(up(h->ozbdesc, ou.bchunks.data(), ou.bchunks.size() * sizeof(OzBChunk)));
+  FKF_TRY(up(h->ozxmap, ou.xmap.data(), ou.xmap.size() * sizeof(TcXChunk)));
+  FKF_TRY(up(h->ozslot, ou.slotpos.data(), ou.slotpos.size() * sizeof(int64_t)));
+  FKF_TRY(up(h->oz_sigslot, ou.sig_slot.data(), ou.sig_slot.size() * sizeof(double)));
+  FKF_TRY(up(h->oz_qslot, ou.q_slot.data(), ou.q_slot.size() * sizeof(double)));
+  FKF_TRY(up(h->oz_qpos, ou.q_pos.data(), ou.q_pos.size() * sizeof(double)));
+  FKF_TRY(up(h->oz_sigpt, ou.sig_pt.data(), ou.sig_pt.size() * sizeof(double)));
+  h->n_ozitem = (int64_t)ou.items.size();
+  h->n_ozred = (int64_t)ou.reduces.size();
+  h->n_oztile = (int64_t)ou.tiles.size();
+  h->n_ozb = (int64_t)ou.bchunks.size();
+  h->n_ozx = (int64_t)ou.xmap.size();
+  h->n_ozz = ou.nz;
+  h->oz_part_rows = ou.part_rows;
+  // columns per pass: a multiple of 128 that keeps the sliced slot workspace under ~16 GB
+  int64_t panel = 1024;
+  while (panel > kM && (double)std::max<int64_t>(h->n_ozz, 1) * (panel / kM) * kAChunk > 16e9) panel /= 2;
+  h->oz_panel = panel;
+  h->ozb_built = false;  // the sliced stream is written when engine 3 is first selected
+  return FKF_OK;
+}
+
+fkf_status hmat_oz_check(fkf_hmat* h) {
+  if (!h->oz_err.p) return FKF_OK;
+  int e = 0;
+  FKF_CUDA(h->ctx, cudaMemcpyAsync(&e, h->oz_err.p, 4, cudaMemcpyDeviceToHost, h->ctx->stream));
+  FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  if (e) {
+    FKF_CUDA(h->ctx, cudaMemsetAsync(h->oz_err.p, 0, 4, h->ctx->stream));
+    return set_err(h->ctx, FKF_ETIMEOUT, "FP64 tensor-core H-apply: an mbarrier wait expired");
+  }
+  return FKF_OK;
+}
+
+fkf_status hmat_oz_prepare(fkf_hmat* h) {
+  if (h->prec != FKF_FP64) return set_err(h->ctx, FKF_EINVAL, "engine 3 needs an FP64 operator");
+  if (!h->ozb_built) FKF_TRY(build_oz_stream(h));
+  return FKF_OK;
+}
+
+fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                                   int64_t ncols) {
+  fkf_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  FKF_TRY(hmat_oz_prepare(h));
+  const int64_t P = h->oz_panel;
+  const int64_t nct_max = cdiv(std::min(ncols, P), kM);
+  if (h->ozx.bytes < (size_t)std::max<int64_t>(h->n_ozx, 1) * nct_max * kAChunk)
+    FKF_TRY(dev_alloc(ctx, h->ozx, (size_t)std::max<int64_t>(h->n_ozx, 1) * nct_max * kAChunk));
+  const size_t zbytes = (size_t)std::max<int64_t>(h->n_ozz, 1) * nct_max * kAChunk;
+  if (h->ozz.bytes < zbytes) {
+    // positions no product lands on (padding slots) are read as zeros
+    FKF_TRY(dev_alloc(ctx, h->ozz, zbytes));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->ozz.p, 0, h->ozz.bytes, st));
+  }
+  if (h->oz_part_rows > 0 && h->ozpart.bytes < (size_t)h->oz_part_rows * P * sizeof(double))
+    FKF_TRY(dev_alloc(ctx, h->ozpart, (size_t)h->oz_part_rows * P * sizeof(double)));
+  if (h->oz_col.bytes < (size_t)P * 16) FKF_TRY(dev_alloc(ctx, h->oz_col, (size_t)P * 16));
+  if (h->oz_err.bytes < 64) {
+    FKF_TRY(dev_alloc(ctx, h->oz_err, 64));
+    FKF_CUDA(ctx, cudaMemsetAsync(h->oz_err.p, 0, 64, st));
+  }
+  double* tau = h->oz_col.as<double>();
+  unsigned long long* cmax = reinterpret_cast<unsigned long long*>(tau + P);
+  unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->oz_err.as<char>() + 16);
+  int sms = 0;
+  FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_oz_apply<OzPh1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_oz_apply<OzPh2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  for (int64_t c0 = 0; c0 < ncols; c0 += P) {
+    const int nc = (int)std::min<int64_t>(P, ncols - c0);
+    const int nct = (int)cdiv(nc, kM);
+    FKF_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), st));
+    FKF_CUDA(ctx, cudaMemsetAsync(cmax, 0, (size_t)nc * sizeof(unsigned long long), st));
+    const int64_t rpb = 2048;
+    k_oz_colmax<<<dim3((unsigned)cdiv(nc, 256), (unsigned)cdiv(h->n, rpb)), 256, 0, st>>>(X + c0, ldx, h->n, nc, rpb,
+                                                                                       cmax);
+    FKF_LAUNCHED(ctx);
+    k_oz_tau<<<(unsigned)cdiv(nc, 256), 256, 0, st>>>(cmax, nc, tau);
+    FKF_LAUNCHED(ctx);
+    if (h->n_ozx > 0) {
+      k_oz_split_x<<<dim3((unsigned)h->n_ozx, (unsigned)nct), 256, 0, st>>>(X + c0, ldx, nc, h->ozxmap.as<TcXChunk>(),
+                                                                           nct, tau, h->ozx.as<uint8_t>());
+      FKF_LAUNCHED(ctx);
+    }
+    if (h->n_ozitem > 0) {
+      const OzPh1 p1{h->ozitem.as<OzItem>(), h->ozx.as<uint8_t>(), h->ozb.as<uint8_t>(), h->ozz.as<uint8_t>(),
+                     h->ozpart.as<double>(), P, h->ozslot.as<int64_t>(), h->oz_sigslot.as<double>(),
+                     h->oz_qslot.as<double>(), nct, nc};
+      const int64_t nt = h->n_ozitem * nct;
+      k_oz_apply<OzPh1><<<(unsigned)std::min<int64_t>(sms, nt), kThreads, kSmem, st>>>(p1, nt, counters,
+                                                                                      h->oz_err.as<int>(), h->tc_polls);
+      FKF_LAUNCHED(ctx);
+    }
+    if (h->n_ozred > 0) {
+      k_oz_reduce<<<dim3((unsigned)h->n_ozred, 4), 256, 0, st>>>(h->ozred.as<P1Reduce>(), h->ozpart.as<double>(), P,
+                                                                h->ozslot.as<int64_t>(), h->oz_qslot.as<double>(),
+                                                                h->ozz.as<uint8_t>(), nct, nc);
+      FKF_LAUNCHED(ctx);
+    }
+    if (ctx->ph2_mark && c0 + P >= ncols) {  // the last phase 2 of this apply starts here
+      FKF_CUDA(ctx, cudaEventRecord(ctx->ph2_mark, st));
+      ctx->ph2_marked = true;
+    }
+    const OzPh2 p2{h->oztile.as<OzTile>(), h->ozseg.as<OzSeg>(), h->ozx.as<uint8_t>(), h->ozz.as<uint8_t>(),
+                   h->ozb.as<uint8_t>(), Y + c0, ldy, h->oz_sigpt.as<double>(), tau, nct, nc};
+    const int64_t nt = h->n_oztile * nct;
+    k_oz_apply<OzPh2><<<(unsigned)std::min<int64_t>(sms, nt), kThreads, kSmem, st>>>(p2, nt, counters + 1,
+                                                                                    h->oz_err.as<int>(), h->tc_polls);
+    FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}

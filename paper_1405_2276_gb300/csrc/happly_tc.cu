@@ -1405,6 +1405,11 @@ fkf_status hmat_apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const 
 }
 
 fkf_status hmat_set_engine(fkf_hmat* h, int engine) {
+  if (engine == 3) {
+    FKF_TRY(hmat_oz_prepare(h));
+    h->engine = 3;
+    return FKF_OK;
+  }
   if (engine != 0 && h->tca_fmt != engine) FKF_TRY(build_stream(h, engine));
   h->engine = engine;
   return FKF_OK;
@@ -1590,6 +1595,7 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
 }
 
 fkf_status hmat_tc_check(fkf_hmat* h) {
+  if (h->prec == FKF_FP64) return hmat_oz_check(h);
   if (!h->tc_err.p) return FKF_OK;
   int e = 0;
   FKF_CUDA(h->ctx, cudaMemcpyAsync(&e, h->tc_err.p, 4, cudaMemcpyDeviceToHost, h->ctx->stream));
