@@ -274,6 +274,7 @@ struct OzUpload {
   std::vector<int64_t> slotpos;      // natural slot -> workspace position of its partner
   std::vector<double> sig_slot;      // per natural slot: power of two >= max |V| of its column
   std::vector<double> q_slot;        // per natural slot: power of two >= the column's L1 norm
+  std::vector<int32_t> q_shift;      // per natural slot: log2(q_slot / sig_slot) >= 0
   std::vector<double> q_pos;         // per workspace position: q_slot of the slot whose product lands there
   std::vector<double> sig_pt;        // per point: power of two >= max |phase-2 operator row element|
   int64_t nz = 0, part_rows = 0;
@@ -316,7 +317,7 @@ struct fkf_hmat {
                    // 3 = integer slices (FP64 operators)
   // engine 3 (FP64 operators): schedule, scales, sliced operator stream,
   // sliced X and slot workspace per column pass, FP64 partials
-  DevBuf ozitem, ozred, oztile, ozseg, ozbdesc, ozxmap, ozslot, oz_sigslot, oz_qslot, oz_qpos, oz_sigpt;
+  DevBuf ozitem, ozred, oztile, ozseg, ozbdesc, ozxmap, ozslot, oz_sigslot, oz_qslot, oz_qshift, oz_qpos, oz_sigpt;
   DevBuf ozb, ozx, ozz, ozpart, oz_col, oz_err;
   int64_t n_ozitem = 0, n_ozred = 0, n_oztile = 0, n_ozb = 0, n_ozx = 0, n_ozz = 0, oz_part_rows = 0;
   int64_t oz_panel = 0;

@@ -561,6 +561,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
     auto pow2ceil = [](double x) { return x > 0 ? std::ldexp(1.0, std::ilogb(x) + 1) : 1.0; };
     ou.sig_slot.assign(std::max<int64_t>(ktot, 1), 1.0);
     ou.q_slot.assign(std::max<int64_t>(ktot, 1), 1.0);
+    ou.q_shift.assign(std::max<int64_t>(ktot, 1), 0);
     for (int c = 0; c < nc; c++)
       for (int64_t q = 0; q < K[c]; q++) {
         double mx = 0, l1 = 0;
@@ -571,6 +572,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
         }
         ou.sig_slot[slot_base[c] + q] = pow2ceil(mx);
         ou.q_slot[slot_base[c] + q] = pow2ceil(l1);
+        ou.q_shift[slot_base[c] + q] = std::ilogb(ou.q_slot[slot_base[c] + q]) - std::ilogb(ou.sig_slot[slot_base[c] + q]);
       }
     ou.q_pos.assign((size_t)std::max<int64_t>(nz, 1) * 16, 1.0);
     for (int64_t g = 0; g < ktot; g++) ou.q_pos[ou.slotpos[g]] = ou.q_slot[g];

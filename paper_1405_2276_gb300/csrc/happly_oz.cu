@@ -8,9 +8,10 @@
 // Slices.  Every value is first scaled by a power of two (exact) into
 // [-1, 1]: operator rows by a scale per row, vector columns by a scale per
 // column.  A value x in [-1, 1] is then
-//     x = sum_{i<7} d_i 2^(-7(i+1)) + r,   d_0 in [-128, 128], d_i in [-64, 64],
-// with d_i = rint(2^7 t_i), t_0 = x, t_{i+1} = 2^7 t_i - d_i and |r| <= 2^-50:
-// every d_i is an integer held exactly by FP16.  A dot product sum_k a_k b_k
+//     x = sum_{i<7} d_i 2^(-7(i+1)) + r,   d_0 in [-128, 128], d_i in [-64, 63],
+// the balanced base-128 digits of the integer rint(2^49 x) (|r| <= 2^-50),
+// taken with integer operations: every d_i is an integer held exactly by
+// FP16.  A dot product sum_k a_k b_k
 // of two such values is sum_{i,j} 2^(-7(i+j+2)) S_ij with integer
 // S_ij = sum_k d^a_{k,i} d^b_{k,j}.  The 28 products with i + j <= 6 are
 // kept (the dropped ones lie below 2^-56 of the scales); those of one weight
@@ -122,15 +123,21 @@ __device__ __forceinline__ double pow2_ceil(double x) {
   return ldexp(1.0, e);
 }
 
-// The seven slices of x in [-1, 1] as FP16 bit patterns.
-__device__ __forceinline__ void slice7(double x, uint16_t (&d)[kSl]) {
+// x in [-1, 1] on the grid of the slices: rint(2^49 x) (the scaling by a
+// power of two is exact; one conversion).
+__device__ __forceinline__ int64_t grid49(double x) { return __double2ll_rn(x * 0x1p49); }
+
+// The seven slices of z = rint(2^49 x), |z| <= 2^49, as FP16 bit patterns:
+// balanced base-128 digits, z = sum_i d_i 128^(6-i), d_i in [-64, 63] for
+// i >= 1 and |d_0| <= 128 (integer operations only).
+__device__ __forceinline__ void digits7(int64_t z, uint16_t (&d)[kSl]) {
 #pragma unroll
-  for (int i = 0; i < kSl; i++) {
-    const double t = x * 128.0;
-    const double r = rint(t);
-    d[i] = __half_as_ushort(__double2half((float)r));
-    x = t - r;
+  for (int i = kSl - 1; i > 0; i--) {
+    const int64_t r = ((z + 64) & 127) - 64;
+    d[i] = __half_as_ushort(__int2half_rn((int)r));
+    z = (z - r) >> 7;
   }
+  d[0] = __half_as_ushort(__int2half_rn((int)z));
 }
 
 // ---- work descriptions ----------------------------------------------------
@@ -143,7 +150,7 @@ struct OzPh1 {
   int64_t ldp;
   const int64_t* slotpos;
   const double* sig;  // per natural slot: row scale of its operator column
-  const double* qs;   // per natural slot: bound of its products
+  const int32_t* qsh; // per natural slot: log2(bound of its products / sig)
   int nct, ncols;
 };
 
@@ -356,31 +363,34 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
       for (int u = 0; u < 8; u++) {  // aligned groups of 4 slots
         const int n0 = 32 * half + 4 * u;
         if (n0 >= it.nq) continue;
-        double z[4];
+        if (it.out_row >= 0) {  // FP64 partial rows: Z / tau_n
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const double r = (double)acc[4 * u + e] * 0x1p-35 + (double)acc6[4 * u + e] * 0x1p-42;
+            ph.part[(it.out_row + n0 + e) * ph.ldp + col] = ph.sig[it.map_off + n0 + e] * 0x1p-14 * r;
+          }
+          continue;
+        }
+        // Z / (tau_n Q_g) on the 2^-49 grid: (acc + acc6 / 2^7) / 2^s with
+        // s = log2(Q_g / sig_g) >= 0, in integers
+        int64_t z[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-          const int64_t g = it.map_off + n0 + e;
-          const double r = (double)acc[4 * u + e] * 0x1p-35 + (double)acc6[4 * u + e] * 0x1p-42;
-          z[e] = ph.sig[g] * 0x1p-14 * r;  // Z / tau_n
-          if (it.out_row < 0) z[e] /= ph.qs[g];
-        }
-        if (it.out_row >= 0) {
-#pragma unroll
-          for (int e = 0; e < 4; e++) ph.part[(it.out_row + n0 + e) * ph.ldp + col] = z[e];
-          continue;
+          const int sh = ph.qsh[it.map_off + n0 + e];
+          const int64_t t = acc[4 * u + e] + __float2ll_rn(acc6[4 * u + e] * 0.0078125f);
+          z[e] = sh > 0 ? (t + (int64_t(1) << (sh - 1))) >> sh : t;
         }
         const int64_t p = ph.slotpos[it.map_off + n0];  // 4 consecutive aligned positions
         uint8_t* ch = ph.zs + ((p >> 4) * ph.nct + ct) * (int64_t)kAChunk + off16(vcol, (int)(p & 15));
-        // slice plane by plane (the same steps as slice7), 4 values at a time
+        // balanced base-128 digits (as digits7), plane by plane, least significant first
 #pragma unroll
-        for (int i = 0; i < kSl; i++) {
+        for (int i = kSl - 1; i >= 0; i--) {
           uint32_t h[4];
 #pragma unroll
           for (int e = 0; e < 4; e++) {
-            const double t = z[e] * 128.0;
-            const double r = rint(t);
-            h[e] = __half_as_ushort(__double2half((float)r));
-            z[e] = t - r;
+            const int64_t r = i > 0 ? ((z[e] + 64) & 127) - 64 : z[e];
+            h[e] = __half_as_ushort(__int2half_rn((int)r));
+            z[e] = (z[e] - r) >> 7;
           }
           *reinterpret_cast<uint2*>(ch + i * kAPlane) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
         }
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(128) k_oz_build_b(const OzBChunk* __restrict__
         x = src[ch.src_off + (int64_t)row * ch.si + (int64_t)k * ch.sk] * rs;
         if (ch.k_off >= 0) x *= q_pos[ch.k_off + k];
       }
-      slice7(x, sl[u]);
+      digits7(grid49(x), sl[u]);
     }
     uint8_t* base = out + c * (int64_t)kBChunk + off16(row, 8 * kg);
 #pragma unroll
@@ -499,13 +509,13 @@ __global__ void __launch_bounds__(256) k_oz_split_x(const double* __restrict__ X
   const int ct = blockIdx.y;
   const int n = threadIdx.x & 127, kg = threadIdx.x >> 7;
   const int col = ct * kM + n;
-  const double inv = col < ncols ? 1.0 / tau[col] : 0.0;
+  const double sc = col < ncols ? 0x1p49 / tau[col] : 0.0;  // a power of two
   uint16_t sl[8][kSl];
 #pragma unroll
   for (int u = 0; u < 8; u++) {
     const int k = 8 * kg + u;
-    const double x = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] * inv : 0.0;
-    slice7(x, sl[u]);
+    const double x = (k < xc.rows && col < ncols) ? X[(xc.row0 + k) * ldx + col] * sc : 0.0;
+    digits7(__double2ll_rn(x), sl[u]);
   }
   uint8_t* base = out + ((int64_t)blockIdx.x * nct + ct) * kAChunk + off16(n, 8 * kg);
 #pragma unroll
@@ -528,7 +538,7 @@ __global__ void k_oz_reduce(const P1Reduce* __restrict__ items, const double* __
     double acc = 0.0;
     for (int c = 0; c < it.nch; c++) acc += part[(it.part_row + (int64_t)c * it.nq + q) * ldp + n];
     uint16_t d[kSl];
-    slice7(acc / qs[it.map_off + q], d);
+    digits7(grid49(acc / qs[it.map_off + q]), d);
     const int64_t p = slotpos[it.map_off + q];
     uint8_t* ch = zs + ((p >> 4) * nct + n / kM) * (int64_t)kAChunk + off16(n % kM, (int)(p & 15));
 #pragma unroll
@@ -568,6 +578,7 @@ fkf_status hmat_upload_oz(fkf_hmat* h, OzUpload& ou) {
   FKF_TRY(up(h->ozslot, ou.slotpos.data(), ou.slotpos.size() * sizeof(int64_t)));
   FKF_TRY(up(h->oz_sigslot, ou.sig_slot.data(), ou.sig_slot.size() * sizeof(double)));
   FKF_TRY(up(h->oz_qslot, ou.q_slot.data(), ou.q_slot.size() * sizeof(double)));
+  FKF_TRY(up(h->oz_qshift, ou.q_shift.data(), ou.q_shift.size() * sizeof(int32_t)));
   FKF_TRY(up(h->oz_qpos, ou.q_pos.data(), ou.q_pos.size() * sizeof(double)));
   FKF_TRY(up(h->oz_sigpt, ou.sig_pt.data(), ou.sig_pt.size() * sizeof(double)));
   h->n_ozitem = (int64_t)ou.items.size();
@@ -651,7 +662,7 @@ fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, do
     if (h->n_ozitem > 0) {
       const OzPh1 p1{h->ozitem.as<OzItem>(), h->ozx.as<uint8_t>(), h->ozb.as<uint8_t>(), h->ozz.as<uint8_t>(),
                      h->ozpart.as<double>(), P, h->ozslot.as<int64_t>(), h->oz_sigslot.as<double>(),
-                     h->oz_qslot.as<double>(), nct, nc};
+                     h->oz_qshift.as<int32_t>(), nct, nc};
       const int64_t nt = h->n_ozitem * nct;
       k_oz_apply<OzPh1><<<(unsigned)std::min<int64_t>(sms, nt), kThreads, kSmem, st>>>(p1, nt, counters,
                                                                                       h->oz_err.as<int>(), h->tc_polls);
