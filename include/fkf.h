@@ -178,10 +178,11 @@ fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t l
  *
  * Same arguments and layout as fkf_hmatrix_apply_clustered (X, Y in cluster
  * order, row-major, precision's element type; the caller passes and owns
- * both), and the same product: for an FP64 operator the same result up to
- * summation order; an FP32 operator always runs the FP32 SIMT tile engine here,
- * whatever fkf_hmatrix_set_engine chose, so against the default tensor-core
- * apply it agrees to FP32 rounding (about 1e-5 relative).  The slot workspace and the split-reduction partials live in a
+ * both), and the same product: an FP64 operator always runs the FP64 SIMT
+ * tile engine here (the same result as engine 0 up to summation order; against
+ * engine 3 about 1e-13 relative); an FP32 operator always runs the FP32 SIMT
+ * tile engine here, whatever fkf_hmatrix_set_engine chose, so against the
+ * default tensor-core apply it agrees to FP32 rounding (about 1e-5 relative).  The slot workspace and the split-reduction partials live in a
  * library-wide static device array of FKF_NOALLOC_SCRATCH_BYTES bytes; the
  * columns are processed in panels as wide as that array allows (at least one
  * column).  An operator that needs more than FKF_NOALLOC_SCRATCH_BYTES for a
@@ -214,16 +215,25 @@ fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, i
  * ETIMEOUT (a tensor-core wait expired). */
 fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t rows, int32_t K, const float* E_dev,
                           int64_t lde, int64_t ke, int32_t ncols, float* C_dev, int64_t ldc);
-/* Engine of the H-apply for an FP32 operator: 2 (default) = 5th-generation
- * tensor cores, tcgen05.mma kind::f16 with a two-term FP16 split of
- * power-of-two scaled operands (hi*hi + hi*lo + lo*hi at twice the TF32
- * rate; scales per slot, point and X column keep FP32-level accuracy);
- * 1 = tensor cores, kind::tf32 with a 3xTF32 split; both accumulate in FP32
- * in TMEM.  0 = the FP32 SIMT tile engine.  FP64 operators always use the FP64
- * SIMT engine.  Selecting another tensor-core format rewrites the operator's
- * split stream (device work, synchronous).  Errors: EINVAL (engine not 0-2,
- * or 1-2 for an FP64 operator).  A tensor-core wait that expires makes the
- * apply (or the filter step) return FKF_ETIMEOUT. */
+/* Engine of the H-apply (the product with Gamma_H of Sec. 2.2.1).
+ * FP32 operators: 2 (default) = 5th-generation tensor cores, tcgen05.mma
+ * kind::f16 with a two-term FP16 split of power-of-two scaled operands
+ * (hi*hi + hi*lo + lo*hi at twice the TF32 rate; scales per slot, point and X
+ * column keep FP32-level accuracy); 1 = tensor cores, kind::tf32 with a
+ * 3xTF32 split; both accumulate in FP32 in TMEM; 0 = the FP32 SIMT tile
+ * engine.  FP64 operators: 0 (default) = the FP64 SIMT tile engine (exact
+ * FP64 arithmetic); 3 = tensor cores with FP64 products assembled from seven
+ * 7-bit integer slices of every value (Ozaki's error-free splitting; FP16
+ * MMAs whose FP32 sums stay exact over blocks of 512 K, 64-bit integer
+ * accumulation between blocks): every value keeps 49 bits relative to its row
+ * or column scale and the slot products 49 bits relative to their L1 bound,
+ * about 1e-13 of max |Y| on random vectors.  Selecting engine 1-3 rewrites
+ * the operator's split (sliced) stream when it is not there yet (device
+ * work, synchronous; engine 3 adds about 14 bytes per stored operator entry
+ * and a sliced slot workspace of 14 bytes per slot and column).  Errors:
+ * EINVAL (engine not 0-3, 1-2 for an FP64 operator, 3 for an FP32 one),
+ * ENOMEM.  A tensor-core wait that expires makes the apply (or the filter
+ * step) return FKF_ETIMEOUT. */
 fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
 /* Poll limit of the tensor-core H-apply's pipeline waits (producer -> MMA ->
  * epilogue mbarrier hand-offs inside a CTA).  A wait that is not satisfied

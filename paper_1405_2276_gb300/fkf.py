@@ -243,7 +243,8 @@ def fkf_rotate_f32(ctx, A, E, C, K=None, ncols=None):
 
 def fkf_hmatrix_set_engine(h, engine: int) -> None:
     """FP32 operators: 2 = tensor cores with scaled 2xFP16 (default), 1 = tensor
-    cores with 3xTF32, 0 = SIMT tile engine."""
+    cores with 3xTF32, 0 = SIMT tile engine.  FP64 operators: 0 = FP64 SIMT
+    tile engine (default), 3 = tensor cores with 7-bit integer slices."""
     _check(_lib.fkf_hmatrix_set_engine(h.ptr, engine), h.ctx)
 
 
