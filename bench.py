@@ -527,6 +527,8 @@ def batch_bench(nb, steps, warmup, mem_reserve_gb=16.0):
         ctx = fkf.fkf_create(0)
         hm = fkf.fkf_hmatrix_build(ctx, wl["points"], nu, ell, 1.0, leaf=64, eta=1.0, aca_tol=1e-8, k_cap=32,
                                    precision=fkf.FKF_FP32)
+        # the batch runs on the tensor-core engine only: the FP32 value copies are not kept
+        fkf.fkf_hmatrix_release_values(hm)
         m = wl["H"].nrows
         # a fixed geometry keeps the rank at m: r_max = m bounds the state's memory
         f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, m, m)

@@ -100,7 +100,7 @@ typedef struct {
   int64_t near_entries;   /* sum over near blocks of |t||s| (stored once) */
   int64_t max_rank;
   double mean_rank;
-  int64_t device_bytes;   /* device memory held by the operator */
+  int64_t device_bytes;   /* device memory the operator holds now (values, schedules, streams, apply workspaces) */
   int64_t flops_per_col;  /* 2 * (entries of Gamma_H used per apply column) */
   int64_t bytes_per_col;  /* algorithmic bytes per apply column besides the operator (read X, write Y) */
   int64_t operator_bytes; /* algorithmic operator bytes read per apply panel */
@@ -246,6 +246,15 @@ fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine);
  * once (the way to exercise the time-out path).  Errors: EINVAL (polls >
  * 2^32 - 1). */
 fkf_status fkf_hmatrix_set_wait_limit(fkf_hmat* h, int64_t polls);
+/* Frees the device copy of an FP32 operator's factor and near-block values
+ * (FP32, about 4 bytes per stored entry), keeping only the split stream that
+ * the tensor-core engine in use (1 or 2) reads, for batches of filters that
+ * must fit many operators in device memory.  Irreversible: afterwards the
+ * SIMT engine, fkf_hmatrix_apply_clustered_noalloc and switching the engine
+ * return FKF_ESTATE; applies, steps and densify on the current engine work
+ * as before (the same results).  Errors: EINVAL (null), ESTATE (an FP64
+ * operator, or engine 0). */
+fkf_status fkf_hmatrix_release_values(fkf_hmat* h);
 /* Current engine of the H-apply (see fkf_hmatrix_set_engine).  Errors: EINVAL (null). */
 fkf_status fkf_hmatrix_get_engine(const fkf_hmat* h, int32_t* engine);
 /* Autotuner of the tensor-core pipeline shape (engine 2): times the FP16

@@ -192,6 +192,7 @@ FKF_API fkf_status fkf_hmatrix_build(fkf_ctx* ctx, const double* points, int64_t
 FKF_API fkf_status fkf_hmatrix_info(const fkf_hmat* h, fkf_hmat_info* info) {
   if (!h || !info) return FKF_EINVAL;
   *info = h->info;
+  info->device_bytes = hmat_device_bytes(h);
   return FKF_OK;
 }
 
@@ -233,8 +234,22 @@ FKF_API fkf_status fkf_hmatrix_autotune(fkf_hmat* h, int64_t ncols, int32_t* var
   return FKF_OK;
 }
 
+FKF_API fkf_status fkf_hmatrix_release_values(fkf_hmat* h) {
+  if (!h) return FKF_EINVAL;
+  if (h->prec != FKF_FP32 || (h->engine != 1 && h->engine != 2))
+    return set_err(h->ctx, FKF_ESTATE, "release_values: an FP32 operator on a tensor-core engine (1, 2) is required");
+  if (h->tca_fmt != h->engine) FKF_TRY(hmat_set_engine(h, h->engine));  // the stream the engine reads
+  FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  h->fac.release();
+  h->nearv.release();
+  h->values_released = true;
+  return FKF_OK;
+}
+
 FKF_API fkf_status fkf_hmatrix_set_engine(fkf_hmat* h, int32_t engine) {
   if (!h) return FKF_EINVAL;
+  if (h->values_released && engine != h->engine)
+    return set_err(h->ctx, FKF_ESTATE, "set_engine: the operator's values were released");
   if (engine < 0 || engine > 3) return set_err(h->ctx, FKF_EINVAL, "set_engine: engine must be 0, 1, 2 or 3");
   if ((engine == 1 || engine == 2) && h->prec != FKF_FP32)
     return set_err(h->ctx, FKF_EINVAL, "set_engine: engines 1 and 2 need an FP32 operator");
@@ -248,6 +263,8 @@ FKF_API fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* 
                                                        int64_t ldy, int64_t ncols) {
   if (!h) return FKF_EINVAL;
   FKF_TRY(check_apply_args(h, X_dev, ldx, Y_dev, ldy, ncols));
+  if (h->values_released)
+    return set_err(h->ctx, FKF_ESTATE, "apply_noalloc: the operator's values were released");
   FKF_TRY(hmat_apply_clustered_noalloc(h, X_dev, ldx, Y_dev, ldy, ncols));
   FKF_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
   return FKF_OK;
@@ -436,7 +453,7 @@ struct ApplyBatch {
   std::vector<Req> reqs;
   std::vector<cudaEvent_t> evs;  // one per step (ready) + done
   cudaEvent_t done = nullptr;
-  bool merged = false;
+  std::vector<bool> merged_req;  // per request: its apply ran in the merged launch
 
   // with mu held, once every step has registered or withdrawn
   void run() {
@@ -456,25 +473,60 @@ struct ApplyBatch {
       ldy.push_back(r.ldy);
       nc.push_back(r.ncols);
     }
-    merged = hmat_tc_multi_ok(hs.data(), (int)hs.size(), nc.data());
+    // the requests that fit one merged launch with the first one (same tensor-core format,
+    // pipeline shape and device, one column pass each); the others are applied one by one
+    // (the largest such group, whatever order the requests arrived in)
+    merged_req.assign(reqs.size(), false);
+    std::vector<size_t> idx;
+    for (size_t k = 0; k < reqs.size(); k++) {
+      if (!hmat_tc_multi_ok(&hs[k], 1, &nc[k])) continue;
+      std::vector<size_t> g{k};
+      for (size_t i = 0; i < reqs.size(); i++) {
+        if (i == k) continue;
+        fkf_hmat* pair[2] = {hs[k], hs[i]};
+        const int64_t pnc[2] = {nc[k], nc[i]};
+        if (hmat_tc_multi_ok(pair, 2, pnc)) g.push_back(i);
+      }
+      if (g.size() > idx.size()) idx.swap(g);
+    }
+    std::sort(idx.begin(), idx.end());
     fkf_status st = FKF_OK;
-    if (merged) {
-      fkf_ctx* lctx = reqs[0].h->ctx;
+    if (idx.size() > 1) {
+      std::vector<fkf_hmat*> mh;
+      std::vector<const float*> mX;
+      std::vector<float*> mY;
+      std::vector<int64_t> mldx, mldy, mnc;
+      for (size_t i : idx) {
+        mh.push_back(hs[i]);
+        mX.push_back(X[i]);
+        mY.push_back(Y[i]);
+        mldx.push_back(ldx[i]);
+        mldy.push_back(ldy[i]);
+        mnc.push_back(nc[i]);
+      }
+      fkf_ctx* lctx = reqs[idx[0]].h->ctx;
       if (cudaSetDevice(lctx->device) != cudaSuccess) st = set_err(lctx, FKF_ECUDA, "cudaSetDevice failed");
-      for (const Req& r : reqs)
-        if (st == FKF_OK && cudaStreamWaitEvent(lctx->stream, r.ready, 0) != cudaSuccess)
+      for (size_t i : idx)
+        if (st == FKF_OK && cudaStreamWaitEvent(lctx->stream, reqs[i].ready, 0) != cudaSuccess)
           st = set_err(lctx, FKF_ECUDA, "batched apply: stream wait failed");
       if (st == FKF_OK)
-        st = hmat_apply_tc_multi(lctx, hs.data(), (int)hs.size(), X.data(), ldx.data(), Y.data(), ldy.data(),
-                                 nc.data());
+        st = hmat_apply_tc_multi(lctx, mh.data(), (int)mh.size(), mX.data(), mldx.data(), mY.data(), mldy.data(),
+                                 mnc.data());
       if (st == FKF_OK && cudaEventRecord(done, lctx->stream) != cudaSuccess)
         st = set_err(lctx, FKF_ECUDA, "batched apply: event record failed");
-    } else {
-      for (const Req& r : reqs)
-        if (st == FKF_OK) st = hmat_apply_clustered(r.h, r.X, r.ldx, r.Y, r.ldy, r.ncols);
+      for (size_t i : idx) merged_req[i] = true;
     }
+    for (size_t i = 0; i < reqs.size(); i++)
+      if (st == FKF_OK && !merged_req[i])
+        st = hmat_apply_clustered(reqs[i].h, reqs[i].X, reqs[i].ldx, reqs[i].Y, reqs[i].ldy, reqs[i].ncols);
     status = st;
     finished = true;
+  }
+
+  bool merged_of(fkf_hmat* h) const {
+    for (size_t i = 0; i < reqs.size(); i++)
+      if (reqs[i].h == h) return merged_req[i];
+    return false;
   }
 
   fkf_status apply(const Req& req) {
@@ -502,6 +554,7 @@ struct ApplyBatch {
 thread_local ApplyBatch* tls_batch = nullptr;
 thread_local int tls_batch_index = -1;
 thread_local bool tls_batch_arrived = false;
+thread_local fkf_hmat* tls_batch_h = nullptr;  // the operator of this thread's batched apply
 }  // namespace
 
 fkf_status hmat_apply_step(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols) {
@@ -509,13 +562,14 @@ fkf_status hmat_apply_step(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int
   if (!b || tls_batch_arrived || h->prec != FKF_FP32 || h->engine == 0)
     return hmat_apply_clustered(h, X, ldx, Y, ldy, ncols);
   tls_batch_arrived = true;
+  tls_batch_h = h;
   fkf_ctx* ctx = h->ctx;
   const cudaEvent_t ready = b->evs[tls_batch_index];
   FKF_CUDA(ctx, cudaEventRecord(ready, ctx->stream));
   const fkf_status st =
       b->apply({h, static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, ncols, ready});
   if (st != FKF_OK) return set_err(ctx, st, "batched H-apply failed");
-  if (b->merged) FKF_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, b->done, 0));
+  if (b->merged_of(h)) FKF_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, b->done, 0));
   return FKF_OK;
 }
 
@@ -545,12 +599,13 @@ FKF_API fkf_status fkf_filter_step_batched(fkf_step_desc* descs, int32_t nb, int
     tls_batch = &batch;
     tls_batch_index = i;
     tls_batch_arrived = false;
+    tls_batch_h = nullptr;
     fkf_status st = FKF_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) st = set_err(ctx, FKF_ECUDA, "cudaSetDevice failed");
     if (st == FKF_OK)
       st = fkf_filter_step(d.filter, d.y, d.m, d.H_rowptr, d.H_col, d.H_val, d.R, d.r_scalar, flags, &d.nll);
     if (!tls_batch_arrived) batch.withdraw();
-    d.merged = tls_batch_arrived && batch.merged ? 1 : 0;
+    d.merged = tls_batch_arrived && batch.merged_of(tls_batch_h) ? 1 : 0;
     tls_batch = nullptr;
     d.status = st;
   };

@@ -322,6 +322,7 @@ struct fkf_hmat {
   int64_t n_ozitem = 0, n_ozred = 0, n_oztile = 0, n_ozb = 0, n_ozx = 0, n_ozz = 0, oz_part_rows = 0;
   int64_t oz_panel = 0;
   bool ozb_built = false;
+  bool values_released = false;  // FP32 factor/near values freed (fkf_hmatrix_release_values)
   // workspace
   DevBuf zmix, part, xperm, yperm;
   int64_t panel = 256;
@@ -329,6 +330,7 @@ struct fkf_hmat {
 
 // happly.cu
 fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh);
+int64_t hmat_device_bytes(const fkf_hmat* h);
 fkf_status hmat_apply_clustered(fkf_hmat* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t ncols);
 // <A, B> = sum_ij A_ij B_ij over nrows x ncols blocks of the operator's
 // element type (FP64 accumulation, fixed order; synchronises).

@@ -235,6 +235,21 @@ fkf_status hmat_permute_rows_f64(fkf_ctx* ctx, const double* src, int64_t lds, c
   return permute_rows<double>(ctx, src, lds, idx_dev, dst, ldd, nrows, ncols);
 }
 
+// Device memory the operator holds now (values, schedules, streams and the
+// apply workspaces allocated so far).
+int64_t hmat_device_bytes(const fkf_hmat* h) {
+  const DevBuf* bufs[] = {&h->fac,    &h->nearv,   &h->slotmap, &h->p1items, &h->p1red,  &h->p2seg,  &h->p2leaf,
+                          &h->perm_d, &h->iperm_d, &h->tcp1,    &h->tcred,   &h->tctile, &h->tcseg,  &h->tc_err,
+                          &h->tca,    &h->tcadesc, &h->tcxmap,  &h->tcslot,  &h->xsplit, &h->zsplit, &h->tc_qslot,
+                          &h->tc_qpos, &h->tc_rpt, &h->tc_col,  &h->ozitem,  &h->ozred,  &h->oztile, &h->ozseg,
+                          &h->ozbdesc, &h->ozxmap, &h->ozslot,  &h->oz_sigslot, &h->oz_qslot, &h->oz_qshift,
+                          &h->oz_qpos, &h->oz_sigpt, &h->ozb,   &h->ozx,     &h->ozz,    &h->ozpart, &h->oz_col,
+                          &h->oz_err,  &h->zmix,   &h->part,    &h->xperm,   &h->yperm};
+  int64_t t = 0;
+  for (const DevBuf* b : bufs) t += (int64_t)b->bytes;
+  return t;
+}
+
 // Lay the host build out as flat device arrays and work lists.
 fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   fkf_ctx* ctx = h->ctx;
@@ -742,11 +757,7 @@ fkf_status hmat_upload(fkf_hmat* h, const HostHmat& hh) {
   in.flops_per_col = 2 * (2 * fe + near_used);
   in.bytes_per_col = 2 * hh.n * (int64_t)w;
   in.operator_bytes = (fe + in.near_entries) * (int64_t)w;
-  in.device_bytes = (int64_t)(h->fac.bytes + h->nearv.bytes + h->slotmap.bytes + h->p1items.bytes +
-                              h->p1red.bytes + h->p2seg.bytes + h->p2leaf.bytes + h->tca.bytes + h->tcp1.bytes +
-                              h->tctile.bytes + h->tcseg.bytes + h->tcred.bytes + h->ozb.bytes + h->ozbdesc.bytes +
-                              h->ozitem.bytes + h->oztile.bytes + h->ozseg.bytes + h->ozx.bytes + h->ozz.bytes +
-                              h->ozpart.bytes);
+  in.device_bytes = hmat_device_bytes(h);
   in.build_seconds = hh.build_seconds;
   return FKF_OK;
 }

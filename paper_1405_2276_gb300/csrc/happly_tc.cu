@@ -1580,9 +1580,10 @@ fkf_status hmat_upload_tc(fkf_hmat* h, TcUpload& tu) {
   h->n_tcx = (int64_t)tu.xmap.size();
   h->n_tcz = tu.nz;
   h->tc_part_rows = tu.part_rows;
-  // columns per pass: keep the split slot workspace under ~24 GB
+  // columns per pass: keep the split slot workspace (FP16 format, the default
+  // engine's) under ~24 GB
   int64_t panel = 1024;
-  while (panel > kN && (double)h->n_tcz * (panel / kN) * Geo<1>::kBChunk > 24e9) panel /= 2;
+  while (panel > kN && (double)h->n_tcz * (panel / kN) * Geo<2>::kBChunk > 24e9) panel /= 2;
   h->tc_panel = panel;
   h->n_tca = (int64_t)ch.size();
   // the stream is sized for the format it holds (build_stream grows it for

@@ -119,6 +119,7 @@ _sigs = {
     "fkf_hmatrix_set_wait_limit": (C.c_int, [_P, C.c_int64]),
     "fkf_eigh": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32]),
     "fkf_hmatrix_get_engine": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "fkf_hmatrix_release_values": (C.c_int, [_P]),
     "fkf_hmatrix_autotune": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -268,6 +269,11 @@ def fkf_eigh(ctx, A, w, want=None) -> None:
 
 def fkf_hmatrix_set_wait_limit(h, polls: int) -> None:
     _check(_lib.fkf_hmatrix_set_wait_limit(h.ptr, int(polls)), h.ctx)
+
+
+def fkf_hmatrix_release_values(h) -> None:
+    """Free the FP32 operator's device value copies (keeps the tensor-core stream)."""
+    _check(_lib.fkf_hmatrix_release_values(h.ptr), h.ctx)
 
 
 def fkf_hmatrix_get_engine(h) -> int:

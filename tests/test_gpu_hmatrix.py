@@ -150,8 +150,8 @@ def test_invalid_arguments(fkf, ctx):
     for engine in (1, 2):  # tensor-core engines need an FP32 operator
         with pytest.raises(fkf.FkfError):
             fkf.fkf_hmatrix_set_engine(hm, engine)
-    with pytest.raises(fkf.FkfError):
-        fkf.fkf_hmatrix_set_engine(hm, 3)
+    with pytest.raises(fkf.FkfError):  # no engine 4
+        fkf.fkf_hmatrix_set_engine(hm, 4)
     fkf.fkf_hmatrix_destroy(hm)
 
 
@@ -259,3 +259,32 @@ def test_autotune_keeps_results(fkf, ctx):
     fkf.fkf_hmatrix_set_engine(hm, 1)
     assert fkf.fkf_hmatrix_autotune(hm, 300) == (v, 0.0)  # nothing to tune on engine 1
     fkf.fkf_hmatrix_destroy(hm)
+
+
+def test_release_values_keeps_tensor_core_results(fkf, ctx):
+    """fkf_hmatrix_release_values frees the FP32 value copies: the tensor-core
+    apply gives bitwise the same result, the paths that read the values refuse."""
+    import torch
+
+    pts = synth.grid_points_2d(48, 40)
+    n = pts.shape[0]
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.15, 1.0, leaf=32, eta=1.0, aca_tol=1e-8, precision=fkf.FKF_FP32)
+    X = torch.from_numpy(np.random.default_rng(3).standard_normal((n, 70))).float().cuda()
+    Y0 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply(hm, X, Y0)
+    before = fkf.fkf_hmatrix_info(hm)["device_bytes"]  # the apply's workspaces included
+    fkf.fkf_hmatrix_release_values(hm)
+    assert fkf.fkf_hmatrix_info(hm)["device_bytes"] < before
+    Y1 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply(hm, X, Y1)
+    assert torch.equal(Y0, Y1)
+    for call in (lambda: fkf.fkf_hmatrix_set_engine(hm, 0),
+                 lambda: fkf.fkf_hmatrix_apply_clustered_noalloc(hm, X, Y1)):
+        with pytest.raises(fkf.FkfError) as e:
+            call()
+        assert e.value.status == fkf.FKF_ESTATE
+    fkf.fkf_hmatrix_destroy(hm)
+    h64 = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.15, 1.0, leaf=32, precision=fkf.FKF_FP64)
+    with pytest.raises(fkf.FkfError):
+        fkf.fkf_hmatrix_release_values(h64)
+    fkf.fkf_hmatrix_destroy(h64)

@@ -56,6 +56,34 @@ def test_apply_timeout_is_reported_and_recoverable(fkf):
     fkf.fkf_destroy(ctx)
 
 
+def test_fp64_slice_engine_timeout_is_reported_and_recoverable(fkf):
+    """The same unwind in the FP64 tensor-core engine (engine 3)."""
+    import torch
+
+    wl = workload(TINY, 3)
+    pts = wl["points"]
+    n = pts.shape[0]
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, TINY["nu"], TINY["ell"], TINY["sigma2"], leaf=64, eta=1.0, aca_tol=1e-8,
+                               precision=fkf.FKF_FP64)
+    fkf.fkf_hmatrix_set_engine(hm, 3)
+    X = torch.from_numpy(np.random.default_rng(6).standard_normal((n, 40))).cuda()
+    Y0 = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply(hm, X, Y0)
+    fkf.fkf_hmatrix_set_wait_limit(hm, 0)
+    Yt = torch.zeros_like(X)
+    with pytest.raises(fkf.FkfError) as e:
+        fkf.fkf_hmatrix_apply(hm, X, Yt)
+    assert e.value.status == fkf.FKF_ETIMEOUT
+    fkf.fkf_hmatrix_set_wait_limit(hm, -1)
+    for _ in range(2):
+        Y1 = torch.empty_like(X)
+        fkf.fkf_hmatrix_apply(hm, X, Y1)
+        assert torch.equal(Y1, Y0)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
 def test_filter_step_timeout_leaves_state_unchanged(fkf):
     wl = workload(TINY, 4)
     pts, h = wl["points"], wl["H"]
