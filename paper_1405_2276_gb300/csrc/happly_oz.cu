@@ -18,11 +18,14 @@
 // w = i + j accumulate in one FP32 TMEM accumulator.  Over a block of 512 K
 // (32 chunks of 16) every partial sum of weight w <= 5 is an integer of
 // magnitude <= 2^24, hence exact in FP32 (the MMA multiplies FP16 integers
-// exactly); weight 6 lies 2^-42 below weight 0, where FP32 rounding is far
-// below FP64's.  After each block the epilogue moves the sums of weights
-// 0..5 into one 64-bit integer accumulator per output (sum_w T_w 2^(7(5-w)),
-// below 2^58 per block) and weight 6 into an FP32 one, and frees TMEM for the
-// next block; at the end of a tile it combines them in FP64 with the scales.
+// exactly).  Weights 0..3 are summed exactly: after each block the epilogue
+// moves them into one 64-bit integer per output (sum_w T_w 2^(7(3-w)), below
+// 2^44 per block) and releases their accumulators; weights 4..6 lie 2^-28 and
+// further below weight 0, where the rounding of an FP32 sum (2^-24 of it) is
+// below 2^-52 of the result, so they accumulate in TMEM over the whole tile,
+// and the MMAs of the next block start on them while the epilogue moves the
+// exact sums.  At the end of a tile everything is combined in FP64 with the
+// scales.
 //
 // The products run in the tensor-core layout of happly_tc.cu, with the MMA
 // roles of its phase 1 in both phases: the vector operand (X or the slot
@@ -55,6 +58,7 @@ namespace {
 
 constexpr int kSl = 7;                   // slices per value
 constexpr int kW = 7;                    // weights w = i + j kept (0 .. 6)
+constexpr int kWx = 4;                   // weights 0 .. 3 are summed exactly (64-bit integers)
 constexpr int kM = 128;                  // vector columns per tile (MMA M, TMEM lanes)
 constexpr int kN = 64;                   // operator rows per tile (MMA N)
 constexpr int kK = 16;                   // K per chunk = one kind::f16 MMA
@@ -232,18 +236,25 @@ __device__ __forceinline__ void producer(const OzSmem& s, const Ph& ph, int64_t 
   }
 }
 
-// The 28 products of one chunk: weight w accumulates at TMEM column 64 w;
-// the first chunk of a block starts every weight afresh.
-__device__ __forceinline__ void issue_chunk(const uint8_t* a, const uint8_t* b, uint32_t tmem, bool first) {
-  const uint32_t a0 = umma::smem_u32(a), b0 = umma::smem_u32(b);
+// The products of one chunk for the weights [w0, w1): weight w accumulates
+// at TMEM column 64 w.  Weights below kWx start afresh at the first chunk of
+// every 512-K block (their sums stay exact integers within a block and are
+// moved to 64-bit registers after it); the others accumulate over the whole
+// tile and start afresh at its first chunk.
+__device__ __forceinline__ void issue_weights(const uint8_t* a, const uint8_t* b, uint32_t tmem, int w0, int w1,
+                                              bool block_start, bool tile_start) {
+  // descriptors of plane 0; plane i starts i planes further on (the start
+  // address field holds addr >> 4 and stays below 2^14 inside shared memory)
+  const uint64_t ad0 = umma::smem_desc(umma::smem_u32(a), kSBO), bd0 = umma::smem_desc(umma::smem_u32(b), kSBO);
 #pragma unroll
   for (int w = 0; w < kW; w++) {
+    if (w < w0 || w >= w1) continue;
+    const bool fresh = w < kWx ? block_start : tile_start;
 #pragma unroll
     for (int i = 0; i <= w; i++) {
       const int j = w - i;
-      const uint64_t ad = umma::smem_desc(a0 + (uint32_t)(i * kAPlane), kSBO);
-      const uint64_t bd = umma::smem_desc(b0 + (uint32_t)(j * kBPlane), kSBO);
-      umma::mma_f16(tmem + (uint32_t)(w * kN), ad, bd, kIdesc, (first && i == 0) ? 0u : 1u);
+      umma::mma_f16(tmem + (uint32_t)(w * kN), ad0 + (uint64_t)(i * (kAPlane >> 4)),
+                    bd0 + (uint64_t)(j * (kBPlane >> 4)), kIdesc, (fresh && i == 0) ? 0u : 1u);
     }
   }
 }
@@ -262,20 +273,26 @@ __device__ __forceinline__ void mma_issuer(const OzSmem& s, uint32_t tmem) {
       continue;
     }
     for (int c = 0; c < nch; c++) {
-      if (c % kKBlock == 0) {  // the epilogue has read the previous block's sums
-        if (fl > 0 && !wait_bar(s, AE, (uint32_t)((fl - 1) & 1))) {
-          ok = false;
-          break;
-        }
-        umma::fence_after_sync();
-      }
       const int st = (int)(g % kStages);
       if (s.failed() || !wait_bar(s, FULL + st, (uint32_t)(g / kStages) & 1)) {
         ok = false;
         break;
       }
       umma::fence_after_sync();
-      issue_chunk(s.a(st), s.b(st), tmem, c % kKBlock == 0);
+      const bool block_start = c % kKBlock == 0;
+      if (block_start && fl > 0) {
+        // inside a tile the weights kept in TMEM go on while the epilogue moves the
+        // exact sums of the previous block; at a tile start the epilogue reads all seven
+        if (c > 0) issue_weights(s.a(st), s.b(st), tmem, kWx, kW, false, false);
+        if (!wait_bar(s, AE, (uint32_t)((fl - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        issue_weights(s.a(st), s.b(st), tmem, 0, c > 0 ? kWx : kW, true, c == 0);
+      } else {
+        issue_weights(s.a(st), s.b(st), tmem, 0, kW, block_start, c == 0);
+      }
       umma::commit(&s.bar[EMPTY + st]);
       g++;
       if (c % kKBlock == kKBlock - 1 || c == nch - 1) {
@@ -303,14 +320,15 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
     const int64_t w = id / ph.nct;
     const int ct = (int)(id % ph.nct);
     const int col = ct * kM + vcol;
-    // weights 0..5: exact integers, summed as sum_w T_w 2^(7(5-w)) in 64 bits
-    // (units of 2^-35; at most 2^58 per block); weight 6 in FP32 (units of 2^-42)
+    // weights 0..3: exact integers, summed as sum_w T_w 2^(7(3-w)) in 64 bits (units of
+    // 2^-21; at most 2^44 per block); weights 4..6 (summed over the tile in TMEM) in FP32 as
+    // T_4 + T_5 2^-7 + T_6 2^-14 (units of 2^-28)
     int64_t acc[32];
-    float acc6[32];
+    float low[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) {
       acc[i] = 0;
-      acc6[i] = 0.f;
+      low[i] = 0.f;
     }
     const int nblk = nch > 0 ? (nch + kKBlock - 1) / kKBlock : 1;
     bool ok = true;
@@ -325,18 +343,20 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
         break;
       }
       if (nch > 0) {
+        const bool last = blk == nblk - 1;
 #pragma unroll
         for (int wt = 0; wt < kW; wt++) {
+          if (wt >= kWx && !last) continue;
 #pragma unroll
           for (int hh = 0; hh < 2; hh++) {
             float v[16];
             umma::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(wt * kN + 32 * half + 16 * hh), v);
 #pragma unroll
             for (int i = 0; i < 16; i++) {
-              if (wt < kW - 1)
-                acc[16 * hh + i] += (int64_t)__float2int_rn(v[i]) << (7 * (kW - 2 - wt));
+              if (wt < kWx)
+                acc[16 * hh + i] += (int64_t)__float2int_rn(v[i]) << (7 * (kWx - 1 - wt));
               else
-                acc6[16 * hh + i] += v[i];
+                low[16 * hh + i] += v[i] * (wt == 4 ? 1.f : (wt == 5 ? 0.0078125f : 0.00006103515625f));
             }
           }
         }
@@ -353,7 +373,7 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
       for (int i = 0; i < 32; i++) {
         const int n = 32 * half + i;
         if (n < t.rows) {
-          const double r = (double)acc[i] * 0x1p-35 + (double)acc6[i] * 0x1p-42;
+          const double r = (double)acc[i] * 0x1p-21 + (double)low[i] * 0x1p-28;
           ph.Y[(t.row0 + n) * ph.ldy + col] = sc * ph.sig[t.row0 + n] * r;
         }
       }
@@ -366,18 +386,18 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
         if (it.out_row >= 0) {  // FP64 partial rows: Z / tau_n
 #pragma unroll
           for (int e = 0; e < 4; e++) {
-            const double r = (double)acc[4 * u + e] * 0x1p-35 + (double)acc6[4 * u + e] * 0x1p-42;
+            const double r = (double)acc[4 * u + e] * 0x1p-21 + (double)low[4 * u + e] * 0x1p-28;
             ph.part[(it.out_row + n0 + e) * ph.ldp + col] = ph.sig[it.map_off + n0 + e] * 0x1p-14 * r;
           }
           continue;
         }
-        // Z / (tau_n Q_g) on the 2^-49 grid: (acc + acc6 / 2^7) / 2^s with
+        // Z / (tau_n Q_g) on the 2^-49 grid: (acc 2^14 + low 2^7) / 2^s with
         // s = log2(Q_g / sig_g) >= 0, in integers
         int64_t z[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
           const int sh = ph.qsh[it.map_off + n0 + e];
-          const int64_t t = acc[4 * u + e] + __float2ll_rn(acc6[4 * u + e] * 0.0078125f);
+          const int64_t t = (acc[4 * u + e] << 14) + __float2ll_rn(low[4 * u + e] * 128.f);
           z[e] = sh > 0 ? (t + (int64_t(1) << (sh - 1))) >> sh : t;
         }
         const int64_t p = ph.slotpos[it.map_off + n0];  // 4 consecutive aligned positions
