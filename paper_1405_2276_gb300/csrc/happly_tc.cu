@@ -598,13 +598,14 @@ __device__ __forceinline__ void producer(const Smem<F>& s, const JobSet<Ph>& js,
 template <int F>
 __device__ __forceinline__ void issue_mma(const uint8_t* a, const uint8_t* b, uint32_t acc, bool first) {
   using G = Geo<F>;
-  const uint32_t a_hi = umma::smem_u32(a), a_lo = a_hi + G::kABytes;
-  const uint32_t b_hi = umma::smem_u32(b), b_lo = b_hi + G::kBBytes;
+  // descriptors by offset from the chunk's first core matrix (see issue_mma_p1)
+  const uint64_t ah0 = umma::smem_desc(umma::smem_u32(a), G::kSBO);
+  const uint64_t bh0 = umma::smem_desc(umma::smem_u32(b), G::kSBO);
 #pragma unroll
   for (int kk = 0; kk < kK / G::kMmaK; kk++) {
-    const uint32_t koff = kk * 2 * umma::kLBO;  // two core matrices along K per MMA
-    const uint64_t ah = umma::smem_desc(a_hi + koff, G::kSBO), al = umma::smem_desc(a_lo + koff, G::kSBO);
-    const uint64_t bh = umma::smem_desc(b_hi + koff, G::kSBO), bl = umma::smem_desc(b_lo + koff, G::kSBO);
+    const uint64_t koff = (uint64_t)((kk * 2 * umma::kLBO) >> 4);  // two core matrices along K per MMA
+    const uint64_t ah = ah0 + koff, al = ah + (uint64_t)(G::kABytes >> 4);
+    const uint64_t bh = bh0 + koff, bl = bh + (uint64_t)(G::kBBytes >> 4);
     const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
     if constexpr (fmt_of(F) == 1) {
       umma::mma_tf32(acc, ah, bh, G::kIdesc, acc0);
@@ -628,15 +629,17 @@ template <int F>
 __device__ __forceinline__ void issue_mma_p1(const uint8_t* op, const uint8_t* x, uint32_t acc, bool first, int nh,
                                              uint32_t idesc) {
   using G = Geo<F>;
-  const uint32_t b_hi = umma::smem_u32(op), b_lo = b_hi + G::kABytes;
+  // descriptors by offset from the chunk's first core matrix (the start
+  // address field holds addr >> 4 and stays below 2^14 inside shared memory)
+  const uint64_t bh0 = umma::smem_desc(umma::smem_u32(op), G::kSBO);
+  const uint64_t ah0 = umma::smem_desc(umma::smem_u32(x), G::kSBO);
   for (int h = 0; h < nh; h++) {
-    const uint32_t a_hi = umma::smem_u32(x) + (uint32_t)h * (G::kBBytes / 2), a_lo = a_hi + G::kBBytes;
     const uint32_t d = acc + (uint32_t)(h * (kN / 2));
 #pragma unroll
     for (int kk = 0; kk < kK / G::kMmaK; kk++) {
-      const uint32_t koff = kk * 2 * umma::kLBO;
-      const uint64_t ah = umma::smem_desc(a_hi + koff, G::kSBO), al = umma::smem_desc(a_lo + koff, G::kSBO);
-      const uint64_t bh = umma::smem_desc(b_hi + koff, G::kSBO), bl = umma::smem_desc(b_lo + koff, G::kSBO);
+      const uint64_t koff = (uint64_t)((kk * 2 * umma::kLBO) >> 4);
+      const uint64_t ah = ah0 + (uint64_t)((h * (G::kBBytes / 2)) >> 4) + koff, al = ah + (uint64_t)(G::kBBytes >> 4);
+      const uint64_t bh = bh0 + koff, bl = bh + (uint64_t)(G::kABytes >> 4);
       const uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
       if constexpr (fmt_of(F) == 1) {
         umma::mma_tf32(d, ah, bh, idesc, acc0);
