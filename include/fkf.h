@@ -215,6 +215,25 @@ fkf_status fkf_hmatrix_apply_clustered_noalloc(fkf_hmat* h, const void* X_dev, i
  * ETIMEOUT (a tensor-core wait expired). */
 fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda, int64_t rows, int32_t K, const float* E_dev,
                           int64_t lde, int64_t ke, int32_t ncols, float* C_dev, int64_t ldc);
+/* FP64 GEMM on the 5th-generation tensor cores: C = alpha op(A) op(B) +
+ * beta C for row-major FP64 device matrices (op(A): M x K, op(B): K x N;
+ * trans_a / trans_b nonzero: A is stored K x M, B is stored N x K; leading
+ * dimensions in elements).  The FP64 products come from seven 7-bit integer
+ * slices of every value (op(A) scaled per row, op(B) per column by powers of
+ * two; Ozaki's error-free splitting) as FP16 MMAs whose FP32 sums stay exact
+ * per block of 512 K, the engine-3 kernel of the H-apply; each element of C
+ * carries an error below about 2^-48 of K max_k |op(A)_ik| max_k |op(B)_kj|
+ * (49 bits of every value relative to its row or column scale).  This is
+ * the product the library's eigensolver uses for its large GEMMs (the paper has
+ * no counterpart: it serves the data-space GEP and merge eigensolves of
+ * Eq. ghep and Alg. lowrankaddition).  The caller owns all three arrays; C
+ * must not overlap A or B.  The context keeps a workspace of about 14 bytes
+ * per element of A and of B (grown on demand).  Synchronises the context's
+ * stream.  Errors: EINVAL (negative sizes, a leading dimension below its row
+ * length, C overlapping A or B), ENOMEM, ECUDA, ETIMEOUT. */
+fkf_status fkf_gemm_f64(fkf_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double* A_dev, int64_t lda, const double* B_dev, int64_t ldb, double beta, double* C_dev,
+                        int64_t ldc);
 /* Engine of the H-apply (the product with Gamma_H of Sec. 2.2.1).
  * FP32 operators: 2 (default) = 5th-generation tensor cores, tcgen05.mma
  * kind::f16 with a two-term FP16 split of power-of-two scaled operands

@@ -295,6 +295,31 @@ FKF_API fkf_status fkf_rotate_f32(fkf_ctx* ctx, const float* A_dev, int64_t lda,
   return tc_gemm_check(ctx, ctx->gemm_ws);
 }
 
+FKF_API fkf_status fkf_gemm_f64(fkf_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
+                                double alpha, const double* A_dev, int64_t lda, const double* B_dev, int64_t ldb,
+                                double beta, double* C_dev, int64_t ldc) {
+  if (!ctx) return FKF_EINVAL;
+  if (M < 0 || N < 0 || K < 0 || ldc < N || lda < (trans_a ? M : K) || ldb < (trans_b ? K : N))
+    return set_err(ctx, FKF_EINVAL, "fkf_gemm_f64: bad sizes");
+  if (M == 0 || N == 0) return FKF_OK;
+  if (!C_dev || (K > 0 && (!A_dev || !B_dev))) return set_err(ctx, FKF_EINVAL, "fkf_gemm_f64: null pointer");
+  auto span = [](const double* p, int64_t nr, int64_t ld, int64_t nc) {
+    const char* b = reinterpret_cast<const char*>(p);
+    return std::make_pair(b, b + ((nr - 1) * ld + nc) * (int64_t)sizeof(double));
+  };
+  auto overlap = [](std::pair<const char*, const char*> a, std::pair<const char*, const char*> b) {
+    return a.first < b.second && b.first < a.second;
+  };
+  const auto c = span(C_dev, M, ldc, N);
+  if (K > 0 && (overlap(c, trans_a ? span(A_dev, K, lda, M) : span(A_dev, M, lda, K)) ||
+                overlap(c, trans_b ? span(B_dev, N, ldb, K) : span(B_dev, K, ldb, N))))
+    return set_err(ctx, FKF_EINVAL, "fkf_gemm_f64: C overlaps A or B");
+  FKF_TRY(gemm_f64_tc(ctx, trans_a != 0, trans_b != 0, M, N, K, alpha, A_dev, lda, B_dev, ldb, beta, C_dev, ldc));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FKF_CUDA(ctx, cudaGetLastError());
+  return gemm_f64_tc_check(ctx);
+}
+
 FKF_API fkf_status fkf_hmatrix_apply(fkf_hmat* h, const void* X_dev, int64_t ldx, void* Y_dev, int64_t ldy,
                                      int64_t ncols) {
   if (!h) return FKF_EINVAL;

@@ -52,6 +52,12 @@ struct TcMultiWs {
   }
 };
 
+// Workspace of the FP64 GEMM on the tensor cores (sliced operands, scales,
+// error flag and tile counter).
+struct OzGemmWs {
+  DevBuf as, bs, sc, ctl;
+};
+
 struct fkf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -62,6 +68,7 @@ struct fkf_ctx {
   std::atomic<int64_t> lib_calls{0};  // cuSOLVER routine calls
   DevBuf solver_info;  // status word for cuSOLVER calls
   TcGemmWs gemm_ws;    // fkf_rotate_f32
+  OzGemmWs ozgemm_ws;  // FP64 GEMMs on the tensor cores (gemm_f64_tc)
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
   cudaStream_t side_lo = nullptr;     // low-priority stream for work that fills SMs beside a persistent kernel
   // When set, the tensor-core H-apply on this context records ph2_mark on the
@@ -351,6 +358,14 @@ fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, do
 fkf_status hmat_oz_check(fkf_hmat* h);
 // Writes the sliced operator stream of engine 3 if it is not there yet.
 fkf_status hmat_oz_prepare(fkf_hmat* h);
+// C = alpha op(A) op(B) + beta C for FP64 row-major device matrices on the
+// tensor cores, by the integer slices of engine 3 (op(A) sliced per row,
+// op(B) per column); C must not overlap A or B.  On ctx->stream; reports an
+// expired pipeline wait through the context's GEMM error flag (checked by
+// gemm_f64_tc_check).
+fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc);
+fkf_status gemm_f64_tc_check(fkf_ctx* ctx);
 
 // happly_tc.cu
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols);

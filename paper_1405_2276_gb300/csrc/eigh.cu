@@ -970,6 +970,17 @@ void build_tree(int off, int s, std::vector<Node>& merges, std::vector<int>& lof
 // and symmetrised): all eigenvalues ascending into w_dev (and w_host); the
 // eigenvectors of the `want` largest (want <= n) into rows 0..want-1 of A,
 // ascending, row q = eigenvector of w[n - want + q].
+// Large FP64 products of the solver on the tensor cores (the integer-slice
+// GEMM of the FP64 H-apply engine: 49 bits of every value relative to its row
+// or column scale), the others on the FP64 tile GEMM.
+static fkf_status gemm_big(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                           const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                           int64_t ldc) {
+  if ((double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
+    return gemm_f64_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return gemm_f64(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<double>& w_host, DevBuf& ws,
                     int want) {
   cudaStream_t st = ctx->stream;
@@ -1115,7 +1126,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
       k_dc_vectors<<<grid_for((int64_t)K * K + (int64_t)K * s), 256, 0, st>>>(s, mg, U, QsT, QselT);
       FKF_LAUNCHED(ctx);
       // QnT (K x s) = UT QselT: row q = the q-th new eigenvector in the node's basis
-      FKF_TRY(gemm_f64(ctx, false, false, K, s, K, 1.0, U, K, QselT, s, 0.0, Qn, s));
+      FKF_TRY(gemm_big(ctx, false, false, K, s, K, 1.0, U, K, QselT, s, 0.0, Qn, s));
     }
     k_dc_order<<<1, 32, 0, st>>>(nd.off, mg, Dv);
     FKF_LAUNCHED(ctx);
@@ -1143,9 +1154,12 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
       FKF_LAUNCHED(ctx);
       double* Xs = X + (j0 + 1) * k;
       // X[j0+1:] -= V (T (V^T X[j0+1:]))
-      FKF_TRY(gram_f64(ctx, nbp, k, rows, Vp, nbp, Xs, k, Y1, k, gws));
+      if ((double)nbp * k * rows >= 1e8 && cdiv(k, 64) >= 16)
+        FKF_TRY(gemm_f64_tc(ctx, true, false, nbp, k, rows, 1.0, Vp, nbp, Xs, k, 0.0, Y1, k));
+      else
+        FKF_TRY(gram_f64(ctx, nbp, k, rows, Vp, nbp, Xs, k, Y1, k, gws));
       FKF_TRY(gemm_f64(ctx, false, false, nbp, k, nbp, 1.0, Tf, nbp, Y1, k, 0.0, QselT, k));
-      FKF_TRY(gemm_f64(ctx, false, false, rows, k, nbp, -1.0, Vp, nbp, QselT, k, 1.0, Xs, k));
+      FKF_TRY(gemm_big(ctx, false, false, rows, k, nbp, -1.0, Vp, nbp, QselT, k, 1.0, Xs, k));
     }
     // eigenvector q (column q of X) -> row q of A
     k_transpose_into<<<grid_for(N * k), 256, 0, st>>>(N, k, X, k, A, N);
@@ -1155,6 +1169,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
   FKF_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   FKF_CUDA(ctx, cudaMemcpyAsync(w_host.data(), w_dev, N * 8, cudaMemcpyDeviceToHost, st));
   FKF_CUDA(ctx, cudaStreamSynchronize(st));
+  FKF_TRY(gemm_f64_tc_check(ctx));
   if (herr) return set_err(ctx, FKF_ENOCONV, "symmetric eigensolver: %s (n=%d)",
                            herr == 1 ? "a grid barrier timed out" : (herr == 2 ? "QL did not converge" :
                                                                                   "secular equation did not converge"),

@@ -52,6 +52,7 @@
 #include <type_traits>
 
 #include "common.h"
+#include "dense.h"
 #include "umma.cuh"
 
 namespace {
@@ -171,8 +172,25 @@ struct OzPh2 {
   int nct, ncols;
 };
 
+// Dense GEMM C = alpha op(A) op(B) + beta C: tile (row tile w of 128 rows of
+// C, column tile ct of 64 columns); op(A) sliced per row (A chunks of row
+// tile w: as + (w * nch + c) * kAChunk), op(B) sliced per column of C (B
+// chunks of column tile ct: bs + (ct * nch + c) * kBChunk).
+struct OzPhGemm {
+  const uint8_t* as;
+  const uint8_t* bs;
+  double* C;
+  int64_t ldc;
+  const double* sa;  // row scales of op(A)
+  const double* sb;  // column scales of op(B)
+  double alpha, beta;
+  int M, N, nch;
+  int nct;
+};
+
 __device__ __forceinline__ int tile_nch(const OzPh1& p, int64_t w) { return p.items[w].nchunk; }
 __device__ __forceinline__ int tile_nch(const OzPh2& p, int64_t w) { return p.tiles[w].nchunk; }
+__device__ __forceinline__ int tile_nch(const OzPhGemm& p, int64_t) { return p.nch; }
 
 // ---- roles ----------------------------------------------------------------
 __device__ __forceinline__ bool next_tile(const OzSmem& s, int qi, int64_t& id, int& nch) {
@@ -215,7 +233,11 @@ __device__ __forceinline__ void producer(const OzSmem& s, const Ph& ph, int64_t 
     e->nch = nch;
     umma::mbar_arrive(&s.bar[QF + slot]);
     if (id < 0) return;
-    if constexpr (std::is_same<Ph, OzPh1>::value) {
+    if constexpr (std::is_same<Ph, OzPhGemm>::value) {
+      for (int c = 0; c < nch; c++)
+        if (!load_chunk(s, g, ph.as + (w * nch + c) * (int64_t)kAChunk, ph.bs + ((int64_t)ct * nch + c) * kBChunk))
+          return;
+    } else if constexpr (std::is_same<Ph, OzPh1>::value) {
       const OzItem it = ph.items[w];
       for (int c = 0; c < nch; c++)
         if (!load_chunk(s, g, ph.xs + ((it.x_chunk0 + c) * ph.nct + ct) * (int64_t)kAChunk,
@@ -319,7 +341,8 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
   for (; next_tile(s, tl, id, nch); tl++) {
     const int64_t w = id / ph.nct;
     const int ct = (int)(id % ph.nct);
-    const int col = ct * kM + vcol;
+    // H-apply: vector column of the pass; GEMM: the row of C
+    const int col = std::is_same<Ph, OzPhGemm>::value ? (int)w * kM + vcol : ct * kM + vcol;
     // weights 0..3: exact integers, summed as sum_w T_w 2^(7(3-w)) in 64 bits (units of
     // 2^-21; at most 2^44 per block); weights 4..6 (summed over the tile in TMEM) in FP32 as
     // T_4 + T_5 2^-7 + T_6 2^-14 (units of 2^-28)
@@ -365,8 +388,21 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
       umma::mbar_arrive(&s.bar[AE]);
     }
     if (!ok) break;
-    if (col >= ph.ncols) continue;
-    if constexpr (std::is_same<Ph, OzPh2>::value) {
+    if constexpr (std::is_same<Ph, OzPhGemm>::value) {
+      if (col >= ph.M) continue;
+      const double sc = ph.alpha * ph.sa[col] * 0x1p-14;
+      double* crow = ph.C + (int64_t)col * ph.ldc;
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const int n = ct * kN + 32 * half + i;
+        if (n < ph.N) {
+          const double r = (double)acc[i] * 0x1p-21 + (double)low[i] * 0x1p-28;
+          const double v = sc * ph.sb[n] * r;
+          crow[n] = ph.beta == 0.0 ? v : fma(ph.beta, crow[n], v);
+        }
+      }
+    } else if constexpr (std::is_same<Ph, OzPh2>::value) {
+      if (col >= ph.ncols) continue;
       const OzTile t = ph.tiles[w];
       const double sc = ph.tau[col] * 0x1p-14;
 #pragma unroll
@@ -378,6 +414,7 @@ __device__ __forceinline__ void epilogue(const OzSmem& s, const Ph& ph, uint32_t
         }
       }
     } else {
+      if (col >= ph.ncols) continue;
       const OzItem it = ph.items[w];
 #pragma unroll
       for (int u = 0; u < 8; u++) {  // aligned groups of 4 slots
@@ -566,6 +603,89 @@ __global__ void k_oz_reduce(const P1Reduce* __restrict__ items, const double* __
   }
 }
 
+// Row maxima of |op(src)| for a transposed view (element (r, k) = src[k * ld + r]):
+// grid (row blocks of 256, K blocks of kSegK); bit patterns of non-negative doubles.
+constexpr int kSegK = 128;
+__global__ void __launch_bounds__(256) k_oz_rowmax_t(const double* __restrict__ src, int64_t ld, int64_t rows,
+                                                     int64_t K, unsigned long long* __restrict__ mx) {
+  const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t k0 = (int64_t)blockIdx.y * kSegK, k1 = min(K, k0 + kSegK);
+  double m = 0.0;
+  for (int64_t k = k0; k < k1; k++) m = fmax(m, fabs(src[k * ld + r]));
+  atomicMax(&mx[r], (unsigned long long)__double_as_longlong(m));
+}
+
+// Row scales of op(src), rows x K: power of two >= max_k |op(src)[r][k]|.
+// Contiguous rows (trans = 0): a warp per row; transposed: from the maxima mx.
+__global__ void __launch_bounds__(256) k_oz_rowscale(const double* __restrict__ src, int64_t ld, int trans,
+                                                     int64_t rows, int64_t K, const unsigned long long* __restrict__ mx,
+                                                     double* __restrict__ s) {
+  if (trans) {
+    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (r < rows) s[r] = pow2_ceil(__longlong_as_double((long long)mx[r]));
+    return;
+  }
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  double m = 0.0;
+  for (int64_t k = lane; k < K; k += 32) m = fmax(m, fabs(src[r * ld + k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) s[r] = pow2_ceil(m);
+}
+
+// op(src) (rows x K) into chunks of TR rows x 16 K x 7 slice planes: chunk
+// (row tile t, K chunk c) at out + (t * nch + c) * 7 * TR * 32 bytes,
+// element (r, k) over its row scale s[r], zero outside rows x K.  Thread
+// (row of the tile, 8 k).
+template <int TR>
+__global__ void __launch_bounds__(2 * TR) k_oz_slice_dense(const double* __restrict__ src, int64_t ld, int trans,
+                                                           int64_t rows, int64_t K, int nch,
+                                                           const double* __restrict__ s, uint8_t* __restrict__ out) {
+  constexpr int kPlane = TR * kK * 2;
+  const int64_t t = blockIdx.x;
+  const int c = blockIdx.y;
+  const int rl = threadIdx.x % TR, kg = threadIdx.x / TR;
+  const int64_t r = t * TR + rl;
+  const double sc = r < rows ? 0x1p49 / s[r] : 0.0;  // a power of two
+  uint16_t sl[8][kSl];
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const int64_t k = (int64_t)c * kK + 8 * kg + u;
+    double x = 0.0;
+    if (r < rows && k < K) x = (trans ? src[k * ld + r] : src[r * ld + k]) * sc;
+    digits7(__double2ll_rn(x), sl[u]);
+  }
+  uint8_t* base = out + (t * nch + c) * (int64_t)(kSl * kPlane) + off16(rl, 8 * kg);
+#pragma unroll
+  for (int i = 0; i < kSl; i++)
+    *reinterpret_cast<uint4*>(base + i * kPlane) =
+        make_uint4((uint32_t)sl[0][i] | ((uint32_t)sl[1][i] << 16), (uint32_t)sl[2][i] | ((uint32_t)sl[3][i] << 16),
+                   (uint32_t)sl[4][i] | ((uint32_t)sl[5][i] << 16), (uint32_t)sl[6][i] | ((uint32_t)sl[7][i] << 16));
+}
+
+// Scales and slices of one GEMM operand viewed as rows x K (trans: element
+// (r, k) = src[k * ld + r]).
+template <int TR>
+fkf_status oz_operand(fkf_ctx* ctx, const double* src, int64_t ld, bool trans, int64_t rows, int64_t K, int nch,
+                      double* s, unsigned long long* mx, uint8_t* out) {
+  cudaStream_t st = ctx->stream;
+  if (trans) {
+    FKF_CUDA(ctx, cudaMemsetAsync(mx, 0, (size_t)rows * sizeof(unsigned long long), st));
+    k_oz_rowmax_t<<<dim3((unsigned)cdiv(rows, 256), (unsigned)cdiv(K, kSegK)), 256, 0, st>>>(src, ld, rows, K, mx);
+    FKF_LAUNCHED(ctx);
+    k_oz_rowscale<<<(unsigned)cdiv(rows, 256), 256, 0, st>>>(src, ld, 1, rows, K, mx, s);
+  } else {
+    k_oz_rowscale<<<(unsigned)cdiv(rows, 8), 256, 0, st>>>(src, ld, 0, rows, K, nullptr, s);
+  }
+  FKF_LAUNCHED(ctx);
+  k_oz_slice_dense<TR><<<dim3((unsigned)cdiv(rows, TR), (unsigned)nch), 2 * TR, 0, st>>>(src, ld, trans ? 1 : 0, rows,
+                                                                                       K, nch, s, out);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
 fkf_status build_oz_stream(fkf_hmat* h) {
   fkf_ctx* ctx = h->ctx;
   if (h->n_ozb > 0) {
@@ -704,6 +824,55 @@ fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, do
     k_oz_apply<OzPh2><<<(unsigned)std::min<int64_t>(sms, nt), kThreads, kSmem, st>>>(p2, nt, counters + 1,
                                                                                     h->oz_err.as<int>(), h->tc_polls);
     FKF_LAUNCHED(ctx);
+  }
+  return FKF_OK;
+}
+
+fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return FKF_OK;
+  if (K <= 0 || alpha == 0.0) return beta == 1.0 ? FKF_OK : scale_f64(ctx, M, N, beta, C, ldc);
+  OzGemmWs& ws = ctx->ozgemm_ws;
+  const int nch = (int)cdiv(K, kK);
+  const int64_t nrt = cdiv(M, kM), nct = cdiv(N, kN);
+  const size_t abytes = (size_t)nrt * nch * kAChunk, bbytes = (size_t)nct * nch * kBChunk;
+  if (ws.as.bytes < abytes) FKF_TRY(dev_alloc(ctx, ws.as, abytes));
+  if (ws.bs.bytes < bbytes) FKF_TRY(dev_alloc(ctx, ws.bs, bbytes));
+  const size_t sbytes = (size_t)(M + N) * 16;
+  if (ws.sc.bytes < sbytes) FKF_TRY(dev_alloc(ctx, ws.sc, sbytes));
+  if (ws.ctl.bytes < 64) {
+    FKF_TRY(dev_alloc(ctx, ws.ctl, 64));
+    FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 64, ctx->stream));
+  }
+  double* sa = ws.sc.as<double>();
+  double* sb = sa + M;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(sb + N);
+  // op(A) by rows of C; op(B) by columns of C: element (n, k) = op(B)[k][n]
+  FKF_TRY(oz_operand<kM>(ctx, A, lda, ta, M, K, nch, sa, mx, ws.as.as<uint8_t>()));
+  FKF_TRY(oz_operand<kN>(ctx, B, ldb, !tb, N, K, nch, sb, mx + M, ws.bs.as<uint8_t>()));
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(ws.ctl.as<char>() + 16);
+  FKF_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream));
+  int sms = 0;
+  FKF_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  FKF_CUDA(ctx, cudaFuncSetAttribute(k_oz_apply<OzPhGemm>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  const OzPhGemm ph{ws.as.as<uint8_t>(), ws.bs.as<uint8_t>(), C, ldc, sa, sb, alpha, beta, (int)M, (int)N, nch,
+                    (int)nct};
+  const int64_t nt = nrt * nct;
+  k_oz_apply<OzPhGemm><<<(unsigned)std::min<int64_t>(sms, nt), kThreads, kSmem, ctx->stream>>>(
+      ph, nt, counter, ws.ctl.as<int>(), kMaxPolls);
+  FKF_LAUNCHED(ctx);
+  return FKF_OK;
+}
+
+fkf_status gemm_f64_tc_check(fkf_ctx* ctx) {
+  OzGemmWs& ws = ctx->ozgemm_ws;
+  if (!ws.ctl.p) return FKF_OK;
+  int e = 0;
+  FKF_CUDA(ctx, cudaMemcpyAsync(&e, ws.ctl.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 4, ctx->stream));
+    return set_err(ctx, FKF_ETIMEOUT, "FP64 tensor-core GEMM: an mbarrier wait expired");
   }
   return FKF_OK;
 }

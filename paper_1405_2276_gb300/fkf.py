@@ -90,6 +90,8 @@ _sigs = {
     "fkf_hmatrix_apply_adjoint": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64,
                                             C.POINTER(C.c_double)]),
     "fkf_hmatrix_apply_clustered_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int64]),
+    "fkf_gemm_f64": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_double, _P, C.c_int64,
+                               _P, C.c_int64, C.c_double, _P, C.c_int64]),
     "fkf_rotate_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, C.c_int64, C.c_int64, C.c_int32, _P,
                                  C.c_int64]),
     "fkf_hmatrix_permutation": (C.c_int, [_P, _P]),
@@ -240,6 +242,15 @@ def fkf_rotate_f32(ctx, A, E, C, K=None, ncols=None):
     ncols = C.shape[1] if ncols is None else ncols
     _check(_lib.fkf_rotate_f32(ctx.ptr, _ptr(A), A.stride(0), A.shape[0], K, _ptr(E), E.stride(0), E.shape[0], ncols,
                                _ptr(C), C.stride(0)), ctx)
+
+
+def fkf_gemm_f64(ctx, A, B, C, alpha=1.0, beta=0.0, trans_a=False, trans_b=False):
+    """C = alpha op(A) op(B) + beta C on the tensor cores (FP64 row-major CUDA
+    tensors, any leading dimensions; FP64 products from integer slices)."""
+    M, N = C.shape
+    K = A.shape[0] if trans_a else A.shape[1]
+    _check(_lib.fkf_gemm_f64(ctx.ptr, int(trans_a), int(trans_b), M, N, K, float(alpha), _ptr(A), A.stride(0),
+                             _ptr(B), B.stride(0), float(beta), _ptr(C), C.stride(0)), ctx)
 
 
 def fkf_hmatrix_set_engine(h, engine: int) -> None:

@@ -165,3 +165,35 @@ def test_fp64_filter_on_slice_engine_time_varying(fkf):
     fkf.fkf_filter_destroy(f)
     fkf.fkf_hmatrix_destroy(hm)
     fkf.fkf_destroy(ctx)
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb,beta", [
+    (1, 1, 1, False, False, 0.0),
+    (300, 200, 700, False, False, 0.0),
+    (129, 65, 1100, True, False, 0.5),
+    (257, 130, 33, False, True, -1.0),
+    (1024, 1024, 1024, True, True, 0.0),
+])
+def test_gemm_f64_on_tensor_cores(fkf, M, N, K, ta, tb, beta):
+    """fkf_gemm_f64 against numpy's FP64 product: the error of each element
+    below 2^-47 of K max_k |a_ik| max_k |b_kj| (plus |beta c_ij|: the slices
+    keep 49 bits of every value relative to its row / column scale); rows and
+    columns of very different magnitude."""
+    import torch
+
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    Aop = rng.standard_normal((M, K)) * np.exp(rng.uniform(-8, 8, (M, 1)))
+    Bop = rng.standard_normal((K, N)) * np.exp(rng.uniform(-8, 8, (1, N)))
+    C0 = rng.standard_normal((M, N))
+    A = np.ascontiguousarray(Aop.T) if ta else Aop
+    B = np.ascontiguousarray(Bop.T) if tb else Bop
+    ctx = fkf.fkf_create(0)
+    Ct = torch.from_numpy(C0.copy()).cuda()
+    fkf.fkf_gemm_f64(ctx, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Ct, alpha=1.5, beta=beta,
+                     trans_a=ta, trans_b=tb)
+    ref = 1.5 * (Aop @ Bop) + beta * C0
+    scale = 1.5 * K * np.abs(Aop).max(axis=1)[:, None] * np.abs(Bop).max(axis=0)[None, :] + abs(beta) * np.abs(C0)
+    err = float(np.max(np.abs(Ct.cpu().numpy() - ref) / scale))
+    print(f"gemm {M}x{N}x{K} ta={ta} tb={tb} beta={beta}: max err / (K max|a| max|b|) {err:.2e}")
+    assert err < 2.0 ** -47
+    fkf.fkf_destroy(ctx)
