@@ -1080,8 +1080,14 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     ctx->launches++;
     const int64_t j1 = j0 + nbp;
     if (j1 < N) {
-      // A[j1:, j1:] -= [V W] [W V]^T = V W^T + W V^T
-      FKF_TRY(gemm_sym_f64(ctx, false, true, N - j1, L, -1.0, VW + j1 * L, L, WV + j1 * L, L, 1.0, A + j1 * N + j1, N));
+      // A[j1:, j1:] -= [V W] [W V]^T = V W^T + W V^T (large trailing blocks on the tensor
+      // cores: both triangles computed, symmetric to rounding; the panel kernel reads rows)
+      if (N - j1 >= 512)
+        FKF_TRY(gemm_f64_tc(ctx, false, true, N - j1, N - j1, L, -1.0, VW + j1 * L, L, WV + j1 * L, L, 1.0,
+                            A + j1 * N + j1, N));
+      else
+        FKF_TRY(gemm_sym_f64(ctx, false, true, N - j1, L, -1.0, VW + j1 * L, L, WV + j1 * L, L, 1.0,
+                             A + j1 * N + j1, N));
     }
   }
 
