@@ -231,7 +231,8 @@ def run_gpu(args, rank, world):
     ev1 = torch.cuda.Event(enable_timing=True)
     phases = np.zeros(6)
     # the timed steps are the profiled range (ncu --profile-from-start off)
-    torch.cuda.profiler.start()
+    if args.profile == "kept":
+        torch.cuda.profiler.start()
     ev0.record(stream)
     t0 = time.time()
     for k in range(args.warmup, total_steps):
@@ -239,7 +240,8 @@ def run_gpu(args, rank, world):
         phases += np.array(fkf.fkf_filter_phase_times(f32))
     ev1.record(stream)
     ev1.synchronize()
-    torch.cuda.profiler.stop()
+    if args.profile == "kept":
+        torch.cuda.profiler.stop()
     wall = time.time() - t0
     ms_dev = ev0.elapsed_time(ev1)
     clk = clocks.stop()
@@ -301,10 +303,12 @@ def run_gpu(args, rank, world):
     # merge eigensolve, rotation) although it brings nothing outside span(W).
     general = max(args.general_steps, 1)
 
-    def timed_steps(step_fn, nsteps, stat_keys):
+    def timed_steps(step_fn, nsteps, stat_keys, prof=False):
         phases = np.zeros(6)
         stats = []
         torch.cuda.synchronize()
+        if prof:
+            torch.cuda.profiler.start()
         ev0.record(stream)
         for k in range(nsteps):
             step_fn(k)
@@ -313,6 +317,8 @@ def run_gpu(args, rank, world):
             stats.append({k2: st[k2] for k2 in stat_keys})
         ev1.record(stream)
         ev1.synchronize()
+        if prof:
+            torch.cuda.profiler.stop()
         ms = ev0.elapsed_time(ev1) / nsteps
         return dict(ms_per_step=ms, steps_per_s=1e3 / ms, steps=nsteps, phases_ms=(phases / nsteps).tolist(),
                     step_stats=stats[-2:], timing="CUDA events on the library stream around the steps")
@@ -320,7 +326,7 @@ def run_gpu(args, rank, world):
     res["fp32_full"] = timed_steps(
         lambda k: fkf.fkf_filter_step(f32, ys_d[k % total_steps], m, rowptr_d, col_d, val_d, None, w["noise"],
                                       flags=fkf.FKF_STEP_INPUTS_ON_DEVICE | fkf.FKF_STEP_FULL_UPDATE, want_nll=False),
-        general, ("r", "last_path", "gep_rank", "new_dirs", "t_eig", "t_lmax"))
+        general, ("r", "last_path", "gep_rank", "new_dirs", "t_eig", "t_lmax"), prof=args.profile == "merge")
     log(f"[bench] FP32 general step, merge forced: {res['fp32_full']['ms_per_step']:.1f} ms/step; phases(ms) "
         + " ".join(f"{p:.1f}" for p in res["fp32_full"]["phases_ms"]) + f"; {res['fp32_full']['step_stats']}")
 
@@ -344,7 +350,8 @@ def run_gpu(args, rank, world):
 
     vr_step(0)
     res["fp32_varying"] = timed_steps(lambda k: vr_step(k + 1), general,
-                                      ("r", "last_path", "gep_rank", "new_dirs", "t_eig"))
+                                      ("r", "last_path", "gep_rank", "new_dirs", "t_eig"),
+                                      prof=args.profile == "new_rays")
     log(f"[bench] FP32 general step, new rays every step: {res['fp32_varying']['ms_per_step']:.1f} ms/step; "
         "phases(ms) " + " ".join(f"{p:.1f}" for p in res["fp32_varying"]["phases_ms"])
         + f"; {res['fp32_varying']['step_stats']}")
@@ -492,6 +499,43 @@ def eigh_bench(sizes, profile=False):
     return out
 
 
+def apply_bench(grid, m, prec, engine, reps=3):
+    """The H-apply alone (profiling captures of its kernels): the operator of the workload's
+    kernel on a grid x grid cell-centre grid (ell 0.1 below 512, the workload's 0.05 at 512),
+    engine `engine`, an N x m block of seeded normal columns; one warm-up apply, then `reps`
+    applies bracketed by cudaProfilerStart/Stop, ms per apply by CUDA events."""
+    import torch
+
+    import synth
+    from paper_1405_2276_gb300 import fkf
+
+    w = WORKLOAD
+    pts = synth.grid_points_2d(grid, grid)
+    n = pts.shape[0]
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, w["nu"], w["ell"] if grid >= 512 else 0.1, w["sigma2"], leaf=w["leaf"],
+                               eta=w["eta"], aca_tol=w["aca_tol"], k_cap=w["k_cap"], precision=prec)
+    fkf.fkf_hmatrix_set_engine(hm, engine)
+    dt = torch.float64 if prec == fkf.FKF_FP64 else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(11)
+    X = torch.randn((n, m), device="cuda", dtype=dt, generator=g)
+    Y = torch.empty_like(X)
+    fkf.fkf_hmatrix_apply_clustered(hm, X, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record()
+    for _ in range(reps):
+        fkf.fkf_hmatrix_apply_clustered(hm, X, Y)
+    e1.record()
+    e1.synchronize()
+    torch.cuda.profiler.stop()
+    out = {"grid": grid, "m": m, "precision": prec, "engine": engine, "ms_per_apply": e0.elapsed_time(e1) / reps}
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+    return out
+
+
 def batch_spec(nb, seed):
     """Uneven filters of the batch workload: N log-uniform in [16384, 262144] on square grids, m
     log-uniform in [64, 1024] as n_src x n_rec rays, nu in {1/2, 3/2}, ell uniform in [0.02, 0.3]."""
@@ -622,6 +666,12 @@ def main():
                     help="medium = 256x256, m=400: for profiler captures only")
     ap.add_argument("--eigh", type=int, nargs="*", default=None,
                     help="only time the FP64 eigensolver on these sizes (profiler range around the timed calls)")
+    ap.add_argument("--apply", type=int, nargs=4, default=None, metavar=("GRID", "M", "PREC", "ENGINE"),
+                    help="only time the H-apply (profiler range around the timed applies): grid size, columns, "
+                         "precision (0 FP64, 1 FP32), engine")
+    ap.add_argument("--profile", default="kept", choices=["kept", "merge", "new_rays"],
+                    help="steps bracketed by cudaProfilerStart/Stop (for ncu --profile-from-start off): the "
+                         "timed kept-basis steps, the merge-forced or the new-rays general steps")
     ap.add_argument("--batch", type=int, default=64,
                     help="also time a batch of this many uneven FP32 filters (sequential vs merged batched steps); "
                          "0 skips it")
@@ -644,6 +694,13 @@ def main():
 
         build()
         print(json.dumps({"eigh_ms": eigh_bench(args.eigh, profile=True)}), flush=True)
+        return
+
+    if args.apply:
+        from paper_1405_2276_gb300 import build
+
+        build()
+        print(json.dumps({"happly": apply_bench(*args.apply)}), flush=True)
         return
 
     if args.impl == "reference":

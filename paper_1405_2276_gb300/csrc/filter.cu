@@ -947,6 +947,19 @@ fkf_status gemm_T<float>(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, i
   return gemm_f32(ctx, ta, tb, M, N, K, (float)alpha, A, lda, B, ldb, (float)beta, C, ldc);
 }
 
+// The data-space products of the general (merge) step: the large ones as FP64
+// GEMMs on the tensor cores (integer slices, 49 bits of every value relative to
+// its row or column scale), the small ones on the FP64 tile GEMM.  Nothing of
+// the step's own runs beside them (unlike the kept-basis weight products, which
+// share the SMs with the H-apply's phase 2 and stay on the FP64 pipe).
+static fkf_status gemm_merge(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                             const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                             int64_t ldc) {
+  if ((double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
+    return gemm_f64_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return gemm_f64(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 static fkf_status gram_T(fkf_ctx* ctx, size_t w, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                          const void* B, int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
   if (w == 8) return gram_f64(ctx, M, N, K, (const double*)A, lda, (const double*)B, ldb, C, ldc, ws);
@@ -1440,9 +1453,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   int mp = mlam, t_eig = 0;
   double t_lmax = r > 0 ? 0.0 : 1.0;  // without W, T = I
   if (r > 0 && mlam > 0) {
-    FKF_TRY(gemm_f64(ctx, true, false, r, mlam, m, 1.0, HW, nm, C, mlam, 0.0, P, mlam));
+    FKF_TRY(gemm_merge(ctx, true, false, r, mlam, m, 1.0, HW, nm, C, mlam, 0.0, P, mlam));
     double* Tm = f->Tm.as<double>();
-    FKF_TRY(gemm_f64(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
+    FKF_TRY(gemm_merge(ctx, true, false, mlam, mlam, r, -1.0, P, mlam, P, mlam, 0.0, Tm, mlam));
     k_add_identity<<<(int)cdiv(mlam, 256), 256, 0, st>>>(mlam, Tm, mlam, 1.0);
     FKF_LAUNCHED(ctx);
     // every eigenvalue of T is bounded by ||T||_F: below the threshold there
@@ -1494,7 +1507,13 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
                                                             f->ZL.as<double>());
       FKF_LAUNCHED(ctx);
     }
-    FKF_TRY(gemm_sym_f64(ctx, false, true, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0, M, nM));
+    // (the eigensolver symmetrises M: the tensor-core product's rounding asymmetry is harmless)
+    if ((double)nM * nM * mlam >= 1e8)
+      FKF_TRY(gemm_f64_tc(ctx, false, true, nM, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam,
+                          0.0, M, nM));
+    else
+      FKF_TRY(gemm_sym_f64(ctx, false, true, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam, 0.0,
+                           M, nM));
     if (r > 0 && diag) {
       k_add_dbar<<<(int)cdiv(r, 256), 256, 0, st>>>(r, f->D.as<double>(), alpha1, M, nM);
       FKF_LAUNCHED(ctx);
@@ -1532,16 +1551,16 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     double* J = f->J.as<double>();        // mlam x rnew
     if (mp > 0) {
       // J = F1 S2 with F1^T (mp x mlam) and S2^T = Sk[:, r:r+mp]
-      FKF_TRY(gemm_f64(ctx, true, true, mlam, rnew, mp, 1.0, f->F1t.as<double>(), mlam, f->Sk.as<double>() + r, nM,
-                       0.0, J, rnew));
-      FKF_TRY(gemm_f64(ctx, false, false, m, rnew, mlam, 1.0, C, mlam, J, rnew, 0.0, EG, rnew));
+      FKF_TRY(gemm_merge(ctx, true, true, mlam, rnew, mp, 1.0, f->F1t.as<double>(), mlam, f->Sk.as<double>() + r,
+                         nM, 0.0, J, rnew));
+      FKF_TRY(gemm_merge(ctx, false, false, m, rnew, mlam, 1.0, C, mlam, J, rnew, 0.0, EG, rnew));
     } else {
       FKF_CUDA(ctx, cudaMemsetAsync(EG, 0, (size_t)m * rnew * 8, st));
     }
     if (r > 0) {
       k_transpose<<<nblk((int64_t)r * rnew), 256, 0, st>>>(r, rnew, f->Sk.as<double>(), nM, EW, rnew);
       FKF_LAUNCHED(ctx);
-      if (mp > 0) FKF_TRY(gemm_f64(ctx, false, false, r, rnew, mlam, -1.0, P, mlam, J, rnew, 1.0, EW, rnew));
+      if (mp > 0) FKF_TRY(gemm_merge(ctx, false, false, r, rnew, mlam, -1.0, P, mlam, J, rnew, 1.0, EW, rnew));
     }
   }
   FKF_CUDA(ctx, cudaEventRecord(f->ev[5], st));
@@ -1577,6 +1596,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
   FKF_CUDA(ctx, cudaGetLastError());
   FKF_TRY(hmat_tc_check(h));
   FKF_TRY(tc_gemm_check(ctx, f->rot));
+  FKF_TRY(gemm_f64_tc_check(ctx));
   // ---- commit
   std::swap(f->s_hat.p, f->s_new.p);
   std::swap(f->D.p, f->Dn.p);
