@@ -57,17 +57,19 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
   }
   __syncthreads();
   for (int j = 0; j < b; j++) {
-    if (t == 0) {
+    // the pivot's square root and reciprocal by one warp (FP64 division is a
+    // long instruction sequence on this part: the other warps do not repeat it)
+    if (t < 32) {
       double d = a[j][j];
       if (!(d > 0.0)) {
-        atomicOr(flag, 1);
+        if (t == 0) atomicOr(flag, 1);
         d = 1.0;
       }
-      a[j][j] = sqrt(d);
+      const double sq = sqrt(d);
+      const double inv = 1.0 / sq;
+      if (t > j && t < b) a[t][j] *= inv;
+      if (t == j) a[j][j] = sq;
     }
-    __syncthreads();
-    const double inv = 1.0 / a[j][j];
-    if (t > j && t < b) a[t][j] *= inv;
     __syncthreads();
     // a[i][l] -= a[i][j] a[l][j] for j < l <= i < b
     const int cnt = (b - j - 1) * (b - j) / 2;
@@ -348,9 +350,19 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       const int rem2 = rem - b1;
       FKF_CUDA(ctx, cudaStreamWaitEvent(bs, evT[k], 0));
       const int64_t skip2 = nf < n ? nf - (k0 + b + b1) : -1;
-      if (rem2 > 0 && skip2 != 0)
-        FKF_TRY(gemm_sym_f64(ctx, false, true, rem2, b, -1.0, P + (int64_t)b1 * lda, lda, P + (int64_t)b1 * lda, lda,
-                             1.0, C + (int64_t)b1 * lda + b1, lda, true, skip2));
+      if (rem2 > 0 && skip2 != 0) {
+        // the columns left of A22 (all of them without a border): large updates as one FP64
+        // GEMM on the tensor cores over the whole rectangle (the upper triangle of the part
+        // still to be factored is scratch), the others on the lower triangle alone
+        const int64_t ncol = skip2 > 0 ? std::min<int64_t>(skip2, rem2) : rem2;
+        double* P2 = P + (int64_t)b1 * lda;
+        if ((double)rem2 * ncol * b >= 1.6e7 && cdiv(rem2, 128) * cdiv(ncol, 64) >= 16)
+          FKF_TRY(gemm_f64_tc(ctx, false, true, rem2, ncol, b, -1.0, P2, lda, P2, lda, 1.0, C + (int64_t)b1 * lda + b1,
+                              lda));
+        else
+          FKF_TRY(gemm_sym_f64(ctx, false, true, rem2, b, -1.0, P2, lda, P2, lda, 1.0, C + (int64_t)b1 * lda + b1, lda,
+                               true, skip2));
+      }
       FKF_CUDA(ctx, cudaEventRecord(evS[k], bs));
     }
     return FKF_OK;
