@@ -385,7 +385,13 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       FKF_CUDA(ctx, cudaStreamWaitEvent(ctx->side_lo, fac, 0));
       const cudaStream_t saved = ctx->stream;
       ctx->stream = ctx->side_lo;
-      const fkf_status ss = gemm_sym_f64(ctx, false, true, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda, true);
+      // (large: one FP64 GEMM on the tensor cores with the low-priority stream's
+      // workspace, both triangles; else the lower triangle on the FP64 tile GEMM)
+      const fkf_status ss =
+          (double)(n - nf) * (n - nf) * nf >= 1e8
+              ? gemm_f64_tc(ctx, false, true, n - nf, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda,
+                            &ctx->ozgemm_ws_lo)
+              : gemm_sym_f64(ctx, false, true, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda, true);
       ctx->stream = saved;
       FKF_TRY(ss);
       FKF_CUDA(ctx, cudaEventRecord(schur_done, ctx->side_lo));

@@ -68,7 +68,8 @@ struct fkf_ctx {
   std::atomic<int64_t> lib_calls{0};  // cuSOLVER routine calls
   DevBuf solver_info;  // status word for cuSOLVER calls
   TcGemmWs gemm_ws;    // fkf_rotate_f32
-  OzGemmWs ozgemm_ws;  // FP64 GEMMs on the tensor cores (gemm_f64_tc)
+  OzGemmWs ozgemm_ws;  // FP64 GEMMs on the tensor cores (gemm_f64_tc) on the context stream
+  OzGemmWs ozgemm_ws_lo;  // the same on the low-priority stream (concurrent with the context stream)
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
   cudaStream_t side_lo = nullptr;     // low-priority stream for work that fills SMs beside a persistent kernel
   // When set, the tensor-core H-apply on this context records ph2_mark on the
@@ -364,7 +365,8 @@ fkf_status hmat_oz_prepare(fkf_hmat* h);
 // expired pipeline wait through the context's GEMM error flag (checked by
 // gemm_f64_tc_check).
 fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc);
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                       OzGemmWs* ws = nullptr);
 fkf_status gemm_f64_tc_check(fkf_ctx* ctx);
 
 // happly_tc.cu

@@ -829,10 +829,11 @@ fkf_status hmat_apply_clustered_oz(fkf_hmat* h, const double* X, int64_t ldx, do
 }
 
 fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                       OzGemmWs* wsp) {
   if (M <= 0 || N <= 0) return FKF_OK;
   if (K <= 0 || alpha == 0.0) return beta == 1.0 ? FKF_OK : scale_f64(ctx, M, N, beta, C, ldc);
-  OzGemmWs& ws = ctx->ozgemm_ws;
+  OzGemmWs& ws = wsp ? *wsp : ctx->ozgemm_ws;
   const int nch = (int)cdiv(K, kK);
   const int64_t nrt = cdiv(M, kM), nct = cdiv(N, kN);
   const size_t abytes = (size_t)nrt * nch * kAChunk, bbytes = (size_t)nct * nch * kBChunk;
@@ -865,14 +866,19 @@ fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int
 }
 
 fkf_status gemm_f64_tc_check(fkf_ctx* ctx) {
-  OzGemmWs& ws = ctx->ozgemm_ws;
-  if (!ws.ctl.p) return FKF_OK;
-  int e = 0;
-  FKF_CUDA(ctx, cudaMemcpyAsync(&e, ws.ctl.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
-  FKF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (e) {
-    FKF_CUDA(ctx, cudaMemsetAsync(ws.ctl.p, 0, 4, ctx->stream));
-    return set_err(ctx, FKF_ETIMEOUT, "FP64 tensor-core GEMM: an mbarrier wait expired");
+  // the context stream's GEMMs, then the low-priority stream's
+  const cudaStream_t streams[2] = {ctx->stream, ctx->side_lo};
+  OzGemmWs* wss[2] = {&ctx->ozgemm_ws, &ctx->ozgemm_ws_lo};
+  for (int i = 0; i < 2; i++) {
+    if (!wss[i]->ctl.p || !streams[i]) continue;
+    int e = 0;
+    FKF_CUDA(ctx, cudaMemcpyAsync(&e, wss[i]->ctl.p, 4, cudaMemcpyDeviceToHost, streams[i]));
+    FKF_CUDA(ctx, cudaStreamSynchronize(streams[i]));
+    if (e) {
+      FKF_CUDA(ctx, cudaMemsetAsync(wss[i]->ctl.p, 0, 4, streams[i]));
+      FKF_CUDA(ctx, cudaStreamSynchronize(streams[i]));
+      return set_err(ctx, FKF_ETIMEOUT, "FP64 tensor-core GEMM: an mbarrier wait expired");
+    }
   }
   return FKF_OK;
 }
