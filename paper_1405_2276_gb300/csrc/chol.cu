@@ -356,7 +356,7 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
         // still to be factored is scratch), the others on the lower triangle alone
         const int64_t ncol = skip2 > 0 ? std::min<int64_t>(skip2, rem2) : rem2;
         double* P2 = P + (int64_t)b1 * lda;
-        if ((double)rem2 * ncol * b >= 1.6e7 && cdiv(rem2, 128) * cdiv(ncol, 64) >= 16)
+        if (ctx->fp64_tc && (double)rem2 * ncol * b >= 1.6e7 && cdiv(rem2, 128) * cdiv(ncol, 64) >= 16)
           FKF_TRY(gemm_f64_tc(ctx, false, true, rem2, ncol, b, -1.0, P2, lda, P2, lda, 1.0, C + (int64_t)b1 * lda + b1,
                               lda));
         else
@@ -388,7 +388,7 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       // (large: one FP64 GEMM on the tensor cores with the low-priority stream's
       // workspace, both triangles; else the lower triangle on the FP64 tile GEMM)
       const fkf_status ss =
-          (double)(n - nf) * (n - nf) * nf >= 1e8
+          ctx->fp64_tc && (double)(n - nf) * (n - nf) * nf >= 1e8
               ? gemm_f64_tc(ctx, false, true, n - nf, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda,
                             &ctx->ozgemm_ws_lo)
               : gemm_sym_f64(ctx, false, true, n - nf, nf, -1.0, L21, lda, L21, lda, 1.0, A22, lda, true);

@@ -70,6 +70,11 @@ struct fkf_ctx {
   TcGemmWs gemm_ws;    // fkf_rotate_f32
   OzGemmWs ozgemm_ws;  // FP64 GEMMs on the tensor cores (gemm_f64_tc) on the context stream
   OzGemmWs ozgemm_ws_lo;  // the same on the low-priority stream (concurrent with the context stream)
+  // Whether the dense FP64 algebra may run its large products on the tensor
+  // cores (49-bit slices; gemm_f64_tc).  Filters with an FP64 state clear it for
+  // the duration of their operations: there the products with cancellation
+  // (Schur complements, I - P^T P, basis tests) keep exact FP64 arithmetic.
+  bool fp64_tc = true;
   cudaStream_t side = nullptr;        // high-priority second stream for critical-path work (created on first use)
   cudaStream_t side_lo = nullptr;     // low-priority stream for work that fills SMs beside a persistent kernel
   // When set, the tensor-core H-apply on this context records ph2_mark on the

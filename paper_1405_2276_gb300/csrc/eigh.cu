@@ -976,7 +976,7 @@ void build_tree(int off, int s, std::vector<Node>& merges, std::vector<int>& lof
 static fkf_status gemm_big(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
                            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                            int64_t ldc) {
-  if ((double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
+  if (ctx->fp64_tc && (double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
     return gemm_f64_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   return gemm_f64(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
@@ -1082,7 +1082,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
     if (j1 < N) {
       // A[j1:, j1:] -= [V W] [W V]^T = V W^T + W V^T (large trailing blocks on the tensor
       // cores: both triangles computed, symmetric to rounding; the panel kernel reads rows)
-      if (N - j1 >= 512)
+      if (ctx->fp64_tc && N - j1 >= 512)
         FKF_TRY(gemm_f64_tc(ctx, false, true, N - j1, N - j1, L, -1.0, VW + j1 * L, L, WV + j1 * L, L, 1.0,
                             A + j1 * N + j1, N));
       else
@@ -1160,7 +1160,7 @@ fkf_status eigh_own(fkf_ctx* ctx, int n, double* A, double* w_dev, std::vector<d
       FKF_LAUNCHED(ctx);
       double* Xs = X + (j0 + 1) * k;
       // X[j0+1:] -= V (T (V^T X[j0+1:]))
-      if ((double)nbp * k * rows >= 1e8 && cdiv(k, 64) >= 16)
+      if (ctx->fp64_tc && (double)nbp * k * rows >= 1e8 && cdiv(k, 64) >= 16)
         FKF_TRY(gemm_f64_tc(ctx, true, false, nbp, k, rows, 1.0, Vp, nbp, Xs, k, 0.0, Y1, k));
       else
         FKF_TRY(gram_f64(ctx, nbp, k, rows, Vp, nbp, Xs, k, Y1, k, gws));

@@ -955,10 +955,20 @@ fkf_status gemm_T<float>(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, i
 static fkf_status gemm_merge(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
                              const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                              int64_t ldc) {
-  if ((double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
+  if (ctx->fp64_tc && (double)M * N * K >= 1e8 && cdiv(M, 128) * cdiv(N, 64) >= 16)
     return gemm_f64_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   return gemm_f64(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
+
+// For the scope of a filter operation: the tensor-core FP64 products only for
+// an FP32 state (an FP64 state keeps exact FP64 arithmetic in its m x m and
+// r x r algebra, where products with cancellation decide ranks).
+struct Fp64TcScope {
+  fkf_ctx* ctx;
+  bool saved;
+  Fp64TcScope(fkf_ctx* c, bool allow) : ctx(c), saved(c->fp64_tc) { ctx->fp64_tc = saved && allow; }
+  ~Fp64TcScope() { ctx->fp64_tc = saved; }
+};
 
 static fkf_status gram_T(fkf_ctx* ctx, size_t w, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                          const void* B, int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
@@ -1508,7 +1518,7 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
       FKF_LAUNCHED(ctx);
     }
     // (the eigensolver symmetrises M: the tensor-core product's rounding asymmetry is harmless)
-    if ((double)nM * nM * mlam >= 1e8)
+    if (ctx->fp64_tc && (double)nM * nM * mlam >= 1e8)
       FKF_TRY(gemm_f64_tc(ctx, false, true, nM, nM, mlam, 1.0, f->ZL.as<double>(), mlam, f->ZL.as<double>(), mlam,
                           0.0, M, nM));
     else
@@ -1626,6 +1636,7 @@ fkf_status filter_step(fkf_filter* f, const double* y, int m, const int64_t* row
                        double boxcox_a) {
   if (!(boxcox_a >= 0.0) || !std::isfinite(boxcox_a))
     return set_err(f->ctx, FKF_EINVAL, "filter_step: Box-Cox parameter must be finite and >= 0 (0: linear)");
+  Fp64TcScope tc(f->ctx, f->w == 4);
   const fkf_status st =
       f->w == 8 ? step_impl<double>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out, boxcox_a)
                 : step_impl<float>(f, y, m, rowptr, col, val, R, r_scalar, flags, nll_out, boxcox_a);
@@ -1686,6 +1697,7 @@ static fkf_status canonicalize(fkf_filter* f) {
     f->diag = true;
     return FKF_OK;
   }
+  Fp64TcScope tc(f->ctx, f->w == 4);
   if (f->w == 8) return canonicalize_impl<double>(f);
   return canonicalize_impl<float>(f);
 }
@@ -1911,6 +1923,7 @@ static fkf_status refresh_impl(fkf_filter* f) {
 }
 
 fkf_status filter_refresh(fkf_filter* f) {
+  Fp64TcScope tc(f->ctx, f->w == 4);
   FKF_TRY(canonicalize(f));
   if (f->w == 8) return refresh_impl<double>(f);
   return refresh_impl<float>(f);
@@ -2321,6 +2334,7 @@ fkf_status filter_nll_gradient(fkf_hmat* h, int K, int m, const double* y, const
                                const double* val, double rho, const double* s0, double alpha0, double* nll,
                                double* gy, double* gs0, double* gsig, double* grho) {
   fkf_ctx* ctx = h->ctx;
+  Fp64TcScope tc(ctx, false);  // the adjoint's data-space recursion keeps exact FP64 products
   if (K < 1 || m < 1) return set_err(ctx, FKF_EINVAL, "nll_gradient: K >= 1 and m >= 1 required");
   if (!(rho > 0) || !(alpha0 >= 0)) return set_err(ctx, FKF_EINVAL, "nll_gradient: rho > 0 and alpha0 >= 0 required");
   if (rowptr[0] != 0) return set_err(ctx, FKF_EINVAL, "nll_gradient: rowptr[0] must be 0");

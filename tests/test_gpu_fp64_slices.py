@@ -197,3 +197,21 @@ def test_gemm_f64_on_tensor_cores(fkf, M, N, K, ta, tb, beta):
     print(f"gemm {M}x{N}x{K} ta={ta} tb={tb} beta={beta}: max err / (K max|a| max|b|) {err:.2e}")
     assert err < 2.0 ** -47
     fkf.fkf_destroy(ctx)
+
+
+def test_gemm_f64_rejects_bad_arguments(fkf):
+    import torch
+
+    ctx = fkf.fkf_create(0)
+    A = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    B = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(fkf.FkfError) as e:  # C overlaps A
+        fkf.fkf_gemm_f64(ctx, A, B, A)
+    assert e.value.status == fkf.FKF_EINVAL
+    with pytest.raises(fkf.FkfError):  # leading dimension below the row length
+        fkf._check(fkf._lib.fkf_gemm_f64(ctx.ptr, 0, 0, 8, 8, 8, 1.0, fkf._ptr(A), 4, fkf._ptr(B), 8, 0.0,
+                                         fkf._ptr(torch.zeros((8, 8), dtype=torch.float64, device="cuda")), 8), ctx)
+    C = torch.ones((8, 8), dtype=torch.float64, device="cuda")
+    fkf.fkf_gemm_f64(ctx, A[:, :0], B[:0, :], C, beta=2.0)  # K = 0: C = beta C
+    assert torch.equal(C, torch.full((8, 8), 2.0, dtype=torch.float64, device="cuda"))
+    fkf.fkf_destroy(ctx)
