@@ -369,6 +369,7 @@ def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
         paths.append(fkf.fkf_filter_get_stats(f)["last_path"])
     assert paths == [0, 1, 1, 1, 0, 1, 1, 1]
     assert fkf.fkf_filter_get_stats(f)["diagonal"] == 0
+    assert fkf.fkf_library_call_count(ctx) == len(seq)  # one vendor routine per step: the innovation solve
     import torch
 
     n = pts.shape[0]
@@ -381,6 +382,35 @@ def test_kept_basis_steps_then_new_operator_match_dense_kf(fkf):
     assert rel_err(st["s"], ref[-1]["s"]) < 1e-10
     assert rel_err(Sig, ref[-1]["Sigma"]) < 1e-10
     np.testing.assert_allclose(W.T @ np.linalg.solve(G, W), np.eye(W.shape[1]), atol=1e-8)
+    fkf.fkf_filter_destroy(f)
+    fkf.fkf_hmatrix_destroy(hm)
+    fkf.fkf_destroy(ctx)
+
+
+def test_innovation_solve_ragged_blocks_match_dense_kf(fkf):
+    """m = 97 and 161 rays: the blocked Cholesky factorisation of the
+    innovation system (bordered on the kept-basis steps) runs over several
+    32-row blocks with a ragged last block; NLL and mean against the dense
+    oracle at 1e-10, and exactly one vendor routine (the innovation solve) per
+    step."""
+    rng = np.random.default_rng(synth.BASE_SEED + 21)
+    nx = ny = 20
+    pts = synth.grid_points_2d(nx, ny)
+    Ha, Hb = synth.varying_ray_operators(rng, nx, ny, [97, 161])
+    seq = [Ha, Ha, Hb, Hb]
+    ys = [rng.standard_normal(h.nrows) * 0.3 for h in seq]
+    G = covariance.dense_gamma(pts, 1.5, 0.25, 1.0)
+    ref = kalman.kf_dense(G, [(ys[k], synth.csr_to_dense(h), 1e-4) for k, h in enumerate(seq)])
+    ctx = fkf.fkf_create(0)
+    hm = fkf.fkf_hmatrix_build(ctx, pts, 1.5, 0.25, 1.0, leaf=32, eta=0.0)
+    f = fkf.fkf_filter_create(hm, None, 0.0, 1e-12, 161, 400)
+    for k, h in enumerate(seq):
+        nll = fkf.fkf_filter_step(f, ys[k], h.nrows, h.rowptr, h.col, h.val, None, 1e-4)
+        assert abs(nll - ref[k]["nll"]) < 1e-10 * abs(ref[k]["nll"]), k
+    n = pts.shape[0]
+    st = fkf.fkf_filter_get(f, n)
+    assert rel_err(st["s"], ref[-1]["s"]) < 1e-10
+    assert fkf.fkf_library_call_count(ctx) == len(seq)
     fkf.fkf_filter_destroy(f)
     fkf.fkf_hmatrix_destroy(hm)
     fkf.fkf_destroy(ctx)
