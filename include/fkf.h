@@ -312,6 +312,9 @@ void fkf_filter_destroy(fkf_filter* f);
                                        byte-identical to the previous step's and that step kept the
                                        basis, reuse its products G = Gamma_H H^T and H [W G] instead
                                        of recomputing them (no densify, no H-apply, no gathers) */
+#define FKF_STEP_DENSE_HT 16        /* give the H-apply a dense H^T even where its FP16 split engine
+                                       would take H^T straight from the sparse column index (same
+                                       result, bit for bit; for checks and measurements) */
 
 /* One predict + update (Sec. 2.4 / Alg. extkalman without linearisation):
  *   y (m), H_k as CSR m x N (rowptr int64 m+1, col int32 original point

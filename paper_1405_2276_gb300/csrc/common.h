@@ -58,6 +58,8 @@ struct OzGemmWs {
   DevBuf as, bs, sc, ctl;
 };
 
+struct TcSparseX;  // a sparse X for the tensor-core H-apply (below)
+
 struct fkf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -85,6 +87,10 @@ struct fkf_ctx {
   // X (ncols unsigned, ordered float bits), already computed on the context
   // stream by the caller: the apply uses them instead of scanning X.
   const unsigned* x_colmax = nullptr;
+  // When set (with x_colmax), X of the next tensor-core H-apply on this
+  // context is this sparse matrix and the X argument is not read: the FP16
+  // split engine scatters its entries straight into the split format.
+  const TcSparseX* x_sparse = nullptr;
   std::vector<cudaEvent_t> side_ev;   // events ordering the two streams
   TcMultiWs multi_ws;                 // merged H-applies of batched steps launched on this context
 };
@@ -326,6 +332,12 @@ struct fkf_hmat {
   int tca_fmt = 0;       // format the split operator stream holds (1, 2)
   int tc_variant = 0;    // pipeline shape of the FP16 engine (0: 4 chunks x 2 stages, 1: 2 x 4; hmat_autotune)
   int zsplit_fmt = 0;    // format last written to the split slot workspace
+  // sparse splits of X (FP16 engine): chunk of each cluster-order row, and the
+  // byte offsets the last sparse split wrote (xs_count of them, in a split of
+  // xs_nct column tiles; xs_count < 0: the split X holds other data)
+  DevBuf tc_rowchunk, xs_pos;
+  int64_t xs_count = -1;
+  int xs_nct = 0;
   int engine = 0;  // 0: SIMT tile engine; tensor cores: 1 = 3xTF32, 2 = scaled 2xFP16 (FP32 operators),
                    // 3 = integer slices (FP64 operators)
   // engine 3 (FP64 operators): schedule, scales, sliced operator stream,
@@ -374,7 +386,21 @@ fkf_status gemm_f64_tc(fkf_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int
                        OzGemmWs* ws = nullptr);
 fkf_status gemm_f64_tc_check(fkf_ctx* ctx);
 
+// A sparse X (N x ncols, cluster order) given by its rows: row i holds the
+// entries (crow[p], cval[p]) for colptr[i] <= p < colptr[i + 1], sorted by
+// column, repeated columns summed in FP32 in that order (the CSC index of H,
+// whose columns are the rows of X = H^T).
+struct TcSparseX {
+  int64_t n, nnz;
+  const int64_t* colptr;
+  const int* crow;
+  const double* cval;
+};
+
 // happly_tc.cu
+// True when an apply of ncols columns on this operator can take a sparse X
+// (ctx->x_sparse): FP32 operator on the FP16 split engine, one column pass.
+bool hmat_sparse_x_ok(const fkf_hmat* h, int64_t ncols);
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols);
 fkf_status hmat_tc_check(fkf_hmat* h);
 void hmat_build_tc_schedule(const std::vector<P2Leaf>& leaves, const std::vector<P2Seg>& segs,

@@ -212,6 +212,21 @@ __global__ void k_densify_csc(int64_t n, const int64_t* __restrict__ colptr, con
       atomicMax(&cmax[crow[p]], __float_as_uint(fabsf((float)row[crow[p]])));
 }
 
+// The column maxima k_densify_csc<float> would record, without writing H^T:
+// per row of H^T, each column's entries summed in FP32 in their order.
+__global__ void k_csc_colmax(int64_t n, const int64_t* __restrict__ colptr, const int* __restrict__ crow,
+                             const double* __restrict__ cval, unsigned* __restrict__ cmax) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p1 = colptr[i + 1];
+  for (int64_t p = colptr[i]; p < p1;) {
+    const int c = crow[p];
+    float v = 0.f;
+    for (; p < p1 && crow[p] == c; p++) v += (float)cval[p];
+    atomicMax(&cmax[c], __float_as_uint(fabsf(v)));
+  }
+}
+
 // out (m x ncols, FP64) = H * src[:, 0:ncols]  (src rows in cluster order)
 // out[j, c] = sum_p val[p] * src[iperm[col[p]], c] for the rows j of a CSR
 // matrix (c < ncols).  One CTA per (row, column block); the row's (index,
@@ -1258,11 +1273,18 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     FKF_LAUNCHED(ctx);
     k_csc_sort<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>());
     FKF_LAUNCHED(ctx);
-    FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
     unsigned* xcmax = sizeof(T) == 4 ? f->xcmax.as<unsigned>() : nullptr;  // the FP32 split's column scales
     if (xcmax) FKF_CUDA(ctx, cudaMemsetAsync(xcmax, 0, (size_t)m * sizeof(unsigned), st));
-    k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
-                                                        f->cval.as<double>(), f->Bt.as<T>(), m, xcmax);
+    // the FP16 split engine takes H^T straight from the CSC index (no dense H^T)
+    const bool sparse_x = sizeof(T) == 4 && !(flags & FKF_STEP_DENSE_HT) && hmat_sparse_x_ok(h, m);
+    if (sparse_x) {
+      k_csc_colmax<<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
+                                                     f->cval.as<double>(), xcmax);
+    } else {
+      FKF_CUDA(ctx, cudaMemsetAsync(f->Bt.p, 0, (size_t)n * m * sizeof(T), st));
+      k_densify_csc<T><<<(int)cdiv(n, 256), 256, 0, st>>>(n, f->colptr.as<int64_t>(), f->crow.as<int>(),
+                                                          f->cval.as<double>(), f->Bt.as<T>(), m, xcmax);
+    }
     FKF_LAUNCHED(ctx);
     // ---- gather HW = H W (needs no product with Gamma)
     csr_gather<T>(m, rowptr, col, val, iperm, n, Wc, ld, r, HWA, nm, st);
@@ -1273,11 +1295,14 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     ctx->ph2_mark = r > 0 ? f->ev_hw : nullptr;
     ctx->ph2_marked = false;
     ctx->x_colmax = xcmax;
+    const TcSparseX sx{n, nnz, f->colptr.as<int64_t>(), f->crow.as<int>(), f->cval.as<double>()};
+    ctx->x_sparse = sparse_x ? &sx : nullptr;
     const fkf_status ast = hmat_apply_step(h, f->Bt.p, m, G, ld, m);
     const bool marked = ctx->ph2_marked;
     ctx->ph2_mark = nullptr;
     ctx->ph2_marked = false;
     ctx->x_colmax = nullptr;
+    ctx->x_sparse = nullptr;
     FKF_TRY(ast);
     if (r > 0 && !marked) FKF_CUDA(ctx, cudaEventRecord(f->ev_hw, st));
     FKF_TRY(weight_products(f, m, HWA, nm));

@@ -305,6 +305,65 @@ __global__ void __launch_bounds__(256) k_tc_split_x(const float* __restrict__ X,
   }
 }
 
+// Sparse X (TcSparseX) into the split format of k_tc_split_x: thread per row
+// i of X, the row's entries summed per column in their order (as a dense X
+// built by adding them to a zero row would hold), times the column scale,
+// split into the row's chunk; pos[p] receives the byte offset of the hi
+// element written for entry p (repeated columns repeat it).  The rest of the
+// split X must already be zero.
+template <int F>
+__global__ void __launch_bounds__(256) k_tc_scatter_x(int64_t n, const int64_t* __restrict__ colptr,
+                                                      const int* __restrict__ crow, const double* __restrict__ cval,
+                                                      int nct, const int* __restrict__ rowchunk,
+                                                      const TcXChunk* __restrict__ xmap,
+                                                      const float* __restrict__ cscale, uint8_t* __restrict__ out,
+                                                      int64_t* __restrict__ pos) {
+  using G = Geo<F>;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p1 = colptr[i + 1];
+  const int c = rowchunk[i];
+  const int k = (int)(i - xmap[c].row0);
+  for (int64_t p = colptr[i]; p < p1;) {
+    const int col = crow[p];
+    float v = 0.f;
+    int64_t q = p;
+    for (; q < p1 && crow[q] == col; q++) v += (float)cval[q];
+    const int64_t base = ((int64_t)c * nct + col / kN) * G::kBChunk;
+    put1<F>(out + base, col % kN, k, v * cscale[col]);
+    const int64_t at = base + G::off(col % kN, k);
+    for (; p < q; p++) pos[p] = at;
+  }
+}
+
+// Zero the elements (hi and lo) a previous sparse split wrote: pos holds
+// their offsets, -1 for entries that wrote none (dropped indices); offsets
+// outside the split X of `bytes` bytes are skipped.
+template <int F>
+__global__ void k_tc_clear_x(const int64_t* __restrict__ pos, int64_t cnt, uint8_t* __restrict__ out,
+                             int64_t bytes) {
+  using G = Geo<F>;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const int64_t at = pos[i];
+  if (at < 0 || (at & (G::kEl - 1)) || at + G::kBBytes + G::kEl > bytes) return;
+  if constexpr (G::kEl == 2) {
+    *reinterpret_cast<uint16_t*>(out + at) = 0;
+    *reinterpret_cast<uint16_t*>(out + at + G::kBBytes) = 0;
+  } else {
+    *reinterpret_cast<uint32_t*>(out + at) = 0;
+    *reinterpret_cast<uint32_t*>(out + at + G::kBBytes) = 0;
+  }
+}
+
+// Chunk of every row of X (each X chunk holds rows [row0, row0 + rows)).
+__global__ void k_tc_rowchunk(const TcXChunk* __restrict__ xmap, int64_t nx, int* __restrict__ rowchunk) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nx) return;
+  const TcXChunk x = xmap[c];
+  for (int k = 0; k < x.rows; k++) rowchunk[x.row0 + k] = (int)c;
+}
+
 // Column maxima of |X| (rows x ncols, ld ldx) as ordered float bits; grid
 // (column blocks of 256, row blocks).
 __global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ X, int64_t ldx, int64_t rows, int ncols,
@@ -1040,7 +1099,10 @@ fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
   const int64_t P = h->tc_panel;
   const int64_t nct_max = cdiv(std::min(nc, P), kN);
   const size_t xbytes = (size_t)std::max<int64_t>(h->n_tcx, 1) * nct_max * G::kBChunk;
-  if (h->xsplit.bytes < xbytes) FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
+  if (h->xsplit.bytes < xbytes) {
+    h->xs_count = -1;  // fresh memory: no known zero pattern
+    FKF_TRY(dev_alloc(ctx, h->xsplit, xbytes));
+  }
   const size_t zbytes = (size_t)std::max<int64_t>(h->n_tcz, 1) * nct_max * G::kBChunk;
   if (h->zsplit.bytes < zbytes || h->zsplit_fmt != fmt_of(F)) {
     // padding slots of the split workspace are never written: they start (and stay) zero
@@ -1065,6 +1127,7 @@ fkf_status tc_buffers(fkf_hmat* h, int64_t nc, cudaStream_t st) {
 template <int F>
 fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaStream_t st, float*& cs,
                          const unsigned* cmax_in) {
+  using G = Geo<F>;
   fkf_ctx* ctx = h->ctx;
   const int64_t P = h->tc_panel;
   const int nct = (int)cdiv(nc, kN);
@@ -1083,11 +1146,49 @@ fkf_status tc_split_pass(fkf_hmat* h, const float* X, int64_t ldx, int nc, cudaS
     k_colscale<<<(unsigned)cdiv(nc, 256), 256, 0, st>>>(cmax, nc, cs);
     FKF_LAUNCHED(ctx);
   }
-  if (h->n_tcx > 0) {
+  if (h->n_tcx == 0) return FKF_OK;
+  const TcSparseX* sx = fmt_of(F) == 2 ? h->ctx->x_sparse : nullptr;
+  if (!sx) {
+    h->xs_count = -1;
     k_tc_split_x<F><<<dim3((unsigned)h->n_tcx, (unsigned)nct), 256, 0, st>>>(X, ldx, nc, h->tcxmap.as<TcXChunk>(), 0,
                                                                              nct, cs, h->xsplit.as<uint8_t>());
     FKF_LAUNCHED(ctx);
+    return FKF_OK;
   }
+  // sparse X: zero what the previous sparse split wrote (or all of the pass's
+  // split X when its content is unknown), then scatter the entries
+  if (!cmax_in) return set_err(ctx, FKF_ESTATE, "sparse X without its column maxima");
+  uint8_t* xs = h->xsplit.as<uint8_t>();
+  if (h->tc_rowchunk.bytes < (size_t)h->n * sizeof(int)) {
+    FKF_TRY(dev_alloc(ctx, h->tc_rowchunk, (size_t)h->n * sizeof(int)));
+    k_tc_rowchunk<<<(unsigned)cdiv(h->n_tcx, 256), 256, 0, st>>>(h->tcxmap.as<TcXChunk>(), h->n_tcx,
+                                                                h->tc_rowchunk.as<int>());
+    FKF_LAUNCHED(ctx);
+  }
+  const int64_t xbytes = h->n_tcx * nct * (int64_t)G::kBChunk;
+  const bool known = h->xs_count >= 0 && h->xs_nct == nct;
+  if (known && h->xs_count > 0) {
+    k_tc_clear_x<F><<<(unsigned)cdiv(h->xs_count, 256), 256, 0, st>>>(h->xs_pos.as<int64_t>(), h->xs_count, xs,
+                                                                      xbytes);
+    FKF_LAUNCHED(ctx);
+  }
+  h->xs_count = -1;  // until the scatter below is queued
+  if (!known) FKF_CUDA(ctx, cudaMemsetAsync(xs, 0, (size_t)xbytes, st));
+  if (h->xs_pos.bytes < (size_t)std::max<int64_t>(sx->nnz, 1) * sizeof(int64_t)) {
+    // a larger record: the clear above has read the old one before it is freed
+    FKF_CUDA(ctx, cudaStreamSynchronize(st));
+    FKF_TRY(dev_alloc(ctx, h->xs_pos, (size_t)std::max<int64_t>(sx->nnz, 1) * sizeof(int64_t)));
+  }
+  // entries the CSC index dropped (column index outside [0, N)) record no offset
+  if (sx->nnz > 0) FKF_CUDA(ctx, cudaMemsetAsync(h->xs_pos.p, 0xff, (size_t)sx->nnz * sizeof(int64_t), st));
+  if (sx->n > 0) {
+    k_tc_scatter_x<F><<<(unsigned)cdiv(sx->n, 256), 256, 0, st>>>(sx->n, sx->colptr, sx->crow, sx->cval, nct,
+                                                                   h->tc_rowchunk.as<int>(), h->tcxmap.as<TcXChunk>(),
+                                                                   cs, xs, h->xs_pos.as<int64_t>());
+    FKF_LAUNCHED(ctx);
+  }
+  h->xs_count = sx->nnz;
+  h->xs_nct = nct;
   return FKF_OK;
 }
 
@@ -1121,6 +1222,8 @@ fkf_status apply_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t 
   fkf_ctx* ctx = h->ctx;
   cudaStream_t st = ctx->stream;
   const int64_t P = h->tc_panel;
+  if (ctx->x_sparse && (fmt_of(F) != 2 || ncols > P))
+    return set_err(ctx, FKF_ESTATE, "sparse X needs the FP16 split engine and one column pass");
   FKF_TRY(tc_buffers<F>(h, ncols, st));
   // tile counters of the two phases at tc_err + 16, + 24 bytes
   unsigned long long* counters = reinterpret_cast<unsigned long long*>(h->tc_err.as<char>() + 16);
@@ -1179,6 +1282,8 @@ fkf_status apply_tc_multi(fkf_ctx* ctx, fkf_hmat* const* hs, int nb, const float
   for (int f = 0; f < nb; f++) {
     fkf_hmat* h = hs[f];
     if (ncols[f] <= 0) continue;
+    if (h->ctx->x_sparse && fmt_of(F) != 2)
+      return set_err(ctx, FKF_ESTATE, "sparse X needs the FP16 split engine");
     if (h->tca_fmt != fmt_of(F)) FKF_TRY(build_stream(h, fmt_of(F)));
     FKF_TRY(tc_buffers<F>(h, ncols[f], st));
     const int nc = (int)ncols[f];
@@ -1319,6 +1424,10 @@ fkf_status build_stream(fkf_hmat* h, int F) {
 }
 
 }  // namespace
+
+bool hmat_sparse_x_ok(const fkf_hmat* h, int64_t ncols) {
+  return h->prec == FKF_FP32 && h->engine == 2 && h->n_tcx > 0 && ncols > 0 && ncols <= h->tc_panel;
+}
 
 // Tensor-core apply for an FP32 operator (cluster order).
 fkf_status hmat_apply_clustered_tc(fkf_hmat* h, const float* X, int64_t ldx, float* Y, int64_t ldy, int64_t ncols) {

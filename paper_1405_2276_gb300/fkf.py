@@ -29,6 +29,7 @@ FKF_STEP_INPUTS_ON_DEVICE = 1
 FKF_STEP_SKIP_MEAN_SYNC = 2
 FKF_STEP_FULL_UPDATE = 4
 FKF_STEP_ALLOW_FIXED_H = 8
+FKF_STEP_DENSE_HT = 16
 
 
 class fkf_matern(C.Structure):
