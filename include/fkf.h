@@ -397,6 +397,8 @@ typedef struct {
   int32_t t_eig;      /* 1 if T = I - P^T P was factored (pivoted Cholesky, pivots above
                          orth_tol); 0 if ||T||_F <= orth_tol showed nothing new */
   double t_lmax;      /* ||T||_F, a bound on every eigenvalue of T */
+  int64_t chol_exact_retries; /* innovation factorisations redone with exact FP64 products after
+                                 the tensor-core slice products left a non-positive pivot */
 } fkf_filter_stats;
 fkf_status fkf_filter_get_stats(const fkf_filter* f, fkf_filter_stats* out);
 

@@ -20,7 +20,7 @@
 #include "dense.h"
 
 #ifndef FKF_CHOL_BLOCK
-#define FKF_CHOL_BLOCK 32
+#define FKF_CHOL_BLOCK 64
 #endif
 
 namespace {
@@ -29,11 +29,30 @@ constexpr int kB = FKF_CHOL_BLOCK;  // block size (a multiple of 32, at most 64)
 constexpr int kV = kB / 32;         // columns per lane in the row kernels
 constexpr int kPB = 32;             // pivots per panel of the pivoted Cholesky
 
-// Factor the b x b diagonal block A (ld lda, lower triangle) in place.  A
-// pivot that is not positive sets *flag and is replaced by 1 so that the
-// factorisation completes without NaNs (the caller reports the failure).
+// 1 / sqrt(d) for d > 0 by Newton's iteration for f(r) = r^-2 - d,
+// r <- r + r (1 - d r^2) / 2 (quadratic convergence), seeded with the
+// single-precision hardware estimate rsqrtf (relative error about 2^-22):
+// two steps bring the error below FP64 rounding.  A pivot's square root and
+// reciprocal then cost a handful of FP64 operations instead of a square root
+// and a division (long FP64 sequences on this part).  d outside the
+// single-precision range takes 1 / sqrt(d).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-36 && d < 1e36)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const double e = fma(-(d * r), r, 1.0);  // 1 - d r^2
+    r = fma(0.5 * r, e, r);
+  }
+  return r;
+}
+
+// Factor the b x b diagonal block A (ld lda, lower triangle) in place; the
+// reciprocals of the factor's diagonal go to dinv[0:b].  A pivot that is not
+// positive sets *flag and is replaced by 1 so that the factorisation
+// completes without NaNs (the caller reports the failure).
 __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int64_t lda, int b,
-                                                    int* __restrict__ flag) {
+                                                    int* __restrict__ flag, double* __restrict__ dinv) {
   __shared__ double a[kB][kB + 1];
   // the lower triangle's entries ordered by column, last column first:
   // entry t = (row, column) packed as row << 8 | column, so that the entries
@@ -57,18 +76,21 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
   }
   __syncthreads();
   for (int j = 0; j < b; j++) {
-    // the pivot's square root and reciprocal by one warp (FP64 division is a
-    // long instruction sequence on this part: the other warps do not repeat it)
+    // the pivot's reciprocal square root by one warp (the other warps do not
+    // repeat it): L_jj = d r, column j below it times r = 1 / L_jj
     if (t < 32) {
       double d = a[j][j];
+      __syncwarp();  // every lane has read the pivot before lane 0 overwrites it
       if (!(d > 0.0)) {
         if (t == 0) atomicOr(flag, 1);
         d = 1.0;
       }
-      const double sq = sqrt(d);
-      const double inv = 1.0 / sq;
-      if (t > j && t < b) a[t][j] *= inv;
-      if (t == j) a[j][j] = sq;
+      const double r = rsqrt_newton(d);
+      for (int i = j + 1 + t; i < b; i += 32) a[i][j] *= r;  // (blocks wider than a warp: two rows per lane)
+      if (t == 0) {
+        a[j][j] = d * r;
+        dinv[j] = r;
+      }
     }
     __syncthreads();
     // a[i][l] -= a[i][j] a[l][j] for j < l <= i < b
@@ -91,9 +113,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
 // x_{j+32}, ...: after x_q is final it is broadcast and every later column
 // subtracts its term, so a row costs b dependent steps (FP64 instructions are
 // slow per warp here; many short rows in flight use all the SMs).
+// dinv_g[0:b]: the reciprocals of Lkk's diagonal (from k_potrf_diag).
 constexpr int kRowWarps = 8;
 __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict__ X, int64_t ldx, int64_t rows,
-                                                              int b, const double* __restrict__ L, int64_t lda) {
+                                                              int b, const double* __restrict__ L, int64_t lda,
+                                                              const double* __restrict__ dinv_g) {
   __shared__ double l[kB][kB + 1];
   __shared__ double dinv[kB];
   const int t = threadIdx.x;
@@ -102,8 +126,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_trsm_rows(double* __restrict
     const int i = e / kB, j = e % kB;
     l[i][j] = (i < b && j <= i) ? L[(int64_t)i * lda + j] : 0.0;
   }
-  __syncthreads();
-  if (t < b) dinv[t] = 1.0 / l[t][t];
+  if (t < b) dinv[t] = dinv_g[t];
   __syncthreads();
   const int lane = t & 31;
   const int64_t r = (int64_t)blockIdx.x * kRowWarps + (t >> 5);
@@ -303,8 +326,10 @@ fkf_status pchol_f64(fkf_ctx* ctx, int n, double* A, int64_t lda, double tol, in
 fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda, DevBuf& ws, cudaEvent_t schur_done) {
   if (n <= 0 || nf <= 0) return FKF_OK;
   nf = std::min(nf, n);
-  if (ws.bytes < 256) FKF_TRY(dev_alloc(ctx, ws, 256));
+  // flag, then the reciprocals of the factor's diagonal (one slot per pivot)
+  if (ws.bytes < 64 + (size_t)nf * sizeof(double)) FKF_TRY(dev_alloc(ctx, ws, 64 + (size_t)nf * sizeof(double)));
   int* flag = ws.as<int>();
+  double* dinv = reinterpret_cast<double*>(ws.as<char>() + 64);
   FKF_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   const int nb = (int)cdiv(nf, kB);
   const bool la = nb >= 2 && n - kB > 2 * kB;
@@ -325,13 +350,13 @@ fkf_status chol_blocked_f64(fkf_ctx* ctx, int n, int nf, double* A, int64_t lda,
       const int k0 = k * kB;
       const int b = std::min(kB, nf - k0);
       double* Akk = A + (int64_t)k0 * lda + k0;
-      FKF_CUDA(ctx, launch_pdl(k_potrf_diag, 1, 256, cs, Akk, lda, b, flag));
+      FKF_CUDA(ctx, launch_pdl(k_potrf_diag, 1, 256, cs, Akk, lda, b, flag, dinv + k0));
       FKF_LAUNCHED(ctx);
       const int rem = n - k0 - b;
       if (rem <= 0) continue;
       double* P = A + (int64_t)(k0 + b) * lda + k0;  // rem x b panel
       FKF_CUDA(ctx, launch_pdl(k_trsm_rows, (unsigned)cdiv(rem, kRowWarps), 32 * kRowWarps, cs, P, lda,
-                               (int64_t)rem, b, (const double*)Akk, lda));
+                               (int64_t)rem, b, (const double*)Akk, lda, (const double*)(dinv + k0)));
       FKF_LAUNCHED(ctx);
       double* C = P + b;  // trailing block at (k0 + b, k0 + b)
       // entries of the trailing block in A22 (relative index >= skip) wait for the final product

@@ -776,6 +776,7 @@ struct fkf_filter {
   int64_t ldwg = 0;
   double trunc_tol = 0, gep_tol = 0, orth_tol = 0;
   int64_t k = 0;
+  int64_t chol_exact_retries = 0;  // innovation factorisations redone with exact FP64 products
   double alpha = 0;
   int r = 0;
   int cur = 0;
@@ -807,6 +808,7 @@ struct fkf_filter {
   DevBuf nu, z, uz, vcoef, HWD, nll, dbar, red, scanws;
   DevBuf Lpv, Gm, F1c, pcws;  // pivoted Cholesky of T: factor, its Gram, the solved factor, workspace
   DevBuf eigws, cholws, gramws, tmp1, tmp2, tmp3;
+  DevBuf sbak;  // copy of the innovation system while its factorisation uses slice products
   TcGemmWs rot;       // tensor-core products (FP32 state): the rotation and the basis test
   DevBuf hw32, c32;   // basis test of the FP32 state: HW and HW^T in FP32, HW HW^T
   cudaEvent_t ev[7] = {};
@@ -984,6 +986,29 @@ struct Fp64TcScope {
   Fp64TcScope(fkf_ctx* c, bool allow) : ctx(c), saved(c->fp64_tc) { ctx->fp64_tc = saved && allow; }
   ~Fp64TcScope() { ctx->fp64_tc = saved; }
 };
+
+// The innovation system's blocked Cholesky factorisation (n x n, lda, the
+// first nf pivots; schur_done as chol_blocked_f64).  Its large trailing
+// updates run on the tensor cores with 49-bit slice products when
+// ctx->fp64_tc is set; the Schur complements cancel, and on a system whose
+// conditioning nears the limit of FP64 the slices' rounding can leave a
+// pivot that is not positive where exact FP64 products would not.  The
+// factorisation then starts again from a copy of the system with exact FP64
+// products throughout.
+static fkf_status chol_innovation(fkf_filter* f, int n, int nf, double* A, int64_t lda, cudaEvent_t schur_done) {
+  fkf_ctx* ctx = f->ctx;
+  if (!ctx->fp64_tc) return chol_blocked_f64(ctx, n, nf, A, lda, f->cholws, schur_done);
+  const size_t bytes = (size_t)n * lda * sizeof(double);
+  if (f->sbak.bytes < bytes) FKF_TRY(dev_alloc(ctx, f->sbak, bytes));
+  FKF_CUDA(ctx, cudaMemcpyAsync(f->sbak.p, A, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  const fkf_status st = chol_blocked_f64(ctx, n, nf, A, lda, f->cholws, schur_done);
+  if (st != FKF_ENOTSPD) return st;
+  // (a failed attempt returns with none of its work in flight)
+  FKF_CUDA(ctx, cudaMemcpyAsync(A, f->sbak.p, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  f->chol_exact_retries++;
+  Fp64TcScope exact(ctx, false);
+  return chol_blocked_f64(ctx, n, nf, A, lda, f->cholws, schur_done);
+}
 
 static fkf_status gram_T(fkf_ctx* ctx, size_t w, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                          const void* B, int64_t ldb, double* C, int64_t ldc, DevBuf& ws) {
@@ -1397,9 +1422,9 @@ static fkf_status step_impl(fkf_filter* f, const double* y_in, int m, const int6
     k_aug_rows<<<nblk(lda_aug * r), 256, 0, st>>>(m, r, HW, nm, f->HWD.as<double>(), diag ? f->D.as<double>() : nullptr,
                                                  diag ? nullptr : Dfc, alpha1, Eaug, lda_aug);
     FKF_LAUNCHED(ctx);
-    FKF_TRY(chol_blocked_f64(ctx, m + r, m, S, lda_aug, f->cholws, f->ev_schur));
+    FKF_TRY(chol_innovation(f, m + r, m, S, lda_aug, f->ev_schur));
   } else {
-    FKF_TRY(chol_blocked_f64(ctx, m, m, S, lda_aug, f->cholws));
+    FKF_TRY(chol_innovation(f, m, m, S, lda_aug, nullptr));
   }
   FKF_CUDA(ctx, cudaMemcpyAsync(f->z.p, f->nu.p, m * 8, cudaMemcpyDeviceToDevice, st));
   FKF_TRY(chol_solve_rowlower_f64(ctx, m, S, lda_aug, f->z.as<double>(), 1));
@@ -2059,6 +2084,7 @@ void filter_stats(const fkf_filter* f, fkf_filter_stats* s) {
   s->new_dirs = f->new_dirs;
   s->t_eig = f->t_eig;
   s->t_lmax = f->t_lmax;
+  s->chol_exact_retries = f->chol_exact_retries;
 }
 
 // ---------------------------------------------------------------------------

@@ -64,7 +64,7 @@ class fkf_step_desc(C.Structure):
 class fkf_filter_stats(C.Structure):
     _fields_ = [("k", C.c_int64), ("alpha", C.c_double), ("r", C.c_int32), ("last_path", C.c_int32),
                 ("diagonal", C.c_int32), ("gep_rank", C.c_int32), ("new_dirs", C.c_int32), ("t_eig", C.c_int32),
-                ("t_lmax", C.c_double)]
+                ("t_lmax", C.c_double), ("chol_exact_retries", C.c_int64)]
 
 
 class FkfError(RuntimeError):
