@@ -182,7 +182,8 @@ fkf_status fkf_hmatrix_apply_clustered(fkf_hmat* h, const void* X_dev, int64_t l
  * tile engine here (the same result as engine 0 up to summation order; against
  * engine 3 about 1e-13 relative); an FP32 operator always runs the FP32 SIMT
  * tile engine here, whatever fkf_hmatrix_set_engine chose, so against the
- * default tensor-core apply it agrees to FP32 rounding (about 1e-5 relative).  The slot workspace and the split-reduction partials live in a
+ * default tensor-core apply it agrees to FP32 rounding (about 1e-5 relative).
+ * The slot workspace and the split-reduction partials live in a
  * library-wide static device array of FKF_NOALLOC_SCRATCH_BYTES bytes; the
  * columns are processed in panels as wide as that array allows (at least one
  * column).  An operator that needs more than FKF_NOALLOC_SCRATCH_BYTES for a
